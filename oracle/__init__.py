@@ -1,0 +1,179 @@
+"""FP64 CPU oracle of semi-Lagrangian Metamorphosis / LDDMM shooting.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline call it; the product path (the CUDA library and its binding) never
+does.  It wraps ``meta_oracle.c`` (plain C, FP64) through ctypes.
+
+Functions (arrays are numpy, converted to float64 C-contiguous):
+
+* ``taps(sigma)``                         -- normalised Gaussian taps, r = ceil(3 sigma)
+* ``blur(f, sigma)``                      -- K * f, separable, zero padding
+* ``diff(f, axis, transpose=False)``      -- central difference D_axis (or its transpose)
+* ``interp(F, disp, transpose=False)``    -- S(y) F with y = x + disp (or S(y)^T F)
+* ``shoot(I0, p0, T, sigma, mu, rho)``    -- states (I_t, p_t), t=0..T, and u_t
+* ``adjoint(I0, p0, gI1, gp1, ...)``      -- gradient of <gI1,I_T>+<gp1,p_T> w.r.t. (I0, p0)
+* ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
+
+Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, dot-product
+transpose identities, finite differences, an independent torch re-implementation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "meta_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libmeta_oracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def build(force: bool = False) -> str:
+    """Compile meta_oracle.c into libmeta_oracle.so (gcc, FP64, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.oracle_taps.argtypes = [ctypes.c_double, _D, ctypes.c_int]
+        lib.oracle_taps.restype = ctypes.c_int
+        lib.oracle_blur.argtypes = [ctypes.c_int, _L, ctypes.c_double, _D, _D]
+        lib.oracle_diff.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.oracle_interp.argtypes = [ctypes.c_int, _L, _D, ctypes.c_int, _D, _D]
+        lib.oracle_shoot.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D]
+        lib.oracle_adjoint.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D]
+        lib.oracle_cost_and_grad.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             _D, _D, _D, _D, _D]
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_max_threads.restype = ctypes.c_int
+        for f in ("oracle_blur", "oracle_diff", "oracle_interp", "oracle_shoot",
+                  "oracle_adjoint", "oracle_cost_and_grad"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _dims(shape) -> ctypes.Array:
+    return (ctypes.c_long * len(shape))(*shape)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError("oracle %s failed with code %d" % (what, rc))
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def taps(sigma: float) -> np.ndarray:
+    """w_k, k = -r..r, r = ceil(3 sigma), sum 1 (the Gaussian RKHS kernel, Sec. 2.1)."""
+    buf = np.zeros(4097)
+    r = _load().oracle_taps(float(sigma), _ptr(buf), buf.size)
+    if r < 0:
+        raise ValueError("bad sigma")
+    return buf[: 2 * r + 1].copy()
+
+
+def blur(f, sigma: float) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    _check(_load().oracle_blur(f.ndim, _dims(f.shape), float(sigma), _ptr(f), _ptr(out)), "blur")
+    return out
+
+
+def diff(f, axis: int, transpose: bool = False) -> np.ndarray:
+    f = _f64(f)
+    out = np.empty_like(f)
+    _check(_load().oracle_diff(f.ndim, _dims(f.shape), int(axis), int(transpose),
+                               _ptr(f), _ptr(out)), "diff")
+    return out
+
+
+def interp(F, disp, transpose: bool = False) -> np.ndarray:
+    """disp has shape [ndim, *F.shape]: the foot of voxel x is x + disp[:, x]."""
+    F = _f64(F)
+    disp = _f64(disp)
+    assert disp.shape == (F.ndim,) + F.shape
+    out = np.empty_like(F)
+    _check(_load().oracle_interp(F.ndim, _dims(F.shape), _ptr(disp), int(transpose),
+                                 _ptr(F), _ptr(out)), "interp")
+    return out
+
+
+def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
+          want_u: bool = False) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
+    """Returns (I[T+1, ...], p[T+1, ...], u[T, ndim, ...] or None)."""
+    I0, p0 = _f64(I0), _f64(p0)
+    shp = I0.shape
+    It = np.empty((T + 1,) + shp)
+    pt = np.empty((T + 1,) + shp)
+    ut = np.empty((T, len(shp)) + shp) if want_u else None
+    _check(_load().oracle_shoot(len(shp), _dims(shp), int(T), float(sigma), float(mu),
+                                float(rho), _ptr(I0), _ptr(p0), _ptr(It), _ptr(pt),
+                                _ptr(ut)), "shoot")
+    return It, pt, ut
+
+
+def adjoint(I0, p0, gI1, gp1, T: int, sigma: float, mu: float,
+            rho: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Returns (gI0, gp0) for the scalar <gI1, I_T> + <gp1, p_T>."""
+    I0, p0, gI1 = _f64(I0), _f64(p0), _f64(gI1)
+    gp1 = None if gp1 is None else _f64(gp1)
+    shp = I0.shape
+    gI0 = np.empty(shp)
+    gp0 = np.empty(shp)
+    _check(_load().oracle_adjoint(len(shp), _dims(shp), int(T), float(sigma), float(mu),
+                                  float(rho), _ptr(I0), _ptr(p0), _ptr(gI1), _ptr(gp1),
+                                  _ptr(gI0), _ptr(gp0)), "adjoint")
+    return gI0, gp0
+
+
+def cost_and_grad(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
+                  want_grad: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+    """Returns (cost3 = [data, lambda*kinetic, lambda*rho*residual], dL/dp0 or None)."""
+    I0, J, p0 = _f64(I0), _f64(J), _f64(p0)
+    shp = I0.shape
+    c3 = np.zeros(3)
+    g = np.empty(shp) if want_grad else None
+    _check(_load().oracle_cost_and_grad(len(shp), _dims(shp), int(T), float(sigma), float(mu),
+                                        float(rho), float(lam), _ptr(I0), _ptr(J), _ptr(p0),
+                                        _ptr(c3), _ptr(g)), "cost_and_grad")
+    return c3, g

@@ -1,0 +1,349 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test ties one part of the oracle to a closed form, an invariant of the
+scheme, a transpose identity, finite differences, or an independent
+re-implementation with library primitives (torch conv / grid_sample /
+autograd).  Together they fail on a dropped term, a wrong sign, a wrong axis
+or index, or a transposed operand anywhere in the forward step, the cost or
+the adjoint.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+import phantoms
+
+RNG = np.random.default_rng(12345)
+
+
+def smooth_random(dims, scale, s=1.5, seed=0):
+    r = np.random.default_rng(seed)
+    return ndimage.gaussian_filter(r.normal(size=dims), s) * scale
+
+
+# ----------------------------------------------------------------- taps / K
+
+@pytest.mark.parametrize("sigma", [0.4, 1.0, 2.5, 3.0, 6.0])
+def test_taps_closed_form(sigma):
+    """Gaussian RKHS kernel (Sec. 2.1): w_k / w_0 = exp(-k^2/2sigma^2), sum 1, r = ceil(3 sigma)."""
+    w = oracle.taps(sigma)
+    r = (w.size - 1) // 2
+    assert r == math.ceil(3 * sigma)
+    assert abs(w.sum() - 1.0) < 1e-15
+    k = np.arange(-r, r + 1)
+    np.testing.assert_allclose(w / w[r], np.exp(-k ** 2 / (2 * sigma ** 2)), rtol=1e-14)
+    np.testing.assert_array_equal(w, w[::-1])
+
+
+@pytest.mark.parametrize("dims", [(21, 23), (13, 15, 17)])
+def test_blur_of_delta_is_tap_product(dims):
+    sigma = 1.3
+    w = oracle.taps(sigma)
+    r = (w.size - 1) // 2
+    f = np.zeros(dims)
+    c = tuple(n // 2 for n in dims)
+    f[c] = 1.0
+    out = oracle.blur(f, sigma)
+    expect = np.zeros(dims)
+    sl = tuple(slice(ci - r, ci + r + 1) for ci in c)
+    prod = w
+    for _ in range(len(dims) - 1):
+        prod = np.multiply.outer(prod, w)
+    expect[sl] = prod
+    np.testing.assert_allclose(out, expect, atol=1e-16, rtol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(9, 12), (6, 7, 8)])
+def test_blur_equals_direct_zero_padded_convolution(dims):
+    """Separable passes == brute-force d-D sum over all offsets, zero outside the grid."""
+    sigma = 1.1
+    w = oracle.taps(sigma)
+    r = (w.size - 1) // 2
+    f = RNG.normal(size=dims)
+    out = oracle.blur(f, sigma)
+    direct = np.zeros(dims)
+    for x in itertools.product(*[range(n) for n in dims]):
+        s = 0.0
+        for k in itertools.product(range(-r, r + 1), repeat=len(dims)):
+            q = tuple(xi + ki for xi, ki in zip(x, k))
+            if all(0 <= qi < n for qi, n in zip(q, dims)):
+                s += np.prod([w[ki + r] for ki in k]) * f[q]
+        direct[x] = s
+    np.testing.assert_allclose(out, direct, atol=1e-14)
+
+
+def test_blur_is_symmetric():
+    """<K a, b> = <a, K b>: zero padding keeps K self-adjoint (used by the adjoint)."""
+    for dims in [(17, 19), (7, 9, 8)]:
+        a, b = RNG.normal(size=dims), RNG.normal(size=dims)
+        lhs = (oracle.blur(a, 2.0) * b).sum()
+        rhs = (a * oracle.blur(b, 2.0)).sum()
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ----------------------------------------------------------------- D
+
+def test_diff_on_affine_function():
+    """Central differences are exact on affine data; replicated edges halve them."""
+    dims = (7, 9, 6)
+    X = np.meshgrid(*[np.arange(n, dtype=float) for n in dims], indexing="ij")
+    a = (0.7, -1.3, 2.1)
+    f = 0.4 + sum(ai * xi for ai, xi in zip(a, X))
+    for ax in range(3):
+        d = oracle.diff(f, ax)
+        inner = [slice(None)] * 3
+        inner[ax] = slice(1, -1)
+        np.testing.assert_allclose(d[tuple(inner)], a[ax], rtol=1e-13)
+        for edge in (0, -1):
+            e = [slice(None)] * 3
+            e[ax] = edge
+            np.testing.assert_allclose(d[tuple(e)], a[ax] / 2, rtol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(2, 5), (6, 7), (4, 3, 5)])
+def test_diff_transpose(dims):
+    for ax in range(len(dims)):
+        u, w = RNG.normal(size=dims), RNG.normal(size=dims)
+        lhs = (oracle.diff(u, ax) * w).sum()
+        rhs = (u * oracle.diff(w, ax, transpose=True)).sum()
+        assert abs(lhs - rhs) < 1e-13 * (1 + abs(lhs))
+
+
+# ----------------------------------------------------------------- S(y)
+
+def test_interp_integer_shift_is_exact_with_border_replication():
+    dims = (11, 13)
+    F = RNG.normal(size=dims)
+    s = (2, -3)
+    disp = np.stack([np.full(dims, float(si)) for si in s])
+    out = oracle.interp(F, disp)
+    idx = np.meshgrid(*[np.arange(n) for n in dims], indexing="ij")
+    src = tuple(np.clip(i + si, 0, n - 1) for i, si, n in zip(idx, s, dims))
+    np.testing.assert_array_equal(out, F[src])
+
+
+def test_interp_reproduces_affine_functions():
+    dims = (8, 9, 10)
+    X = np.meshgrid(*[np.arange(n, dtype=float) for n in dims], indexing="ij")
+    a = (0.3, -0.8, 1.7)
+    F = 1.0 + sum(ai * xi for ai, xi in zip(a, X))
+    disp = RNG.uniform(-1.5, 1.5, size=(3,) + dims)
+    feet = [np.clip(xi + di, 0, n - 1) for xi, di, n in zip(X, disp, dims)]
+    expect = 1.0 + sum(ai * yi for ai, yi in zip(a, feet))
+    np.testing.assert_allclose(oracle.interp(F, disp), expect, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(7, 8), (5, 6, 4)])
+def test_interp_transpose(dims):
+    disp = RNG.uniform(-2.5, 2.5, size=(len(dims),) + dims)
+    a, b = RNG.normal(size=dims), RNG.normal(size=dims)
+    lhs = (oracle.interp(a, disp) * b).sum()
+    rhs = (a * oracle.interp(b, disp, transpose=True)).sum()
+    assert abs(lhs - rhs) < 1e-13 * (1 + abs(lhs))
+
+
+def test_interp_zero_displacement_is_identity_bitwise():
+    dims = (6, 9, 5)
+    F = RNG.normal(size=dims)
+    np.testing.assert_array_equal(oracle.interp(F, np.zeros((3,) + dims)), F)
+
+
+# ----------------------------------------------------------------- shooting
+
+def test_zero_momentum_leaves_image_unchanged_bitwise():
+    w = phantoms.disk_pair_64(random_p0=False)
+    It, pt, _ = oracle.shoot(w.I0[0], w.p0[0], w.T, w.sigma, 0.1, 1.0)
+    np.testing.assert_array_equal(It[-1], w.I0[0].astype(np.float64))
+    np.testing.assert_array_equal(pt[-1], 0.0)
+
+
+def test_flat_image_gets_mu_times_momentum():
+    """grad I_0 = 0 => v_0 = 0, y = x: one step of Eq. 1 gives I_1 = I_0 + mu p0, p_1 = p0.
+
+    With a constant p0 the image stays flat, v stays 0 and the T steps add up to
+    I_T = I_0 + mu p0 (dt T = 1)."""
+    dims = (10, 12)
+    I0 = np.full(dims, 0.3)
+    p0 = RNG.normal(size=dims)
+    mu = 0.37
+    It, pt, _ = oracle.shoot(I0, p0, 1, 2.0, mu, 1.0)
+    np.testing.assert_array_equal(pt[-1], p0)
+    np.testing.assert_array_equal(It[-1], I0 + mu * p0)
+    It, pt, _ = oracle.shoot(I0, np.full(dims, -0.8), 8, 2.0, mu, 1.0)
+    np.testing.assert_array_equal(pt[-1], -0.8)
+    np.testing.assert_allclose(It[-1], 0.3 - mu * 0.8, rtol=1e-14)
+
+
+def test_lddmm_is_pure_transport():
+    """mu = 0: every update is a convex combination, so min I0 <= I_T <= max I0."""
+    I, _ = phantoms.random_fields(3, 1, (24, 20))
+    p = smooth_random((24, 20), 200.0)
+    It, _, ut = oracle.shoot(I[0], p, 6, 2.0, 0.0, 1.0, want_u=True)
+    assert np.abs(ut).max() / 6 > 0.15  # non-trivial displacements
+    assert It[-1].min() >= I[0].min() - 1e-15 and It[-1].max() <= I[0].max() + 1e-15
+    assert np.abs(It[-1] - I[0]).max() > 1e-2
+
+
+def test_rho_rescaling_invariance():
+    """(rho, mu, p0) and (1, mu/rho, rho p0) give the same I_T and p_T scaled by rho."""
+    I, _ = phantoms.random_fields(4, 1, (18, 16))
+    p = smooth_random((18, 16), 15.0)
+    rho, mu = 2.5, 0.4
+    A = oracle.shoot(I[0], p, 5, 1.5, mu, rho)
+    B = oracle.shoot(I[0], rho * p, 5, 1.5, mu / rho, 1.0)
+    np.testing.assert_allclose(A[0][-1], B[0][-1], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(rho * A[1][-1], B[1][-1], rtol=1e-12, atol=1e-13)
+
+
+def test_integer_translation_equivariance():
+    dims = (40, 44)
+    I = np.zeros(dims)
+    p = np.zeros(dims)
+    core_I = ndimage.gaussian_filter(RNG.uniform(size=(8, 8)), 1.0)
+    core_p = smooth_random((8, 8), 40.0, s=1.0)
+    I[14:22, 12:20] = core_I
+    p[14:22, 12:20] = core_p
+    sh = (3, 7)
+    I2, p2 = np.roll(I, sh, (0, 1)), np.roll(p, sh, (0, 1))
+    A = oracle.shoot(I, p, 4, 1.0, 0.2, 1.0)
+    B = oracle.shoot(I2, p2, 4, 1.0, 0.2, 1.0)
+    np.testing.assert_allclose(np.roll(A[0][-1], sh, (0, 1)), B[0][-1], atol=1e-13)
+    np.testing.assert_allclose(np.roll(A[1][-1], sh, (0, 1)), B[1][-1], atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(14, 17), (8, 9, 7)])
+def test_flip_and_transpose_equivariance(dims):
+    """Mirroring an axis (or swapping two) commutes with the scheme: catches axis mix-ups."""
+    I, _ = phantoms.random_fields(6, 1, dims)
+    I = I[0].astype(np.float64)
+    p = smooth_random(dims, 20.0, seed=3)
+    J = np.clip(I + 0.05 * smooth_random(dims, 1.0, seed=4), 0, 1)
+    args = (5, 1.2, 0.3, 1.4, 1e-2)
+    c0, g0 = oracle.cost_and_grad(I, J, p, *args)
+    It0, pt0, _ = oracle.shoot(I, p, *args[:4])
+    ops = [lambda a, ax=ax: np.flip(a, ax) for ax in range(len(dims))]
+    ops.append(lambda a: np.swapaxes(a, 0, 1))
+    for op in ops:
+        c1, g1 = oracle.cost_and_grad(op(I), op(J), op(p), *args)
+        It1, pt1, _ = oracle.shoot(op(I), op(p), *args[:4])
+        np.testing.assert_allclose(c1, c0, rtol=1e-11)
+        np.testing.assert_allclose(It1[-1], op(It0[-1]), atol=1e-12)
+        np.testing.assert_allclose(pt1[-1], op(pt0[-1]), atol=1e-11)
+        np.testing.assert_allclose(g1, op(g0), atol=1e-10 * np.abs(g0).max())
+
+
+# ----------------------------------------------------------------- cost (Eq. 4)
+
+def test_cost_at_zero_momentum():
+    w = phantoms.disk_pair_64(random_p0=False)
+    c, g = oracle.cost_and_grad(w.I0[0], w.J[0], w.p0[0], w.T, w.sigma, 0.1, 1.0, 1e-3)
+    I0, J = w.I0[0].astype(float), w.J[0].astype(float)
+    assert abs(c[0] - 0.5 * ((I0 - J) ** 2).sum()) < 1e-12 * c[0]
+    assert c[1] == 0.0 and c[2] == 0.0
+
+
+def test_kinetic_term_of_a_single_delta():
+    """p0 = a delta at x0: <m0, K m0> = |grad S(x0)|^2 w_0^d (centre tap), residual = rho."""
+    dims = (21, 22)
+    I, _ = phantoms.random_fields(8, 1, dims)
+    S = I[0].astype(np.float64)
+    sigma, rho, lam = 1.7, 2.0, 0.5
+    x0 = (10, 9)
+    p0 = np.zeros(dims)
+    p0[x0] = 1.0
+    c, _ = oracle.cost_and_grad(S, S, p0, 3, sigma, 0.2, rho, lam, want_grad=False)
+    w0 = oracle.taps(sigma)[(oracle.taps(sigma).size - 1) // 2]
+    g = [0.5 * (S[x0[0] + 1, x0[1]] - S[x0[0] - 1, x0[1]]),
+         0.5 * (S[x0[0], x0[1] + 1] - S[x0[0], x0[1] - 1])]
+    assert abs(c[1] - lam * (g[0] ** 2 + g[1] ** 2) * w0 ** 2) < 1e-14
+    assert abs(c[2] - lam * rho) < 1e-15
+
+
+# ----------------------------------------------------------------- gradient
+
+def _fd_problem(dims, seed):
+    I, _ = phantoms.random_fields(seed, 1, dims)
+    I = I[0].astype(np.float64)
+    J = np.clip(I + 0.2 * smooth_random(dims, 1.0, seed=seed + 1), 0, 1)
+    p = smooth_random(dims, 25.0, seed=seed + 2)
+    return I, J, p
+
+
+@pytest.mark.parametrize("dims,T,sigma", [((16, 16), 5, 1.5), ((8, 8, 8), 4, 1.0)])
+def test_gradient_matches_central_differences(dims, T, sigma):
+    I, J, p = _fd_problem(dims, 20)
+    args = (T, sigma, 0.25, 1.3, 0.05)
+    _, g = oracle.cost_and_grad(I, J, p, *args)
+    _, _, u = oracle.shoot(I, p, *args[:4], want_u=True)
+    assert np.abs(u).max() * 1.3 / T > 0.05  # feet well away from grid nodes
+
+    def L(q):
+        return oracle.cost_and_grad(I, J, q, *args, want_grad=False)[0].sum()
+
+    r = np.random.default_rng(7)
+    for _ in range(3):
+        h = r.normal(size=dims)
+        eps = 1e-6
+        fd = (L(p + eps * h) - L(p - eps * h)) / (2 * eps)
+        an = (g * h).sum()
+        assert abs(fd - an) < 2e-6 * abs(an) + 1e-9
+    # single coordinates, including edge voxels
+    for idx in [(0,) * len(dims), tuple(n // 2 for n in dims), tuple(n - 1 for n in dims)]:
+        e = np.zeros(dims)
+        e[idx] = 1.0
+        fd = (L(p + 1e-4 * e) - L(p - 1e-4 * e)) / 2e-4
+        assert abs(fd - g[idx]) < 1e-6 * abs(g[idx]) + 1e-8
+
+
+def test_taylor_remainder_is_second_order():
+    I, J, p = _fd_problem((14, 15), 30)
+    args = (4, 1.2, 0.1, 1.0, 0.02)
+    c, g = oracle.cost_and_grad(I, J, p, *args)
+    L0 = c.sum()
+    h = np.random.default_rng(2).normal(size=p.shape)
+    rem = []
+    for eps in (1e-2, 5e-3, 2.5e-3):
+        L = oracle.cost_and_grad(I, J, p + eps * h, *args, want_grad=False)[0].sum()
+        rem.append(abs(L - L0 - eps * (g * h).sum()))
+    assert 3.0 < rem[0] / rem[1] < 5.0 and 3.0 < rem[1] / rem[2] < 5.0
+
+
+def test_adjoint_of_shooting_map_dot_product():
+    """<gI1, dI_T> + <gp1, dp_T> = <gI0, dI0> + <gp0, dp0> for a tangent (dI0, dp0)."""
+    dims = (12, 13)
+    I, J, p = _fd_problem(dims, 40)
+    args = (4, 1.3, 0.4, 1.1)
+    r = np.random.default_rng(9)
+    gI1, gp1 = r.normal(size=dims), r.normal(size=dims)
+    dI, dp = r.normal(size=dims), r.normal(size=dims)
+    gI0, gp0 = oracle.adjoint(I, p, gI1, gp1, *args)
+    eps = 1e-6
+    Ap = oracle.shoot(I + eps * dI, p + eps * dp, *args)
+    Am = oracle.shoot(I - eps * dI, p - eps * dp, *args)
+    tang = ((Ap[0][-1] - Am[0][-1]) * gI1).sum() + ((Ap[1][-1] - Am[1][-1]) * gp1).sum()
+    tang /= 2 * eps
+    adj = (gI0 * dI).sum() + (gp0 * dp).sum()
+    assert abs(tang - adj) < 1e-6 * abs(adj)
+
+
+@pytest.mark.parametrize("dims", [(16, 20), (9, 11, 10)])
+def test_oracle_matches_independent_torch_implementation(dims):
+    """grid_sample + conv + torch.autograd in FP64 reproduce the oracle to ~1e-13."""
+    torch = pytest.importorskip("torch")
+    from baseline import torch_scheme as ts
+    I, J, p = _fd_problem(dims, 50)
+    T, sig, mu, rho, lam = 5, 1.5, 0.3, 1.7, 1e-2
+    c, g = oracle.cost_and_grad(I, J, p, T, sig, mu, rho, lam)
+    It, pt, _ = oracle.shoot(I, p, T, sig, mu, rho)
+    t = lambda a: torch.tensor(np.asarray(a)[None], dtype=torch.float64)
+    tmu, trho = torch.tensor([mu], dtype=torch.float64), torch.tensor([rho], dtype=torch.float64)
+    c2, g2 = ts.cost_and_grad(t(I), t(J), t(p), T, sig, tmu, trho, lam)
+    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, tmu, trho)
+    np.testing.assert_allclose(IT[0].numpy(), It[-1], atol=1e-12)
+    np.testing.assert_allclose(pT[0].numpy(), pt[-1], atol=1e-11)
+    np.testing.assert_allclose(c2[0].numpy(), c, rtol=1e-12)
+    np.testing.assert_allclose(g2[0].numpy(), g, atol=1e-12 * np.abs(g).max())
