@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark: fused forward + adjoint voxel-steps/s of semi-Lagrangian
+Metamorphosis shooting (arXiv:2106.08817) on GB300.
+
+One step = one cost_and_grad over the whole batch: T forward shooting steps,
+the Eq. 4 cost, and T adjoint steps giving dL/dp0.  Between timed steps p0
+takes a gradient-descent update and L2 is flushed (both outside the timed
+events).  voxel-steps = batch x voxels x T per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ellipses16x256|disk64|head128|mri160]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (the deliberately slow reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+adjoint voxel-steps/s, % HBM roofline vs torch autograd, same GPU, grad relL2<=1e-3"
+UNIT = "voxel-steps/s"
+
+# Algorithmic HBM bytes per voxel of one launch of each kernel class (FP32):
+# what the kernel must read and write once, halos and gathers not counted.
+def bytes_per_voxel(kclass: str, d: int) -> int:
+    return {
+        "pack": 16,
+        "xpass_m": 8 + 4 * d,          # read I, p; write d components of m~
+        "strided_fwd": 8 * d,          # read + write d components (per pass)
+        "advect": 16 + 4 * d,          # read u (d), I, p; write I', p'
+        "cost": 24 + 4 * d,            # read I_T, J, I_0, p_0, u_0 (d); write I^, p^
+        "adj_init": 16,
+        "adj_pre": 20 + 4 * d,         # read u (d), I^', p^', p_t; write p~^, div^
+        "adj_gather": 28 + 8 * d,      # read u (d), I^', p~^, div^, I_t, p_t; write v^ (d), I^, p^
+        "xpass_adj": 8 * d,            # read + write d components
+        "strided_adj": 8 * d,
+        "adj_gradp": 24 + 4 * d,       # read m^ (d), I_t, p_t, I^, p^; write I^, p^
+        "unpack": 16,
+    }[kclass]
+
+
+def workload(name: str):
+    import phantoms
+    if name == "ellipses16x256":
+        return phantoms.ellipse_pairs()
+    if name == "disk64":
+        return phantoms.disk_pair_64(random_p0=False)
+    if name == "head128":
+        return phantoms.head_pair_3d()
+    if name == "mri160":
+        return phantoms.mri_pair_3d()
+    raise SystemExit("unknown workload %s" % name)
+
+
+def workload_config(w, name: str) -> dict:
+    return {"workload": name, "batch": w.batch, "dims": list(w.dims), "T": w.T,
+            "sigma": w.sigma, "mu": sorted(set(float(x) for x in w.mu)),
+            "rho": float(w.rho[0]), "lambda": float(w.lam[0]),
+            "step": "cost_and_grad over the batch: T forward steps + Eq. 4 cost + T adjoint "
+                    "steps; p0 gradient-descent update between timed steps",
+            "l2": "flushed (256 MiB write) between timed steps",
+            "p0": "gradient descent from 0 (warm-up steps included)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.err = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError as e:
+            self.err = str(e)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        if self.err or not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "note": self.err or "no nvidia-smi samples"}
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_08817_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kclass: str, launch_voxels: int):
+    """Per-launch DRAM bytes of `kclass` from the committed ncu summary, scaled to
+    this launch's voxel count; None when missing or taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("sources_hash") != kernel_sources_hash():
+        return None
+    k = d.get("kernels", {}).get(kclass)
+    if not k:
+        return None
+    return float(k["dram_bytes_per_launch"]) * launch_voxels / float(k["voxels_per_launch"])
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(w, target_s: float, max_instances: int = None):
+    """Time oracle cost_and_grad on instances 0, 1, ... until ~target_s seconds."""
+    import oracle
+    oracle.set_threads(oracle.max_threads())
+    done, t0 = 0, time.perf_counter()
+    n_max = max_instances or w.batch
+    while done < n_max:
+        b = done % w.batch
+        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
+                             float(w.rho[b]), float(w.lam[b]))
+        done += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    el = time.perf_counter() - t0
+    return done, el, oracle.max_threads()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    import oracle
+    oracle.build()
+    oracle.set_threads(oracle.max_threads())
+    vs = w.voxels * w.T
+    for i in range(args.warmup):
+        b = i % w.batch
+        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
+                             float(w.rho[b]), float(w.lam[b]))
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        b = i % w.batch
+        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
+                             float(w.rho[b]), float(w.lam[b]))
+    el = time.perf_counter() - t0
+    value = vs * args.steps / el
+    cores = oracle.max_threads()
+    sample = ("one instance's cost_and_grad (%s, T=%d fwd + adjoint, FP64) per step, "
+              "cycling over the %d instances" % ("x".join(map(str, w.dims)), w.T, w.batch))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2106_08817_gb300 as meta
+
+    w = workload(args.workload)
+    B, d, T = w.batch, w.ndim, w.T
+    N = w.voxels
+    vs_per_step = B * N * T
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    I0, J, p0 = t(w.I0), t(w.J), t(w.p0)
+    mu, rho, lam = t(w.mu), t(w.rho), t(w.lam)
+    ws = meta.Workspace(w.dims, B, T, w.sigma, dev)
+    cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
+    grad = torch.empty_like(I0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    alpha = 0.02
+
+    def gd_update():
+        # p0 <- p0 - alpha * g / max|g| per instance (outside the timed events)
+        gmax = grad.abs().amax(dim=tuple(range(1, d + 1)), keepdim=True).clamp_min(1e-30)
+        p0.sub_(alpha * grad / gmax)
+
+    def step():
+        meta.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam, workspace=ws,
+                           out=(cost, grad))
+
+    for _ in range(args.warmup):
+        step()
+        gd_update()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed in between
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+            gd_update()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / args.steps
+    if world > 1:
+        m = torch.tensor([ms], device=dev)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        ms = float(m.item())
+    value = world * vs_per_step / (ms * 1e-3)
+    first_cost = cost.clone()
+
+    # ---- kernel timing: the same steps again, every library launch bracketed by events
+    meta.timer_start(1 << 16)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+        gd_update()
+    torch.cuda.synchronize()
+    kt = meta.timer_stop()
+    launches_per_step = sum(v[2] for v in kt.values()) / args.steps
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_scopes, _ = kt[dom]
+    avg_ms = dom_ms / max(dom_scopes, 1)
+    per_launch_bytes = bytes_per_voxel(dom, d) * B * N
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    traffic = ncu_traffic(dom, B * N)
+    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[2],
+                   "share": round(v[0] / max(sum(x[0] for x in kt.values()), 1e-9), 4),
+                   "avg_us": round(v[0] / max(v[1], 1) * 1e3, 3),
+                   "GBps_algorithmic": round(bytes_per_voxel(k, d) * B * N / (v[0] / v[1] * 1e-3)
+                                             / 1e9, 1) if v[1] else None}
+               for k, v in kt.items() if v[1]}
+
+    # ---- end to end through the public API: pinned host inputs, H2D + call + D2H
+    hI, hJ, hp = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                  for a in (w.I0, w.J, p0.cpu().numpy()))
+    hcost = torch.empty((B, 3), dtype=torch.float64).pin_memory()
+    hgrad = torch.empty(grad.shape, dtype=torch.float32).pin_memory()
+    dI, dJ, dp = torch.empty_like(I0), torch.empty_like(J), torch.empty_like(p0)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        e2e_ev[k][0].record(stream)
+        dI.copy_(hI, non_blocking=True)
+        dJ.copy_(hJ, non_blocking=True)
+        dp.copy_(hp, non_blocking=True)
+        meta.cost_and_grad(dI, dJ, dp, T, w.sigma, mu, rho, lam, workspace=ws, out=(cost, grad))
+        hcost.copy_(cost, non_blocking=True)
+        hgrad.copy_(grad, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    if world > 1:
+        m = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        e2e_ms = float(m.item())
+    h2d = 3 * B * N * 4
+    d2h = B * 3 * 8 + B * N * 4
+
+    # ---- torch.autograd through the same scheme in PyTorch ops, same GPU, FP32
+    torch_cmp = None
+    if not args.no_torch:
+        from baseline import torch_scheme as ts
+        steps_t = max(1, min(args.steps, 5))
+        for _ in range(2):
+            ts.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam)
+        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps_t)]
+        torch.cuda.synchronize()
+        for k in range(steps_t):
+            flush.zero_()
+            tev[k][0].record(stream)
+            ts.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam)
+            tev[k][1].record(stream)
+        torch.cuda.synchronize()
+        tms = sum(a.elapsed_time(b) for a, b in tev) / steps_t
+        torch_cmp = {"value": world * vs_per_step / (tms * 1e-3), "unit": UNIT,
+                     "ms_per_step": tms, "steps": steps_t,
+                     "speedup_ours_over_torch": tms / ms,
+                     "what": "baseline/torch_scheme.py: grid_sample + grouped conv + "
+                             "torch.autograd, FP32, eager"}
+
+    fault = ws.status()
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            n_inst, el, cores = oracle_sample(w, args.cpu_seconds)
+            cpu = {"value": n_inst * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d of %d instances, one FP64 cost_and_grad each (%s, T=%d), "
+                             "%.1f s" % (n_inst, B, "x".join(map(str, w.dims)), T, el)}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": workload_config(w, args.workload),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src
+                         if peak_src == "measured" else "fallback 6800 GB/s",
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_us": avg_ms * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * vs_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk.summary(),
+            "torch_autograd": torch_cmp,
+            "kernels": kernels,
+            "device_fault_bits": fault,
+            "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ellipses16x256")
+    ap.add_argument("--no-torch", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

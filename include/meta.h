@@ -1,0 +1,146 @@
+/*
+ * meta.h -- C ABI of the GB300 (sm_103a) library for semi-Lagrangian geodesic
+ * shooting in Metamorphosis / LDDMM image registration and for the gradient of
+ * the inexact-matching cost with respect to the initial momentum.
+ *
+ * Method: A. François, P. Gori, J. Glaunès, "Metamorphic image registration
+ * using a semi-Lagrangian scheme", arXiv:2106.08817.
+ *
+ * What one shooting step computes (Eq. 3, integrated in the semi-Lagrangian
+ * form of Sec. 2.3, Eq. 5-9), with dt = 1/T, voxel units, axis 0 first:
+ *
+ *     v   = -rho * K_sigma * (p grad I)        Gaussian RKHS kernel K (Sec. 2.1)
+ *     y   = x - dt v                          backtracked grid, clamped to the domain
+ *     I~  = I(y), p~ = p(y)                   bi/trilinear interpolation
+ *     p'  = p~ (1 - dt div v)                 continuity equation (Eq. 7-9)
+ *     I'  = I~ + dt mu p~                     image evolution (Eq. 1 / Eq. 5)
+ *
+ * rho plays the role of rho/mu in Eq. 3, so mu = 0, rho = 1 is LDDMM (Sec. 2.1).
+ * Cost (Eq. 4), per instance, returned as three terms:
+ *
+ *     L = 1/2 sum (I_T - J)^2 + lambda [ <m0, K m0> + rho sum p0^2 ],  m0 = p0 grad I_0
+ *
+ * Discrete conventions: K has taps exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma),
+ * normalised to sum 1, applied separably with zero padding outside the domain;
+ * grad and div use central differences with the edge neighbour replicated;
+ * interpolation clamps the foot to [0, n-1] per axis.  The gradient is the
+ * exact transpose of this discrete scheme (what automatic differentiation of
+ * the scheme gives, Sec. 3), computed by a hand-written adjoint.
+ *
+ * Conventions of every call:
+ *   - Arrays are FP32, C-contiguous [batch, (D,) H, W] (axis 0 first), device
+ *     pointers owned by the caller.  mu, rho, lambda are device arrays [batch].
+ *   - `ws` is a device workspace of at least meta_workspace_size() bytes, owned
+ *     by the caller, 256-byte aligned.  The library allocates nothing.  Its
+ *     first 16 bytes hold the device fault word: zero them once before the
+ *     first call (e.g. cudaMemset of the whole workspace).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     only enqueues work on it (no host synchronisation, no host<->device
+ *     copies); outputs are valid once the stream has reached them.
+ *   - Errors are returned as codes; nothing aborts.  Faults detected on the
+ *     device (a bounded wait that ran out) are latched in the workspace and
+ *     returned by meta_workspace_status().
+ *   - Calls that share a workspace must be ordered on one stream.
+ */
+#ifndef META_H
+#define META_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    META_OK = 0,
+    META_ERR_INVALID_ARG = 1, /* null pointer, bad T / sigma / batch / ndim */
+    META_ERR_SHAPE = 2,       /* an extent < 2, or a size beyond the limits below */
+    META_ERR_WORKSPACE = 3,   /* ws too small or misaligned */
+    META_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed */
+    META_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out */
+    META_ERR_NONFINITE = 6,   /* reserved: non-finite cost detected */
+    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, or the driver lacks TMA support */
+} meta_status;
+
+/* Shape of one batch of independent registration problems. */
+typedef struct {
+    int ndim;     /* 2 or 3 */
+    int dims[3];  /* extents, axis 0 first: (H, W) or (D, H, W); each in [2, 65536] */
+    int batch;    /* number of independent instances, >= 1 */
+    int T;        /* number of time steps, dt = 1/T, in [1, 4096] */
+    float sigma;  /* std (voxels) of the Gaussian RKHS kernel, in (0, 18] */
+} meta_problem;
+
+/* Bytes of workspace that every call below needs for this problem.
+ * The workspace holds the whole trajectory (I_t, p_t), t = 0..T, and the
+ * smoothed momenta u_t = K(p_t grad I_t), t < T, so that the adjoint needs no
+ * recomputation: about (2(T+1) + d T + 3d + 8) * batch * voxels * 4 bytes. */
+meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes);
+
+/* Forward shooting (Eq. 3, Sec. 2.3): (I0, p0) -> (I1, p1) = (I_T, p_T).
+ * I1, p1 may be NULL (the trajectory is still kept in ws for
+ * meta_shoot_adjoint).  mu and rho: device [batch]. */
+meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const float* p0,
+                               const float* mu, const float* rho, float* I1, float* p1,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of the shooting map, run on the trajectory that the last
+ * meta_shoot_forward left in ws (same prob, mu, rho).  Given gI1, gp1, the
+ * gradient of a scalar with respect to I_T and p_T (gp1 may be NULL: zero),
+ * writes its gradient with respect to p0 (gp0) and, if gI0 is not NULL, I0.
+ * This is the discrete transpose of every step, run from t = T-1 down to 0. */
+meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const float* rho,
+                               const float* gI1, const float* gp1, float* gI0, float* gp0,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Cost of Eq. 4 and its gradient with respect to p0, per instance.
+ * cost: device double [batch][3] = { 1/2 sum (I_T - J)^2,
+ *                                    lambda <m0, K m0>,
+ *                                    lambda rho sum p0^2 }.
+ * grad: device float [batch, (D,) H, W] = dL/dp0 (may be NULL: cost only).
+ * Summation of the cost is deterministic (fixed tree, FP64 partials). */
+meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const float* J,
+                               const float* p0, const float* mu, const float* rho,
+                               const float* lambda, double* cost, float* grad, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* Device-side fault word latched in ws since it was last cleared (0 = none).
+ * Synchronises `stream`.  clear != 0 resets it. */
+meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
+                                  unsigned int* fault_bits);
+
+/* Human-readable name of a status code (static string). */
+const char* meta_status_string(meta_status s);
+
+/* Kernel classes reported by the timer below. */
+enum {
+    META_K_PACK = 0,       /* copy I0, p0 into the pitched trajectory */
+    META_K_XPASS_M,        /* m = p grad I fused with the x pass of K */
+    META_K_STRIDED_FWD,    /* y (and z) passes of K in the forward step */
+    META_K_ADVECT,         /* backtrack + interpolate + momentum/intensity update */
+    META_K_COST,           /* Eq. 4 partial sums and their final reduction */
+    META_K_ADJ_INIT,       /* adjoint start from gI1, gp1 */
+    META_K_ADJ_PRE,        /* pointwise part of the adjoint step */
+    META_K_ADJ_GATHER,     /* gather-form transpose of the interpolation, v^ */
+    META_K_XPASS_ADJ,      /* x pass of K on v^ */
+    META_K_STRIDED_ADJ,    /* y (and z) passes of K on v^ */
+    META_K_ADJ_GRADP,      /* transpose of m = p grad I */
+    META_K_UNPACK,         /* copy I_T, p_T out */
+    META_K_COUNT
+};
+
+/* Profiling aid, off by default, not thread-safe: after meta_timer_start(cap)
+ * every kernel launched by the calls above (up to cap launches) is bracketed
+ * by a pair of CUDA events on the call's stream.  meta_timer_stop()
+ * synchronises those events, writes per kernel class (arrays of META_K_COUNT)
+ * the summed device milliseconds and the number of launches, and turns the
+ * timer off.  The events are host objects created by meta_timer_start. */
+meta_status meta_timer_start(int cap);
+meta_status meta_timer_stop(float* ms_per_class, int* launches_per_class);
+const char* meta_kernel_name(int kernel_class);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* META_H */

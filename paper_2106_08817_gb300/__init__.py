@@ -1,0 +1,307 @@
+"""Python binding of the sm_103a semi-Lagrangian Metamorphosis / LDDMM library.
+
+Thin argument marshalling over the C ABI of ``include/meta.h`` (ctypes): every
+step of the shooting, the cost and the adjoint runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors, the workspace) and the
+current stream only.  There is no CPU fallback: if ``libmeta.so`` is missing
+or no CUDA device is present, every call raises.
+
+Method: François, Gori, Glaunès, "Metamorphic image registration using a
+semi-Lagrangian scheme", arXiv:2106.08817 (Eq. 3 shooting in the
+semi-Lagrangian form of Sec. 2.3; Eq. 4 cost; its gradient w.r.t. p0).
+
+Arrays are float32 [B, (D,) H, W] (a single instance may omit B); mu, rho and
+lam are scalars or per-instance sequences / tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple, Union
+
+import torch
+
+__all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_adjoint", "cost_and_grad",
+           "Shoot", "shoot", "library_path", "STATUS", "timer_start", "timer_stop",
+           "KERNEL_CLASSES"]
+
+KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
+                  "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack")
+# kernels launched per timed scope of each class (the cost scope launches two)
+_LAUNCHES_PER_SCOPE = {"cost": 2}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmeta.so")
+_lib = None
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported shape", 3: "workspace",
+          4: "CUDA error", 5: "device-side wait timed out", 6: "non-finite",
+          7: "unsupported device or driver"}
+
+
+class MetaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, STATUS.get(code, "?"), code))
+        self.code = code
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3), ("batch", ctypes.c_int),
+                ("T", ctypes.c_int), ("sigma", ctypes.c_float)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libmeta.so is not built (run __graft_entry__.build() or "
+                               "python paper_2106_08817_gb300/_build.py)")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, V, F, D = ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+        S = ctypes.c_size_t
+        lib.meta_workspace_size.argtypes = [P, ctypes.POINTER(S)]
+        lib.meta_shoot_forward.argtypes = [P, F, F, F, F, F, F, V, S, V]
+        lib.meta_shoot_adjoint.argtypes = [P, F, F, F, F, F, F, V, S, V]
+        lib.meta_cost_and_grad.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V]
+        lib.meta_workspace_status.argtypes = [V, S, ctypes.c_int, V,
+                                              ctypes.POINTER(ctypes.c_uint)]
+        lib.meta_status_string.argtypes = [ctypes.c_int]
+        lib.meta_status_string.restype = ctypes.c_char_p
+        lib.meta_timer_start.argtypes = [ctypes.c_int]
+        lib.meta_timer_stop.argtypes = [ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int)]
+        lib.meta_kernel_name.argtypes = [ctypes.c_int]
+        lib.meta_kernel_name.restype = ctypes.c_char_p
+        for f in ("meta_workspace_size", "meta_shoot_forward", "meta_shoot_adjoint",
+                  "meta_cost_and_grad", "meta_workspace_status", "meta_timer_start",
+                  "meta_timer_stop"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float) -> _Problem:
+    d3 = list(dims) + [0] * (3 - len(dims))
+    return _Problem(int(ndim), (ctypes.c_int * 3)(*d3), int(batch), int(T), float(sigma))
+
+
+def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float) -> int:
+    n = ctypes.c_size_t(0)
+    rc = _load().meta_workspace_size(ctypes.byref(_problem(len(dims), dims, batch, T, sigma)),
+                                     ctypes.byref(n))
+    if rc:
+        raise MetaError(rc, "meta_workspace_size")
+    return int(n.value)
+
+
+class Workspace:
+    """Device workspace (a zero-initialised uint8 tensor) of one problem shape.
+
+    It keeps the trajectory of the last forward shooting; calls that share it
+    must run on one stream.
+    """
+
+    def __init__(self, dims: Sequence[int], batch: int, T: int, sigma: float,
+                 device: Union[torch.device, str, int] = "cuda"):
+        self.key = (tuple(int(x) for x in dims), int(batch), int(T), float(sigma))
+        self.nbytes = workspace_size(dims, batch, T, sigma)
+        self.buf = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
+
+    def matches(self, dims, batch, T, sigma) -> bool:
+        return self.key == (tuple(int(x) for x in dims), int(batch), int(T), float(sigma))
+
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def status(self, clear: bool = False) -> int:
+        """Device fault bits latched since the last clear (synchronises the stream)."""
+        bits = ctypes.c_uint(0)
+        _load().meta_workspace_status(ctypes.c_void_p(self.ptr()), self.nbytes, int(clear),
+                                      _stream(self.buf.device), ctypes.byref(bits))
+        return int(bits.value)
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _as_batch(x: torch.Tensor, name: str) -> Tuple[torch.Tensor, bool]:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if x.dtype != torch.float32:
+        raise TypeError("%s must be float32" % name)
+    squeeze = False
+    return x.contiguous(), squeeze
+
+
+def _shape(I0: torch.Tensor, ndim: Optional[int]) -> Tuple[torch.Tensor, int, Tuple[int, ...], bool]:
+    """Arrays are [B, *dims] (ndim = I0.dim() - 1 by default); with ndim = I0.dim()
+    a single instance [*dims] is accepted and results drop the batch axis."""
+    if ndim is None:
+        ndim = I0.dim() - 1
+    if ndim not in (2, 3):
+        raise ValueError("ndim must be 2 or 3 (got array of rank %d)" % I0.dim())
+    if I0.dim() == ndim:
+        return I0.unsqueeze(0), ndim, tuple(I0.shape), True
+    if I0.dim() == ndim + 1:
+        return I0, ndim, tuple(I0.shape[1:]), False
+    raise ValueError("expected [B, *dims] or [*dims] with ndim = %d" % ndim)
+
+
+def _coef(v, B: int, device) -> torch.Tensor:
+    t = torch.as_tensor(v, dtype=torch.float32, device=device).reshape(-1)
+    if t.numel() == 1:
+        t = t.expand(B)
+    if t.numel() != B:
+        raise ValueError("per-instance coefficient has %d values for batch %d" % (t.numel(), B))
+    return t.contiguous()
+
+
+def _p(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+_ws_cache = {}
+
+
+def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace]) -> Workspace:
+    if ws is not None:
+        if not ws.matches(dims, B, T, sigma):
+            raise ValueError("workspace was made for another problem")
+        return ws
+    key = (tuple(dims), B, T, float(sigma), str(device), torch.cuda.current_stream(device).cuda_stream)
+    w = _ws_cache.get(key)
+    if w is None:
+        w = Workspace(dims, B, T, sigma, device)
+        _ws_cache[key] = w
+    return w
+
+
+def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
+                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None
+                  ) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
+    """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory)."""
+    I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    B, dev = I0b.shape[0], I0b.device
+    ws = _workspace(dims, B, T, sigma, dev, workspace)
+    mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
+    I1 = torch.empty_like(I0b)
+    p1 = torch.empty_like(I0b)
+    pr = _problem(nd, dims, B, T, sigma)
+    rc = _load().meta_shoot_forward(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
+                                    _p(I1), _p(p1), ctypes.c_void_p(ws.ptr()), ws.nbytes,
+                                    _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_shoot_forward")
+    if sq:
+        I1, p1 = I1[0], p1[0]
+    return I1, p1, ws
+
+
+def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Workspace, T: int,
+                  sigma: float, mu, rho=1.0, want_gI0: bool = True, ndim: Optional[int] = None
+                  ) -> Tuple[Optional[torch.Tensor], torch.Tensor]:
+    """Adjoint of the shooting map on the trajectory kept in `workspace`:
+    returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1, dL/dp_T = gp1."""
+    g1, nd, dims, sq = _shape(_as_batch(gI1, "gI1")[0], ndim)
+    B, dev = g1.shape[0], g1.device
+    if not workspace.matches(dims, B, T, sigma):
+        raise ValueError("workspace was made for another problem")
+    gp1b = None if gp1 is None else _as_batch(gp1, "gp1")[0].reshape(g1.shape)
+    mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
+    gp0 = torch.empty_like(g1)
+    gI0 = torch.empty_like(g1) if want_gI0 else None
+    pr = _problem(nd, dims, B, T, sigma)
+    rc = _load().meta_shoot_adjoint(ctypes.byref(pr), _p(mu_t), _p(rho_t), _p(g1), _p(gp1b),
+                                    _p(gI0), _p(gp0), ctypes.c_void_p(workspace.ptr()),
+                                    workspace.nbytes, _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_shoot_adjoint")
+    if sq:
+        gp0 = gp0[0]
+        gI0 = None if gI0 is None else gI0[0]
+    return gI0, gp0
+
+
+def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
+                  mu, rho=1.0, lam=1e-3, want_grad: bool = True,
+                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
+                  out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None
+                  ) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+    """Eq. 4 cost per instance ([B, 3] float64: data, lambda*kinetic, lambda*rho*residual)
+    and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint."""
+    I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
+    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    B, dev = I0b.shape[0], I0b.device
+    ws = _workspace(dims, B, T, sigma, dev, workspace)
+    mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
+    if out is not None:
+        cost, grad = out
+    else:
+        cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
+        grad = torch.empty_like(I0b) if want_grad else None
+    pr = _problem(nd, dims, B, T, sigma)
+    rc = _load().meta_cost_and_grad(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b), _p(mu_t),
+                                    _p(rho_t), _p(lam_t), _p(cost), _p(grad),
+                                    ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_cost_and_grad")
+    if sq and grad is not None and out is None:
+        grad = grad[0]
+    return cost, grad
+
+
+class Shoot(torch.autograd.Function):
+    """(I0, p0) -> (I_T, p_T) with the hand-written adjoint as backward.
+
+    forward keeps the trajectory in a fresh workspace; backward runs the
+    discrete transpose of every step on it (no recomputation needed).
+    """
+
+    @staticmethod
+    def forward(ctx, I0, p0, T, sigma, mu, rho):
+        I0c, p0c = I0.detach().contiguous(), p0.detach().contiguous()
+        b_, nd, dims, sq = _shape(I0c, None)
+        ws = Workspace(dims, b_.shape[0], T, sigma, I0c.device)
+        I1, p1, _ = shoot_forward(I0c, p0c, T, sigma, mu, rho, workspace=ws)
+        ctx.ws, ctx.args, ctx.shape = ws, (T, sigma, mu, rho), I0c.shape
+        return I1, p1
+
+    @staticmethod
+    def backward(ctx, gI1, gp1):
+        T, sigma, mu, rho = ctx.args
+        if gI1 is None:
+            gI1 = torch.zeros(ctx.shape, device=ctx.ws.buf.device)
+        gI0, gp0 = shoot_adjoint(gI1.contiguous(), None if gp1 is None else gp1.contiguous(),
+                                 ctx.ws, T, sigma, mu, rho, want_gI0=ctx.needs_input_grad[0])
+        return gI0, gp0, None, None, None, None
+
+
+def shoot(I0, p0, T: int, sigma: float, mu, rho=1.0):
+    """Differentiable shooting: torch autograd calls the library's adjoint."""
+    return Shoot.apply(I0, p0, T, sigma, mu, rho)
+
+
+def timer_start(cap: int = 1 << 16) -> None:
+    """Bracket every following library launch with CUDA events (profiling aid)."""
+    rc = _load().meta_timer_start(int(cap))
+    if rc:
+        raise MetaError(rc, "meta_timer_start")
+
+
+def timer_stop() -> dict:
+    """{kernel class: (summed device ms, scopes timed, kernels launched)} since timer_start."""
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_float * n)()
+    cnt = (ctypes.c_int * n)()
+    rc = _load().meta_timer_stop(ms, cnt)
+    if rc:
+        raise MetaError(rc, "meta_timer_stop")
+    return {k: (float(ms[i]), int(cnt[i]), int(cnt[i]) * _LAUNCHES_PER_SCOPE.get(k, 1))
+            for i, k in enumerate(KERNEL_CLASSES)}

@@ -1,0 +1,509 @@
+// meta_api.cu -- the C ABI of include/meta.h: argument validation, workspace
+// layout, Gaussian tap tables, TMA tensor maps and the launch sequence of the
+// forward shooting, the cost and the discrete adjoint (arXiv:2106.08817,
+// Eq. 3-4 and Sec. 2.3).  Host code only; it never allocates device memory.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "meta.h"
+#include "meta_kernels.h"
+
+namespace meta {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Workspace map (byte offsets from the workspace base).
+struct Layout {
+    Geom g;
+    int ndim, T, nblk;
+    size_t off_fault, off_maxdisp, off_partials;
+    size_t off_states, off_u, off_SA, off_SB, off_SV;
+    size_t off_IA, off_PA, off_IB, off_PB, off_PTH, off_DH, off_IHP, off_PHP;
+    size_t total;
+};
+
+meta_status validate(const meta_problem* pr) {
+    if (!pr) return META_ERR_INVALID_ARG;
+    if (pr->ndim != 2 && pr->ndim != 3) return META_ERR_INVALID_ARG;
+    if (pr->batch < 1 || pr->batch > 16384) return META_ERR_INVALID_ARG;
+    if (pr->T < 1 || pr->T > 4096) return META_ERR_INVALID_ARG;
+    if (!(pr->sigma > 0.f) || !(pr->sigma <= 18.f)) return META_ERR_INVALID_ARG;
+    for (int a = 0; a < pr->ndim; ++a)
+        if (pr->dims[a] < 2 || pr->dims[a] > 65536) return META_ERR_SHAPE;
+    if (pr->ndim == 3) {
+        // x-pass grid.y = ceil(ny/4) * ceil(nz/4); strided grids = tiles * extent
+        const long long gy = (long long)((pr->dims[1] + 3) / 4) * ((pr->dims[0] + 3) / 4);
+        const long long gy1 = (long long)((pr->dims[1] + kTA - 1) / kTA) * pr->dims[0];
+        const long long gy0 = (long long)((pr->dims[0] + kTA - 1) / kTA) * pr->dims[1];
+        const long long gp = (long long)((pr->dims[1] + 7) / 8) * pr->dims[0];
+        if (gy > 65535 || gy1 > 65535 || gy0 > 65535 || gp > 65535) return META_ERR_SHAPE;
+    } else {
+        if ((pr->dims[0] + 7) / 8 > 65535) return META_ERR_SHAPE;
+    }
+    return META_OK;
+}
+
+Layout make_layout(const meta_problem* pr) {
+    Layout L;
+    std::memset(&L, 0, sizeof(L));
+    const int d = pr->ndim;
+    L.ndim = d;
+    L.T = pr->T;
+    Geom& g = L.g;
+    g.nz = d == 3 ? pr->dims[0] : 1;
+    g.ny = pr->dims[d - 2];
+    g.nx = pr->dims[d - 1];
+    g.P = (g.nx + 3) / 4 * 4;
+    g.slab = (long long)g.ny * g.P;
+    g.inst = (long long)g.nz * g.slab;
+    g.B = pr->batch;
+    const long long N = (long long)g.nz * g.ny * g.nx;
+    long long nblk = (N + 2047) / 2048;
+    if (nblk < 1) nblk = 1;
+    if (nblk > 256) nblk = 256;
+    L.nblk = (int)nblk;
+
+    const size_t fslice = (size_t)g.inst * 4;  // bytes of one pitched field
+    const size_t B = (size_t)g.B;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    L.off_fault = take(16);
+    L.off_maxdisp = take(sizeof(unsigned int) * (size_t)pr->T * B);
+    L.off_partials = take(sizeof(double) * 3 * B * (size_t)L.nblk);
+    L.off_states = take(fslice * 2 * B * (size_t)(pr->T + 1));
+    L.off_u = take(fslice * (size_t)d * B * (size_t)pr->T);
+    L.off_SA = take(fslice * (size_t)d * B);
+    L.off_SB = take(fslice * (size_t)d * B);
+    L.off_SV = take(fslice * (size_t)d * B);
+    L.off_IA = take(fslice * B);
+    L.off_PA = take(fslice * B);
+    L.off_IB = take(fslice * B);
+    L.off_PB = take(fslice * B);
+    L.off_PTH = take(fslice * B);
+    L.off_DH = take(fslice * B);
+    L.off_IHP = take(fslice * B);
+    L.off_PHP = take(fslice * B);
+    L.total = off;
+    return L;
+}
+
+// Gaussian taps of K: exp(-k^2 / (2 sigma^2)), |k| <= r = ceil(3 sigma),
+// normalised to sum 1 in double and rounded to float.
+//  xpass:   w[k'] = tap(k' - r4) for k' in [r4 - r, r4 + r], 0 elsewhere,
+//           kp = roundup(r4 + r + 1, 8)   (window starts r4 left of the output)
+//  strided: w[k']  = tap(k' - r) for k' in [0, 2r], kp = roundup(2r + 1, 8)
+void make_taps(float sigma, Taps* xpass, Taps* strided) {
+    const int r = (int)std::ceil(3.0 * (double)sigma);
+    double t[2 * kMaxR + 1];
+    double Z = 0.0;
+    for (int k = -r; k <= r; ++k) {
+        t[k + r] = std::exp(-(double)k * (double)k / (2.0 * (double)sigma * (double)sigma));
+        Z += t[k + r];
+    }
+    const int r4 = (r + 3) / 4 * 4;
+    std::memset(xpass, 0, sizeof(Taps));
+    std::memset(strided, 0, sizeof(Taps));
+    xpass->r = strided->r = r;
+    xpass->r4 = strided->r4 = r4;
+    xpass->kp = (r4 + r + 1 + 7) / 8 * 8;
+    strided->kp = (2 * r + 1 + 7) / 8 * 8;
+    for (int k = -r; k <= r; ++k) {
+        xpass->w[r4 + k] = (float)(t[k + r] / Z);
+        strided->w[r + k] = (float)(t[k + r] / Z);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map over `nslices` pitched slices starting at `base`: dims
+// {nx, ny, (nz), nslices}; zero fill outside (the zero padding of K).
+bool encode_map(CUtensorMap* m, const Geom& g, int ndim, void* base, int nslices, int bx,
+                int by, int bz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+    cuuint32_t rank;
+    if (ndim == 2) {
+        rank = 3;
+        dims[0] = g.nx;
+        dims[1] = g.ny;
+        dims[2] = nslices;
+        strides[0] = (cuuint64_t)g.P * 4;
+        strides[1] = (cuuint64_t)g.inst * 4;
+        box[0] = bx;
+        box[1] = by;
+        box[2] = 1;
+    } else {
+        rank = 4;
+        dims[0] = g.nx;
+        dims[1] = g.ny;
+        dims[2] = g.nz;
+        dims[3] = nslices;
+        strides[0] = (cuuint64_t)g.P * 4;
+        strides[1] = (cuuint64_t)g.slab * 4;
+        strides[2] = (cuuint64_t)g.inst * 4;
+        box[0] = bx;
+        box[1] = by;
+        box[2] = bz;
+        box[3] = 1;
+    }
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct Ctx {
+    Layout L;
+    char* ws;
+    Taps tx, ts;
+    CUtensorMap tmI, tmP, tmSAy, tmSBz, tmSVx;
+    cudaStream_t st;
+    unsigned int* fault;
+    unsigned int* maxdisp;
+    double* partials;
+    float *states, *u, *SA, *SB, *SV, *IA, *PA, *IB, *PB, *PTH, *DH, *IHP, *PHP;
+};
+
+meta_status map_status(cudaError_t e) { return e == cudaSuccess ? META_OK : META_ERR_CUDA; }
+
+// Optional per-launch event timer (profiling aid; see meta_timer_start).
+struct Timer {
+    bool on = false;
+    int cap = 0, used = 0;
+    std::vector<cudaEvent_t> ev;  // 2 per launch
+    std::vector<int> cls;
+};
+Timer g_timer;
+
+struct Timed {
+    int slot = -1;
+    cudaStream_t st;
+    Timed(int k, cudaStream_t s) : st(s) {
+        if (g_timer.on && g_timer.used < g_timer.cap) {
+            slot = g_timer.used++;
+            g_timer.cls[slot] = k;
+            cudaEventRecord(g_timer.ev[2 * slot], st);
+        }
+    }
+    ~Timed() {
+        if (slot >= 0) cudaEventRecord(g_timer.ev[2 * slot + 1], st);
+    }
+};
+
+meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* stream, Ctx* c) {
+    meta_status s = validate(pr);
+    if (s != META_OK) return s;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return META_ERR_WORKSPACE;
+    c->L = make_layout(pr);
+    if (ws_bytes < c->L.total) return META_ERR_WORKSPACE;
+    c->ws = static_cast<char*>(ws);
+    c->st = static_cast<cudaStream_t>(stream);
+    const Layout& L = c->L;
+    c->fault = reinterpret_cast<unsigned int*>(c->ws + L.off_fault);
+    c->maxdisp = reinterpret_cast<unsigned int*>(c->ws + L.off_maxdisp);
+    c->partials = reinterpret_cast<double*>(c->ws + L.off_partials);
+    auto F = [&](size_t off) { return reinterpret_cast<float*>(c->ws + off); };
+    c->states = F(L.off_states);
+    c->u = F(L.off_u);
+    c->SA = F(L.off_SA);
+    c->SB = F(L.off_SB);
+    c->SV = F(L.off_SV);
+    c->IA = F(L.off_IA);
+    c->PA = F(L.off_PA);
+    c->IB = F(L.off_IB);
+    c->PB = F(L.off_PB);
+    c->PTH = F(L.off_PTH);
+    c->DH = F(L.off_DH);
+    c->IHP = F(L.off_IHP);
+    c->PHP = F(L.off_PHP);
+    make_taps(pr->sigma, &c->tx, &c->ts);
+    const Geom& g = L.g;
+    const int d = L.ndim, B = g.B;
+    const int LW = kTX + 2 * (c->tx.r4 + 8);
+    const int nst = 2 * B * (L.T + 1);
+    bool ok = true;
+    if (d == 2) {
+        ok &= encode_map(&c->tmI, g, 2, c->states, nst, LW, kRows + 2, 1);
+        ok &= encode_map(&c->tmP, g, 2, c->states, nst, LW, kRows, 1);
+        ok &= encode_map(&c->tmSAy, g, 2, c->SA, d * B, kTXS, kTA + c->ts.kp, 1);
+        ok &= encode_map(&c->tmSVx, g, 2, c->SV, d * B, LW, kRows, 1);
+        c->tmSBz = c->tmSAy;
+    } else {
+        ok &= encode_map(&c->tmI, g, 3, c->states, nst, LW, 6, 6);
+        ok &= encode_map(&c->tmP, g, 3, c->states, nst, LW, 4, 4);
+        ok &= encode_map(&c->tmSAy, g, 3, c->SA, d * B, kTXS, kTA + c->ts.kp, 1);
+        ok &= encode_map(&c->tmSBz, g, 3, c->SB, d * B, kTXS, 1, kTA + c->ts.kp);
+        ok &= encode_map(&c->tmSVx, g, 3, c->SV, d * B, LW, 4, 4);
+    }
+    return ok ? META_OK : META_ERR_UNSUPPORTED;
+}
+
+#define META_TRY(expr)                                  \
+    do {                                                \
+        meta_status _s = map_status(expr);              \
+        if (_s != META_OK) return _s;                   \
+    } while (0)
+
+// Launch `expr` (a launcher returning cudaError_t) as kernel class k.
+#define META_LAUNCH(k, st, expr)                        \
+    do {                                                \
+        Timed _t((k), (st));                            \
+        meta_status _s = map_status(expr);              \
+        if (_s != META_OK) return _s;                   \
+    } while (0)
+
+// Forward shooting t = 0..T-1 (the initial state is already in slot 0).
+meta_status run_forward(Ctx& c, const Coefs& cf) {
+    const Layout& L = c.L;
+    const Geom& g = L.g;
+    const int d = L.ndim, B = g.B;
+    META_TRY(cudaMemsetAsync(c.maxdisp, 0, sizeof(unsigned int) * (size_t)L.T * B, c.st));
+    for (int t = 0; t < L.T; ++t) {
+        float* ut = c.u + (size_t)t * d * B * g.inst;
+        // m = p grad I, blurred along x  ->  SA
+        META_LAUNCH(META_K_XPASS_M, c.st,
+                    launch_xpass(d, true, c.tmI, c.tmP, c.tx, g, 2 * t * B, (2 * t + 1) * B, 0, 0,
+                                 c.SA, c.fault, c.st));
+        if (d == 2) {
+            META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                        launch_strided(2, 0, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut,
+                                       c.fault, c.st));
+        } else {
+            META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                        launch_strided(3, 1, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, c.SB,
+                                       c.fault, c.st));
+            META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                        launch_strided(3, 0, c.tmSBz, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut,
+                                       c.fault, c.st));
+        }
+        META_LAUNCH(META_K_ADVECT, c.st, launch_advect(g, d, cf, t, c.states, c.u, c.maxdisp, c.st));
+    }
+    return META_OK;
+}
+
+// Reverse sweep; (IA, PA) hold the adjoints of (I_T, p_T) on entry.
+// mode 1: cost gradient into out0; mode 2: shooting adjoint into out0 / gI0.
+meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
+    const Layout& L = c.L;
+    const Geom& g = L.g;
+    const int d = L.ndim, B = g.B;
+    float* Icur = c.IA;
+    float* Pcur = c.PA;
+    float* Inext = c.IB;
+    float* Pnext = c.PB;
+    for (int t = L.T - 1; t >= 0; --t) {
+        META_LAUNCH(META_K_ADJ_PRE, c.st,
+                    launch_adj_pre(g, d, cf, t, c.states, c.u, Icur, Pcur, c.PTH, c.DH, c.st));
+        META_LAUNCH(META_K_ADJ_GATHER, c.st,
+                    launch_adj_gather(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, c.PTH, c.DH,
+                                      c.SV, c.IHP, c.PHP, c.st));
+        // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
+        META_LAUNCH(META_K_XPASS_ADJ, c.st,
+                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
+                                 c.fault, c.st));
+        float* mh;
+        if (d == 2) {
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(2, 0, c.tmSAy, c.ts, g, 0, 0, d * B, cf.rho, -1.f, c.SB,
+                                       c.fault, c.st));
+            mh = c.SB;
+        } else {
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(3, 1, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, c.SB,
+                                       c.fault, c.st));
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(3, 0, c.tmSBz, c.ts, g, 0, 0, d * B, cf.rho, -1.f, c.SV,
+                                       c.fault, c.st));
+            mh = c.SV;
+        }
+        const int m = (t == 0) ? mode : 0;
+        META_LAUNCH(META_K_ADJ_GRADP, c.st,
+                    launch_adj_gradp(g, d, cf, t, m, c.states, c.u, mh, c.IHP, c.PHP, Inext,
+                                     Pnext, out0, gI0, c.st));
+        float* tI = Icur;
+        float* tP = Pcur;
+        Icur = Inext;
+        Pcur = Pnext;
+        Inext = tI;
+        Pnext = tP;
+    }
+    return META_OK;
+}
+
+}  // namespace
+}  // namespace meta
+
+using namespace meta;
+
+extern "C" {
+
+meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes) {
+    if (!bytes) return META_ERR_INVALID_ARG;
+    const meta_status s = validate(prob);
+    if (s != META_OK) return s;
+    *bytes = make_layout(prob).total;
+    return META_OK;
+}
+
+meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const float* p0,
+                               const float* mu, const float* rho, float* I1, float* p1, void* ws,
+                               size_t ws_bytes, void* stream) {
+    if (!I0 || !p0 || !mu || !rho) return META_ERR_INVALID_ARG;
+    Ctx c;
+    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const Geom& g = c.L.g;
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    META_LAUNCH(META_K_PACK, c.st,
+                launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
+    s = run_forward(c, cf);
+    if (s != META_OK) return s;
+    if (I1 || p1) {
+        const size_t slot = (size_t)c.L.T * 2 * g.B * g.inst;
+        META_LAUNCH(META_K_UNPACK, c.st,
+                    launch_unpack(g, c.L.ndim, c.states + slot,
+                                  c.states + slot + (size_t)g.B * g.inst, I1, p1, c.st));
+    }
+    return META_OK;
+}
+
+meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const float* rho,
+                               const float* gI1, const float* gp1, float* gI0, float* gp0,
+                               void* ws, size_t ws_bytes, void* stream) {
+    if (!mu || !rho || !gI1 || !gp0) return META_ERR_INVALID_ARG;
+    Ctx c;
+    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    META_LAUNCH(META_K_ADJ_INIT, c.st, launch_adj_init(c.L.g, c.L.ndim, gI1, gp1, c.IA, c.PA, c.st));
+    return run_adjoint(c, cf, 2, gp0, gI0);
+}
+
+meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const float* J,
+                               const float* p0, const float* mu, const float* rho,
+                               const float* lambda, double* cost, float* grad, void* ws,
+                               size_t ws_bytes, void* stream) {
+    if (!I0 || !J || !p0 || !mu || !rho || !lambda || !cost) return META_ERR_INVALID_ARG;
+    Ctx c;
+    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const Geom& g = c.L.g;
+    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T};
+    META_LAUNCH(META_K_PACK, c.st,
+                launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
+    s = run_forward(c, cf);
+    if (s != META_OK) return s;
+    META_LAUNCH(META_K_COST, c.st,
+                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.IA, c.PA, c.partials,
+                            c.L.nblk, cost, c.st));
+    if (!grad) return META_OK;
+    return run_adjoint(c, cf, 1, grad, nullptr);
+}
+
+meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
+                                  unsigned int* fault_bits) {
+    if (!ws || ws_bytes < 16 || !fault_bits) return META_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int* f = static_cast<unsigned int*>(ws);  // off_fault == 0
+    if (cudaStreamSynchronize(st) != cudaSuccess) return META_ERR_CUDA;
+    if (cudaMemcpy(fault_bits, f, sizeof(unsigned int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return META_ERR_CUDA;
+    if (clear) {
+        if (cudaMemsetAsync(f, 0, sizeof(unsigned int), st) != cudaSuccess) return META_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return META_ERR_CUDA;
+    }
+    return *fault_bits ? META_ERR_TIMEOUT : META_OK;
+}
+
+meta_status meta_timer_start(int cap) {
+    if (cap < 1 || cap > (1 << 22)) return META_ERR_INVALID_ARG;
+    Timer& T = g_timer;
+    if ((int)T.ev.size() < 2 * cap) {
+        const size_t old = T.ev.size();
+        T.ev.resize(2 * (size_t)cap);
+        for (size_t i = old; i < T.ev.size(); ++i)
+            if (cudaEventCreate(&T.ev[i]) != cudaSuccess) {
+                T.ev.resize(i);
+                return META_ERR_CUDA;
+            }
+    }
+    T.cls.assign(cap, -1);
+    T.cap = cap;
+    T.used = 0;
+    T.on = true;
+    return META_OK;
+}
+
+meta_status meta_timer_stop(float* ms_per_class, int* launches_per_class) {
+    Timer& T = g_timer;
+    if (!T.on) return META_ERR_INVALID_ARG;
+    T.on = false;
+    for (int k = 0; k < META_K_COUNT; ++k) {
+        if (ms_per_class) ms_per_class[k] = 0.f;
+        if (launches_per_class) launches_per_class[k] = 0;
+    }
+    for (int i = 0; i < T.used; ++i) {
+        if (cudaEventSynchronize(T.ev[2 * i + 1]) != cudaSuccess) return META_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, T.ev[2 * i], T.ev[2 * i + 1]) != cudaSuccess)
+            return META_ERR_CUDA;
+        const int k = T.cls[i];
+        if (k >= 0 && k < META_K_COUNT) {
+            if (ms_per_class) ms_per_class[k] += ms;
+            if (launches_per_class) launches_per_class[k] += 1;
+        }
+    }
+    T.used = 0;
+    return META_OK;
+}
+
+const char* meta_kernel_name(int k) {
+    static const char* names[META_K_COUNT] = {
+        "pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init",
+        "adj_pre", "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack"};
+    return (k >= 0 && k < META_K_COUNT) ? names[k] : "unknown";
+}
+
+const char* meta_status_string(meta_status s) {
+    switch (s) {
+        case META_OK: return "ok";
+        case META_ERR_INVALID_ARG: return "invalid argument";
+        case META_ERR_SHAPE: return "unsupported shape";
+        case META_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case META_ERR_CUDA: return "CUDA error";
+        case META_ERR_TIMEOUT: return "device-side wait timed out";
+        case META_ERR_NONFINITE: return "non-finite value";
+        case META_ERR_UNSUPPORTED: return "unsupported device or driver";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,321 @@
+// meta_blur.cu -- the Gaussian RKHS kernel K (Sec. 2.1 of arXiv:2106.08817)
+// as separable 1-D passes, sm_103a.
+//
+//  * k_xpass<NDIM, GRADP>: pass along the contiguous axis x.  With GRADP it is
+//    fused with the momentum field of Eq. 3: it stages I and p tiles (with a
+//    one-voxel halo in y/z for the central differences) by TMA, forms
+//    m_i = p * D_i I in shared memory, and blurs every component along x.
+//    Without GRADP it blurs one component field.
+//  * k_strided<NDIM, AXIS>: pass along a strided axis (y, or z in 3-D): a
+//    column tile with an r-voxel halo is staged by one TMA load; the
+//    out-of-bounds fill of TMA supplies the zero padding of K.
+//
+// Every thread produces 8 consecutive outputs from a register window that
+// slides over shared memory in chunks of 8 taps, so each shared-memory value
+// feeds up to 8 FMAs.  No tensor cores: a banded Toeplitz product of 37 taps
+// over 4-12 bytes per voxel is not a dense contraction.
+#include "meta_kernels.h"
+
+namespace meta {
+
+template <int NDIM, bool GRADP>
+__global__ void __launch_bounds__(256)
+k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
+        const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0,
+        float* __restrict__ out, unsigned int* fault) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* base = reinterpret_cast<float*>(smem_raw + 128);
+
+    const int HX = taps.r4 + 8;       // x halo (multiple of 4)
+    const int LW = kTX + 2 * HX;      // staged row length
+    const int rowsI = (NDIM == 2) ? (kRows + 2) : 36;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTX;
+    int y0, z0;
+    if constexpr (NDIM == 2) {
+        y0 = blockIdx.y * kRows;
+        z0 = 0;
+    } else {
+        const int nty = (g.ny + 3) / 4;
+        y0 = (blockIdx.y % nty) * 4;
+        z0 = (blockIdx.y / nty) * 4;
+    }
+    // GRADP: one CTA per instance b = blockIdx.z.  Plain: one CTA per slice.
+    const int b = GRADP ? (int)blockIdx.z : (int)(blockIdx.z % g.B);
+
+    // sub-buffers start on 128-byte boundaries (TMA destinations)
+    float* sI = base;
+    float* sP = GRADP ? sI + ((rowsI * LW + 31) & ~31) : nullptr;
+    float* sM = GRADP ? sP + ((kRows * LW + 31) & ~31) : base;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if constexpr (GRADP) {
+            mbar_arrive_expect_tx(bar, (uint32_t)((rowsI + kRows) * LW * 4));
+            tma_load_box<NDIM>(sI, &tmI, bar, x0 - HX, y0 - 1, z0 - 1, sliceI + b);
+            tma_load_box<NDIM>(sP, &tmP, bar, x0 - HX, y0, z0, sliceP + b);
+        } else {
+            mbar_arrive_expect_tx(bar, (uint32_t)(kRows * LW * 4));
+            tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)blockIdx.z);
+        }
+    }
+    // every thread waits (bounded); the CTA leaves together if any wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0, fault))) return;
+
+    const int ncomp = GRADP ? NDIM : 1;
+    if constexpr (GRADP) {
+        // m_i = p * D_i I on the whole staged row range (finite everywhere;
+        // columns 0 and LW-1 only ever meet zero taps).
+        for (int idx = tid; idx < kRows * LW; idx += blockDim.x) {
+            const int row = idx / LW;
+            const int c = idx - row * LW;
+            const int ty = (NDIM == 2) ? row : (row & 3);
+            const int tz = (NDIM == 2) ? 0 : (row >> 2);
+            const int x = x0 - HX + c, y = y0 + ty, z = z0 + tz;
+            float m[NDIM];
+            if (x < 0 || x >= g.nx || y >= g.ny || z >= g.nz) {
+#pragma unroll
+                for (int a = 0; a < NDIM; ++a) m[a] = 0.f;
+            } else {
+                const int rI = (NDIM == 2) ? (ty + 1) : ((tz + 1) * 6 + ty + 1);
+                const float* Ir = sI + rI * LW;
+                const int cl = (x > 0) ? max(c - 1, 0) : c;
+                const int cr = (x < g.nx - 1) ? min(c + 1, LW - 1) : c;
+                const float gx = 0.5f * (Ir[cr] - Ir[cl]);
+                const float gy = 0.5f * (sI[(rI + (y < g.ny - 1 ? 1 : 0)) * LW + c] -
+                                         sI[(rI - (y > 0 ? 1 : 0)) * LW + c]);
+                const float p = sP[row * LW + c];
+                if constexpr (NDIM == 2) {
+                    m[0] = p * gy;
+                    m[1] = p * gx;
+                } else {
+                    const float gz = 0.5f * (sI[(rI + (z < g.nz - 1 ? 6 : 0)) * LW + c] -
+                                             sI[(rI - (z > 0 ? 6 : 0)) * LW + c]);
+                    m[0] = p * gz;
+                    m[1] = p * gy;
+                    m[2] = p * gx;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) sM[(a * kRows + row) * LW + c] = m[a];
+        }
+        __syncthreads();
+    }
+
+    // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`.
+    const int tx = tid & 15;
+    const int row = tid >> 4;
+    const int ty = (NDIM == 2) ? row : (row & 3);
+    const int tz = (NDIM == 2) ? 0 : (row >> 2);
+    const int y = y0 + ty, z = z0 + tz;
+    const int x = x0 + tx * kBX;
+    const bool row_ok = (y < g.ny) && (z < g.nz);
+    for (int a = 0; a < ncomp; ++a) {
+        const float* src = sM + (a * kRows + row) * LW + tx * kBX + (HX - taps.r4);
+        float acc[kBX];
+#pragma unroll
+        for (int j = 0; j < kBX; ++j) acc[j] = 0.f;
+        float4 c0 = lds4(src), c1 = lds4(src + 4);
+        for (int kb = 0; kb < taps.kp; kb += 8) {
+            const float4 n0 = lds4(src + kb + 8), n1 = lds4(src + kb + 12);
+            const float win[16] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w,
+                                   n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const float wt = taps.w[kb + kk];
+#pragma unroll
+                for (int j = 0; j < kBX; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+            }
+            c0 = n0;
+            c1 = n1;
+        }
+        if (row_ok) {
+            const int slice = GRADP ? (out_slice0 + a * g.B + b) : (out_slice0 + (int)blockIdx.z);
+            float* o = out + (long long)slice * g.inst + gidx(g, z, y, x);
+            if (x < g.P) *reinterpret_cast<float4*>(o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            if (x + 4 < g.P)
+                *reinterpret_cast<float4*>(o + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        }
+    }
+}
+
+// AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
+template <int NDIM, int AXIS>
+__global__ void __launch_bounds__(512)
+k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g,
+          int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul,
+          float* __restrict__ out, unsigned int* fault) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* s = reinterpret_cast<float*>(smem_raw + 128);
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 31;
+    const int ta = tid >> 5;
+    const int x0 = blockIdx.x * kTXS;
+    const int slice = blockIdx.z;           // comp * B + b
+    const int b = slice % g.B;
+    int a0, y, z, n_axis;
+    if constexpr (NDIM == 2) {
+        a0 = blockIdx.y * kTA;
+        y = 0;
+        z = 0;
+        n_axis = g.ny;
+    } else if constexpr (AXIS == 1) {
+        const int nt = (g.ny + kTA - 1) / kTA;
+        a0 = (blockIdx.y % nt) * kTA;
+        z = blockIdx.y / nt;
+        y = 0;
+        n_axis = g.ny;
+    } else {
+        const int nt = (g.nz + kTA - 1) / kTA;
+        a0 = (blockIdx.y % nt) * kTA;
+        y = blockIdx.y / nt;
+        z = 0;
+        n_axis = g.nz;
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(kTXS * (kTA + taps.kp) * 4));
+        if constexpr (NDIM == 2)
+            tma_load_3d(s, &tm, bar, x0, a0 - taps.r, in_slice0 + slice);
+        else if constexpr (AXIS == 1)
+            tma_load_4d(s, &tm, bar, x0, a0 - taps.r, z, in_slice0 + slice);
+        else
+            tma_load_4d(s, &tm, bar, x0, y, a0 - taps.r, in_slice0 + slice);
+    }
+    // every thread waits (bounded); the CTA leaves together if any wait ran out
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0, fault))) return;
+
+    const float* src = s + (ta * kBA) * kTXS + tx;
+    float acc[kBA];
+    float cur[8];
+#pragma unroll
+    for (int j = 0; j < kBA; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cur[j] = src[j * kTXS];
+    for (int kb = 0; kb < taps.kp; kb += 8) {
+        float win[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            win[j] = cur[j];
+            win[8 + j] = src[(kb + 8 + j) * kTXS];
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const float wt = taps.w[kb + kk];
+#pragma unroll
+            for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cur[j] = win[8 + j];
+    }
+    const int x = x0 + tx;
+    if (x >= g.nx) return;
+    const float sc = scale ? scale_mul * scale[b] : 1.f;
+    float* o = out + (long long)(out_slice0 + slice) * g.inst;
+#pragma unroll
+    for (int j = 0; j < kBA; ++j) {
+        const int a = a0 + ta * kBA + j;
+        if (a < n_axis) {
+            long long off;
+            if constexpr (NDIM == 2)
+                off = gidx(g, 0, a, x);
+            else if constexpr (AXIS == 1)
+                off = gidx(g, z, a, x);
+            else
+                off = gidx(g, a, y, x);
+            o[off] = sc * acc[j];
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+size_t xpass_smem(int ndim, bool gradp, int r4) {
+    const int LW = kTX + 2 * (r4 + 8);
+    if (!gradp) return 128 + (size_t)kRows * LW * 4;
+    const int rowsI = ndim == 2 ? kRows + 2 : 36;
+    const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)((kRows * LW + 31) & ~31) +
+                     (size_t)ndim * kRows * LW;
+    return 128 + f * 4;
+}
+
+size_t strided_smem(int kp) { return 128 + (size_t)kTXS * (kTA + kp) * 4; }
+
+template <int NDIM, bool GRADP>
+static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps,
+                                  const Geom& g, int sliceI, int sliceP, int out_slice0,
+                                  int nslices, float* out, unsigned int* fault, cudaStream_t st) {
+    const size_t smem = xpass_smem(NDIM, GRADP, taps.r4);
+    cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.nx + kTX - 1) / kTX,
+              NDIM == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
+              GRADP ? g.B : nslices);
+    k_xpass<NDIM, GRADP><<<grid, 256, smem, st>>>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                                  out, fault);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
+                         const Taps& taps, const Geom& g, int sliceI, int sliceP, int out_slice0,
+                         int nslices, float* out, unsigned int* fault, cudaStream_t st) {
+    if (ndim == 2)
+        return gradp ? launch_xpass_t<2, true>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                               nslices, out, fault, st)
+                     : launch_xpass_t<2, false>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                                nslices, out, fault, st);
+    return gradp ? launch_xpass_t<3, true>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0, nslices,
+                                           out, fault, st)
+                 : launch_xpass_t<3, false>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                            nslices, out, fault, st);
+}
+
+template <int NDIM, int AXIS>
+static cudaError_t launch_strided_t(const CUtensorMap& tm, const Taps& taps, const Geom& g,
+                                    int in_slice0, int out_slice0, int nslices,
+                                    const float* scale, float scale_mul, float* out,
+                                    unsigned int* fault, cudaStream_t st) {
+    const size_t smem = strided_smem(taps.kp);
+    cudaError_t e = cudaFuncSetAttribute(k_strided<NDIM, AXIS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    unsigned gy;
+    if (NDIM == 2)
+        gy = (g.ny + kTA - 1) / kTA;
+    else if (AXIS == 1)
+        gy = ((g.ny + kTA - 1) / kTA) * g.nz;
+    else
+        gy = ((g.nz + kTA - 1) / kTA) * g.ny;
+    dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
+    k_strided<NDIM, AXIS><<<grid, 512, smem, st>>>(tm, taps, g, in_slice0, out_slice0, scale,
+                                                   scale_mul, out, fault);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps& taps,
+                           const Geom& g, int in_slice0, int out_slice0, int nslices,
+                           const float* scale, float scale_mul, float* out, unsigned int* fault,
+                           cudaStream_t st) {
+    if (ndim == 2)
+        return launch_strided_t<2, 0>(tm, taps, g, in_slice0, out_slice0, nslices, scale,
+                                      scale_mul, out, fault, st);
+    if (axis == 1)
+        return launch_strided_t<3, 1>(tm, taps, g, in_slice0, out_slice0, nslices, scale,
+                                      scale_mul, out, fault, st);
+    return launch_strided_t<3, 0>(tm, taps, g, in_slice0, out_slice0, nslices, scale, scale_mul,
+                                  out, fault, st);
+}
+
+}  // namespace meta

@@ -1,0 +1,176 @@
+// meta_common.cuh -- shared definitions of the sm_103a semi-Lagrangian
+// Metamorphosis kernels: geometry, tap tables, TMA / mbarrier helpers in
+// inline PTX, the relative-coordinate foot computation and the workspace map.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace meta {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxTaps = 128;  // padded tap table length (r <= 54)
+constexpr int kMaxR = 54;      // sigma <= 18
+constexpr int kBX = 8;         // x-pass: outputs per thread along x
+constexpr int kTX = 128;       // x-pass: outputs per CTA along x
+constexpr int kRows = 16;      // x-pass: rows per CTA (2-D: 16 y; 3-D: 4 z x 4 y)
+constexpr int kBA = 8;         // strided pass: outputs per thread along the axis
+constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
+constexpr int kTXS = 32;       // strided pass: columns per CTA
+
+// Fault bits latched in the workspace header.
+constexpr unsigned kFaultTmaTimeout = 1u;
+
+// ---------------------------------------------------------------- geometry
+// An instance is an (nz,) ny x nx grid stored with row pitch P floats
+// (P = nx rounded up to a multiple of 4, so that every row starts on a 16-byte
+// boundary as TMA requires).  For 2-D problems nz = 1.
+struct Geom {
+    int nz, ny, nx;   // extents (nz = 1 in 2-D)
+    int P;            // row pitch in floats
+    long long slab;   // ny * P
+    long long inst;   // nz * ny * P  (floats per instance slice)
+    int B;            // batch
+};
+
+__host__ __device__ inline long long gidx(const Geom& g, int z, int y, int x) {
+    return (long long)z * g.slab + (long long)y * g.P + x;
+}
+
+// Gaussian taps passed by value (constant bank, uniform reads).
+struct Taps {
+    int r;       // radius ceil(3 sigma)
+    int kp;      // taps in the loop, multiple of 8 (zero padded)
+    int r4;      // x-pass: radius rounded up to a multiple of 4
+    float w[kMaxTaps];
+};
+
+// Per-launch scalars of the scheme.
+struct Coefs {
+    const float* mu;      // [B]
+    const float* rho;     // [B]
+    const float* lambda;  // [B]
+    float dt;             // 1/T
+};
+
+// ------------------------------------------------- relative-coordinate foot
+// Foot of voxel c displaced by d (y = c + d), clamped to [0, n-1].  Computed
+// from the displacement rather than from the absolute coordinate so that
+// sub-ulp displacements keep their sign in FP32.  i0 = floor(y) lowered to
+// n-2 at the far edge, f = y - i0 in [0, 1], inside = clamp inactive.
+struct Foot1 {
+    int i0;
+    float f;
+    bool inside;
+};
+
+__device__ __forceinline__ Foot1 foot1(int c, float d, int n) {
+    Foot1 r;
+    const float lo = -(float)c;           // y <= 0      <=> d <= -c
+    const float hi = (float)(n - 1 - c);  // y >= n - 1  <=> d >= n-1-c
+    if (d <= lo) {
+        r.i0 = 0;
+        r.f = 0.f;
+        r.inside = false;
+    } else if (d >= hi) {
+        r.i0 = n - 2;
+        r.f = 1.f;
+        r.inside = false;
+    } else {
+        const float fl = floorf(d);
+        r.i0 = c + (int)fl;
+        r.f = d - fl;
+        r.inside = true;
+    }
+    return r;
+}
+
+// ----------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on phase `parity`: gives up after ~2 s (or 2^24 polls), latches
+// kFaultTmaTimeout in *fault and returns false.  A TMA copy that completes
+// normally takes microseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned int* fault) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && globaltimer_ns() - t0 > 2000000000ull) break;
+    }
+    atomicOr(fault, kFaultTmaTimeout);
+    return false;
+}
+
+// Tiled TMA loads into shared memory, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Load a box whose innermost coordinate is x, at (x, y[, z], slice).
+template <int NDIM>
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                             int x, int y, int z, int slice) {
+    if constexpr (NDIM == 2)
+        tma_load_3d(dst, map, bar, x, y, slice);
+    else
+        tma_load_4d(dst, map, bar, x, y, z, slice);
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+}
+
+}  // namespace meta

@@ -1,0 +1,56 @@
+// meta_kernels.h -- internal launchers of the sm_103a kernels (not part of the C ABI).
+#pragma once
+
+#include "meta_common.cuh"
+
+namespace meta {
+
+// Blur passes (meta_blur.cu).
+size_t xpass_smem(int ndim, bool gradp, int r4);
+size_t strided_smem(int kp);
+
+// x-pass.  gradp: reads I slice (sliceI + b) with a one-voxel y/z halo and p
+// slice (sliceP + b) through tmI / tmP, writes NDIM component slices
+// out_slice0 + a*B + b.  Plain: reads slice sliceI + s through tmI and writes
+// out_slice0 + s, for s < nslices.
+cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
+                         const Taps& taps, const Geom& g, int sliceI, int sliceP, int out_slice0,
+                         int nslices, float* out, unsigned int* fault, cudaStream_t st);
+
+// Strided pass along `axis` (2-D: 0 = y; 3-D: 1 = y, 0 = z) of slices
+// in_slice0 + s -> out_slice0 + s, s < nslices, multiplied by
+// scale_mul * scale[s % B] when scale is not null.
+cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps& taps,
+                           const Geom& g, int in_slice0, int out_slice0, int nslices,
+                           const float* scale, float scale_mul, float* out, unsigned int* fault,
+                           cudaStream_t st);
+
+// Pointwise / gather kernels (meta_step.cu).  Buffers are pitched slices of
+// g.inst floats; `states` holds slice (t*2 + f)*B + b for f = 0 (I), 1 (p);
+// `u` holds slice (t*NDIM + a)*B + b.
+cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p0, float* dstI,
+                        float* dstP, cudaStream_t st);
+cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const float* srcP,
+                          float* I1, float* p1, cudaStream_t st);
+cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
+                          const float* u, unsigned int* maxdisp, cudaStream_t st);
+cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
+                        const float* u, const float* J, float* Ih, float* ph, double* partials,
+                        int nblk, double* cost, cudaStream_t st);
+cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
+                            float* Ih, float* ph, cudaStream_t st);
+cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
+                           const float* u, const float* Ih1, const float* ph1, float* pth,
+                           float* dh, cudaStream_t st);
+cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
+                              const float* states, const float* u, const unsigned int* maxdisp,
+                              const float* Ih1, const float* pth, const float* dh, float* vh,
+                              float* Ihp, float* php, cudaStream_t st);
+// mode 0: write (Ih, ph) pitched; mode 1: cost gradient into grad (contiguous);
+// mode 2: shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
+cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
+                             const float* states, const float* u, const float* mh,
+                             const float* Ihp, const float* php, float* Ih, float* ph,
+                             float* grad_or_gp0, float* gI0, cudaStream_t st);
+
+}  // namespace meta

@@ -1,0 +1,591 @@
+// meta_step.cu -- pointwise and gather kernels of the semi-Lagrangian step and
+// of its discrete adjoint (arXiv:2106.08817, Eq. 3-4, Sec. 2.3), sm_103a.
+//
+// Forward step t (after the blur passes have produced u_t = K(p_t grad I_t)):
+//   k_advect      div v, foot y = x - dt v (v = -rho u), bi/trilinear gathers of
+//                 I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~,
+//                 and the per-instance max displacement (window of the adjoint).
+// Adjoint step t (reverse), the transpose of the step above:
+//   k_adj_pre     per source x: p~^ = p^'(1 - dt div v) + dt mu I^', div^ = -dt p~ p^'
+//   k_adj_gather  per node n: S^T by gather over the sources whose foot cell
+//                 touches n (fixed order, no atomics), the foot derivative y^,
+//                 and v^ = -dt y^ + D^T div^
+//   (blur of v^ with K = K^T, scaled by -rho, in meta_blur.cu)
+//   k_adj_gradp   p^ += sum_i m^_i D_i I,  I^ += sum_i D_i^T (m^_i p)
+// Cost (Eq. 4): k_cost_partials + k_cost_final, FP64 partials in a fixed tree.
+#include "meta_kernels.h"
+
+namespace meta {
+
+namespace {
+
+constexpr int kPX = 32, kPY = 8;  // pointwise block
+
+struct Vox {
+    int b, z, y, x;
+    bool ok;
+};
+
+template <int NDIM>
+__device__ __forceinline__ Vox vox_of(const Geom& g) {
+    Vox v;
+    const int nyt = (g.ny + kPY - 1) / kPY;
+    v.b = blockIdx.z;
+    v.x = blockIdx.x * kPX + threadIdx.x;
+    v.y = (blockIdx.y % nyt) * kPY + threadIdx.y;
+    v.z = (NDIM == 3) ? (int)(blockIdx.y / nyt) : 0;
+    v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
+    return v;
+}
+
+template <int NDIM>
+dim3 pgrid(const Geom& g) {
+    return dim3((g.nx + kPX - 1) / kPX, ((g.ny + kPY - 1) / kPY) * g.nz, g.B);
+}
+
+__device__ __forceinline__ long long cidx(const Geom& g, const Vox& v) {
+    return (((long long)v.b * g.nz + v.z) * g.ny + v.y) * g.nx + v.x;
+}
+
+__device__ __forceinline__ const float* slice_of(const float* base, const Geom& g, long long s) {
+    return base + s * g.inst;
+}
+__device__ __forceinline__ float* slice_of(float* base, const Geom& g, long long s) {
+    return base + s * g.inst;
+}
+
+// Displacement of the foot along one axis, y - x = -dt v = (dt rho) u.  The
+// forward step and every adjoint kernel call exactly this expression, so the
+// gather-form transpose sees bit-identical feet.
+__device__ __forceinline__ float disp_of(float dtrho, float u) { return dtrho * u; }
+
+// Central difference of f at linear offset o along a stride s, edge replicated.
+__device__ __forceinline__ float cdiff(const float* f, long long o, long long s, int c, int n) {
+    const long long hi = (c < n - 1) ? s : 0;
+    const long long lo = (c > 0) ? s : 0;
+    return 0.5f * (f[o + hi] - f[o - lo]);
+}
+
+// (D^T w)[c] along a stride s: rows c-1 and c+1 of D, plus the edge rows.
+__device__ __forceinline__ float cdiff_T(const float* w, long long o, long long s, int c, int n) {
+    float r = 0.f;
+    if (c >= 1) r += 0.5f * w[o - s];
+    if (c == n - 1) r += 0.5f * w[o];
+    if (c <= n - 2) r -= 0.5f * w[o + s];
+    if (c == 0) r -= 0.5f * w[o];
+    return r;
+}
+
+template <int NDIM>
+struct Feet {
+    Foot1 f[NDIM];
+    long long base;  // linear offset of the lower corner
+};
+
+template <int NDIM>
+__device__ __forceinline__ Feet<NDIM> feet_of(const Geom& g, const Vox& v, const float* d) {
+    Feet<NDIM> F;
+    if constexpr (NDIM == 2) {
+        F.f[0] = foot1(v.y, d[0], g.ny);
+        F.f[1] = foot1(v.x, d[1], g.nx);
+        F.base = gidx(g, 0, F.f[0].i0, F.f[1].i0);
+    } else {
+        F.f[0] = foot1(v.z, d[0], g.nz);
+        F.f[1] = foot1(v.y, d[1], g.ny);
+        F.f[2] = foot1(v.x, d[2], g.nx);
+        F.base = gidx(g, F.f[0].i0, F.f[1].i0, F.f[2].i0);
+    }
+    return F;
+}
+
+// Multilinear interpolant of `f` at the feet.
+template <int NDIM>
+__device__ __forceinline__ float interp(const Geom& g, const Feet<NDIM>& F, const float* f) {
+    const float* p = f + F.base;
+    if constexpr (NDIM == 2) {
+        const float fy = F.f[0].f, fx = F.f[1].f;
+        const float a = (1.f - fx) * p[0] + fx * p[1];
+        const float b = (1.f - fx) * p[g.P] + fx * p[g.P + 1];
+        return (1.f - fy) * a + fy * b;
+    } else {
+        const float fz = F.f[0].f, fy = F.f[1].f, fx = F.f[2].f;
+        const long long S = g.slab, P = g.P;
+        const float a0 = (1.f - fx) * p[0] + fx * p[1];
+        const float a1 = (1.f - fx) * p[P] + fx * p[P + 1];
+        const float a2 = (1.f - fx) * p[S] + fx * p[S + 1];
+        const float a3 = (1.f - fx) * p[S + P] + fx * p[S + P + 1];
+        const float b0 = (1.f - fy) * a0 + fy * a1;
+        const float b1 = (1.f - fy) * a2 + fy * a3;
+        return (1.f - fz) * b0 + fz * b1;
+    }
+}
+
+// Value and the derivatives along each axis (zero where the clamp is active).
+template <int NDIM>
+__device__ __forceinline__ void interp_grad(const Geom& g, const Feet<NDIM>& F, const float* f,
+                                            float* val, float* dv) {
+    const float* p = f + F.base;
+    if constexpr (NDIM == 2) {
+        const float fy = F.f[0].f, fx = F.f[1].f;
+        const float c00 = p[0], c01 = p[1], c10 = p[g.P], c11 = p[g.P + 1];
+        const float a = (1.f - fx) * c00 + fx * c01;
+        const float b = (1.f - fx) * c10 + fx * c11;
+        *val = (1.f - fy) * a + fy * b;
+        dv[0] = F.f[0].inside ? (b - a) : 0.f;
+        dv[1] = F.f[1].inside ? ((1.f - fy) * (c01 - c00) + fy * (c11 - c10)) : 0.f;
+    } else {
+        const float fz = F.f[0].f, fy = F.f[1].f, fx = F.f[2].f;
+        const long long S = g.slab, P = g.P;
+        const float c000 = p[0], c001 = p[1], c010 = p[P], c011 = p[P + 1];
+        const float c100 = p[S], c101 = p[S + 1], c110 = p[S + P], c111 = p[S + P + 1];
+        const float a0 = (1.f - fx) * c000 + fx * c001;
+        const float a1 = (1.f - fx) * c010 + fx * c011;
+        const float a2 = (1.f - fx) * c100 + fx * c101;
+        const float a3 = (1.f - fx) * c110 + fx * c111;
+        const float b0 = (1.f - fy) * a0 + fy * a1;
+        const float b1 = (1.f - fy) * a2 + fy * a3;
+        *val = (1.f - fz) * b0 + fz * b1;
+        dv[0] = F.f[0].inside ? (b1 - b0) : 0.f;
+        dv[1] = F.f[1].inside ? ((1.f - fz) * (a1 - a0) + fz * (a3 - a2)) : 0.f;
+        const float e0 = (1.f - fy) * (c001 - c000) + fy * (c011 - c010);
+        const float e1 = (1.f - fy) * (c101 - c100) + fy * (c111 - c110);
+        dv[2] = F.f[2].inside ? ((1.f - fz) * e0 + fz * e1) : 0.f;
+    }
+}
+
+template <int NDIM>
+__device__ __forceinline__ void axis_info(const Geom& g, const Vox& v, int* c, int* n,
+                                          long long* s) {
+    if constexpr (NDIM == 2) {
+        c[0] = v.y; n[0] = g.ny; s[0] = g.P;
+        c[1] = v.x; n[1] = g.nx; s[1] = 1;
+    } else {
+        c[0] = v.z; n[0] = g.nz; s[0] = g.slab;
+        c[1] = v.y; n[1] = g.ny; s[1] = g.P;
+        c[2] = v.x; n[2] = g.nx; s[2] = 1;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
+    const long long ci = cidx(g, v);
+    dI[o] = I0[ci];
+    dP[o] = p0[ci];
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, float* I1, float* p1) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
+    const long long ci = cidx(g, v);
+    if (I1) I1[ci] = sI[o];
+    if (p1) p1[ci] = sP[o];
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
+         unsigned int* __restrict__ maxdisp) {
+    const Vox v = vox_of<NDIM>(g);
+    float dmax = 0.f;
+    if (v.ok) {
+        const int b = v.b;
+        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+        const float dtrho = dt * rho;
+        const long long o = gidx(g, v.z, v.y, v.x);
+        int c[NDIM], n[NDIM];
+        long long s[NDIM];
+        axis_info<NDIM>(g, v, c, n, s);
+        float d[NDIM];
+        float du = 0.f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+            d[a] = disp_of(dtrho, ua[o]);
+            du += cdiff(ua, o, s[a], c[a], n[a]);
+            dmax = fmaxf(dmax, fabsf(d[a]));
+        }
+        const float div = -rho * du;  // div v, v = -rho u
+        const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+        const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+        const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+        const float Iw = interp<NDIM>(g, F, It);
+        const float pw = interp<NDIM>(g, F, pt);
+        float* I1 = slice_of(states, g, ((long long)(t + 1) * 2 + 0) * g.B + b);
+        float* p1 = slice_of(states, g, ((long long)(t + 1) * 2 + 1) * g.B + b);
+        p1[o] = pw * (1.f - dt * div);
+        I1[o] = Iw + (dt * mu) * pw;
+    }
+    // per-instance max |displacement| (non-negative floats order like their bits)
+    const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+    if ((threadIdx.x & 31) == 0 && m != 0u)
+        atomicMax(maxdisp + (long long)t * g.B + blockIdx.z, m);
+}
+
+// Cost partials: one CTA = 256 threads over a fixed voxel range of instance
+// blockIdx.y; also writes the adjoint start I^_T = I_T - J, p^_T = 0.
+template <int NDIM>
+__global__ void __launch_bounds__(256)
+k_cost_partials(Geom g, int T, const float* __restrict__ states, const float* __restrict__ u,
+                const float* __restrict__ J, float* Ih, float* ph, double* partials) {
+    const int b = blockIdx.y;
+    const long long N = (long long)g.nz * g.ny * g.nx;
+    const float* IT = slice_of(states, g, ((long long)T * 2 + 0) * g.B + b);
+    const float* I0 = slice_of(states, g, (0LL * 2 + 0) * g.B + b);
+    const float* p0 = slice_of(states, g, (0LL * 2 + 1) * g.B + b);
+    double data = 0.0, kin = 0.0, res = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        Vox v;
+        v.b = b;
+        v.x = (int)(i % g.nx);
+        v.y = (int)((i / g.nx) % g.ny);
+        v.z = (int)(i / ((long long)g.nx * g.ny));
+        const long long o = gidx(g, v.z, v.y, v.x);
+        const float r = IT[o] - J[(long long)b * N + i];
+        data += 0.5 * (double)r * (double)r;
+        int c[NDIM], n[NDIM];
+        long long s[NDIM];
+        axis_info<NDIM>(g, v, c, n, s);
+        const float p = p0[o];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float ga = cdiff(I0, o, s[a], c[a], n[a]);
+            const float* ua = slice_of(u, g, (0LL * NDIM + a) * g.B + b);
+            kin += (double)(p * ga) * (double)ua[o];
+        }
+        res += (double)p * (double)p;
+        float* Ihb = slice_of(Ih, g, b);
+        float* phb = slice_of(ph, g, b);
+        Ihb[o] = r;
+        phb[o] = 0.f;
+    }
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = data;
+    red[1][threadIdx.x] = kin;
+    red[2][threadIdx.x] = res;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3)
+        partials[((long long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256)
+k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
+    const int b = blockIdx.x;
+    __shared__ double red[3][256];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) acc[k] += partials[((long long)b * nblk + i) * 3 + k];
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double lam = (double)cf.lambda[b], rho = (double)cf.rho[b];
+        cost[b * 3 + 0] = red[0][0];
+        cost[b * 3 + 1] = lam * red[1][0];
+        cost[b * 3 + 2] = lam * rho * red[2][0];
+    }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_init(Geom g, const float* __restrict__ gI1, const float* __restrict__ gp1, float* Ih,
+           float* ph) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
+    const long long ci = cidx(g, v);
+    Ih[o] = gI1[ci];
+    ph[o] = gp1 ? gp1[ci] : 0.f;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_pre(Geom g, Coefs cf, int t, const float* __restrict__ states, const float* __restrict__ u,
+          const float* __restrict__ Ih1, const float* __restrict__ ph1, float* pth, float* dh) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const float dtrho = dt * rho;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    float d[NDIM];
+    float du = 0.f;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+        d[a] = disp_of(dtrho, ua[o]);
+        du += cdiff(ua, o, s[a], c[a], n[a]);
+    }
+    const float div = -rho * du;
+    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float pw = interp<NDIM>(g, F, pt);
+    const long long ob = (long long)b * g.inst + o;
+    const float phv = ph1[ob];
+    pth[ob] = phv * (1.f - dt * div) + (dt * mu) * Ih1[ob];
+    dh[ob] = -dt * pw * phv;
+}
+
+// Weight with which source foot F passes value to node coordinate nc (one axis).
+__device__ __forceinline__ float node_weight(const Foot1& f, int nc) {
+    if (nc == f.i0) return 1.f - f.f;
+    if (nc == f.i0 + 1) return f.f;
+    return 0.f;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gather(Geom g, Coefs cf, int t, const float* __restrict__ states,
+             const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+             const float* __restrict__ Ih1, const float* __restrict__ pth,
+             const float* __restrict__ dh, float* vh, float* Ihp, float* php) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float rho = cf.rho[b], dt = cf.dt;
+    const float dtrho = dt * rho;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ob = (long long)b * g.inst + o;
+    const float* Ihb = Ih1 + (long long)b * g.inst;
+    const float* pthb = pth + (long long)b * g.inst;
+    const float* dhb = dh + (long long)b * g.inst;
+    const float* ub[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) ub[a] = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+
+    // S^T by gather: every source x within R of this node whose foot cell has
+    // this node as a corner contributes weight * value.  Fixed loop order.
+    const float md = __uint_as_float(maxdisp[(long long)t * g.B + b]);
+    const int R = (int)ceilf(md) + 1;
+    float accI = 0.f, accP = 0.f;
+    int lo[NDIM], hi[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        lo[a] = max(c[a] - R, 0);
+        hi[a] = min(c[a] + R, n[a] - 1);
+    }
+    if constexpr (NDIM == 2) {
+        for (int sy = lo[0]; sy <= hi[0]; ++sy) {
+            for (int sx = lo[1]; sx <= hi[1]; ++sx) {
+                const long long so = gidx(g, 0, sy, sx);
+                const Foot1 fy = foot1(sy, disp_of(dtrho, ub[0][so]), g.ny);
+                if (!(c[0] == fy.i0 || c[0] == fy.i0 + 1)) continue;
+                const Foot1 fx = foot1(sx, disp_of(dtrho, ub[1][so]), g.nx);
+                if (!(c[1] == fx.i0 || c[1] == fx.i0 + 1)) continue;
+                const float w = node_weight(fy, c[0]) * node_weight(fx, c[1]);
+                accI += w * Ihb[so];
+                accP += w * pthb[so];
+            }
+        }
+    } else {
+        for (int sz = lo[0]; sz <= hi[0]; ++sz) {
+            for (int sy = lo[1]; sy <= hi[1]; ++sy) {
+                for (int sx = lo[2]; sx <= hi[2]; ++sx) {
+                    const long long so = gidx(g, sz, sy, sx);
+                    const Foot1 fz = foot1(sz, disp_of(dtrho, ub[0][so]), g.nz);
+                    if (!(c[0] == fz.i0 || c[0] == fz.i0 + 1)) continue;
+                    const Foot1 fy = foot1(sy, disp_of(dtrho, ub[1][so]), g.ny);
+                    if (!(c[1] == fy.i0 || c[1] == fy.i0 + 1)) continue;
+                    const Foot1 fx = foot1(sx, disp_of(dtrho, ub[2][so]), g.nx);
+                    if (!(c[2] == fx.i0 || c[2] == fx.i0 + 1)) continue;
+                    const float w =
+                        node_weight(fz, c[0]) * node_weight(fy, c[1]) * node_weight(fx, c[2]);
+                    accI += w * Ihb[so];
+                    accP += w * pthb[so];
+                }
+            }
+        }
+    }
+    Ihp[ob] = accI;
+    php[ob] = accP;
+
+    // Foot derivative of this node's own backtracking: y^_a.
+    float d[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) d[a] = disp_of(dtrho, ub[a][o]);
+    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    float Iv, pv, dI[NDIM], dP[NDIM];
+    interp_grad<NDIM>(g, F, It, &Iv, dI);
+    interp_grad<NDIM>(g, F, pt, &pv, dP);
+    const float Ihv = Ihb[o], pthv = pthb[o];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float yh = dI[a] * Ihv + dP[a] * pthv;
+        const float vha = -dt * yh + cdiff_T(dhb, o, s[a], c[a], n[a]);
+        vh[((long long)a * g.B + b) * g.inst + o] = vha;
+    }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+            const float* __restrict__ u, const float* __restrict__ mh,
+            const float* __restrict__ Ihp, const float* __restrict__ php, float* Ih, float* ph,
+            float* out0, float* gI0) {
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ob = (long long)b * g.inst + o;
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    float phv = php[ob];
+    float Ihv = Ihp[ob];
+    float kg = 0.f;  // sum_a g_a u_a (cost gradient at t = 0)
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ma = mh + ((long long)a * g.B + b) * g.inst;
+        const float ga = cdiff(It, o, s[a], c[a], n[a]);
+        phv += ma[o] * ga;
+        // D_a^T (m^_a p) at this node
+        float r = 0.f;
+        const long long sa = s[a];
+        if (c[a] >= 1) r += 0.5f * (ma[o - sa] * pt[o - sa]);
+        if (c[a] == n[a] - 1) r += 0.5f * (ma[o] * pt[o]);
+        if (c[a] <= n[a] - 2) r -= 0.5f * (ma[o + sa] * pt[o + sa]);
+        if (c[a] == 0) r -= 0.5f * (ma[o] * pt[o]);
+        Ihv += r;
+        if (mode == 1) kg += ga * slice_of(u, g, (0LL * NDIM + a) * g.B + b)[o];
+    }
+    if (mode == 0) {
+        Ih[ob] = Ihv;
+        ph[ob] = phv;
+    } else {
+        const long long ci = cidx(g, v);
+        if (mode == 1) {
+            const float lam = cf.lambda[b], rho = cf.rho[b];
+            out0[ci] = phv + lam * (2.f * kg + 2.f * rho * pt[o]);
+        } else {
+            out0[ci] = phv;
+            if (gI0) gI0[ci] = Ihv;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p0, float* dI,
+                        float* dP, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_pack<2><<<pgrid<2>(g), blk, 0, st>>>(g, I0, p0, dI, dP);
+    else
+        k_pack<3><<<pgrid<3>(g), blk, 0, st>>>(g, I0, p0, dI, dP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float* sP, float* I1,
+                          float* p1, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_unpack<2><<<pgrid<2>(g), blk, 0, st>>>(g, sI, sP, I1, p1);
+    else
+        k_unpack<3><<<pgrid<3>(g), blk, 0, st>>>(g, sI, sP, I1, p1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
+                          const float* u, unsigned int* maxdisp, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_advect<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp);
+    else
+        k_advect<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
+                        const float* u, const float* J, float* Ih, float* ph, double* partials,
+                        int nblk, double* cost, cudaStream_t st) {
+    const dim3 grid(nblk, g.B);
+    if (ndim == 2)
+        k_cost_partials<2><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, partials);
+    else
+        k_cost_partials<3><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cost_final<<<g.B, 256, 0, st>>>(nblk, c, partials, cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
+                            float* Ih, float* ph, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_adj_init<2><<<pgrid<2>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph);
+    else
+        k_adj_init<3><<<pgrid<3>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
+                           const float* u, const float* Ih1, const float* ph1, float* pth,
+                           float* dh, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_adj_pre<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, Ih1, ph1, pth, dh);
+    else
+        k_adj_pre<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, Ih1, ph1, pth, dh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
+                              const float* states, const float* u, const unsigned int* maxdisp,
+                              const float* Ih1, const float* pth, const float* dh, float* vh,
+                              float* Ihp, float* php, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_adj_gather<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth, dh,
+                                                     vh, Ihp, php);
+    else
+        k_adj_gather<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth, dh,
+                                                     vh, Ihp, php);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
+                             const float* states, const float* u, const float* mh,
+                             const float* Ihp, const float* php, float* Ih, float* ph,
+                             float* out0, float* gI0, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        k_adj_gradp<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, mode, states, u, mh, Ihp, php, Ih,
+                                                    ph, out0, gI0);
+    else
+        k_adj_gradp<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, mode, states, u, mh, Ihp, php, Ih,
+                                                    ph, out0, gI0);
+    return cudaGetLastError();
+}
+
+}  // namespace meta

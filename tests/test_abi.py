@@ -1,0 +1,89 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/meta.h declares, and rejects bad arguments with error codes before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def meta():
+    from paper_2106_08817_gb300 import _build
+    _build.build()
+    import paper_2106_08817_gb300 as m
+    return m
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "meta.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(meta_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("meta_shoot_forward", "meta_shoot_adjoint", "meta_cost_and_grad",
+                 "meta_workspace_size", "meta_status_string", "meta_workspace_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(meta):
+    lib = meta._load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(meta):
+    lib = meta._load()
+    for code in range(8):
+        assert lib.meta_status_string(code).decode()
+    assert lib.meta_status_string(99).decode() == "unknown status"
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(ndim=4), 1), (dict(ndim=1), 1), (dict(batch=0), 1), (dict(T=0), 1),
+    (dict(T=5000), 1), (dict(sigma=0.0), 1), (dict(sigma=-1.0), 1), (dict(sigma=19.0), 1),
+    (dict(sigma=float("nan")), 1), (dict(dims=(1, 5)), 2), (dict(dims=(5, 70000)), 2),
+])
+def test_invalid_problems_are_rejected(meta, kw, code):
+    prm = dict(ndim=2, dims=(16, 16), batch=1, T=4, sigma=2.0)
+    prm.update(kw)
+    pr = meta._problem(prm["ndim"], prm["dims"], prm["batch"], prm["T"], prm["sigma"])
+    n = ctypes.c_size_t(0)
+    assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == code
+
+
+def test_workspace_size_grows_with_T_and_batch(meta):
+    a = meta.workspace_size((64, 64), 1, 10, 3.0)
+    b = meta.workspace_size((64, 64), 2, 10, 3.0)
+    c = meta.workspace_size((64, 64), 1, 20, 3.0)
+    assert b > a and c > a
+    # the trajectory (2 (T+1) + d T fields) dominates: check the order of magnitude
+    fields = 2 * 11 + 2 * 10 + 3 * 2 + 8
+    assert fields * 64 * 64 * 4 <= a < (fields + 8) * 64 * 64 * 4
+
+
+def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
+    lib = meta._load()
+    pr = meta._problem(2, (16, 16), 1, 4, 2.0)
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    need = meta.workspace_size((16, 16), 1, 4, 2.0)
+    # null inputs
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), null, fake, fake, fake, fake, fake, fake,
+                                  fake, fake, need, null) == 1
+    assert lib.meta_shoot_forward(ctypes.byref(pr), fake, null, fake, fake, fake, fake, fake,
+                                  need, null) == 1
+    assert lib.meta_shoot_adjoint(ctypes.byref(pr), fake, fake, fake, fake, fake, null, fake,
+                                  need, null) == 1
+    # workspace: null, misaligned, too small
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, null, need, null) == 3
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, ctypes.c_void_p(0x1010), need, null) == 3
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, fake, need - 1, null) == 3

@@ -1,0 +1,206 @@
+"""Parity of the sm_103a library (through the C ABI) with the FP64 oracle.
+
+Tolerances: I_T and p_T max-abs <= 1e-4 (scaled by max(1, |p|) for p) for
+images in [0, 1]; dL/dp0 relative L2 <= 1e-3; the three cost terms relative
+1e-5 (FP64 accumulation of FP32 fields).  Inputs are the seeded phantoms of
+the workloads and random smooth fields on ragged shapes that span several
+tiles (x tiles are 128 wide, strided tiles 128 long, pointwise tiles 32 x 8).
+"""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+import phantoms
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FWD_ATOL = 1e-4
+GRAD_RTOL = 1e-3
+COST_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def meta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_08817_gb300 import _build
+    _build.build()
+    import paper_2106_08817_gb300 as m
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum()) / max(np.sqrt((b ** 2).sum()), 1e-300))
+
+
+def smooth_p(seed, shape, scale, s=2.0):
+    r = np.random.default_rng(seed)
+    out = np.empty(shape, np.float32)
+    for b in range(shape[0]):
+        out[b] = ndimage.gaussian_filter(r.normal(size=shape[1:]), s) * scale
+    return out
+
+
+def check_forward(meta, I0, p0, T, sigma, mu, rho):
+    I1, p1, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho)
+    I1, p1 = I1.cpu().numpy(), p1.cpu().numpy()
+    for b in range(I0.shape[0]):
+        mb = mu[b] if np.ndim(mu) else mu
+        rb = rho[b] if np.ndim(rho) else rho
+        It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb)
+        assert np.abs(I1[b] - It[-1]).max() <= FWD_ATOL, b
+        assert np.abs(p1[b] - pt[-1]).max() <= FWD_ATOL * max(1.0, np.abs(pt[-1]).max()), b
+    assert ws.status() == 0
+
+
+def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL):
+    cost, grad = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam)
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
+    worst = 0.0
+    for b in range(I0.shape[0]):
+        pick = lambda v: v[b] if np.ndim(v) else v
+        c, g = oracle.cost_and_grad(I0[b], J[b], p0[b], T, sigma, pick(mu), pick(rho), pick(lam))
+        np.testing.assert_allclose(cost[b], c, rtol=COST_RTOL, atol=1e-12)
+        e = rel_l2(grad[b], g)
+        worst = max(worst, e)
+        assert e <= grad_rtol, (b, e)
+    return worst
+
+
+# ----------------------------------------------------------------- forward
+
+def test_zero_momentum_leaves_image_unchanged_bitwise(meta):
+    w = phantoms.disk_pair_64(random_p0=False)
+    I1, p1, _ = meta.shoot_forward(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho)
+    np.testing.assert_array_equal(I1.cpu().numpy(), w.I0)
+    np.testing.assert_array_equal(p1.cpu().numpy(), 0.0)
+
+
+def test_forward_disk64(meta):
+    w = phantoms.disk_pair_64()
+    check_forward(meta, w.I0, w.p0, w.T, w.sigma, float(w.mu[0]), float(w.rho[0]))
+
+
+@pytest.mark.parametrize("dims,B,T,sigma", [((37, 141), 3, 4, 2.3), ((130, 259), 2, 3, 4.0),
+                                            ((5, 3), 2, 2, 0.7), ((64, 64), 1, 1, 18.0)])
+def test_forward_ragged_2d(meta, dims, B, T, sigma):
+    I0, _ = phantoms.random_fields(11, B, dims)
+    p0 = smooth_p(12, (B,) + dims, 40.0)
+    check_forward(meta, I0, p0, T, sigma, [0.0, 0.3, 0.1][:B], [1.0, 0.7, 1.5][:B])
+
+
+@pytest.mark.parametrize("dims,B,T,sigma", [((9, 13, 135), 2, 3, 1.5), ((21, 6, 10), 1, 4, 2.0)])
+def test_forward_ragged_3d(meta, dims, B, T, sigma):
+    I0, _ = phantoms.random_fields(13, B, dims)
+    p0 = smooth_p(14, (B,) + dims, 30.0, s=1.5)
+    check_forward(meta, I0, p0, T, sigma, [0.2, 0.0][:B], [1.0, 1.3][:B])
+
+
+# ----------------------------------------------------------------- cost + gradient
+
+def test_cost_and_grad_disk64(meta):
+    w = phantoms.disk_pair_64()
+    check_cost_grad(meta, w.I0, w.J, w.p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+
+
+def test_cost_and_grad_disk64_zero_momentum(meta):
+    w = phantoms.disk_pair_64(random_p0=False)
+    check_cost_grad(meta, w.I0, w.J, w.p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+
+
+@pytest.mark.parametrize("dims,B,T,sigma,scale", [((37, 141), 3, 4, 2.3, 40.0),
+                                                  ((70, 33), 2, 5, 3.0, 300.0)])
+def test_cost_and_grad_ragged_2d(meta, dims, B, T, sigma, scale):
+    I0, _ = phantoms.random_fields(21, B, dims)
+    J, _ = phantoms.random_fields(22, B, dims)
+    p0 = smooth_p(23, (B,) + dims, scale)
+    check_cost_grad(meta, I0, J, p0, T, sigma, np.array([0.0, 0.2, 0.05][:B]),
+                    np.array([1.0, 0.8, 1.2][:B]), np.array([1e-3, 1e-2, 0.1][:B]))
+
+
+@pytest.mark.parametrize("dims,B,T,sigma", [((9, 13, 135), 2, 3, 1.5), ((12, 10, 11), 1, 4, 1.0)])
+def test_cost_and_grad_ragged_3d(meta, dims, B, T, sigma):
+    I0, _ = phantoms.random_fields(31, B, dims)
+    J, _ = phantoms.random_fields(32, B, dims)
+    p0 = smooth_p(33, (B,) + dims, 30.0, s=1.5)
+    check_cost_grad(meta, I0, J, p0, T, sigma, np.array([0.1, 0.0][:B]),
+                    np.array([1.0, 1.1][:B]), np.array([1e-3, 1e-2][:B]))
+
+
+def test_large_displacements_widen_the_gather_window(meta):
+    """Per-step displacements of several voxels: the adjoint's gather window must grow."""
+    dims = (48, 52)
+    I0, _ = phantoms.random_fields(41, 1, dims)
+    J, _ = phantoms.random_fields(42, 1, dims)
+    p0 = smooth_p(43, (1,) + dims, 3000.0, s=3.0)
+    _, _, u = oracle.shoot(I0[0], p0[0], 3, 2.0, 0.1, 1.0, want_u=True)
+    assert np.abs(u).max() / 3 > 2.0
+    check_cost_grad(meta, I0, J, p0, 3, 2.0, 0.1, 1.0, 1e-3)
+
+
+def test_shoot_adjoint_and_autograd_function(meta):
+    dims = (40, 45)
+    B, T, sigma = 2, 4, 2.0
+    mu, rho = [0.2, 0.0], [1.0, 1.4]
+    I0, _ = phantoms.random_fields(51, B, dims)
+    p0 = smooth_p(52, (B,) + dims, 50.0)
+    r = np.random.default_rng(53)
+    gI1 = r.normal(size=(B,) + dims).astype(np.float32)
+    gp1 = r.normal(size=(B,) + dims).astype(np.float32)
+    tI, tp = cuda(I0).requires_grad_(True), cuda(p0).requires_grad_(True)
+    I1, p1 = meta.shoot(tI, tp, T, sigma, mu, rho)
+    (I1 * cuda(gI1)).sum().add_((p1 * cuda(gp1)).sum()).backward()
+    for b in range(B):
+        gI0, gp0 = oracle.adjoint(I0[b], p0[b], gI1[b], gp1[b], T, sigma, mu[b], rho[b])
+        assert rel_l2(tp.grad[b].cpu().numpy(), gp0) <= GRAD_RTOL
+        assert rel_l2(tI.grad[b].cpu().numpy(), gI0) <= GRAD_RTOL
+
+
+def test_results_are_deterministic(meta):
+    w = phantoms.disk_pair_64()
+    a = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
+    b = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+# ----------------------------------------------------------------- workload sizes
+
+def test_ellipse_batch_16x256_full_size(meta):
+    """The 16 x 256^2, T=20, sigma=6 batch (mu in {0, 0.05, 0.2}) at two momenta."""
+    w = phantoms.ellipse_pairs()
+    oracle.set_threads(oracle.max_threads())
+    check_cost_grad(meta, w.I0, w.J, w.p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+    p0 = smooth_p(61, w.p0.shape, 2.0, s=4.0)
+    check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+
+
+def test_head_128_full_size(meta):
+    """128^3, T=20, sigma=5 head phantom: cost and gradient at a smooth momentum."""
+    w = phantoms.head_pair_3d()
+    oracle.set_threads(oracle.max_threads())
+    p0 = smooth_p(62, w.p0.shape, 3.0, s=3.0)
+    check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+
+
+def test_mri_volume_downsampled_and_full_size_properties(meta):
+    """160x192x160 (sigma 6): parity on the 2x block-averaged copy (sigma 3) and,
+    at full size, the p0 = 0 invariance and the rho-rescaling identity."""
+    w = phantoms.mri_pair_3d()
+    I0s, Js = phantoms.block_average(w.I0), phantoms.block_average(w.J)
+    p0s = smooth_p(63, I0s.shape, 3.0, s=2.0)
+    oracle.set_threads(oracle.max_threads())
+    check_cost_grad(meta, I0s, Js, p0s, w.T, w.sigma / 2, w.mu, w.rho, w.lam)
+    # full size: p0 = 0 leaves the image unchanged bit for bit
+    I1, p1, _ = meta.shoot_forward(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho)
+    assert torch.equal(I1.cpu(), torch.from_numpy(w.I0)) and bool((p1 == 0).all())
+    # full size: (rho, mu, p0) and (1, mu/rho, rho p0) shoot to the same image
+    p0 = smooth_p(64, w.I0.shape, 3.0, s=3.0)
+    A = meta.shoot_forward(cuda(w.I0), cuda(p0), w.T, w.sigma, 0.1, 2.0)[0]
+    B = meta.shoot_forward(cuda(w.I0), cuda(2.0 * p0), w.T, w.sigma, 0.05, 1.0)[0]
+    assert float((A - B).abs().max()) <= FWD_ATOL
