@@ -104,8 +104,12 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
                                const float* lambda, double* cost, float* grad, void* ws,
                                size_t ws_bytes, void* stream);
 
-/* Device-side fault word latched in ws since it was last cleared (0 = none).
- * Synchronises `stream`.  clear != 0 resets it. */
+/* Device-side status word latched in ws since it was last cleared.  Bit 0: a
+ * bounded TMA wait ran out (the call's results are invalid; returns
+ * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step
+ * displacements beyond the deterministic gather window (8 voxels in 2-D, 3 in
+ * 3-D) and transposed the interpolation by an atomic scatter instead, so its
+ * summation order is not fixed.  Synchronises `stream`.  clear != 0 resets it. */
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
                                   unsigned int* fault_bits);
 

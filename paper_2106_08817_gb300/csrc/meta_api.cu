@@ -41,7 +41,9 @@ meta_status validate(const meta_problem* pr) {
         const long long gy1 = (long long)((pr->dims[1] + kTA - 1) / kTA) * pr->dims[0];
         const long long gy0 = (long long)((pr->dims[0] + kTA - 1) / kTA) * pr->dims[1];
         const long long gp = (long long)((pr->dims[1] + 7) / 8) * pr->dims[0];
-        if (gy > 65535 || gy1 > 65535 || gy0 > 65535 || gp > 65535) return META_ERR_SHAPE;
+        const long long gg = (long long)((pr->dims[1] + 7) / 8) * ((pr->dims[0] + 3) / 4);
+        if (gy > 65535 || gy1 > 65535 || gy0 > 65535 || gp > 65535 || gg > 65535)
+            return META_ERR_SHAPE;
     } else {
         if ((pr->dims[0] + 7) / 8 > 65535) return META_ERR_SHAPE;
     }
@@ -321,7 +323,8 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
     float* Pnext = c.PB;
     for (int t = L.T - 1; t >= 0; --t) {
         META_LAUNCH(META_K_ADJ_PRE, c.st,
-                    launch_adj_pre(g, d, cf, t, c.states, c.u, Icur, Pcur, c.PTH, c.DH, c.st));
+                    launch_adj_pre(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, Pcur, c.PTH, c.DH,
+                                   c.IHP, c.PHP, c.fault, c.st));
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
                     launch_adj_gather(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, c.PTH, c.DH,
                                       c.SV, c.IHP, c.PHP, c.st));
@@ -346,8 +349,8 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         }
         const int m = (t == 0) ? mode : 0;
         META_LAUNCH(META_K_ADJ_GRADP, c.st,
-                    launch_adj_gradp(g, d, cf, t, m, c.states, c.u, mh, c.IHP, c.PHP, Inext,
-                                     Pnext, out0, gI0, c.st));
+                    launch_adj_gradp(g, d, cf, t, m, c.states, c.u, c.maxdisp, mh, c.IHP, c.PHP,
+                                     Inext, Pnext, out0, gI0, c.st));
         float* tI = Icur;
         float* tP = Pcur;
         Icur = Inext;
@@ -403,7 +406,8 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
-    META_LAUNCH(META_K_ADJ_INIT, c.st, launch_adj_init(c.L.g, c.L.ndim, gI1, gp1, c.IA, c.PA, c.st));
+    META_LAUNCH(META_K_ADJ_INIT, c.st,
+                launch_adj_init(c.L.g, c.L.ndim, gI1, gp1, c.IA, c.PA, c.IHP, c.PHP, c.st));
     return run_adjoint(c, cf, 2, gp0, gI0);
 }
 
@@ -422,8 +426,8 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.IA, c.PA, c.partials,
-                            c.L.nblk, cost, c.st));
+                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.IA, c.PA, c.IHP, c.PHP,
+                            c.partials, c.L.nblk, cost, c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
 }
@@ -440,7 +444,7 @@ meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* st
         if (cudaMemsetAsync(f, 0, sizeof(unsigned int), st) != cudaSuccess) return META_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return META_ERR_CUDA;
     }
-    return *fault_bits ? META_ERR_TIMEOUT : META_OK;
+    return (*fault_bits & kFaultTmaTimeout) ? META_ERR_TIMEOUT : META_OK;
 }
 
 meta_status meta_timer_start(int cap) {

@@ -19,8 +19,9 @@ constexpr int kBA = 8;         // strided pass: outputs per thread along the axi
 constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 
-// Fault bits latched in the workspace header.
-constexpr unsigned kFaultTmaTimeout = 1u;
+// Fault / information bits latched in the workspace header.
+constexpr unsigned kFaultTmaTimeout = 1u;  // a bounded TMA wait ran out (fault)
+constexpr unsigned kInfoScatter = 2u;      // adjoint used the atomic scatter (large steps)
 
 // ---------------------------------------------------------------- geometry
 // An instance is an (nz,) ny x nx grid stored with row pitch P floats

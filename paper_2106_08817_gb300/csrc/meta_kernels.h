@@ -35,13 +35,16 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
                           const float* u, unsigned int* maxdisp, cudaStream_t st);
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                        const float* u, const float* J, float* Ih, float* ph, double* partials,
-                        int nblk, double* cost, cudaStream_t st);
+                        const float* u, const float* J, float* Ih, float* ph, float* Ihp,
+                        float* php, double* partials, int nblk, double* cost, cudaStream_t st);
 cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
-                            float* Ih, float* ph, cudaStream_t st);
+                            float* Ih, float* ph, float* Ihp, float* php, cudaStream_t st);
+// Pointwise part of adjoint step t; when the step's displacements exceed the
+// gather window it also scatters S^T into Ihp / php (atomics).
 cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
-                           const float* u, const float* Ih1, const float* ph1, float* pth,
-                           float* dh, cudaStream_t st);
+                           const float* u, const unsigned int* maxdisp, const float* Ih1,
+                           const float* ph1, float* pth, float* dh, float* Ihp, float* php,
+                           unsigned int* fault, cudaStream_t st);
 cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
                               const float* states, const float* u, const unsigned int* maxdisp,
                               const float* Ih1, const float* pth, const float* dh, float* vh,
@@ -49,8 +52,8 @@ cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
 // mode 0: write (Ih, ph) pitched; mode 1: cost gradient into grad (contiguous);
 // mode 2: shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
-                             const float* states, const float* u, const float* mh,
-                             const float* Ihp, const float* php, float* Ih, float* ph,
+                             const float* states, const float* u, const unsigned int* maxdisp,
+                             const float* mh, float* Ihp, float* php, float* Ih, float* ph,
                              float* grad_or_gp0, float* gI0, cudaStream_t st);
 
 }  // namespace meta

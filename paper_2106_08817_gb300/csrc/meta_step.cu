@@ -235,7 +235,8 @@ k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __res
 template <int NDIM>
 __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, int T, const float* __restrict__ states, const float* __restrict__ u,
-                const float* __restrict__ J, float* Ih, float* ph, double* partials) {
+                const float* __restrict__ J, float* Ih, float* ph, float* Ihp, float* php,
+                double* partials) {
     const int b = blockIdx.y;
     const long long N = (long long)g.nz * g.ny * g.nx;
     const float* IT = slice_of(states, g, ((long long)T * 2 + 0) * g.B + b);
@@ -263,10 +264,10 @@ k_cost_partials(Geom g, int T, const float* __restrict__ states, const float* __
             kin += (double)(p * ga) * (double)ua[o];
         }
         res += (double)p * (double)p;
-        float* Ihb = slice_of(Ih, g, b);
-        float* phb = slice_of(ph, g, b);
-        Ihb[o] = r;
-        phb[o] = 0.f;
+        slice_of(Ih, g, b)[o] = r;
+        slice_of(ph, g, b)[o] = 0.f;
+        slice_of(Ihp, g, b)[o] = 0.f;  // scatter accumulators start at zero
+        slice_of(php, g, b)[o] = 0.f;
     }
     __shared__ double red[3][256];
     red[0][threadIdx.x] = data;
@@ -307,19 +308,55 @@ k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* co
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, const float* __restrict__ gI1, const float* __restrict__ gp1, float* Ih,
-           float* ph) {
+           float* ph, float* Ihp, float* php) {
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
     Ih[o] = gI1[ci];
     ph[o] = gp1 ? gp1[ci] : 0.f;
+    Ihp[o] = 0.f;  // scatter accumulators start at zero
+    php[o] = 0.f;
+}
+
+// Window radius of the gather-form transpose at step t: a source x feeds node
+// n only if n lies in the cell of its foot, so |n - x| <= 1 + |d| per axis and
+// R = 1 + floor(max |d|) bounds every contributing source.
+__device__ __forceinline__ int gather_radius(const unsigned int* maxdisp, int t, int B, int b) {
+    return 1 + (int)floorf(__uint_as_float(maxdisp[(long long)t * B + b]));
+}
+
+template <int NDIM>
+struct GatherTile;  // node tile of the gather kernel (256 nodes per CTA)
+template <>
+struct GatherTile<2> {
+    static constexpr int TX = 32, TY = 8, TZ = 1, RMAX = 8;
+};
+template <>
+struct GatherTile<3> {
+    static constexpr int TX = 8, TY = 8, TZ = 4, RMAX = 3;
+};
+
+template <int NDIM>
+__host__ __device__ constexpr int gather_region() {
+    using G = GatherTile<NDIM>;
+    return (G::TX + 2 * G::RMAX) * (G::TY + 2 * G::RMAX) *
+           (NDIM == 3 ? (G::TZ + 2 * G::RMAX) : 1);
+}
+
+template <int NDIM>
+dim3 gather_grid(const Geom& g) {
+    using G = GatherTile<NDIM>;
+    return dim3((g.nx + G::TX - 1) / G::TX,
+                ((g.ny + G::TY - 1) / G::TY) * ((g.nz + G::TZ - 1) / G::TZ), g.B);
 }
 
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_pre(Geom g, Coefs cf, int t, const float* __restrict__ states, const float* __restrict__ u,
-          const float* __restrict__ Ih1, const float* __restrict__ ph1, float* pth, float* dh) {
+          const unsigned int* __restrict__ maxdisp, const float* __restrict__ Ih1,
+          const float* __restrict__ ph1, float* pth, float* dh, float* Ihp, float* php,
+          unsigned int* fault) {
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
@@ -343,15 +380,36 @@ k_adj_pre(Geom g, Coefs cf, int t, const float* __restrict__ states, const float
     const float pw = interp<NDIM>(g, F, pt);
     const long long ob = (long long)b * g.inst + o;
     const float phv = ph1[ob];
-    pth[ob] = phv * (1.f - dt * div) + (dt * mu) * Ih1[ob];
+    const float Ihv = Ih1[ob];
+    const float pthv = phv * (1.f - dt * div) + (dt * mu) * Ihv;
+    pth[ob] = pthv;
     dh[ob] = -dt * pw * phv;
+    if (gather_radius(maxdisp, t, g.B, b) > GatherTile<NDIM>::RMAX) {
+        // Displacements beyond the gather window: scatter S^T with atomics
+        // (work bounded by 2^d per source; summation order not fixed).
+        if (o == 0) atomicOr(fault, kInfoScatter);
+        float* Ib = Ihp + (long long)b * g.inst;
+        float* Pb = php + (long long)b * g.inst;
+#pragma unroll
+        for (int k = 0; k < (1 << NDIM); ++k) {
+            float w = 1.f;
+            long long q = F.base;
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) {
+                const int up = (k >> a) & 1;
+                w *= up ? F.f[a].f : 1.f - F.f[a].f;
+                q += up ? s[a] : 0;
+            }
+            atomicAdd(Ib + q, w * Ihv);
+            atomicAdd(Pb + q, w * pthv);
+        }
+    }
 }
 
-// Weight with which source foot F passes value to node coordinate nc (one axis).
-__device__ __forceinline__ float node_weight(const Foot1& f, int nc) {
-    if (nc == f.i0) return 1.f - f.f;
-    if (nc == f.i0 + 1) return f.f;
-    return 0.f;
+// Packs the foot cell of a source relative to the source (one byte per axis,
+// offset + 64) with bit 31 set for sources outside the domain.
+__device__ __forceinline__ int pack_cell(const int* off) {
+    return (off[0] + 64) | ((off[1] + 64) << 8) | ((off[2] + 64) << 16);
 }
 
 template <int NDIM>
@@ -360,69 +418,135 @@ k_adj_gather(Geom g, Coefs cf, int t, const float* __restrict__ states,
              const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
              const float* __restrict__ Ih1, const float* __restrict__ pth,
              const float* __restrict__ dh, float* vh, float* Ihp, float* php) {
-    const Vox v = vox_of<NDIM>(g);
-    if (!v.ok) return;
-    const int b = v.b;
+    using G = GatherTile<NDIM>;
+    constexpr int REG = gather_region<NDIM>();
+    __shared__ int s_cell[REG];
+    __shared__ float s_f[NDIM][REG];
+    __shared__ float s_I[REG];
+    __shared__ float s_P[REG];
+
+    const int b = blockIdx.z;
     const float rho = cf.rho[b], dt = cf.dt;
     const float dtrho = dt * rho;
-    const long long o = gidx(g, v.z, v.y, v.x);
-    const long long ob = (long long)b * g.inst + o;
-    const float* Ihb = Ih1 + (long long)b * g.inst;
-    const float* pthb = pth + (long long)b * g.inst;
-    const float* dhb = dh + (long long)b * g.inst;
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    const int ntx = (g.ny + G::TY - 1) / G::TY;
+    const int x0 = blockIdx.x * G::TX;
+    const int y0 = (blockIdx.y % ntx) * G::TY;
+    const int z0 = (blockIdx.y / ntx) * G::TZ;
+    // this thread's node
+    Vox v;
+    v.b = b;
+    if constexpr (NDIM == 2) {
+        v.x = x0 + threadIdx.x;
+        v.y = y0 + threadIdx.y;
+        v.z = 0;
+    } else {
+        v.x = x0 + (tid & 7);
+        v.y = y0 + ((tid >> 3) & 7);
+        v.z = z0 + (tid >> 6);
+    }
+    v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
     const float* ub[NDIM];
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) ub[a] = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
-    int c[NDIM], n[NDIM];
-    long long s[NDIM];
-    axis_info<NDIM>(g, v, c, n, s);
+    const float* Ihb = Ih1 + (long long)b * g.inst;
+    const float* pthb = pth + (long long)b * g.inst;
+    const float* dhb = dh + (long long)b * g.inst;
+    const int R = gather_radius(maxdisp, t, g.B, b);
+    const bool tiled = R <= G::RMAX;  // uniform over the CTA
 
-    // S^T by gather: every source x within R of this node whose foot cell has
-    // this node as a corner contributes weight * value.  Fixed loop order.
-    const float md = __uint_as_float(maxdisp[(long long)t * g.B + b]);
-    const int R = (int)ceilf(md) + 1;
     float accI = 0.f, accP = 0.f;
-    int lo[NDIM], hi[NDIM];
+    if (tiled) {
+        // Phase 1: foot records of every source of the tile grown by R.
+        const int RX = G::TX + 2 * R, RY = G::TY + 2 * R;
+        const int RZ = (NDIM == 3) ? G::TZ + 2 * R : 1;
+        const int nreg = RX * RY * RZ;
+        for (int i = tid; i < nreg; i += kPX * kPY) {
+            const int rx = i % RX;
+            const int ry = (i / RX) % RY;
+            const int rz = i / (RX * RY);
+            const int sx = x0 - R + rx, sy = y0 - R + ry;
+            const int sz = (NDIM == 3) ? z0 - R + rz : 0;
+            int cell = (int)0x80000000;
+            float fI = 0.f, fP = 0.f;
+            float ff[NDIM];
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        lo[a] = max(c[a] - R, 0);
-        hi[a] = min(c[a] + R, n[a] - 1);
-    }
-    if constexpr (NDIM == 2) {
-        for (int sy = lo[0]; sy <= hi[0]; ++sy) {
-            for (int sx = lo[1]; sx <= hi[1]; ++sx) {
-                const long long so = gidx(g, 0, sy, sx);
-                const Foot1 fy = foot1(sy, disp_of(dtrho, ub[0][so]), g.ny);
-                if (!(c[0] == fy.i0 || c[0] == fy.i0 + 1)) continue;
-                const Foot1 fx = foot1(sx, disp_of(dtrho, ub[1][so]), g.nx);
-                if (!(c[1] == fx.i0 || c[1] == fx.i0 + 1)) continue;
-                const float w = node_weight(fy, c[0]) * node_weight(fx, c[1]);
-                accI += w * Ihb[so];
-                accP += w * pthb[so];
-            }
-        }
-    } else {
-        for (int sz = lo[0]; sz <= hi[0]; ++sz) {
-            for (int sy = lo[1]; sy <= hi[1]; ++sy) {
-                for (int sx = lo[2]; sx <= hi[2]; ++sx) {
-                    const long long so = gidx(g, sz, sy, sx);
+            for (int a = 0; a < NDIM; ++a) ff[a] = 0.f;
+            if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
+                const long long so = gidx(g, sz, sy, sx);
+                int off[3] = {0, 0, 0};
+                if constexpr (NDIM == 2) {
+                    const Foot1 fy = foot1(sy, disp_of(dtrho, ub[0][so]), g.ny);
+                    const Foot1 fx = foot1(sx, disp_of(dtrho, ub[1][so]), g.nx);
+                    off[0] = fy.i0 - sy;
+                    off[1] = fx.i0 - sx;
+                    ff[0] = fy.f;
+                    ff[1] = fx.f;
+                } else {
                     const Foot1 fz = foot1(sz, disp_of(dtrho, ub[0][so]), g.nz);
-                    if (!(c[0] == fz.i0 || c[0] == fz.i0 + 1)) continue;
                     const Foot1 fy = foot1(sy, disp_of(dtrho, ub[1][so]), g.ny);
-                    if (!(c[1] == fy.i0 || c[1] == fy.i0 + 1)) continue;
                     const Foot1 fx = foot1(sx, disp_of(dtrho, ub[2][so]), g.nx);
-                    if (!(c[2] == fx.i0 || c[2] == fx.i0 + 1)) continue;
-                    const float w =
-                        node_weight(fz, c[0]) * node_weight(fy, c[1]) * node_weight(fx, c[2]);
-                    accI += w * Ihb[so];
-                    accP += w * pthb[so];
+                    off[0] = fz.i0 - sz;
+                    off[1] = fy.i0 - sy;
+                    off[2] = fx.i0 - sx;
+                    ff[0] = fz.f;
+                    ff[1] = fy.f;
+                    ff[2] = fx.f;
+                }
+                cell = pack_cell(off);
+                fI = Ihb[so];
+                fP = pthb[so];
+            }
+            s_cell[i] = cell;
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) s_f[a][i] = ff[a];
+            s_I[i] = fI;
+            s_P[i] = fP;
+        }
+        __syncthreads();
+        // Phase 2: S^T by gather over the window, fixed order, no atomics.
+        if (v.ok) {
+            const int lx = v.x - x0 + R, ly = v.y - y0 + R;
+            const int lz = (NDIM == 3) ? v.z - z0 + R : 0;
+            for (int dz = (NDIM == 3 ? -R : 0); dz <= (NDIM == 3 ? R : 0); ++dz) {
+                for (int dy = -R; dy <= R; ++dy) {
+                    const int rowbase = ((lz + dz) * RY + (ly + dy)) * RX + lx;
+                    for (int dx = -R; dx <= R; ++dx) {
+                        const int i = rowbase + dx;
+                        const int cell = s_cell[i];
+                        // node - source - offset must be 0 or 1 on every axis
+                        const int ex = -dx - (((cell >> ((NDIM - 1) * 8)) & 0xff) - 64);
+                        const int ey = -dy - (((cell >> ((NDIM - 2) * 8)) & 0xff) - 64);
+                        int ez = 0;
+                        if constexpr (NDIM == 3) ez = -dz - ((cell & 0xff) - 64);
+                        if (cell < 0 || (unsigned)ex > 1u || (unsigned)ey > 1u || (unsigned)ez > 1u)
+                            continue;
+                        float w;
+                        if constexpr (NDIM == 2) {
+                            const float fy = s_f[0][i], fx = s_f[1][i];
+                            w = (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
+                        } else {
+                            const float fz = s_f[0][i], fy = s_f[1][i], fx = s_f[2][i];
+                            w = (ez ? fz : 1.f - fz) * (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
+                        }
+                        accI += w * s_I[i];
+                        accP += w * s_P[i];
+                    }
                 }
             }
         }
     }
-    Ihp[ob] = accI;
-    php[ob] = accP;
+    if (!v.ok) return;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ob = (long long)b * g.inst + o;
+    if (tiled) {
+        Ihp[ob] = accI;
+        php[ob] = accP;
+    }  // else: k_adj_pre scattered S^T into Ihp / php already
 
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
     // Foot derivative of this node's own backtracking: y^_a.
     float d[NDIM];
 #pragma unroll
@@ -445,8 +569,8 @@ k_adj_gather(Geom g, Coefs cf, int t, const float* __restrict__ states,
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
-            const float* __restrict__ u, const float* __restrict__ mh,
-            const float* __restrict__ Ihp, const float* __restrict__ php, float* Ih, float* ph,
+            const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+            const float* __restrict__ mh, float* Ihp, float* php, float* Ih, float* ph,
             float* out0, float* gI0) {
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
@@ -460,6 +584,10 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
     const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
     float phv = php[ob];
     float Ihv = Ihp[ob];
+    if (t > 0 && gather_radius(maxdisp, t - 1, g.B, b) > GatherTile<NDIM>::RMAX) {
+        Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
+        php[ob] = 0.f;
+    }
     float kg = 0.f;  // sum_a g_a u_a (cost gradient at t = 0)
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
@@ -526,13 +654,13 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float*
 }
 
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                        const float* u, const float* J, float* Ih, float* ph, double* partials,
-                        int nblk, double* cost, cudaStream_t st) {
+                        const float* u, const float* J, float* Ih, float* ph, float* Ihp,
+                        float* php, double* partials, int nblk, double* cost, cudaStream_t st) {
     const dim3 grid(nblk, g.B);
     if (ndim == 2)
-        k_cost_partials<2><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, partials);
+        k_cost_partials<2><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, Ihp, php, partials);
     else
-        k_cost_partials<3><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, partials);
+        k_cost_partials<3><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, Ihp, php, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_cost_final<<<g.B, 256, 0, st>>>(nblk, c, partials, cost);
@@ -540,23 +668,26 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const fl
 }
 
 cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
-                            float* Ih, float* ph, cudaStream_t st) {
+                            float* Ih, float* ph, float* Ihp, float* php, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_init<2><<<pgrid<2>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph);
+        k_adj_init<2><<<pgrid<2>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph, Ihp, php);
     else
-        k_adj_init<3><<<pgrid<3>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph);
+        k_adj_init<3><<<pgrid<3>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph, Ihp, php);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
-                           const float* u, const float* Ih1, const float* ph1, float* pth,
-                           float* dh, cudaStream_t st) {
+                           const float* u, const unsigned int* maxdisp, const float* Ih1,
+                           const float* ph1, float* pth, float* dh, float* Ihp, float* php,
+                           unsigned int* fault, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_pre<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, Ih1, ph1, pth, dh);
+        k_adj_pre<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, ph1, pth, dh,
+                                                  Ihp, php, fault);
     else
-        k_adj_pre<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, Ih1, ph1, pth, dh);
+        k_adj_pre<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, ph1, pth, dh,
+                                                  Ihp, php, fault);
     return cudaGetLastError();
 }
 
@@ -566,25 +697,25 @@ cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
                               float* Ihp, float* php, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_gather<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth, dh,
-                                                     vh, Ihp, php);
+        k_adj_gather<2><<<gather_grid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth,
+                                                           dh, vh, Ihp, php);
     else
-        k_adj_gather<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth, dh,
-                                                     vh, Ihp, php);
+        k_adj_gather<3><<<gather_grid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth,
+                                                           dh, vh, Ihp, php);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
-                             const float* states, const float* u, const float* mh,
-                             const float* Ihp, const float* php, float* Ih, float* ph,
+                             const float* states, const float* u, const unsigned int* maxdisp,
+                             const float* mh, float* Ihp, float* php, float* Ih, float* ph,
                              float* out0, float* gI0, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_gradp<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, mode, states, u, mh, Ihp, php, Ih,
-                                                    ph, out0, gI0);
+        k_adj_gradp<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, mode, states, u, maxdisp, mh, Ihp,
+                                                    php, Ih, ph, out0, gI0);
     else
-        k_adj_gradp<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, mode, states, u, mh, Ihp, php, Ih,
-                                                    ph, out0, gI0);
+        k_adj_gradp<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, mode, states, u, maxdisp, mh, Ihp,
+                                                    php, Ih, ph, out0, gI0);
     return cudaGetLastError();
 }
 

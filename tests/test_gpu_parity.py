@@ -56,11 +56,16 @@ def check_forward(meta, I0, p0, T, sigma, mu, rho):
         It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb)
         assert np.abs(I1[b] - It[-1]).max() <= FWD_ATOL, b
         assert np.abs(p1[b] - pt[-1]).max() <= FWD_ATOL * max(1.0, np.abs(pt[-1]).max()), b
-    assert ws.status() == 0
+    assert ws.status(clear=True) & 1 == 0
 
 
 def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL):
-    cost, grad = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam)
+    B = I0.shape[0]
+    ws = meta.Workspace(I0.shape[1:], B, T, sigma)
+    cost, grad = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                                    workspace=ws)
+    check_cost_grad.status = ws.status()
+    assert check_cost_grad.status & 1 == 0
     cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
     worst = 0.0
     for b in range(I0.shape[0]):
@@ -115,7 +120,7 @@ def test_cost_and_grad_disk64_zero_momentum(meta):
 
 
 @pytest.mark.parametrize("dims,B,T,sigma,scale", [((37, 141), 3, 4, 2.3, 40.0),
-                                                  ((70, 33), 2, 5, 3.0, 300.0)])
+                                                  ((70, 33), 2, 5, 3.0, 100.0)])
 def test_cost_and_grad_ragged_2d(meta, dims, B, T, sigma, scale):
     I0, _ = phantoms.random_fields(21, B, dims)
     J, _ = phantoms.random_fields(22, B, dims)
@@ -133,15 +138,23 @@ def test_cost_and_grad_ragged_3d(meta, dims, B, T, sigma):
                     np.array([1.0, 1.1][:B]), np.array([1e-3, 1e-2][:B]))
 
 
-def test_large_displacements_widen_the_gather_window(meta):
-    """Per-step displacements of several voxels: the adjoint's gather window must grow."""
-    dims = (48, 52)
-    I0, _ = phantoms.random_fields(41, 1, dims)
-    J, _ = phantoms.random_fields(42, 1, dims)
-    p0 = smooth_p(43, (1,) + dims, 3000.0, s=3.0)
-    _, _, u = oracle.shoot(I0[0], p0[0], 3, 2.0, 0.1, 1.0, want_u=True)
-    assert np.abs(u).max() / 3 > 2.0
-    check_cost_grad(meta, I0, J, p0, 3, 2.0, 0.1, 1.0, 1e-3)
+@pytest.mark.parametrize("dims,seed,scale,T,sigma,mu,rho,lam", [
+    ((70, 33), 21, 200.0, 5, 3.0, 0.2, 0.8, 1e-2),     # per-step |d|: .2 1.6 4.3 8.1 17
+    ((14, 16, 18), 31, 300.0, 4, 1.5, 0.1, 1.0, 1e-3),  # per-step |d|: .3 1.8 4.8 17
+])
+def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam):
+    """Per-step displacements of 0.2 to 17 voxels: the gather window grows with
+    them (R = 1 + floor(max|d|)) and, beyond 8 voxels in 2-D or 3 in 3-D, the
+    adjoint switches to the atomic scatter.  These inputs stay well conditioned
+    in FP32 (an FP32 torch implementation of the same scheme is within 3e-5)."""
+    I0, _ = phantoms.random_fields(seed, 1, dims)
+    J, _ = phantoms.random_fields(seed + 1, 1, dims)
+    p0 = smooth_p(seed + 2, (1,) + dims, scale)
+    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True)
+    per_step = [np.abs(u[k]).max() * rho / T for k in range(T)]
+    assert max(per_step) > 9 and min(per_step) < 1
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam)
+    assert check_cost_grad.status & 2  # the scatter fallback ran
 
 
 def test_shoot_adjoint_and_autograd_function(meta):
