@@ -104,6 +104,32 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
                                const float* lambda, double* cost, float* grad, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* Size of the library's own device scratch used by meta_cost_and_grad_noalloc. */
+#define META_NOALLOC_MAX_BYTES (64u << 20)
+
+/* meta_cost_and_grad without a workspace argument.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * themselves.  Examples are code that runs while its stream is being captured
+ * into a CUDA graph, where an allocation is not a stream operation and may not
+ * be made; plug-ins whose host application owns every device allocation
+ * through its own pool; and real-time loops that must never enter the
+ * driver's allocator.  The caller passes inputs and outputs only (same
+ * meaning as meta_cost_and_grad).
+ *
+ * The scratch is one fixed array of META_NOALLOC_MAX_BYTES (64 MiB) that every
+ * GPU which loads this library holds until the process exits.  A problem whose
+ * meta_workspace_size exceeds it is rejected with META_ERR_WORKSPACE before any
+ * GPU work; the call itself allocates nothing.  The first call on a device
+ * looks up the array's device address (with that device current); make that
+ * first call before any stream capture.  Every call uses the same array, which
+ * keeps the previous call's contents (its status word is cleared at each call):
+ * calls that overlap on the GPU -- from two streams or two threads -- race and
+ * corrupt each other, so order them on one stream. */
+meta_status meta_cost_and_grad_noalloc(const meta_problem* prob, const float* I0, const float* J,
+                                       const float* p0, const float* mu, const float* rho,
+                                       const float* lambda, double* cost, float* grad,
+                                       void* stream);
+
 /* Device-side status word latched in ws since it was last cleared.  Bit 0: a
  * bounded TMA wait ran out (the call's results are invalid; returns
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step

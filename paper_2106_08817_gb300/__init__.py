@@ -67,6 +67,8 @@ def _load():
         lib.meta_shoot_forward.argtypes = [P, F, F, F, F, F, F, V, S, V]
         lib.meta_shoot_adjoint.argtypes = [P, F, F, F, F, F, F, V, S, V]
         lib.meta_cost_and_grad.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V]
+        lib.meta_cost_and_grad_noalloc.argtypes = [P, F, F, F, F, F, F, D, F, V]
+        lib.meta_cost_and_grad_noalloc.restype = ctypes.c_int
         lib.meta_workspace_status.argtypes = [V, S, ctypes.c_int, V,
                                               ctypes.POINTER(ctypes.c_uint)]
         lib.meta_status_string.argtypes = [ctypes.c_int]
@@ -253,6 +255,38 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     if rc:
         raise MetaError(rc, "meta_cost_and_grad")
     if sq and grad is not None and out is None:
+        grad = grad[0]
+    return cost, grad
+
+
+NOALLOC_MAX_BYTES = 64 << 20
+
+
+def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int,
+                          sigma: float, mu, rho=1.0, lam=1e-3, ndim: Optional[int] = None,
+                          out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None
+                          ) -> Tuple[torch.Tensor, torch.Tensor]:
+    """cost_and_grad on the library's fixed 64 MiB device scratch: no workspace
+    argument.  For callers that cannot allocate device memory; pass `out` (and
+    device tensors for mu, rho, lam) so that this call allocates nothing either.
+    Calls share the scratch: order them on one stream."""
+    I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
+    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    B, dev = I0b.shape[0], I0b.device
+    mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
+    if out is not None:
+        cost, grad = out
+    else:
+        cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
+        grad = torch.empty_like(I0b)
+    pr = _problem(nd, dims, B, T, sigma)
+    rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
+                                            _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
+                                            _p(grad), _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_cost_and_grad_noalloc")
+    if sq and out is None:
         grad = grad[0]
     return cost, grad
 

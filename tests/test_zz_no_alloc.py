@@ -1,0 +1,76 @@
+"""meta_cost_and_grad_noalloc: the entry point for callers that cannot allocate
+device memory (graph-capture regions, plug-ins whose host owns the device
+memory, real-time loops).  It runs on the library's fixed 64 MiB device array
+instead of a caller-provided workspace, so it must give what meta_cost_and_grad
+gives, call after call, although the array keeps the previous call's contents.
+
+Collected last on purpose (file name): a failure here leaves every other test
+already run.  Works alone in a fresh process and after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import phantoms
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 1e-3   # the gradient tolerance of the parity tests
+COST_RTOL = 1e-5   # the cost tolerance of the parity tests
+
+
+@pytest.fixture(scope="module")
+def meta():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_08817_gb300 import _build
+    _build.build()
+    import paper_2106_08817_gb300 as m
+    return m
+
+
+def _noalloc_via_c_abi(meta, I0, J, p0, T, sigma, mu, rho, lam):
+    """Call the C entry point directly (ctypes), outputs preallocated here."""
+    lib = meta._load()
+    B = I0.shape[0]
+    cost = torch.full((B, 3), float("nan"), dtype=torch.float64, device="cuda")
+    grad = torch.full_like(I0, float("nan"))
+    pr = meta._problem(I0.dim() - 1, tuple(I0.shape[1:]), B, T, sigma)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    rc = lib.meta_cost_and_grad_noalloc(ctypes.byref(pr), p(I0), p(J), p(p0), p(mu), p(rho),
+                                        p(lam), p(cost), p(grad),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, meta.STATUS.get(rc, rc)
+    return cost, grad
+
+
+def test_noalloc_matches_workspace_entry_point_on_two_calls_in_a_row(meta):
+    dims = (64, 64)
+    w = phantoms.disk_pair_64()
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    I0, J = t(w.I0), t(w.J)
+    mu, rho, lam = t(w.mu), t(w.rho), t(w.lam)
+    r = np.random.default_rng(77)
+    momenta = [t(w.p0), t(ndimage.gaussian_filter(r.normal(size=dims), 2.0)[None] * 20.0)]
+    for p0 in momenta:  # two calls in a row, different inputs
+        c_ref, g_ref = meta.cost_and_grad(I0, J, p0, w.T, w.sigma, mu, rho, lam)
+        c_na, g_na = _noalloc_via_c_abi(meta, I0, J, p0, w.T, w.sigma, mu, rho, lam)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(c_na.cpu().numpy(), c_ref.cpu().numpy(), rtol=COST_RTOL)
+        a, b = g_na.cpu().numpy(), g_ref.cpu().numpy()
+        assert np.isfinite(a).all()
+        assert np.linalg.norm(a - b) <= GRAD_RTOL * np.linalg.norm(b)
+
+
+def test_noalloc_rejects_problems_beyond_its_fixed_scratch(meta):
+    lib = meta._load()
+    big = meta._problem(2, (256, 256), 16, 20, 6.0)  # needs ~384 MiB of workspace
+    assert meta.workspace_size((256, 256), 16, 20, 6.0) > meta.NOALLOC_MAX_BYTES
+    fake = ctypes.c_void_p(0x1000)
+    rc = lib.meta_cost_and_grad_noalloc(ctypes.byref(big), fake, fake, fake, fake, fake, fake,
+                                        fake, fake, ctypes.c_void_p(0))
+    assert rc == 3  # META_ERR_WORKSPACE, before any GPU work
