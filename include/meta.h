@@ -74,7 +74,7 @@ typedef struct {
 /* Bytes of workspace that every call below needs for this problem.
  * The workspace holds the whole trajectory (I_t, p_t), t = 0..T, and the
  * smoothed momenta u_t = K(p_t grad I_t), t < T, so that the adjoint needs no
- * recomputation: about (2(T+1) + d T + 3d + 8) * batch * voxels * 4 bytes. */
+ * recomputation: about (2(T+1) + d T + 3d + 6) * batch * voxels * 4 bytes. */
 meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes);
 
 /* Forward shooting (Eq. 3, Sec. 2.3): (I0, p0) -> (I1, p1) = (I_T, p_T).
@@ -103,6 +103,23 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
                                const float* p0, const float* mu, const float* rho,
                                const float* lambda, double* cost, float* grad, void* ws,
                                size_t ws_bytes, void* stream);
+
+/* A recorded meta_cost_and_grad call.  meta_plan_create records the whole
+ * launch sequence of one call, for exactly these arguments, into a CUDA graph
+ * (on a private stream; nothing runs yet).  meta_plan_launch replays it on
+ * `stream` with a single graph launch: the caller updates the contents of I0,
+ * J, p0, mu, rho, lambda in place between launches (e.g. one gradient-descent
+ * step on p0) and reads cost and grad after the stream reaches them.  The plan
+ * keeps the pointers, not the data; the buffers and ws must outlive it, and
+ * launches that share ws must be ordered on one stream.  Same status codes as
+ * meta_cost_and_grad; creation may allocate driver resources for the graph. */
+typedef struct meta_plan meta_plan;
+meta_status meta_plan_create(const meta_problem* prob, const float* I0, const float* J,
+                             const float* p0, const float* mu, const float* rho,
+                             const float* lambda, double* cost, float* grad, void* ws,
+                             size_t ws_bytes, meta_plan** plan);
+meta_status meta_plan_launch(meta_plan* plan, void* stream);
+meta_status meta_plan_destroy(meta_plan* plan);
 
 /* Size of the library's own device scratch used by meta_cost_and_grad_noalloc. */
 #define META_NOALLOC_MAX_BYTES (64u << 20)

@@ -23,7 +23,7 @@ import torch
 
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_adjoint", "cost_and_grad",
            "Shoot", "shoot", "library_path", "STATUS", "timer_start", "timer_stop",
-           "KERNEL_CLASSES"]
+           "KERNEL_CLASSES", "CostAndGradPlan"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack")
@@ -67,6 +67,12 @@ def _load():
         lib.meta_shoot_forward.argtypes = [P, F, F, F, F, F, F, V, S, V]
         lib.meta_shoot_adjoint.argtypes = [P, F, F, F, F, F, F, V, S, V]
         lib.meta_cost_and_grad.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V]
+        lib.meta_plan_create.argtypes = [P, F, F, F, F, F, F, D, F, V, S,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        lib.meta_plan_launch.argtypes = [V, V]
+        lib.meta_plan_destroy.argtypes = [V]
+        for f in ("meta_plan_create", "meta_plan_launch", "meta_plan_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.meta_cost_and_grad_noalloc.argtypes = [P, F, F, F, F, F, F, D, F, V]
         lib.meta_cost_and_grad_noalloc.restype = ctypes.c_int
         lib.meta_workspace_status.argtypes = [V, S, ctypes.c_int, V,
@@ -257,6 +263,51 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     if sq and grad is not None and out is None:
         grad = grad[0]
     return cost, grad
+
+
+class CostAndGradPlan:
+    """A cost_and_grad call recorded once into a CUDA graph (meta_plan_*).
+
+    The plan owns fixed input/output tensors (I0, J, p0, mu, rho, lam, cost,
+    grad) and its workspace: update the inputs in place (e.g. ``plan.p0.sub_(...)``)
+    and call ``launch()``; results appear in ``plan.cost`` / ``plan.grad``.
+    """
+
+    def __init__(self, I0, J, p0, T: int, sigma: float, mu, rho=1.0, lam=1e-3,
+                 ndim: Optional[int] = None):
+        I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
+        B, dev = I0b.shape[0], I0b.device
+        self.I0 = I0b.clone()
+        self.J = _as_batch(J, "J")[0].reshape(I0b.shape).clone()
+        self.p0 = _as_batch(p0, "p0")[0].reshape(I0b.shape).clone()
+        self.mu, self.rho, self.lam = (_coef(mu, B, dev).clone(), _coef(rho, B, dev).clone(),
+                                       _coef(lam, B, dev).clone())
+        self.cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
+        self.grad = torch.empty_like(I0b)
+        self.ws = Workspace(dims, B, T, sigma, dev)
+        self.device = dev
+        pr = _problem(nd, dims, B, T, sigma)
+        h = ctypes.c_void_p(0)
+        torch.cuda.synchronize(dev)
+        rc = _load().meta_plan_create(ctypes.byref(pr), _p(self.I0), _p(self.J), _p(self.p0),
+                                      _p(self.mu), _p(self.rho), _p(self.lam), _p(self.cost),
+                                      _p(self.grad), ctypes.c_void_p(self.ws.ptr()),
+                                      self.ws.nbytes, ctypes.byref(h))
+        if rc:
+            raise MetaError(rc, "meta_plan_create")
+        self._h = h
+
+    def launch(self):
+        rc = _load().meta_plan_launch(self._h, _stream(self.device))
+        if rc:
+            raise MetaError(rc, "meta_plan_launch")
+        return self.cost, self.grad
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.meta_plan_destroy(h)
+            self._h = None
 
 
 NOALLOC_MAX_BYTES = 64 << 20

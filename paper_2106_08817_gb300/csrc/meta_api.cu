@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "meta.h"
@@ -23,7 +24,7 @@ struct Layout {
     int ndim, T, nblk;
     size_t off_fault, off_maxdisp, off_partials;
     size_t off_states, off_u, off_SA, off_SB, off_SV;
-    size_t off_IA, off_PA, off_IB, off_PB, off_PTH, off_DH, off_IHP, off_PHP;
+    size_t off_IA, off_PA, off_IB, off_PB, off_IHP, off_PHP;
     size_t total;
 };
 
@@ -79,7 +80,7 @@ Layout make_layout(const meta_problem* pr) {
         return o;
     };
     L.off_fault = take(16);
-    L.off_maxdisp = take(sizeof(unsigned int) * (size_t)pr->T * B);
+    L.off_maxdisp = take(sizeof(unsigned int) * kMaxdispStride * (size_t)pr->T * B);
     L.off_partials = take(sizeof(double) * 3 * B * (size_t)L.nblk);
     L.off_states = take(fslice * 2 * B * (size_t)(pr->T + 1));
     L.off_u = take(fslice * (size_t)d * B * (size_t)pr->T);
@@ -90,8 +91,6 @@ Layout make_layout(const meta_problem* pr) {
     L.off_PA = take(fslice * B);
     L.off_IB = take(fslice * B);
     L.off_PB = take(fslice * B);
-    L.off_PTH = take(fslice * B);
-    L.off_DH = take(fslice * B);
     L.off_IHP = take(fslice * B);
     L.off_PHP = take(fslice * B);
     L.total = off;
@@ -191,7 +190,7 @@ struct Ctx {
     unsigned int* fault;
     unsigned int* maxdisp;
     double* partials;
-    float *states, *u, *SA, *SB, *SV, *IA, *PA, *IB, *PB, *PTH, *DH, *IHP, *PHP;
+    float *states, *u, *SA, *SB, *SV, *IA, *PA, *IB, *PB, *IHP, *PHP;
 };
 
 meta_status map_status(cudaError_t e) { return e == cudaSuccess ? META_OK : META_ERR_CUDA; }
@@ -242,8 +241,6 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     c->PA = F(L.off_PA);
     c->IB = F(L.off_IB);
     c->PB = F(L.off_PB);
-    c->PTH = F(L.off_PTH);
-    c->DH = F(L.off_DH);
     c->IHP = F(L.off_IHP);
     c->PHP = F(L.off_PHP);
     make_taps(pr->sigma, &c->tx, &c->ts);
@@ -287,7 +284,8 @@ meta_status run_forward(Ctx& c, const Coefs& cf) {
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    META_TRY(cudaMemsetAsync(c.maxdisp, 0, sizeof(unsigned int) * (size_t)L.T * B, c.st));
+    META_TRY(cudaMemsetAsync(c.maxdisp, 0, sizeof(unsigned int) * kMaxdispStride * (size_t)L.T * B,
+                             c.st));
     for (int t = 0; t < L.T; ++t) {
         float* ut = c.u + (size_t)t * d * B * g.inst;
         // m = p grad I, blurred along x  ->  SA
@@ -322,12 +320,9 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
     float* Inext = c.IB;
     float* Pnext = c.PB;
     for (int t = L.T - 1; t >= 0; --t) {
-        META_LAUNCH(META_K_ADJ_PRE, c.st,
-                    launch_adj_pre(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, Pcur, c.PTH, c.DH,
-                                   c.IHP, c.PHP, c.fault, c.st));
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
-                    launch_adj_gather(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, c.PTH, c.DH,
-                                      c.SV, c.IHP, c.PHP, c.st));
+                    launch_adj_transport(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, Pcur, c.SV,
+                                         c.IHP, c.PHP, c.fault, c.st));
         // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
                     launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
@@ -430,6 +425,67 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
                             c.partials, c.L.nblk, cost, c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
+}
+
+struct meta_plan {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+meta_status meta_plan_create(const meta_problem* prob, const float* I0, const float* J,
+                             const float* p0, const float* mu, const float* rho,
+                             const float* lambda, double* cost, float* grad, void* ws,
+                             size_t ws_bytes, meta_plan** plan) {
+    if (!plan) return META_ERR_INVALID_ARG;
+    *plan = nullptr;
+    size_t need = 0;
+    meta_status s = meta_workspace_size(prob, &need);
+    if (s != META_OK) return s;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return META_ERR_CUDA;
+    const bool timer_was_on = g_timer.on;
+    g_timer.on = false;  // the recorded sequence carries no timing events
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        g_timer.on = timer_was_on;
+        cudaStreamDestroy(cs);
+        return META_ERR_CUDA;
+    }
+    s = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes, cs);
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    g_timer.on = timer_was_on;
+    cudaStreamDestroy(cs);
+    if (s != META_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s != META_OK ? s : META_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return META_ERR_CUDA;
+    }
+    meta_plan* p = new (std::nothrow) meta_plan{graph, exec};
+    if (!p) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return META_ERR_INVALID_ARG;
+    }
+    *plan = p;
+    return META_OK;
+}
+
+meta_status meta_plan_launch(meta_plan* plan, void* stream) {
+    if (!plan) return META_ERR_INVALID_ARG;
+    return map_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+}
+
+meta_status meta_plan_destroy(meta_plan* plan) {
+    if (!plan) return META_OK;
+    cudaGraphExecDestroy(plan->exec);
+    cudaGraphDestroy(plan->graph);
+    delete plan;
+    return META_OK;
 }
 
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,

@@ -19,6 +19,11 @@ constexpr int kBA = 8;         // strided pass: outputs per thread along the axi
 constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 
+// The max displacement of step t, instance b lives at maxdisp[kMaxdispStride *
+// (t * B + b)]: one 128-byte line per slot, so that the per-CTA atomics of
+// different instances do not queue on one L2 line.
+constexpr int kMaxdispStride = 32;
+
 // Fault / information bits latched in the workspace header.
 constexpr unsigned kFaultTmaTimeout = 1u;  // a bounded TMA wait ran out (fault)
 constexpr unsigned kInfoScatter = 2u;      // adjoint used the atomic scatter (large steps)

@@ -39,16 +39,14 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const fl
                         float* php, double* partials, int nblk, double* cost, cudaStream_t st);
 cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
                             float* Ih, float* ph, float* Ihp, float* php, cudaStream_t st);
-// Pointwise part of adjoint step t; when the step's displacements exceed the
-// gather window it also scatters S^T into Ihp / php (atomics).
-cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
-                           const float* u, const unsigned int* maxdisp, const float* Ih1,
-                           const float* ph1, float* pth, float* dh, float* Ihp, float* php,
-                           unsigned int* fault, cudaStream_t st);
-cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
-                              const float* states, const float* u, const unsigned int* maxdisp,
-                              const float* Ih1, const float* pth, const float* dh, float* vh,
-                              float* Ihp, float* php, cudaStream_t st);
+// Adjoint step t except the blur and the D^T(m^ p) part: S^T of I^' and of
+// p~^ (gather into Ihp / php, or atomic scatter for steps whose displacements
+// exceed the gather window, added to the zeroed Ihp / php), and v^ into vh.
+cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
+                                 const float* states, const float* u,
+                                 const unsigned int* maxdisp, const float* Ih1, const float* ph1,
+                                 float* vh, float* Ihp, float* php, unsigned int* fault,
+                                 cudaStream_t st);
 // mode 0: write (Ih, ph) pitched; mode 1: cost gradient into grad (contiguous);
 // mode 2: shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,

@@ -6,10 +6,11 @@
 //                 I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~,
 //                 and the per-instance max displacement (window of the adjoint).
 // Adjoint step t (reverse), the transpose of the step above:
-//   k_adj_pre     per source x: p~^ = p^'(1 - dt div v) + dt mu I^', div^ = -dt p~ p^'
-//   k_adj_gather  per node n: S^T by gather over the sources whose foot cell
-//                 touches n (fixed order, no atomics), the foot derivative y^,
-//                 and v^ = -dt y^ + D^T div^
+//   k_adj_transport  per source x of a tile and its halo:
+//                 p~^ = p^'(1 - dt div v) + dt mu I^', div^ = -dt p~ p^' and the
+//                 foot record (shared memory); per node n: S^T by gather over the
+//                 sources whose foot cell touches n (fixed order, no atomics), the
+//                 foot derivative y^, and v^ = -dt y^ + D^T div^
 //   (blur of v^ with K = K^T, scaled by -rho, in meta_blur.cu)
 //   k_adj_gradp   p^ += sum_i m^_i D_i I,  I^ += sum_i D_i^T (m^_i p)
 // Cost (Eq. 4): k_cost_partials + k_cost_final, FP64 partials in a fixed tree.
@@ -66,14 +67,47 @@ __device__ __forceinline__ float cdiff(const float* f, long long o, long long s,
     return 0.5f * (f[o + hi] - f[o - lo]);
 }
 
-// (D^T w)[c] along a stride s: rows c-1 and c+1 of D, plus the edge rows.
-__device__ __forceinline__ float cdiff_T(const float* w, long long o, long long s, int c, int n) {
-    float r = 0.f;
-    if (c >= 1) r += 0.5f * w[o - s];
-    if (c == n - 1) r += 0.5f * w[o];
-    if (c <= n - 2) r -= 0.5f * w[o + s];
-    if (c == 0) r -= 0.5f * w[o];
-    return r;
+// Stages rows [ylo, ylo + ROWS) x columns [xlo, xlo + W) of one pitched slice
+// into shared memory (row stride W) with asynchronous 16-byte copies; parts
+// outside the slice are zero-filled.  xlo and W are multiples of 4, so every
+// 16-byte chunk lies inside one padded row.  All copies of a CTA are in flight
+// together; call cp_async_wait_all() and __syncthreads() before reading.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(valid ? 16u : 0u)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int W, int ROWS>
+__device__ __forceinline__ void stage_async(float* dst, const float* __restrict__ src,
+                                            const Geom& g, int xlo, int ylo) {
+    constexpr int NC4 = W / 4;
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    for (int i = tid; i < ROWS * NC4; i += kPX * kPY) {
+        const int r = i / NC4, c = i - r * NC4;
+        const int y = ylo + r, x = xlo + 4 * c;
+        const bool ok = (y >= 0 && y < g.ny && x >= 0 && x < g.P);
+        cp_async16(dst + r * W + 4 * c, ok ? src + y * g.P + x : src, ok);
+    }
+}
+
+// Bilinear value (and derivatives) at lower corner p[0] with row stride W;
+// the same expressions as interp / interp_grad below.
+__device__ __forceinline__ float bilin(const float* p, int W, float fy, float fx) {
+    const float a = (1.f - fx) * p[0] + fx * p[1];
+    const float b = (1.f - fx) * p[W] + fx * p[W + 1];
+    return (1.f - fy) * a + fy * b;
+}
+__device__ __forceinline__ void bilin_grad(const float* p, int W, float fy, float fx, bool iny,
+                                           bool inx, float* dy, float* dx) {
+    const float c00 = p[0], c01 = p[1], c10 = p[W], c11 = p[W + 1];
+    const float a = (1.f - fx) * c00 + fx * c01;
+    const float b = (1.f - fx) * c10 + fx * c11;
+    *dy = iny ? (b - a) : 0.f;
+    *dx = inx ? ((1.f - fy) * (c01 - c00) + fy * (c11 - c10)) : 0.f;
 }
 
 template <int NDIM>
@@ -190,6 +224,70 @@ k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, flo
     if (p1) p1[ci] = sP[o];
 }
 
+// 2-D advect on a 32 x 8 tile: u staged with a one-voxel halo, I_t and p_t
+// with a four-voxel halo (feet whose cell leaves it read global memory).
+constexpr int kAdvHalo = 4;
+
+__global__ void __launch_bounds__(kPX * kPY)
+k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
+           unsigned int* __restrict__ maxdisp) {
+    constexpr int W = kPX + 2 * kAdvHalo;        // 40
+    constexpr int HU = kPY + 2;                  // 10
+    constexpr int HI = kPY + 2 * kAdvHalo;       // 16
+    __shared__ __align__(16) float sU0[HU * W], sU1[HU * W], sI[HI * W], sP[HI * W];
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+    const float* u0 = slice_of(u, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* u1 = slice_of(u, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    stage_async<W, HU>(sU0, u0, g, x0 - kAdvHalo, y0 - 1);
+    stage_async<W, HU>(sU1, u1, g, x0 - kAdvHalo, y0 - 1);
+    stage_async<W, HI>(sI, It, g, x0 - kAdvHalo, y0 - kAdvHalo);
+    stage_async<W, HI>(sP, pt, g, x0 - kAdvHalo, y0 - kAdvHalo);
+    cp_async_wait_all();
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    float dmax = 0.f;
+    if (x < g.nx && y < g.ny) {
+        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+        const float dtrho = dt * rho;
+        const int ui = (threadIdx.y + 1) * W + threadIdx.x + kAdvHalo;
+        const float d0 = disp_of(dtrho, sU0[ui]);
+        const float d1 = disp_of(dtrho, sU1[ui]);
+        float du = 0.f;
+        du += 0.5f * (sU0[ui + (y < g.ny - 1 ? W : 0)] - sU0[ui - (y > 0 ? W : 0)]);
+        du += 0.5f * (sU1[ui + (x < g.nx - 1 ? 1 : 0)] - sU1[ui - (x > 0 ? 1 : 0)]);
+        dmax = fmaxf(fabsf(d0), fabsf(d1));
+        const float div = -rho * du;
+        const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
+        const int ly = fy.i0 - (y0 - kAdvHalo), lx = fx.i0 - (x0 - kAdvHalo);
+        float Iw, pw;
+        if (ly >= 0 && ly + 1 < HI && lx >= 0 && lx + 1 < W) {
+            Iw = bilin(sI + ly * W + lx, W, fy.f, fx.f);
+            pw = bilin(sP + ly * W + lx, W, fy.f, fx.f);
+        } else {
+            const int o = fy.i0 * g.P + fx.i0;
+            Iw = bilin(It + o, g.P, fy.f, fx.f);
+            pw = bilin(pt + o, g.P, fy.f, fx.f);
+        }
+        const int o = y * g.P + x;
+        float* I1 = slice_of(states, g, ((long long)(t + 1) * 2 + 0) * g.B + b);
+        float* p1 = slice_of(states, g, ((long long)(t + 1) * 2 + 1) * g.B + b);
+        p1[o] = pw * (1.f - dt * div);
+        I1[o] = Iw + (dt * mu) * pw;
+    }
+    // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
+    __shared__ unsigned int s_m;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_m = 0u;
+    __syncthreads();
+    const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && s_m != 0u)
+        atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
+}
+
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
@@ -224,10 +322,16 @@ k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __res
         p1[o] = pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
-    // per-instance max |displacement| (non-negative floats order like their bits)
+    // per-instance max |displacement| (non-negative floats order like their bits),
+    // one atomic per CTA
+    __shared__ unsigned int s_m;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_m = 0u;
+    __syncthreads();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
-    if ((threadIdx.x & 31) == 0 && m != 0u)
-        atomicMax(maxdisp + (long long)t * g.B + blockIdx.z, m);
+    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && s_m != 0u)
+        atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + blockIdx.z), s_m);
 }
 
 // Cost partials: one CTA = 256 threads over a fixed voxel range of instance
@@ -323,7 +427,7 @@ k_adj_init(Geom g, const float* __restrict__ gI1, const float* __restrict__ gp1,
 // n only if n lies in the cell of its foot, so |n - x| <= 1 + |d| per axis and
 // R = 1 + floor(max |d|) bounds every contributing source.
 __device__ __forceinline__ int gather_radius(const unsigned int* maxdisp, int t, int B, int b) {
-    return 1 + (int)floorf(__uint_as_float(maxdisp[(long long)t * B + b]));
+    return 1 + (int)floorf(__uint_as_float(maxdisp[kMaxdispStride * ((long long)t * B + b)]));
 }
 
 template <int NDIM>
@@ -334,7 +438,7 @@ struct GatherTile<2> {
 };
 template <>
 struct GatherTile<3> {
-    static constexpr int TX = 8, TY = 8, TZ = 4, RMAX = 3;
+    static constexpr int TX = 8, TY = 8, TZ = 4, RMAX = 2;
 };
 
 template <int NDIM>
@@ -351,89 +455,243 @@ dim3 gather_grid(const Geom& g) {
                 ((g.ny + G::TY - 1) / G::TY) * ((g.nz + G::TZ - 1) / G::TZ), g.B);
 }
 
+// Packs the foot cell of a source relative to the source: one byte per axis
+// (offset + 64), bit 24 + a when the clamp on axis a is inactive, bit 31 for
+// sources outside the domain.
+__device__ __forceinline__ int pack_cell(const int* off, const bool* inside) {
+    return (off[0] + 64) | ((off[1] + 64) << 8) | ((off[2] + 64) << 16) |
+           (inside[0] ? (1 << 24) : 0) | (inside[1] ? (1 << 25) : 0) |
+           (inside[2] ? (1 << 26) : 0);
+}
+__device__ __forceinline__ int cell_off(int cell, int a) { return ((cell >> (8 * a)) & 0xff) - 64; }
+
+// S^T at one node by gather over the staged foot records of its window
+// (2R+1)^d, in a fixed order: node - source - cell offset must be 0 or 1 on
+// every axis.  Records are indexed ((z * RY) + y) * RX + x in the staged region.
 template <int NDIM>
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_pre(Geom g, Coefs cf, int t, const float* __restrict__ states, const float* __restrict__ u,
-          const unsigned int* __restrict__ maxdisp, const float* __restrict__ Ih1,
-          const float* __restrict__ ph1, float* pth, float* dh, float* Ihp, float* php,
-          unsigned int* fault) {
-    const Vox v = vox_of<NDIM>(g);
-    if (!v.ok) return;
-    const int b = v.b;
-    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-    const float dtrho = dt * rho;
-    const long long o = gidx(g, v.z, v.y, v.x);
-    int c[NDIM], n[NDIM];
-    long long s[NDIM];
-    axis_info<NDIM>(g, v, c, n, s);
-    float d[NDIM];
-    float du = 0.f;
-#pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
-        d[a] = disp_of(dtrho, ua[o]);
-        du += cdiff(ua, o, s[a], c[a], n[a]);
-    }
-    const float div = -rho * du;
-    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
-    const float pw = interp<NDIM>(g, F, pt);
-    const long long ob = (long long)b * g.inst + o;
-    const float phv = ph1[ob];
-    const float Ihv = Ih1[ob];
-    const float pthv = phv * (1.f - dt * div) + (dt * mu) * Ihv;
-    pth[ob] = pthv;
-    dh[ob] = -dt * pw * phv;
-    if (gather_radius(maxdisp, t, g.B, b) > GatherTile<NDIM>::RMAX) {
-        // Displacements beyond the gather window: scatter S^T with atomics
-        // (work bounded by 2^d per source; summation order not fixed).
-        if (o == 0) atomicOr(fault, kInfoScatter);
-        float* Ib = Ihp + (long long)b * g.inst;
-        float* Pb = php + (long long)b * g.inst;
-#pragma unroll
-        for (int k = 0; k < (1 << NDIM); ++k) {
-            float w = 1.f;
-            long long q = F.base;
-#pragma unroll
-            for (int a = 0; a < NDIM; ++a) {
-                const int up = (k >> a) & 1;
-                w *= up ? F.f[a].f : 1.f - F.f[a].f;
-                q += up ? s[a] : 0;
+__device__ __forceinline__ void gather_window(const int* s_cell, const float* const* s_f,
+                                              const float* s_I, const float* s_P, int RX, int RY,
+                                              int lx, int ly, int lz, int R, float* accI,
+                                              float* accP) {
+    float aI = 0.f, aP = 0.f;
+    for (int dz = (NDIM == 3 ? -R : 0); dz <= (NDIM == 3 ? R : 0); ++dz) {
+        for (int dy = -R; dy <= R; ++dy) {
+            const int rowbase = ((lz + dz) * RY + (ly + dy)) * RX + lx;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int i = rowbase + dx;
+                const int cell = s_cell[i];
+                const int ex = -dx - cell_off(cell, NDIM - 1);
+                const int ey = -dy - cell_off(cell, NDIM - 2);
+                const int ez = (NDIM == 3) ? -dz - cell_off(cell, 0) : 0;
+                if (cell < 0 || (unsigned)ex > 1u || (unsigned)ey > 1u || (unsigned)ez > 1u)
+                    continue;
+                float w;
+                if constexpr (NDIM == 2) {
+                    const float fy = s_f[0][i], fx = s_f[1][i];
+                    w = (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
+                } else {
+                    const float fz = s_f[0][i], fy = s_f[1][i], fx = s_f[2][i];
+                    w = (ez ? fz : 1.f - fz) * (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
+                }
+                aI += w * s_I[i];
+                aP += w * s_P[i];
             }
-            atomicAdd(Ib + q, w * Ihv);
-            atomicAdd(Pb + q, w * pthv);
         }
     }
-}
-
-// Packs the foot cell of a source relative to the source (one byte per axis,
-// offset + 64) with bit 31 set for sources outside the domain.
-__device__ __forceinline__ int pack_cell(const int* off) {
-    return (off[0] + 64) | ((off[1] + 64) << 8) | ((off[2] + 64) << 16);
+    *accI = aI;
+    *accP = aP;
 }
 
 template <int NDIM>
+__host__ __device__ constexpr int transport_smem_words() {
+    // general path: cell, f[NDIM], I, P, D records over the RMAX region;
+    // 2-D fast path: records over tile (+) 2 and six staged windows.
+    return NDIM == 2 ? ((1 + 2 + 3) * gather_region<2>() > 6400 ? (1 + 2 + 3) * gather_region<2>()
+                                                                 : 6400)
+                     : (1 + 3 + 3) * gather_region<3>();
+}
+
+constexpr int kFastH2 = 2;  // 2-D fast path: per-step displacement < 2 voxels
+
+// 2-D adjoint step for instances whose per-step displacement is below
+// H <= kFastH2 voxels: u, I_t, p_t, I^' and p^' are staged asynchronously over
+// the tile grown by the halos the step needs (u: H+1, I_t/p_t: 2H+1, I^'/p^': H),
+// and every stencil, interpolation and gather then reads shared memory.
+template <int H>
+__device__ __forceinline__ void transport_fast2d(const Geom& g, float rho, float mu, float dt,
+                                                 const float* It, const float* pt,
+                                                 const float* u0, const float* u1,
+                                                 const float* Ihb, const float* phb, float* vh0,
+                                                 float* vh1, float* Ihpb, float* phpb,
+                                                 float* smem, unsigned int* s_dmax) {
+    using G = GatherTile<2>;
+    constexpr int WU = G::TX + 8, WI = G::TX + 16, WA = G::TX + 8;
+    constexpr int HU = G::TY + 2 * H + 2, HI = G::TY + 4 * H + 2, HA = G::TY + 2 * H;
+    constexpr int RX = G::TX + 2 * H, RY = G::TY + 2 * H, NR = RX * RY;
+    const float dtrho = dt * rho;
+    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+    int* s_cell = reinterpret_cast<int*>(smem);
+    float* s_f0 = smem + NR;
+    float* s_f1 = s_f0 + NR;
+    float* s_I = s_f1 + NR;
+    float* s_P = s_I + NR;
+    float* s_D = s_P + NR;
+    float* sU0 = s_D + NR;   // 16-byte aligned: NR * 6 words is a multiple of 4
+    float* sU1 = sU0 + WU * HU;
+    float* sI = sU1 + WU * HU;
+    float* sP = sI + WI * HI;
+    float* sIh = sP + WI * HI;
+    float* sPh = sIh + WA * HA;
+    const int xu = x0 - 4, yu = y0 - H - 1;
+    const int xi = x0 - 8, yi = y0 - 2 * H - 1;
+    const int xa = x0 - 4, ya = y0 - H;
+    stage_async<WU, HU>(sU0, u0, g, xu, yu);
+    stage_async<WU, HU>(sU1, u1, g, xu, yu);
+    stage_async<WI, HI>(sI, It, g, xi, yi);
+    stage_async<WI, HI>(sP, pt, g, xi, yi);
+    stage_async<WA, HA>(sIh, Ihb, g, xa, ya);
+    stage_async<WA, HA>(sPh, phb, g, xa, ya);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // Phase 1: records of the sources of tile (+) H.
+    float dmax = 0.f;
+    for (int i = tid; i < NR; i += kPX * kPY) {
+        const int ry = i / RX, rx = i - ry * RX;
+        const int sx = x0 - H + rx, sy = y0 - H + ry;
+        int cell = (int)0x80000000;
+        float f0 = 0.f, f1 = 0.f, fI = 0.f, fP = 0.f, fD = 0.f;
+        if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
+            const int ui = (sy - yu) * WU + (sx - xu);
+            const float d0 = disp_of(dtrho, sU0[ui]);
+            const float d1 = disp_of(dtrho, sU1[ui]);
+            dmax = fmaxf(dmax, fmaxf(fabsf(d0), fabsf(d1)));
+            float du = 0.f;
+            du += 0.5f * (sU0[ui + (sy < g.ny - 1 ? WU : 0)] - sU0[ui - (sy > 0 ? WU : 0)]);
+            du += 0.5f * (sU1[ui + (sx < g.nx - 1 ? 1 : 0)] - sU1[ui - (sx > 0 ? 1 : 0)]);
+            const float div = -rho * du;
+            const Foot1 fy = foot1(sy, d0, g.ny), fx = foot1(sx, d1, g.nx);
+            const float pw = bilin(sP + (fy.i0 - yi) * WI + (fx.i0 - xi), WI, fy.f, fx.f);
+            const int ai = (sy - ya) * WA + (sx - xa);
+            const float phv = sPh[ai];
+            fI = sIh[ai];
+            fP = phv * (1.f - dt * div) + (dt * mu) * fI;
+            fD = -dt * pw * phv;
+            const int off[3] = {fy.i0 - sy, fx.i0 - sx, 0};
+            const bool ins[3] = {fy.inside, fx.inside, false};
+            cell = pack_cell(off, ins);
+            f0 = fy.f;
+            f1 = fx.f;
+        }
+        s_cell[i] = cell;
+        s_f0[i] = f0;
+        s_f1[i] = f1;
+        s_I[i] = fI;
+        s_P[i] = fP;
+        s_D[i] = fD;
+    }
+    const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+    if ((tx & 31) == 0 && wmax) atomicMax(s_dmax, wmax);
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) return;
+    const int me = (ty + H) * RX + tx + H;
+    const int R = 1 + (int)floorf(__uint_as_float(*s_dmax));
+    const float* fptr[2] = {s_f0, s_f1};
+    float accI, accP;
+    gather_window<2>(s_cell, fptr, s_I, s_P, RX, RY, tx + H, ty + H, 0, R, &accI, &accP);
+    const int o = y * g.P + x;
+    Ihpb[o] = accI;
+    phpb[o] = accP;
+
+    // y^ from this node's own foot, v^ = -dt y^ + D^T div^.
+    const int cell = s_cell[me];
+    const int iy = y + cell_off(cell, 0), ix = x + cell_off(cell, 1);
+    const float fy = s_f0[me], fx = s_f1[me];
+    const bool iny = (cell >> 24) & 1, inx = (cell >> 25) & 1;
+    const int ci = (iy - yi) * WI + (ix - xi);
+    float dIy, dIx, dPy, dPx;
+    bilin_grad(sI + ci, WI, fy, fx, iny, inx, &dIy, &dIx);
+    bilin_grad(sP + ci, WI, fy, fx, iny, inx, &dPy, &dPx);
+    const float Ihv = s_I[me], pthv = s_P[me];
+    float dT0 = 0.f, dT1 = 0.f;
+    if (y >= 1) dT0 += 0.5f * s_D[me - RX];
+    if (y == g.ny - 1) dT0 += 0.5f * s_D[me];
+    if (y <= g.ny - 2) dT0 -= 0.5f * s_D[me + RX];
+    if (y == 0) dT0 -= 0.5f * s_D[me];
+    if (x >= 1) dT1 += 0.5f * s_D[me - 1];
+    if (x == g.nx - 1) dT1 += 0.5f * s_D[me];
+    if (x <= g.nx - 2) dT1 -= 0.5f * s_D[me + 1];
+    if (x == 0) dT1 -= 0.5f * s_D[me];
+    vh0[o] = -dt * (dIy * Ihv + dPy * pthv) + dT0;
+    vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
+}
+
+// One adjoint step t, fused: for every source of the node tile grown by a halo
+// H it forms p~^ = p^'(1 - dt div v) + dt mu I^' and div^ = -dt p~ p^' and the
+// foot record, then for every node of the tile
+//   I^ (partial) = S^T I^',  p^ (partial) = S^T p~^      (gather, fixed order)
+//   v^_a = -dt y^_a + D_a^T div^,  y^_a = d(interp I_t)/dy_a I^' + d(interp p_t)/dy_a p~^.
+// Gather mode (R <= RMAX): H = R and the window of each node is the tile's own
+// R_tile = 1 + floor(max |d| over the staged sources) <= R.  Scatter mode
+// (R > RMAX): H = 1 and each CTA scatters S^T of its own sources into Ihp / php
+// with atomics (bounded work; k_adj_gradp reads them after the launch).
+// 2-D instances with R <= kFastH2 take transport_fast2d.
+template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_gather(Geom g, Coefs cf, int t, const float* __restrict__ states,
-             const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
-             const float* __restrict__ Ih1, const float* __restrict__ pth,
-             const float* __restrict__ dh, float* vh, float* Ihp, float* php) {
+k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
+                const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+                const float* __restrict__ Ih1, const float* __restrict__ ph1, float* vh,
+                float* Ihp, float* php, unsigned int* fault) {
     using G = GatherTile<NDIM>;
     constexpr int REG = gather_region<NDIM>();
-    __shared__ int s_cell[REG];
-    __shared__ float s_f[NDIM][REG];
-    __shared__ float s_I[REG];
-    __shared__ float s_P[REG];
+    __shared__ __align__(16) float smem[transport_smem_words<NDIM>()];
+    __shared__ unsigned int s_dmax;
 
     const int b = blockIdx.z;
-    const float rho = cf.rho[b], dt = cf.dt;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
     const float dtrho = dt * rho;
     const int tid = threadIdx.y * kPX + threadIdx.x;
-    const int ntx = (g.ny + G::TY - 1) / G::TY;
+    const float* ub[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) ub[a] = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* Ihb = Ih1 + (long long)b * g.inst;
+    const float* phb = ph1 + (long long)b * g.inst;
+    float* Isc = Ihp + (long long)b * g.inst;
+    float* Psc = php + (long long)b * g.inst;
+    const int Rinst = gather_radius(maxdisp, t, g.B, b);
+    if (tid == 0) s_dmax = 0u;
+    if constexpr (NDIM == 2) {
+        if (Rinst <= kFastH2) {
+            __syncthreads();
+            float* vh0 = vh + (long long)b * g.inst;
+            float* vh1 = vh + ((long long)g.B + b) * g.inst;
+            if (Rinst == 1)
+                transport_fast2d<1>(g, rho, mu, dt, It, pt, ub[0], ub[1], Ihb, phb, vh0, vh1, Isc,
+                                    Psc, smem, &s_dmax);
+            else
+                transport_fast2d<2>(g, rho, mu, dt, It, pt, ub[0], ub[1], Ihb, phb, vh0, vh1, Isc,
+                                    Psc, smem, &s_dmax);
+            return;
+        }
+    }
+    int* s_cell = reinterpret_cast<int*>(smem);
+    const float* s_fc[NDIM];
+    float* s_f[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) s_fc[a] = s_f[a] = smem + (1 + a) * REG;
+    float* s_I = smem + (1 + NDIM) * REG;   // I^' of the source
+    float* s_P = s_I + REG;                 // p~^ of the source
+    float* s_D = s_P + REG;                 // div^ of the source
+
+    const int nty = (g.ny + G::TY - 1) / G::TY;
     const int x0 = blockIdx.x * G::TX;
-    const int y0 = (blockIdx.y % ntx) * G::TY;
-    const int z0 = (blockIdx.y / ntx) * G::TZ;
-    // this thread's node
+    const int y0 = (blockIdx.y % nty) * G::TY;
+    const int z0 = (blockIdx.y / nty) * G::TZ;
     Vox v;
     v.b = b;
     if constexpr (NDIM == 2) {
@@ -446,123 +704,140 @@ k_adj_gather(Geom g, Coefs cf, int t, const float* __restrict__ states,
         v.z = z0 + (tid >> 6);
     }
     v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
-    const float* ub[NDIM];
-#pragma unroll
-    for (int a = 0; a < NDIM; ++a) ub[a] = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
-    const float* Ihb = Ih1 + (long long)b * g.inst;
-    const float* pthb = pth + (long long)b * g.inst;
-    const float* dhb = dh + (long long)b * g.inst;
-    const int R = gather_radius(maxdisp, t, g.B, b);
-    const bool tiled = R <= G::RMAX;  // uniform over the CTA
+    const bool gather = Rinst <= G::RMAX;  // uniform over the CTA
+    const int H = gather ? Rinst : 1;
+    const int RX = G::TX + 2 * H, RY = G::TY + 2 * H;
+    const int RZ = (NDIM == 3) ? G::TZ + 2 * H : 1;
+    const int nreg = RX * RY * RZ;
+    __syncthreads();
 
-    float accI = 0.f, accP = 0.f;
-    if (tiled) {
-        // Phase 1: foot records of every source of the tile grown by R.
-        const int RX = G::TX + 2 * R, RY = G::TY + 2 * R;
-        const int RZ = (NDIM == 3) ? G::TZ + 2 * R : 1;
-        const int nreg = RX * RY * RZ;
-        for (int i = tid; i < nreg; i += kPX * kPY) {
-            const int rx = i % RX;
-            const int ry = (i / RX) % RY;
-            const int rz = i / (RX * RY);
-            const int sx = x0 - R + rx, sy = y0 - R + ry;
-            const int sz = (NDIM == 3) ? z0 - R + rz : 0;
-            int cell = (int)0x80000000;
-            float fI = 0.f, fP = 0.f;
-            float ff[NDIM];
+    // Phase 1: per staged source.
+    float dmax = 0.f;
+    bool scattered = false;
+    for (int i = tid; i < nreg; i += kPX * kPY) {
+        const int rx = i % RX;
+        const int ry = (i / RX) % RY;
+        const int rz = i / (RX * RY);
+        Vox sv;
+        sv.b = b;
+        sv.x = x0 - H + rx;
+        sv.y = y0 - H + ry;
+        sv.z = (NDIM == 3) ? z0 - H + rz : 0;
+        int cell = (int)0x80000000;
+        float ff[NDIM], fI = 0.f, fP = 0.f, fD = 0.f;
 #pragma unroll
-            for (int a = 0; a < NDIM; ++a) ff[a] = 0.f;
-            if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
-                const long long so = gidx(g, sz, sy, sx);
-                int off[3] = {0, 0, 0};
-                if constexpr (NDIM == 2) {
-                    const Foot1 fy = foot1(sy, disp_of(dtrho, ub[0][so]), g.ny);
-                    const Foot1 fx = foot1(sx, disp_of(dtrho, ub[1][so]), g.nx);
-                    off[0] = fy.i0 - sy;
-                    off[1] = fx.i0 - sx;
-                    ff[0] = fy.f;
-                    ff[1] = fx.f;
-                } else {
-                    const Foot1 fz = foot1(sz, disp_of(dtrho, ub[0][so]), g.nz);
-                    const Foot1 fy = foot1(sy, disp_of(dtrho, ub[1][so]), g.ny);
-                    const Foot1 fx = foot1(sx, disp_of(dtrho, ub[2][so]), g.nx);
-                    off[0] = fz.i0 - sz;
-                    off[1] = fy.i0 - sy;
-                    off[2] = fx.i0 - sx;
-                    ff[0] = fz.f;
-                    ff[1] = fy.f;
-                    ff[2] = fx.f;
-                }
-                cell = pack_cell(off);
-                fI = Ihb[so];
-                fP = pthb[so];
+        for (int a = 0; a < NDIM; ++a) ff[a] = 0.f;
+        if (sv.x >= 0 && sv.x < g.nx && sv.y >= 0 && sv.y < g.ny && sv.z >= 0 && sv.z < g.nz) {
+            const long long so = gidx(g, sv.z, sv.y, sv.x);
+            int c[NDIM], n[NDIM];
+            long long st[NDIM];
+            axis_info<NDIM>(g, sv, c, n, st);
+            float d[NDIM];
+            float du = 0.f;
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) {
+                d[a] = disp_of(dtrho, ub[a][so]);
+                du += cdiff(ub[a], so, st[a], c[a], n[a]);
+                dmax = fmaxf(dmax, fabsf(d[a]));
             }
-            s_cell[i] = cell;
+            const float div = -rho * du;
+            const Feet<NDIM> F = feet_of<NDIM>(g, sv, d);
+            const float pw = interp<NDIM>(g, F, pt);
+            const float phv = phb[so];
+            fI = Ihb[so];
+            fP = phv * (1.f - dt * div) + (dt * mu) * fI;
+            fD = -dt * pw * phv;
+            int off[3] = {0, 0, 0};
+            bool ins[3] = {false, false, false};
 #pragma unroll
-            for (int a = 0; a < NDIM; ++a) s_f[a][i] = ff[a];
-            s_I[i] = fI;
-            s_P[i] = fP;
-        }
-        __syncthreads();
-        // Phase 2: S^T by gather over the window, fixed order, no atomics.
-        if (v.ok) {
-            const int lx = v.x - x0 + R, ly = v.y - y0 + R;
-            const int lz = (NDIM == 3) ? v.z - z0 + R : 0;
-            for (int dz = (NDIM == 3 ? -R : 0); dz <= (NDIM == 3 ? R : 0); ++dz) {
-                for (int dy = -R; dy <= R; ++dy) {
-                    const int rowbase = ((lz + dz) * RY + (ly + dy)) * RX + lx;
-                    for (int dx = -R; dx <= R; ++dx) {
-                        const int i = rowbase + dx;
-                        const int cell = s_cell[i];
-                        // node - source - offset must be 0 or 1 on every axis
-                        const int ex = -dx - (((cell >> ((NDIM - 1) * 8)) & 0xff) - 64);
-                        const int ey = -dy - (((cell >> ((NDIM - 2) * 8)) & 0xff) - 64);
-                        int ez = 0;
-                        if constexpr (NDIM == 3) ez = -dz - ((cell & 0xff) - 64);
-                        if (cell < 0 || (unsigned)ex > 1u || (unsigned)ey > 1u || (unsigned)ez > 1u)
-                            continue;
-                        float w;
-                        if constexpr (NDIM == 2) {
-                            const float fy = s_f[0][i], fx = s_f[1][i];
-                            w = (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
-                        } else {
-                            const float fz = s_f[0][i], fy = s_f[1][i], fx = s_f[2][i];
-                            w = (ez ? fz : 1.f - fz) * (ey ? fy : 1.f - fy) * (ex ? fx : 1.f - fx);
-                        }
-                        accI += w * s_I[i];
-                        accP += w * s_P[i];
+            for (int a = 0; a < NDIM; ++a) {
+                off[a] = F.f[a].i0 - c[a];
+                ins[a] = F.f[a].inside;
+                ff[a] = F.f[a].f;
+            }
+            cell = pack_cell(off, ins);
+            const bool own = sv.x >= x0 && sv.x < x0 + G::TX && sv.y >= y0 && sv.y < y0 + G::TY &&
+                             (NDIM == 2 || (sv.z >= z0 && sv.z < z0 + G::TZ));
+            if (!gather && own) {
+                // S^T by scatter: 2^d corners per source, order not fixed.
+                scattered = true;
+#pragma unroll
+                for (int k = 0; k < (1 << NDIM); ++k) {
+                    float w = 1.f;
+                    long long q = F.base;
+#pragma unroll
+                    for (int a = 0; a < NDIM; ++a) {
+                        const int up = (k >> a) & 1;
+                        w *= up ? F.f[a].f : 1.f - F.f[a].f;
+                        q += up ? st[a] : 0;
                     }
+                    atomicAdd(Isc + q, w * fI);
+                    atomicAdd(Psc + q, w * fP);
                 }
             }
         }
+        s_cell[i] = cell;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) s_f[a][i] = ff[a];
+        s_I[i] = fI;
+        s_P[i] = fP;
+        s_D[i] = fD;
     }
+    if (scattered) atomicOr(fault, kInfoScatter);
+    const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+    if ((tid & 31) == 0 && wmax) atomicMax(&s_dmax, wmax);
+    __syncthreads();
+
     if (!v.ok) return;
+    const int lx = v.x - x0 + H, ly = v.y - y0 + H;
+    const int lz = (NDIM == 3) ? v.z - z0 + H : 0;
+    const int me = (lz * RY + ly) * RX + lx;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ob = (long long)b * g.inst + o;
-    if (tiled) {
+
+    // Phase 2a: S^T by gather over the tile's window (fixed order, no atomics).
+    if (gather) {
+        const int R = 1 + (int)floorf(__uint_as_float(s_dmax));  // <= Rinst
+        float accI, accP;
+        gather_window<NDIM>(s_cell, s_fc, s_I, s_P, RX, RY, lx, ly, lz, R, &accI, &accP);
         Ihp[ob] = accI;
         php[ob] = accP;
-    }  // else: k_adj_pre scattered S^T into Ihp / php already
+    }
 
+    // Phase 2b: foot derivative of this node's own backtracking, and v^.
     int c[NDIM], n[NDIM];
-    long long s[NDIM];
-    axis_info<NDIM>(g, v, c, n, s);
-    // Foot derivative of this node's own backtracking: y^_a.
-    float d[NDIM];
+    long long st[NDIM];
+    axis_info<NDIM>(g, v, c, n, st);
+    const int cell = s_cell[me];
+    Feet<NDIM> F;
+    int i0[NDIM];
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) d[a] = disp_of(dtrho, ub[a][o]);
-    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    for (int a = 0; a < NDIM; ++a) {
+        i0[a] = c[a] + cell_off(cell, a);
+        F.f[a].i0 = i0[a];
+        F.f[a].f = s_f[a][me];
+        F.f[a].inside = (cell >> (24 + a)) & 1;
+    }
+    if constexpr (NDIM == 2)
+        F.base = gidx(g, 0, i0[0], i0[1]);
+    else
+        F.base = gidx(g, i0[0], i0[1], i0[2]);
     float Iv, pv, dI[NDIM], dP[NDIM];
     interp_grad<NDIM>(g, F, It, &Iv, dI);
     interp_grad<NDIM>(g, F, pt, &pv, dP);
-    const float Ihv = Ihb[o], pthv = pthb[o];
+    const float Ihv = s_I[me], pthv = s_P[me];
+    const int rstride[3] = {RX * RY, RX, 1};
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
+        const int rs = (NDIM == 2) ? rstride[a + 1] : rstride[a];
+        // (D_a^T div^) at this node from the staged neighbours
+        float dT = 0.f;
+        if (c[a] >= 1) dT += 0.5f * s_D[me - rs];
+        if (c[a] == n[a] - 1) dT += 0.5f * s_D[me];
+        if (c[a] <= n[a] - 2) dT -= 0.5f * s_D[me + rs];
+        if (c[a] == 0) dT -= 0.5f * s_D[me];
         const float yh = dI[a] * Ihv + dP[a] * pthv;
-        const float vha = -dt * yh + cdiff_T(dhb, o, s[a], c[a], n[a]);
-        vh[((long long)a * g.B + b) * g.inst + o] = vha;
+        vh[((long long)a * g.B + b) * g.inst + o] = -dt * yh + dT;
     }
 }
 
@@ -647,7 +922,8 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float*
                           const float* u, unsigned int* maxdisp, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_advect<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp);
+        k_advect2d<<<dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st>>>(
+            g, c, t, states, u, maxdisp);
     else
         k_advect<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp);
     return cudaGetLastError();
@@ -677,31 +953,18 @@ cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_pre(const Geom& g, int ndim, const Coefs& c, int t, const float* states,
-                           const float* u, const unsigned int* maxdisp, const float* Ih1,
-                           const float* ph1, float* pth, float* dh, float* Ihp, float* php,
-                           unsigned int* fault, cudaStream_t st) {
+cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
+                                 const float* states, const float* u,
+                                 const unsigned int* maxdisp, const float* Ih1, const float* ph1,
+                                 float* vh, float* Ihp, float* php, unsigned int* fault,
+                                 cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_pre<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, ph1, pth, dh,
-                                                  Ihp, php, fault);
+        k_adj_transport<2><<<gather_grid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1,
+                                                              ph1, vh, Ihp, php, fault);
     else
-        k_adj_pre<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, ph1, pth, dh,
-                                                  Ihp, php, fault);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adj_gather(const Geom& g, int ndim, const Coefs& c, int t,
-                              const float* states, const float* u, const unsigned int* maxdisp,
-                              const float* Ih1, const float* pth, const float* dh, float* vh,
-                              float* Ihp, float* php, cudaStream_t st) {
-    const dim3 blk(kPX, kPY);
-    if (ndim == 2)
-        k_adj_gather<2><<<gather_grid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth,
-                                                           dh, vh, Ihp, php);
-    else
-        k_adj_gather<3><<<gather_grid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1, pth,
-                                                           dh, vh, Ihp, php);
+        k_adj_transport<3><<<gather_grid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1,
+                                                              ph1, vh, Ihp, php, fault);
     return cudaGetLastError();
 }
 

@@ -175,6 +175,21 @@ def test_shoot_adjoint_and_autograd_function(meta):
         assert rel_l2(tI.grad[b].cpu().numpy(), gI0) <= GRAD_RTOL
 
 
+def test_plan_replays_the_recorded_call(meta):
+    """meta_plan: a recorded cost_and_grad gives bit-identical results to the eager
+    call, and picks up in-place updates of its inputs on every launch."""
+    w = phantoms.disk_pair_64()
+    plan = meta.CostAndGradPlan(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho,
+                                w.lam)
+    for k in range(3):
+        c1, g1 = plan.launch()
+        c2, g2 = meta.cost_and_grad(plan.I0, plan.J, plan.p0, w.T, w.sigma, w.mu, w.rho, w.lam)
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2) and torch.equal(g1, g2)
+        plan.p0.sub_(0.5 * g1 / g1.abs().max())  # a gradient-descent step in place
+    assert plan.ws.status() == 0
+
+
 def test_results_are_deterministic(meta):
     w = phantoms.disk_pair_64()
     a = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
