@@ -23,6 +23,8 @@ __global__ void __launch_bounds__(256)
 k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
         const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0,
         float* __restrict__ out, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
@@ -150,6 +152,8 @@ __global__ void __launch_bounds__(512)
 k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g,
           int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul,
           float* __restrict__ out, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* s = reinterpret_cast<float*>(smem_raw + 128);
@@ -263,8 +267,8 @@ static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP
     dim3 grid((g.nx + kTX - 1) / kTX,
               NDIM == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
               GRADP ? g.B : nslices);
-    k_xpass<NDIM, GRADP><<<grid, 256, smem, st>>>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
-                                                  out, fault);
+    META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP>, grid, 256, smem, st, tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                                  out, fault));
     return cudaGetLastError();
 }
 
@@ -299,8 +303,8 @@ static cudaError_t launch_strided_t(const CUtensorMap& tm, const Taps& taps, con
     else
         gy = ((g.nz + kTA - 1) / kTA) * g.ny;
     dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
-    k_strided<NDIM, AXIS><<<grid, 512, smem, st>>>(tm, taps, g, in_slice0, out_slice0, scale,
-                                                   scale_mul, out, fault);
+    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS>, grid, 512, smem, st, tm, taps, g, in_slice0, out_slice0, scale,
+                                                   scale_mul, out, fault));
     return cudaGetLastError();
 }
 

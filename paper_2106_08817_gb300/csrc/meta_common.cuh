@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 namespace meta {
 
@@ -175,8 +176,50 @@ __device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, 
         tma_load_4d(dst, map, bar, x, y, z, slice);
 }
 
+// Programmatic dependent launch: a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor in the
+// stream finishes.  pdl_wait() blocks until the predecessor has completed and
+// its writes are visible, so every kernel calls it before reading anything the
+// previous kernel wrote; pdl_trigger() lets the successor start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ float4 lds4(const float* p) {
     return *reinterpret_cast<const float4*>(p);
 }
+
+// PDL is on unless the environment sets META_NO_PDL=1 (read once).
+inline bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("META_NO_PDL");
+        return !(e && e[0] == '1');
+    }();
+    return on;
+}
+
+// Launches `kern` on `st` with the programmatic-serialization attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+#define META_CHECK_LAUNCH(x)                    \
+    do {                                        \
+        const cudaError_t _e = (x);             \
+        if (_e != cudaSuccess) return _e;       \
+    } while (0)
 
 }  // namespace meta

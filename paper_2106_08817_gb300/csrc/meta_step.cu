@@ -205,6 +205,8 @@ __device__ __forceinline__ void axis_info(const Geom& g, const Vox& v, int* c, i
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
@@ -216,6 +218,8 @@ k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, float* I1, float* p1) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
@@ -231,6 +235,8 @@ constexpr int kAdvHalo = 4;
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
            unsigned int* __restrict__ maxdisp) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     constexpr int W = kPX + 2 * kAdvHalo;        // 40
     constexpr int HU = kPY + 2;                  // 10
     constexpr int HI = kPY + 2 * kAdvHalo;       // 16
@@ -292,6 +298,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
          unsigned int* __restrict__ maxdisp) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     float dmax = 0.f;
     if (v.ok) {
@@ -341,6 +349,8 @@ __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, int T, const float* __restrict__ states, const float* __restrict__ u,
                 const float* __restrict__ J, float* Ih, float* ph, float* Ihp, float* php,
                 double* partials) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const int b = blockIdx.y;
     const long long N = (long long)g.nz * g.ny * g.nx;
     const float* IT = slice_of(states, g, ((long long)T * 2 + 0) * g.B + b);
@@ -389,6 +399,8 @@ k_cost_partials(Geom g, int T, const float* __restrict__ states, const float* __
 
 __global__ void __launch_bounds__(256)
 k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const int b = blockIdx.x;
     __shared__ double red[3][256];
     double acc[3] = {0.0, 0.0, 0.0};
@@ -413,6 +425,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, const float* __restrict__ gI1, const float* __restrict__ gp1, float* Ih,
            float* ph, float* Ihp, float* php) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
@@ -629,6 +643,260 @@ __device__ __forceinline__ void transport_fast2d(const Geom& g, float rho, float
     vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
 }
 
+// Per-axis weights with which a source passes its value to the nodes s-1, s,
+// s+1 when its foot moved by less than one voxel: the cell offset is -1 or 0,
+// so the two non-zero corner weights land on (s-1, s) or (s, s+1).
+__device__ __forceinline__ void axis_weights(const Foot1& f, int s, float* w) {
+    const bool down = (f.i0 - s) < 0;
+    w[0] = down ? 1.f - f.f : 0.f;
+    w[1] = down ? f.f : 1.f - f.f;
+    w[2] = down ? 0.f : f.f;
+}
+
+// 2-D adjoint step for instances whose per-step displacement is below one
+// voxel (H = R = 1).  Same staging as transport_fast2d<1>; the window becomes
+// nine branch-free products of per-axis weights (zero weights add exact
+// zeros, so sums equal the record-based gather's).
+__device__ __forceinline__ void transport_r1_2d(const Geom& g, float rho, float mu, float dt,
+                                                const float* It, const float* pt,
+                                                const float* u0, const float* u1,
+                                                const float* Ihb, const float* phb, float* vh0,
+                                                float* vh1, float* Ihpb, float* phpb,
+                                                float* smem) {
+    using G = GatherTile<2>;
+    constexpr int H = 1;
+    constexpr int WU = G::TX + 8, WI = G::TX + 16, WA = G::TX + 8;
+    constexpr int HU = G::TY + 2 * H + 2, HI = G::TY + 4 * H + 2, HA = G::TY + 2 * H;
+    constexpr int RX = G::TX + 2 * H, RY = G::TY + 2 * H, NR = RX * RY;
+    const float dtrho = dt * rho;
+    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+    float* sWy = smem;             // [3][NR]
+    float* sWx = sWy + 3 * NR;     // [3][NR]
+    float* s_I = sWx + 3 * NR;
+    float* s_P = s_I + NR;
+    float* s_D = s_P + NR;
+    float* sU0 = s_D + NR;         // 9 * NR = 3060 words: 16-byte aligned
+    float* sU1 = sU0 + WU * HU;
+    float* sI = sU1 + WU * HU;
+    float* sP = sI + WI * HI;
+    float* sIh = sP + WI * HI;
+    float* sPh = sIh + WA * HA;
+    const int xu = x0 - 4, yu = y0 - H - 1;
+    const int xi = x0 - 8, yi = y0 - 2 * H - 1;
+    const int xa = x0 - 4, ya = y0 - H;
+    stage_async<WU, HU>(sU0, u0, g, xu, yu);
+    stage_async<WU, HU>(sU1, u1, g, xu, yu);
+    stage_async<WI, HI>(sI, It, g, xi, yi);
+    stage_async<WI, HI>(sP, pt, g, xi, yi);
+    stage_async<WA, HA>(sIh, Ihb, g, xa, ya);
+    stage_async<WA, HA>(sPh, phb, g, xa, ya);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // Phase 1: per-axis weights, I^', p~^ and div^ of the sources of tile (+) 1.
+    for (int i = tid; i < NR; i += kPX * kPY) {
+        const int ry = i / RX, rx = i - ry * RX;
+        const int sx = x0 - H + rx, sy = y0 - H + ry;
+        float wy[3] = {0.f, 0.f, 0.f}, wx[3] = {0.f, 0.f, 0.f};
+        float fI = 0.f, fP = 0.f, fD = 0.f;
+        if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
+            const int ui = (sy - yu) * WU + (sx - xu);
+            const float d0 = disp_of(dtrho, sU0[ui]);
+            const float d1 = disp_of(dtrho, sU1[ui]);
+            float du = 0.f;
+            du += 0.5f * (sU0[ui + (sy < g.ny - 1 ? WU : 0)] - sU0[ui - (sy > 0 ? WU : 0)]);
+            du += 0.5f * (sU1[ui + (sx < g.nx - 1 ? 1 : 0)] - sU1[ui - (sx > 0 ? 1 : 0)]);
+            const float div = -rho * du;
+            const Foot1 fy = foot1(sy, d0, g.ny), fx = foot1(sx, d1, g.nx);
+            const float pw = bilin(sP + (fy.i0 - yi) * WI + (fx.i0 - xi), WI, fy.f, fx.f);
+            const int ai = (sy - ya) * WA + (sx - xa);
+            const float phv = sPh[ai];
+            fI = sIh[ai];
+            fP = phv * (1.f - dt * div) + (dt * mu) * fI;
+            fD = -dt * pw * phv;
+            axis_weights(fy, sy, wy);
+            axis_weights(fx, sx, wx);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sWy[k * NR + i] = wy[k];
+            sWx[k * NR + i] = wx[k];
+        }
+        s_I[i] = fI;
+        s_P[i] = fP;
+        s_D[i] = fD;
+    }
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) return;
+    const int me = (ty + H) * RX + tx + H;
+    // Phase 2a: S^T, sources at (dy, dx) in {-1,0,1}^2 pass weight
+    // wy[1 - dy] * wx[1 - dx] to this node.
+    float accI = 0.f, accP = 0.f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int i = me + dy * RX + dx;
+            const float w = sWy[(1 - dy) * NR + i] * sWx[(1 - dx) * NR + i];
+            accI += w * s_I[i];
+            accP += w * s_P[i];
+        }
+    }
+    const int o = y * g.P + x;
+    Ihpb[o] = accI;
+    phpb[o] = accP;
+
+    // Phase 2b: y^ from this node's own foot (recomputed from the staged u).
+    const int ui = (y - yu) * WU + (x - xu);
+    const Foot1 fy = foot1(y, disp_of(dtrho, sU0[ui]), g.ny);
+    const Foot1 fx = foot1(x, disp_of(dtrho, sU1[ui]), g.nx);
+    const int ci = (fy.i0 - yi) * WI + (fx.i0 - xi);
+    float dIy, dIx, dPy, dPx;
+    bilin_grad(sI + ci, WI, fy.f, fx.f, fy.inside, fx.inside, &dIy, &dIx);
+    bilin_grad(sP + ci, WI, fy.f, fx.f, fy.inside, fx.inside, &dPy, &dPx);
+    const float Ihv = s_I[me], pthv = s_P[me];
+    float dT0 = 0.f, dT1 = 0.f;
+    if (y >= 1) dT0 += 0.5f * s_D[me - RX];
+    if (y == g.ny - 1) dT0 += 0.5f * s_D[me];
+    if (y <= g.ny - 2) dT0 -= 0.5f * s_D[me + RX];
+    if (y == 0) dT0 -= 0.5f * s_D[me];
+    if (x >= 1) dT1 += 0.5f * s_D[me - 1];
+    if (x == g.nx - 1) dT1 += 0.5f * s_D[me];
+    if (x <= g.nx - 2) dT1 -= 0.5f * s_D[me + 1];
+    if (x == 0) dT1 -= 0.5f * s_D[me];
+    vh0[o] = -dt * (dIy * Ihv + dPy * pthv) + dT0;
+    vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
+}
+
+// 3-D adjoint step for instances whose per-step displacement is below one
+// voxel (R = 1): per-axis weight records of the sources of tile (+) 1 in shared
+// memory, a branch-free 27-candidate window, operands read through L1 with
+// 32-bit offsets inside the instance.  Same expressions as the general path.
+__device__ __forceinline__ void transport_r1_3d(const Geom& g, float rho, float mu, float dt,
+                                                const float* It, const float* pt,
+                                                const float* u0, const float* u1,
+                                                const float* u2, const float* Ihb,
+                                                const float* phb, float* vh0, float* vh1,
+                                                float* vh2, float* Ihpb, float* phpb,
+                                                float* smem) {
+    using G = GatherTile<3>;
+    constexpr int RX = G::TX + 2, RY = G::TY + 2, RZ = G::TZ + 2, NR = RX * RY * RZ;
+    const float dtrho = dt * rho;
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    const int nty = (g.ny + G::TY - 1) / G::TY;
+    const int x0 = blockIdx.x * G::TX;
+    const int y0 = (blockIdx.y % nty) * G::TY;
+    const int z0 = (blockIdx.y / nty) * G::TZ;
+    const int P = g.P, S = (int)g.slab;
+    float* sW = smem;          // [9][NR]: wz[3], wy[3], wx[3]
+    float* s_I = sW + 9 * NR;
+    float* s_P = s_I + NR;
+    float* s_D = s_P + NR;
+
+    for (int i = tid; i < NR; i += kPX * kPY) {
+        const int rz = i / (RX * RY), ry = (i / RX) % RY, rx = i % RX;
+        const int sx = x0 - 1 + rx, sy = y0 - 1 + ry, sz = z0 - 1 + rz;
+        float w[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float fI = 0.f, fP = 0.f, fD = 0.f;
+        if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
+            const int o = sz * S + sy * P + sx;
+            const float a0 = __ldg(u0 + o), a1 = __ldg(u1 + o), a2 = __ldg(u2 + o);
+            const float d0 = disp_of(dtrho, a0), d1 = disp_of(dtrho, a1), d2 = disp_of(dtrho, a2);
+            float du = 0.f;
+            du += 0.5f * (__ldg(u0 + o + (sz < g.nz - 1 ? S : 0)) - __ldg(u0 + o - (sz > 0 ? S : 0)));
+            du += 0.5f * (__ldg(u1 + o + (sy < g.ny - 1 ? P : 0)) - __ldg(u1 + o - (sy > 0 ? P : 0)));
+            du += 0.5f * (__ldg(u2 + o + (sx < g.nx - 1 ? 1 : 0)) - __ldg(u2 + o - (sx > 0 ? 1 : 0)));
+            const float div = -rho * du;
+            const Foot1 fz = foot1(sz, d0, g.nz), fy = foot1(sy, d1, g.ny), fx = foot1(sx, d2, g.nx);
+            const float* q = pt + (fz.i0 * S + fy.i0 * P + fx.i0);
+            const float c0 = (1.f - fx.f) * __ldg(q) + fx.f * __ldg(q + 1);
+            const float c1 = (1.f - fx.f) * __ldg(q + P) + fx.f * __ldg(q + P + 1);
+            const float c2 = (1.f - fx.f) * __ldg(q + S) + fx.f * __ldg(q + S + 1);
+            const float c3 = (1.f - fx.f) * __ldg(q + S + P) + fx.f * __ldg(q + S + P + 1);
+            const float b0 = (1.f - fy.f) * c0 + fy.f * c1;
+            const float b1 = (1.f - fy.f) * c2 + fy.f * c3;
+            const float pw = (1.f - fz.f) * b0 + fz.f * b1;
+            const float phv = __ldg(phb + o);
+            fI = __ldg(Ihb + o);
+            fP = phv * (1.f - dt * div) + (dt * mu) * fI;
+            fD = -dt * pw * phv;
+            axis_weights(fz, sz, w);
+            axis_weights(fy, sy, w + 3);
+            axis_weights(fx, sx, w + 6);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sW[k * NR + i] = w[k];
+        s_I[i] = fI;
+        s_P[i] = fP;
+        s_D[i] = fD;
+    }
+    __syncthreads();
+
+    const int x = x0 + (tid & 7), y = y0 + ((tid >> 3) & 7), z = z0 + (tid >> 6);
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    const int me = ((z - z0 + 1) * RY + (y - y0 + 1)) * RX + (x - x0 + 1);
+    float accI = 0.f, accP = 0.f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int i = me + (dz * RY + dy) * RX + dx;
+                const float w = (sW[(1 - dz) * NR + i] * sW[(4 - dy) * NR + i]) *
+                                sW[(7 - dx) * NR + i];
+                accI += w * s_I[i];
+                accP += w * s_P[i];
+            }
+        }
+    }
+    const int o = z * S + y * P + x;
+    Ihpb[o] = accI;
+    phpb[o] = accP;
+
+    // y^ from this node's own foot, v^ = -dt y^ + D^T div^.
+    const Foot1 fz = foot1(z, disp_of(dtrho, __ldg(u0 + o)), g.nz);
+    const Foot1 fy = foot1(y, disp_of(dtrho, __ldg(u1 + o)), g.ny);
+    const Foot1 fx = foot1(x, disp_of(dtrho, __ldg(u2 + o)), g.nx);
+    const int cb = fz.i0 * S + fy.i0 * P + fx.i0;
+    float dI[3], dP[3];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+        const float* q = (f == 0 ? It : pt) + cb;
+        const float c000 = __ldg(q), c001 = __ldg(q + 1), c010 = __ldg(q + P), c011 = __ldg(q + P + 1);
+        const float c100 = __ldg(q + S), c101 = __ldg(q + S + 1), c110 = __ldg(q + S + P),
+                    c111 = __ldg(q + S + P + 1);
+        const float a0 = (1.f - fx.f) * c000 + fx.f * c001;
+        const float a1 = (1.f - fx.f) * c010 + fx.f * c011;
+        const float a2 = (1.f - fx.f) * c100 + fx.f * c101;
+        const float a3 = (1.f - fx.f) * c110 + fx.f * c111;
+        const float b0 = (1.f - fy.f) * a0 + fy.f * a1;
+        const float b1 = (1.f - fy.f) * a2 + fy.f * a3;
+        float* dv = f == 0 ? dI : dP;
+        dv[0] = fz.inside ? (b1 - b0) : 0.f;
+        dv[1] = fy.inside ? ((1.f - fz.f) * (a1 - a0) + fz.f * (a3 - a2)) : 0.f;
+        const float e0 = (1.f - fy.f) * (c001 - c000) + fy.f * (c011 - c010);
+        const float e1 = (1.f - fy.f) * (c101 - c100) + fy.f * (c111 - c110);
+        dv[2] = fx.inside ? ((1.f - fz.f) * e0 + fz.f * e1) : 0.f;
+    }
+    const float Ihv = s_I[me], pthv = s_P[me];
+    const int rs[3] = {RX * RY, RX, 1};
+    const int cc[3] = {z, y, x}, nn[3] = {g.nz, g.ny, g.nx};
+    float* vhs[3] = {vh0, vh1, vh2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float dT = 0.f;
+        if (cc[a] >= 1) dT += 0.5f * s_D[me - rs[a]];
+        if (cc[a] == nn[a] - 1) dT += 0.5f * s_D[me];
+        if (cc[a] <= nn[a] - 2) dT -= 0.5f * s_D[me + rs[a]];
+        if (cc[a] == 0) dT -= 0.5f * s_D[me];
+        vhs[a][o] = -dt * (dI[a] * Ihv + dP[a] * pthv) + dT;
+    }
+}
+
 // One adjoint step t, fused: for every source of the node tile grown by a halo
 // H it forms p~^ = p^'(1 - dt div v) + dt mu I^' and div^ = -dt p~ p^' and the
 // foot record, then for every node of the tile
@@ -645,6 +913,8 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
                 const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
                 const float* __restrict__ Ih1, const float* __restrict__ ph1, float* vh,
                 float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     using G = GatherTile<NDIM>;
     constexpr int REG = gather_region<NDIM>();
     __shared__ __align__(16) float smem[transport_smem_words<NDIM>()];
@@ -665,14 +935,23 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
     float* Psc = php + (long long)b * g.inst;
     const int Rinst = gather_radius(maxdisp, t, g.B, b);
     if (tid == 0) s_dmax = 0u;
+    if constexpr (NDIM == 3) {
+        if (Rinst == 1) {
+            __syncthreads();
+            transport_r1_3d(g, rho, mu, dt, It, pt, ub[0], ub[1], ub[2], Ihb, phb,
+                            vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
+                            vh + (2LL * g.B + b) * g.inst, Isc, Psc, smem);
+            return;
+        }
+    }
     if constexpr (NDIM == 2) {
         if (Rinst <= kFastH2) {
             __syncthreads();
             float* vh0 = vh + (long long)b * g.inst;
             float* vh1 = vh + ((long long)g.B + b) * g.inst;
             if (Rinst == 1)
-                transport_fast2d<1>(g, rho, mu, dt, It, pt, ub[0], ub[1], Ihb, phb, vh0, vh1, Isc,
-                                    Psc, smem, &s_dmax);
+                transport_r1_2d(g, rho, mu, dt, It, pt, ub[0], ub[1], Ihb, phb, vh0, vh1, Isc,
+                                Psc, smem);
             else
                 transport_fast2d<2>(g, rho, mu, dt, It, pt, ub[0], ub[1], Ihb, phb, vh0, vh1, Isc,
                                     Psc, smem, &s_dmax);
@@ -841,12 +1120,90 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
     }
 }
 
+// 2-D k_adj_gradp on a 32 x 8 tile: m^ (both components), I_t and p_t staged
+// with a one-voxel halo by cp.async; the same expressions as k_adj_gradp.
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+              const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+              const float* __restrict__ mh, float* Ihp, float* php, float* Ih, float* ph,
+              float* out0, float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    constexpr int W = kPX + 8, HR = kPY + 2;
+    __shared__ __align__(16) float sM0[HR * W], sM1[HR * W], sI[HR * W], sP[HR * W];
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* m0 = mh + (long long)b * g.inst;
+    const float* m1 = mh + ((long long)g.B + b) * g.inst;
+    stage_async<W, HR>(sM0, m0, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sM1, m1, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sI, It, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sP, pt, g, x0 - 4, y0 - 1);
+    cp_async_wait_all();
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int o = y * g.P + x;
+    const long long ob = (long long)b * g.inst + o;
+    const int c = (threadIdx.y + 1) * W + threadIdx.x + 4;
+    float phv = php[ob];
+    float Ihv = Ihp[ob];
+    if (t > 0 && gather_radius(maxdisp, t - 1, g.B, b) > GatherTile<2>::RMAX) {
+        Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
+        php[ob] = 0.f;
+    }
+    // axis 0 (y): stride W in the staged tile
+    const float g0 = 0.5f * (sI[c + (y < g.ny - 1 ? W : 0)] - sI[c - (y > 0 ? W : 0)]);
+    phv += sM0[c] * g0;
+    {
+        float r = 0.f;
+        if (y >= 1) r += 0.5f * (sM0[c - W] * sP[c - W]);
+        if (y == g.ny - 1) r += 0.5f * (sM0[c] * sP[c]);
+        if (y <= g.ny - 2) r -= 0.5f * (sM0[c + W] * sP[c + W]);
+        if (y == 0) r -= 0.5f * (sM0[c] * sP[c]);
+        Ihv += r;
+    }
+    // axis 1 (x)
+    const float g1 = 0.5f * (sI[c + (x < g.nx - 1 ? 1 : 0)] - sI[c - (x > 0 ? 1 : 0)]);
+    phv += sM1[c] * g1;
+    {
+        float r = 0.f;
+        if (x >= 1) r += 0.5f * (sM1[c - 1] * sP[c - 1]);
+        if (x == g.nx - 1) r += 0.5f * (sM1[c] * sP[c]);
+        if (x <= g.nx - 2) r -= 0.5f * (sM1[c + 1] * sP[c + 1]);
+        if (x == 0) r -= 0.5f * (sM1[c] * sP[c]);
+        Ihv += r;
+    }
+    if (mode == 0) {
+        Ih[ob] = Ihv;
+        ph[ob] = phv;
+    } else {
+        const long long ci = ((long long)b * g.ny + y) * g.nx + x;
+        if (mode == 1) {
+            const float* u0 = slice_of(u, g, 0LL * g.B + b);
+            const float* u1 = slice_of(u, g, 1LL * g.B + b);
+            float kg = 0.f;
+            kg += g0 * u0[o];
+            kg += g1 * u1[o];
+            const float lam = cf.lambda[b], rho = cf.rho[b];
+            out0[ci] = phv + lam * (2.f * kg + 2.f * rho * sP[c]);
+        } else {
+            out0[ci] = phv;
+            if (gI0) gI0[ci] = Ihv;
+        }
+    }
+}
+
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
             const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
             const float* __restrict__ mh, float* Ihp, float* php, float* Ih, float* ph,
             float* out0, float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
@@ -902,9 +1259,9 @@ cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p
                         float* dP, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_pack<2><<<pgrid<2>(g), blk, 0, st>>>(g, I0, p0, dI, dP);
+        META_CHECK_LAUNCH(launch_k(k_pack<2>, pgrid<2>(g), blk, 0, st, g, I0, p0, dI, dP));
     else
-        k_pack<3><<<pgrid<3>(g), blk, 0, st>>>(g, I0, p0, dI, dP);
+        META_CHECK_LAUNCH(launch_k(k_pack<3>, pgrid<3>(g), blk, 0, st, g, I0, p0, dI, dP));
     return cudaGetLastError();
 }
 
@@ -912,9 +1269,9 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
                           float* p1, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_unpack<2><<<pgrid<2>(g), blk, 0, st>>>(g, sI, sP, I1, p1);
+        META_CHECK_LAUNCH(launch_k(k_unpack<2>, pgrid<2>(g), blk, 0, st, g, sI, sP, I1, p1));
     else
-        k_unpack<3><<<pgrid<3>(g), blk, 0, st>>>(g, sI, sP, I1, p1);
+        META_CHECK_LAUNCH(launch_k(k_unpack<3>, pgrid<3>(g), blk, 0, st, g, sI, sP, I1, p1));
     return cudaGetLastError();
 }
 
@@ -922,10 +1279,10 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float*
                           const float* u, unsigned int* maxdisp, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_advect2d<<<dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st>>>(
-            g, c, t, states, u, maxdisp);
+        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, 
+            g, c, t, states, u, maxdisp));
     else
-        k_advect<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp);
+        META_CHECK_LAUNCH(launch_k(k_advect<3>, pgrid<3>(g), blk, 0, st, g, c, t, states, u, maxdisp));
     return cudaGetLastError();
 }
 
@@ -934,12 +1291,12 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const fl
                         float* php, double* partials, int nblk, double* cost, cudaStream_t st) {
     const dim3 grid(nblk, g.B);
     if (ndim == 2)
-        k_cost_partials<2><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, Ihp, php, partials);
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, T, states, u, J, Ih, ph, Ihp, php, partials));
     else
-        k_cost_partials<3><<<grid, 256, 0, st>>>(g, T, states, u, J, Ih, ph, Ihp, php, partials);
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, T, states, u, J, Ih, ph, Ihp, php, partials));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_cost_final<<<g.B, 256, 0, st>>>(nblk, c, partials, cost);
+    META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
     return cudaGetLastError();
 }
 
@@ -947,9 +1304,9 @@ cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const flo
                             float* Ih, float* ph, float* Ihp, float* php, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_init<2><<<pgrid<2>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph, Ihp, php);
+        META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, gI1, gp1, Ih, ph, Ihp, php));
     else
-        k_adj_init<3><<<pgrid<3>(g), blk, 0, st>>>(g, gI1, gp1, Ih, ph, Ihp, php);
+        META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, gI1, gp1, Ih, ph, Ihp, php));
     return cudaGetLastError();
 }
 
@@ -960,11 +1317,11 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
                                  cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_transport<2><<<gather_grid<2>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1,
-                                                              ph1, vh, Ihp, php, fault);
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<2>, gather_grid<2>(g), blk, 0, st, g, c, t, states, u, maxdisp, Ih1,
+                                                              ph1, vh, Ihp, php, fault));
     else
-        k_adj_transport<3><<<gather_grid<3>(g), blk, 0, st>>>(g, c, t, states, u, maxdisp, Ih1,
-                                                              ph1, vh, Ihp, php, fault);
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<3>, gather_grid<3>(g), blk, 0, st, g, c, t, states, u, maxdisp, Ih1,
+                                                              ph1, vh, Ihp, php, fault));
     return cudaGetLastError();
 }
 
@@ -974,11 +1331,11 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
                              float* out0, float* gI0, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        k_adj_gradp<2><<<pgrid<2>(g), blk, 0, st>>>(g, c, t, mode, states, u, maxdisp, mh, Ihp,
-                                                    php, Ih, ph, out0, gI0);
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, g, c, t, mode, states, u, maxdisp, mh, Ihp,
+                                                    php, Ih, ph, out0, gI0));
     else
-        k_adj_gradp<3><<<pgrid<3>(g), blk, 0, st>>>(g, c, t, mode, states, u, maxdisp, mh, Ihp,
-                                                    php, Ih, ph, out0, gI0);
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3>, pgrid<3>(g), blk, 0, st, g, c, t, mode, states, u, maxdisp, mh, Ihp,
+                                                    php, Ih, ph, out0, gI0));
     return cudaGetLastError();
 }
 
