@@ -52,17 +52,38 @@ def bytes_per_voxel(kclass: str, d: int) -> int:
     }[kclass]
 
 
-def workload(name: str):
+def workload(name: str, rank: int = 0):
+    """The named workload; rank r > 0 gets its own seeded instances (weak scaling:
+    every rank registers its own batch of the same size, nothing is exchanged)."""
     import phantoms
+    off = 7919 * rank
     if name == "ellipses16x256":
-        return phantoms.ellipse_pairs()
+        return phantoms.ellipse_pairs(seed=1002 + off)
+    if name == "ellipses2x32":  # tiny case for the multi-rank CPU test
+        return phantoms.ellipse_pairs(batch=2, size=(32, 32), T=3, sigma=1.5, seed=1002 + off)
     if name == "disk64":
-        return phantoms.disk_pair_64(random_p0=False)
+        return phantoms.disk_pair_64(seed=1001 + off, random_p0=False)
     if name == "head128":
-        return phantoms.head_pair_3d()
+        return phantoms.head_pair_3d(seed=1003 + off)
     if name == "mri160":
-        return phantoms.mri_pair_3d()
+        return phantoms.mri_pair_3d(seed=1005 + off)
     raise SystemExit("unknown workload %s" % name)
+
+
+def reduce_max(x: float, world: int, device) -> float:
+    """Max over ranks (the slowest rank sets the job time); identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(voxel_steps_per_rank_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job voxel-steps/s: all ranks' work over the slowest rank's step time."""
+    return world * voxel_steps_per_rank_step / (ms_per_step * 1e-3)
 
 
 def workload_config(w, name: str) -> dict:
@@ -245,7 +266,7 @@ def run_ours(args):
         dist.barrier()
     import paper_2106_08817_gb300 as meta
 
-    w = workload(args.workload)
+    w = workload(args.workload, rank)
     B, d, T = w.batch, w.ndim, w.T
     N = w.voxels
     vs_per_step = B * N * T
@@ -293,12 +314,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = sum(step_ms) / args.steps
-    if world > 1:
-        m = torch.tensor([ms], device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        ms = float(m.item())
-    value = world * vs_per_step / (ms * 1e-3)
+    ms = reduce_max(sum(step_ms) / args.steps, world, dev)
+    value = job_value(vs_per_step, world, ms)
     first_cost = cost.clone()
 
     # ---- kernel timing: the same steps again, every library launch bracketed by events
@@ -343,11 +360,7 @@ def run_ours(args):
         hgrad.copy_(grad, non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
-    if world > 1:
-        m = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        e2e_ms = float(m.item())
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps, world, dev)
     h2d = 3 * B * N * 4
     d2h = B * 3 * 8 + B * N * 4
 
@@ -368,7 +381,7 @@ def run_ours(args):
             tev[k][1].record(stream)
         torch.cuda.synchronize()
         tms = sum(a.elapsed_time(b) for a, b in tev) / steps_t
-        torch_cmp = {"value": world * vs_per_step / (tms * 1e-3), "unit": UNIT,
+        torch_cmp = {"value": job_value(vs_per_step, world, tms), "unit": UNIT,
                      "ms_per_step": tms, "steps": steps_t,
                      "speedup_ours_over_torch": tms / ms,
                      "what": "baseline/torch_scheme.py: grid_sample + grouped conv + "
@@ -396,7 +409,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_us": avg_ms * 1e3},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * vs_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_value(vs_per_step, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
