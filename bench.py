@@ -8,7 +8,7 @@ takes a gradient-descent update and L2 is flushed (both outside the timed
 events).  voxel-steps = batch x voxels x T per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload ellipses16x256|disk64|head128|mri160]
+                    [--workload ellipses16x256|disk64|head128|mri160|mix64]
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 the host cores instead (the deliberately slow reference arm).
@@ -84,6 +84,13 @@ def reduce_max(x: float, world: int, device) -> float:
 def job_value(voxel_steps_per_rank_step: float, world: int, ms_per_step: float) -> float:
     """Whole-job voxel-steps/s: all ranks' work over the slowest rank's step time."""
     return world * voxel_steps_per_rank_step / (ms_per_step * 1e-3)
+
+
+def launches_per_call(kclass: str, d: int, T: int) -> int:
+    """Launches of a kernel class in one cost_and_grad (T steps each way)."""
+    return {"pack": 1, "xpass_m": T, "strided_fwd": T * (d - 1), "advect": T, "cost": 1,
+            "adj_gather": T, "xpass_adj": T, "strided_adj": T * (d - 1), "adj_gradp": T
+            }.get(kclass, 0)
 
 
 def workload_config(w, name: str) -> dict:
@@ -424,6 +431,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_mix(args):
+    """The 64 uneven 2-D/3-D pairs of phantoms.mixed_pairs in one CUDA graph with
+    parallel branches (meta_plan_create_group); value = sum of voxel-steps / time."""
+    import torch
+    import phantoms
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2106_08817_gb300 as meta
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    ws = phantoms.mixed_pairs(seed=1004 + 7919 * int(os.environ.get("RANK", "0")))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    probs = [dict(I0=t(w.I0), J=t(w.J), p0=t(w.p0), T=w.T, sigma=w.sigma, mu=t(w.mu),
+                  rho=t(w.rho), lam=t(w.lam)) for w in ws]
+    plan = meta.GroupPlan(probs, streams=args.streams)
+    vs = plan.voxel_steps()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def gd():
+        for it in plan.items:
+            g = it["grad"]
+            gmax = g.abs().amax(dim=tuple(range(1, g.dim())), keepdim=True).clamp_min(1e-30)
+            it["p0"].sub_(0.02 * g / gmax)
+
+    for _ in range(args.warmup):
+        plan.launch()
+        gd()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            plan.launch()
+            evs[k][1].record(stream)
+            gd()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    # per-class times from eager calls of every member
+    meta.timer_start(1 << 18)
+    for it in plan.items:
+        meta.cost_and_grad(it["I0"], it["J"], it["p0"], it["T"], it["sigma"], it["mu"], it["rho"],
+                           it["lam"], workspace=it["ws"], out=(it["cost"], it["grad"]))
+    torch.cuda.synchronize()
+    kt = meta.timer_stop()
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_bytes = sum(bytes_per_voxel(dom, len(it["dims"])) * it["B"] * int(np.prod(it["dims"])) *
+                    launches_per_call(dom, len(it["dims"]), it["T"]) for it in plan.items)
+    achieved = dom_bytes / (kt[dom][0] * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    fault = max(it["ws"].status() for it in plan.items)
+    print(json.dumps({
+        "metric": METRIC, "value": vs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mix64", "pairs": len(ws),
+                   "sizes": sorted(set("x".join(map(str, w.dims)) for w in ws)),
+                   "voxel_steps_per_step": vs, "graph_branches": args.streams,
+                   "step": "one graph launch of 64 cost_and_grad calls (parallel branches)",
+                   "l2": "flushed (256 MiB write) between timed steps"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src},
+        "gpu_launches": int(sum(v[2] for v in kt.values()) * args.steps),
+        "clocks": clk.summary(), "device_fault_bits": fault,
+        "kernels": {k: {"ms_total": round(v[0], 3), "launches": v[2]} for k, v in kt.items() if v[1]},
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,11 +512,14 @@ def main():
     ap.add_argument("--no-torch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mix64":
+        run_mix(args)
     else:
         run_ours(args)
 

@@ -118,6 +118,19 @@ meta_status meta_plan_create(const meta_problem* prob, const float* I0, const fl
                              const float* p0, const float* mu, const float* rho,
                              const float* lambda, double* cost, float* grad, void* ws,
                              size_t ws_bytes, meta_plan** plan);
+/* The same for n independent problems of different shapes, sizes, T or sigma
+ * (2-D and 3-D may be mixed).  Problem k has its own inputs, outputs and
+ * workspace (arrays of n host-side entries, each a device pointer as in
+ * meta_cost_and_grad).  The n calls are recorded into one CUDA graph as
+ * parallel branches (up to `streams` concurrent ones), so a single
+ * meta_plan_launch runs the whole mixed batch and independent problems
+ * overlap on the GPU. */
+meta_status meta_plan_create_group(int n, const meta_problem* probs, const float* const* I0,
+                                   const float* const* J, const float* const* p0,
+                                   const float* const* mu, const float* const* rho,
+                                   const float* const* lambda, double* const* cost,
+                                   float* const* grad, void* const* ws, const size_t* ws_bytes,
+                                   int streams, meta_plan** plan);
 meta_status meta_plan_launch(meta_plan* plan, void* stream);
 meta_status meta_plan_destroy(meta_plan* plan);
 

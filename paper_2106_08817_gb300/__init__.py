@@ -19,11 +19,12 @@ import ctypes
 import os
 from typing import Optional, Sequence, Tuple, Union
 
+import numpy as np
 import torch
 
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_adjoint", "cost_and_grad",
            "Shoot", "shoot", "library_path", "STATUS", "timer_start", "timer_stop",
-           "KERNEL_CLASSES", "CostAndGradPlan"]
+           "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack")
@@ -69,6 +70,11 @@ def _load():
         lib.meta_cost_and_grad.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V]
         lib.meta_plan_create.argtypes = [P, F, F, F, F, F, F, D, F, V, S,
                                          ctypes.POINTER(ctypes.c_void_p)]
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        lib.meta_plan_create_group.argtypes = [ctypes.c_int, P, PP, PP, PP, PP, PP, PP, PP, PP,
+                                               PP, ctypes.POINTER(S), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_void_p)]
+        lib.meta_plan_create_group.restype = ctypes.c_int
         lib.meta_plan_launch.argtypes = [V, V]
         lib.meta_plan_destroy.argtypes = [V]
         for f in ("meta_plan_create", "meta_plan_launch", "meta_plan_destroy"):
@@ -302,6 +308,65 @@ class CostAndGradPlan:
         if rc:
             raise MetaError(rc, "meta_plan_launch")
         return self.cost, self.grad
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.meta_plan_destroy(h)
+            self._h = None
+
+
+class GroupPlan:
+    """Many independent problems of different shapes / T / sigma (2-D and 3-D
+    mixed) recorded into one CUDA graph as parallel branches (meta_plan_create_group).
+
+    `problems` is a list of dicts with keys I0, J, p0 ([B, *dims] CUDA tensors),
+    T, sigma, mu, rho, lam.  Each item keeps its own copies of the inputs
+    (``plan.items[k]["p0"]`` etc.), cost [B, 3] and grad; ``launch()`` runs all.
+    """
+
+    def __init__(self, problems, streams: int = 8):
+        self.items = []
+        n = len(problems)
+        probs = (_Problem * n)()
+        ptr = lambda: (ctypes.c_void_p * n)()
+        I0s, Js, p0s, mus, rhos, lams, costs, grads, wss = (ptr() for _ in range(9))
+        wsb = (ctypes.c_size_t * n)()
+        dev = None
+        for k, pb in enumerate(problems):
+            I0b, nd, dims, _ = _shape(_as_batch(pb["I0"], "I0")[0], pb.get("ndim"))
+            B, dev = I0b.shape[0], I0b.device
+            it = {"I0": I0b.clone(), "J": _as_batch(pb["J"], "J")[0].reshape(I0b.shape).clone(),
+                  "p0": _as_batch(pb["p0"], "p0")[0].reshape(I0b.shape).clone(),
+                  "mu": _coef(pb["mu"], B, dev).clone(), "rho": _coef(pb.get("rho", 1.0), B, dev).clone(),
+                  "lam": _coef(pb.get("lam", 1e-3), B, dev).clone(),
+                  "cost": torch.empty((B, 3), dtype=torch.float64, device=dev),
+                  "grad": torch.empty_like(I0b), "T": int(pb["T"]), "sigma": float(pb["sigma"]),
+                  "dims": dims, "B": B}
+            it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev)
+            probs[k] = _problem(nd, dims, B, it["T"], it["sigma"])
+            for arr, key in ((I0s, "I0"), (Js, "J"), (p0s, "p0"), (mus, "mu"), (rhos, "rho"),
+                             (lams, "lam"), (costs, "cost"), (grads, "grad")):
+                arr[k] = it[key].data_ptr()
+            wss[k] = it["ws"].ptr()
+            wsb[k] = it["ws"].nbytes
+            self.items.append(it)
+        self.device = dev
+        h = ctypes.c_void_p(0)
+        torch.cuda.synchronize(dev)
+        rc = _load().meta_plan_create_group(n, probs, I0s, Js, p0s, mus, rhos, lams, costs,
+                                            grads, wss, wsb, int(streams), ctypes.byref(h))
+        if rc:
+            raise MetaError(rc, "meta_plan_create_group")
+        self._h = h
+
+    def launch(self):
+        rc = _load().meta_plan_launch(self._h, _stream(self.device))
+        if rc:
+            raise MetaError(rc, "meta_plan_launch")
+
+    def voxel_steps(self) -> int:
+        return sum(it["B"] * int(np.prod(it["dims"])) * it["T"] for it in self.items)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -475,6 +475,89 @@ meta_status meta_plan_create(const meta_problem* prob, const float* I0, const fl
     return META_OK;
 }
 
+meta_status meta_plan_create_group(int n, const meta_problem* probs, const float* const* I0,
+                                   const float* const* J, const float* const* p0,
+                                   const float* const* mu, const float* const* rho,
+                                   const float* const* lambda, double* const* cost,
+                                   float* const* grad, void* const* ws, const size_t* ws_bytes,
+                                   int streams, meta_plan** plan) {
+    if (!plan || n < 1 || !probs || !I0 || !J || !p0 || !mu || !rho || !lambda || !cost ||
+        !grad || !ws || !ws_bytes)
+        return META_ERR_INVALID_ARG;
+    *plan = nullptr;
+    for (int k = 0; k < n; ++k) {
+        size_t need = 0;
+        const meta_status s = meta_workspace_size(&probs[k], &need);
+        if (s != META_OK) return s;
+        if (ws_bytes[k] < need) return META_ERR_WORKSPACE;
+    }
+    if (streams < 1) streams = 1;
+    if (streams > n) streams = n;
+    if (streams > 64) streams = 64;
+    cudaStream_t root, br[64];
+    cudaEvent_t fork, done[64];
+    int made = 0;
+    meta_status status = META_OK;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking) != cudaSuccess) return META_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(root);
+        return META_ERR_CUDA;
+    }
+    for (; made < streams; ++made) {
+        if (cudaStreamCreateWithFlags(&br[made], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[made], cudaEventDisableTiming) != cudaSuccess) {
+            status = META_ERR_CUDA;
+            break;
+        }
+    }
+    const bool timer_was_on = g_timer.on;
+    g_timer.on = false;
+    if (status == META_OK &&
+        cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        status = META_ERR_CUDA;
+    else if (status == META_OK) {
+        // fork every branch stream from the root, record problem k on branch k % streams
+        if (cudaEventRecord(fork, root) != cudaSuccess) status = META_ERR_CUDA;
+        for (int j = 0; j < streams && status == META_OK; ++j)
+            if (cudaStreamWaitEvent(br[j], fork, 0) != cudaSuccess) status = META_ERR_CUDA;
+        for (int k = 0; k < n && status == META_OK; ++k)
+            status = meta_cost_and_grad(&probs[k], I0[k], J[k], p0[k], mu[k], rho[k], lambda[k],
+                                        cost[k], grad[k], ws[k], ws_bytes[k], br[k % streams]);
+        // join
+        for (int j = 0; j < streams; ++j) {
+            cudaEventRecord(done[j], br[j]);
+            cudaStreamWaitEvent(root, done[j], 0);
+        }
+        const cudaError_t e = cudaStreamEndCapture(root, &graph);
+        if (status == META_OK && e != cudaSuccess) status = META_ERR_CUDA;
+    }
+    g_timer.on = timer_was_on;
+    cudaGetLastError();
+    cudaGraphExec_t exec = nullptr;
+    if (status == META_OK && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
+        status = META_ERR_CUDA;
+    for (int j = 0; j < made; ++j) {
+        cudaStreamDestroy(br[j]);
+        cudaEventDestroy(done[j]);
+    }
+    cudaEventDestroy(fork);
+    cudaStreamDestroy(root);
+    if (status != META_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return status;
+    }
+    meta_plan* p = new (std::nothrow) meta_plan{graph, exec};
+    if (!p) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return META_ERR_INVALID_ARG;
+    }
+    *plan = p;
+    return META_OK;
+}
+
 meta_status meta_plan_launch(meta_plan* plan, void* stream) {
     if (!plan) return META_ERR_INVALID_ARG;
     return map_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));

@@ -232,3 +232,27 @@ def random_fields(seed: int, batch: int, dims: Sequence[int], p_std: float = 0.0
         I[b] = np.clip(0.8 * img + ramp, 0.0, 1.0)
         p[b] = rng.normal(0.0, p_std, dims)
     return I, p
+
+
+def mixed_pairs(n: int = 64, seed: int = 1004) -> List[Workload]:
+    """`n` single-pair workloads of uneven size and dimension: sizes drawn from
+    {96^2, 160^2, 224^2, 64^3, 96^3}, T from {10, 15, 20}, sigma_K ~ U[2, 6],
+    mu ~ U[0, 0.2], rho = 1, lambda = 1e-3; 2-D pairs as ellipse_pairs, 3-D as
+    head_pair_3d (blob radius ~ U[10, 25] scaled to the volume)."""
+    rng = np.random.default_rng(seed)
+    sizes = [(96, 96), (160, 160), (224, 224), (64, 64, 64), (96, 96, 96)]
+    out = []
+    for i in range(n):
+        dims = sizes[int(rng.integers(0, len(sizes)))]
+        T = int(rng.choice([10, 15, 20]))
+        sigma = float(rng.uniform(2.0, 6.0))
+        mu = float(rng.uniform(0.0, 0.2))
+        sub = int(rng.integers(0, 2 ** 31))
+        if len(dims) == 2:
+            w = ellipse_pairs(batch=1, size=dims, T=T, sigma=sigma, mus=(mu,), seed=sub)
+        else:
+            w = head_pair_3d(dims=dims, T=T, sigma=sigma, mu=mu,
+                             blob_radius=float(rng.uniform(10, 25)) * dims[0] / 160.0, seed=sub)
+        w.name = "mix%d" % i
+        out.append(w)
+    return out
