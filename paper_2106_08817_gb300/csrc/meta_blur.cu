@@ -18,7 +18,9 @@
 
 namespace meta {
 
-template <int NDIM, bool GRADP>
+// KC > 0: the tap loop has KC chunks of 8 at compile time (fully unrolled,
+// taps read as immediate constant-bank operands); KC = 0: runtime taps.kp.
+template <int NDIM, bool GRADP, int KC>
 __global__ void __launch_bounds__(256)
 k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
         const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0,
@@ -73,8 +75,10 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     if constexpr (GRADP) {
         // m_i = p * D_i I on the whole staged row range (finite everywhere;
         // columns 0 and LW-1 only ever meet zero taps).
+        const float inv_lw = 1.f / (float)LW;
         for (int idx = tid; idx < kRows * LW; idx += blockDim.x) {
-            const int row = idx / LW;
+            // idx < 2^12, so the rounded float quotient is the exact integer one
+            const int row = (int)(((float)idx + 0.5f) * inv_lw);
             const int c = idx - row * LW;
             const int ty = (NDIM == 2) ? row : (row & 3);
             const int tz = (NDIM == 2) ? 0 : (row >> 2);
@@ -122,19 +126,37 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
         float acc[kBX];
 #pragma unroll
         for (int j = 0; j < kBX; ++j) acc[j] = 0.f;
-        float4 c0 = lds4(src), c1 = lds4(src + 4);
-        for (int kb = 0; kb < taps.kp; kb += 8) {
-            const float4 n0 = lds4(src + kb + 8), n1 = lds4(src + kb + 12);
-            const float win[16] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w,
-                                   n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+        if constexpr (KC > 0) {
+            float win[8 * KC + 8];
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const float wt = taps.w[kb + kk];
-#pragma unroll
-                for (int j = 0; j < kBX; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+            for (int q = 0; q < 2 * KC + 2; ++q) {
+                const float4 v = lds4(src + 4 * q);
+                win[4 * q] = v.x;
+                win[4 * q + 1] = v.y;
+                win[4 * q + 2] = v.z;
+                win[4 * q + 3] = v.w;
             }
-            c0 = n0;
-            c1 = n1;
+#pragma unroll
+            for (int k = 0; k < 8 * KC; ++k) {
+                const float wt = taps.w[k];
+#pragma unroll
+                for (int j = 0; j < kBX; ++j) acc[j] = fmaf(wt, win[j + k], acc[j]);
+            }
+        } else {
+            float4 c0 = lds4(src), c1 = lds4(src + 4);
+            for (int kb = 0; kb < taps.kp; kb += 8) {
+                const float4 n0 = lds4(src + kb + 8), n1 = lds4(src + kb + 12);
+                const float win[16] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w,
+                                       n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const float wt = taps.w[kb + kk];
+#pragma unroll
+                    for (int j = 0; j < kBX; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+                }
+                c0 = n0;
+                c1 = n1;
+            }
         }
         if (row_ok) {
             const int slice = GRADP ? (out_slice0 + a * g.B + b) : (out_slice0 + (int)blockIdx.z);
@@ -147,7 +169,7 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
 }
 
 // AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
-template <int NDIM, int AXIS>
+template <int NDIM, int AXIS, int KC>
 __global__ void __launch_bounds__(512)
 k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g,
           int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul,
@@ -202,26 +224,38 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
 
     const float* src = s + (ta * kBA) * kTXS + tx;
     float acc[kBA];
-    float cur[8];
 #pragma unroll
     for (int j = 0; j < kBA; ++j) acc[j] = 0.f;
+    if constexpr (KC > 0) {
+        float win[8 * KC + 8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) cur[j] = src[j * kTXS];
-    for (int kb = 0; kb < taps.kp; kb += 8) {
-        float win[16];
+        for (int q = 0; q < 8 * KC + 8; ++q) win[q] = src[q * kTXS];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            win[j] = cur[j];
-            win[8 + j] = src[(kb + 8 + j) * kTXS];
+        for (int k = 0; k < 8 * KC; ++k) {
+            const float wt = taps.w[k];
+#pragma unroll
+            for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + k], acc[j]);
         }
+    } else {
+        float cur[8];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const float wt = taps.w[kb + kk];
+        for (int j = 0; j < 8; ++j) cur[j] = src[j * kTXS];
+        for (int kb = 0; kb < taps.kp; kb += 8) {
+            float win[16];
 #pragma unroll
-            for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+            for (int j = 0; j < 8; ++j) {
+                win[j] = cur[j];
+                win[8 + j] = src[(kb + 8 + j) * kTXS];
+            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const float wt = taps.w[kb + kk];
+#pragma unroll
+                for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cur[j] = win[8 + j];
         }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) cur[j] = win[8 + j];
     }
     const int x = x0 + tx;
     if (x >= g.nx) return;
@@ -256,20 +290,45 @@ size_t xpass_smem(int ndim, bool gradp, int r4) {
 
 size_t strided_smem(int kp) { return 128 + (size_t)kTXS * (kTA + kp) * 4; }
 
-template <int NDIM, bool GRADP>
-static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps,
-                                  const Geom& g, int sliceI, int sliceP, int out_slice0,
-                                  int nslices, float* out, unsigned int* fault, cudaStream_t st) {
+template <int NDIM, bool GRADP, int KC>
+static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tmP,
+                                   const Taps& taps, const Geom& g, int sliceI, int sliceP,
+                                   int out_slice0, int nslices, float* out, unsigned int* fault,
+                                   cudaStream_t st) {
     const size_t smem = xpass_smem(NDIM, GRADP, taps.r4);
-    cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP>,
+    cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + kTX - 1) / kTX,
               NDIM == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
               GRADP ? g.B : nslices);
-    META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP>, grid, 256, smem, st, tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
-                                                  out, fault));
-    return cudaGetLastError();
+    META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP, KC>, grid, 256, smem, st, tmI, tmP, taps, g,
+                               sliceI, sliceP, out_slice0, out, fault));
+    return cudaSuccess;
+}
+
+// Compile-time tap loops for up to 7 chunks of 8 (sigma <= 8); runtime beyond.
+template <int NDIM, bool GRADP>
+static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps,
+                                  const Geom& g, int sliceI, int sliceP, int out_slice0,
+                                  int nslices, float* out, unsigned int* fault, cudaStream_t st) {
+#define META_XPASS_KC(K)                                                                      \
+    case K:                                                                                   \
+        return launch_xpass_kc<NDIM, GRADP, K>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0, \
+                                               nslices, out, fault, st);
+    switch (taps.kp / 8) {
+        META_XPASS_KC(1)
+        META_XPASS_KC(2)
+        META_XPASS_KC(3)
+        META_XPASS_KC(4)
+        META_XPASS_KC(5)
+        META_XPASS_KC(6)
+        META_XPASS_KC(7)
+        default:
+            return launch_xpass_kc<NDIM, GRADP, 0>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                                                   nslices, out, fault, st);
+    }
+#undef META_XPASS_KC
 }
 
 cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
@@ -286,13 +345,13 @@ cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUt
                                             nslices, out, fault, st);
 }
 
-template <int NDIM, int AXIS>
-static cudaError_t launch_strided_t(const CUtensorMap& tm, const Taps& taps, const Geom& g,
-                                    int in_slice0, int out_slice0, int nslices,
-                                    const float* scale, float scale_mul, float* out,
-                                    unsigned int* fault, cudaStream_t st) {
+template <int NDIM, int AXIS, int KC>
+static cudaError_t launch_strided_kc(const CUtensorMap& tm, const Taps& taps, const Geom& g,
+                                     int in_slice0, int out_slice0, int nslices,
+                                     const float* scale, float scale_mul, float* out,
+                                     unsigned int* fault, cudaStream_t st) {
     const size_t smem = strided_smem(taps.kp);
-    cudaError_t e = cudaFuncSetAttribute(k_strided<NDIM, AXIS>,
+    cudaError_t e = cudaFuncSetAttribute(k_strided<NDIM, AXIS, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned gy;
@@ -303,9 +362,33 @@ static cudaError_t launch_strided_t(const CUtensorMap& tm, const Taps& taps, con
     else
         gy = ((g.nz + kTA - 1) / kTA) * g.ny;
     dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
-    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS>, grid, 512, smem, st, tm, taps, g, in_slice0, out_slice0, scale,
-                                                   scale_mul, out, fault));
-    return cudaGetLastError();
+    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, 512, smem, st, tm, taps, g,
+                               in_slice0, out_slice0, scale, scale_mul, out, fault));
+    return cudaSuccess;
+}
+
+template <int NDIM, int AXIS>
+static cudaError_t launch_strided_t(const CUtensorMap& tm, const Taps& taps, const Geom& g,
+                                    int in_slice0, int out_slice0, int nslices,
+                                    const float* scale, float scale_mul, float* out,
+                                    unsigned int* fault, cudaStream_t st) {
+#define META_STRIDED_KC(K)                                                                   \
+    case K:                                                                                  \
+        return launch_strided_kc<NDIM, AXIS, K>(tm, taps, g, in_slice0, out_slice0, nslices, \
+                                                scale, scale_mul, out, fault, st);
+    switch (taps.kp / 8) {
+        META_STRIDED_KC(1)
+        META_STRIDED_KC(2)
+        META_STRIDED_KC(3)
+        META_STRIDED_KC(4)
+        META_STRIDED_KC(5)
+        META_STRIDED_KC(6)
+        META_STRIDED_KC(7)
+        default:
+            return launch_strided_kc<NDIM, AXIS, 0>(tm, taps, g, in_slice0, out_slice0, nslices,
+                                                    scale, scale_mul, out, fault, st);
+    }
+#undef META_STRIDED_KC
 }
 
 cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps& taps,
