@@ -74,7 +74,7 @@ typedef struct {
 /* Bytes of workspace that every call below needs for this problem.
  * The workspace holds the whole trajectory (I_t, p_t), t = 0..T, and the
  * smoothed momenta u_t = K(p_t grad I_t), t < T, so that the adjoint needs no
- * recomputation: about (2(T+1) + d T + 3d + 6) * batch * voxels * 4 bytes. */
+ * recomputation: about (2(T+1) + d T + 4d + 6) * batch * voxels * 4 bytes. */
 meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes);
 
 /* Forward shooting (Eq. 3, Sec. 2.3): (I0, p0) -> (I1, p1) = (I_T, p_T).

@@ -1,0 +1,750 @@
+// meta_adjoint.cu -- the cost of Eq. 4 and the discrete adjoint of the
+// semi-Lagrangian step (arXiv:2106.08817, Eq. 3-4, Sec. 2.3), sm_103a.
+//
+// The adjoint runs t = T-1 .. 0 and is the exact transpose of forward step t
+// (y = x - dt v, I~ = S(y) I_t, p~ = S(y) p_t, p' = p~ (1 - dt div v),
+// I' = I~ + dt mu p~, v = -rho K (p grad I)).  With I^' = I^_{t+1} and
+// p^' = p^_{t+1}:
+//
+//   record of step t at every source x (built by the kernel that produced
+//   I^', p^' at x -- the cost kernel, the adjoint start, or k_adj_gradp of
+//   step t+1):  the cell and f of the foot of x,  I^'(x),
+//       p~^(x) = p^'(x) (1 - dt div v_t(x)) + dt mu I^'(x),
+//       div^(x) = -dt p~_t(x) p^'(x)
+//   k_adj_transport  Ihp = S^T I^', php = S^T p~^ (gather over the sources
+//       whose foot cell touches the node: fixed order, no atomics) and
+//       v^ = -dt y^ + D^T div^, y^ = dI~/dy I^' + dp~/dy p~^ at the node's foot
+//   blur of v^ with K = K^T, scaled by -rho (meta_blur.cu)  ->  m^
+//   k_adj_gradp      p^_t = php + sum_i m^_i D_i I_t,
+//                    I^_t = Ihp + sum_i D_i^T (m^_i p_t),
+//       then the record of step t-1 (or, at t = 0, the outputs; the cost
+//       gradient adds lambda (2 sum_i (D_i I_0)(K m0)_i + 2 rho p0)).
+//
+// Each record is built once per voxel, so the transport only gathers.
+#include "meta_stencil.cuh"
+
+namespace meta {
+namespace {
+
+// Window radius of the gather-form transpose at step t: a source x feeds node
+// n only if n lies in the cell of its foot, so |n - x| <= 1 + |d| per axis and
+// R = 1 + floor(max |d|) bounds every contributing source.
+__device__ __forceinline__ int gather_radius(const unsigned int* maxdisp, int t, int B, int b) {
+    return 1 + (int)floorf(__uint_as_float(maxdisp[kMaxdispStride * ((long long)t * B + b)]));
+}
+
+// Largest window gathered; beyond it the transport scatters with atomics.
+template <int NDIM>
+struct GatherTile;  // node tile of the transport kernel (256 nodes per CTA)
+template <>
+struct GatherTile<2> {
+    static constexpr int TX = 32, TY = 8, TZ = 1, RMAX = 8;
+};
+template <>
+struct GatherTile<3> {
+    static constexpr int TX = 32, TY = 4, TZ = 2, RMAX = 2;  // a warp = one x row
+};
+
+template <int NDIM>
+dim3 gather_grid(const Geom& g) {
+    using G = GatherTile<NDIM>;
+    return dim3((g.nx + G::TX - 1) / G::TX,
+                ((g.ny + G::TY - 1) / G::TY) * ((g.nz + G::TZ - 1) / G::TZ), g.B);
+}
+
+// Foot cell relative to the source: one byte per axis (offset + 64), bit
+// 24 + a when the clamp on axis a is inactive.
+__device__ __forceinline__ int pack_cell(const int* off, const bool* inside) {
+    return (off[0] + 64) | ((off[1] + 64) << 8) | ((off[2] + 64) << 16) |
+           (inside[0] ? (1 << 24) : 0) | (inside[1] ? (1 << 25) : 0) |
+           (inside[2] ? (1 << 26) : 0);
+}
+__device__ __forceinline__ int cell_off(int cell, int a) { return ((cell >> (8 * a)) & 0xff) - 64; }
+
+// (D^T w)[c] along a stride s: rows c-1 and c+1 of D, plus the edge rows.
+__device__ __forceinline__ float cdiff_T(const float* w, long long o, long long s, int c, int n) {
+    float r = 0.f;
+    if (c >= 1) r += 0.5f * w[o - s];
+    if (c == n - 1) r += 0.5f * w[o];
+    if (c <= n - 2) r -= 0.5f * w[o + s];
+    if (c == 0) r -= 0.5f * w[o];
+    return r;
+}
+
+// Record fields: slice (k * B + b) of `rec` for k = 0 cell (int bits),
+// 1..NDIM f per axis, NDIM+1 I^', NDIM+2 p~^, NDIM+3 div^.
+template <int NDIM>
+struct Rec {
+    static constexpr int kCell = 0, kI = NDIM + 1, kP = NDIM + 2, kD = NDIM + 3;
+};
+
+// Record of step t at voxel v (pitched offset o in its instance) from
+// I^' = Ih1 and p^' = ph1.  The same expressions as the forward step t.
+template <int NDIM>
+__device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int t, const Vox& v,
+                                             long long o, float Ih1, float ph1,
+                                             const float* __restrict__ states,
+                                             const float* __restrict__ u, float* rec) {
+    const int b = v.b;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const float dtrho = dt * rho;
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    float d[NDIM];
+    float du = 0.f;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+        d[a] = disp_of(dtrho, ua[o]);
+        du += cdiff(ua, o, s[a], c[a], n[a]);
+    }
+    const float div = -rho * du;
+    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+    const float pw = interp<NDIM>(g, F, slice_of(states, g, ((long long)t * 2 + 1) * g.B + b));
+    int off[3] = {0, 0, 0};
+    bool ins[3] = {false, false, false};
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        off[a] = F.f[a].i0 - c[a];
+        ins[a] = F.f[a].inside;
+    }
+    const long long sl = (long long)g.B * g.inst;
+    float* r = rec + (long long)b * g.inst + o;
+    r[Rec<NDIM>::kCell * sl] = __int_as_float(pack_cell(off, ins));
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) r[(1 + a) * sl] = F.f[a].f;
+    r[Rec<NDIM>::kI * sl] = Ih1;
+    r[Rec<NDIM>::kP * sl] = ph1 * (1.f - dt * div) + (dt * mu) * Ih1;
+    r[Rec<NDIM>::kD * sl] = -dt * pw * ph1;
+}
+
+// Per-axis weights with which a source whose foot moved by less than one
+// voxel passes its value to the nodes s-1, s, s+1 (cell offset -1 or 0).
+__device__ __forceinline__ void axis_weights(int off, float f, float* w) {
+    const bool down = off < 0;
+    w[0] = down ? 1.f - f : 0.f;
+    w[1] = down ? f : 1.f - f;
+    w[2] = down ? 0.f : f;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Cost partials: one CTA = 256 threads over a fixed voxel range of instance
+// blockIdx.y; also starts the adjoint: I^_T = I_T - J, p^_T = 0 -> record T-1.
+template <int NDIM>
+__global__ void __launch_bounds__(256)
+k_cost_partials(Geom g, Coefs cf, int T, const float* __restrict__ states,
+                const float* __restrict__ u, const float* __restrict__ J, float* rec, float* Ihp,
+                float* php, double* partials) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const int b = blockIdx.y;
+    const long long N = (long long)g.nz * g.ny * g.nx;
+    const float* IT = slice_of(states, g, ((long long)T * 2 + 0) * g.B + b);
+    const float* I0 = slice_of(states, g, (0LL * 2 + 0) * g.B + b);
+    const float* p0 = slice_of(states, g, (0LL * 2 + 1) * g.B + b);
+    double data = 0.0, kin = 0.0, res = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        Vox v;
+        v.b = b;
+        v.x = (int)(i % g.nx);
+        v.y = (int)((i / g.nx) % g.ny);
+        v.z = (int)(i / ((long long)g.nx * g.ny));
+        v.ok = true;
+        const long long o = gidx(g, v.z, v.y, v.x);
+        const float r = IT[o] - J[(long long)b * N + i];
+        data += 0.5 * (double)r * (double)r;
+        int c[NDIM], n[NDIM];
+        long long s[NDIM];
+        axis_info<NDIM>(g, v, c, n, s);
+        const float p = p0[o];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float ga = cdiff(I0, o, s[a], c[a], n[a]);
+            const float* ua = slice_of(u, g, (0LL * NDIM + a) * g.B + b);
+            kin += (double)(p * ga) * (double)ua[o];
+        }
+        res += (double)p * (double)p;
+        build_record<NDIM>(g, cf, T - 1, v, o, r, 0.f, states, u, rec);
+        slice_of(Ihp, g, b)[o] = 0.f;  // scatter accumulators start at zero
+        slice_of(php, g, b)[o] = 0.f;
+    }
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = data;
+    red[1][threadIdx.x] = kin;
+    red[2][threadIdx.x] = res;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3)
+        partials[((long long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256)
+k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const int b = blockIdx.x;
+    __shared__ double red[3][256];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) acc[k] += partials[((long long)b * nblk + i) * 3 + k];
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double lam = (double)cf.lambda[b], rho = (double)cf.rho[b];
+        cost[b * 3 + 0] = red[0][0];
+        cost[b * 3 + 1] = lam * red[1][0];
+        cost[b * 3 + 2] = lam * rho * red[2][0];
+    }
+}
+
+// Adjoint start from given gradients w.r.t. (I_T, p_T): record of step T-1.
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_init(Geom g, Coefs cf, int T, const float* __restrict__ states, const float* __restrict__ u,
+           const float* __restrict__ gI1, const float* __restrict__ gp1, float* rec, float* Ihp,
+           float* php) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ci = cidx(g, v);
+    build_record<NDIM>(g, cf, T - 1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u, rec);
+    slice_of(Ihp, g, v.b)[o] = 0.f;  // scatter accumulators start at zero
+    slice_of(php, g, v.b)[o] = 0.f;
+}
+
+// 2-D adjoint step t with R = 1, all operands staged: the records (cell, f_y,
+// f_x, I^', p~^, div^) and I_t, p_t over the tile grown by one voxel, by
+// cp.async.  The same expressions as the generic path of k_adj_transport.
+__device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const float* rb,
+                                                long long sl, const float* It, const float* pt,
+                                                float* vh0, float* vh1, float* Ihpb,
+                                                float* phpb, float* smem) {
+    constexpr int TX = 32, TY = 8, W = TX + 8, HR = TY + 2, WIN = W * HR;
+    constexpr int RX = TX + 2, RY = TY + 2, NR = RX * RY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+    float* sC = smem;            // cell bits
+    float* sF0 = sC + WIN;
+    float* sF1 = sF0 + WIN;
+    float* sI = sF1 + WIN;       // I^'
+    float* sP = sI + WIN;        // p~^
+    float* sD = sP + WIN;        // div^
+    float* sIt = sD + WIN;
+    float* sPt = sIt + WIN;
+    float* sW = sPt + WIN;       // [6][NR]: wy[3], wx[3]
+    const int xl = x0 - 4, yl = y0 - 1;
+    stage_async<W, HR>(sC, rb, g, xl, yl);
+    stage_async<W, HR>(sF0, rb + sl, g, xl, yl);
+    stage_async<W, HR>(sF1, rb + 2 * sl, g, xl, yl);
+    stage_async<W, HR>(sI, rb + 3 * sl, g, xl, yl);
+    stage_async<W, HR>(sP, rb + 4 * sl, g, xl, yl);
+    stage_async<W, HR>(sD, rb + 5 * sl, g, xl, yl);
+    stage_async<W, HR>(sIt, It, g, xl, yl);
+    stage_async<W, HR>(sPt, pt, g, xl, yl);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = tid; i < NR; i += kPX * kPY) {
+        const int ry = i / RX, rx = i - ry * RX;
+        const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
+        const int wi = ry * W + rx + 3;  // window index of source (sy, sx)
+        float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
+            const int cell = __float_as_int(sC[wi]);
+            axis_weights(cell_off(cell, 0), sF0[wi], w);
+            axis_weights(cell_off(cell, 1), sF1[wi], w + 3);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sW[k * NR + i] = w[k];
+    }
+    __syncthreads();
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= g.nx || y >= g.ny) return;
+    const int me = (ty + 1) * RX + tx + 1;   // region index of the node
+    const int mw = (ty + 1) * W + tx + 4;    // window index of the node
+    float accI = 0.f, accP = 0.f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int i = me + dy * RX + dx;
+            const int wi = mw + dy * W + dx;
+            const float wgt = sW[(1 - dy) * NR + i] * sW[(3 + 1 - dx) * NR + i];
+            accI += wgt * sI[wi];
+            accP += wgt * sP[wi];
+        }
+    }
+    const int o = y * g.P + x;
+    Ihpb[o] = accI;
+    phpb[o] = accP;
+    // y^ from the node's own foot (cell within one voxel of the node)
+    const int cell = __float_as_int(sC[mw]);
+    const float fy = sF0[mw], fx = sF1[mw];
+    const bool iny = (cell >> 24) & 1, inx = (cell >> 25) & 1;
+    const int ci = mw + cell_off(cell, 0) * W + cell_off(cell, 1);
+    float dIy, dIx, dPy, dPx;
+    bilin_grad(sIt + ci, W, fy, fx, iny, inx, &dIy, &dIx);
+    bilin_grad(sPt + ci, W, fy, fx, iny, inx, &dPy, &dPx);
+    const float Ihv = sI[mw], pthv = sP[mw];
+    float dT0 = 0.f, dT1 = 0.f;
+    if (y >= 1) dT0 += 0.5f * sD[mw - W];
+    if (y == g.ny - 1) dT0 += 0.5f * sD[mw];
+    if (y <= g.ny - 2) dT0 -= 0.5f * sD[mw + W];
+    if (y == 0) dT0 -= 0.5f * sD[mw];
+    if (x >= 1) dT1 += 0.5f * sD[mw - 1];
+    if (x == g.nx - 1) dT1 += 0.5f * sD[mw];
+    if (x <= g.nx - 2) dT1 -= 0.5f * sD[mw + 1];
+    if (x == 0) dT1 -= 0.5f * sD[mw];
+    vh0[o] = -dt * (dIy * Ihv + dPy * pthv) + dT0;
+    vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
+}
+
+// S^T and v^ of adjoint step t from the records of step t.
+//   R = 1 (every per-step displacement under one voxel): the records of the
+//     tile grown by one voxel become per-axis weights in shared memory and
+//     each node sums 3^d branch-free products (zero weights add exact zeros).
+//   1 < R <= RMAX: each node gathers over its (2R+1)^d window from the
+//     records in global memory (same order, same products).
+//   R > RMAX: each source scatters its 2^d corner terms with atomics into the
+//     zeroed Ihp / php (bounded work; summation order not fixed; info bit).
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
+                const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
+                float* vh, float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    using G = GatherTile<NDIM>;
+    constexpr int RX = G::TX + 2, RY = G::TY + 2, RZ = (NDIM == 3) ? G::TZ + 2 : 1;
+    constexpr int NR = RX * RY * RZ;
+    // 2-D: sized for transport_r1_2d (8 staged windows of 40 x 10 + 6 x 340 weights)
+    constexpr int NRW = (NDIM == 2) ? (8 * 400 + 6 * 340 + 3 * NDIM - 1) / (3 * NDIM) : NR;
+    __shared__ __align__(16) float sW[3 * NDIM][NRW];
+    __shared__ float sI[NR], sP[NR];
+
+    const int b = blockIdx.z;
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    const int nty = (g.ny + G::TY - 1) / G::TY;
+    const int x0 = blockIdx.x * G::TX;
+    const int y0 = (blockIdx.y % nty) * G::TY;
+    const int z0 = (blockIdx.y / nty) * G::TZ;
+    Vox v;
+    v.b = b;
+    if constexpr (NDIM == 2) {
+        v.x = x0 + threadIdx.x;
+        v.y = y0 + threadIdx.y;
+        v.z = 0;
+    } else {
+        v.x = x0 + (tid & 31);
+        v.y = y0 + ((tid >> 5) & 3);
+        v.z = z0 + (tid >> 7);
+    }
+    v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
+    const long long sl = (long long)g.B * g.inst;
+    const float* rb = rec + (long long)b * g.inst;  // record field k at rb + k * sl
+    const float* rI = rb + Rec<NDIM>::kI * sl;
+    const float* rP = rb + Rec<NDIM>::kP * sl;
+    const float* rD = rb + Rec<NDIM>::kD * sl;
+    const int R = gather_radius(maxdisp, t, g.B, b);
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long st[NDIM];
+    axis_info<NDIM>(g, v, c, n, st);
+    float accI = 0.f, accP = 0.f;
+
+    if constexpr (NDIM == 2) {
+        if (R == 1) {  // uniform over the CTA
+            transport_r1_2d(g, cf.dt, rb, sl, slice_of(states, g, ((long long)t * 2 + 0) * g.B + b),
+                            slice_of(states, g, ((long long)t * 2 + 1) * g.B + b),
+                            vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
+                            Ihp + (long long)b * g.inst, php + (long long)b * g.inst,
+                            &sW[0][0]);
+            return;
+        }
+    }
+    if (R == 1) {  // uniform over the CTA
+        for (int i = tid; i < NR; i += kPX * kPY) {
+            const int rz = i / (RX * RY), ry = (i / RX) % RY, rx = i % RX;
+            const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
+            const int sz = (NDIM == 3) ? z0 - 1 + rz : 0;
+            float w[3 * NDIM];
+#pragma unroll
+            for (int k = 0; k < 3 * NDIM; ++k) w[k] = 0.f;
+            float fI = 0.f, fP = 0.f;
+            if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
+                const long long so = gidx(g, sz, sy, sx);
+                const int cell = __float_as_int(__ldg(rb + so));
+#pragma unroll
+                for (int a = 0; a < NDIM; ++a)
+                    axis_weights(cell_off(cell, a), __ldg(rb + (1 + a) * sl + so), w + 3 * a);
+                fI = __ldg(rI + so);
+                fP = __ldg(rP + so);
+            }
+#pragma unroll
+            for (int k = 0; k < 3 * NDIM; ++k) sW[k][i] = w[k];
+            sI[i] = fI;
+            sP[i] = fP;
+        }
+        __syncthreads();
+        if (!v.ok) return;
+        const int me = ((NDIM == 3 ? v.z - z0 + 1 : 0) * RY + (v.y - y0 + 1)) * RX + (v.x - x0 + 1);
+        // the source at offset e from the node passes weight w_a[1 - e_a] per axis
+#pragma unroll
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int i = me + (dz * RY + dy) * RX + dx;
+                    float w;
+                    if constexpr (NDIM == 2)
+                        w = sW[1 - dy][i] * sW[3 + 1 - dx][i];
+                    else
+                        w = (sW[1 - dz][i] * sW[3 + 1 - dy][i]) * sW[6 + 1 - dx][i];
+                    accI += w * sI[i];
+                    accP += w * sP[i];
+                }
+            }
+        }
+        Ihp[(long long)b * g.inst + o] = accI;
+        php[(long long)b * g.inst + o] = accP;
+    } else if (R <= G::RMAX) {
+        if (!v.ok) return;
+        int lo[NDIM], hi[NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            lo[a] = max(c[a] - R, 0);
+            hi[a] = min(c[a] + R, n[a] - 1);
+        }
+        int e[3];
+        const int zlo = (NDIM == 3) ? lo[0] : 0, zhi = (NDIM == 3) ? hi[0] : 0;
+        for (int sz = zlo; sz <= zhi; ++sz) {
+            for (int sy = lo[NDIM - 2]; sy <= hi[NDIM - 2]; ++sy) {
+                for (int sx = lo[NDIM - 1]; sx <= hi[NDIM - 1]; ++sx) {
+                    const long long so = gidx(g, sz, sy, sx);
+                    const int cell = __float_as_int(__ldg(rb + so));
+                    const int sc[3] = {NDIM == 3 ? sz : sy, NDIM == 3 ? sy : sx, sx};
+                    bool hit = true;
+#pragma unroll
+                    for (int a = 0; a < NDIM; ++a) {
+                        e[a] = c[a] - sc[a] - cell_off(cell, a);  // node - foot cell: 0 or 1
+                        hit = hit && (unsigned)e[a] <= 1u;
+                    }
+                    if (!hit) continue;
+                    float w = 1.f;
+#pragma unroll
+                    for (int a = 0; a < NDIM; ++a) {
+                        const float f = __ldg(rb + (1 + a) * sl + so);
+                        w = (a == 0) ? (e[a] ? f : 1.f - f) : w * (e[a] ? f : 1.f - f);
+                    }
+                    accI += w * __ldg(rI + so);
+                    accP += w * __ldg(rP + so);
+                }
+            }
+        }
+        Ihp[(long long)b * g.inst + o] = accI;
+        php[(long long)b * g.inst + o] = accP;
+    } else {
+        if (!v.ok) return;
+        if (tid == 0) atomicOr(fault, kInfoScatter);
+        const int cell = __float_as_int(__ldg(rb + o));
+        const float fI = __ldg(rI + o), fP = __ldg(rP + o);
+        float f[NDIM];
+        long long q0 = 0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            f[a] = __ldg(rb + (1 + a) * sl + o);
+            q0 += (long long)(c[a] + cell_off(cell, a)) * st[a];
+        }
+        float* Isc = Ihp + (long long)b * g.inst;
+        float* Psc = php + (long long)b * g.inst;
+#pragma unroll
+        for (int k = 0; k < (1 << NDIM); ++k) {
+            float w = 1.f;
+            long long q = q0;
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) {
+                const int up = (k >> a) & 1;
+                w *= up ? f[a] : 1.f - f[a];
+                q += up ? st[a] : 0;
+            }
+            atomicAdd(Isc + q, w * fI);
+            atomicAdd(Psc + q, w * fP);
+        }
+    }
+
+    // y^ from this node's own foot, v^ = -dt y^ + D^T div^.
+    const float dt = cf.dt;
+    const int cell = __float_as_int(__ldg(rb + o));
+    Feet<NDIM> F;
+    int i0[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        i0[a] = c[a] + cell_off(cell, a);
+        F.f[a].i0 = i0[a];
+        F.f[a].f = __ldg(rb + (1 + a) * sl + o);
+        F.f[a].inside = (cell >> (24 + a)) & 1;
+    }
+    if constexpr (NDIM == 2)
+        F.base = gidx(g, 0, i0[0], i0[1]);
+    else
+        F.base = gidx(g, i0[0], i0[1], i0[2]);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    float Iv, pv, dI[NDIM], dP[NDIM];
+    interp_grad<NDIM>(g, F, It, &Iv, dI);
+    interp_grad<NDIM>(g, F, pt, &pv, dP);
+    const float Ihv = __ldg(rI + o), pthv = __ldg(rP + o);
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float yh = dI[a] * Ihv + dP[a] * pthv;
+        vh[((long long)a * g.B + b) * g.inst + o] = -dt * yh + cdiff_T(rD, o, st[a], c[a], n[a]);
+    }
+}
+
+// Shared tail of the gradp kernels: the record of step t-1 (t > 0) or the
+// outputs at t = 0 (mode 1: cost gradient, mode 2: shooting adjoint).
+template <int NDIM>
+__device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t, int mode,
+                                           const Vox& v, long long o, float Ihv, float phv,
+                                           float kg, float p0v, const float* states,
+                                           const float* u, float* rec, float* out0,
+                                           float* gI0) {
+    if (t > 0) {
+        build_record<NDIM>(g, cf, t - 1, v, o, Ihv, phv, states, u, rec);
+    } else {
+        const long long ci = cidx(g, v);
+        if (mode == 1) {
+            const float lam = cf.lambda[v.b], rho = cf.rho[v.b];
+            out0[ci] = phv + lam * (2.f * kg + 2.f * rho * p0v);
+        } else {
+            out0[ci] = phv;
+            if (gI0) gI0[ci] = Ihv;
+        }
+    }
+}
+
+// 2-D adj_gradp on a 32 x 8 tile: m^ (both components), I_t and p_t staged
+// with a one-voxel halo by cp.async.  When the record of step t-1 has R = 1,
+// u_{t-1} and p_{t-1} are staged too and the record is built from them (the
+// same expressions as build_record).
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+              const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+              const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* out0,
+              float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    constexpr int W = kPX + 8, HR = kPY + 2;
+    __shared__ __align__(16) float sM0[HR * W], sM1[HR * W], sI[HR * W], sP[HR * W];
+    __shared__ __align__(16) float sU0[HR * W], sU1[HR * W], sPp[HR * W];
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* m0 = mh + (long long)b * g.inst;
+    const float* m1 = mh + ((long long)g.B + b) * g.inst;
+    const int Rprev = (t > 0) ? gather_radius(maxdisp, t - 1, g.B, b) : 0;
+    const bool staged_rec = (t > 0) && Rprev == 1;  // uniform over the CTA
+    stage_async<W, HR>(sM0, m0, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sM1, m1, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sI, It, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sP, pt, g, x0 - 4, y0 - 1);
+    if (staged_rec) {
+        stage_async<W, HR>(sU0, slice_of(u, g, ((long long)(t - 1) * 2 + 0) * g.B + b), g,
+                           x0 - 4, y0 - 1);
+        stage_async<W, HR>(sU1, slice_of(u, g, ((long long)(t - 1) * 2 + 1) * g.B + b), g,
+                           x0 - 4, y0 - 1);
+        stage_async<W, HR>(sPp, slice_of(states, g, ((long long)(t - 1) * 2 + 1) * g.B + b), g,
+                           x0 - 4, y0 - 1);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    Vox v;
+    v.b = b;
+    v.x = x0 + threadIdx.x;
+    v.y = y0 + threadIdx.y;
+    v.z = 0;
+    v.ok = v.x < g.nx && v.y < g.ny;
+    if (!v.ok) return;
+    const int x = v.x, y = v.y;
+    const int o = y * g.P + x;
+    const long long ob = (long long)b * g.inst + o;
+    const int c = (threadIdx.y + 1) * W + threadIdx.x + 4;
+    float phv = php[ob];
+    float Ihv = Ihp[ob];
+    if (Rprev > GatherTile<2>::RMAX) {
+        Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
+        php[ob] = 0.f;
+    }
+    // axis 0 (y): stride W in the staged tile
+    const float g0 = 0.5f * (sI[c + (y < g.ny - 1 ? W : 0)] - sI[c - (y > 0 ? W : 0)]);
+    phv += sM0[c] * g0;
+    {
+        float r = 0.f;
+        if (y >= 1) r += 0.5f * (sM0[c - W] * sP[c - W]);
+        if (y == g.ny - 1) r += 0.5f * (sM0[c] * sP[c]);
+        if (y <= g.ny - 2) r -= 0.5f * (sM0[c + W] * sP[c + W]);
+        if (y == 0) r -= 0.5f * (sM0[c] * sP[c]);
+        Ihv += r;
+    }
+    // axis 1 (x)
+    const float g1 = 0.5f * (sI[c + (x < g.nx - 1 ? 1 : 0)] - sI[c - (x > 0 ? 1 : 0)]);
+    phv += sM1[c] * g1;
+    {
+        float r = 0.f;
+        if (x >= 1) r += 0.5f * (sM1[c - 1] * sP[c - 1]);
+        if (x == g.nx - 1) r += 0.5f * (sM1[c] * sP[c]);
+        if (x <= g.nx - 2) r -= 0.5f * (sM1[c + 1] * sP[c + 1]);
+        if (x == 0) r -= 0.5f * (sM1[c] * sP[c]);
+        Ihv += r;
+    }
+    if (staged_rec) {
+        // record of step t-1 from the staged u_{t-1}, p_{t-1}
+        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+        const float dtrho = dt * rho;
+        const float d0 = disp_of(dtrho, sU0[c]), d1 = disp_of(dtrho, sU1[c]);
+        float du = 0.f;
+        du += 0.5f * (sU0[c + (y < g.ny - 1 ? W : 0)] - sU0[c - (y > 0 ? W : 0)]);
+        du += 0.5f * (sU1[c + (x < g.nx - 1 ? 1 : 0)] - sU1[c - (x > 0 ? 1 : 0)]);
+        const float div = -rho * du;
+        const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
+        const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
+        const bool ins[3] = {fy.inside, fx.inside, false};
+        const float pw = bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
+        const long long sl = (long long)g.B * g.inst;
+        float* r = rec + ob;
+        r[Rec<2>::kCell * sl] = __int_as_float(pack_cell(off, ins));
+        r[sl] = fy.f;
+        r[2 * sl] = fx.f;
+        r[Rec<2>::kI * sl] = Ihv;
+        r[Rec<2>::kP * sl] = phv * (1.f - dt * div) + (dt * mu) * Ihv;
+        r[Rec<2>::kD * sl] = -dt * pw * phv;
+        return;
+    }
+    float kg = 0.f;
+    if (t == 0 && mode == 1) {
+        kg += g0 * slice_of(u, g, 0LL * g.B + b)[o];
+        kg += g1 * slice_of(u, g, 1LL * g.B + b)[o];
+    }
+    gradp_tail<2>(g, cf, t, mode, v, o, Ihv, phv, kg, sP[c], states, u, rec, out0, gI0);
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+            const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
+            const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* out0,
+            float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ob = (long long)b * g.inst + o;
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    float phv = php[ob];
+    float Ihv = Ihp[ob];
+    if (t > 0 && gather_radius(maxdisp, t - 1, g.B, b) > GatherTile<NDIM>::RMAX) {
+        Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
+        php[ob] = 0.f;
+    }
+    float kg = 0.f;  // sum_a g_a u_a (cost gradient at t = 0)
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ma = mh + ((long long)a * g.B + b) * g.inst;
+        const float ga = cdiff(It, o, s[a], c[a], n[a]);
+        phv += ma[o] * ga;
+        // D_a^T (m^_a p) at this node
+        float r = 0.f;
+        const long long sa = s[a];
+        if (c[a] >= 1) r += 0.5f * (ma[o - sa] * pt[o - sa]);
+        if (c[a] == n[a] - 1) r += 0.5f * (ma[o] * pt[o]);
+        if (c[a] <= n[a] - 2) r -= 0.5f * (ma[o + sa] * pt[o + sa]);
+        if (c[a] == 0) r -= 0.5f * (ma[o] * pt[o]);
+        Ihv += r;
+        if (t == 0 && mode == 1) kg += ga * slice_of(u, g, (0LL * NDIM + a) * g.B + b)[o];
+    }
+    gradp_tail<NDIM>(g, cf, t, mode, v, o, Ihv, phv, kg, pt[o], states, u, rec, out0, gI0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
+                        const float* u, const float* J, float* rec, float* Ihp, float* php,
+                        double* partials, int nblk, double* cost, cudaStream_t st) {
+    const dim3 grid(nblk, g.B);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, T, states, u, J,
+                                   rec, Ihp, php, partials));
+    else
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, T, states, u, J,
+                                   rec, Ihp, php, partials));
+    META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
+                            const float* u, const float* gI1, const float* gp1, float* rec,
+                            float* Ihp, float* php, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, T, states, u,
+                                   gI1, gp1, rec, Ihp, php));
+    else
+        META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, T, states, u,
+                                   gI1, gp1, rec, Ihp, php));
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
+                                 const float* states, const unsigned int* maxdisp,
+                                 const float* rec, float* vh, float* Ihp, float* php,
+                                 unsigned int* fault, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<2>, gather_grid<2>(g), blk, 0, st, g, c, t,
+                                   states, maxdisp, rec, vh, Ihp, php, fault));
+    else
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<3>, gather_grid<3>(g), blk, 0, st, g, c, t,
+                                   states, maxdisp, rec, vh, Ihp, php, fault));
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
+                             const float* states, const float* u, const unsigned int* maxdisp,
+                             const float* mh, float* Ihp, float* php, float* rec, float* out0,
+                             float* gI0, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp2d,
+                                   dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk,
+                                   0, st, g, c, t, mode, states, u, maxdisp, mh, Ihp, php, rec,
+                                   out0, gI0));
+    else
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3>, pgrid<3>(g), blk, 0, st, g, c, t, mode, states,
+                                   u, maxdisp, mh, Ihp, php, rec, out0, gI0));
+    return cudaSuccess;
+}
+
+}  // namespace meta

@@ -24,7 +24,7 @@ struct Layout {
     int ndim, T, nblk;
     size_t off_fault, off_maxdisp, off_partials;
     size_t off_states, off_u, off_SA, off_SB, off_SV;
-    size_t off_IA, off_PA, off_IB, off_PB, off_IHP, off_PHP;
+    size_t off_REC, off_IHP, off_PHP;
     size_t total;
 };
 
@@ -42,7 +42,7 @@ meta_status validate(const meta_problem* pr) {
         const long long gy1 = (long long)((pr->dims[1] + kTA - 1) / kTA) * pr->dims[0];
         const long long gy0 = (long long)((pr->dims[0] + kTA - 1) / kTA) * pr->dims[1];
         const long long gp = (long long)((pr->dims[1] + 7) / 8) * pr->dims[0];
-        const long long gg = (long long)((pr->dims[1] + 7) / 8) * ((pr->dims[0] + 3) / 4);
+        const long long gg = (long long)((pr->dims[1] + 3) / 4) * ((pr->dims[0] + 1) / 2);
         if (gy > 65535 || gy1 > 65535 || gy0 > 65535 || gp > 65535 || gg > 65535)
             return META_ERR_SHAPE;
     } else {
@@ -87,10 +87,7 @@ Layout make_layout(const meta_problem* pr) {
     L.off_SA = take(fslice * (size_t)d * B);
     L.off_SB = take(fslice * (size_t)d * B);
     L.off_SV = take(fslice * (size_t)d * B);
-    L.off_IA = take(fslice * B);
-    L.off_PA = take(fslice * B);
-    L.off_IB = take(fslice * B);
-    L.off_PB = take(fslice * B);
+    L.off_REC = take(fslice * (size_t)(d + 4) * B);
     L.off_IHP = take(fslice * B);
     L.off_PHP = take(fslice * B);
     L.total = off;
@@ -190,7 +187,7 @@ struct Ctx {
     unsigned int* fault;
     unsigned int* maxdisp;
     double* partials;
-    float *states, *u, *SA, *SB, *SV, *IA, *PA, *IB, *PB, *IHP, *PHP;
+    float *states, *u, *SA, *SB, *SV, *REC, *IHP, *PHP;
 };
 
 meta_status map_status(cudaError_t e) { return e == cudaSuccess ? META_OK : META_ERR_CUDA; }
@@ -237,10 +234,7 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     c->SA = F(L.off_SA);
     c->SB = F(L.off_SB);
     c->SV = F(L.off_SV);
-    c->IA = F(L.off_IA);
-    c->PA = F(L.off_PA);
-    c->IB = F(L.off_IB);
-    c->PB = F(L.off_PB);
+    c->REC = F(L.off_REC);
     c->IHP = F(L.off_IHP);
     c->PHP = F(L.off_PHP);
     make_taps(pr->sigma, &c->tx, &c->ts);
@@ -309,20 +303,17 @@ meta_status run_forward(Ctx& c, const Coefs& cf) {
     return META_OK;
 }
 
-// Reverse sweep; (IA, PA) hold the adjoints of (I_T, p_T) on entry.
-// mode 1: cost gradient into out0; mode 2: shooting adjoint into out0 / gI0.
+// Reverse sweep; REC holds the records of step T-1 on entry (from the cost
+// kernel or the adjoint start).  mode 1: cost gradient into out0; mode 2:
+// shooting adjoint into out0 / gI0.
 meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    float* Icur = c.IA;
-    float* Pcur = c.PA;
-    float* Inext = c.IB;
-    float* Pnext = c.PB;
     for (int t = L.T - 1; t >= 0; --t) {
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
-                    launch_adj_transport(g, d, cf, t, c.states, c.u, c.maxdisp, Icur, Pcur, c.SV,
-                                         c.IHP, c.PHP, c.fault, c.st));
+                    launch_adj_transport(g, d, cf, t, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
+                                         c.PHP, c.fault, c.st));
         // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
                     launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
@@ -345,13 +336,7 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         const int m = (t == 0) ? mode : 0;
         META_LAUNCH(META_K_ADJ_GRADP, c.st,
                     launch_adj_gradp(g, d, cf, t, m, c.states, c.u, c.maxdisp, mh, c.IHP, c.PHP,
-                                     Inext, Pnext, out0, gI0, c.st));
-        float* tI = Icur;
-        float* tP = Pcur;
-        Icur = Inext;
-        Pcur = Pnext;
-        Inext = tI;
-        Pnext = tP;
+                                     c.REC, out0, gI0, c.st));
     }
     return META_OK;
 }
@@ -402,7 +387,8 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     if (s != META_OK) return s;
     const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
     META_LAUNCH(META_K_ADJ_INIT, c.st,
-                launch_adj_init(c.L.g, c.L.ndim, gI1, gp1, c.IA, c.PA, c.IHP, c.PHP, c.st));
+                launch_adj_init(c.L.g, c.L.ndim, cf, c.L.T, c.states, c.u, gI1, gp1, c.REC, c.IHP,
+                                c.PHP, c.st));
     return run_adjoint(c, cf, 2, gp0, gI0);
 }
 
@@ -421,7 +407,7 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.IA, c.PA, c.IHP, c.PHP,
+                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.REC, c.IHP, c.PHP,
                             c.partials, c.L.nblk, cost, c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);

@@ -34,24 +34,29 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
                           float* I1, float* p1, cudaStream_t st);
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
                           const float* u, unsigned int* maxdisp, cudaStream_t st);
+// Adjoint (meta_adjoint.cu).  `rec` holds the records of one adjoint step:
+// slice (k * B + b), k = 0 foot cell (int bits), 1..NDIM f per axis, NDIM+1
+// I^', NDIM+2 p~^, NDIM+3 div^.  Ihp / php: the S^T accumulators.
+// Eq. 4 partial sums, their reduction into cost[B][3], and the records of step
+// T-1 from I^_T = I_T - J, p^_T = 0.
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                        const float* u, const float* J, float* Ih, float* ph, float* Ihp,
-                        float* php, double* partials, int nblk, double* cost, cudaStream_t st);
-cudaError_t launch_adj_init(const Geom& g, int ndim, const float* gI1, const float* gp1,
-                            float* Ih, float* ph, float* Ihp, float* php, cudaStream_t st);
-// Adjoint step t except the blur and the D^T(m^ p) part: S^T of I^' and of
-// p~^ (gather into Ihp / php, or atomic scatter for steps whose displacements
-// exceed the gather window, added to the zeroed Ihp / php), and v^ into vh.
+                        const float* u, const float* J, float* rec, float* Ihp, float* php,
+                        double* partials, int nblk, double* cost, cudaStream_t st);
+// Records of step T-1 from given gradients gI1, gp1 (gp1 nullable: zero).
+cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
+                            const float* u, const float* gI1, const float* gp1, float* rec,
+                            float* Ihp, float* php, cudaStream_t st);
+// S^T of I^' and p~^ into Ihp / php and v^ (d slices) into vh, for step t.
 cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
-                                 const float* states, const float* u,
-                                 const unsigned int* maxdisp, const float* Ih1, const float* ph1,
-                                 float* vh, float* Ihp, float* php, unsigned int* fault,
-                                 cudaStream_t st);
-// mode 0: write (Ih, ph) pitched; mode 1: cost gradient into grad (contiguous);
-// mode 2: shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
+                                 const float* states, const unsigned int* maxdisp,
+                                 const float* rec, float* vh, float* Ihp, float* php,
+                                 unsigned int* fault, cudaStream_t st);
+// I^_t, p^_t from Ihp / php and m^, then the records of step t-1 (t > 0) or
+// the outputs at t = 0: mode 1 cost gradient into grad (contiguous); mode 2
+// shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
                              const float* states, const float* u, const unsigned int* maxdisp,
-                             const float* mh, float* Ihp, float* php, float* Ih, float* ph,
+                             const float* mh, float* Ihp, float* php, float* rec,
                              float* grad_or_gp0, float* gI0, cudaStream_t st);
 
 }  // namespace meta

@@ -63,7 +63,7 @@ def test_workspace_size_grows_with_T_and_batch(meta):
     c = meta.workspace_size((64, 64), 1, 20, 3.0)
     assert b > a and c > a
     # the trajectory (2 (T+1) + d T fields) dominates: check the order of magnitude
-    fields = 2 * 11 + 2 * 10 + 3 * 2 + 6
+    fields = 2 * 11 + 2 * 10 + 4 * 2 + 6
     assert fields * 64 * 64 * 4 <= a < (fields + 8) * 64 * 64 * 4
 
 
