@@ -170,7 +170,7 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
 
 // AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
 template <int NDIM, int AXIS, int KC>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(256)
 k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g,
           int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul,
           float* __restrict__ out, unsigned int* fault) {
@@ -227,9 +227,9 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
 #pragma unroll
     for (int j = 0; j < kBA; ++j) acc[j] = 0.f;
     if constexpr (KC > 0) {
-        float win[8 * KC + 8];
+        float win[8 * KC + kBA];
 #pragma unroll
-        for (int q = 0; q < 8 * KC + 8; ++q) win[q] = src[q * kTXS];
+        for (int q = 0; q < 8 * KC + kBA; ++q) win[q] = src[q * kTXS];
 #pragma unroll
         for (int k = 0; k < 8 * KC; ++k) {
             const float wt = taps.w[k];
@@ -237,16 +237,15 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
             for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + k], acc[j]);
         }
     } else {
-        float cur[8];
+        float cur[kBA];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cur[j] = src[j * kTXS];
+        for (int j = 0; j < kBA; ++j) cur[j] = src[j * kTXS];
         for (int kb = 0; kb < taps.kp; kb += 8) {
-            float win[16];
+            float win[kBA + 8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                win[j] = cur[j];
-                win[8 + j] = src[(kb + 8 + j) * kTXS];
-            }
+            for (int j = 0; j < kBA; ++j) win[j] = cur[j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) win[kBA + j] = src[(kb + kBA + j) * kTXS];
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const float wt = taps.w[kb + kk];
@@ -254,7 +253,7 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
                 for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) cur[j] = win[8 + j];
+            for (int j = 0; j < kBA; ++j) cur[j] = win[8 + j];
         }
     }
     const int x = x0 + tx;
@@ -362,7 +361,7 @@ static cudaError_t launch_strided_kc(const CUtensorMap& tm, const Taps& taps, co
     else
         gy = ((g.nz + kTA - 1) / kTA) * g.ny;
     dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
-    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, 512, smem, st, tm, taps, g,
+    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, 256, smem, st, tm, taps, g,
                                in_slice0, out_slice0, scale, scale_mul, out, fault));
     return cudaSuccess;
 }

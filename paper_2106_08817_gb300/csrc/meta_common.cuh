@@ -16,7 +16,7 @@ constexpr int kMaxR = 54;      // sigma <= 18
 constexpr int kBX = 8;         // x-pass: outputs per thread along x
 constexpr int kTX = 128;       // x-pass: outputs per CTA along x
 constexpr int kRows = 16;      // x-pass: rows per CTA (2-D: 16 y; 3-D: 4 z x 4 y)
-constexpr int kBA = 8;         // strided pass: outputs per thread along the axis
+constexpr int kBA = 16;        // strided pass: outputs per thread along the axis
 constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 
