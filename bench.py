@@ -41,13 +41,13 @@ def bytes_per_voxel(kclass: str, d: int) -> int:
         "xpass_m": 8 + 4 * d,          # read I, p; write d components of m~
         "strided_fwd": 8 * d,          # read + write d components (per pass)
         "advect": 16 + 4 * d,          # read u (d), I, p; write I', p'
-        "cost": 24 + 4 * d,            # read I_T, J, I_0, p_0, u_0 (d); write I^, p^
-        "adj_init": 16,
-        "adj_pre": 20 + 4 * d,         # read u (d), I^', p^', p_t; write p~^, div^
-        "adj_gather": 24 + 8 * d,      # read u (d), I^', p^', I_t, p_t; write v^ (d), I^, p^
+        "cost": 44 + 12 * d,           # read I_T, J, I_0, p_0, u_0, u_T-1, p_T-1; write record
+        "adj_init": 36 + 8 * d,        # read gI1, gp1, u_T-1, p_T-1; write record, zero S^T sums
+        "adj_pre": 20 + 4 * d,         # (no longer launched)
+        "adj_gather": 32 + 8 * d,      # read record (d+4), I_t, p_t; write v^ (d), S^T I^', S^T p~^
         "xpass_adj": 8 * d,            # read + write d components
         "strided_adj": 8 * d,
-        "adj_gradp": 24 + 4 * d,       # read m^ (d), I_t, p_t, I^, p^; write I^, p^
+        "adj_gradp": 36 + 12 * d,      # read m^ (d), I_t, p_t, S^T sums, u_t-1 (d), p_t-1; write record
         "unpack": 16,
     }[kclass]
 
