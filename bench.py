@@ -281,7 +281,7 @@ def run_ours(args):
     I0, J, p0 = t(w.I0), t(w.J), t(w.p0)
     mu, rho, lam = t(w.mu), t(w.rho), t(w.lam)
     # the call recorded once into a CUDA graph (meta_plan_*); inputs updated in place
-    plan = meta.CostAndGradPlan(I0, J, p0, T, w.sigma, mu, rho, lam)
+    plan = meta.CostAndGradPlan(I0, J, p0, T, w.sigma, mu, rho, lam, ckpt=args.ckpt)
     I0, J, p0, cost, grad, ws = plan.I0, plan.J, plan.p0, plan.cost, plan.grad, plan.ws
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -297,7 +297,7 @@ def run_ours(args):
 
     def step_eager():
         meta.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam, workspace=ws,
-                           out=(cost, grad))
+                           out=(cost, grad), ckpt=args.ckpt)
 
     for _ in range(args.warmup):
         step()
@@ -407,7 +407,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic", "config": workload_config(w, args.workload),
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), ckpt_stride=args.ckpt,
+                           workspace_bytes=ws.nbytes),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src
@@ -513,6 +515,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
+    ap.add_argument("--ckpt", type=int, default=0,
+                    help="step checkpoint stride (0: keep the whole trajectory)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

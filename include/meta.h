@@ -69,12 +69,18 @@ typedef struct {
     int batch;    /* number of independent instances, >= 1 */
     int T;        /* number of time steps, dt = 1/T, in [1, 4096] */
     float sigma;  /* std (voxels) of the Gaussian RKHS kernel, in (0, 18] */
+    int ckpt_stride; /* 0 or 1: keep every state (fastest); k in [2, T-1]: keep every
+                        k-th state and recompute each segment of k steps during the
+                        adjoint (step checkpointing), trading k forward steps of
+                        compute per segment for memory */
 } meta_problem;
 
 /* Bytes of workspace that every call below needs for this problem.
- * The workspace holds the whole trajectory (I_t, p_t), t = 0..T, and the
- * smoothed momenta u_t = K(p_t grad I_t), t < T, so that the adjoint needs no
- * recomputation: about (2(T+1) + d T + 4d + 6) * batch * voxels * 4 bytes. */
+ * With ckpt_stride <= 1 the workspace holds the whole trajectory (I_t, p_t),
+ * t = 0..T, and the smoothed momenta u_t = K(p_t grad I_t), t < T, so that the
+ * adjoint needs no recomputation: about (2(T+1) + d T + 4d + 6) * batch *
+ * voxels * 4 bytes.  With ckpt_stride = k > 1: about
+ * (2(ceil(T/k) + k) + d(k+1) + 4d + 8) * batch * voxels * 4 bytes. */
 meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes);
 
 /* Forward shooting (Eq. 3, Sec. 2.3): (I0, p0) -> (I1, p1) = (I_T, p_T).
@@ -88,7 +94,9 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
  * meta_shoot_forward left in ws (same prob, mu, rho).  Given gI1, gp1, the
  * gradient of a scalar with respect to I_T and p_T (gp1 may be NULL: zero),
  * writes its gradient with respect to p0 (gp0) and, if gI0 is not NULL, I0.
- * This is the discrete transpose of every step, run from t = T-1 down to 0. */
+ * This is the discrete transpose of every step, run from t = T-1 down to 0.
+ * With ckpt_stride > 1 it first recomputes the last segment from its
+ * checkpoint, so it may be called again on the same trajectory. */
 meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const float* rho,
                                const float* gI1, const float* gp1, float* gI0, float* gp0,
                                void* ws, size_t ws_bytes, void* stream);

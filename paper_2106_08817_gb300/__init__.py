@@ -48,7 +48,7 @@ class MetaError(RuntimeError):
 
 class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3), ("batch", ctypes.c_int),
-                ("T", ctypes.c_int), ("sigma", ctypes.c_float)]
+                ("T", ctypes.c_int), ("sigma", ctypes.c_float), ("ckpt_stride", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -98,15 +98,18 @@ def _load():
     return _lib
 
 
-def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float) -> _Problem:
+def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float,
+             ckpt: int = 0) -> _Problem:
     d3 = list(dims) + [0] * (3 - len(dims))
-    return _Problem(int(ndim), (ctypes.c_int * 3)(*d3), int(batch), int(T), float(sigma))
+    return _Problem(int(ndim), (ctypes.c_int * 3)(*d3), int(batch), int(T), float(sigma),
+                    int(ckpt))
 
 
-def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float) -> int:
+def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float, ckpt: int = 0) -> int:
+    """Workspace bytes; ckpt > 1 keeps every ckpt-th state and recomputes the rest."""
     n = ctypes.c_size_t(0)
-    rc = _load().meta_workspace_size(ctypes.byref(_problem(len(dims), dims, batch, T, sigma)),
-                                     ctypes.byref(n))
+    rc = _load().meta_workspace_size(
+        ctypes.byref(_problem(len(dims), dims, batch, T, sigma, ckpt)), ctypes.byref(n))
     if rc:
         raise MetaError(rc, "meta_workspace_size")
     return int(n.value)
@@ -120,13 +123,15 @@ class Workspace:
     """
 
     def __init__(self, dims: Sequence[int], batch: int, T: int, sigma: float,
-                 device: Union[torch.device, str, int] = "cuda"):
-        self.key = (tuple(int(x) for x in dims), int(batch), int(T), float(sigma))
-        self.nbytes = workspace_size(dims, batch, T, sigma)
+                 device: Union[torch.device, str, int] = "cuda", ckpt: int = 0):
+        self.key = (tuple(int(x) for x in dims), int(batch), int(T), float(sigma), int(ckpt))
+        self.ckpt = int(ckpt)
+        self.nbytes = workspace_size(dims, batch, T, sigma, ckpt)
         self.buf = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
 
-    def matches(self, dims, batch, T, sigma) -> bool:
-        return self.key == (tuple(int(x) for x in dims), int(batch), int(T), float(sigma))
+    def matches(self, dims, batch, T, sigma, ckpt: int = 0) -> bool:
+        return self.key == (tuple(int(x) for x in dims), int(batch), int(T), float(sigma),
+                            int(ckpt))
 
     def ptr(self) -> int:
         return self.buf.data_ptr()
@@ -182,31 +187,32 @@ def _p(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
 _ws_cache = {}
 
 
-def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace]) -> Workspace:
+def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0) -> Workspace:
     if ws is not None:
-        if not ws.matches(dims, B, T, sigma):
+        if not ws.matches(dims, B, T, sigma, ckpt):
             raise ValueError("workspace was made for another problem")
         return ws
-    key = (tuple(dims), B, T, float(sigma), str(device), torch.cuda.current_stream(device).cuda_stream)
+    key = (tuple(dims), B, T, float(sigma), int(ckpt), str(device),
+           torch.cuda.current_stream(device).cuda_stream)
     w = _ws_cache.get(key)
     if w is None:
-        w = Workspace(dims, B, T, sigma, device)
+        w = Workspace(dims, B, T, sigma, device, ckpt)
         _ws_cache[key] = w
     return w
 
 
 def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
-                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None
-                  ) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
+                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
+                  ckpt: int = 0) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
     """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, workspace)
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     I1 = torch.empty_like(I0b)
     p1 = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
     rc = _load().meta_shoot_forward(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
                                     _p(I1), _p(p1), ctypes.c_void_p(ws.ptr()), ws.nbytes,
                                     _stream(dev))
@@ -224,13 +230,13 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
     returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1, dL/dp_T = gp1."""
     g1, nd, dims, sq = _shape(_as_batch(gI1, "gI1")[0], ndim)
     B, dev = g1.shape[0], g1.device
-    if not workspace.matches(dims, B, T, sigma):
+    if not workspace.matches(dims, B, T, sigma, workspace.ckpt):
         raise ValueError("workspace was made for another problem")
     gp1b = None if gp1 is None else _as_batch(gp1, "gp1")[0].reshape(g1.shape)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     gp0 = torch.empty_like(g1)
     gI0 = torch.empty_like(g1) if want_gI0 else None
-    pr = _problem(nd, dims, B, T, sigma)
+    pr = _problem(nd, dims, B, T, sigma, workspace.ckpt)
     rc = _load().meta_shoot_adjoint(ctypes.byref(pr), _p(mu_t), _p(rho_t), _p(g1), _p(gp1b),
                                     _p(gI0), _p(gp0), ctypes.c_void_p(workspace.ptr()),
                                     workspace.nbytes, _stream(dev))
@@ -245,7 +251,7 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
 def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
                   mu, rho=1.0, lam=1e-3, want_grad: bool = True,
                   workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                  out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None
+                  out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0
                   ) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
     """Eq. 4 cost per instance ([B, 3] float64: data, lambda*kinetic, lambda*rho*residual)
     and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint."""
@@ -253,14 +259,14 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, workspace)
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     if out is not None:
         cost, grad = out
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b) if want_grad else None
-    pr = _problem(nd, dims, B, T, sigma)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
     rc = _load().meta_cost_and_grad(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b), _p(mu_t),
                                     _p(rho_t), _p(lam_t), _p(cost), _p(grad),
                                     ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev))
@@ -280,7 +286,7 @@ class CostAndGradPlan:
     """
 
     def __init__(self, I0, J, p0, T: int, sigma: float, mu, rho=1.0, lam=1e-3,
-                 ndim: Optional[int] = None):
+                 ndim: Optional[int] = None, ckpt: int = 0):
         I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
         B, dev = I0b.shape[0], I0b.device
         self.I0 = I0b.clone()
@@ -290,9 +296,9 @@ class CostAndGradPlan:
                                        _coef(lam, B, dev).clone())
         self.cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         self.grad = torch.empty_like(I0b)
-        self.ws = Workspace(dims, B, T, sigma, dev)
+        self.ws = Workspace(dims, B, T, sigma, dev, ckpt)
         self.device = dev
-        pr = _problem(nd, dims, B, T, sigma)
+        pr = _problem(nd, dims, B, T, sigma, ckpt)
         h = ctypes.c_void_p(0)
         torch.cuda.synchronize(dev)
         rc = _load().meta_plan_create(ctypes.byref(pr), _p(self.I0), _p(self.J), _p(self.p0),
@@ -343,8 +349,9 @@ class GroupPlan:
                   "cost": torch.empty((B, 3), dtype=torch.float64, device=dev),
                   "grad": torch.empty_like(I0b), "T": int(pb["T"]), "sigma": float(pb["sigma"]),
                   "dims": dims, "B": B}
-            it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev)
-            probs[k] = _problem(nd, dims, B, it["T"], it["sigma"])
+            it["ckpt"] = int(pb.get("ckpt", 0))
+            it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev, it["ckpt"])
+            probs[k] = _problem(nd, dims, B, it["T"], it["sigma"], it["ckpt"])
             for arr, key in ((I0s, "I0"), (Js, "J"), (p0s, "p0"), (mus, "mu"), (rhos, "rho"),
                              (lams, "lam"), (costs, "cost"), (grads, "grad")):
                 arr[k] = it[key].data_ptr()
@@ -380,7 +387,7 @@ NOALLOC_MAX_BYTES = 64 << 20
 
 def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int,
                           sigma: float, mu, rho=1.0, lam=1e-3, ndim: Optional[int] = None,
-                          out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None
+                          out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0
                           ) -> Tuple[torch.Tensor, torch.Tensor]:
     """cost_and_grad on the library's fixed 64 MiB device scratch: no workspace
     argument.  For callers that cannot allocate device memory; pass `out` (and
@@ -396,7 +403,7 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma)
+    pr = _problem(nd, dims, B, T, sigma, ckpt)
     rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
                                             _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
                                             _p(grad), _stream(dev))

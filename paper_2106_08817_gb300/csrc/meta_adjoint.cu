@@ -79,10 +79,11 @@ struct Rec {
 };
 
 // Record of step t at voxel v (pitched offset o in its instance) from
-// I^' = Ih1 and p^' = ph1.  The same expressions as the forward step t.
+// I^' = Ih1 and p^' = ph1; state t sits in slot s_state, u_t in slot s_u.  The
+// same expressions as the forward step t.
 template <int NDIM>
-__device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int t, const Vox& v,
-                                             long long o, float Ih1, float ph1,
+__device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
+                                             const Vox& v, long long o, float Ih1, float ph1,
                                              const float* __restrict__ states,
                                              const float* __restrict__ u, float* rec) {
     const int b = v.b;
@@ -95,13 +96,14 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
     float du = 0.f;
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
-        const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+        const float* ua = slice_of(u, g, ((long long)s_u * NDIM + a) * g.B + b);
         d[a] = disp_of(dtrho, ua[o]);
         du += cdiff(ua, o, s[a], c[a], n[a]);
     }
     const float div = -rho * du;
     const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-    const float pw = interp<NDIM>(g, F, slice_of(states, g, ((long long)t * 2 + 1) * g.B + b));
+    const float pw =
+        interp<NDIM>(g, F, slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b));
     int off[3] = {0, 0, 0};
     bool ins[3] = {false, false, false};
 #pragma unroll
@@ -134,16 +136,16 @@ __device__ __forceinline__ void axis_weights(int off, float f, float* w) {
 // blockIdx.y; also starts the adjoint: I^_T = I_T - J, p^_T = 0 -> record T-1.
 template <int NDIM>
 __global__ void __launch_bounds__(256)
-k_cost_partials(Geom g, Coefs cf, int T, const float* __restrict__ states,
+k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
                 const float* __restrict__ u, const float* __restrict__ J, float* rec, float* Ihp,
                 float* php, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const int b = blockIdx.y;
     const long long N = (long long)g.nz * g.ny * g.nx;
-    const float* IT = slice_of(states, g, ((long long)T * 2 + 0) * g.B + b);
-    const float* I0 = slice_of(states, g, (0LL * 2 + 0) * g.B + b);
-    const float* p0 = slice_of(states, g, (0LL * 2 + 1) * g.B + b);
+    const float* IT = slice_of(states, g, ((long long)sl.sT * 2 + 0) * g.B + b);
+    const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
+    const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
     double data = 0.0, kin = 0.0, res = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -163,11 +165,11 @@ k_cost_partials(Geom g, Coefs cf, int T, const float* __restrict__ states,
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const float ga = cdiff(I0, o, s[a], c[a], n[a]);
-            const float* ua = slice_of(u, g, (0LL * NDIM + a) * g.B + b);
+            const float* ua = slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b);
             kin += (double)(p * ga) * (double)ua[o];
         }
         res += (double)p * (double)p;
-        build_record<NDIM>(g, cf, T - 1, v, o, r, 0.f, states, u, rec);
+        build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec);
         slice_of(Ihp, g, b)[o] = 0.f;  // scatter accumulators start at zero
         slice_of(php, g, b)[o] = 0.f;
     }
@@ -212,16 +214,16 @@ k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* co
 // Adjoint start from given gradients w.r.t. (I_T, p_T): record of step T-1.
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_init(Geom g, Coefs cf, int T, const float* __restrict__ states, const float* __restrict__ u,
-           const float* __restrict__ gI1, const float* __restrict__ gp1, float* rec, float* Ihp,
-           float* php) {
+k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
+           const float* __restrict__ u, const float* __restrict__ gI1,
+           const float* __restrict__ gp1, float* rec, float* Ihp, float* php) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
-    build_record<NDIM>(g, cf, T - 1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u, rec);
+    build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u, rec);
     slice_of(Ihp, g, v.b)[o] = 0.f;  // scatter accumulators start at zero
     slice_of(php, g, v.b)[o] = 0.f;
 }
@@ -312,6 +314,22 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
     vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
 }
 
+// Records of step t from raw adjoints I^_{t+1}, p^_{t+1} (pitched), once the
+// forward segment holding step t has been recomputed (step checkpointing).
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
+              const float* __restrict__ u, const float* __restrict__ rawI,
+              const float* __restrict__ rawP, float* rec) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long ob = (long long)v.b * g.inst + o;
+    build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, rawI[ob], rawP[ob], states, u, rec);
+}
+
 // S^T and v^ of adjoint step t from the records of step t.
 //   R = 1 (every per-step displacement under one voxel): the records of the
 //     tile grown by one voxel become per-axis weights in shared memory and
@@ -322,7 +340,7 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
 //     zeroed Ihp / php (bounded work; summation order not fixed; info bit).
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
+k_adj_transport(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states,
                 const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
                 float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
@@ -353,11 +371,11 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
         v.z = z0 + (tid >> 7);
     }
     v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
-    const long long sl = (long long)g.B * g.inst;
-    const float* rb = rec + (long long)b * g.inst;  // record field k at rb + k * sl
-    const float* rI = rb + Rec<NDIM>::kI * sl;
-    const float* rP = rb + Rec<NDIM>::kP * sl;
-    const float* rD = rb + Rec<NDIM>::kD * sl;
+    const long long rsl = (long long)g.B * g.inst;
+    const float* rb = rec + (long long)b * g.inst;  // record field k at rb + k * rsl
+    const float* rI = rb + Rec<NDIM>::kI * rsl;
+    const float* rP = rb + Rec<NDIM>::kP * rsl;
+    const float* rD = rb + Rec<NDIM>::kD * rsl;
     const int R = gather_radius(maxdisp, t, g.B, b);
     const long long o = gidx(g, v.z, v.y, v.x);
     int c[NDIM], n[NDIM];
@@ -367,8 +385,9 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
 
     if constexpr (NDIM == 2) {
         if (R == 1) {  // uniform over the CTA
-            transport_r1_2d(g, cf.dt, rb, sl, slice_of(states, g, ((long long)t * 2 + 0) * g.B + b),
-                            slice_of(states, g, ((long long)t * 2 + 1) * g.B + b),
+            transport_r1_2d(g, cf.dt, rb, rsl,
+                            slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b),
+                            slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b),
                             vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
                             Ihp + (long long)b * g.inst, php + (long long)b * g.inst,
                             &sW[0][0]);
@@ -389,7 +408,7 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
                 const int cell = __float_as_int(__ldg(rb + so));
 #pragma unroll
                 for (int a = 0; a < NDIM; ++a)
-                    axis_weights(cell_off(cell, a), __ldg(rb + (1 + a) * sl + so), w + 3 * a);
+                    axis_weights(cell_off(cell, a), __ldg(rb + (1 + a) * rsl + so), w + 3 * a);
                 fI = __ldg(rI + so);
                 fP = __ldg(rP + so);
             }
@@ -447,7 +466,7 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
                     float w = 1.f;
 #pragma unroll
                     for (int a = 0; a < NDIM; ++a) {
-                        const float f = __ldg(rb + (1 + a) * sl + so);
+                        const float f = __ldg(rb + (1 + a) * rsl + so);
                         w = (a == 0) ? (e[a] ? f : 1.f - f) : w * (e[a] ? f : 1.f - f);
                     }
                     accI += w * __ldg(rI + so);
@@ -466,7 +485,7 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
         long long q0 = 0;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
-            f[a] = __ldg(rb + (1 + a) * sl + o);
+            f[a] = __ldg(rb + (1 + a) * rsl + o);
             q0 += (long long)(c[a] + cell_off(cell, a)) * st[a];
         }
         float* Isc = Ihp + (long long)b * g.inst;
@@ -495,15 +514,15 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
     for (int a = 0; a < NDIM; ++a) {
         i0[a] = c[a] + cell_off(cell, a);
         F.f[a].i0 = i0[a];
-        F.f[a].f = __ldg(rb + (1 + a) * sl + o);
+        F.f[a].f = __ldg(rb + (1 + a) * rsl + o);
         F.f[a].inside = (cell >> (24 + a)) & 1;
     }
     if constexpr (NDIM == 2)
         F.base = gidx(g, 0, i0[0], i0[1]);
     else
         F.base = gidx(g, i0[0], i0[1], i0[2]);
-    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     float Iv, pv, dI[NDIM], dP[NDIM];
     interp_grad<NDIM>(g, F, It, &Iv, dI);
     interp_grad<NDIM>(g, F, pt, &pv, dP);
@@ -515,16 +534,21 @@ k_adj_transport(Geom g, Coefs cf, int t, const float* __restrict__ states,
     }
 }
 
-// Shared tail of the gradp kernels: the record of step t-1 (t > 0) or the
-// outputs at t = 0 (mode 1: cost gradient, mode 2: shooting adjoint).
+// Shared tail of the gradp kernels.  mode 0: the record of step t-1; mode 3:
+// raw I^_t, p^_t into rawI / rawP (step t-1 lies in a forward segment that is
+// recomputed first); at t = 0, mode 1: the cost gradient, mode 2: the
+// shooting adjoint.
 template <int NDIM>
 __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t, int mode,
-                                           const Vox& v, long long o, float Ihv, float phv,
-                                           float kg, float p0v, const float* states,
-                                           const float* u, float* rec, float* out0,
-                                           float* gI0) {
-    if (t > 0) {
-        build_record<NDIM>(g, cf, t - 1, v, o, Ihv, phv, states, u, rec);
+                                           const Slots& sl, const Vox& v, long long o, float Ihv,
+                                           float phv, float kg, float p0v, const float* states,
+                                           const float* u, float* rec, float* rawI, float* rawP,
+                                           float* out0, float* gI0) {
+    if (mode == 0) {
+        build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, Ihv, phv, states, u, rec);
+    } else if (mode == 3) {
+        rawI[(long long)v.b * g.inst + o] = Ihv;
+        rawP[(long long)v.b * g.inst + o] = phv;
     } else {
         const long long ci = cidx(g, v);
         if (mode == 1) {
@@ -542,10 +566,10 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
 // u_{t-1} and p_{t-1} are staged too and the record is built from them (the
 // same expressions as build_record).
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
               const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
-              const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* out0,
-              float* gI0) {
+              const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI,
+              float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     constexpr int W = kPX + 8, HR = kPY + 2;
@@ -553,22 +577,22 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, const float* __restrict__ state
     __shared__ __align__(16) float sU0[HR * W], sU1[HR * W], sPp[HR * W];
     const int b = blockIdx.z;
     const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
-    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     const float* m0 = mh + (long long)b * g.inst;
     const float* m1 = mh + ((long long)g.B + b) * g.inst;
     const int Rprev = (t > 0) ? gather_radius(maxdisp, t - 1, g.B, b) : 0;
-    const bool staged_rec = (t > 0) && Rprev == 1;  // uniform over the CTA
+    const bool staged_rec = (mode == 0) && Rprev == 1;  // uniform over the CTA
     stage_async<W, HR>(sM0, m0, g, x0 - 4, y0 - 1);
     stage_async<W, HR>(sM1, m1, g, x0 - 4, y0 - 1);
     stage_async<W, HR>(sI, It, g, x0 - 4, y0 - 1);
     stage_async<W, HR>(sP, pt, g, x0 - 4, y0 - 1);
     if (staged_rec) {
-        stage_async<W, HR>(sU0, slice_of(u, g, ((long long)(t - 1) * 2 + 0) * g.B + b), g,
+        stage_async<W, HR>(sU0, slice_of(u, g, ((long long)sl.ut1 * 2 + 0) * g.B + b), g,
                            x0 - 4, y0 - 1);
-        stage_async<W, HR>(sU1, slice_of(u, g, ((long long)(t - 1) * 2 + 1) * g.B + b), g,
+        stage_async<W, HR>(sU1, slice_of(u, g, ((long long)sl.ut1 * 2 + 1) * g.B + b), g,
                            x0 - 4, y0 - 1);
-        stage_async<W, HR>(sPp, slice_of(states, g, ((long long)(t - 1) * 2 + 1) * g.B + b), g,
+        stage_async<W, HR>(sPp, slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b), g,
                            x0 - 4, y0 - 1);
     }
     cp_async_wait_all();
@@ -625,30 +649,31 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, const float* __restrict__ state
         const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
         const bool ins[3] = {fy.inside, fx.inside, false};
         const float pw = bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
-        const long long sl = (long long)g.B * g.inst;
+        const long long rsl = (long long)g.B * g.inst;
         float* r = rec + ob;
-        r[Rec<2>::kCell * sl] = __int_as_float(pack_cell(off, ins));
-        r[sl] = fy.f;
-        r[2 * sl] = fx.f;
-        r[Rec<2>::kI * sl] = Ihv;
-        r[Rec<2>::kP * sl] = phv * (1.f - dt * div) + (dt * mu) * Ihv;
-        r[Rec<2>::kD * sl] = -dt * pw * phv;
+        r[Rec<2>::kCell * rsl] = __int_as_float(pack_cell(off, ins));
+        r[rsl] = fy.f;
+        r[2 * rsl] = fx.f;
+        r[Rec<2>::kI * rsl] = Ihv;
+        r[Rec<2>::kP * rsl] = phv * (1.f - dt * div) + (dt * mu) * Ihv;
+        r[Rec<2>::kD * rsl] = -dt * pw * phv;
         return;
     }
     float kg = 0.f;
     if (t == 0 && mode == 1) {
-        kg += g0 * slice_of(u, g, 0LL * g.B + b)[o];
-        kg += g1 * slice_of(u, g, 1LL * g.B + b)[o];
+        kg += g0 * slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o];
+        kg += g1 * slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o];
     }
-    gradp_tail<2>(g, cf, t, mode, v, o, Ihv, phv, kg, sP[c], states, u, rec, out0, gI0);
+    gradp_tail<2>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI, rawP, out0,
+                  gI0);
 }
 
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
+k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
             const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
-            const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* out0,
-            float* gI0) {
+            const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI,
+            float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
@@ -659,8 +684,8 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
     int c[NDIM], n[NDIM];
     long long s[NDIM];
     axis_info<NDIM>(g, v, c, n, s);
-    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     float phv = php[ob];
     float Ihv = Ihp[ob];
     if (t > 0 && gather_radius(maxdisp, t - 1, g.B, b) > GatherTile<NDIM>::RMAX) {
@@ -681,69 +706,86 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, const float* __restrict__ states,
         if (c[a] <= n[a] - 2) r -= 0.5f * (ma[o + sa] * pt[o + sa]);
         if (c[a] == 0) r -= 0.5f * (ma[o] * pt[o]);
         Ihv += r;
-        if (t == 0 && mode == 1) kg += ga * slice_of(u, g, (0LL * NDIM + a) * g.B + b)[o];
+        if (t == 0 && mode == 1) kg += ga * slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b)[o];
     }
-    gradp_tail<NDIM>(g, cf, t, mode, v, o, Ihv, phv, kg, pt[o], states, u, rec, out0, gI0);
+    gradp_tail<NDIM>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, pt[o], states, u, rec, rawI, rawP,
+                     out0, gI0);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                        const float* u, const float* J, float* rec, float* Ihp, float* php,
-                        double* partials, int nblk, double* cost, cudaStream_t st) {
+cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                        const float* states, const float* u, const float* J, float* rec,
+                        float* Ihp, float* php, double* partials, int nblk, double* cost,
+                        cudaStream_t st) {
     const dim3 grid(nblk, g.B);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, T, states, u, J,
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, sl, states, u, J,
                                    rec, Ihp, php, partials));
     else
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, T, states, u, J,
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, sl, states, u, J,
                                    rec, Ihp, php, partials));
     META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
     return cudaSuccess;
 }
 
-cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                            const float* u, const float* gI1, const float* gp1, float* rec,
-                            float* Ihp, float* php, cudaStream_t st) {
+cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* states, const float* u, const float* gI1,
+                            const float* gp1, float* rec, float* Ihp, float* php,
+                            cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, T, states, u,
+        META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
                                    gI1, gp1, rec, Ihp, php));
     else
-        META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, T, states, u,
+        META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
                                    gI1, gp1, rec, Ihp, php));
     return cudaSuccess;
 }
 
-cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
+cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                               const float* states, const float* u, const float* rawI,
+                               const float* rawP, float* rec, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_adj_records<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawI, rawP, rec));
+    else
+        META_CHECK_LAUNCH(launch_k(k_adj_records<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawI, rawP, rec));
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                                  const float* states, const unsigned int* maxdisp,
                                  const float* rec, float* vh, float* Ihp, float* php,
                                  unsigned int* fault, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_adj_transport<2>, gather_grid<2>(g), blk, 0, st, g, c, t,
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<2>, gather_grid<2>(g), blk, 0, st, g, c, t, sl,
                                    states, maxdisp, rec, vh, Ihp, php, fault));
     else
-        META_CHECK_LAUNCH(launch_k(k_adj_transport<3>, gather_grid<3>(g), blk, 0, st, g, c, t,
+        META_CHECK_LAUNCH(launch_k(k_adj_transport<3>, gather_grid<3>(g), blk, 0, st, g, c, t, sl,
                                    states, maxdisp, rec, vh, Ihp, php, fault));
     return cudaSuccess;
 }
 
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
-                             const float* states, const float* u, const unsigned int* maxdisp,
-                             const float* mh, float* Ihp, float* php, float* rec, float* out0,
-                             float* gI0, cudaStream_t st) {
+                             const Slots& sl, const float* states, const float* u,
+                             const unsigned int* maxdisp, const float* mh, float* Ihp, float* php,
+                             float* rec, float* rawI, float* rawP, float* out0, float* gI0,
+                             cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_gradp2d,
                                    dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk,
-                                   0, st, g, c, t, mode, states, u, maxdisp, mh, Ihp, php, rec,
-                                   out0, gI0));
+                                   0, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
+                                   rec, rawI, rawP, out0, gI0));
     else
-        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3>, pgrid<3>(g), blk, 0, st, g, c, t, mode, states,
-                                   u, maxdisp, mh, Ihp, php, rec, out0, gI0));
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3>, pgrid<3>(g), blk, 0, st, g, c, t, mode, sl,
+                                   states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0));
     return cudaSuccess;
 }
 

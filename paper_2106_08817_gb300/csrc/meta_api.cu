@@ -22,10 +22,32 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Layout {
     Geom g;
     int ndim, T, nblk;
+    int k;        // checkpoint stride; 0 = every state kept (slot = time)
+    int nseg;     // segments of k steps (k > 0)
+    int nstate;   // state slots
+    int nu;       // u slots
     size_t off_fault, off_maxdisp, off_partials;
     size_t off_states, off_u, off_SA, off_SB, off_SV;
-    size_t off_REC, off_IHP, off_PHP;
+    size_t off_REC, off_IHP, off_PHP, off_RAW;
     size_t total;
+
+    // Keeping every state: slot = time.  With stride k: state t of segment s
+    // (t in [s k, s k + k]) lives in checkpoint slot s when t = s k, else in
+    // segment slot nseg + (t - s k) - 1; u_t in slot t % k, u_0 in slot k.
+    int state_slot(int t, int s) const {
+        if (k == 0) return t;
+        return t == s * k ? s : nseg + (t - s * k) - 1;
+    }
+    int u_slot(int t) const { return k == 0 ? t : (t == 0 ? k : t % k); }
+    int seg_of(int t) const { return k == 0 ? 0 : t / k; }
+    int seg_end(int s) const { return k == 0 ? T : (s * k + k < T ? s * k + k : T); }
+    // slot written by the first forward pass for time t + 1
+    int forward_out_slot(int t) const {
+        if (k == 0) return t + 1;
+        if ((t + 1) % k == 0 && t + 1 < T) return (t + 1) / k;  // next checkpoint
+        return state_slot(t + 1, t / k);
+    }
+    int final_slot() const { return k == 0 ? T : state_slot(T, (T - 1) / k); }
 };
 
 meta_status validate(const meta_problem* pr) {
@@ -34,6 +56,7 @@ meta_status validate(const meta_problem* pr) {
     if (pr->batch < 1 || pr->batch > 16384) return META_ERR_INVALID_ARG;
     if (pr->T < 1 || pr->T > 4096) return META_ERR_INVALID_ARG;
     if (!(pr->sigma > 0.f) || !(pr->sigma <= 18.f)) return META_ERR_INVALID_ARG;
+    if (pr->ckpt_stride < 0 || pr->ckpt_stride > 4096) return META_ERR_INVALID_ARG;
     for (int a = 0; a < pr->ndim; ++a)
         if (pr->dims[a] < 2 || pr->dims[a] > 65536) return META_ERR_SHAPE;
     if (pr->ndim == 3) {
@@ -65,6 +88,11 @@ Layout make_layout(const meta_problem* pr) {
     g.slab = (long long)g.ny * g.P;
     g.inst = (long long)g.nz * g.slab;
     g.B = pr->batch;
+    // a stride of 0, 1 or >= T keeps every state
+    L.k = (pr->ckpt_stride > 1 && pr->ckpt_stride < pr->T) ? pr->ckpt_stride : 0;
+    L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
+    L.nstate = L.k ? L.nseg + L.k : pr->T + 1;
+    L.nu = L.k ? L.k + 1 : pr->T;
     const long long N = (long long)g.nz * g.ny * g.nx;
     long long nblk = (N + 2047) / 2048;
     if (nblk < 1) nblk = 1;
@@ -82,14 +110,15 @@ Layout make_layout(const meta_problem* pr) {
     L.off_fault = take(16);
     L.off_maxdisp = take(sizeof(unsigned int) * kMaxdispStride * (size_t)pr->T * B);
     L.off_partials = take(sizeof(double) * 3 * B * (size_t)L.nblk);
-    L.off_states = take(fslice * 2 * B * (size_t)(pr->T + 1));
-    L.off_u = take(fslice * (size_t)d * B * (size_t)pr->T);
+    L.off_states = take(fslice * 2 * B * (size_t)L.nstate);
+    L.off_u = take(fslice * (size_t)d * B * (size_t)L.nu);
     L.off_SA = take(fslice * (size_t)d * B);
     L.off_SB = take(fslice * (size_t)d * B);
     L.off_SV = take(fslice * (size_t)d * B);
     L.off_REC = take(fslice * (size_t)(d + 4) * B);
     L.off_IHP = take(fslice * B);
     L.off_PHP = take(fslice * B);
+    L.off_RAW = L.k ? take(fslice * 2 * B) : 0;  // raw I^, p^ at segment starts
     L.total = off;
     return L;
 }
@@ -187,7 +216,7 @@ struct Ctx {
     unsigned int* fault;
     unsigned int* maxdisp;
     double* partials;
-    float *states, *u, *SA, *SB, *SV, *REC, *IHP, *PHP;
+    float *states, *u, *SA, *SB, *SV, *REC, *IHP, *PHP, *RAW;
 };
 
 meta_status map_status(cudaError_t e) { return e == cudaSuccess ? META_OK : META_ERR_CUDA; }
@@ -235,13 +264,14 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     c->SB = F(L.off_SB);
     c->SV = F(L.off_SV);
     c->REC = F(L.off_REC);
+    c->RAW = L.k ? F(L.off_RAW) : nullptr;
     c->IHP = F(L.off_IHP);
     c->PHP = F(L.off_PHP);
     make_taps(pr->sigma, &c->tx, &c->ts);
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
     const int LW = kTX + 2 * (c->tx.r4 + 8);
-    const int nst = 2 * B * (L.T + 1);
+    const int nst = 2 * B * L.nstate;
     bool ok = true;
     if (d == 2) {
         ok &= encode_map(&c->tmI, g, 2, c->states, nst, LW, kRows + 2, 1);
@@ -273,46 +303,106 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
         if (_s != META_OK) return _s;                   \
     } while (0)
 
-// Forward shooting t = 0..T-1 (the initial state is already in slot 0).
-meta_status run_forward(Ctx& c, const Coefs& cf) {
+// Forward step t: m = p grad I and the blur into u slot su, then the advect
+// from state slot sin to sout.
+meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int su,
+                         bool advect) {
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    META_TRY(cudaMemsetAsync(c.maxdisp, 0, sizeof(unsigned int) * kMaxdispStride * (size_t)L.T * B,
-                             c.st));
-    for (int t = 0; t < L.T; ++t) {
-        float* ut = c.u + (size_t)t * d * B * g.inst;
-        // m = p grad I, blurred along x  ->  SA
-        META_LAUNCH(META_K_XPASS_M, c.st,
-                    launch_xpass(d, true, c.tmI, c.tmP, c.tx, g, 2 * t * B, (2 * t + 1) * B, 0, 0,
-                                 c.SA, c.fault, c.st));
-        if (d == 2) {
-            META_LAUNCH(META_K_STRIDED_FWD, c.st,
-                        launch_strided(2, 0, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut,
-                                       c.fault, c.st));
-        } else {
-            META_LAUNCH(META_K_STRIDED_FWD, c.st,
-                        launch_strided(3, 1, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, c.SB,
-                                       c.fault, c.st));
-            META_LAUNCH(META_K_STRIDED_FWD, c.st,
-                        launch_strided(3, 0, c.tmSBz, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut,
-                                       c.fault, c.st));
-        }
-        META_LAUNCH(META_K_ADVECT, c.st, launch_advect(g, d, cf, t, c.states, c.u, c.maxdisp, c.st));
+    float* ut = c.u + (size_t)su * d * B * g.inst;
+    META_LAUNCH(META_K_XPASS_M, c.st,
+                launch_xpass(d, true, c.tmI, c.tmP, c.tx, g, 2 * sin * B, (2 * sin + 1) * B, 0, 0,
+                             c.SA, c.fault, c.st));
+    if (d == 2) {
+        META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                    launch_strided(2, 0, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut, c.fault,
+                                   c.st));
+    } else {
+        META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                    launch_strided(3, 1, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, c.SB,
+                                   c.fault, c.st));
+        META_LAUNCH(META_K_STRIDED_FWD, c.st,
+                    launch_strided(3, 0, c.tmSBz, c.ts, g, 0, 0, d * B, nullptr, 1.f, ut, c.fault,
+                                   c.st));
+    }
+    if (advect) {
+        Slots sl{};
+        sl.st = sin;
+        sl.st1 = sout;
+        sl.ut = su;
+        META_LAUNCH(META_K_ADVECT, c.st,
+                    launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.st));
     }
     return META_OK;
 }
 
+// Forward shooting t = 0..T-1 (the initial state is already in slot 0).
+meta_status run_forward(Ctx& c, const Coefs& cf) {
+    const Layout& L = c.L;
+    META_TRY(cudaMemsetAsync(c.maxdisp, 0,
+                             sizeof(unsigned int) * kMaxdispStride * (size_t)L.T * L.g.B, c.st));
+    for (int t = 0; t < L.T; ++t) {
+        const meta_status s = forward_step(c, cf, t, L.state_slot(t, L.seg_of(t)),
+                                           L.forward_out_slot(t), L.u_slot(t), true);
+        if (s != META_OK) return s;
+    }
+    return META_OK;
+}
+
+// Recomputes forward segment s from its checkpoint: the states and u of its
+// steps (the segment's last state is not needed by the adjoint).
+meta_status recompute_segment(Ctx& c, const Coefs& cf, int s) {
+    const Layout& L = c.L;
+    const int e = L.seg_end(s);
+    for (int t = s * L.k; t < e; ++t) {
+        const meta_status st = forward_step(c, cf, t, L.state_slot(t, s),
+                                            L.state_slot(t + 1, s), L.u_slot(t), t + 1 < e);
+        if (st != META_OK) return st;
+    }
+    return META_OK;
+}
+
+// Slots of the cost / adjoint start: records of step T-1, states T and 0, u_0.
+Slots start_slots(const Layout& L) {
+    Slots sl{};
+    sl.st1 = L.state_slot(L.T - 1, L.seg_of(L.T - 1));
+    sl.ut1 = L.u_slot(L.T - 1);
+    sl.s0 = 0;
+    sl.u0 = L.u_slot(0);
+    sl.sT = L.final_slot();
+    return sl;
+}
+
 // Reverse sweep; REC holds the records of step T-1 on entry (from the cost
 // kernel or the adjoint start).  mode 1: cost gradient into out0; mode 2:
-// shooting adjoint into out0 / gI0.
+// shooting adjoint into out0 / gI0.  With step checkpointing, each segment
+// but the last (still in place after the forward) is recomputed before its
+// steps; the adjoint of the segment's first step writes raw I^, p^ whose
+// record is built once the previous segment is back.
 meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
+    const int s_last = L.seg_of(L.T - 1);
+    float* rawI = c.RAW;
+    float* rawP = c.RAW ? c.RAW + (size_t)B * g.inst : nullptr;
     for (int t = L.T - 1; t >= 0; --t) {
+        const int s = L.seg_of(t);
+        if (L.k && s != s_last && t == L.seg_end(s) - 1) {
+            meta_status st = recompute_segment(c, cf, s);
+            if (st != META_OK) return st;
+            Slots rs{};
+            rs.st1 = L.state_slot(t, s);
+            rs.ut1 = L.u_slot(t);
+            META_LAUNCH(META_K_ADJ_INIT, c.st,
+                        launch_adj_records(g, d, cf, rs, c.states, c.u, rawI, rawP, c.REC, c.st));
+        }
+        Slots sl{};
+        sl.st = L.state_slot(t, s);
+        sl.u0 = L.u_slot(0);
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
-                    launch_adj_transport(g, d, cf, t, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
+                    launch_adj_transport(g, d, cf, t, sl, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
                                          c.PHP, c.fault, c.st));
         // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
@@ -333,10 +423,19 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
                                        c.fault, c.st));
             mh = c.SV;
         }
-        const int m = (t == 0) ? mode : 0;
+        int m;
+        if (t == 0) {
+            m = mode;
+        } else if (L.k && t == s * L.k) {
+            m = 3;  // step t-1 belongs to segment s-1, not recomputed yet
+        } else {
+            m = 0;
+            sl.st1 = L.state_slot(t - 1, s);
+            sl.ut1 = L.u_slot(t - 1);
+        }
         META_LAUNCH(META_K_ADJ_GRADP, c.st,
-                    launch_adj_gradp(g, d, cf, t, m, c.states, c.u, c.maxdisp, mh, c.IHP, c.PHP,
-                                     c.REC, out0, gI0, c.st));
+                    launch_adj_gradp(g, d, cf, t, m, sl, c.states, c.u, c.maxdisp, mh, c.IHP,
+                                     c.PHP, c.REC, rawI, rawP, out0, gI0, c.st));
     }
     return META_OK;
 }
@@ -370,7 +469,7 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     if (I1 || p1) {
-        const size_t slot = (size_t)c.L.T * 2 * g.B * g.inst;
+        const size_t slot = (size_t)c.L.final_slot() * 2 * g.B * g.inst;
         META_LAUNCH(META_K_UNPACK, c.st,
                     launch_unpack(g, c.L.ndim, c.states + slot,
                                   c.states + slot + (size_t)g.B * g.inst, I1, p1, c.st));
@@ -386,9 +485,15 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    // With checkpoints, an earlier adjoint left another segment in the segment
+    // slots: bring the last one back so that the adjoint can be called again.
+    if (c.L.k) {
+        s = recompute_segment(c, cf, c.L.seg_of(c.L.T - 1));
+        if (s != META_OK) return s;
+    }
     META_LAUNCH(META_K_ADJ_INIT, c.st,
-                launch_adj_init(c.L.g, c.L.ndim, cf, c.L.T, c.states, c.u, gI1, gp1, c.REC, c.IHP,
-                                c.PHP, c.st));
+                launch_adj_init(c.L.g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, gI1, gp1,
+                                c.REC, c.IHP, c.PHP, c.st));
     return run_adjoint(c, cf, 2, gp0, gI0);
 }
 
@@ -407,8 +512,8 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, c.L.T, c.states, c.u, J, c.REC, c.IHP, c.PHP,
-                            c.partials, c.L.nblk, cost, c.st));
+                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.REC, c.IHP,
+                            c.PHP, c.partials, c.L.nblk, cost, c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
 }

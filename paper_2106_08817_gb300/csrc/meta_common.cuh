@@ -53,6 +53,20 @@ struct Taps {
     float w[kMaxTaps];
 };
 
+// Slot indices of the times a launch touches.  A state slot holds one (I, p)
+// pair of the trajectory buffer (slices (2 slot + f) B + b), a u slot one u_t
+// (slices (slot d + a) B + b).  Keeping every state, slot = time; with step
+// checkpointing the host maps times onto checkpoint and segment slots.
+struct Slots {
+    int st;   // state of time t (input)
+    int st1;  // advect: state of t+1 (output); adjoint: state of the record's time
+    int ut;   // u of step t
+    int ut1;  // adjoint: u of the record's time
+    int s0;   // state of time 0
+    int u0;   // u of step 0
+    int sT;   // state of time T
+};
+
 // Per-launch scalars of the scheme.
 struct Coefs {
     const float* mu;      // [B]

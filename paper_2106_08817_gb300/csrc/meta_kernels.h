@@ -32,31 +32,42 @@ cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p
                         float* dstP, cudaStream_t st);
 cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const float* srcP,
                           float* I1, float* p1, cudaStream_t st);
-cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
-                          const float* u, unsigned int* maxdisp, cudaStream_t st);
+// Forward step t: reads state slot sl.st and u slot sl.ut, writes slot sl.st1.
+cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
+                          float* states, const float* u, unsigned int* maxdisp, cudaStream_t st);
 // Adjoint (meta_adjoint.cu).  `rec` holds the records of one adjoint step:
 // slice (k * B + b), k = 0 foot cell (int bits), 1..NDIM f per axis, NDIM+1
 // I^', NDIM+2 p~^, NDIM+3 div^.  Ihp / php: the S^T accumulators.
-// Eq. 4 partial sums, their reduction into cost[B][3], and the records of step
-// T-1 from I^_T = I_T - J, p^_T = 0.
-cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                        const float* u, const float* J, float* rec, float* Ihp, float* php,
-                        double* partials, int nblk, double* cost, cudaStream_t st);
+// Eq. 4 partial sums (states sl.sT, sl.s0, u sl.u0), their reduction into
+// cost[B][3], and the records of step T-1 (state sl.st1, u sl.ut1) from
+// I^_T = I_T - J, p^_T = 0.
+cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                        const float* states, const float* u, const float* J, float* rec,
+                        float* Ihp, float* php, double* partials, int nblk, double* cost,
+                        cudaStream_t st);
 // Records of step T-1 from given gradients gI1, gp1 (gp1 nullable: zero).
-cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, int T, const float* states,
-                            const float* u, const float* gI1, const float* gp1, float* rec,
-                            float* Ihp, float* php, cudaStream_t st);
-// S^T of I^' and p~^ into Ihp / php and v^ (d slices) into vh, for step t.
-cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
+cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* states, const float* u, const float* gI1,
+                            const float* gp1, float* rec, float* Ihp, float* php,
+                            cudaStream_t st);
+// Records of a step (state sl.st1, u sl.ut1) from pitched raw adjoints.
+cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                               const float* states, const float* u, const float* rawI,
+                               const float* rawP, float* rec, cudaStream_t st);
+// S^T of I^' and p~^ into Ihp / php and v^ (d slices) into vh, for step t
+// (state slot sl.st).
+cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                                  const float* states, const unsigned int* maxdisp,
                                  const float* rec, float* vh, float* Ihp, float* php,
                                  unsigned int* fault, cudaStream_t st);
-// I^_t, p^_t from Ihp / php and m^, then the records of step t-1 (t > 0) or
-// the outputs at t = 0: mode 1 cost gradient into grad (contiguous); mode 2
-// shooting adjoint into gp0 / gI0 (contiguous, gI0 nullable).
+// I^_t, p^_t from Ihp / php and m^ (state slot sl.st), then by mode: 0 the
+// records of step t-1 (state sl.st1, u sl.ut1); 3 raw I^_t, p^_t into rawI /
+// rawP; at t = 0, 1 the cost gradient (u sl.u0) and 2 the shooting adjoint,
+// into contiguous grad_or_gp0 / gI0 (gI0 nullable).
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
-                             const float* states, const float* u, const unsigned int* maxdisp,
-                             const float* mh, float* Ihp, float* php, float* rec,
-                             float* grad_or_gp0, float* gI0, cudaStream_t st);
+                             const Slots& sl, const float* states, const float* u,
+                             const unsigned int* maxdisp, const float* mh, float* Ihp, float* php,
+                             float* rec, float* rawI, float* rawP, float* grad_or_gp0,
+                             float* gI0, cudaStream_t st);
 
 }  // namespace meta

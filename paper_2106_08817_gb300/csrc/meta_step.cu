@@ -45,8 +45,8 @@ k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, flo
 constexpr int kAdvHalo = 4;
 
 __global__ void __launch_bounds__(kPX * kPY)
-k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
-           unsigned int* __restrict__ maxdisp) {
+k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
+           const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     constexpr int W = kPX + 2 * kAdvHalo;        // 40
@@ -55,10 +55,10 @@ k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __r
     __shared__ __align__(16) float sU0[HU * W], sU1[HU * W], sI[HI * W], sP[HI * W];
     const int b = blockIdx.z;
     const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
-    const float* u0 = slice_of(u, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* u1 = slice_of(u, g, ((long long)t * 2 + 1) * g.B + b);
-    const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+    const float* u0 = slice_of(u, g, ((long long)sl.ut * 2 + 0) * g.B + b);
+    const float* u1 = slice_of(u, g, ((long long)sl.ut * 2 + 1) * g.B + b);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     stage_async<W, HU>(sU0, u0, g, x0 - kAdvHalo, y0 - 1);
     stage_async<W, HU>(sU1, u1, g, x0 - kAdvHalo, y0 - 1);
     stage_async<W, HI>(sI, It, g, x0 - kAdvHalo, y0 - kAdvHalo);
@@ -90,8 +90,8 @@ k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __r
             pw = bilin(pt + o, g.P, fy.f, fx.f);
         }
         const int o = y * g.P + x;
-        float* I1 = slice_of(states, g, ((long long)(t + 1) * 2 + 0) * g.B + b);
-        float* p1 = slice_of(states, g, ((long long)(t + 1) * 2 + 1) * g.B + b);
+        float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+        float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
         p1[o] = pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
@@ -108,8 +108,8 @@ k_advect2d(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __r
 
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
-k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __restrict__ u,
-         unsigned int* __restrict__ maxdisp) {
+k_advect(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
+         const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
@@ -126,19 +126,19 @@ k_advect(Geom g, Coefs cf, int t, float* __restrict__ states, const float* __res
         float du = 0.f;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
-            const float* ua = slice_of(u, g, ((long long)t * NDIM + a) * g.B + b);
+            const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
             d[a] = disp_of(dtrho, ua[o]);
             du += cdiff(ua, o, s[a], c[a], n[a]);
             dmax = fmaxf(dmax, fabsf(d[a]));
         }
         const float div = -rho * du;  // div v, v = -rho u
         const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-        const float* It = slice_of(states, g, ((long long)t * 2 + 0) * g.B + b);
-        const float* pt = slice_of(states, g, ((long long)t * 2 + 1) * g.B + b);
+        const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+        const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
         const float Iw = interp<NDIM>(g, F, It);
         const float pw = interp<NDIM>(g, F, pt);
-        float* I1 = slice_of(states, g, ((long long)(t + 1) * 2 + 0) * g.B + b);
-        float* p1 = slice_of(states, g, ((long long)(t + 1) * 2 + 1) * g.B + b);
+        float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+        float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
         p1[o] = pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
@@ -178,14 +178,13 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
     return cudaGetLastError();
 }
 
-cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, float* states,
-                          const float* u, unsigned int* maxdisp, cudaStream_t st) {
+cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
+                          float* states, const float* u, unsigned int* maxdisp, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, 
-            g, c, t, states, u, maxdisp));
+        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, g, c, t, sl, states, u, maxdisp));
     else
-        META_CHECK_LAUNCH(launch_k(k_advect<3>, pgrid<3>(g), blk, 0, st, g, c, t, states, u, maxdisp));
+        META_CHECK_LAUNCH(launch_k(k_advect<3>, pgrid<3>(g), blk, 0, st, g, c, t, sl, states, u, maxdisp));
     return cudaGetLastError();
 }
 

@@ -67,6 +67,20 @@ def test_workspace_size_grows_with_T_and_batch(meta):
     assert fields * 64 * 64 * 4 <= a < (fields + 8) * 64 * 64 * 4
 
 
+def test_checkpointing_shrinks_the_workspace(meta):
+    """ckpt_stride k keeps ceil(T/k) checkpoints plus one segment instead of T+1 states."""
+    full = meta.workspace_size((64, 64, 64), 1, 20, 5.0)
+    k5 = meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=5)
+    f = 64 * 64 * 64 * 4
+    assert full >= (2 * 21 + 3 * 20) * f
+    assert k5 <= (2 * (4 + 5) + 3 * 6 + 4 * 3 + 8 + 1) * f
+    assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=1) == full
+    assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=20) == full
+    pr = meta._problem(3, (8, 8, 8), 1, 4, 1.0, -1)
+    n = ctypes.c_size_t(0)
+    assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == 1
+
+
 def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
     lib = meta._load()
     pr = meta._problem(2, (16, 16), 1, 4, 2.0)

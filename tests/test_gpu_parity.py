@@ -219,6 +219,35 @@ def test_group_plan_runs_mixed_shapes_in_one_graph(meta):
     assert rel_l2(it["grad"][0].cpu().numpy(), g_ref) <= GRAD_RTOL
 
 
+@pytest.mark.parametrize("dims,B,T,sigma,k", [((37, 141), 2, 7, 2.3, 2), ((37, 141), 2, 7, 2.3, 3),
+                                              ((64, 64), 1, 10, 3.0, 5), ((12, 10, 11), 2, 6, 1.5, 4),
+                                              ((70, 33), 1, 5, 3.0, 2)])
+def test_step_checkpointing_gives_identical_results(meta, dims, B, T, sigma, k):
+    """Keeping every k-th state and recomputing segments in the adjoint runs the same
+    kernels on the same values: cost, gradient and shooting adjoint bit for bit."""
+    I0, _ = phantoms.random_fields(101, B, dims)
+    J, _ = phantoms.random_fields(102, B, dims)
+    scale = 100.0 if dims == (70, 33) else 30.0  # the last case has 1-2 voxel steps (R = 2)
+    p0 = smooth_p(103, (B,) + dims, scale)
+    args = (T, sigma, [0.1, 0.0][:B], [1.0, 1.2][:B], [1e-2, 1e-3][:B])
+    c1, g1 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    c2, g2 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args, ckpt=k)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2) and torch.equal(g1, g2)
+    # the shooting map and its adjoint with checkpoints
+    r = np.random.default_rng(104)
+    gI1 = cuda(r.normal(size=(B,) + dims))
+    I1a, p1a, wa = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, args[2], args[3])
+    I1b, p1b, wb = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, args[2], args[3], ckpt=k)
+    assert torch.equal(I1a, I1b) and torch.equal(p1a, p1b)
+    ga = meta.shoot_adjoint(gI1, None, wa, T, sigma, args[2], args[3])
+    gb = meta.shoot_adjoint(gI1, None, wb, T, sigma, args[2], args[3])
+    assert torch.equal(ga[0], gb[0]) and torch.equal(ga[1], gb[1])
+    gc = meta.shoot_adjoint(gI1, None, wb, T, sigma, args[2], args[3])  # again, same trajectory
+    assert torch.equal(ga[0], gc[0]) and torch.equal(ga[1], gc[1])
+    assert wb.nbytes < wa.nbytes
+
+
 def test_results_are_deterministic(meta):
     w = phantoms.disk_pair_64()
     a = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
