@@ -21,6 +21,8 @@
 //       gradient adds lambda (2 sum_i (D_i I_0)(K m0)_i + 2 rho p0)).
 //
 // Each record is built once per voxel, so the transport only gathers.
+#include <cmath>
+
 #include "meta_stencil.cuh"
 
 namespace meta {
@@ -33,23 +35,22 @@ __device__ __forceinline__ int gather_radius(const unsigned int* maxdisp, int t,
     return 1 + (int)floorf(__uint_as_float(maxdisp[kMaxdispStride * ((long long)t * B + b)]));
 }
 
-// Largest window gathered; beyond it the transport scatters with atomics.
+// Node tile of the 2-D transport kernel and the largest window gathered;
+// beyond it the transport scatters with atomics.
 template <int NDIM>
-struct GatherTile;  // node tile of the transport kernel (256 nodes per CTA)
+struct GatherTile;
 template <>
 struct GatherTile<2> {
-    static constexpr int TX = 32, TY = 8, TZ = 1, RMAX = 8;
+    static constexpr int TX = 32, TY = 8, RMAX = 8;
 };
 template <>
 struct GatherTile<3> {
-    static constexpr int TX = 32, TY = 4, TZ = 2, RMAX = 2;  // a warp = one x row
+    static constexpr int RMAX = 2;  // nodes are marched along z (k_adj_transport3d)
 };
 
-template <int NDIM>
-dim3 gather_grid(const Geom& g) {
-    using G = GatherTile<NDIM>;
-    return dim3((g.nx + G::TX - 1) / G::TX,
-                ((g.ny + G::TY - 1) / G::TY) * ((g.nz + G::TZ - 1) / G::TZ), g.B);
+dim3 gather_grid2d(const Geom& g) {
+    using G = GatherTile<2>;
+    return dim3((g.nx + G::TX - 1) / G::TX, (g.ny + G::TY - 1) / G::TY, g.B);
 }
 
 // Foot cell relative to the source: one byte per axis (offset + 64), bit
@@ -268,6 +269,10 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
             const int cell = __float_as_int(sC[wi]);
             axis_weights(cell_off(cell, 0), sF0[wi], w);
             axis_weights(cell_off(cell, 1), sF1[wi], w + 3);
+        } else {
+            // pitch padding is never written: keep whatever it holds out of 0 * x
+            sI[wi] = 0.f;
+            sP[wi] = 0.f;
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) sW[k * NR + i] = w[k];
@@ -330,118 +335,30 @@ k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, rawI[ob], rawP[ob], states, u, rec);
 }
 
-// S^T and v^ of adjoint step t from the records of step t.
-//   R = 1 (every per-step displacement under one voxel): the records of the
-//     tile grown by one voxel become per-axis weights in shared memory and
-//     each node sums 3^d branch-free products (zero weights add exact zeros).
-//   1 < R <= RMAX: each node gathers over its (2R+1)^d window from the
-//     records in global memory (same order, same products).
-//   R > RMAX: each source scatters its 2^d corner terms with atomics into the
-//     zeroed Ihp / php (bounded work; summation order not fixed; info bit).
+// S^T and v^ of adjoint step t at one node v, from the records of step t in
+// global memory, for R > 1 (R = 1 has staged paths below).
+//   1 < R <= RMAX: the node gathers over its (2R+1)^d window in a fixed order.
+//   R > RMAX: the node's own source scatters its 2^d corner terms with
+//     atomics into the zeroed Ihp / php (bounded work; summation order not
+//     fixed; info bit).
 template <int NDIM>
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_transport(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states,
-                const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
-                float* vh, float* Ihp, float* php, unsigned int* fault) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    using G = GatherTile<NDIM>;
-    constexpr int RX = G::TX + 2, RY = G::TY + 2, RZ = (NDIM == 3) ? G::TZ + 2 : 1;
-    constexpr int NR = RX * RY * RZ;
-    // 2-D: sized for transport_r1_2d (8 staged windows of 40 x 10 + 6 x 340 weights)
-    constexpr int NRW = (NDIM == 2) ? (8 * 400 + 6 * 340 + 3 * NDIM - 1) / (3 * NDIM) : NR;
-    __shared__ __align__(16) float sW[3 * NDIM][NRW];
-    __shared__ float sI[NR], sP[NR];
-
-    const int b = blockIdx.z;
-    const int tid = threadIdx.y * kPX + threadIdx.x;
-    const int nty = (g.ny + G::TY - 1) / G::TY;
-    const int x0 = blockIdx.x * G::TX;
-    const int y0 = (blockIdx.y % nty) * G::TY;
-    const int z0 = (blockIdx.y / nty) * G::TZ;
-    Vox v;
-    v.b = b;
-    if constexpr (NDIM == 2) {
-        v.x = x0 + threadIdx.x;
-        v.y = y0 + threadIdx.y;
-        v.z = 0;
-    } else {
-        v.x = x0 + (tid & 31);
-        v.y = y0 + ((tid >> 5) & 3);
-        v.z = z0 + (tid >> 7);
-    }
-    v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
+__device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, const Slots& sl,
+                                               const float* __restrict__ states, int R,
+                                               const float* __restrict__ rec, float* vh,
+                                               float* Ihp, float* php, unsigned int* fault,
+                                               const Vox& v) {
+    const int b = v.b;
     const long long rsl = (long long)g.B * g.inst;
     const float* rb = rec + (long long)b * g.inst;  // record field k at rb + k * rsl
     const float* rI = rb + Rec<NDIM>::kI * rsl;
     const float* rP = rb + Rec<NDIM>::kP * rsl;
     const float* rD = rb + Rec<NDIM>::kD * rsl;
-    const int R = gather_radius(maxdisp, t, g.B, b);
     const long long o = gidx(g, v.z, v.y, v.x);
     int c[NDIM], n[NDIM];
     long long st[NDIM];
     axis_info<NDIM>(g, v, c, n, st);
-    float accI = 0.f, accP = 0.f;
-
-    if constexpr (NDIM == 2) {
-        if (R == 1) {  // uniform over the CTA
-            transport_r1_2d(g, cf.dt, rb, rsl,
-                            slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b),
-                            slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b),
-                            vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
-                            Ihp + (long long)b * g.inst, php + (long long)b * g.inst,
-                            &sW[0][0]);
-            return;
-        }
-    }
-    if (R == 1) {  // uniform over the CTA
-        for (int i = tid; i < NR; i += kPX * kPY) {
-            const int rz = i / (RX * RY), ry = (i / RX) % RY, rx = i % RX;
-            const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
-            const int sz = (NDIM == 3) ? z0 - 1 + rz : 0;
-            float w[3 * NDIM];
-#pragma unroll
-            for (int k = 0; k < 3 * NDIM; ++k) w[k] = 0.f;
-            float fI = 0.f, fP = 0.f;
-            if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
-                const long long so = gidx(g, sz, sy, sx);
-                const int cell = __float_as_int(__ldg(rb + so));
-#pragma unroll
-                for (int a = 0; a < NDIM; ++a)
-                    axis_weights(cell_off(cell, a), __ldg(rb + (1 + a) * rsl + so), w + 3 * a);
-                fI = __ldg(rI + so);
-                fP = __ldg(rP + so);
-            }
-#pragma unroll
-            for (int k = 0; k < 3 * NDIM; ++k) sW[k][i] = w[k];
-            sI[i] = fI;
-            sP[i] = fP;
-        }
-        __syncthreads();
-        if (!v.ok) return;
-        const int me = ((NDIM == 3 ? v.z - z0 + 1 : 0) * RY + (v.y - y0 + 1)) * RX + (v.x - x0 + 1);
-        // the source at offset e from the node passes weight w_a[1 - e_a] per axis
-#pragma unroll
-        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz) {
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int i = me + (dz * RY + dy) * RX + dx;
-                    float w;
-                    if constexpr (NDIM == 2)
-                        w = sW[1 - dy][i] * sW[3 + 1 - dx][i];
-                    else
-                        w = (sW[1 - dz][i] * sW[3 + 1 - dy][i]) * sW[6 + 1 - dx][i];
-                    accI += w * sI[i];
-                    accP += w * sP[i];
-                }
-            }
-        }
-        Ihp[(long long)b * g.inst + o] = accI;
-        php[(long long)b * g.inst + o] = accP;
-    } else if (R <= G::RMAX) {
-        if (!v.ok) return;
+    if (R <= GatherTile<NDIM>::RMAX) {
+        float accI = 0.f, accP = 0.f;
         int lo[NDIM], hi[NDIM];
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
@@ -477,8 +394,7 @@ k_adj_transport(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ sta
         Ihp[(long long)b * g.inst + o] = accI;
         php[(long long)b * g.inst + o] = accP;
     } else {
-        if (!v.ok) return;
-        if (tid == 0) atomicOr(fault, kInfoScatter);
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(fault, kInfoScatter);
         const int cell = __float_as_int(__ldg(rb + o));
         const float fI = __ldg(rI + o), fP = __ldg(rP + o);
         float f[NDIM];
@@ -532,6 +448,249 @@ k_adj_transport(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ sta
         const float yh = dI[a] * Ihv + dP[a] * pthv;
         vh[((long long)a * g.B + b) * g.inst + o] = -dt * yh + cdiff_T(rD, o, st[a], c[a], n[a]);
     }
+}
+
+// 2-D S^T and v^ of adjoint step t: transport_r1_2d when every per-step
+// displacement is under one voxel (R = 1), else transport_node per node.
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states,
+                  const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
+                  float* vh, float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    // 8 staged windows of 40 x 10 and 6 x 340 weights (transport_r1_2d)
+    __shared__ __align__(16) float s2[8 * 400 + 6 * 340];
+    using G = GatherTile<2>;
+    const int b = blockIdx.z;
+    const int R = gather_radius(maxdisp, t, g.B, b);
+    if (R == 1) {  // uniform over the CTA
+        const long long rsl = (long long)g.B * g.inst;
+        transport_r1_2d(g, cf.dt, rec + (long long)b * g.inst, rsl,
+                        slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b),
+                        slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b),
+                        vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
+                        Ihp + (long long)b * g.inst, php + (long long)b * g.inst, s2);
+        return;
+    }
+    Vox v;
+    v.b = b;
+    v.x = blockIdx.x * G::TX + threadIdx.x;
+    v.y = blockIdx.y * G::TY + threadIdx.y;
+    v.z = 0;
+    if (v.x >= g.nx || v.y >= g.ny) return;
+    transport_node<2>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+}
+
+// 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 8 column of nodes over
+// planes [zs, zs + zc) and marches along z.
+//   R = 1: plane p of the records (cell, f_z, f_y, f_x, I^', p~^, div^) and of
+//     I_t, p_t, grown by one voxel in x and y, is staged by cp.async into a
+//     ring of 4 plane slots (plane p + 1 loads while plane p is used).  Its
+//     sources are packed once into the float4 (g_z, g_y, g_x, I^') and p~^,
+//     where per axis g = f - 1 if the foot cell lies below the source (cell
+//     offset -1) and g = f otherwise.  The weight with which a source at
+//     offset e from a node passes its value along one axis is then max(g, 0)
+//     for e = -1, 1 - |g| for e = 0, max(-g, 0) for e = +1 (the bilinear
+//     weights f and 1 - f; 1 - |g| = f when the cell lies below holds up to
+//     one rounding).  Each thread reads the 9 sources of plane p around its
+//     column once and adds them to its running sums of nodes p+1, p, p-1
+//     (branch-free; zero weights add exact zeros); node p-1 is then complete
+//     and takes y^, D^T div^ from the staged planes p-2 .. p.  Every staged
+//     value is read from L2 about 1.6 times.
+//   R > 1: transport_node for each node of the column.
+constexpr int kMW = 40, kMHY = 10, kMPL = kMW * kMHY;   // staged plane window (x, y)
+constexpr int kMRX = 34, kMRY = 10, kMPR = kMRX * kMRY;  // source region of a plane
+constexpr int kMF = 9;                                   // staged fields per plane
+constexpr int kMChunks = kMF * kMHY * (kMW / 4);         // 16-byte copies per plane
+constexpr int kMPer = (kMChunks + kPX * kPY - 1) / (kPX * kPY);
+constexpr size_t kMarchSmem = (size_t)(4 * kMF * kMPL + 5 * kMPR) * sizeof(float);
+
+// Axis weight of a source at compile-time offset E from the node (see above).
+template <int E>
+__device__ __forceinline__ float gw(float g) {
+    if constexpr (E < 0) return fmaxf(g, 0.f);
+    else if constexpr (E > 0) return fmaxf(-g, 0.f);
+    else return 1.f - fabsf(g);
+}
+
+// Packs the sources of one staged plane at z (zero outside the domain).
+__device__ __forceinline__ void march_pack(const float* raw, float4* q, float* pp, const Geom& g,
+                                           int x0, int y0, int z) {
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    const bool zin = z >= 0 && z < g.nz;
+    for (int i = tid; i < kMPR; i += kPX * kPY) {
+        const int ry = i / kMRX, rx = i - ry * kMRX;
+        const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
+        const int wi = ry * kMW + rx + 3;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float pv = 0.f;
+        if (zin && sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
+            const int cell = __float_as_int(raw[wi]);
+            const float fz = raw[kMPL + wi], fy = raw[2 * kMPL + wi], fx = raw[3 * kMPL + wi];
+            v.x = cell_off(cell, 0) < 0 ? fz - 1.f : fz;
+            v.y = cell_off(cell, 1) < 0 ? fy - 1.f : fy;
+            v.z = cell_off(cell, 2) < 0 ? fx - 1.f : fx;
+            v.w = raw[4 * kMPL + wi];
+            pv = raw[5 * kMPL + wi];
+        }
+        q[i] = v;
+        pp[i] = pv;
+    }
+}
+
+__global__ void __launch_bounds__(kPX * kPY, 3)
+k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states,
+                  const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
+                  float* vh, float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    extern __shared__ __align__(16) float sm[];
+    const int b = blockIdx.z;
+    const int nxc = (g.nx + 31) / 32;
+    const int x0 = (blockIdx.x % nxc) * 32;
+    const int zs = (blockIdx.x / nxc) * zc;
+    const int ze = min(zs + zc, g.nz);
+    const int y0 = blockIdx.y * 8;
+    const int R = gather_radius(maxdisp, t, g.B, b);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kPX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool col_ok = x < g.nx && y < g.ny;
+    if (R != 1) {  // uniform over the CTA
+        if (!col_ok) return;
+        Vox v;
+        v.b = b;
+        v.x = x;
+        v.y = y;
+        for (int z = zs; z < ze; ++z) {
+            v.z = z;
+            transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+        }
+        return;
+    }
+    const long long rsl = (long long)g.B * g.inst;
+    const float* rb = rec + (long long)b * g.inst;
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    float* raw = sm;                                              // [4][kMF][kMPL]
+    float4* Q = reinterpret_cast<float4*>(sm + 4 * kMF * kMPL);  // [kMPR]
+    float* PP = sm + 4 * kMF * kMPL + 4 * kMPR;                   // [kMPR]
+    // ring slot of plane p: (p - zs + 1) & 3
+    auto rslot = [&](int p) { return raw + ((p - zs + 1) & 3) * (kMF * kMPL); };
+    // this thread's 16-byte copies of every plane: source (plane 0), slot offset
+    const float* csrc[kMPer];
+    int cdst[kMPer];
+    bool cok[kMPer];
+#pragma unroll
+    for (int j = 0; j < kMPer; ++j) {
+        const int i = tid + j * kPX * kPY;
+        const int k = i / (kMHY * (kMW / 4)), r = i - k * (kMHY * (kMW / 4));
+        const int row = r / (kMW / 4), c = r - row * (kMW / 4);
+        const int yy = y0 - 1 + row, xx = x0 - 4 + 4 * c;
+        const float* base = (k < 7) ? rb + k * rsl : (k == 7 ? It : pt);
+        cok[j] = i < kMChunks && yy >= 0 && yy < g.ny && xx >= 0 && xx < g.P;
+        csrc[j] = cok[j] ? base + (long long)yy * g.P + xx : base;
+        cdst[j] = (i < kMChunks) ? k * kMPL + row * kMW + 4 * c : -1;
+    }
+    auto load_plane = [&](int p) {
+        float* dst = rslot(p);
+        const bool zin = p >= 0 && p < g.nz;
+        const long long zo = zin ? (long long)p * g.slab : 0;
+#pragma unroll
+        for (int j = 0; j < kMPer; ++j)
+            if (cdst[j] >= 0) cp_async16(dst + cdst[j], csrc[j] + (cok[j] && zin ? zo : 0),
+                                         cok[j] && zin);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const float dt = cf.dt;
+    const int mw = (ty + 1) * kMW + tx + 4;   // window index of the node in a plane
+    const int me = (ty + 1) * kMRX + tx + 1;  // region index of the node in a plane
+    // running sums of S^T I^' and S^T p~^ at nodes p-1, p, p+1
+    float aIm = 0.f, aPm = 0.f, aI0 = 0.f, aP0 = 0.f, aIp = 0.f, aPp = 0.f;
+    load_plane(zs - 1);
+    for (int p = zs - 1; p <= ze; ++p) {
+        __syncthreads();  // every read of the slot of plane p-3 and of Q / PP is done
+        if (p + 1 <= ze) load_plane(p + 1);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane p landed
+        __syncthreads();
+        march_pack(rslot(p), Q, PP, g, x0, y0, p);
+        __syncthreads();
+        if (!col_ok) continue;
+        // plane p is at dz = -1 from node p+1, 0 from node p, +1 from node p-1
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int i = me + dy * kMRX + dx;
+                const float4 qv = Q[i];
+                float wy, wx;
+                if (dy < 0) wy = gw<-1>(qv.y); else if (dy > 0) wy = gw<1>(qv.y); else wy = gw<0>(qv.y);
+                if (dx < 0) wx = gw<-1>(qv.z); else if (dx > 0) wx = gw<1>(qv.z); else wx = gw<0>(qv.z);
+                const float wyx = wy * wx;
+                const float tI = wyx * qv.w, tP = wyx * PP[i];
+                const float wm = gw<1>(qv.x), w0 = gw<0>(qv.x), wp = gw<-1>(qv.x);
+                aIm += wm * tI;
+                aPm += wm * tP;
+                aI0 += w0 * tI;
+                aP0 += w0 * tP;
+                aIp += wp * tI;
+                aPp += wp * tP;
+            }
+        }
+        const int z = p - 1;  // complete: planes z-1 .. z+1 added
+        if (z >= zs) {
+            const long long o = gidx(g, z, y, x);
+            Ihp[(long long)b * g.inst + o] = aIm;
+            php[(long long)b * g.inst + o] = aPm;
+            // y^ from the node's own foot (cell within one voxel of the node)
+            const float* c0 = rslot(z);
+            const int cell = __float_as_int(c0[mw]);
+            const float fz = c0[kMPL + mw], fy = c0[2 * kMPL + mw], fx = c0[3 * kMPL + mw];
+            const int oz = cell_off(cell, 0);
+            const int ci = mw + cell_off(cell, 1) * kMW + cell_off(cell, 2);
+            const float* lo = rslot(z + oz);  // planes z + oz and z + oz + 1
+            const float* hi = rslot(z + oz + 1);
+            const bool inz = (cell >> 24) & 1, iny = (cell >> 25) & 1, inx = (cell >> 26) & 1;
+            float Iv, pv, dI[3], dP[3];
+            trilin_grad_pq(lo + 7 * kMPL + ci, hi + 7 * kMPL + ci, kMW, fz, fy, fx, inz, iny,
+                           inx, &Iv, dI);
+            trilin_grad_pq(lo + 8 * kMPL + ci, hi + 8 * kMPL + ci, kMW, fz, fy, fx, inz, iny,
+                           inx, &pv, dP);
+            const float Ihv = c0[4 * kMPL + mw], pthv = c0[5 * kMPL + mw];
+            const float* sD = c0 + 6 * kMPL;
+            float dT[3];
+            {  // (D^T div^) along z: the neighbouring planes' div^
+                float r = 0.f;
+                if (z >= 1) r += 0.5f * rslot(z - 1)[6 * kMPL + mw];
+                if (z == g.nz - 1) r += 0.5f * sD[mw];
+                if (z <= g.nz - 2) r -= 0.5f * rslot(z + 1)[6 * kMPL + mw];
+                if (z == 0) r -= 0.5f * sD[mw];
+                dT[0] = r;
+            }
+            const int c2[2] = {y, x}, n2[2] = {g.ny, g.nx}, s2[2] = {kMW, 1};
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                float r = 0.f;
+                if (c2[a] >= 1) r += 0.5f * sD[mw - s2[a]];
+                if (c2[a] == n2[a] - 1) r += 0.5f * sD[mw];
+                if (c2[a] <= n2[a] - 2) r -= 0.5f * sD[mw + s2[a]];
+                if (c2[a] == 0) r -= 0.5f * sD[mw];
+                dT[1 + a] = r;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                vh[((long long)a * g.B + b) * g.inst + o] =
+                    -dt * (dI[a] * Ihv + dP[a] * pthv) + dT[a];
+        }
+        aIm = aI0;
+        aPm = aP0;
+        aI0 = aIp;
+        aP0 = aPp;
+        aIp = 0.f;
+        aPp = 0.f;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Shared tail of the gradp kernels.  mode 0: the record of step t-1; mode 3:
@@ -758,17 +917,54 @@ cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Sl
     return cudaSuccess;
 }
 
+// Planes per CTA of the 3-D transport: the chunk that best trades the two
+// halo planes of each chunk against the fill of the last wave (3 CTAs of
+// kMarchSmem per SM).
+int march_chunk(const Geom& g) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm <= 0)
+            nsm = 152;
+    }
+    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.B;
+    const int cand[] = {4, 6, 8, 12, 16, 24, 32};
+    int best = 8;
+    double best_s = -1.0;
+    for (int zc : cand) {
+        const int nch = (g.nz + zc - 1) / zc;
+        const double waves = (double)(cols * nch) / (3.0 * nsm);
+        const double fill = waves / std::ceil(waves);
+        const double zr = (double)g.nz / nch;  // planes per chunk
+        const double s = fill * zr / (zr + 2.0);
+        if (s > best_s + 1e-9) {
+            best_s = s;
+            best = zc;
+        }
+    }
+    return best;
+}
+
 cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                                  const float* states, const unsigned int* maxdisp,
                                  const float* rec, float* vh, float* Ihp, float* php,
                                  unsigned int* fault, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
-    if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_adj_transport<2>, gather_grid<2>(g), blk, 0, st, g, c, t, sl,
+    if (ndim == 2) {
+        META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, 0, st, g, c, t, sl,
                                    states, maxdisp, rec, vh, Ihp, php, fault));
-    else
-        META_CHECK_LAUNCH(launch_k(k_adj_transport<3>, gather_grid<3>(g), blk, 0, st, g, c, t, sl,
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_adj_transport3d,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMarchSmem);
+        if (e != cudaSuccess) return e;
+        const int zc = march_chunk(g);
+        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
+        META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, g, c, t, sl, zc,
                                    states, maxdisp, rec, vh, Ihp, php, fault));
+    }
     return cudaSuccess;
 }
 

@@ -270,7 +270,7 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     make_taps(pr->sigma, &c->tx, &c->ts);
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    const int LW = kTX + 2 * (c->tx.r4 + 8);
+    const int LW = xpass_lw(c->tx.r4);
     const int nst = 2 * B * L.nstate;
     bool ok = true;
     if (d == 2) {

@@ -32,7 +32,7 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     float* base = reinterpret_cast<float*>(smem_raw + 128);
 
     const int HX = taps.r4 + 8;       // x halo (multiple of 4)
-    const int LW = kTX + 2 * HX;      // staged row length
+    const int LW = xpass_lw(taps.r4); // staged row length
     const int rowsI = (NDIM == 2) ? (kRows + 2) : 36;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTX;
@@ -68,8 +68,11 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
             tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)blockIdx.z);
         }
     }
-    // every thread waits (bounded); the CTA leaves together if any wait ran out
-    if (__syncthreads_or(!mbar_wait_bounded(bar, 0, fault))) return;
+    // warp 0 waits (bounded) while the others sleep in the barrier; the CTA
+    // leaves together if the wait ran out
+    bool landed = true;
+    if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
+    if (__syncthreads_or(!landed)) return;
 
     const int ncomp = GRADP ? NDIM : 1;
     if constexpr (GRADP) {
@@ -114,8 +117,10 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     }
 
     // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`.
-    const int tx = tid & 15;
-    const int row = tid >> 4;
+    // Lanes alternate between two rows, so a quarter-warp's 16-byte loads
+    // cover 4 columns of each row (odd row stride in 16-byte units).
+    const int tx = (tid >> 1) & 15;
+    const int row = ((tid >> 5) << 1) | (tid & 1);
     const int ty = (NDIM == 2) ? row : (row & 3);
     const int tz = (NDIM == 2) ? 0 : (row >> 2);
     const int y = y0 + ty, z = z0 + tz;
@@ -219,8 +224,11 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
         else
             tma_load_4d(s, &tm, bar, x0, y, a0 - taps.r, in_slice0 + slice);
     }
-    // every thread waits (bounded); the CTA leaves together if any wait ran out
-    if (__syncthreads_or(!mbar_wait_bounded(bar, 0, fault))) return;
+    // warp 0 waits (bounded) while the others sleep in the barrier; the CTA
+    // leaves together if the wait ran out
+    bool landed = true;
+    if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
+    if (__syncthreads_or(!landed)) return;
 
     const float* src = s + (ta * kBA) * kTXS + tx;
     float acc[kBA];
@@ -279,7 +287,7 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
 // ------------------------------------------------------------ launchers
 
 size_t xpass_smem(int ndim, bool gradp, int r4) {
-    const int LW = kTX + 2 * (r4 + 8);
+    const int LW = xpass_lw(r4);
     if (!gradp) return 128 + (size_t)kRows * LW * 4;
     const int rowsI = ndim == 2 ? kRows + 2 : 36;
     const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)((kRows * LW + 31) & ~31) +

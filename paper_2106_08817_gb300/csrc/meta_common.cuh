@@ -20,6 +20,14 @@ constexpr int kBA = 16;        // strided pass: outputs per thread along the axi
 constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 
+// Staged row length of the x pass for halo r4 (+ 8 alignment columns per
+// side): kTX + 2 (r4 + 8), plus 4 pad columns where the TMA box allows, so
+// that the row stride in 16-byte units is odd and the two rows a quarter-warp
+// reads hit all eight 16-byte bank groups.
+__host__ __device__ constexpr int xpass_lw(int r4) {
+    return kTX + 2 * (r4 + 8) + ((kTX + 2 * (r4 + 8) + 4 <= 256) ? 4 : 0);
+}
+
 // The max displacement of step t, instance b lives at maxdisp[kMaxdispStride *
 // (t * B + b)]: one 128-byte line per slot, so that the per-CTA atomics of
 // different instances do not queue on one L2 line.
@@ -127,14 +135,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// One try_wait; the thread may be suspended for up to 100 us (suspend-time
+// hint) while the phase is still pending, so waiting warps take few issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
         : "memory");
     return ok != 0;
 }
@@ -154,7 +164,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0; it < (1u << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u && globaltimer_ns() - t0 > 2000000000ull) break;
+        if ((it & 15u) == 15u && globaltimer_ns() - t0 > 2000000000ull) break;
     }
     atomicOr(fault, kFaultTmaTimeout);
     return false;

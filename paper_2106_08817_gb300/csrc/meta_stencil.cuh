@@ -83,6 +83,23 @@ __device__ __forceinline__ void stage_async(float* dst, const float* __restrict_
     }
 }
 
+// 3-D form: the box z in [zlo, zlo + HZ), y in [ylo, ylo + HY), x in
+// [xlo, xlo + W) of one pitched 3-D slice, stored [HZ][HY][W].
+template <int W, int HY, int HZ>
+__device__ __forceinline__ void stage_async3(float* dst, const float* __restrict__ src,
+                                             const Geom& g, int xlo, int ylo, int zlo) {
+    constexpr int NC4 = W / 4;
+    const int tid = threadIdx.y * kPX + threadIdx.x;
+    for (int i = tid; i < HZ * HY * NC4; i += kPX * kPY) {
+        const int r = i / NC4, c = i - r * NC4;
+        const int zz = r / HY, yy = r - zz * HY;
+        const int z = zlo + zz, y = ylo + yy, x = xlo + 4 * c;
+        const bool ok = (z >= 0 && z < g.nz && y >= 0 && y < g.ny && x >= 0 && x < g.P);
+        cp_async16(dst + r * W + 4 * c,
+                   ok ? src + (long long)z * g.slab + (long long)y * g.P + x : src, ok);
+    }
+}
+
 // Bilinear value (and derivatives) at lower corner p[0] with row stride W;
 // the same expressions as interp / interp_grad below.
 __device__ __forceinline__ float bilin(const float* p, int W, float fy, float fx) {
@@ -121,6 +138,47 @@ __device__ __forceinline__ Feet<NDIM> feet_of(const Geom& g, const Vox& v, const
     return F;
 }
 
+// Trilinear value at lower corner p[0] with row stride P and plane stride S
+// (global or shared memory); the same expressions everywhere.
+template <typename I>
+__device__ __forceinline__ float trilin(const float* p, I P, I S, float fz, float fy, float fx) {
+    const float a0 = (1.f - fx) * p[0] + fx * p[1];
+    const float a1 = (1.f - fx) * p[P] + fx * p[P + 1];
+    const float a2 = (1.f - fx) * p[S] + fx * p[S + 1];
+    const float a3 = (1.f - fx) * p[S + P] + fx * p[S + P + 1];
+    const float b0 = (1.f - fy) * a0 + fy * a1;
+    const float b1 = (1.f - fy) * a2 + fy * a3;
+    return (1.f - fz) * b0 + fz * b1;
+}
+
+// Trilinear value and its derivatives along z, y, x (zero where the clamp on
+// that axis is active), with the lower z plane at p and the upper at q.
+template <typename I>
+__device__ __forceinline__ void trilin_grad_pq(const float* p, const float* q, I P, float fz,
+                                               float fy, float fx, bool inz, bool iny, bool inx,
+                                               float* val, float* dv) {
+    const float c000 = p[0], c001 = p[1], c010 = p[P], c011 = p[P + 1];
+    const float c100 = q[0], c101 = q[1], c110 = q[P], c111 = q[P + 1];
+    const float a0 = (1.f - fx) * c000 + fx * c001;
+    const float a1 = (1.f - fx) * c010 + fx * c011;
+    const float a2 = (1.f - fx) * c100 + fx * c101;
+    const float a3 = (1.f - fx) * c110 + fx * c111;
+    const float b0 = (1.f - fy) * a0 + fy * a1;
+    const float b1 = (1.f - fy) * a2 + fy * a3;
+    *val = (1.f - fz) * b0 + fz * b1;
+    dv[0] = inz ? (b1 - b0) : 0.f;
+    dv[1] = iny ? ((1.f - fz) * (a1 - a0) + fz * (a3 - a2)) : 0.f;
+    const float e0 = (1.f - fy) * (c001 - c000) + fy * (c011 - c010);
+    const float e1 = (1.f - fy) * (c101 - c100) + fy * (c111 - c110);
+    dv[2] = inx ? ((1.f - fz) * e0 + fz * e1) : 0.f;
+}
+template <typename I>
+__device__ __forceinline__ void trilin_grad(const float* p, I P, I S, float fz, float fy,
+                                            float fx, bool inz, bool iny, bool inx, float* val,
+                                            float* dv) {
+    trilin_grad_pq<I>(p, p + S, P, fz, fy, fx, inz, iny, inx, val, dv);
+}
+
 // Multilinear interpolant of `f` at the feet.
 template <int NDIM>
 __device__ __forceinline__ float interp(const Geom& g, const Feet<NDIM>& F, const float* f) {
@@ -131,15 +189,7 @@ __device__ __forceinline__ float interp(const Geom& g, const Feet<NDIM>& F, cons
         const float b = (1.f - fx) * p[g.P] + fx * p[g.P + 1];
         return (1.f - fy) * a + fy * b;
     } else {
-        const float fz = F.f[0].f, fy = F.f[1].f, fx = F.f[2].f;
-        const long long S = g.slab, P = g.P;
-        const float a0 = (1.f - fx) * p[0] + fx * p[1];
-        const float a1 = (1.f - fx) * p[P] + fx * p[P + 1];
-        const float a2 = (1.f - fx) * p[S] + fx * p[S + 1];
-        const float a3 = (1.f - fx) * p[S + P] + fx * p[S + P + 1];
-        const float b0 = (1.f - fy) * a0 + fy * a1;
-        const float b1 = (1.f - fy) * a2 + fy * a3;
-        return (1.f - fz) * b0 + fz * b1;
+        return trilin<long long>(p, g.P, g.slab, F.f[0].f, F.f[1].f, F.f[2].f);
     }
 }
 
@@ -157,22 +207,8 @@ __device__ __forceinline__ void interp_grad(const Geom& g, const Feet<NDIM>& F, 
         dv[0] = F.f[0].inside ? (b - a) : 0.f;
         dv[1] = F.f[1].inside ? ((1.f - fy) * (c01 - c00) + fy * (c11 - c10)) : 0.f;
     } else {
-        const float fz = F.f[0].f, fy = F.f[1].f, fx = F.f[2].f;
-        const long long S = g.slab, P = g.P;
-        const float c000 = p[0], c001 = p[1], c010 = p[P], c011 = p[P + 1];
-        const float c100 = p[S], c101 = p[S + 1], c110 = p[S + P], c111 = p[S + P + 1];
-        const float a0 = (1.f - fx) * c000 + fx * c001;
-        const float a1 = (1.f - fx) * c010 + fx * c011;
-        const float a2 = (1.f - fx) * c100 + fx * c101;
-        const float a3 = (1.f - fx) * c110 + fx * c111;
-        const float b0 = (1.f - fy) * a0 + fy * a1;
-        const float b1 = (1.f - fy) * a2 + fy * a3;
-        *val = (1.f - fz) * b0 + fz * b1;
-        dv[0] = F.f[0].inside ? (b1 - b0) : 0.f;
-        dv[1] = F.f[1].inside ? ((1.f - fz) * (a1 - a0) + fz * (a3 - a2)) : 0.f;
-        const float e0 = (1.f - fy) * (c001 - c000) + fy * (c011 - c010);
-        const float e1 = (1.f - fy) * (c101 - c100) + fy * (c111 - c110);
-        dv[2] = F.f[2].inside ? ((1.f - fz) * e0 + fz * e1) : 0.f;
+        trilin_grad<long long>(p, g.P, g.slab, F.f[0].f, F.f[1].f, F.f[2].f, F.f[0].inside,
+                               F.f[1].inside, F.f[2].inside, val, dv);
     }
 }
 

@@ -248,6 +248,29 @@ def test_step_checkpointing_gives_identical_results(meta, dims, B, T, sigma, k):
     assert wb.nbytes < wa.nbytes
 
 
+@pytest.mark.parametrize("dims,B,T,sigma,k,scale", [((37, 141), 2, 5, 2.3, 0, 30.0),
+                                                    ((70, 33), 1, 5, 3.0, 2, 100.0),
+                                                    ((12, 10, 11), 2, 4, 1.5, 0, 30.0),
+                                                    ((13, 9, 22), 1, 6, 1.5, 3, 30.0)])
+def test_workspace_contents_do_not_matter(meta, dims, B, T, sigma, k, scale):
+    """Only the first 16 bytes of a workspace need zeroing: one whose other bytes
+    are all 0xFF (NaN as floats) gives the same results bit for bit, so nothing
+    reads memory (pitch padding included) before the library wrote it."""
+    I0, _ = phantoms.random_fields(111, B, dims)
+    J, _ = phantoms.random_fields(112, B, dims)
+    p0 = smooth_p(113, (B,) + dims, scale)
+    args = (T, sigma, [0.1, 0.0][:B], [1.0, 1.2][:B], [1e-2, 1e-3][:B])
+    w0 = meta.Workspace(dims, B, T, sigma, "cuda", k)
+    wn = meta.Workspace(dims, B, T, sigma, "cuda", k)
+    wn.buf.fill_(255)
+    wn.buf[:16].zero_()
+    c0, g0 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args, workspace=w0, ckpt=k)
+    cn, gn = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args, workspace=wn, ckpt=k)
+    torch.cuda.synchronize()
+    assert torch.isfinite(g0).all()
+    assert torch.equal(c0, cn) and torch.equal(g0, gn)
+
+
 def test_results_are_deterministic(meta):
     w = phantoms.disk_pair_64()
     a = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
