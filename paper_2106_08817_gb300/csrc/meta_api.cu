@@ -88,6 +88,9 @@ Layout make_layout(const meta_problem* pr) {
     g.slab = (long long)g.ny * g.P;
     g.inst = (long long)g.nz * g.slab;
     g.B = pr->batch;
+    g.txw = even_tile(g.nx, kTX, kBX);
+    g.ly = even_tile(g.ny, kTA, kBA);
+    g.lz = d == 3 ? even_tile(g.nz, kTA, kBA) : kBA;
     // a stride of 0, 1 or >= T keeps every state
     L.k = (pr->ckpt_stride > 1 && pr->ckpt_stride < pr->T) ? pr->ckpt_stride : 0;
     L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
@@ -270,20 +273,20 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     make_taps(pr->sigma, &c->tx, &c->ts);
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    const int LW = xpass_lw(c->tx.r4);
+    const int LW = xpass_lw(g.txw, c->tx.r4);
     const int nst = 2 * B * L.nstate;
     bool ok = true;
     if (d == 2) {
         ok &= encode_map(&c->tmI, g, 2, c->states, nst, LW, kRows + 2, 1);
         ok &= encode_map(&c->tmP, g, 2, c->states, nst, LW, kRows, 1);
-        ok &= encode_map(&c->tmSAy, g, 2, c->SA, d * B, kTXS, kTA + c->ts.kp, 1);
+        ok &= encode_map(&c->tmSAy, g, 2, c->SA, d * B, kTXS, g.ly + c->ts.kp, 1);
         ok &= encode_map(&c->tmSVx, g, 2, c->SV, d * B, LW, kRows, 1);
         c->tmSBz = c->tmSAy;
     } else {
         ok &= encode_map(&c->tmI, g, 3, c->states, nst, LW, 6, 6);
         ok &= encode_map(&c->tmP, g, 3, c->states, nst, LW, 4, 4);
-        ok &= encode_map(&c->tmSAy, g, 3, c->SA, d * B, kTXS, kTA + c->ts.kp, 1);
-        ok &= encode_map(&c->tmSBz, g, 3, c->SB, d * B, kTXS, 1, kTA + c->ts.kp);
+        ok &= encode_map(&c->tmSAy, g, 3, c->SA, d * B, kTXS, g.ly + c->ts.kp, 1);
+        ok &= encode_map(&c->tmSBz, g, 3, c->SB, d * B, kTXS, 1, g.lz + c->ts.kp);
         ok &= encode_map(&c->tmSVx, g, 3, c->SV, d * B, LW, 4, 4);
     }
     return ok ? META_OK : META_ERR_UNSUPPORTED;

@@ -31,11 +31,11 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
 
-    const int HX = taps.r4 + 8;       // x halo (multiple of 4)
-    const int LW = xpass_lw(taps.r4); // staged row length
+    const int HX = taps.r4 + 8;              // x halo (multiple of 4)
+    const int LW = xpass_lw(g.txw, taps.r4); // staged row length
     const int rowsI = (NDIM == 2) ? (kRows + 2) : 36;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTX;
+    const int x0 = blockIdx.x * g.txw;
     int y0, z0;
     if constexpr (NDIM == 2) {
         y0 = blockIdx.y * kRows;
@@ -116,11 +116,19 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
         __syncthreads();
     }
 
-    // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`.
-    // Lanes alternate between two rows, so a quarter-warp's 16-byte loads
-    // cover 4 columns of each row (odd row stride in 16-byte units).
-    const int tx = (tid >> 1) & 15;
-    const int row = ((tid >> 5) << 1) | (tid & 1);
+    // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`,
+    // g.txw / 8 threads per row.  With 16 per row, lanes alternate between
+    // two rows, so a quarter-warp's 16-byte loads cover 4 columns of each row
+    // (odd row stride in 16-byte units).
+    const int tpr = g.txw / kBX;
+    int tx, row;
+    if (tpr == 16) {
+        tx = (tid >> 1) & 15;
+        row = ((tid >> 5) << 1) | (tid & 1);
+    } else {
+        row = tid / tpr;
+        tx = tid - row * tpr;
+    }
     const int ty = (NDIM == 2) ? row : (row & 3);
     const int tz = (NDIM == 2) ? 0 : (row >> 2);
     const int y = y0 + ty, z = z0 + tz;
@@ -191,21 +199,25 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     const int x0 = blockIdx.x * kTXS;
     const int slice = blockIdx.z;           // comp * B + b
     const int b = slice % g.B;
-    int a0, y, z, n_axis;
+    // tile of L = g.ly or g.lz outputs along the axis, L / kBA warps
+    int a0, y, z, n_axis, L;
     if constexpr (NDIM == 2) {
-        a0 = blockIdx.y * kTA;
+        L = g.ly;
+        a0 = blockIdx.y * L;
         y = 0;
         z = 0;
         n_axis = g.ny;
     } else if constexpr (AXIS == 1) {
-        const int nt = (g.ny + kTA - 1) / kTA;
-        a0 = (blockIdx.y % nt) * kTA;
+        L = g.ly;
+        const int nt = (g.ny + L - 1) / L;
+        a0 = (blockIdx.y % nt) * L;
         z = blockIdx.y / nt;
         y = 0;
         n_axis = g.ny;
     } else {
-        const int nt = (g.nz + kTA - 1) / kTA;
-        a0 = (blockIdx.y % nt) * kTA;
+        L = g.lz;
+        const int nt = (g.nz + L - 1) / L;
+        a0 = (blockIdx.y % nt) * L;
         y = blockIdx.y / nt;
         z = 0;
         n_axis = g.nz;
@@ -216,7 +228,7 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     }
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)(kTXS * (kTA + taps.kp) * 4));
+        mbar_arrive_expect_tx(bar, (uint32_t)(kTXS * (L + taps.kp) * 4));
         if constexpr (NDIM == 2)
             tma_load_3d(s, &tm, bar, x0, a0 - taps.r, in_slice0 + slice);
         else if constexpr (AXIS == 1)
@@ -286,8 +298,8 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
 
 // ------------------------------------------------------------ launchers
 
-size_t xpass_smem(int ndim, bool gradp, int r4) {
-    const int LW = xpass_lw(r4);
+size_t xpass_smem(int ndim, bool gradp, int txw, int r4) {
+    const int LW = xpass_lw(txw, r4);
     if (!gradp) return 128 + (size_t)kRows * LW * 4;
     const int rowsI = ndim == 2 ? kRows + 2 : 36;
     const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)((kRows * LW + 31) & ~31) +
@@ -295,21 +307,22 @@ size_t xpass_smem(int ndim, bool gradp, int r4) {
     return 128 + f * 4;
 }
 
-size_t strided_smem(int kp) { return 128 + (size_t)kTXS * (kTA + kp) * 4; }
+size_t strided_smem(int len, int kp) { return 128 + (size_t)kTXS * (len + kp) * 4; }
 
 template <int NDIM, bool GRADP, int KC>
 static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tmP,
                                    const Taps& taps, const Geom& g, int sliceI, int sliceP,
                                    int out_slice0, int nslices, float* out, unsigned int* fault,
                                    cudaStream_t st) {
-    const size_t smem = xpass_smem(NDIM, GRADP, taps.r4);
+    const size_t smem = xpass_smem(NDIM, GRADP, g.txw, taps.r4);
     cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + kTX - 1) / kTX,
+    dim3 grid((g.nx + g.txw - 1) / g.txw,
               NDIM == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
               GRADP ? g.B : nslices);
-    META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP, KC>, grid, 256, smem, st, tmI, tmP, taps, g,
+    const int threads = g.txw / kBX * kRows;
+    META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP, KC>, grid, threads, smem, st, tmI, tmP, taps, g,
                                sliceI, sliceP, out_slice0, out, fault));
     return cudaSuccess;
 }
@@ -357,19 +370,20 @@ static cudaError_t launch_strided_kc(const CUtensorMap& tm, const Taps& taps, co
                                      int in_slice0, int out_slice0, int nslices,
                                      const float* scale, float scale_mul, float* out,
                                      unsigned int* fault, cudaStream_t st) {
-    const size_t smem = strided_smem(taps.kp);
+    const int L = (NDIM == 3 && AXIS == 0) ? g.lz : g.ly;
+    const size_t smem = strided_smem(L, taps.kp);
     cudaError_t e = cudaFuncSetAttribute(k_strided<NDIM, AXIS, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned gy;
     if (NDIM == 2)
-        gy = (g.ny + kTA - 1) / kTA;
+        gy = (g.ny + L - 1) / L;
     else if (AXIS == 1)
-        gy = ((g.ny + kTA - 1) / kTA) * g.nz;
+        gy = ((g.ny + L - 1) / L) * g.nz;
     else
-        gy = ((g.nz + kTA - 1) / kTA) * g.ny;
+        gy = ((g.nz + L - 1) / L) * g.ny;
     dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
-    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, 256, smem, st, tm, taps, g,
+    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, L / kBA * 32, smem, st, tm, taps, g,
                                in_slice0, out_slice0, scale, scale_mul, out, fault));
     return cudaSuccess;
 }

@@ -14,18 +14,27 @@ namespace meta {
 constexpr int kMaxTaps = 128;  // padded tap table length (r <= 54)
 constexpr int kMaxR = 54;      // sigma <= 18
 constexpr int kBX = 8;         // x-pass: outputs per thread along x
-constexpr int kTX = 128;       // x-pass: outputs per CTA along x
+constexpr int kTX = 128;       // x-pass: largest tile width along x
 constexpr int kRows = 16;      // x-pass: rows per CTA (2-D: 16 y; 3-D: 4 z x 4 y)
 constexpr int kBA = 16;        // strided pass: outputs per thread along the axis
-constexpr int kTA = 128;       // strided pass: outputs per CTA along the axis
+constexpr int kTA = 128;       // strided pass: largest tile length along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 
-// Staged row length of the x pass for halo r4 (+ 8 alignment columns per
-// side): kTX + 2 (r4 + 8), plus 4 pad columns where the TMA box allows, so
-// that the row stride in 16-byte units is odd and the two rows a quarter-warp
-// reads hit all eight 16-byte bank groups.
-__host__ __device__ constexpr int xpass_lw(int r4) {
-    return kTX + 2 * (r4 + 8) + ((kTX + 2 * (r4 + 8) + 4 <= 256) ? 4 : 0);
+// Tiles of a blur pass split an extent n into ceil(n / maxlen) equal tiles,
+// each rounded up to a multiple of q, so that no CTA carries a mostly empty
+// tail tile (160 = 2 x 80 rather than 128 + 32).
+inline int even_tile(int n, int maxlen, int q) {
+    const int nt = (n + maxlen - 1) / maxlen;
+    const int l = (n + nt - 1) / nt;
+    return (l + q - 1) / q * q;
+}
+
+// Staged row length of the x pass for tile width txw and halo r4 (+ 8
+// alignment columns per side): txw + 2 (r4 + 8), plus 4 pad columns where the
+// TMA box allows, so that the row stride in 16-byte units is odd and two rows
+// read by one quarter-warp hit all eight 16-byte bank groups.
+__host__ __device__ constexpr int xpass_lw(int txw, int r4) {
+    return txw + 2 * (r4 + 8) + ((txw + 2 * (r4 + 8) + 4 <= 256) ? 4 : 0);
 }
 
 // The max displacement of step t, instance b lives at maxdisp[kMaxdispStride *
@@ -47,6 +56,8 @@ struct Geom {
     long long slab;   // ny * P
     long long inst;   // nz * ny * P  (floats per instance slice)
     int B;            // batch
+    int txw;          // x-pass tile width (multiple of kBX, <= kTX)
+    int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTA)
 };
 
 __host__ __device__ inline long long gidx(const Geom& g, int z, int y, int x) {

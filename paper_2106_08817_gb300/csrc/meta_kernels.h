@@ -6,8 +6,8 @@
 namespace meta {
 
 // Blur passes (meta_blur.cu).
-size_t xpass_smem(int ndim, bool gradp, int r4);
-size_t strided_smem(int kp);
+size_t xpass_smem(int ndim, bool gradp, int txw, int r4);
+size_t strided_smem(int len, int kp);
 
 // x-pass.  gradp: reads I slice (sliceI + b) with a one-voxel y/z halo and p
 // slice (sliceP + b) through tmI / tmP, writes NDIM component slices
