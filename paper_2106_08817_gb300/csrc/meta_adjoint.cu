@@ -21,8 +21,6 @@
 //       gradient adds lambda (2 sum_i (D_i I_0)(K m0)_i + 2 rho p0)).
 //
 // Each record is built once per voxel, so the transport only gathers.
-#include <cmath>
-
 #include "meta_stencil.cuh"
 
 namespace meta {
@@ -917,36 +915,6 @@ cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Sl
     return cudaSuccess;
 }
 
-// Planes per CTA of the 3-D transport: the chunk that best trades the two
-// halo planes of each chunk against the fill of the last wave (3 CTAs of
-// kMarchSmem per SM).
-int march_chunk(const Geom& g) {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            nsm <= 0)
-            nsm = 152;
-    }
-    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.B;
-    const int cand[] = {4, 6, 8, 12, 16, 24, 32};
-    int best = 8;
-    double best_s = -1.0;
-    for (int zc : cand) {
-        const int nch = (g.nz + zc - 1) / zc;
-        const double waves = (double)(cols * nch) / (3.0 * nsm);
-        const double fill = waves / std::ceil(waves);
-        const double zr = (double)g.nz / nch;  // planes per chunk
-        const double s = fill * zr / (zr + 2.0);
-        if (s > best_s + 1e-9) {
-            best_s = s;
-            best = zc;
-        }
-    }
-    return best;
-}
-
 cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                                  const float* states, const unsigned int* maxdisp,
                                  const float* rec, float* vh, float* Ihp, float* php,
@@ -960,7 +928,7 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = march_chunk(g);
+        const int zc = march_chunk(g, 3, 2);
         const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
         META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, g, c, t, sl, zc,
                                    states, maxdisp, rec, vh, Ihp, php, fault));

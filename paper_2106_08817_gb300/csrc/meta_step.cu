@@ -1,7 +1,7 @@
 // meta_step.cu -- the forward semi-Lagrangian step (arXiv:2106.08817, Eq. 3
 // integrated as in Sec. 2.3), sm_103a.  After the blur passes have produced
 // u_t = K(p_t grad I_t) (v_t = -rho u_t):
-//   k_advect / k_advect2d  div v, foot y = x - dt v, bi/trilinear gathers of
+//   k_advect2d / k_advect3d  div v, foot y = x - dt v, bi/trilinear gathers of
 //       I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~, and
 //       the per-instance max displacement (the window of the adjoint).
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
@@ -106,52 +106,142 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
         atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
 
-template <int NDIM>
+// 3-D advect: a CTA owns a 32 x 8 column over planes [zs, zs + zc) and
+// marches along z.  Plane p of u (three components, one-voxel y halo) and of
+// I_t, p_t (two-voxel y halo), all with x in [x0 - 4, x0 + 36), is staged by
+// cp.async into a ring of 6 plane slots (plane z + 3 loads while plane z is
+// computed from planes z-2 .. z+2).  Feet whose cell leaves the staged planes
+// read global memory.
+constexpr int kAW = 40, kAUR = 10, kAIR = 12;          // window width, u rows, I/p rows
+constexpr int kAUS = kAW * kAUR, kAIS = kAW * kAIR;    // floats per staged field plane
+constexpr int kASlot = 3 * kAUS + 2 * kAIS;            // floats per ring slot
+constexpr int kAChunks = (3 * kAUR + 2 * kAIR) * (kAW / 4);
+constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
+constexpr size_t kAdvMarchSmem = (size_t)6 * kASlot * sizeof(float);
+
 __global__ void __launch_bounds__(kPX * kPY)
-k_advect(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
-         const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
+k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states,
+           const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    const Vox v = vox_of<NDIM>(g);
-    float dmax = 0.f;
-    if (v.ok) {
-        const int b = v.b;
-        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-        const float dtrho = dt * rho;
-        const long long o = gidx(g, v.z, v.y, v.x);
-        int c[NDIM], n[NDIM];
-        long long s[NDIM];
-        axis_info<NDIM>(g, v, c, n, s);
-        float d[NDIM];
-        float du = 0.f;
+    extern __shared__ __align__(16) float sm[];
+    const int b = blockIdx.z;
+    const int nxc = (g.nx + 31) / 32;
+    const int x0 = (blockIdx.x % nxc) * 32;
+    const int zs = (blockIdx.x / nxc) * zc;
+    const int ze = min(zs + zc, g.nz);
+    const int y0 = blockIdx.y * 8;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kPX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool col_ok = x < g.nx && y < g.ny;
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+    float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+    const float* ua[3];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
-            d[a] = disp_of(dtrho, ua[o]);
-            du += cdiff(ua, o, s[a], c[a], n[a]);
-            dmax = fmaxf(dmax, fabsf(d[a]));
+    for (int a = 0; a < 3; ++a) ua[a] = slice_of(u, g, ((long long)sl.ut * 3 + a) * g.B + b);
+    // ring slot of plane p: (p - zs + 2) % 6; slot = u0 u1 u2 [kAUR rows], I p [kAIR rows]
+    auto slot = [&](int p) { return sm + ((p - zs + 2) % 6) * kASlot; };
+    // this thread's 16-byte copies of every plane: source (plane 0), slot offset
+    const float* csrc[kAPer];
+    int cdst[kAPer];
+    bool cok[kAPer];
+#pragma unroll
+    for (int j = 0; j < kAPer; ++j) {
+        const int i = tid + j * kPX * kPY;
+        const int r = i / (kAW / 4), c = i - r * (kAW / 4);  // staged row, chunk
+        const float* base;
+        int yy, dst;
+        if (r < 3 * kAUR) {
+            const int a = r / kAUR, row = r - a * kAUR;
+            base = a == 0 ? ua[0] : (a == 1 ? ua[1] : ua[2]);
+            yy = y0 - 1 + row;
+            dst = a * kAUS + row * kAW + 4 * c;
+        } else {
+            const int f = (r - 3 * kAUR) / kAIR, row = (r - 3 * kAUR) - f * kAIR;
+            base = f == 0 ? It : pt;
+            yy = y0 - 2 + row;
+            dst = 3 * kAUS + f * kAIS + row * kAW + 4 * c;
         }
+        const int xx = x0 - 4 + 4 * c;
+        cok[j] = i < kAChunks && yy >= 0 && yy < g.ny && xx >= 0 && xx < g.P;
+        csrc[j] = cok[j] ? base + (long long)yy * g.P + xx : base;
+        cdst[j] = i < kAChunks ? dst : -1;
+    }
+    auto load_plane = [&](int p) {
+        float* d = slot(p);
+        const bool zin = p >= 0 && p < g.nz;
+        const long long zo = zin ? (long long)p * g.slab : 0;
+#pragma unroll
+        for (int j = 0; j < kAPer; ++j)
+            if (cdst[j] >= 0) cp_async16(d + cdst[j], csrc[j] + (cok[j] && zin ? zo : 0),
+                                         cok[j] && zin);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const float dtrho = dt * rho;
+    const int ui = (ty + 1) * kAW + tx + 4;  // node in a u plane
+    float dmax = 0.f;
+    for (int p = zs - 2; p <= zs + 2; ++p) load_plane(p);
+    for (int z = zs; z < ze; ++z) {
+        __syncthreads();  // every read of the slot of plane z-3 is done
+        if (z + 3 <= ze + 1) load_plane(z + 3);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+2 landed
+        __syncthreads();
+        if (!col_ok) continue;
+        const float* s0 = slot(z);
+        const float* sm1 = slot(z - 1);
+        const float* sp1 = slot(z + 1);
+        float d[3];
+        float du = 0.f;
+        {  // axis 0 (z): neighbouring planes
+            d[0] = disp_of(dtrho, s0[ui]);
+            const float hi = (z < g.nz - 1) ? sp1[ui] : s0[ui];
+            const float lo = (z > 0) ? sm1[ui] : s0[ui];
+            du += 0.5f * (hi - lo);
+        }
+        {  // axis 1 (y)
+            const float* u1 = s0 + kAUS;
+            d[1] = disp_of(dtrho, u1[ui]);
+            du += 0.5f * (u1[ui + (y < g.ny - 1 ? kAW : 0)] - u1[ui - (y > 0 ? kAW : 0)]);
+        }
+        {  // axis 2 (x)
+            const float* u2 = s0 + 2 * kAUS;
+            d[2] = disp_of(dtrho, u2[ui]);
+            du += 0.5f * (u2[ui + (x < g.nx - 1 ? 1 : 0)] - u2[ui - (x > 0 ? 1 : 0)]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
         const float div = -rho * du;  // div v, v = -rho u
-        const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-        const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
-        const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
-        const float Iw = interp<NDIM>(g, F, It);
-        const float pw = interp<NDIM>(g, F, pt);
-        float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
-        float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+        const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
+        const int kz = fz.i0 - (z - 2), ky = fy.i0 - (y0 - 2), kx = fx.i0 - (x0 - 4);
+        float Iw, pw;
+        if (kz >= 0 && kz + 1 < 5 && ky >= 0 && ky + 1 < kAIR && kx >= 0 && kx + 1 < kAW) {
+            const float* lo = slot(fz.i0) + 3 * kAUS + ky * kAW + kx;
+            const float* hi = slot(fz.i0 + 1) + 3 * kAUS + ky * kAW + kx;
+            Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
+            pw = trilin_pq<int>(lo + kAIS, hi + kAIS, kAW, fz.f, fy.f, fx.f);
+        } else {
+            const long long gi = gidx(g, fz.i0, fy.i0, fx.i0);
+            Iw = trilin<long long>(It + gi, g.P, g.slab, fz.f, fy.f, fx.f);
+            pw = trilin<long long>(pt + gi, g.P, g.slab, fz.f, fy.f, fx.f);
+        }
+        const long long o = gidx(g, z, y, x);
         p1[o] = pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
-    // per-instance max |displacement| (non-negative floats order like their bits),
-    // one atomic per CTA
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
     __shared__ unsigned int s_m;
-    if (threadIdx.x == 0 && threadIdx.y == 0) s_m = 0u;
+    if (tid == 0) s_m = 0u;
     __syncthreads();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
-    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
     __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0 && s_m != 0u)
-        atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + blockIdx.z), s_m);
+    if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
 
 }  // namespace
@@ -184,7 +274,15 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, g, c, t, sl, states, u, maxdisp));
     else
-        META_CHECK_LAUNCH(launch_k(k_advect<3>, pgrid<3>(g), blk, 0, st, g, c, t, sl, states, u, maxdisp));
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_advect3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kAdvMarchSmem);
+        if (e != cudaSuccess) return e;
+        const int zc = march_chunk(g, 4, 4);
+        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
+        META_CHECK_LAUNCH(launch_k(k_advect3d, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc,
+                                   states, u, maxdisp));
+    }
     return cudaGetLastError();
 }
 
