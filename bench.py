@@ -35,6 +35,31 @@ UNIT = "voxel-steps/s"
 
 # Algorithmic HBM bytes per voxel of one launch of each kernel class (FP32):
 # what the kernel must read and write once, halos and gathers not counted.
+# Bytes per voxel-step of the whole path (forward + adjoint, FP32): the fixed
+# model of the method's data movement (forward 24 + 8d^2, adjoint 48 + 12d + 8d^2,
+# plus a recomputed forward with v stored, F + 4d): 224 B in 2-D, 360 B in 3-D.
+def model_bytes_per_voxel_step(d: int) -> int:
+    F = 24 + 8 * d * d
+    A = 48 + 12 * d + 8 * d * d
+    return 2 * F + 4 * d + A
+
+
+# This implementation's own algorithmic bytes per voxel-step: one forward step
+# (xpass_m, d-1 strided passes, advect) and one adjoint step (transport,
+# xpass_adj, d-1 strided passes, gradp); with checkpoint stride k, the forward
+# steps recomputed in the adjoint (all but the last segment) on top.
+def own_bytes_per_voxel_step(d: int, T: int, k: int) -> float:
+    fwd = (bytes_per_voxel("xpass_m", d) + (d - 1) * bytes_per_voxel("strided_fwd", d)
+           + bytes_per_voxel("advect", d))
+    adj = (bytes_per_voxel("adj_gather", d) + bytes_per_voxel("xpass_adj", d)
+           + (d - 1) * bytes_per_voxel("strided_adj", d) + bytes_per_voxel("adj_gradp", d))
+    rec = 0.0
+    if 1 < k < T:
+        last = T - (T - 1) // k * k  # steps of the last segment (not recomputed)
+        rec = (T - last) / T * fwd
+    return fwd + adj + rec
+
+
 def bytes_per_voxel(kclass: str, d: int) -> int:
     return {
         "pack": 16,
@@ -280,6 +305,12 @@ def run_ours(args):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     I0, J, p0 = t(w.I0), t(w.J), t(w.p0)
     mu, rho, lam = t(w.mu), t(w.rho), t(w.lam)
+    # tile shapes: the autotuner times the call on these inputs (before the plan
+    # records them; outside every timed region)
+    if args.no_autotune:
+        tiles = meta.tuning(w.dims, B, w.sigma)
+    else:
+        tiles = meta.autotune(I0, J, p0, T, w.sigma, mu, rho, lam, ckpt=args.ckpt)
     # the call recorded once into a CUDA graph (meta_plan_*); inputs updated in place
     plan = meta.CostAndGradPlan(I0, J, p0, T, w.sigma, mu, rho, lam, ckpt=args.ckpt)
     I0, J, p0, cost, grad, ws = plan.I0, plan.J, plan.p0, plan.cost, plan.grad, plan.ws
@@ -409,7 +440,16 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), ckpt_stride=args.ckpt,
-                           workspace_bytes=ws.nbytes),
+                           workspace_bytes=ws.nbytes, tiles=tiles,
+                           autotuned=not args.no_autotune),
+            "path_roofline": {
+                "model_bytes_per_voxel_step": model_bytes_per_voxel_step(d),
+                "model_GBps": value * model_bytes_per_voxel_step(d) / 1e9,
+                "model_frac": value * model_bytes_per_voxel_step(d) / 1e9 / peak,
+                "own_bytes_per_voxel_step": own_bytes_per_voxel_step(d, T, args.ckpt),
+                "own_GBps": value * own_bytes_per_voxel_step(d, T, args.ckpt) / 1e9,
+                "own_frac": value * own_bytes_per_voxel_step(d, T, args.ckpt) / 1e9 / peak,
+                "peak_GBps": peak},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src
@@ -515,6 +555,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in tile shapes instead of the autotuner's")
     ap.add_argument("--ckpt", type=int, default=0,
                     help="step checkpoint stride (0: keep the whole trajectory)")
     args = ap.parse_args()

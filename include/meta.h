@@ -168,12 +168,48 @@ meta_status meta_cost_and_grad_noalloc(const meta_problem* prob, const float* I0
                                        const float* lambda, double* cost, float* grad,
                                        void* stream);
 
+/* Tile shapes of the kernels for one problem shape (ndim, dims, batch,
+ * sigma): planes per CTA of the 3-D kernels that march along z (adjoint
+ * transport, advect), tile lengths of the strided blur passes along y and z,
+ * and the tile width of the x pass.  0 in a field means the built-in choice
+ * (extents split into equal tiles of at most 128; a wave-fill heuristic for
+ * the plane chunks). */
+typedef struct {
+    int zc_transport; /* 3-D only; in [1, dims[0]] */
+    int zc_advect;    /* 3-D only; in [1, dims[0]] */
+    int ly;           /* multiple of 16 in [16, 128] */
+    int lz;           /* 3-D only; multiple of 16 in [16, 128] */
+    int txw;          /* multiple of 8 in [8, 128] */
+} meta_tuning;
+
+/* Autotuner: times meta_cost_and_grad on these inputs (same arguments) for
+ * candidate tile shapes, one field at a time in the order above, keeps the
+ * fastest of each, and records the result for the problem shape in a
+ * process-wide table that every later call (and meta_plan_create) with that
+ * shape uses.  Results do not depend on the tile shapes beyond summation
+ * order.  Blocking: synchronises `stream` (not capturable); overwrites cost and
+ * grad; `out` (may be NULL) receives the choice. */
+meta_status meta_autotune(const meta_problem* prob, const float* I0, const float* J,
+                          const float* p0, const float* mu, const float* rho, const float* lambda,
+                          double* cost, float* grad, void* ws, size_t ws_bytes, void* stream,
+                          meta_tuning* out);
+
+/* The tile shapes a call with this problem uses (tuned, set, or built-in,
+ * with 0 fields resolved). */
+meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out);
+
+/* Records tile shapes for the problem shape (tun == NULL: forget them).
+ * META_ERR_INVALID_ARG if a field is out of its range or a resulting grid
+ * exceeds the launch limits. */
+meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun);
+
 /* Device-side status word latched in ws since it was last cleared.  Bit 0: a
  * bounded TMA wait ran out (the call's results are invalid; returns
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step
- * displacements beyond the deterministic gather window (8 voxels in 2-D, 3 in
- * 3-D) and transposed the interpolation by an atomic scatter instead, so its
- * summation order is not fixed.  Synchronises `stream`.  clear != 0 resets it. */
+ * displacements beyond the deterministic gather window (8 voxels or more in
+ * 2-D, 2 or more in 3-D) and transposed the interpolation by an atomic scatter
+ * instead, so its summation order is not fixed.  Synchronises `stream`.
+ * clear != 0 resets it. */
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
                                   unsigned int* fault_bits);
 

@@ -51,6 +51,11 @@ class _Problem(ctypes.Structure):
                 ("T", ctypes.c_int), ("sigma", ctypes.c_float), ("ckpt_stride", ctypes.c_int)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("zc_transport", ctypes.c_int), ("zc_advect", ctypes.c_int), ("ly", ctypes.c_int),
+                ("lz", ctypes.c_int), ("txw", ctypes.c_int)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -88,6 +93,12 @@ def _load():
         lib.meta_timer_start.argtypes = [ctypes.c_int]
         lib.meta_timer_stop.argtypes = [ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int)]
+        T = ctypes.POINTER(_Tuning)
+        lib.meta_autotune.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V, T]
+        lib.meta_tuning_get.argtypes = [P, T]
+        lib.meta_tuning_set.argtypes = [P, T]
+        for f in ("meta_autotune", "meta_tuning_get", "meta_tuning_set"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.meta_kernel_name.argtypes = [ctypes.c_int]
         lib.meta_kernel_name.restype = ctypes.c_char_p
         for f in ("meta_workspace_size", "meta_shoot_forward", "meta_shoot_adjoint",
@@ -275,6 +286,53 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     if sq and grad is not None and out is None:
         grad = grad[0]
     return cost, grad
+
+
+TUNING_FIELDS = ("zc_transport", "zc_advect", "ly", "lz", "txw")
+
+
+def tuning(dims: Sequence[int], batch: int, sigma: float) -> dict:
+    """Tile shapes that calls with this problem shape use (tuned, set or built-in)."""
+    t = _Tuning()
+    rc = _load().meta_tuning_get(ctypes.byref(_problem(len(dims), dims, batch, 1, sigma)),
+                                 ctypes.byref(t))
+    if rc:
+        raise MetaError(rc, "meta_tuning_get")
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+
+def set_tuning(dims: Sequence[int], batch: int, sigma: float, tun: Optional[dict]) -> None:
+    """Records tile shapes for the problem shape (None: back to the built-in choice)."""
+    pr = _problem(len(dims), dims, batch, 1, sigma)
+    if tun is None:
+        rc = _load().meta_tuning_set(ctypes.byref(pr), None)
+    else:
+        t = _Tuning(*[int(tun.get(f, 0)) for f in TUNING_FIELDS])
+        rc = _load().meta_tuning_set(ctypes.byref(pr), ctypes.byref(t))
+    if rc:
+        raise MetaError(rc, "meta_tuning_set")
+
+
+def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu,
+             rho=1.0, lam=1e-3, ndim: Optional[int] = None, ckpt: int = 0) -> dict:
+    """Times cost_and_grad on these inputs for candidate tile shapes (meta_autotune),
+    records the fastest for the problem shape and returns it.  Blocking."""
+    I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
+    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
+    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    B, dev = I0b.shape[0], I0b.device
+    ws = _workspace(dims, B, T, sigma, dev, None, ckpt)
+    mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
+    cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
+    grad = torch.empty_like(I0b)
+    t = _Tuning()
+    rc = _load().meta_autotune(ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt)), _p(I0b),
+                               _p(Jb), _p(p0b), _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
+                               _p(grad), ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev),
+                               ctypes.byref(t))
+    if rc:
+        raise MetaError(rc, "meta_autotune")
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
 
 
 class CostAndGradPlan:

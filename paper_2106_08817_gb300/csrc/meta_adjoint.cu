@@ -928,7 +928,7 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = march_chunk(g, 3, 2);
+        const int zc = g.zct > 0 ? g.zct : march_chunk(g, 3, 2);
         const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
         META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, g, c, t, sl, zc,
                                    states, maxdisp, rec, vh, Ihp, php, fault));

@@ -4,6 +4,7 @@
 // Eq. 3-4 and Sec. 2.3).  Host code only; it never allocates device memory.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -11,10 +12,33 @@
 #include "meta.h"
 #include "meta_kernels.h"
 
+#include <map>
+#include <tuple>
+
 namespace meta {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// Process-wide tile shapes per problem shape (meta_autotune / meta_tuning_set).
+using TuneKey = std::tuple<int, int, int, int, int, uint32_t>;
+std::mutex g_tune_mu;
+std::map<TuneKey, meta_tuning> g_tune;
+
+TuneKey tune_key(const meta_problem* pr) {
+    uint32_t sb;
+    std::memcpy(&sb, &pr->sigma, 4);
+    return TuneKey(pr->ndim, pr->dims[0], pr->ndim == 3 ? pr->dims[1] : 0,
+                   pr->dims[pr->ndim - 1], pr->batch, sb);
+}
+
+bool find_tuning(const meta_problem* pr, meta_tuning* t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(pr));
+    if (it == g_tune.end()) return false;
+    *t = it->second;
+    return true;
+}
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -91,6 +115,17 @@ Layout make_layout(const meta_problem* pr) {
     g.txw = even_tile(g.nx, kTX, kBX);
     g.ly = even_tile(g.ny, kTA, kBA);
     g.lz = d == 3 ? even_tile(g.nz, kTA, kBA) : kBA;
+    g.zct = g.zca = 0;
+    meta_tuning tn;
+    if (find_tuning(pr, &tn)) {
+        if (tn.txw > 0) g.txw = tn.txw;
+        if (tn.ly > 0) g.ly = tn.ly;
+        if (d == 3 && tn.lz > 0) g.lz = tn.lz;
+        if (d == 3) {
+            g.zct = tn.zc_transport;
+            g.zca = tn.zc_advect;
+        }
+    }
     // a stride of 0, 1 or >= T keeps every state
     L.k = (pr->ckpt_stride > 1 && pr->ckpt_stride < pr->T) ? pr->ckpt_stride : 0;
     L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
@@ -449,6 +484,136 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
 using namespace meta;
 
 extern "C" {
+
+meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
+    const meta_status s = validate(prob);
+    if (s != META_OK) return s;
+    if (!tun) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.erase(tune_key(prob));
+        return META_OK;
+    }
+    const int d = prob->ndim;
+    const int nz = d == 3 ? prob->dims[0] : 1, ny = prob->dims[d - 2];
+    auto len_ok = [](int v, int q) { return v == 0 || (v >= q && v <= 128 && v % q == 0); };
+    if (!len_ok(tun->ly, kBA) || !len_ok(tun->lz, kBA) || !len_ok(tun->txw, kBX))
+        return META_ERR_INVALID_ARG;
+    if (tun->zc_transport < 0 || tun->zc_transport > nz || tun->zc_advect < 0 ||
+        tun->zc_advect > nz)
+        return META_ERR_INVALID_ARG;
+    if (d == 2 && (tun->lz != 0 || tun->zc_transport != 0 || tun->zc_advect != 0))
+        return META_ERR_INVALID_ARG;
+    // grid limits of the strided passes (y: tiles * nz, z: tiles * ny)
+    if (tun->ly && (long long)((ny + tun->ly - 1) / tun->ly) * nz > 65535)
+        return META_ERR_INVALID_ARG;
+    if (tun->lz && (long long)((nz + tun->lz - 1) / tun->lz) * ny > 65535)
+        return META_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(prob)] = *tun;
+    return META_OK;
+}
+
+meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
+    if (!out) return META_ERR_INVALID_ARG;
+    const meta_status s = validate(prob);
+    if (s != META_OK) return s;
+    const Layout L = make_layout(prob);
+    out->ly = L.g.ly;
+    out->txw = L.g.txw;
+    if (L.ndim == 3) {
+        out->lz = L.g.lz;
+        out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 3, 2);
+        out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 4, 4);
+    } else {
+        out->lz = out->zc_transport = out->zc_advect = 0;
+    }
+    return META_OK;
+}
+
+meta_status meta_autotune(const meta_problem* prob, const float* I0, const float* J,
+                          const float* p0, const float* mu, const float* rho, const float* lambda,
+                          double* cost, float* grad, void* ws, size_t ws_bytes, void* stream,
+                          meta_tuning* out) {
+    meta_status s = validate(prob);
+    if (s != META_OK) return s;
+    meta_tuning cur;
+    s = meta_tuning_get(prob, &cur);
+    if (s != META_OK) return s;
+    const int d = prob->ndim;
+    const int nz = d == 3 ? prob->dims[0] : 1, ny = prob->dims[d - 2], nx = prob->dims[d - 1];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return META_ERR_CUDA;
+    }
+    // one warm-up, then the best of three timed calls
+    auto time_it = [&](float* ms) -> meta_status {
+        meta_status r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws,
+                                           ws_bytes, stream);
+        if (r != META_OK) return r;
+        float best = 1e30f;
+        for (int k = 0; k < 3; ++k) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return META_ERR_CUDA;
+            r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes,
+                                   stream);
+            if (r != META_OK) return r;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return META_ERR_CUDA;
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return META_ERR_CUDA;
+            best = t < best ? t : best;
+        }
+        *ms = best;
+        return META_OK;
+    };
+    auto lens = [](int n, int q) {  // equal tiles of at most 48 .. 128
+        std::vector<int> v;
+        for (int m : {48, 64, 96, 128}) {
+            const int l = even_tile(n, m, q);
+            if (l <= 128 && std::find(v.begin(), v.end(), l) == v.end()) v.push_back(l);
+        }
+        return v;
+    };
+    std::vector<std::pair<int*, std::vector<int>>> params;
+    if (d == 3) {
+        std::vector<int> zs;
+        for (int z : {2, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+            if (z <= nz) zs.push_back(z);
+        params.push_back({&cur.zc_transport, zs});
+        params.push_back({&cur.zc_advect, zs});
+        params.push_back({&cur.lz, lens(nz, kBA)});
+    }
+    params.push_back({&cur.ly, lens(ny, kBA)});
+    params.push_back({&cur.txw, lens(nx, kBX)});
+    meta_status res = META_OK;
+    for (auto& pv : params) {
+        int best_v = *pv.first;
+        float best_ms = 1e30f;
+        for (int v : pv.second) {
+            *pv.first = v;
+            if (meta_tuning_set(prob, &cur) != META_OK) continue;  // over a launch limit
+            float ms = 0.f;
+            res = time_it(&ms);
+            if (res != META_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+            }
+        }
+        *pv.first = best_v;
+        if (res != META_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res != META_OK) {
+        meta_tuning_set(prob, nullptr);
+        return res;
+    }
+    res = meta_tuning_set(prob, &cur);
+    if (res == META_OK && out) *out = cur;
+    return res;
+}
 
 meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes) {
     if (!bytes) return META_ERR_INVALID_ARG;

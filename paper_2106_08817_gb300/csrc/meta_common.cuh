@@ -3,6 +3,8 @@
 // inline PTX, the relative-coordinate foot computation and the workspace map.
 #pragma once
 
+#include <cmath>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -58,7 +60,38 @@ struct Geom {
     int B;            // batch
     int txw;          // x-pass tile width (multiple of kBX, <= kTX)
     int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTA)
+    int zct, zca;     // planes per CTA of the 3-D transport / advect (0: heuristic)
 };
+
+// Planes per CTA of a kernel that marches along z over 32 x 8 columns: the
+// chunk that best trades the `halo` extra planes each chunk stages against
+// the fill of the last wave (ctas_per_sm resident CTAs per SM).
+inline int march_chunk(const Geom& g, int ctas_per_sm, int halo) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm <= 0)
+            nsm = 152;
+    }
+    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.B;
+    const int cand[] = {4, 6, 8, 12, 16, 24, 32};
+    int best = 8;
+    double best_s = -1.0;
+    for (int zc : cand) {
+        const int nch = (g.nz + zc - 1) / zc;
+        const double waves = (double)(cols * nch) / ((double)ctas_per_sm * nsm);
+        const double fill = waves / std::ceil(waves);
+        const double zr = (double)g.nz / nch;  // planes per chunk
+        const double s = fill * zr / (zr + halo);
+        if (s > best_s + 1e-9) {
+            best_s = s;
+            best = zc;
+        }
+    }
+    return best;
+}
 
 __host__ __device__ inline long long gidx(const Geom& g, int z, int y, int x) {
     return (long long)z * g.slab + (long long)y * g.P + x;

@@ -4,8 +4,6 @@
 // its derivatives.
 #pragma once
 
-#include <cmath>
-
 #include "meta_kernels.h"
 
 namespace meta {
@@ -165,36 +163,6 @@ __device__ __forceinline__ float trilin_pq(const float* p, const float* q, I P, 
     const float b0 = (1.f - fy) * a0 + fy * a1;
     const float b1 = (1.f - fy) * a2 + fy * a3;
     return (1.f - fz) * b0 + fz * b1;
-}
-
-// Planes per CTA of a kernel that marches along z over 32 x 8 columns: the
-// chunk that best trades the `halo` extra planes each chunk stages against
-// the fill of the last wave (ctas_per_sm resident CTAs per SM).
-inline int march_chunk(const Geom& g, int ctas_per_sm, int halo) {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            nsm <= 0)
-            nsm = 152;
-    }
-    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.B;
-    const int cand[] = {4, 6, 8, 12, 16, 24, 32};
-    int best = 8;
-    double best_s = -1.0;
-    for (int zc : cand) {
-        const int nch = (g.nz + zc - 1) / zc;
-        const double waves = (double)(cols * nch) / ((double)ctas_per_sm * nsm);
-        const double fill = waves / std::ceil(waves);
-        const double zr = (double)g.nz / nch;  // planes per chunk
-        const double s = fill * zr / (zr + halo);
-        if (s > best_s + 1e-9) {
-            best_s = s;
-            best = zc;
-        }
-    }
-    return best;
 }
 
 // Trilinear value and its derivatives along z, y, x (zero where the clamp on

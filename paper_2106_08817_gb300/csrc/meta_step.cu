@@ -192,9 +192,11 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+2 landed
         __syncthreads();
         if (!col_ok) continue;
-        const float* s0 = slot(z);
+        const float* sm2 = slot(z - 2);
         const float* sm1 = slot(z - 1);
+        const float* s0 = slot(z);
         const float* sp1 = slot(z + 1);
+        const float* sp2 = slot(z + 2);
         float d[3];
         float du = 0.f;
         {  // axis 0 (z): neighbouring planes
@@ -220,8 +222,11 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
         const int kz = fz.i0 - (z - 2), ky = fy.i0 - (y0 - 2), kx = fx.i0 - (x0 - 4);
         float Iw, pw;
         if (kz >= 0 && kz + 1 < 5 && ky >= 0 && ky + 1 < kAIR && kx >= 0 && kx + 1 < kAW) {
-            const float* lo = slot(fz.i0) + 3 * kAUS + ky * kAW + kx;
-            const float* hi = slot(fz.i0 + 1) + 3 * kAUS + ky * kAW + kx;
+            // planes z - 2 + kz and z - 1 + kz
+            const float* pl = kz == 0 ? sm2 : (kz == 1 ? sm1 : (kz == 2 ? s0 : sp1));
+            const float* ph = kz == 0 ? sm1 : (kz == 1 ? s0 : (kz == 2 ? sp1 : sp2));
+            const float* lo = pl + 3 * kAUS + ky * kAW + kx;
+            const float* hi = ph + 3 * kAUS + ky * kAW + kx;
             Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
             pw = trilin_pq<int>(lo + kAIS, hi + kAIS, kAW, fz.f, fy.f, fx.f);
         } else {
@@ -278,7 +283,7 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
         cudaError_t e = cudaFuncSetAttribute(k_advect3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kAdvMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = march_chunk(g, 4, 4);
+        const int zc = g.zca > 0 ? g.zca : march_chunk(g, 4, 4);
         const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
         META_CHECK_LAUNCH(launch_k(k_advect3d, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc,
                                    states, u, maxdisp));

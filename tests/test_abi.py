@@ -81,6 +81,33 @@ def test_checkpointing_shrinks_the_workspace(meta):
     assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == 1
 
 
+def test_tuning_table_round_trip_and_validation(meta):
+    """Tile shapes per problem shape: built-in equal tiles, set / get / forget,
+    and range checks before anything runs."""
+    dims, B, s = (160, 192, 160), 1, 6.0
+    meta.set_tuning(dims, B, s, None)
+    t0 = meta.tuning(dims, B, s)
+    assert (t0["ly"], t0["lz"], t0["txw"]) == (96, 80, 80)  # 192 = 2 x 96, 160 = 2 x 80
+    assert 1 <= t0["zc_transport"] <= 160 and 1 <= t0["zc_advect"] <= 160
+    mine = dict(zc_transport=8, zc_advect=16, ly=64, lz=48, txw=64)
+    meta.set_tuning(dims, B, s, mine)
+    assert meta.tuning(dims, B, s) == mine
+    meta.set_tuning(dims, B, s, dict(ly=32))  # zero fields: built-in choice
+    assert meta.tuning(dims, B, s)["ly"] == 32 and meta.tuning(dims, B, s)["lz"] == 80
+    for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
+                dict(lz=-16), dict(zc_advect=-1)):
+        with pytest.raises(meta.MetaError):
+            meta.set_tuning(dims, B, s, bad)
+    with pytest.raises(meta.MetaError):
+        meta.set_tuning((64, 64), 1, 2.0, dict(lz=16))  # 2-D problems have no z tiles
+    with pytest.raises(meta.MetaError):  # y tiles x nz beyond the launch grid limit
+        meta.set_tuning((4000, 2000, 64), 1, 2.0, dict(ly=16))
+    meta.set_tuning(dims, B, s, None)
+    assert meta.tuning(dims, B, s) == t0
+    t2 = meta.tuning((256, 256), 16, 6.0)
+    assert (t2["ly"], t2["txw"], t2["lz"], t2["zc_transport"]) == (128, 128, 0, 0)
+
+
 def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
     lib = meta._load()
     pr = meta._problem(2, (16, 16), 1, 4, 2.0)

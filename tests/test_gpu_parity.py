@@ -271,6 +271,29 @@ def test_workspace_contents_do_not_matter(meta, dims, B, T, sigma, k, scale):
     assert torch.equal(c0, cn) and torch.equal(g0, gn)
 
 
+@pytest.mark.parametrize("dims,B,T,sigma", [((37, 141), 2, 5, 2.3), ((21, 45, 70), 2, 4, 2.0)])
+def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma):
+    """Every output is summed in the same order whatever the tiles: explicit odd
+    tile shapes and the autotuner's choice give the built-in results bit for bit."""
+    I0, _ = phantoms.random_fields(121, B, dims)
+    J, _ = phantoms.random_fields(122, B, dims)
+    p0 = smooth_p(123, (B,) + dims, 30.0)
+    args = (T, sigma, [0.1, 0.0][:B], [1.0, 1.2][:B], [1e-2, 1e-3][:B])
+    meta.set_tuning(dims, B, sigma, None)
+    c0, g0 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    odd = dict(ly=16, txw=8) if len(dims) == 2 else dict(zc_transport=1, zc_advect=3, ly=16,
+                                                         lz=16, txw=24)
+    meta.set_tuning(dims, B, sigma, odd)
+    c1, g1 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    chosen = meta.autotune(cuda(I0), cuda(J), cuda(p0), *args)
+    assert meta.tuning(dims, B, sigma) == chosen
+    c2, g2 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    meta.set_tuning(dims, B, sigma, None)
+    torch.cuda.synchronize()
+    assert torch.equal(c0, c1) and torch.equal(g0, g1)
+    assert torch.equal(c0, c2) and torch.equal(g0, g2)
+
+
 def test_results_are_deterministic(meta):
     w = phantoms.disk_pair_64()
     a = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam)
