@@ -76,59 +76,76 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
 
     const int ncomp = GRADP ? NDIM : 1;
     if constexpr (GRADP) {
-        // m_i = p * D_i I on the whole staged row range (finite everywhere;
-        // columns 0 and LW-1 only ever meet zero taps).
-        const float inv_lw = 1.f / (float)LW;
-        for (int idx = tid; idx < kRows * LW; idx += blockDim.x) {
+        // m_i = p * D_i I on the whole staged row range, four columns per
+        // thread (finite everywhere; columns 0 and LW-1 only ever meet zero
+        // taps, and there the missing neighbour is replaced by the column itself).
+        const int LW4 = LW / 4;
+        const float inv_lw4 = 1.f / (float)LW4;
+        for (int idx = tid; idx < kRows * LW4; idx += blockDim.x) {
             // idx < 2^12, so the rounded float quotient is the exact integer one
-            const int row = (int)(((float)idx + 0.5f) * inv_lw);
-            const int c = idx - row * LW;
+            const int row = (int)(((float)idx + 0.5f) * inv_lw4);
+            const int c = 4 * (idx - row * LW4);
             const int ty = (NDIM == 2) ? row : (row & 3);
             const int tz = (NDIM == 2) ? 0 : (row >> 2);
-            const int x = x0 - HX + c, y = y0 + ty, z = z0 + tz;
-            float m[NDIM];
-            if (x < 0 || x >= g.nx || y >= g.ny || z >= g.nz) {
+            const int y = y0 + ty, z = z0 + tz;
+            float mo[NDIM][4];
 #pragma unroll
-                for (int a = 0; a < NDIM; ++a) m[a] = 0.f;
-            } else {
+            for (int a = 0; a < NDIM; ++a)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mo[a][j] = 0.f;
+            if (y < g.ny && z < g.nz) {
                 const int rI = (NDIM == 2) ? (ty + 1) : ((tz + 1) * 6 + ty + 1);
                 const float* Ir = sI + rI * LW;
-                const int cl = (x > 0) ? max(c - 1, 0) : c;
-                const int cr = (x < g.nx - 1) ? min(c + 1, LW - 1) : c;
-                const float gx = 0.5f * (Ir[cr] - Ir[cl]);
-                const float gy = 0.5f * (sI[(rI + (y < g.ny - 1 ? 1 : 0)) * LW + c] -
-                                         sI[(rI - (y > 0 ? 1 : 0)) * LW + c]);
-                const float p = sP[row * LW + c];
-                if constexpr (NDIM == 2) {
-                    m[0] = p * gy;
-                    m[1] = p * gx;
-                } else {
-                    const float gz = 0.5f * (sI[(rI + (z < g.nz - 1 ? 6 : 0)) * LW + c] -
-                                             sI[(rI - (z > 0 ? 6 : 0)) * LW + c]);
-                    m[0] = p * gz;
-                    m[1] = p * gy;
-                    m[2] = p * gx;
+                const float4 ic = lds4(Ir + c);
+                const float iv[6] = {c > 0 ? Ir[c - 1] : ic.x, ic.x, ic.y, ic.z, ic.w,
+                                     c + 4 < LW ? Ir[c + 4] : ic.w};
+                const float4 yu = lds4(sI + (rI + (y < g.ny - 1 ? 1 : 0)) * LW + c);
+                const float4 yd = lds4(sI + (rI - (y > 0 ? 1 : 0)) * LW + c);
+                const float yuv[4] = {yu.x, yu.y, yu.z, yu.w}, ydv[4] = {yd.x, yd.y, yd.z, yd.w};
+                const float4 p4 = lds4(sP + row * LW + c);
+                const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+                float zuv[4] = {0.f, 0.f, 0.f, 0.f}, zdv[4] = {0.f, 0.f, 0.f, 0.f};
+                if constexpr (NDIM == 3) {
+                    const float4 zu = lds4(sI + (rI + (z < g.nz - 1 ? 6 : 0)) * LW + c);
+                    const float4 zd = lds4(sI + (rI - (z > 0 ? 6 : 0)) * LW + c);
+                    zuv[0] = zu.x; zuv[1] = zu.y; zuv[2] = zu.z; zuv[3] = zu.w;
+                    zdv[0] = zd.x; zdv[1] = zd.y; zdv[2] = zd.z; zdv[3] = zd.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int x = x0 - HX + c + j;
+                    if (x < 0 || x >= g.nx) continue;
+                    const float gx = 0.5f * ((x < g.nx - 1 ? iv[j + 2] : iv[j + 1]) -
+                                             (x > 0 ? iv[j] : iv[j + 1]));
+                    const float gy = 0.5f * (yuv[j] - ydv[j]);
+                    if constexpr (NDIM == 2) {
+                        mo[0][j] = pv[j] * gy;
+                        mo[1][j] = pv[j] * gx;
+                    } else {
+                        const float gz = 0.5f * (zuv[j] - zdv[j]);
+                        mo[0][j] = pv[j] * gz;
+                        mo[1][j] = pv[j] * gy;
+                        mo[2][j] = pv[j] * gx;
+                    }
                 }
             }
 #pragma unroll
-            for (int a = 0; a < NDIM; ++a) sM[(a * kRows + row) * LW + c] = m[a];
+            for (int a = 0; a < NDIM; ++a)
+                *reinterpret_cast<float4*>(sM + (a * kRows + row) * LW + c) =
+                    make_float4(mo[a][0], mo[a][1], mo[a][2], mo[a][3]);
         }
         __syncthreads();
     }
 
     // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`,
-    // g.txw / 8 threads per row.  With 16 per row, lanes alternate between
-    // two rows, so a quarter-warp's 16-byte loads cover 4 columns of each row
-    // (odd row stride in 16-byte units).
+    // g.txw / 8 threads per row.  Consecutive threads alternate between the two
+    // rows of a row pair, so a quarter-warp's 16-byte loads cover columns of
+    // both rows and, with the row stride odd in 16-byte units, spread over the
+    // bank groups.
     const int tpr = g.txw / kBX;
-    int tx, row;
-    if (tpr == 16) {
-        tx = (tid >> 1) & 15;
-        row = ((tid >> 5) << 1) | (tid & 1);
-    } else {
-        row = tid / tpr;
-        tx = tid - row * tpr;
-    }
+    const int local = tid % (2 * tpr), pair = tid / (2 * tpr);
+    const int tx = local >> 1;
+    const int row = 2 * pair + (local & 1);
     const int ty = (NDIM == 2) ? row : (row & 3);
     const int tz = (NDIM == 2) ? 0 : (row >> 2);
     const int y = y0 + ty, z = z0 + tz;

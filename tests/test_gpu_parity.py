@@ -320,6 +320,36 @@ def test_head_128_full_size(meta):
     check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam)
 
 
+def test_mri_registration_parity_along_gradient_descent(meta):
+    """The 160x192x160 pipeline on its 2x block-averaged copy (80x96x80, sigma 3,
+    checkpoint stride 5): 100 gradient-descent iterations of a recorded plan on the
+    GPU; cost and dL/dp0 against the oracle at iterations 0, 10 and 100, on the
+    GPU's own p0 iterates; the data term decreases."""
+    w = phantoms.mri_pair_3d()
+    I0s, Js = phantoms.block_average(w.I0), phantoms.block_average(w.J)
+    sigma = w.sigma / 2
+    mu, rho, lam = float(w.mu[0]), float(w.rho[0]), float(w.lam[0])
+    plan = meta.CostAndGradPlan(cuda(I0s), cuda(Js), cuda(np.zeros_like(I0s)), w.T, sigma, mu,
+                                rho, lam, ckpt=5)
+    oracle.set_threads(oracle.max_threads())
+    data = []
+    for it in range(101):
+        plan.launch()
+        if it in (0, 10, 100):
+            torch.cuda.synchronize()
+            p_it = plan.p0.cpu().numpy()[0].astype(np.float64)
+            c, g = oracle.cost_and_grad(I0s[0], Js[0], p_it, w.T, sigma, mu, rho, lam)
+            np.testing.assert_allclose(plan.cost.cpu().numpy()[0], c, rtol=COST_RTOL, atol=1e-12)
+            e = rel_l2(plan.grad.cpu().numpy()[0], g)
+            assert e <= GRAD_RTOL, (it, e)
+            data.append(float(c[0]))
+        # normalised gradient step (the bench's update)
+        gmax = plan.grad.abs().max().clamp_min(1e-30)
+        plan.p0.sub_(0.02 * plan.grad / gmax)
+    assert plan.ws.status() & 1 == 0
+    assert data[1] < data[0] and data[2] < data[0], data
+
+
 def test_mri_volume_downsampled_and_full_size_properties(meta):
     """160x192x160 (sigma 6): parity on the 2x block-averaged copy (sigma 3) and,
     at full size, the p0 = 0 invariance and the rho-rescaling identity."""
