@@ -77,32 +77,24 @@ struct Rec {
     static constexpr int kCell = 0, kI = NDIM + 1, kP = NDIM + 2, kD = NDIM + 3;
 };
 
-// Record of step t at voxel v (pitched offset o in its instance) from
-// I^' = Ih1 and p^' = ph1; state t sits in slot s_state, u_t in slot s_u.  The
-// same expressions as the forward step t.
+// Record of step t at voxel v from I^' = Ih1, p^' = ph1, the displacement d
+// of the foot per axis and div v_t (the same expressions as the forward step),
+// with p_t at pprev.
 template <int NDIM>
-__device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
-                                             const Vox& v, long long o, float Ih1, float ph1,
-                                             const float* __restrict__ states,
-                                             const float* __restrict__ u, float* rec) {
+__device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
+                                            long long o, float Ih1, float ph1, const float* d,
+                                            float div, const float* __restrict__ pprev,
+                                            float* rec) {
     const int b = v.b;
-    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-    const float dtrho = dt * rho;
-    int c[NDIM], n[NDIM];
-    long long s[NDIM];
-    axis_info<NDIM>(g, v, c, n, s);
-    float d[NDIM];
-    float du = 0.f;
-#pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        const float* ua = slice_of(u, g, ((long long)s_u * NDIM + a) * g.B + b);
-        d[a] = disp_of(dtrho, ua[o]);
-        du += cdiff(ua, o, s[a], c[a], n[a]);
-    }
-    const float div = -rho * du;
+    const float mu = cf.mu[b], dt = cf.dt;
     const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-    const float pw =
-        interp<NDIM>(g, F, slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b));
+    float pw;
+    if constexpr (NDIM == 2)
+        pw = rn_bilin(pprev + F.base, g.P, F.f[0].f, F.f[1].f);
+    else
+        pw = rn_trilin(pprev + F.base, pprev + F.base + g.slab, g.P, F.f[0].f, F.f[1].f,
+                       F.f[2].f);
+    const int c[3] = {NDIM == 3 ? v.z : v.y, NDIM == 3 ? v.y : v.x, v.x};
     int off[3] = {0, 0, 0};
     bool ins[3] = {false, false, false};
 #pragma unroll
@@ -116,8 +108,34 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) r[(1 + a) * sl] = F.f[a].f;
     r[Rec<NDIM>::kI * sl] = Ih1;
-    r[Rec<NDIM>::kP * sl] = ph1 * (1.f - dt * div) + (dt * mu) * Ih1;
-    r[Rec<NDIM>::kD * sl] = -dt * pw * ph1;
+    r[Rec<NDIM>::kP * sl] = rn_ptilde_hat(ph1, Ih1, dt, mu, div);
+    r[Rec<NDIM>::kD * sl] = rn_div_hat(dt, pw, ph1);
+}
+
+// Record of step t at voxel v (pitched offset o in its instance) from
+// I^' = Ih1 and p^' = ph1; state t sits in slot s_state, u_t in slot s_u.  The
+// same expressions as the forward step t.
+template <int NDIM>
+__device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
+                                             const Vox& v, long long o, float Ih1, float ph1,
+                                             const float* __restrict__ states,
+                                             const float* __restrict__ u, float* rec) {
+    const int b = v.b;
+    const float rho = cf.rho[b], dtrho = cf.dt * rho;
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    float d[NDIM];
+    float du = 0.f;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)s_u * NDIM + a) * g.B + b);
+        d[a] = disp_of(dtrho, ua[o]);
+        const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
+        du = __fadd_rn(du, rn_cdiff(ua[o + hi], ua[o - lo]));
+    }
+    emit_record<NDIM>(g, cf, v, o, Ih1, ph1, d, __fmul_rn(-rho, du),
+                      slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b), rec);
 }
 
 // Per-axis weights with which a source whose foot moved by less than one
@@ -131,8 +149,8 @@ __device__ __forceinline__ void axis_weights(int off, float f, float* w) {
 
 // ------------------------------------------------------------------ kernels
 
-// Cost partials: one CTA = 256 threads over a fixed voxel range of instance
-// blockIdx.y; also starts the adjoint: I^_T = I_T - J, p^_T = 0 -> record T-1.
+// Cost partials: one CTA = 8 warps over a fixed set of (z, y) rows of
+// instance blockIdx.y; also starts the adjoint: I^_T = I_T - J, p^_T = 0 -> record T-1.
 template <int NDIM>
 __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
@@ -146,16 +164,19 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
     const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
     double data = 0.0, kin = 0.0, res = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
+    // one warp per (z, y) row at a time; a fixed assignment, so fixed sums
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrows = g.nz * g.ny;
+    for (int row = blockIdx.x * 8 + warp; row < nrows; row += gridDim.x * 8)
+    for (int x = lane; x < g.nx; x += 32) {
         Vox v;
         v.b = b;
-        v.x = (int)(i % g.nx);
-        v.y = (int)((i / g.nx) % g.ny);
-        v.z = (int)(i / ((long long)g.nx * g.ny));
+        v.z = row / g.ny;
+        v.y = row - v.z * g.ny;
+        v.x = x;
         v.ok = true;
         const long long o = gidx(g, v.z, v.y, v.x);
-        const float r = IT[o] - J[(long long)b * N + i];
+        const float r = IT[o] - J[(long long)b * N + (long long)row * g.nx + x];
         data += 0.5 * (double)r * (double)r;
         int c[NDIM], n[NDIM];
         long long s[NDIM];
@@ -799,21 +820,21 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
         const float dtrho = dt * rho;
         const float d0 = disp_of(dtrho, sU0[c]), d1 = disp_of(dtrho, sU1[c]);
         float du = 0.f;
-        du += 0.5f * (sU0[c + (y < g.ny - 1 ? W : 0)] - sU0[c - (y > 0 ? W : 0)]);
-        du += 0.5f * (sU1[c + (x < g.nx - 1 ? 1 : 0)] - sU1[c - (x > 0 ? 1 : 0)]);
-        const float div = -rho * du;
+        du = __fadd_rn(du, rn_cdiff(sU0[c + (y < g.ny - 1 ? W : 0)], sU0[c - (y > 0 ? W : 0)]));
+        du = __fadd_rn(du, rn_cdiff(sU1[c + (x < g.nx - 1 ? 1 : 0)], sU1[c - (x > 0 ? 1 : 0)]));
+        const float div = __fmul_rn(-rho, du);
         const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
         const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
         const bool ins[3] = {fy.inside, fx.inside, false};
-        const float pw = bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
+        const float pw = rn_bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
         const long long rsl = (long long)g.B * g.inst;
         float* r = rec + ob;
         r[Rec<2>::kCell * rsl] = __int_as_float(pack_cell(off, ins));
         r[rsl] = fy.f;
         r[2 * rsl] = fx.f;
         r[Rec<2>::kI * rsl] = Ihv;
-        r[Rec<2>::kP * rsl] = phv * (1.f - dt * div) + (dt * mu) * Ihv;
-        r[Rec<2>::kD * rsl] = -dt * pw * phv;
+        r[Rec<2>::kP * rsl] = rn_ptilde_hat(phv, Ihv, dt, mu, div);
+        r[Rec<2>::kD * rsl] = rn_div_hat(dt, pw, phv);
         return;
     }
     float kg = 0.f;

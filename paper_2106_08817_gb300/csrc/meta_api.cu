@@ -131,10 +131,10 @@ Layout make_layout(const meta_problem* pr) {
     L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
     L.nstate = L.k ? L.nseg + L.k : pr->T + 1;
     L.nu = L.k ? L.k + 1 : pr->T;
-    const long long N = (long long)g.nz * g.ny * g.nx;
-    long long nblk = (N + 2047) / 2048;
+    // cost partial sums: one CTA of 8 warps per 8 rows, at most 4096 per instance
+    long long nblk = ((long long)g.nz * g.ny + 7) / 8;
     if (nblk < 1) nblk = 1;
-    if (nblk > 256) nblk = 256;
+    if (nblk > 4096) nblk = 4096;
     L.nblk = (int)nblk;
 
     const size_t fslice = (size_t)g.inst * 4;  // bytes of one pitched field

@@ -116,6 +116,34 @@ __device__ __forceinline__ void bilin_grad(const float* p, int W, float fy, floa
     *dx = inx ? ((1.f - fy) * (c01 - c00) + fy * (c11 - c10)) : 0.f;
 }
 
+// Record arithmetic of the adjoint with every rounding explicit (no FMA
+// contraction), so that every kernel that builds a record of a step -- from
+// staged tiles or from global memory -- writes the same bits.
+__device__ __forceinline__ float rn_cdiff(float hi, float lo) {
+    return __fmul_rn(0.5f, __fsub_rn(hi, lo));
+}
+__device__ __forceinline__ float rn_lerp(float a, float b, float f) {
+    return __fadd_rn(__fmul_rn(__fsub_rn(1.f, f), a), __fmul_rn(f, b));
+}
+__device__ __forceinline__ float rn_bilin(const float* p, long long W, float fy, float fx) {
+    return rn_lerp(rn_lerp(p[0], p[1], fx), rn_lerp(p[W], p[W + 1], fx), fy);
+}
+__device__ __forceinline__ float rn_trilin(const float* p, const float* q, long long P, float fz,
+                                           float fy, float fx) {
+    const float b0 = rn_lerp(rn_lerp(p[0], p[1], fx), rn_lerp(p[P], p[P + 1], fx), fy);
+    const float b1 = rn_lerp(rn_lerp(q[0], q[1], fx), rn_lerp(q[P], q[P + 1], fx), fy);
+    return rn_lerp(b0, b1, fz);
+}
+// p~^ = p^' (1 - dt div) + dt mu I^'  and  div^ = -dt p~ p^'
+__device__ __forceinline__ float rn_ptilde_hat(float ph1, float Ih1, float dt, float mu,
+                                               float div) {
+    return __fadd_rn(__fmul_rn(ph1, __fsub_rn(1.f, __fmul_rn(dt, div))),
+                     __fmul_rn(__fmul_rn(dt, mu), Ih1));
+}
+__device__ __forceinline__ float rn_div_hat(float dt, float pw, float ph1) {
+    return __fmul_rn(__fmul_rn(-dt, pw), ph1);
+}
+
 template <int NDIM>
 struct Feet {
     Foot1 f[NDIM];
