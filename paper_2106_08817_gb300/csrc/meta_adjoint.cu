@@ -138,13 +138,18 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
                       slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b), rec);
 }
 
-// Per-axis weights with which a source whose foot moved by less than one
-// voxel passes its value to the nodes s-1, s, s+1 (cell offset -1 or 0).
-__device__ __forceinline__ void axis_weights(int off, float f, float* w) {
-    const bool down = off < 0;
-    w[0] = down ? 1.f - f : 0.f;
-    w[1] = down ? f : 1.f - f;
-    w[2] = down ? 0.f : f;
+// Packed per-axis weights of a source whose foot moved by less than one voxel:
+// g = f - 1 if its foot cell lies below the source (cell offset -1), g = f
+// otherwise.  A source at offset E (-1, 0, +1) from a node passes its value to
+// it with weight max(g, 0), 1 - |g|, max(-g, 0) along that axis -- the bilinear
+// weights f and 1 - f (1 - |g| = f when the cell lies below holds up to one
+// rounding).
+__device__ __forceinline__ float pack_g(int off, float f) { return off < 0 ? f - 1.f : f; }
+template <int E>
+__device__ __forceinline__ float gw(float g) {
+    if constexpr (E < 0) return fmaxf(g, 0.f);
+    else if constexpr (E > 0) return fmaxf(-g, 0.f);
+    else return 1.f - fabsf(g);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -250,7 +255,8 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
 
 // 2-D adjoint step t with R = 1, all operands staged: the records (cell, f_y,
 // f_x, I^', p~^, div^) and I_t, p_t over the tile grown by one voxel, by
-// cp.async.  The same expressions as the generic path of k_adj_transport.
+// cp.async.  Each source of the grown tile is packed once into the float4
+// (g_y, g_x, I^', p~^) (pack_g); each node then sums 9 branch-free products.
 __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const float* rb,
                                                 long long sl, const float* It, const float* pt,
                                                 float* vh0, float* vh1, float* Ihpb,
@@ -267,7 +273,7 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
     float* sD = sP + WIN;        // div^
     float* sIt = sD + WIN;
     float* sPt = sIt + WIN;
-    float* sW = sPt + WIN;       // [6][NR]: wy[3], wx[3]
+    float4* sQ = reinterpret_cast<float4*>(sPt + WIN);  // [NR]: g_y, g_x, I^', p~^
     const int xl = x0 - 4, yl = y0 - 1;
     stage_async<W, HR>(sC, rb, g, xl, yl);
     stage_async<W, HR>(sF0, rb + sl, g, xl, yl);
@@ -283,18 +289,13 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
         const int ry = i / RX, rx = i - ry * RX;
         const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
         const int wi = ry * W + rx + 3;  // window index of source (sy, sx)
-        float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);  // outside: no weight, no value
         if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
             const int cell = __float_as_int(sC[wi]);
-            axis_weights(cell_off(cell, 0), sF0[wi], w);
-            axis_weights(cell_off(cell, 1), sF1[wi], w + 3);
-        } else {
-            // pitch padding is never written: keep whatever it holds out of 0 * x
-            sI[wi] = 0.f;
-            sP[wi] = 0.f;
+            q = make_float4(pack_g(cell_off(cell, 0), sF0[wi]), pack_g(cell_off(cell, 1), sF1[wi]),
+                            sI[wi], sP[wi]);
         }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sW[k * NR + i] = w[k];
+        sQ[i] = q;
     }
     __syncthreads();
     const int x = x0 + tx, y = y0 + ty;
@@ -302,15 +303,18 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
     const int me = (ty + 1) * RX + tx + 1;   // region index of the node
     const int mw = (ty + 1) * W + tx + 4;    // window index of the node
     float accI = 0.f, accP = 0.f;
+    // the source at offset (dy, dx) from the node passes weight gw<dy> gw<dx>
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
-            const int i = me + dy * RX + dx;
-            const int wi = mw + dy * W + dx;
-            const float wgt = sW[(1 - dy) * NR + i] * sW[(3 + 1 - dx) * NR + i];
-            accI += wgt * sI[wi];
-            accP += wgt * sP[wi];
+            const float4 q = sQ[me + dy * RX + dx];
+            float wy, wx;
+            if (dy < 0) wy = gw<-1>(q.x); else if (dy > 0) wy = gw<1>(q.x); else wy = gw<0>(q.x);
+            if (dx < 0) wx = gw<-1>(q.y); else if (dx > 0) wx = gw<1>(q.y); else wx = gw<0>(q.y);
+            const float wgt = wy * wx;
+            accI += wgt * q.z;
+            accP += wgt * q.w;
         }
     }
     const int o = y * g.P + x;
@@ -524,13 +528,6 @@ constexpr int kMChunks = kMF * kMHY * (kMW / 4);         // 16-byte copies per p
 constexpr int kMPer = (kMChunks + kPX * kPY - 1) / (kPX * kPY);
 constexpr size_t kMarchSmem = (size_t)(4 * kMF * kMPL + 5 * kMPR) * sizeof(float);
 
-// Axis weight of a source at compile-time offset E from the node (see above).
-template <int E>
-__device__ __forceinline__ float gw(float g) {
-    if constexpr (E < 0) return fmaxf(g, 0.f);
-    else if constexpr (E > 0) return fmaxf(-g, 0.f);
-    else return 1.f - fabsf(g);
-}
 
 // Packs the sources of one staged plane at z (zero outside the domain).
 __device__ __forceinline__ void march_pack(const float* raw, float4* q, float* pp, const Geom& g,
@@ -546,9 +543,9 @@ __device__ __forceinline__ void march_pack(const float* raw, float4* q, float* p
         if (zin && sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny) {
             const int cell = __float_as_int(raw[wi]);
             const float fz = raw[kMPL + wi], fy = raw[2 * kMPL + wi], fx = raw[3 * kMPL + wi];
-            v.x = cell_off(cell, 0) < 0 ? fz - 1.f : fz;
-            v.y = cell_off(cell, 1) < 0 ? fy - 1.f : fy;
-            v.z = cell_off(cell, 2) < 0 ? fx - 1.f : fx;
+            v.x = pack_g(cell_off(cell, 0), fz);
+            v.y = pack_g(cell_off(cell, 1), fy);
+            v.z = pack_g(cell_off(cell, 2), fx);
             v.w = raw[4 * kMPL + wi];
             pv = raw[5 * kMPL + wi];
         }

@@ -295,21 +295,23 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     }
     const int x = x0 + tx;
     if (x >= g.nx) return;
-    const float sc = scale ? scale_mul * scale[b] : 1.f;
-    float* o = out + (long long)(out_slice0 + slice) * g.inst;
+    // outputs a = a0 + ta kBA + j along the axis: one pointer stepped by the
+    // axis stride (P for y, slab for z)
+    const int a_first = a0 + ta * kBA;
+    const long long stride = (NDIM == 3 && AXIS == 0) ? g.slab : (long long)g.P;
+    float* op = out + (long long)(out_slice0 + slice) * g.inst +
+                ((NDIM == 2) ? gidx(g, 0, a_first, x)
+                             : (AXIS == 1 ? gidx(g, z, a_first, x) : gidx(g, a_first, y, x)));
+    const int nj = min(kBA, n_axis - a_first);
+    if (scale) {
+        const float sc = scale_mul * scale[b];
 #pragma unroll
-    for (int j = 0; j < kBA; ++j) {
-        const int a = a0 + ta * kBA + j;
-        if (a < n_axis) {
-            long long off;
-            if constexpr (NDIM == 2)
-                off = gidx(g, 0, a, x);
-            else if constexpr (AXIS == 1)
-                off = gidx(g, z, a, x);
-            else
-                off = gidx(g, a, y, x);
-            o[off] = sc * acc[j];
-        }
+        for (int j = 0; j < kBA; ++j)
+            if (j < nj) op[j * stride] = sc * acc[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < kBA; ++j)
+            if (j < nj) op[j * stride] = acc[j];
     }
 }
 
