@@ -208,9 +208,10 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kclass: str, launch_voxels: int):
-    """Per-launch DRAM bytes of `kclass` from the committed ncu summary, scaled to
-    this launch's voxel count; None when missing or taken on other kernel sources."""
+def ncu_traffic(kclass: str, ndim: int, launch_voxels: int):
+    """Per-launch DRAM bytes of `kclass` in `ndim` dimensions from the committed ncu
+    summary, scaled to this launch's voxel count; None when missing or taken on
+    other kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -218,7 +219,7 @@ def ncu_traffic(kclass: str, launch_voxels: int):
         d = json.load(f)
     if d.get("sources_hash") != kernel_sources_hash():
         return None
-    k = d.get("kernels", {}).get(kclass)
+    k = d.get("kernels", {}).get("%s@%d" % (kclass, ndim))
     if not k:
         return None
     return float(k["dram_bytes_per_launch"]) * launch_voxels / float(k["voxels_per_launch"])
@@ -371,7 +372,7 @@ def run_ours(args):
     per_launch_bytes = bytes_per_voxel(dom, d) * B * N
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peak, peak_src = peaks()
-    traffic = ncu_traffic(dom, B * N)
+    traffic = ncu_traffic(dom, d, B * N)
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[2],
                    "share": round(v[0] / max(sum(x[0] for x in kt.values()), 1e-9), 4),
                    "avg_us": round(v[0] / max(v[1], 1) * 1e3, 3),
