@@ -116,6 +116,10 @@ Layout make_layout(const meta_problem* pr) {
     g.ly = even_tile(g.ny, kTA, kBA);
     g.lz = d == 3 ? even_tile(g.nz, kTA, kBA) : kBA;
     g.zct = g.zca = 0;
+    {
+        const unsigned long long nyt = (unsigned long long)(g.ny + 7) / 8;
+        g.nyt_mul = nyt == 1 ? 0u : (unsigned)(((1ull << 32) + nyt - 1) / nyt);
+    }
     meta_tuning tn;
     if (find_tuning(pr, &tn)) {
         if (tn.txw > 0) g.txw = tn.txw;

@@ -61,7 +61,14 @@ struct Geom {
     int txw;          // x-pass tile width (multiple of kBX, <= kTX)
     int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTA)
     int zct, zca;     // planes per CTA of the 3-D transport / advect (0: heuristic)
+    unsigned nyt_mul; // ceil(2^32 / nyt), nyt = ceil(ny / 8): q = umulhi(n, nyt_mul) = n / nyt
+                      // exactly for n * nyt < 2^32 (n < 65536, nyt <= 8192); 0 when nyt = 1
 };
+
+// n / nyt for a grid index n of the pointwise kernels (see Geom::nyt_mul).
+__device__ __forceinline__ int div_nyt(const Geom& g, int n) {
+    return g.nyt_mul ? (int)__umulhi((unsigned)n, g.nyt_mul) : n;
+}
 
 // Planes per CTA of a kernel that marches along z over 32 x 8 columns: the
 // chunk that best trades the `halo` extra planes each chunk stages against

@@ -20,10 +20,11 @@ template <int NDIM>
 __device__ __forceinline__ Vox vox_of(const Geom& g) {
     Vox v;
     const int nyt = (g.ny + kPY - 1) / kPY;
+    const int zq = (NDIM == 3) ? div_nyt(g, blockIdx.y) : 0;
     v.b = blockIdx.z;
     v.x = blockIdx.x * kPX + threadIdx.x;
-    v.y = (blockIdx.y % nyt) * kPY + threadIdx.y;
-    v.z = (NDIM == 3) ? (int)(blockIdx.y / nyt) : 0;
+    v.y = ((int)blockIdx.y - zq * nyt) * kPY + threadIdx.y;
+    v.z = zq;
     v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
     return v;
 }
