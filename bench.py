@@ -145,12 +145,18 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # wait for the sampler's first line, so that the samples kept (those
+            # after this point) fall inside the timed region
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError as e:
             self.err = str(e)
+        self.first = len(self.lines)
         return self
 
     def _read(self):
@@ -167,6 +173,8 @@ class ClockSampler:
             self.th.join(timeout=2)
 
     def summary(self):
+        if len(self.lines) > self.first:
+            self.lines = self.lines[self.first:]  # samples taken during the timed region
         if self.err or not self.lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
                     "note": self.err or "no nvidia-smi samples"}
@@ -548,7 +556,7 @@ def run_mix(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ellipses16x256")

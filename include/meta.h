@@ -75,7 +75,8 @@ typedef struct {
                         compute per segment for memory */
 } meta_problem;
 
-/* Bytes of workspace that every call below needs for this problem.
+/* Bytes of workspace that every call below needs for this problem (enough
+ * for any batch split of meta_plan_create as well).
  * With ckpt_stride <= 1 the workspace holds the whole trajectory (I_t, p_t),
  * t = 0..T, and the smoothed momenta u_t = K(p_t grad I_t), t < T, so that the
  * adjoint needs no recomputation: about (2(T+1) + d T + 4d + 6) * batch *
@@ -180,15 +181,19 @@ typedef struct {
     int ly;           /* multiple of 16 in [16, 128] */
     int lz;           /* 3-D only; multiple of 16 in [16, 128] */
     int txw;          /* multiple of 8 in [8, 128] */
+    int split;        /* meta_plan_create records the batch as this many sub-batches on
+                         parallel graph branches, in [1, min(batch, 16)]; the eager calls
+                         ignore it */
 } meta_tuning;
 
 /* Autotuner: times meta_cost_and_grad on these inputs (same arguments) for
  * candidate tile shapes, one field at a time in the order above, keeps the
- * fastest of each, and records the result for the problem shape in a
- * process-wide table that every later call (and meta_plan_create) with that
- * shape uses.  Results do not depend on the tile shapes beyond summation
- * order.  Blocking: synchronises `stream` (not capturable); overwrites cost and
- * grad; `out` (may be NULL) receives the choice. */
+ * fastest of each, then times recorded plans (meta_plan_create) for the batch
+ * split, and records the result for the problem shape in a process-wide table
+ * that every later call and plan with that shape uses.  No field changes any
+ * result: every output is summed in the same order.  Blocking: synchronises
+ * `stream` (not capturable); overwrites cost and grad; `out` (may be NULL)
+ * receives the choice. */
 meta_status meta_autotune(const meta_problem* prob, const float* I0, const float* J,
                           const float* p0, const float* mu, const float* rho, const float* lambda,
                           double* cost, float* grad, void* ws, size_t ws_bytes, void* stream,

@@ -53,7 +53,7 @@ class _Problem(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("zc_transport", ctypes.c_int), ("zc_advect", ctypes.c_int), ("ly", ctypes.c_int),
-                ("lz", ctypes.c_int), ("txw", ctypes.c_int)]
+                ("lz", ctypes.c_int), ("txw", ctypes.c_int), ("split", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -288,7 +288,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     return cost, grad
 
 
-TUNING_FIELDS = ("zc_transport", "zc_advect", "ly", "lz", "txw")
+TUNING_FIELDS = ("zc_transport", "zc_advect", "ly", "lz", "txw", "split")
 
 
 def tuning(dims: Sequence[int], batch: int, sigma: float) -> dict:

@@ -40,6 +40,15 @@ bool find_tuning(const meta_problem* pr, meta_tuning* t) {
     return true;
 }
 
+constexpr int kMaxSplit = 16;  // largest batch split of a recorded plan
+
+// Sub-batch k of a batch split into S: instances [first, first + count).
+void split_range(int B, int S, int k, int* first, int* count) {
+    const int q = B / S, r = B % S;
+    *first = k * q + (k < r ? k : r);
+    *count = q + (k < r ? 1 : 0);
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Workspace map (byte offsets from the workspace base).
@@ -482,6 +491,44 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
     return META_OK;
 }
 
+// Workspace bytes of a batch split into S sub-batches, each in its own
+// 256-byte aligned region.
+size_t split_bytes(const meta_problem* pr, int S) {
+    size_t total = 0;
+    for (int k = 0; k < S; ++k) {
+        int first, count;
+        split_range(pr->batch, S, k, &first, &count);
+        meta_problem sub = *pr;
+        sub.batch = count;
+        total += align_up(make_layout(&sub).total, kAlign);
+    }
+    return total;
+}
+
+// One cost_and_grad call with an optional fault word other than the one in
+// its workspace (the sub-batches of a split plan all report to the first).
+meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const float* J,
+                               const float* p0, const float* mu, const float* rho,
+                               const float* lambda, double* cost, float* grad, void* ws,
+                               size_t ws_bytes, void* stream, unsigned int* fault) {
+    if (!I0 || !J || !p0 || !mu || !rho || !lambda || !cost) return META_ERR_INVALID_ARG;
+    Ctx c;
+    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    if (fault) c.fault = fault;
+    const Geom& g = c.L.g;
+    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T};
+    META_LAUNCH(META_K_PACK, c.st,
+                launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
+    s = run_forward(c, cf);
+    if (s != META_OK) return s;
+    META_LAUNCH(META_K_COST, c.st,
+                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.REC, c.IHP,
+                            c.PHP, c.partials, c.L.nblk, cost, c.st));
+    if (!grad) return META_OK;
+    return run_adjoint(c, cf, 1, grad, nullptr);
+}
+
 }  // namespace
 }  // namespace meta
 
@@ -507,6 +554,8 @@ meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
         return META_ERR_INVALID_ARG;
     if (d == 2 && (tun->lz != 0 || tun->zc_transport != 0 || tun->zc_advect != 0))
         return META_ERR_INVALID_ARG;
+    if (tun->split < 0 || tun->split > (prob->batch < kMaxSplit ? prob->batch : kMaxSplit))
+        return META_ERR_INVALID_ARG;
     // grid limits of the strided passes (y: tiles * nz, z: tiles * ny)
     if (tun->ly && (long long)((ny + tun->ly - 1) / tun->ly) * nz > 65535)
         return META_ERR_INVALID_ARG;
@@ -524,6 +573,8 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
     const Layout L = make_layout(prob);
     out->ly = L.g.ly;
     out->txw = L.g.txw;
+    meta_tuning tn;
+    out->split = (find_tuning(prob, &tn) && tn.split > 0) ? tn.split : 1;
     if (L.ndim == 3) {
         out->lz = L.g.lz;
         out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 3, 2);
@@ -608,6 +659,40 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         *pv.first = best_v;
         if (res != META_OK) break;
     }
+    // batch split of the recorded plan: time plan launches
+    if (res == META_OK && prob->batch > 1) {
+        int best_v = cur.split, nbest = 0;
+        float best_ms = 1e30f;
+        for (int S : {1, 2, 4, 8, 16}) {
+            if (S > prob->batch || S > kMaxSplit) break;
+            cur.split = S;
+            if (meta_tuning_set(prob, &cur) != META_OK) continue;
+            meta_plan* pl = nullptr;
+            res = meta_plan_create(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes, &pl);
+            if (res != META_OK) break;
+            float best = 1e30f;
+            for (int k = 0; k < 4 && res == META_OK; ++k) {
+                if (cudaEventRecord(e0, st) != cudaSuccess ||
+                    meta_plan_launch(pl, stream) != META_OK ||
+                    cudaEventRecord(e1, st) != cudaSuccess ||
+                    cudaEventSynchronize(e1) != cudaSuccess) {
+                    res = META_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) res = META_ERR_CUDA;
+                if (k > 0 && ms < best) best = ms;  // launch 0 warms up
+            }
+            meta_plan_destroy(pl);
+            if (res != META_OK) break;
+            ++nbest;
+            if (best < best_ms) {
+                best_ms = best;
+                best_v = S;
+            }
+        }
+        cur.split = nbest ? best_v : cur.split;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (res != META_OK) {
@@ -623,7 +708,13 @@ meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes) {
     if (!bytes) return META_ERR_INVALID_ARG;
     const meta_status s = validate(prob);
     if (s != META_OK) return s;
-    *bytes = make_layout(prob).total;
+    size_t total = make_layout(prob).total;
+    const int smax = prob->batch < kMaxSplit ? prob->batch : kMaxSplit;
+    for (int S = 2; S <= smax; ++S) {
+        const size_t b = split_bytes(prob, S);
+        total = b > total ? b : total;
+    }
+    *bytes = total;
     return META_OK;
 }
 
@@ -673,27 +764,148 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
                                const float* p0, const float* mu, const float* rho,
                                const float* lambda, double* cost, float* grad, void* ws,
                                size_t ws_bytes, void* stream) {
-    if (!I0 || !J || !p0 || !mu || !rho || !lambda || !cost) return META_ERR_INVALID_ARG;
-    Ctx c;
-    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
-    if (s != META_OK) return s;
-    const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T};
-    META_LAUNCH(META_K_PACK, c.st,
-                launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
-    s = run_forward(c, cf);
-    if (s != META_OK) return s;
-    META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.REC, c.IHP,
-                            c.PHP, c.partials, c.L.nblk, cost, c.st));
-    if (!grad) return META_OK;
-    return run_adjoint(c, cf, 1, grad, nullptr);
+    return cost_and_grad_impl(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes, stream,
+                              nullptr);
 }
 
 struct meta_plan {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
+
+// Records problem k on branch k % streams of one graph (fork from a root
+// stream, join back); `fault` (nullable) overrides every call's fault word.
+static meta_status record_branches(int n, const meta_problem* probs, const float* const* I0,
+                                   const float* const* J, const float* const* p0,
+                                   const float* const* mu, const float* const* rho,
+                                   const float* const* lambda, double* const* cost,
+                                   float* const* grad, void* const* ws, const size_t* ws_bytes,
+                                   int streams, unsigned int* fault, meta_plan** plan) {
+    *plan = nullptr;
+    if (streams < 1) streams = 1;
+    if (streams > n) streams = n;
+    if (streams > 64) streams = 64;
+    cudaStream_t root, br[64];
+    cudaEvent_t fork, done[64];
+    int made = 0;
+    meta_status status = META_OK;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking) != cudaSuccess) return META_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(root);
+        return META_ERR_CUDA;
+    }
+    for (; made < streams; ++made) {
+        if (cudaStreamCreateWithFlags(&br[made], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[made], cudaEventDisableTiming) != cudaSuccess) {
+            status = META_ERR_CUDA;
+            break;
+        }
+    }
+    const bool timer_was_on = g_timer.on;
+    g_timer.on = false;
+    if (status == META_OK &&
+        cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        status = META_ERR_CUDA;
+    else if (status == META_OK) {
+        // fork every branch stream from the root, record problem k on branch k % streams
+        if (cudaEventRecord(fork, root) != cudaSuccess) status = META_ERR_CUDA;
+        for (int j = 0; j < streams && status == META_OK; ++j)
+            if (cudaStreamWaitEvent(br[j], fork, 0) != cudaSuccess) status = META_ERR_CUDA;
+        for (int k = 0; k < n && status == META_OK; ++k)
+            status = cost_and_grad_impl(&probs[k], I0[k], J[k], p0[k], mu[k], rho[k], lambda[k],
+                                        cost[k], grad[k], ws[k], ws_bytes[k], br[k % streams],
+                                        fault);
+        // join
+        for (int j = 0; j < streams; ++j) {
+            cudaEventRecord(done[j], br[j]);
+            cudaStreamWaitEvent(root, done[j], 0);
+        }
+        const cudaError_t e = cudaStreamEndCapture(root, &graph);
+        if (status == META_OK && e != cudaSuccess) status = META_ERR_CUDA;
+    }
+    g_timer.on = timer_was_on;
+    cudaGetLastError();
+    cudaGraphExec_t exec = nullptr;
+    if (status == META_OK && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
+        status = META_ERR_CUDA;
+    for (int j = 0; j < made; ++j) {
+        cudaStreamDestroy(br[j]);
+        cudaEventDestroy(done[j]);
+    }
+    cudaEventDestroy(fork);
+    cudaStreamDestroy(root);
+    if (status != META_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        return status;
+    }
+    meta_plan* p = new (std::nothrow) meta_plan{graph, exec};
+    if (!p) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return META_ERR_INVALID_ARG;
+    }
+    *plan = p;
+    return META_OK;
+}
+
+
+// The batch recorded as S sub-batches on parallel branches of one graph: the
+// kernels of one branch fill the GPU while another's drain.  Sub-batch k runs
+// on its own 256-byte aligned region of ws and reports faults to the first
+// region's word (the header of ws); every instance is computed as in one call.
+static meta_status plan_create_split(const meta_problem* prob, int S, const float* I0,
+                                     const float* J, const float* p0, const float* mu,
+                                     const float* rho, const float* lambda, double* cost,
+                                     float* grad, void* ws, size_t ws_bytes, meta_plan** plan) {
+    if (!I0 || !J || !p0 || !mu || !rho || !lambda || !cost || !ws) return META_ERR_INVALID_ARG;
+    if (split_bytes(prob, S) > ws_bytes) return META_ERR_WORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return META_ERR_WORKSPACE;
+    // sub-batches take the tile shapes tuned for the whole batch
+    meta_tuning parent;
+    if (find_tuning(prob, &parent)) {
+        parent.split = 0;
+        for (int k = 0; k < S; ++k) {
+            int first, count;
+            split_range(prob->batch, S, k, &first, &count);
+            meta_problem sub = *prob;
+            sub.batch = count;
+            meta_tuning have;
+            if (!find_tuning(&sub, &have)) meta_tuning_set(&sub, &parent);
+        }
+    }
+    long long N = 1;
+    for (int a = 0; a < prob->ndim; ++a) N *= prob->dims[a];
+    std::vector<meta_problem> probs(S);
+    std::vector<const float*> vI0(S), vJ(S), vp0(S), vmu(S), vrho(S), vlam(S);
+    std::vector<double*> vcost(S);
+    std::vector<float*> vgrad(S);
+    std::vector<void*> vws(S);
+    std::vector<size_t> vwsb(S);
+    size_t off = 0;
+    for (int k = 0; k < S; ++k) {
+        int first, count;
+        split_range(prob->batch, S, k, &first, &count);
+        probs[k] = *prob;
+        probs[k].batch = count;
+        vI0[k] = I0 + first * N;
+        vJ[k] = J + first * N;
+        vp0[k] = p0 + first * N;
+        vmu[k] = mu + first;
+        vrho[k] = rho + first;
+        vlam[k] = lambda + first;
+        vcost[k] = cost + 3 * (long long)first;
+        vgrad[k] = grad ? grad + first * N : nullptr;
+        const size_t b = align_up(make_layout(&probs[k]).total, kAlign);
+        vws[k] = static_cast<char*>(ws) + off;
+        vwsb[k] = b;
+        off += b;
+    }
+    return record_branches(S, probs.data(), vI0.data(), vJ.data(), vp0.data(), vmu.data(),
+                           vrho.data(), vlam.data(), vcost.data(), vgrad.data(), vws.data(),
+                           vwsb.data(), S, reinterpret_cast<unsigned int*>(ws), plan);
+}
 
 meta_status meta_plan_create(const meta_problem* prob, const float* I0, const float* J,
                              const float* p0, const float* mu, const float* rho,
@@ -704,6 +916,10 @@ meta_status meta_plan_create(const meta_problem* prob, const float* I0, const fl
     size_t need = 0;
     meta_status s = meta_workspace_size(prob, &need);
     if (s != META_OK) return s;
+    meta_tuning tn;
+    const int S = (find_tuning(prob, &tn) && tn.split > 1 && tn.split <= prob->batch) ? tn.split : 1;
+    if (S > 1) return plan_create_split(prob, S, I0, J, p0, mu, rho, lambda, cost, grad, ws,
+                                        ws_bytes, plan);
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return META_ERR_CUDA;
     const bool timer_was_on = g_timer.on;
@@ -754,71 +970,8 @@ meta_status meta_plan_create_group(int n, const meta_problem* probs, const float
         if (s != META_OK) return s;
         if (ws_bytes[k] < need) return META_ERR_WORKSPACE;
     }
-    if (streams < 1) streams = 1;
-    if (streams > n) streams = n;
-    if (streams > 64) streams = 64;
-    cudaStream_t root, br[64];
-    cudaEvent_t fork, done[64];
-    int made = 0;
-    meta_status status = META_OK;
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking) != cudaSuccess) return META_ERR_CUDA;
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
-        cudaStreamDestroy(root);
-        return META_ERR_CUDA;
-    }
-    for (; made < streams; ++made) {
-        if (cudaStreamCreateWithFlags(&br[made], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&done[made], cudaEventDisableTiming) != cudaSuccess) {
-            status = META_ERR_CUDA;
-            break;
-        }
-    }
-    const bool timer_was_on = g_timer.on;
-    g_timer.on = false;
-    if (status == META_OK &&
-        cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        status = META_ERR_CUDA;
-    else if (status == META_OK) {
-        // fork every branch stream from the root, record problem k on branch k % streams
-        if (cudaEventRecord(fork, root) != cudaSuccess) status = META_ERR_CUDA;
-        for (int j = 0; j < streams && status == META_OK; ++j)
-            if (cudaStreamWaitEvent(br[j], fork, 0) != cudaSuccess) status = META_ERR_CUDA;
-        for (int k = 0; k < n && status == META_OK; ++k)
-            status = meta_cost_and_grad(&probs[k], I0[k], J[k], p0[k], mu[k], rho[k], lambda[k],
-                                        cost[k], grad[k], ws[k], ws_bytes[k], br[k % streams]);
-        // join
-        for (int j = 0; j < streams; ++j) {
-            cudaEventRecord(done[j], br[j]);
-            cudaStreamWaitEvent(root, done[j], 0);
-        }
-        const cudaError_t e = cudaStreamEndCapture(root, &graph);
-        if (status == META_OK && e != cudaSuccess) status = META_ERR_CUDA;
-    }
-    g_timer.on = timer_was_on;
-    cudaGetLastError();
-    cudaGraphExec_t exec = nullptr;
-    if (status == META_OK && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
-        status = META_ERR_CUDA;
-    for (int j = 0; j < made; ++j) {
-        cudaStreamDestroy(br[j]);
-        cudaEventDestroy(done[j]);
-    }
-    cudaEventDestroy(fork);
-    cudaStreamDestroy(root);
-    if (status != META_OK) {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        return status;
-    }
-    meta_plan* p = new (std::nothrow) meta_plan{graph, exec};
-    if (!p) {
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        return META_ERR_INVALID_ARG;
-    }
-    *plan = p;
-    return META_OK;
+    return record_branches(n, probs, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes,
+                           streams, nullptr, plan);
 }
 
 meta_status meta_plan_launch(meta_plan* plan, void* stream) {

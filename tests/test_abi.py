@@ -88,14 +88,14 @@ def test_tuning_table_round_trip_and_validation(meta):
     meta.set_tuning(dims, B, s, None)
     t0 = meta.tuning(dims, B, s)
     assert (t0["ly"], t0["lz"], t0["txw"]) == (96, 80, 80)  # 192 = 2 x 96, 160 = 2 x 80
-    assert 1 <= t0["zc_transport"] <= 160 and 1 <= t0["zc_advect"] <= 160
-    mine = dict(zc_transport=8, zc_advect=16, ly=64, lz=48, txw=64)
+    assert 1 <= t0["zc_transport"] <= 160 and 1 <= t0["zc_advect"] <= 160 and t0["split"] == 1
+    mine = dict(zc_transport=8, zc_advect=16, ly=64, lz=48, txw=64, split=1)
     meta.set_tuning(dims, B, s, mine)
     assert meta.tuning(dims, B, s) == mine
     meta.set_tuning(dims, B, s, dict(ly=32))  # zero fields: built-in choice
     assert meta.tuning(dims, B, s)["ly"] == 32 and meta.tuning(dims, B, s)["lz"] == 80
     for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
-                dict(lz=-16), dict(zc_advect=-1)):
+                dict(lz=-16), dict(zc_advect=-1), dict(split=2)):  # split <= batch (1 here)
         with pytest.raises(meta.MetaError):
             meta.set_tuning(dims, B, s, bad)
     with pytest.raises(meta.MetaError):
@@ -105,7 +105,23 @@ def test_tuning_table_round_trip_and_validation(meta):
     meta.set_tuning(dims, B, s, None)
     assert meta.tuning(dims, B, s) == t0
     t2 = meta.tuning((256, 256), 16, 6.0)
-    assert (t2["ly"], t2["txw"], t2["lz"], t2["zc_transport"]) == (128, 128, 0, 0)
+    assert (t2["ly"], t2["txw"], t2["lz"], t2["zc_transport"], t2["split"]) == (128, 128, 0, 0, 1)
+    meta.set_tuning((256, 256), 16, 6.0, dict(split=4))
+    assert meta.tuning((256, 256), 16, 6.0)["split"] == 4
+    with pytest.raises(meta.MetaError):
+        meta.set_tuning((256, 256), 16, 6.0, dict(split=17))
+    meta.set_tuning((256, 256), 16, 6.0, None)
+
+
+def test_workspace_covers_every_batch_split(meta):
+    """A split plan runs sub-batch k in its own aligned region of the caller's
+    workspace: meta_workspace_size covers the sum for every split."""
+    one = meta.workspace_size((37, 141), 1, 5, 2.3)
+    for B in (2, 5, 16):  # split into B regions of one instance each
+        n = meta.workspace_size((37, 141), B, 5, 2.3)
+        assert B * one <= n <= B * one + 64 * 1024
+    n = meta.workspace_size((37, 141), 40, 5, 2.3)  # at most 16 regions
+    assert abs(n - 40 * one) <= 64 * 1024
 
 
 def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):

@@ -288,10 +288,16 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
     chosen = meta.autotune(cuda(I0), cuda(J), cuda(p0), *args)
     assert meta.tuning(dims, B, sigma) == chosen
     c2, g2 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    # a plan that records the batch as two sub-batches on parallel graph branches
+    meta.set_tuning(dims, B, sigma, dict(odd, split=2))
+    plan = meta.CostAndGradPlan(cuda(I0), cuda(J), cuda(p0), *args)
+    plan.launch()
     meta.set_tuning(dims, B, sigma, None)
     torch.cuda.synchronize()
     assert torch.equal(c0, c1) and torch.equal(g0, g1)
     assert torch.equal(c0, c2) and torch.equal(g0, g2)
+    assert torch.equal(c0, plan.cost) and torch.equal(g0, plan.grad)
+    assert plan.ws.status() & 1 == 0
 
 
 def test_results_are_deterministic(meta):
