@@ -142,8 +142,11 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     const float* ua[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) ua[a] = slice_of(u, g, ((long long)sl.ut * 3 + a) * g.B + b);
-    // ring slot of plane p: (p - zs + 2) % 6; slot = u0 u1 u2 [kAUR rows], I p [kAIR rows]
-    auto slot = [&](int p) { return sm + ((p - zs + 2) % 6) * kASlot; };
+    // ring of 6 slots, each u0 u1 u2 [kAUR rows], I p [kAIR rows]; q[i] holds plane
+    // z - 2 + i while plane z is computed (rotated once per plane)
+    float* q[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q[i] = sm + i * kASlot;
     // this thread's 16-byte copies of every plane: source (plane 0), slot offset
     const float* csrc[kAPer];
     int cdst[kAPer];
@@ -170,8 +173,7 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
         csrc[j] = cok[j] ? base + (long long)yy * g.P + xx : base;
         cdst[j] = i < kAChunks ? dst : -1;
     }
-    auto load_plane = [&](int p) {
-        float* d = slot(p);
+    auto load_plane = [&](float* d, int p) {
         const bool zin = p >= 0 && p < g.nz;
         const long long zo = zin ? (long long)p * g.slab : 0;
 #pragma unroll
@@ -184,19 +186,26 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     const float dtrho = dt * rho;
     const int ui = (ty + 1) * kAW + tx + 4;  // node in a u plane
     float dmax = 0.f;
-    for (int p = zs - 2; p <= zs + 2; ++p) load_plane(p);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) load_plane(q[i], zs - 2 + i);
     for (int z = zs; z < ze; ++z) {
-        __syncthreads();  // every read of the slot of plane z-3 is done
-        if (z + 3 <= ze + 1) load_plane(z + 3);
+        __syncthreads();  // every read of the slot of plane z-3 (now q[5]) is done
+        if (z + 3 <= ze + 1) load_plane(q[5], z + 3);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+2 landed
         __syncthreads();
+        const float* sm2 = q[0];
+        const float* sm1 = q[1];
+        const float* s0 = q[2];
+        const float* sp1 = q[3];
+        const float* sp2 = q[4];
+        {
+            float* t0 = q[0];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) q[i] = q[i + 1];
+            q[5] = t0;
+        }
         if (!col_ok) continue;
-        const float* sm2 = slot(z - 2);
-        const float* sm1 = slot(z - 1);
-        const float* s0 = slot(z);
-        const float* sp1 = slot(z + 1);
-        const float* sp2 = slot(z + 2);
         float d[3];
         float du = 0.f;
         {  // axis 0 (z): neighbouring planes
