@@ -95,6 +95,10 @@ def workload(name: str, rank: int = 0):
     raise SystemExit("unknown workload %s" % name)
 
 
+# step-checkpoint stride the workload's configuration names (0: keep the trajectory)
+WORKLOAD_CKPT = {"head128": 5, "mri160": 5}
+
+
 def reduce_max(x: float, world: int, device) -> float:
     """Max over ranks (the slowest rank sets the job time); identity for one rank."""
     if world <= 1:
@@ -566,11 +570,14 @@ def main():
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in tile shapes instead of the autotuner's")
-    ap.add_argument("--ckpt", type=int, default=0,
-                    help="step checkpoint stride (0: keep the whole trajectory)")
+    ap.add_argument("--ckpt", type=int, default=None,
+                    help="step checkpoint stride (0: keep the whole trajectory; default: the "
+                         "workload's, 5 for head128 and mri160, else 0)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.ckpt is None:
+        args.ckpt = WORKLOAD_CKPT.get(args.workload, 0)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "mix64":
