@@ -159,8 +159,9 @@ __device__ __forceinline__ float gw(float g) {
 template <int NDIM>
 __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
-                const float* __restrict__ u, const float* __restrict__ J, float* rec, float* Ihp,
-                float* php, double* partials) {
+                const float* __restrict__ u, const float* __restrict__ J,
+                const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php,
+                double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const int b = blockIdx.y;
@@ -168,6 +169,8 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     const float* IT = slice_of(states, g, ((long long)sl.sT * 2 + 0) * g.B + b);
     const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
     const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
+    // the transport of step T-1 scatters into Ihp / php only beyond the gather window
+    const bool zero_sums = gather_radius(maxdisp, g.nT - 1, g.B, b) > GatherTile<NDIM>::RMAX;
     double data = 0.0, kin = 0.0, res = 0.0;
     // one warp per (z, y) row at a time; a fixed assignment, so fixed sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -195,8 +198,10 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
         }
         res += (double)p * (double)p;
         build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec);
-        slice_of(Ihp, g, b)[o] = 0.f;  // scatter accumulators start at zero
-        slice_of(php, g, b)[o] = 0.f;
+        if (zero_sums) {  // scatter accumulators start at zero
+            slice_of(Ihp, g, b)[o] = 0.f;
+            slice_of(php, g, b)[o] = 0.f;
+        }
     }
     __shared__ double red[3][256];
     red[0][threadIdx.x] = data;
@@ -241,7 +246,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
            const float* __restrict__ u, const float* __restrict__ gI1,
-           const float* __restrict__ gp1, float* rec, float* Ihp, float* php) {
+           const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec,
+           float* Ihp, float* php) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
@@ -249,8 +255,10 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
     build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u, rec);
-    slice_of(Ihp, g, v.b)[o] = 0.f;  // scatter accumulators start at zero
-    slice_of(php, g, v.b)[o] = 0.f;
+    if (gather_radius(maxdisp, g.nT - 1, g.B, v.b) > GatherTile<NDIM>::RMAX) {
+        slice_of(Ihp, g, v.b)[o] = 0.f;  // the first transport scatters into these
+        slice_of(php, g, v.b)[o] = 0.f;
+    }
 }
 
 // 2-D adjoint step t with R = 1, all operands staged: the records (cell, f_y,
@@ -892,31 +900,31 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
-                        const float* states, const float* u, const float* J, float* rec,
-                        float* Ihp, float* php, double* partials, int nblk, double* cost,
-                        cudaStream_t st) {
+                        const float* states, const float* u, const float* J,
+                        const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
+                        double* partials, int nblk, double* cost, cudaStream_t st) {
     const dim3 grid(nblk, g.B);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   rec, Ihp, php, partials));
+                                   maxdisp, rec, Ihp, php, partials));
     else
         META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   rec, Ihp, php, partials));
+                                   maxdisp, rec, Ihp, php, partials));
     META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
     return cudaSuccess;
 }
 
 cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* states, const float* u, const float* gI1,
-                            const float* gp1, float* rec, float* Ihp, float* php,
-                            cudaStream_t st) {
+                            const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp,
+                            float* php, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, rec, Ihp, php));
+                                   gI1, gp1, maxdisp, rec, Ihp, php));
     else
         META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, rec, Ihp, php));
+                                   gI1, gp1, maxdisp, rec, Ihp, php));
     return cudaSuccess;
 }
 

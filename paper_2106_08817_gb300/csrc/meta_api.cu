@@ -121,6 +121,7 @@ Layout make_layout(const meta_problem* pr) {
     g.slab = (long long)g.ny * g.P;
     g.inst = (long long)g.nz * g.slab;
     g.B = pr->batch;
+    g.nT = pr->T;
     g.txw = even_tile(g.nx, kTX, kBX);
     g.ly = even_tile(g.ny, kTA, kBA);
     g.lz = d == 3 ? even_tile(g.nz, kTA, kBA) : kBA;
@@ -523,8 +524,8 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.REC, c.IHP,
-                            c.PHP, c.partials, c.L.nblk, cost, c.st));
+                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.maxdisp,
+                            c.REC, c.IHP, c.PHP, c.partials, c.L.nblk, cost, c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
 }
@@ -756,7 +757,7 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     }
     META_LAUNCH(META_K_ADJ_INIT, c.st,
                 launch_adj_init(c.L.g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, gI1, gp1,
-                                c.REC, c.IHP, c.PHP, c.st));
+                                c.maxdisp, c.REC, c.IHP, c.PHP, c.st));
     return run_adjoint(c, cf, 2, gp0, gI0);
 }
 

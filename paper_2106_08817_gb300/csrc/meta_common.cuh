@@ -58,6 +58,7 @@ struct Geom {
     long long slab;   // ny * P
     long long inst;   // nz * ny * P  (floats per instance slice)
     int B;            // batch
+    int nT;           // time steps T
     int txw;          // x-pass tile width (multiple of kBX, <= kTX)
     int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTA)
     int zct, zca;     // planes per CTA of the 3-D transport / advect (0: heuristic)

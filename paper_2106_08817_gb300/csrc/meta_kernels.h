@@ -42,14 +42,14 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
 // cost[B][3], and the records of step T-1 (state sl.st1, u sl.ut1) from
 // I^_T = I_T - J, p^_T = 0.
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
-                        const float* states, const float* u, const float* J, float* rec,
-                        float* Ihp, float* php, double* partials, int nblk, double* cost,
-                        cudaStream_t st);
+                        const float* states, const float* u, const float* J,
+                        const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
+                        double* partials, int nblk, double* cost, cudaStream_t st);
 // Records of step T-1 from given gradients gI1, gp1 (gp1 nullable: zero).
 cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* states, const float* u, const float* gI1,
-                            const float* gp1, float* rec, float* Ihp, float* php,
-                            cudaStream_t st);
+                            const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp,
+                            float* php, cudaStream_t st);
 // Records of a step (state sl.st1, u sl.ut1) from pitched raw adjoints.
 cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                                const float* states, const float* u, const float* rawI,

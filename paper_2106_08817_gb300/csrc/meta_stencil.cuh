@@ -84,23 +84,6 @@ __device__ __forceinline__ void stage_async(float* dst, const float* __restrict_
     }
 }
 
-// 3-D form: the box z in [zlo, zlo + HZ), y in [ylo, ylo + HY), x in
-// [xlo, xlo + W) of one pitched 3-D slice, stored [HZ][HY][W].
-template <int W, int HY, int HZ>
-__device__ __forceinline__ void stage_async3(float* dst, const float* __restrict__ src,
-                                             const Geom& g, int xlo, int ylo, int zlo) {
-    constexpr int NC4 = W / 4;
-    const int tid = threadIdx.y * kPX + threadIdx.x;
-    for (int i = tid; i < HZ * HY * NC4; i += kPX * kPY) {
-        const int r = i / NC4, c = i - r * NC4;
-        const int zz = r / HY, yy = r - zz * HY;
-        const int z = zlo + zz, y = ylo + yy, x = xlo + 4 * c;
-        const bool ok = (z >= 0 && z < g.nz && y >= 0 && y < g.ny && x >= 0 && x < g.P);
-        cp_async16(dst + r * W + 4 * c,
-                   ok ? src + (long long)z * g.slab + (long long)y * g.P + x : src, ok);
-    }
-}
-
 // Bilinear value (and derivatives) at lower corner p[0] with row stride W;
 // the same expressions as interp / interp_grad below.
 __device__ __forceinline__ float bilin(const float* p, int W, float fy, float fx) {
