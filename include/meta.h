@@ -218,6 +218,16 @@ meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun);
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
                                   unsigned int* fault_bits);
 
+/* Self-test of device-side failure detection: enqueues one small kernel that
+ * waits, exactly as the blur kernels wait for their TMA tiles, on an mbarrier
+ * armed for bytes that never arrive, with the bound limit_ns (in [1 ms, 2 s])
+ * instead of the 2 s of the real waits.  The wait runs out and latches bit 0 in
+ * the status word of ws, which meta_workspace_status then reports as
+ * META_ERR_TIMEOUT; nothing faults, the context stays usable, and clearing the
+ * word restores the workspace. */
+meta_status meta_selftest_timeout(void* ws, size_t ws_bytes, unsigned long long limit_ns,
+                                  void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* meta_status_string(meta_status s);
 

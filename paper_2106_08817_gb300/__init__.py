@@ -93,6 +93,8 @@ def _load():
         lib.meta_timer_start.argtypes = [ctypes.c_int]
         lib.meta_timer_stop.argtypes = [ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int)]
+        lib.meta_selftest_timeout.argtypes = [V, S, ctypes.c_ulonglong, V]
+        lib.meta_selftest_timeout.restype = ctypes.c_int
         T = ctypes.POINTER(_Tuning)
         lib.meta_autotune.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V, T]
         lib.meta_tuning_get.argtypes = [P, T]
@@ -146,6 +148,14 @@ class Workspace:
 
     def ptr(self) -> int:
         return self.buf.data_ptr()
+
+    def selftest_timeout(self, limit_ns: int = 50_000_000) -> None:
+        """Enqueues a bounded device wait that runs out (meta_selftest_timeout): the
+        timeout bit then shows in status()."""
+        rc = _load().meta_selftest_timeout(ctypes.c_void_p(self.ptr()), self.nbytes,
+                                           int(limit_ns), _stream(self.buf.device))
+        if rc:
+            raise MetaError(rc, "meta_selftest_timeout")
 
     def status(self, clear: bool = False) -> int:
         """Device fault bits latched since the last clear (synchronises the stream)."""

@@ -988,6 +988,15 @@ meta_status meta_plan_destroy(meta_plan* plan) {
     return META_OK;
 }
 
+meta_status meta_selftest_timeout(void* ws, size_t ws_bytes, unsigned long long limit_ns,
+                                  void* stream) {
+    if (!ws || ws_bytes < 16 || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return META_ERR_WORKSPACE;
+    if (limit_ns < 1000000ull || limit_ns > 2000000000ull) return META_ERR_INVALID_ARG;
+    return map_status(launch_wait_selftest(static_cast<unsigned int*>(ws), limit_ns,
+                                           static_cast<cudaStream_t>(stream)));
+}
+
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
                                   unsigned int* fault_bits) {
     if (!ws || ws_bytes < 16 || !fault_bits) return META_ERR_INVALID_ARG;

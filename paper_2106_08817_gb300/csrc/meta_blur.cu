@@ -315,6 +315,29 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     }
 }
 
+// Self-test of the failure path: one CTA arms an mbarrier for 16 bytes that no
+// copy ever delivers and waits on it exactly as the blur kernels wait on their
+// TMA tiles, with a short limit.  The wait runs out, latches kFaultTmaTimeout
+// in *fault and the CTA returns; nothing faults and nothing is left in flight.
+__global__ void __launch_bounds__(64) k_wait_selftest(unsigned int* fault, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) mbar_arrive_expect_tx(&bar, 16u);  // 16 bytes that never arrive
+    bool landed = true;
+    if (tid < 32) landed = mbar_wait_bounded(&bar, 0, fault, limit_ns);
+    if (__syncthreads_or(!landed)) return;
+}
+
+cudaError_t launch_wait_selftest(unsigned int* fault, unsigned long long limit_ns, cudaStream_t st) {
+    k_wait_selftest<<<1, 64, 0, st>>>(fault, limit_ns);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launchers
 
 size_t xpass_smem(int ndim, bool gradp, int txw, int r4) {

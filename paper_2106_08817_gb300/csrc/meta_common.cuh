@@ -207,16 +207,17 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// Bounded wait on phase `parity`: gives up after ~2 s (or 2^24 polls), latches
-// kFaultTmaTimeout in *fault and returns false.  A TMA copy that completes
-// normally takes microseconds.
+// Bounded wait on phase `parity`: gives up after limit_ns (2 s by default; or
+// 2^24 polls), latches kFaultTmaTimeout in *fault and returns false.  A TMA
+// copy that completes normally takes microseconds.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  unsigned int* fault) {
+                                                  unsigned int* fault,
+                                                  uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0; it < (1u << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 15u) == 15u && globaltimer_ns() - t0 > 2000000000ull) break;
+        if ((it & 15u) == 15u && globaltimer_ns() - t0 > limit_ns) break;
     }
     atomicOr(fault, kFaultTmaTimeout);
     return false;

@@ -9,6 +9,10 @@ namespace meta {
 size_t xpass_smem(int ndim, bool gradp, int txw, int r4);
 size_t strided_smem(int len, int kp);
 
+// Failure-path self-test: a bounded mbarrier wait that runs out after limit_ns
+// and latches the timeout bit in *fault.
+cudaError_t launch_wait_selftest(unsigned int* fault, unsigned long long limit_ns, cudaStream_t st);
+
 // x-pass.  gradp: reads I slice (sliceI + b) with a one-voxel y/z halo and p
 // slice (sliceP + b) through tmI / tmP, writes NDIM component slices
 // out_slice0 + a*B + b.  Plain: reads slice sliceI + s through tmI and writes

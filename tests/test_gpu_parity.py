@@ -6,6 +6,8 @@ images in [0, 1]; dL/dp0 relative L2 <= 1e-3; the three cost terms relative
 the workloads and random smooth fields on ragged shapes that span several
 tiles (x tiles are 128 wide, strided tiles 128 long, pointwise tiles 32 x 8).
 """
+import ctypes
+
 import numpy as np
 import pytest
 from scipy import ndimage
@@ -298,6 +300,32 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
     assert torch.equal(c0, c2) and torch.equal(g0, g2)
     assert torch.equal(c0, plan.cost) and torch.equal(g0, plan.grad)
     assert plan.ws.status() & 1 == 0
+
+
+def test_device_wait_timeout_is_reported_and_cleared(meta):
+    """Failure detection without a fault: a bounded device wait that nothing
+    satisfies runs out (50 ms), latches the timeout bit, the status call reports
+    it, and after clearing it the same workspace runs a call normally."""
+    dims, B, T, sigma = (37, 45), 1, 3, 2.0
+    ws = meta.Workspace(dims, B, T, sigma)
+    assert ws.status(clear=True) == 0
+    ws.selftest_timeout(50_000_000)
+    assert ws.status() & 1 == 1
+    lib = meta._load()
+    bits = ctypes.c_uint(0)
+    rc = lib.meta_workspace_status(ctypes.c_void_p(ws.ptr()), ws.nbytes, 1,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                   ctypes.byref(bits))
+    assert rc == 5 and bits.value & 1  # META_ERR_TIMEOUT, then cleared
+    assert ws.status() == 0
+    I0, _ = phantoms.random_fields(131, B, dims)
+    J, _ = phantoms.random_fields(132, B, dims)
+    c, g = meta.cost_and_grad(cuda(I0), cuda(J), cuda(np.zeros((B,) + dims)), T, sigma, 0.1, 1.0,
+                              1e-3, workspace=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0 and torch.isfinite(g).all()
+    with pytest.raises(meta.MetaError):
+        ws.selftest_timeout(10)  # below the 1 ms floor
 
 
 def test_results_are_deterministic(meta):
