@@ -140,6 +140,22 @@ def test_cost_and_grad_ragged_3d(meta, dims, B, T, sigma):
                     np.array([1.0, 1.1][:B]), np.array([1e-3, 1e-2][:B]))
 
 
+@pytest.mark.parametrize("dims,T,sigma", [((2, 4099), 3, 1.5), ((3000, 3), 2, 2.0),
+                                          ((2, 3, 700), 2, 1.0), ((500, 2, 3), 2, 1.0),
+                                          ((3, 129, 2), 3, 1.2)])
+def test_extreme_aspect_ratios(meta, dims, T, sigma):
+    """Images 2-3 voxels wide along some axis and thousands long along another: the
+    shortest blur tiles, marching kernels with fewer than 32 columns or 2 rows,
+    pitch padding on narrow rows; forward and cost / gradient against the oracle."""
+    B = 2
+    I0, _ = phantoms.random_fields(141, B, dims)
+    J, _ = phantoms.random_fields(142, B, dims)
+    p0 = smooth_p(143, (B,) + dims, 20.0, s=1.0)
+    check_forward(meta, I0, p0, T, sigma, [0.1, 0.0], [1.0, 1.3])
+    check_cost_grad(meta, I0, J, p0, T, sigma, np.array([0.1, 0.0]), np.array([1.0, 1.3]),
+                    np.array([1e-3, 1e-2]))
+
+
 @pytest.mark.parametrize("dims,seed,scale,T,sigma,mu,rho,lam", [
     ((70, 33), 21, 200.0, 5, 3.0, 0.2, 0.8, 1e-2),     # per-step |d|: .2 1.6 4.3 8.1 17
     ((14, 16, 18), 31, 300.0, 4, 1.5, 0.1, 1.0, 1e-3),  # per-step |d|: .3 1.8 4.8 17
