@@ -264,14 +264,29 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
 #pragma unroll
     for (int j = 0; j < kBA; ++j) acc[j] = 0.f;
     if constexpr (KC > 0) {
-        float win[8 * KC + kBA];
+        // outputs in pairs (2i, 2i+1): tap k reads inputs (2i+k, 2i+k+1), an
+        // even-aligned pair for even k and an odd-aligned one for odd k; each
+        // lane is the scalar fmaf of the other branch, in the same order
+        constexpr int NW = 8 * KC + kBA;
+        float2 ev[NW / 2], od[NW / 2 - 1];
 #pragma unroll
-        for (int q = 0; q < 8 * KC + kBA; ++q) win[q] = src[q * kTXS];
+        for (int m = 0; m < NW / 2; ++m) ev[m] = make_float2(src[(2 * m) * kTXS], src[(2 * m + 1) * kTXS]);
+#pragma unroll
+        for (int m = 0; m < NW / 2 - 1; ++m) od[m] = make_float2(ev[m].y, ev[m + 1].x);
+        float2 a2[kBA / 2];
+#pragma unroll
+        for (int i = 0; i < kBA / 2; ++i) a2[i] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 8 * KC; ++k) {
-            const float wt = taps.w[k];
+            const float2 wt = make_float2(taps.w[k], taps.w[k]);
 #pragma unroll
-            for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + k], acc[j]);
+            for (int i = 0; i < kBA / 2; ++i)
+                a2[i] = ffma2(wt, (k & 1) ? od[i + (k >> 1)] : ev[i + (k >> 1)], a2[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kBA / 2; ++i) {
+            acc[2 * i] = a2[i].x;
+            acc[2 * i + 1] = a2[i].y;
         }
     } else {
         float cur[kBA];

@@ -168,6 +168,18 @@ __device__ __forceinline__ Foot1 foot1(int c, float d, int n) {
 }
 
 // ----------------------------------------------------------- PTX helpers
+// Two independent FP32 fused multiply-adds in one instruction (fma.rn.f32x2,
+// sm_100 and later): lane k of the result is fmaf(a.k, b.k, c.k), rounded
+// exactly as the scalar fmaf.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&d);
+}
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
