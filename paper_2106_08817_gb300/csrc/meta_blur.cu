@@ -157,20 +157,32 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
 #pragma unroll
         for (int j = 0; j < kBX; ++j) acc[j] = 0.f;
         if constexpr (KC > 0) {
-            float win[8 * KC + 8];
+            // outputs in pairs (2i, 2i+1) with packed FMAs over even- and
+            // odd-aligned input pairs (per lane the scalar fmaf, same order)
+            constexpr int NW = 8 * KC + 8;
+            float2 ev[NW / 2], od[NW / 2 - 1];
 #pragma unroll
             for (int q = 0; q < 2 * KC + 2; ++q) {
                 const float4 v = lds4(src + 4 * q);
-                win[4 * q] = v.x;
-                win[4 * q + 1] = v.y;
-                win[4 * q + 2] = v.z;
-                win[4 * q + 3] = v.w;
+                ev[2 * q] = make_float2(v.x, v.y);
+                ev[2 * q + 1] = make_float2(v.z, v.w);
             }
 #pragma unroll
-            for (int k = 0; k < 8 * KC; ++k) {
-                const float wt = taps.w[k];
+            for (int m = 0; m < NW / 2 - 1; ++m) od[m] = make_float2(ev[m].y, ev[m + 1].x);
+            float2 a2[kBX / 2];
 #pragma unroll
-                for (int j = 0; j < kBX; ++j) acc[j] = fmaf(wt, win[j + k], acc[j]);
+            for (int i = 0; i < kBX / 2; ++i) a2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 8 * KC; ++k) {
+                const float2 wt = make_float2(taps.w[k], taps.w[k]);
+#pragma unroll
+                for (int i = 0; i < kBX / 2; ++i)
+                    a2[i] = ffma2(wt, (k & 1) ? od[i + (k >> 1)] : ev[i + (k >> 1)], a2[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < kBX / 2; ++i) {
+                acc[2 * i] = a2[i].x;
+                acc[2 * i + 1] = a2[i].y;
             }
         } else {
             float4 c0 = lds4(src), c1 = lds4(src + 4);
