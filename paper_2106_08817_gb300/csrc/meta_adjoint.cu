@@ -310,7 +310,7 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
     if (x >= g.nx || y >= g.ny) return;
     const int me = (ty + 1) * RX + tx + 1;   // region index of the node
     const int mw = (ty + 1) * W + tx + 4;    // window index of the node
-    float accI = 0.f, accP = 0.f;
+    float2 acc = make_float2(0.f, 0.f);  // S^T I^', S^T p~^ (one packed FMA per source)
     // the source at offset (dy, dx) from the node passes weight gw<dy> gw<dx>
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
@@ -321,10 +321,10 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
             if (dy < 0) wy = gw<-1>(q.x); else if (dy > 0) wy = gw<1>(q.x); else wy = gw<0>(q.x);
             if (dx < 0) wx = gw<-1>(q.y); else if (dx > 0) wx = gw<1>(q.y); else wx = gw<0>(q.y);
             const float wgt = wy * wx;
-            accI += wgt * q.z;
-            accP += wgt * q.w;
+            acc = ffma2(make_float2(wgt, wgt), make_float2(q.z, q.w), acc);
         }
     }
+    const float accI = acc.x, accP = acc.y;
     const int o = y * g.P + x;
     Ihpb[o] = accI;
     phpb[o] = accP;
@@ -629,8 +629,8 @@ k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __rest
     const float dt = cf.dt;
     const int mw = (ty + 1) * kMW + tx + 4;   // window index of the node in a plane
     const int me = (ty + 1) * kMRX + tx + 1;  // region index of the node in a plane
-    // running sums of S^T I^' and S^T p~^ at nodes p-1, p, p+1
-    float aIm = 0.f, aPm = 0.f, aI0 = 0.f, aP0 = 0.f, aIp = 0.f, aPp = 0.f;
+    // running sums (S^T I^', S^T p~^) at nodes p-1, p, p+1 (packed FMAs)
+    float2 am = make_float2(0.f, 0.f), a0 = am, ap = am;
     load_plane(zs - 1);
     for (int p = zs - 1; p <= ze; ++p) {
         __syncthreads();  // every read of the slot of plane p-3 and of Q / PP is done
@@ -652,21 +652,18 @@ k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __rest
                 if (dy < 0) wy = gw<-1>(qv.y); else if (dy > 0) wy = gw<1>(qv.y); else wy = gw<0>(qv.y);
                 if (dx < 0) wx = gw<-1>(qv.z); else if (dx > 0) wx = gw<1>(qv.z); else wx = gw<0>(qv.z);
                 const float wyx = wy * wx;
-                const float tI = wyx * qv.w, tP = wyx * PP[i];
+                const float2 tv = fmul2(make_float2(wyx, wyx), make_float2(qv.w, PP[i]));
                 const float wm = gw<1>(qv.x), w0 = gw<0>(qv.x), wp = gw<-1>(qv.x);
-                aIm += wm * tI;
-                aPm += wm * tP;
-                aI0 += w0 * tI;
-                aP0 += w0 * tP;
-                aIp += wp * tI;
-                aPp += wp * tP;
+                am = ffma2(make_float2(wm, wm), tv, am);
+                a0 = ffma2(make_float2(w0, w0), tv, a0);
+                ap = ffma2(make_float2(wp, wp), tv, ap);
             }
         }
         const int z = p - 1;  // complete: planes z-1 .. z+1 added
         if (z >= zs) {
             const long long o = gidx(g, z, y, x);
-            Ihp[(long long)b * g.inst + o] = aIm;
-            php[(long long)b * g.inst + o] = aPm;
+            Ihp[(long long)b * g.inst + o] = am.x;
+            php[(long long)b * g.inst + o] = am.y;
             // y^ from the node's own foot (cell within one voxel of the node)
             const float* c0 = rslot(z);
             const int cell = __float_as_int(c0[mw]);
@@ -707,12 +704,9 @@ k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __rest
                 vh[((long long)a * g.B + b) * g.inst + o] =
                     -dt * (dI[a] * Ihv + dP[a] * pthv) + dT[a];
         }
-        aIm = aI0;
-        aPm = aP0;
-        aI0 = aIp;
-        aP0 = aPp;
-        aIp = 0.f;
-        aPp = 0.f;
+        am = a0;
+        a0 = ap;
+        ap = make_float2(0.f, 0.f);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
