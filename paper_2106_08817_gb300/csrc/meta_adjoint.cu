@@ -11,11 +11,11 @@
 //   step t+1):  the cell and f of the foot of x,  I^'(x),
 //       p~^(x) = p^'(x) (1 - dt div v_t(x)) + dt mu I^'(x),
 //       div^(x) = -dt p~_t(x) p^'(x)
-//   k_adj_transport  Ihp = S^T I^', php = S^T p~^ (gather over the sources
-//       whose foot cell touches the node: fixed order, no atomics) and
+//   k_adj_transport2d / 3d  Ihp = S^T I^', php = S^T p~^ (gather over the
+//       sources whose foot cell touches the node: fixed order, no atomics) and
 //       v^ = -dt y^ + D^T div^, y^ = dI~/dy I^' + dp~/dy p~^ at the node's foot
 //   blur of v^ with K = K^T, scaled by -rho (meta_blur.cu)  ->  m^
-//   k_adj_gradp      p^_t = php + sum_i m^_i D_i I_t,
+//   k_adj_gradp2d / k_adj_gradp<3>  p^_t = php + sum_i m^_i D_i I_t,
 //                    I^_t = Ihp + sum_i D_i^T (m^_i p_t),
 //       then the record of step t-1 (or, at t = 0, the outputs; the cost
 //       gradient adds lambda (2 sum_i (D_i I_0)(K m0)_i + 2 rho p0)).

@@ -10,10 +10,13 @@
 //    column tile with an r-voxel halo is staged by one TMA load; the
 //    out-of-bounds fill of TMA supplies the zero padding of K.
 //
-// Every thread produces 8 consecutive outputs from a register window that
-// slides over shared memory in chunks of 8 taps, so each shared-memory value
-// feeds up to 8 FMAs.  No tensor cores: a banded Toeplitz product of 37 taps
-// over 4-12 bytes per voxel is not a dense contraction.
+// Every thread produces consecutive outputs (8 along x, 16 along a strided
+// axis) from a register window loaded once from shared memory, so each loaded
+// value feeds up to that many FMAs.  With KC chunks of 8 taps known at compile
+// time the outputs are computed in pairs by packed FP32 FMAs (fma.rn.f32x2,
+// each lane the scalar fmaf in the same order).  Tiles split each extent into
+// equal parts (Geom::txw, ly, lz).  No tensor cores: a banded Toeplitz product
+// of 37 taps over 4-12 bytes per voxel is not a dense contraction.
 #include "meta_kernels.h"
 
 namespace meta {

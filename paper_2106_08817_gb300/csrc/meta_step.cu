@@ -3,7 +3,8 @@
 // u_t = K(p_t grad I_t) (v_t = -rho u_t):
 //   k_advect2d / k_advect3d  div v, foot y = x - dt v, bi/trilinear gathers of
 //       I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~, and
-//       the per-instance max displacement (the window of the adjoint).
+//       the per-instance max displacement (the window of the adjoint); 2-D on
+//       staged 32 x 8 tiles, 3-D marching along z through a ring of planes.
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
 //       pitched trajectory.
 #include "meta_stencil.cuh"
