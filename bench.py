@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -211,12 +212,20 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_sources_hash() -> str:
+def code_of(text: str) -> str:
+    """C/CUDA source without comments and with whitespace collapsed (what the
+    compiler sees; comment edits do not change it)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_sources_hash(csrc: str = None) -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2106_08817_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2106_08817_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
