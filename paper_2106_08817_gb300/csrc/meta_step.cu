@@ -41,9 +41,11 @@ k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, flo
     if (p1) p1[ci] = sP[o];
 }
 
-// 2-D advect on a 32 x 8 tile: u staged with a one-voxel halo, I_t and p_t
-// with a four-voxel halo (feet whose cell leaves it read global memory).
+// 2-D advect on a 32 x 16 tile, two rows per thread (y and y + 8): u staged
+// with a one-voxel halo, I_t and p_t with a four-voxel halo (feet whose cell
+// leaves it read global memory).
 constexpr int kAdvHalo = 4;
+constexpr int kAdvTY = 2 * kPY;  // rows per tile
 
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
@@ -51,11 +53,11 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     constexpr int W = kPX + 2 * kAdvHalo;        // 40
-    constexpr int HU = kPY + 2;                  // 10
-    constexpr int HI = kPY + 2 * kAdvHalo;       // 16
+    constexpr int HU = kAdvTY + 2;               // 18
+    constexpr int HI = kAdvTY + 2 * kAdvHalo;    // 24
     __shared__ __align__(16) float sU0[HU * W], sU1[HU * W], sI[HI * W], sP[HI * W];
     const int b = blockIdx.z;
-    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kAdvTY;
     const float* u0 = slice_of(u, g, ((long long)sl.ut * 2 + 0) * g.B + b);
     const float* u1 = slice_of(u, g, ((long long)sl.ut * 2 + 1) * g.B + b);
     const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
@@ -66,18 +68,24 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
     stage_async<W, HI>(sP, pt, g, x0 - kAdvHalo, y0 - kAdvHalo);
     cp_async_wait_all();
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int x = x0 + threadIdx.x;
     float dmax = 0.f;
-    if (x < g.nx && y < g.ny) {
-        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-        const float dtrho = dt * rho;
-        const int ui = (threadIdx.y + 1) * W + threadIdx.x + kAdvHalo;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const float dtrho = dt * rho;
+    float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+    float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int ty = threadIdx.y + rr * kPY;
+        const int y = y0 + ty;
+        if (x >= g.nx || y >= g.ny) continue;
+        const int ui = (ty + 1) * W + threadIdx.x + kAdvHalo;
         const float d0 = disp_of(dtrho, sU0[ui]);
         const float d1 = disp_of(dtrho, sU1[ui]);
         float du = 0.f;
         du += 0.5f * (sU0[ui + (y < g.ny - 1 ? W : 0)] - sU0[ui - (y > 0 ? W : 0)]);
         du += 0.5f * (sU1[ui + (x < g.nx - 1 ? 1 : 0)] - sU1[ui - (x > 0 ? 1 : 0)]);
-        dmax = fmaxf(fabsf(d0), fabsf(d1));
+        dmax = fmaxf(dmax, fmaxf(fabsf(d0), fabsf(d1)));
         const float div = -rho * du;
         const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
         const int ly = fy.i0 - (y0 - kAdvHalo), lx = fx.i0 - (x0 - kAdvHalo);
@@ -91,8 +99,6 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
             pw = bilin(pt + o, g.P, fy.f, fx.f);
         }
         const int o = y * g.P + x;
-        float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
-        float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
         p1[o] = pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
@@ -287,7 +293,7 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk, 0, st, g, c, t, sl, states, u, maxdisp));
+        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B), blk, 0, st, g, c, t, sl, states, u, maxdisp));
     else
     {
         cudaError_t e = cudaFuncSetAttribute(k_advect3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
