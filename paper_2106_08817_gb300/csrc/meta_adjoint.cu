@@ -738,8 +738,8 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
     }
 }
 
-// 2-D adj_gradp on a 32 x 8 tile: m^ (both components), I_t and p_t staged
-// with a one-voxel halo by cp.async.  When the record of step t-1 has R = 1,
+// 2-D adj_gradp on a 32 x 16 tile, two rows per thread (y and y + 8): m^
+// (both components), I_t and p_t staged with a one-voxel halo by cp.async.  When the record of step t-1 has R = 1,
 // u_{t-1} and p_{t-1} are staged too and the record is built from them (the
 // same expressions as build_record).
 __global__ void __launch_bounds__(kPX * kPY)
@@ -749,11 +749,11 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
               float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    constexpr int W = kPX + 8, HR = kPY + 2;
+    constexpr int TY = 2 * kPY, W = kPX + 8, HR = TY + 2;
     __shared__ __align__(16) float sM0[HR * W], sM1[HR * W], sI[HR * W], sP[HR * W];
     __shared__ __align__(16) float sU0[HR * W], sU1[HR * W], sPp[HR * W];
     const int b = blockIdx.z;
-    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * TY;
     const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
     const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     const float* m0 = mh + (long long)b * g.inst;
@@ -774,75 +774,79 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
     }
     cp_async_wait_all();
     __syncthreads();
-    Vox v;
-    v.b = b;
-    v.x = x0 + threadIdx.x;
-    v.y = y0 + threadIdx.y;
-    v.z = 0;
-    v.ok = v.x < g.nx && v.y < g.ny;
-    if (!v.ok) return;
-    const int x = v.x, y = v.y;
-    const int o = y * g.P + x;
-    const long long ob = (long long)b * g.inst + o;
-    const int c = (threadIdx.y + 1) * W + threadIdx.x + 4;
-    float phv = php[ob];
-    float Ihv = Ihp[ob];
-    if (Rprev > GatherTile<2>::RMAX) {
-        Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
-        php[ob] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int ty = threadIdx.y + rr * kPY;
+        Vox v;
+        v.b = b;
+        v.x = x0 + threadIdx.x;
+        v.y = y0 + ty;
+        v.z = 0;
+        v.ok = v.x < g.nx && v.y < g.ny;
+        if (!v.ok) continue;
+        const int x = v.x, y = v.y;
+        const int o = y * g.P + x;
+        const long long ob = (long long)b * g.inst + o;
+        const int c = (ty + 1) * W + threadIdx.x + 4;
+        float phv = php[ob];
+        float Ihv = Ihp[ob];
+        if (Rprev > GatherTile<2>::RMAX) {
+            Ihp[ob] = 0.f;  // the next (earlier) step scatters into these
+            php[ob] = 0.f;
+        }
+        // axis 0 (y): stride W in the staged tile
+        const float g0 = 0.5f * (sI[c + (y < g.ny - 1 ? W : 0)] - sI[c - (y > 0 ? W : 0)]);
+        phv += sM0[c] * g0;
+        {
+            float r = 0.f;
+            if (y >= 1) r += 0.5f * (sM0[c - W] * sP[c - W]);
+            if (y == g.ny - 1) r += 0.5f * (sM0[c] * sP[c]);
+            if (y <= g.ny - 2) r -= 0.5f * (sM0[c + W] * sP[c + W]);
+            if (y == 0) r -= 0.5f * (sM0[c] * sP[c]);
+            Ihv += r;
+        }
+        // axis 1 (x)
+        const float g1 = 0.5f * (sI[c + (x < g.nx - 1 ? 1 : 0)] - sI[c - (x > 0 ? 1 : 0)]);
+        phv += sM1[c] * g1;
+        {
+            float r = 0.f;
+            if (x >= 1) r += 0.5f * (sM1[c - 1] * sP[c - 1]);
+            if (x == g.nx - 1) r += 0.5f * (sM1[c] * sP[c]);
+            if (x <= g.nx - 2) r -= 0.5f * (sM1[c + 1] * sP[c + 1]);
+            if (x == 0) r -= 0.5f * (sM1[c] * sP[c]);
+            Ihv += r;
+        }
+        if (staged_rec) {
+            // record of step t-1 from the staged u_{t-1}, p_{t-1}
+            const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+            const float dtrho = dt * rho;
+            const float d0 = disp_of(dtrho, sU0[c]), d1 = disp_of(dtrho, sU1[c]);
+            float du = 0.f;
+            du = __fadd_rn(du, rn_cdiff(sU0[c + (y < g.ny - 1 ? W : 0)], sU0[c - (y > 0 ? W : 0)]));
+            du = __fadd_rn(du, rn_cdiff(sU1[c + (x < g.nx - 1 ? 1 : 0)], sU1[c - (x > 0 ? 1 : 0)]));
+            const float div = __fmul_rn(-rho, du);
+            const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
+            const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
+            const bool ins[3] = {fy.inside, fx.inside, false};
+            const float pw = rn_bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
+            const long long rsl = (long long)g.B * g.inst;
+            float* r = rec + ob;
+            r[Rec<2>::kCell * rsl] = __int_as_float(pack_cell(off, ins));
+            r[rsl] = fy.f;
+            r[2 * rsl] = fx.f;
+            r[Rec<2>::kI * rsl] = Ihv;
+            r[Rec<2>::kP * rsl] = rn_ptilde_hat(phv, Ihv, dt, mu, div);
+            r[Rec<2>::kD * rsl] = rn_div_hat(dt, pw, phv);
+            continue;
+        }
+        float kg = 0.f;
+        if (t == 0 && mode == 1) {
+            kg += g0 * slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o];
+            kg += g1 * slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o];
+        }
+        gradp_tail<2>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI, rawP,
+                      out0, gI0);
     }
-    // axis 0 (y): stride W in the staged tile
-    const float g0 = 0.5f * (sI[c + (y < g.ny - 1 ? W : 0)] - sI[c - (y > 0 ? W : 0)]);
-    phv += sM0[c] * g0;
-    {
-        float r = 0.f;
-        if (y >= 1) r += 0.5f * (sM0[c - W] * sP[c - W]);
-        if (y == g.ny - 1) r += 0.5f * (sM0[c] * sP[c]);
-        if (y <= g.ny - 2) r -= 0.5f * (sM0[c + W] * sP[c + W]);
-        if (y == 0) r -= 0.5f * (sM0[c] * sP[c]);
-        Ihv += r;
-    }
-    // axis 1 (x)
-    const float g1 = 0.5f * (sI[c + (x < g.nx - 1 ? 1 : 0)] - sI[c - (x > 0 ? 1 : 0)]);
-    phv += sM1[c] * g1;
-    {
-        float r = 0.f;
-        if (x >= 1) r += 0.5f * (sM1[c - 1] * sP[c - 1]);
-        if (x == g.nx - 1) r += 0.5f * (sM1[c] * sP[c]);
-        if (x <= g.nx - 2) r -= 0.5f * (sM1[c + 1] * sP[c + 1]);
-        if (x == 0) r -= 0.5f * (sM1[c] * sP[c]);
-        Ihv += r;
-    }
-    if (staged_rec) {
-        // record of step t-1 from the staged u_{t-1}, p_{t-1}
-        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-        const float dtrho = dt * rho;
-        const float d0 = disp_of(dtrho, sU0[c]), d1 = disp_of(dtrho, sU1[c]);
-        float du = 0.f;
-        du = __fadd_rn(du, rn_cdiff(sU0[c + (y < g.ny - 1 ? W : 0)], sU0[c - (y > 0 ? W : 0)]));
-        du = __fadd_rn(du, rn_cdiff(sU1[c + (x < g.nx - 1 ? 1 : 0)], sU1[c - (x > 0 ? 1 : 0)]));
-        const float div = __fmul_rn(-rho, du);
-        const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
-        const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
-        const bool ins[3] = {fy.inside, fx.inside, false};
-        const float pw = rn_bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);
-        const long long rsl = (long long)g.B * g.inst;
-        float* r = rec + ob;
-        r[Rec<2>::kCell * rsl] = __int_as_float(pack_cell(off, ins));
-        r[rsl] = fy.f;
-        r[2 * rsl] = fx.f;
-        r[Rec<2>::kI * rsl] = Ihv;
-        r[Rec<2>::kP * rsl] = rn_ptilde_hat(phv, Ihv, dt, mu, div);
-        r[Rec<2>::kD * rsl] = rn_div_hat(dt, pw, phv);
-        return;
-    }
-    float kg = 0.f;
-    if (t == 0 && mode == 1) {
-        kg += g0 * slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o];
-        kg += g1 * slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o];
-    }
-    gradp_tail<2>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI, rawP, out0,
-                  gI0);
 }
 
 template <int NDIM>
@@ -964,7 +968,7 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_gradp2d,
-                                   dim3((g.nx + kPX - 1) / kPX, (g.ny + kPY - 1) / kPY, g.B), blk,
+                                   dim3((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B), blk,
                                    0, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
                                    rec, rawI, rawP, out0, gI0));
     else
