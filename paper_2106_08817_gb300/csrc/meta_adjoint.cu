@@ -39,7 +39,7 @@ template <int NDIM>
 struct GatherTile;
 template <>
 struct GatherTile<2> {
-    static constexpr int TX = 32, TY = 8, RMAX = 8;
+    static constexpr int TX = 32, TY = 16, RMAX = 8;
 };
 template <>
 struct GatherTile<3> {
@@ -261,15 +261,15 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     }
 }
 
-// 2-D adjoint step t with R = 1, all operands staged: the records (cell, f_y,
-// f_x, I^', p~^, div^) and I_t, p_t over the tile grown by one voxel, by
-// cp.async.  Each source of the grown tile is packed once into the float4
+// 2-D adjoint step t with R = 1 on a 32 x 16 tile (two rows per thread), all
+// operands staged: the records (cell, f_y, f_x, I^', p~^, div^) and I_t, p_t
+// over the tile grown by one voxel, by cp.async.  Each source of the grown tile is packed once into the float4
 // (g_y, g_x, I^', p~^) (pack_g); each node then sums 9 branch-free products.
 __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const float* rb,
                                                 long long sl, const float* It, const float* pt,
                                                 float* vh0, float* vh1, float* Ihpb,
                                                 float* phpb, float* smem) {
-    constexpr int TX = 32, TY = 8, W = TX + 8, HR = TY + 2, WIN = W * HR;
+    constexpr int TX = 32, TY = 16, W = TX + 8, HR = TY + 2, WIN = W * HR;
     constexpr int RX = TX + 2, RY = TY + 2, NR = RX * RY;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
@@ -306,48 +306,51 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
         sQ[i] = q;
     }
     __syncthreads();
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= g.nx || y >= g.ny) return;
-    const int me = (ty + 1) * RX + tx + 1;   // region index of the node
-    const int mw = (ty + 1) * W + tx + 4;    // window index of the node
-    float2 acc = make_float2(0.f, 0.f);  // S^T I^', S^T p~^ (one packed FMA per source)
-    // the source at offset (dy, dx) from the node passes weight gw<dy> gw<dx>
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
+    for (int rr = 0; rr < 2; ++rr) {  // rows ty and ty + 8 of the tile
+        const int ly = ty + rr * kPY;
+        const int x = x0 + tx, y = y0 + ly;
+        if (x >= g.nx || y >= g.ny) continue;
+        const int me = (ly + 1) * RX + tx + 1;  // region index of the node
+        const int mw = (ly + 1) * W + tx + 4;   // window index of the node
+        float2 acc = make_float2(0.f, 0.f);     // S^T I^', S^T p~^ (one packed FMA per source)
+        // the source at offset (dy, dx) from the node passes weight gw<dy> gw<dx>
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const float4 q = sQ[me + dy * RX + dx];
-            float wy, wx;
-            if (dy < 0) wy = gw<-1>(q.x); else if (dy > 0) wy = gw<1>(q.x); else wy = gw<0>(q.x);
-            if (dx < 0) wx = gw<-1>(q.y); else if (dx > 0) wx = gw<1>(q.y); else wx = gw<0>(q.y);
-            const float wgt = wy * wx;
-            acc = ffma2(make_float2(wgt, wgt), make_float2(q.z, q.w), acc);
+        for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const float4 q = sQ[me + dy * RX + dx];
+                float wy, wx;
+                if (dy < 0) wy = gw<-1>(q.x); else if (dy > 0) wy = gw<1>(q.x); else wy = gw<0>(q.x);
+                if (dx < 0) wx = gw<-1>(q.y); else if (dx > 0) wx = gw<1>(q.y); else wx = gw<0>(q.y);
+                const float wgt = wy * wx;
+                acc = ffma2(make_float2(wgt, wgt), make_float2(q.z, q.w), acc);
+            }
         }
+        const int o = y * g.P + x;
+        Ihpb[o] = acc.x;
+        phpb[o] = acc.y;
+        // y^ from the node's own foot (cell within one voxel of the node)
+        const int cell = __float_as_int(sC[mw]);
+        const float fy = sF0[mw], fx = sF1[mw];
+        const bool iny = (cell >> 24) & 1, inx = (cell >> 25) & 1;
+        const int ci = mw + cell_off(cell, 0) * W + cell_off(cell, 1);
+        float dIy, dIx, dPy, dPx;
+        bilin_grad(sIt + ci, W, fy, fx, iny, inx, &dIy, &dIx);
+        bilin_grad(sPt + ci, W, fy, fx, iny, inx, &dPy, &dPx);
+        const float Ihv = sI[mw], pthv = sP[mw];
+        float dT0 = 0.f, dT1 = 0.f;
+        if (y >= 1) dT0 += 0.5f * sD[mw - W];
+        if (y == g.ny - 1) dT0 += 0.5f * sD[mw];
+        if (y <= g.ny - 2) dT0 -= 0.5f * sD[mw + W];
+        if (y == 0) dT0 -= 0.5f * sD[mw];
+        if (x >= 1) dT1 += 0.5f * sD[mw - 1];
+        if (x == g.nx - 1) dT1 += 0.5f * sD[mw];
+        if (x <= g.nx - 2) dT1 -= 0.5f * sD[mw + 1];
+        if (x == 0) dT1 -= 0.5f * sD[mw];
+        vh0[o] = -dt * (dIy * Ihv + dPy * pthv) + dT0;
+        vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
     }
-    const float accI = acc.x, accP = acc.y;
-    const int o = y * g.P + x;
-    Ihpb[o] = accI;
-    phpb[o] = accP;
-    // y^ from the node's own foot (cell within one voxel of the node)
-    const int cell = __float_as_int(sC[mw]);
-    const float fy = sF0[mw], fx = sF1[mw];
-    const bool iny = (cell >> 24) & 1, inx = (cell >> 25) & 1;
-    const int ci = mw + cell_off(cell, 0) * W + cell_off(cell, 1);
-    float dIy, dIx, dPy, dPx;
-    bilin_grad(sIt + ci, W, fy, fx, iny, inx, &dIy, &dIx);
-    bilin_grad(sPt + ci, W, fy, fx, iny, inx, &dPy, &dPx);
-    const float Ihv = sI[mw], pthv = sP[mw];
-    float dT0 = 0.f, dT1 = 0.f;
-    if (y >= 1) dT0 += 0.5f * sD[mw - W];
-    if (y == g.ny - 1) dT0 += 0.5f * sD[mw];
-    if (y <= g.ny - 2) dT0 -= 0.5f * sD[mw + W];
-    if (y == 0) dT0 -= 0.5f * sD[mw];
-    if (x >= 1) dT1 += 0.5f * sD[mw - 1];
-    if (x == g.nx - 1) dT1 += 0.5f * sD[mw];
-    if (x <= g.nx - 2) dT1 -= 0.5f * sD[mw + 1];
-    if (x == 0) dT1 -= 0.5f * sD[mw];
-    vh0[o] = -dt * (dIy * Ihv + dPy * pthv) + dT0;
-    vh1[o] = -dt * (dIx * Ihv + dPx * pthv) + dT1;
 }
 
 // Records of step t from raw adjoints I^_{t+1}, p^_{t+1} (pitched), once the
@@ -489,8 +492,8 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
                   float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    // 8 staged windows of 40 x 10 and 6 x 340 weights (transport_r1_2d)
-    __shared__ __align__(16) float s2[8 * 400 + 6 * 340];
+    // 8 staged windows of 40 x 18 and 34 x 18 packed sources (transport_r1_2d)
+    __shared__ __align__(16) float s2[8 * 720 + 4 * 612];
     using G = GatherTile<2>;
     const int b = blockIdx.z;
     const int R = gather_radius(maxdisp, t, g.B, b);
@@ -503,13 +506,15 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
                         Ihp + (long long)b * g.inst, php + (long long)b * g.inst, s2);
         return;
     }
-    Vox v;
-    v.b = b;
-    v.x = blockIdx.x * G::TX + threadIdx.x;
-    v.y = blockIdx.y * G::TY + threadIdx.y;
-    v.z = 0;
-    if (v.x >= g.nx || v.y >= g.ny) return;
-    transport_node<2>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+    for (int rr = 0; rr < 2; ++rr) {
+        Vox v;
+        v.b = b;
+        v.x = blockIdx.x * G::TX + threadIdx.x;
+        v.y = blockIdx.y * G::TY + threadIdx.y + rr * kPY;
+        v.z = 0;
+        if (v.x >= g.nx || v.y >= g.ny) continue;
+        transport_node<2>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+    }
 }
 
 // 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 8 column of nodes over
