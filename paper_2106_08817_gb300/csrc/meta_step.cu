@@ -114,17 +114,18 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
 }
 
 // 3-D advect: a CTA owns a 32 x 8 column over planes [zs, zs + zc) and
-// marches along z.  Plane p of u (three components, one-voxel y halo) and of
-// I_t, p_t (two-voxel y halo), all with x in [x0 - 4, x0 + 36), is staged by
-// cp.async into a ring of 6 plane slots (plane z + 3 loads while plane z is
-// computed from planes z-2 .. z+2).  Feet whose cell leaves the staged planes
-// read global memory.
-constexpr int kAW = 40, kAUR = 10, kAIR = 12;          // window width, u rows, I/p rows
+// marches along z.  Plane p of u (three components) and of I_t, p_t, with a
+// one-voxel y halo and x in [x0 - 4, x0 + 36), is staged by cp.async into a
+// ring of 4 plane slots (plane z + 2 loads while plane z is computed from
+// planes z-1 .. z+1).  Feet whose cell leaves the staged planes (per-step
+// displacements of a voxel or more) read global memory.
+constexpr int kAW = 40, kAUR = 10, kAIR = 10;          // window width, u rows, I/p rows
 constexpr int kAUS = kAW * kAUR, kAIS = kAW * kAIR;    // floats per staged field plane
 constexpr int kASlot = 3 * kAUS + 2 * kAIS;            // floats per ring slot
 constexpr int kAChunks = (3 * kAUR + 2 * kAIR) * (kAW / 4);
 constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
-constexpr size_t kAdvMarchSmem = (size_t)6 * kASlot * sizeof(float);
+constexpr int kARing = 4;                              // plane slots
+constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float);
 
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states,
@@ -149,11 +150,11 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     const float* ua[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) ua[a] = slice_of(u, g, ((long long)sl.ut * 3 + a) * g.B + b);
-    // ring of 6 slots, each u0 u1 u2 [kAUR rows], I p [kAIR rows]; q[i] holds plane
-    // z - 2 + i while plane z is computed (rotated once per plane)
-    float* q[6];
+    // ring of 4 slots, each u0 u1 u2 I p [kAUR rows]; q[i] holds plane z - 1 + i
+    // while plane z is computed (rotated once per plane)
+    float* q[kARing];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) q[i] = sm + i * kASlot;
+    for (int i = 0; i < kARing; ++i) q[i] = sm + i * kASlot;
     // this thread's 16-byte copies of every plane: source (plane 0), slot offset
     const float* csrc[kAPer];
     int cdst[kAPer];
@@ -172,7 +173,7 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
         } else {
             const int f = (r - 3 * kAUR) / kAIR, row = (r - 3 * kAUR) - f * kAIR;
             base = f == 0 ? It : pt;
-            yy = y0 - 2 + row;
+            yy = y0 - 1 + row;
             dst = 3 * kAUS + f * kAIS + row * kAW + 4 * c;
         }
         const int xx = x0 - 4 + 4 * c;
@@ -194,23 +195,21 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     const int ui = (ty + 1) * kAW + tx + 4;  // node in a u plane
     float dmax = 0.f;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) load_plane(q[i], zs - 2 + i);
+    for (int i = 0; i < 3; ++i) load_plane(q[i], zs - 1 + i);
     for (int z = zs; z < ze; ++z) {
-        __syncthreads();  // every read of the slot of plane z-3 (now q[5]) is done
-        if (z + 3 <= ze + 1) load_plane(q[5], z + 3);
+        __syncthreads();  // every read of the slot of plane z-2 (now q[3]) is done
+        if (z + 2 <= ze) load_plane(q[3], z + 2);
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+2 landed
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+1 landed
         __syncthreads();
-        const float* sm2 = q[0];
-        const float* sm1 = q[1];
-        const float* s0 = q[2];
-        const float* sp1 = q[3];
-        const float* sp2 = q[4];
+        const float* sm1 = q[0];
+        const float* s0 = q[1];
+        const float* sp1 = q[2];
         {
             float* t0 = q[0];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) q[i] = q[i + 1];
-            q[5] = t0;
+            for (int i = 0; i < kARing - 1; ++i) q[i] = q[i + 1];
+            q[kARing - 1] = t0;
         }
         if (!col_ok) continue;
         float d[3];
@@ -235,12 +234,12 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
         for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
         const float div = -rho * du;  // div v, v = -rho u
         const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
-        const int kz = fz.i0 - (z - 2), ky = fy.i0 - (y0 - 2), kx = fx.i0 - (x0 - 4);
+        const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
         float Iw, pw;
-        if (kz >= 0 && kz + 1 < 5 && ky >= 0 && ky + 1 < kAIR && kx >= 0 && kx + 1 < kAW) {
-            // planes z - 2 + kz and z - 1 + kz
-            const float* pl = kz == 0 ? sm2 : (kz == 1 ? sm1 : (kz == 2 ? s0 : sp1));
-            const float* ph = kz == 0 ? sm1 : (kz == 1 ? s0 : (kz == 2 ? sp1 : sp2));
+        if (kz >= 0 && kz + 1 < 3 && ky >= 0 && ky + 1 < kAIR && kx >= 0 && kx + 1 < kAW) {
+            // planes z - 1 + kz and z + kz
+            const float* pl = kz == 0 ? sm1 : s0;
+            const float* ph = kz == 0 ? s0 : sp1;
             const float* lo = pl + 3 * kAUS + ky * kAW + kx;
             const float* hi = ph + 3 * kAUS + ky * kAW + kx;
             Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
