@@ -187,8 +187,8 @@ typedef struct {
 } meta_tuning;
 
 /* Autotuner: times meta_cost_and_grad on these inputs (same arguments) for
- * candidate tile shapes, one field at a time in the order above, keeps the
- * fastest of each, then times recorded plans (meta_plan_create) for the batch
+ * candidate tile shapes (median of five calls after a warm-up), one field at a
+ * time in the order above, keeps the fastest of each, then times recorded plans (meta_plan_create) for the batch
  * split, and records the result for the problem shape in a process-wide table
  * that every later call and plan with that shape uses.  No field changes any
  * result: every output is summed in the same order.  Blocking: synchronises

@@ -603,24 +603,23 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         if (e0) cudaEventDestroy(e0);
         return META_ERR_CUDA;
     }
-    // one warm-up, then the best of three timed calls
+    // one warm-up, then the median of five timed calls
     auto time_it = [&](float* ms) -> meta_status {
         meta_status r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws,
                                            ws_bytes, stream);
         if (r != META_OK) return r;
-        float best = 1e30f;
-        for (int k = 0; k < 3; ++k) {
+        float tk[5];
+        for (int k = 0; k < 5; ++k) {
             if (cudaEventRecord(e0, st) != cudaSuccess) return META_ERR_CUDA;
             r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes,
                                    stream);
             if (r != META_OK) return r;
             if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
                 return META_ERR_CUDA;
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return META_ERR_CUDA;
-            best = t < best ? t : best;
+            if (cudaEventElapsedTime(&tk[k], e0, e1) != cudaSuccess) return META_ERR_CUDA;
         }
-        *ms = best;
+        std::sort(tk, tk + 5);
+        *ms = tk[2];
         return META_OK;
     };
     auto lens = [](int n, int q) {  // equal tiles of at most 48 .. 128
@@ -671,8 +670,8 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
             meta_plan* pl = nullptr;
             res = meta_plan_create(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes, &pl);
             if (res != META_OK) break;
-            float best = 1e30f;
-            for (int k = 0; k < 4 && res == META_OK; ++k) {
+            float tk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < 6 && res == META_OK; ++k) {
                 if (cudaEventRecord(e0, st) != cudaSuccess ||
                     meta_plan_launch(pl, stream) != META_OK ||
                     cudaEventRecord(e1, st) != cudaSuccess ||
@@ -680,10 +679,10 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
                     res = META_ERR_CUDA;
                     break;
                 }
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) res = META_ERR_CUDA;
-                if (k > 0 && ms < best) best = ms;  // launch 0 warms up
+                if (cudaEventElapsedTime(&tk[k], e0, e1) != cudaSuccess) res = META_ERR_CUDA;
             }
+            std::sort(tk + 1, tk + 6);  // launch 0 warms up
+            const float best = tk[3];   // median of the other five
             meta_plan_destroy(pl);
             if (res != META_OK) break;
             ++nbest;
