@@ -1,0 +1,58 @@
+"""Host-side pieces of bench.py that need no GPU: the byte models behind
+`path_roofline`, the source hash that guards the committed ncu traffic, and the
+traffic lookup."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_model_bytes_per_voxel_step():
+    # forward F = 24 + 8 d^2, adjoint A = 48 + 12 d + 8 d^2, recompute F + 4d
+    assert bench.model_bytes_per_voxel_step(2) == 224
+    assert bench.model_bytes_per_voxel_step(3) == 360
+
+
+def test_own_bytes_add_the_recomputed_forward_steps():
+    keep2, keep3 = bench.own_bytes_per_voxel_step(2, 20, 0), bench.own_bytes_per_voxel_step(3, 20, 0)
+    assert (keep2, keep3) == (196.0, 296.0)
+    fwd3 = (bench.bytes_per_voxel("xpass_m", 3) + 2 * bench.bytes_per_voxel("strided_fwd", 3)
+            + bench.bytes_per_voxel("advect", 3))
+    # T = 20, k = 5: segments 0..2 are recomputed (15 of 20 steps), the last is not
+    assert bench.own_bytes_per_voxel_step(3, 20, 5) == pytest.approx(keep3 + 15 / 20 * fwd3)
+    # T = 10, k = 4: segments [0,4), [4,8) recomputed, [8,10) kept: 8 of 10 steps
+    assert bench.own_bytes_per_voxel_step(3, 10, 4) == pytest.approx(keep3 + 8 / 10 * fwd3)
+    # strides of 0, 1 or >= T keep the whole trajectory
+    for k in (0, 1, 20, 25):
+        assert bench.own_bytes_per_voxel_step(3, 20, k) == keep3
+
+
+def test_source_hash_ignores_comments_but_not_code(tmp_path):
+    src = os.path.join(ROOT, "paper_2106_08817_gb300", "csrc")
+    dst = tmp_path / "csrc"
+    shutil.copytree(src, dst)
+    h0 = bench.kernel_sources_hash(str(dst))
+    assert h0 == bench.kernel_sources_hash()
+    f = dst / "meta_blur.cu"
+    text = f.read_text()
+    f.write_text("// an added comment\n" + text.replace("namespace meta {", "namespace meta {  /* x */", 1))
+    assert bench.kernel_sources_hash(str(dst)) == h0
+    f.write_text(text.replace("kBX", "kBX + 0", 1))
+    assert bench.kernel_sources_hash(str(dst)) != h0
+
+
+def test_committed_traffic_is_scaled_by_voxels_and_keyed_by_dimension():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        d = json.load(fh)
+    if d.get("sources_hash") != bench.kernel_sources_hash():
+        pytest.skip("traffic.json was taken on other kernel sources")
+    k2 = d["kernels"]["adj_gather@2"]
+    full = bench.ncu_traffic("adj_gather", 2, k2["voxels_per_launch"])
+    assert full == pytest.approx(k2["dram_bytes_per_launch"])
+    assert bench.ncu_traffic("adj_gather", 2, k2["voxels_per_launch"] // 2) == pytest.approx(full / 2)
+    assert bench.ncu_traffic("no_such_class", 2, 1000) is None
