@@ -75,6 +75,8 @@ def bytes_per_voxel(kclass: str, d: int) -> int:
         "strided_adj": 8 * d,
         "adj_gradp": 36 + 12 * d,      # read m^ (d), I_t, p_t, S^T sums, u_t-1 (d), p_t-1; write record
         "unpack": 16,
+        "deform": 12 * d,              # read u (d), phi_t - Id (d) at the feet; write phi_t+1 - Id
+        "deform_out": 8 * d + 4,       # read phi_T - Id (d); write it (d) and det D phi_T
     }[kclass]
 
 
@@ -300,6 +302,53 @@ def run_reference(args):
     }), flush=True)
 
 
+def measure_deformation(meta, w, I0, p0, mu, rho, ws, ckpt, flush, stream, reps=10):
+    """Forward shooting with the deformation of the grid (meta_shoot_deform) against
+    plain forward shooting, L2 flushed before every call, and the deformation step
+    kernel's algorithmic bandwidth (its own CUDA events) against the HBM peak."""
+    import torch
+    B, N, d = w.batch, w.voxels, w.ndim
+
+    def fwd():
+        meta.shoot_forward(I0, p0, w.T, w.sigma, mu, rho, workspace=ws, ckpt=ckpt)
+
+    def dfm():
+        meta.shoot_deform(I0, p0, w.T, w.sigma, mu, rho, workspace=ws, ckpt=ckpt)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+    ms_fwd, ms_dfm = timed(fwd), timed(dfm)
+    meta.timer_start(1 << 14)
+    for _ in range(reps):
+        flush.zero_()
+        dfm()
+    torch.cuda.synchronize()
+    kt = meta.timer_stop()
+    peak, _ = peaks()
+    out = {"ms_shoot_forward": ms_fwd, "ms_shoot_deform": ms_dfm,
+           "overhead_frac": ms_dfm / ms_fwd - 1.0, "reps": reps}
+    for k in ("deform", "deform_out"):
+        ms, scopes, _ = kt[k]
+        avg = ms / max(scopes, 1)
+        gbps = bytes_per_voxel(k, d) * B * N / (avg * 1e-3) / 1e9
+        out[k] = {"launches": scopes, "avg_us": avg * 1e3,
+                  "bytes_per_voxel": bytes_per_voxel(k, d), "GBps_algorithmic": gbps,
+                  "frac_of_measured_hbm": gbps / peak}
+    return out
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -401,6 +450,11 @@ def run_ours(args):
                                              / 1e9, 1) if v[1] else None}
                for k, v in kt.items() if v[1]}
 
+    # ---- deformation of the grid: forward shooting with phi_T and det D phi_T
+    deformation = None
+    if not args.no_deform:
+        deformation = measure_deformation(meta, w, I0, p0, mu, rho, ws, args.ckpt, flush, stream)
+
     # ---- end to end through the public API: pinned host inputs, H2D + launch + D2H
     hI, hJ, hp = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                   for a in (w.I0, w.J, p0.cpu().numpy()))
@@ -485,6 +539,7 @@ def run_ours(args):
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
             "torch_autograd": torch_cmp,
+            "deformation": deformation,
             "kernels": kernels,
             "device_fault_bits": fault,
             "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
@@ -575,6 +630,8 @@ def main():
     ap.add_argument("--workload", default="ellipses16x256")
     ap.add_argument("--no-torch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-deform", action="store_true",
+                    help="skip the deformation measurement (meta_shoot_deform)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",

@@ -91,6 +91,27 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
                                const float* mu, const float* rho, float* I1, float* p1,
                                void* ws, size_t ws_bytes, void* stream);
 
+/* Forward shooting that also integrates the deformation of the grid (the
+ * deformation grids of Fig. 1-2, obtained by integrating every v_t):
+ *
+ *     phi_0 = Id,   phi_{t+1} = phi_t o (Id - dt v_t),
+ *
+ * composed at the same clamped feet y = x - dt v_t as the image, by the same
+ * bi/trilinear interpolation: phi_{t+1}(x) = S(y) phi_t.  For mu = 0 this is the
+ * map the image is carried by: an image affine in x is transported exactly as
+ * I_T = I_0 o phi_T.
+ *   phi: device float [batch][ndim][(D,) H, W], component a = phi_T(x)_a - x_a
+ *        (axis 0 first), in voxels; may be NULL.
+ *   jac: device float [batch, (D,) H, W] = det D phi_T, with D the central
+ *        difference inside the domain and the one-sided difference on its two
+ *        edge layers per axis (so det D Id = 1 everywhere); may be NULL.
+ * At least one of phi, jac is not NULL (else META_ERR_INVALID_ARG).  I1, p1 as
+ * in meta_shoot_forward, and the trajectory is left in ws for
+ * meta_shoot_adjoint in the same way.  Same workspace as every other call. */
+meta_status meta_shoot_deform(const meta_problem* prob, const float* I0, const float* p0,
+                              const float* mu, const float* rho, float* I1, float* p1,
+                              float* phi, float* jac, void* ws, size_t ws_bytes, void* stream);
+
 /* Adjoint of the shooting map, run on the trajectory that the last
  * meta_shoot_forward left in ws (same prob, mu, rho).  Given gI1, gp1, the
  * gradient of a scalar with respect to I_T and p_T (gp1 may be NULL: zero),
@@ -245,6 +266,8 @@ enum {
     META_K_STRIDED_ADJ,    /* y (and z) passes of K on v^ */
     META_K_ADJ_GRADP,      /* transpose of m = p grad I */
     META_K_UNPACK,         /* copy I_T, p_T out */
+    META_K_DEFORM,         /* one step of the deformation phi_{t+1} = phi_t o (Id - dt v_t) */
+    META_K_DEFORM_OUT,     /* phi_T - Id and det D phi_T out */
     META_K_COUNT
 };
 

@@ -13,6 +13,8 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``shoot(I0, p0, T, sigma, mu, rho)``    -- states (I_t, p_t), t=0..T, and u_t
 * ``adjoint(I0, p0, gI1, gp1, ...)``      -- gradient of <gI1,I_T>+<gp1,p_T> w.r.t. (I0, p0)
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
+* ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
+* ``jacobian_det(phi)``                   -- det D phi of a map given in coordinates (numpy)
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, dot-product
 transpose identities, finite differences, an independent torch re-implementation).
@@ -177,3 +179,37 @@ def cost_and_grad(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: f
                                         float(rho), float(lam), _ptr(I0), _ptr(J), _ptr(p0),
                                         _ptr(c3), _ptr(g)), "cost_and_grad")
     return c3, g
+
+
+def jacobian_det(phi) -> np.ndarray:
+    """det D phi for a map phi [ndim, *shape] given by its coordinates (axis 0 first).
+    D phi_a / D x_e is numpy.gradient along axis e: the central difference inside,
+    the one-sided difference on the first and last layer (unit spacing)."""
+    phi = _f64(phi)
+    nd = phi.shape[0]
+    A = np.empty(phi.shape[1:] + (nd, nd))
+    for a in range(nd):
+        for e in range(nd):
+            A[..., a, e] = np.gradient(phi[a], axis=e)
+    return np.linalg.det(A)
+
+
+def deformation(I0, p0, T: int, sigma: float, mu: float,
+                rho: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Deformation of the grid along the shot (the deformation grids of Fig. 1-2,
+    obtained by integrating every v_t): phi_0 = Id and phi_{t+1} = phi_t o (Id - dt v_t),
+    each composition evaluated as S(y) phi_t, the interpolation of phi_t (in
+    coordinates) at the clamped foot y of step t, exactly as the image is.
+    Returns (phi_T - Id as [ndim, *shape], det D phi_T)."""
+    I0 = _f64(I0)
+    shp = I0.shape
+    nd = len(shp)
+    _, _, u = shoot(I0, p0, T, sigma, mu, rho, want_u=True)
+    ident = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shp],
+                                 indexing="ij"))
+    phi = ident.copy()
+    dt = 1.0 / T
+    for t in range(T):
+        disp = -dt * (-rho * u[t])  # y - x = -dt v_t, v_t = -rho u_t
+        phi = np.stack([interp(phi[a], disp) for a in range(nd)])
+    return phi - ident, jacobian_det(phi)

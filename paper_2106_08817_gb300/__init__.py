@@ -22,12 +22,13 @@ from typing import Optional, Sequence, Tuple, Union
 import numpy as np
 import torch
 
-__all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_adjoint", "cost_and_grad",
-           "Shoot", "shoot", "library_path", "STATUS", "timer_start", "timer_stop",
-           "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan"]
+__all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoot_adjoint",
+           "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
+           "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
-                  "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack")
+                  "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
+                  "deform_out")
 # kernels launched per timed scope of each class (the cost scope launches two)
 _LAUNCHES_PER_SCOPE = {"cost": 2}
 
@@ -71,6 +72,7 @@ def _load():
         S = ctypes.c_size_t
         lib.meta_workspace_size.argtypes = [P, ctypes.POINTER(S)]
         lib.meta_shoot_forward.argtypes = [P, F, F, F, F, F, F, V, S, V]
+        lib.meta_shoot_deform.argtypes = [P, F, F, F, F, F, F, F, F, V, S, V]
         lib.meta_shoot_adjoint.argtypes = [P, F, F, F, F, F, F, V, S, V]
         lib.meta_cost_and_grad.argtypes = [P, F, F, F, F, F, F, D, F, V, S, V]
         lib.meta_plan_create.argtypes = [P, F, F, F, F, F, F, D, F, V, S,
@@ -103,7 +105,8 @@ def _load():
             getattr(lib, f).restype = ctypes.c_int
         lib.meta_kernel_name.argtypes = [ctypes.c_int]
         lib.meta_kernel_name.restype = ctypes.c_char_p
-        for f in ("meta_workspace_size", "meta_shoot_forward", "meta_shoot_adjoint",
+        for f in ("meta_workspace_size", "meta_shoot_forward", "meta_shoot_deform",
+                  "meta_shoot_adjoint",
                   "meta_cost_and_grad", "meta_workspace_status", "meta_timer_start",
                   "meta_timer_stop"):
             getattr(lib, f).restype = ctypes.c_int
@@ -242,6 +245,38 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
     if sq:
         I1, p1 = I1[0], p1[0]
     return I1, p1, ws
+
+
+def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
+                 workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
+                 ckpt: int = 0, want_phi: bool = True, want_jac: bool = True
+                 ) -> Tuple[torch.Tensor, torch.Tensor, Optional[torch.Tensor],
+                            Optional[torch.Tensor], Workspace]:
+    """Shooting with the deformation of the grid, phi_0 = Id, phi_{t+1} = phi_t o (Id - dt v_t):
+    returns (I_T, p_T, phi_T - Id as [B, ndim, *dims] or None, det D phi_T or None,
+    workspace with the trajectory)."""
+    if not (want_phi or want_jac):
+        raise ValueError("ask for phi, jac or both")
+    I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    B, dev = I0b.shape[0], I0b.device
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
+    mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
+    I1 = torch.empty_like(I0b)
+    p1 = torch.empty_like(I0b)
+    phi = torch.empty((B, nd) + tuple(dims), dtype=torch.float32, device=dev) if want_phi else None
+    jac = torch.empty_like(I0b) if want_jac else None
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
+    rc = _load().meta_shoot_deform(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
+                                   _p(I1), _p(p1), _p(phi), _p(jac), ctypes.c_void_p(ws.ptr()),
+                                   ws.nbytes, _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_shoot_deform")
+    if sq:
+        I1, p1 = I1[0], p1[0]
+        phi = None if phi is None else phi[0]
+        jac = None if jac is None else jac[0]
+    return I1, p1, phi, jac, ws
 
 
 def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Workspace, T: int,

@@ -389,8 +389,11 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
     return META_OK;
 }
 
-// Forward shooting t = 0..T-1 (the initial state is already in slot 0).
-meta_status run_forward(Ctx& c, const Coefs& cf) {
+// Forward shooting t = 0..T-1 (the initial state is already in slot 0).  With
+// wT not null it also integrates the deformation w_t = phi_t - Id, ping-ponged
+// between SV and REC (neither is used by a forward pass), and sets *wT to the
+// buffer that holds w_T.
+meta_status run_forward(Ctx& c, const Coefs& cf, const float** wT = nullptr) {
     const Layout& L = c.L;
     META_TRY(cudaMemsetAsync(c.maxdisp, 0,
                              sizeof(unsigned int) * kMaxdispStride * (size_t)L.T * L.g.B, c.st));
@@ -398,6 +401,13 @@ meta_status run_forward(Ctx& c, const Coefs& cf) {
         const meta_status s = forward_step(c, cf, t, L.state_slot(t, L.seg_of(t)),
                                            L.forward_out_slot(t), L.u_slot(t), true);
         if (s != META_OK) return s;
+        if (wT) {
+            float* wout = (t & 1) ? c.REC : c.SV;
+            const float* win = t == 0 ? nullptr : ((t & 1) ? c.SV : c.REC);
+            META_LAUNCH(META_K_DEFORM, c.st,
+                        launch_deform(L.g, L.ndim, cf, L.u_slot(t), c.u, win, wout, c.st));
+            *wT = wout;
+        }
     }
     return META_OK;
 }
@@ -740,6 +750,30 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
     return META_OK;
 }
 
+meta_status meta_shoot_deform(const meta_problem* prob, const float* I0, const float* p0,
+                              const float* mu, const float* rho, float* I1, float* p1,
+                              float* phi, float* jac, void* ws, size_t ws_bytes, void* stream) {
+    if (!I0 || !p0 || !mu || !rho || (!phi && !jac)) return META_ERR_INVALID_ARG;
+    Ctx c;
+    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const Geom& g = c.L.g;
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    META_LAUNCH(META_K_PACK, c.st,
+                launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
+    const float* wT = nullptr;
+    s = run_forward(c, cf, &wT);
+    if (s != META_OK) return s;
+    META_LAUNCH(META_K_DEFORM_OUT, c.st, launch_deform_out(g, c.L.ndim, wT, phi, jac, c.st));
+    if (I1 || p1) {
+        const size_t slot = (size_t)c.L.final_slot() * 2 * g.B * g.inst;
+        META_LAUNCH(META_K_UNPACK, c.st,
+                    launch_unpack(g, c.L.ndim, c.states + slot,
+                                  c.states + slot + (size_t)g.B * g.inst, I1, p1, c.st));
+    }
+    return META_OK;
+}
+
 meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const float* rho,
                                const float* gI1, const float* gp1, float* gI0, float* gp0,
                                void* ws, size_t ws_bytes, void* stream) {
@@ -1056,7 +1090,8 @@ meta_status meta_timer_stop(float* ms_per_class, int* launches_per_class) {
 const char* meta_kernel_name(int k) {
     static const char* names[META_K_COUNT] = {
         "pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init",
-        "adj_pre", "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack"};
+        "adj_pre", "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack",
+        "deform", "deform_out"};
     return (k >= 0 && k < META_K_COUNT) ? names[k] : "unknown";
 }
 

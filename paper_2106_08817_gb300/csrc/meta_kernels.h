@@ -39,6 +39,14 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
 // Forward step t: reads state slot sl.st and u slot sl.ut, writes slot sl.st1.
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st);
+// Deformation step t: w_{t+1} = (y - x) + S(y) w_t from u slot su, with
+// w = phi - Id in slices a*B + b of win / wout (win NULL: w_t = 0).
+cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const float* u,
+                          const float* win, float* wout, cudaStream_t st);
+// phi - Id (contiguous [B][ndim][N]) and det D phi ([B][N]) from pitched w;
+// either output may be NULL.
+cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* phi, float* jac,
+                              cudaStream_t st);
 // Adjoint (meta_adjoint.cu).  `rec` holds the records of one adjoint step:
 // slice (k * B + b), k = 0 foot cell (int bits), 1..NDIM f per axis, NDIM+1
 // I^', NDIM+2 p~^, NDIM+3 div^.  Ihp / php: the S^T accumulators.

@@ -5,6 +5,7 @@
 //       I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~, and
 //       the per-instance max displacement (the window of the adjoint); 2-D on
 //       staged 32 x 8 tiles, 3-D marching along z through a ring of planes.
+//   k_deform / k_deform_out  the deformation phi_t of the grid and det D phi_T.
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
 //       pitched trajectory.
 #include "meta_stencil.cuh"
@@ -264,6 +265,82 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
 
+// Deformation of the grid (the deformation grids of Fig. 1-2, Sec. 3): phi_0 = Id and
+// phi_{t+1} = phi_t o (Id - dt v_t), i.e. phi_{t+1}(x) = S(y) phi_t at the same
+// clamped foot y as the advect of step t.  Kept as the displacement
+// w_t = phi_t - Id: the multilinear interpolant reproduces Id at a clamped foot,
+// so w_{t+1}(x) = (y - x) + S(y) w_t.  w_t is slice a * B + b of win (NULL at
+// t = 0, where w_0 = 0), w_{t+1} goes to the same slices of wout.
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_deform(Geom g, Coefs cf, int su, const float* __restrict__ u, const float* __restrict__ win,
+         float* __restrict__ wout) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float dtrho = cf.dt * cf.rho[b];
+    const long long o = gidx(g, v.z, v.y, v.x);
+    float d[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a)
+        d[a] = disp_of(dtrho, slice_of(u, g, ((long long)su * NDIM + a) * g.B + b)[o]);
+    const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        float w = (float)(F.f[a].i0 - c[a]) + F.f[a].f;  // y - x on axis a
+        if (win) w += interp<NDIM>(g, F, slice_of(win, g, (long long)a * g.B + b));
+        slice_of(wout, g, (long long)a * g.B + b)[o] = w;
+    }
+}
+
+// The deformation out of the pitched w = phi - Id: phi (contiguous
+// [B][NDIM][N], nullable) = w, and jac (contiguous [B][N], nullable) =
+// det(D phi) = det(Id + D w), D the central difference inside and the
+// one-sided difference at the two edges of each axis.
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_deform_out(Geom g, const float* __restrict__ w, float* __restrict__ phi,
+             float* __restrict__ jac) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    const long long N = (long long)g.nz * g.ny * g.nx;
+    const long long xi = cidx(g, v) - (long long)b * N;  // voxel index in the instance
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    float A[NDIM][NDIM];  // A[a][e] = d phi_a / d x_e
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* wa = slice_of(w, g, (long long)a * g.B + b);
+        if (phi) phi[((long long)b * NDIM + a) * N + xi] = wa[o];
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e) {
+            const long long hi = (c[e] < n[e] - 1) ? s[e] : 0, lo = (c[e] > 0) ? s[e] : 0;
+            const float h = (hi != 0 && lo != 0) ? 0.5f : 1.f;
+            A[a][e] = (a == e ? 1.f : 0.f) + h * (wa[o + hi] - wa[o - lo]);
+        }
+    }
+    if (!jac) return;
+    float det;
+    if constexpr (NDIM == 2) {
+        det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    } else {
+        det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+              A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+              A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    }
+    jac[(long long)b * N + xi] = det;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -303,6 +380,26 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
         META_CHECK_LAUNCH(launch_k(k_advect3d, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc,
                                    states, u, maxdisp));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const float* u,
+                          const float* win, float* wout, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_deform<2>, pgrid<2>(g), blk, 0, st, g, c, su, u, win, wout));
+    else
+        META_CHECK_LAUNCH(launch_k(k_deform<3>, pgrid<3>(g), blk, 0, st, g, c, su, u, win, wout));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* phi, float* jac,
+                              cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_deform_out<2>, pgrid<2>(g), blk, 0, st, g, w, phi, jac));
+    else
+        META_CHECK_LAUNCH(launch_k(k_deform_out<3>, pgrid<3>(g), blk, 0, st, g, w, phi, jac));
     return cudaGetLastError();
 }
 

@@ -137,6 +137,13 @@ def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
                                   need, null) == 1
     assert lib.meta_shoot_adjoint(ctypes.byref(pr), fake, fake, fake, fake, fake, null, fake,
                                   need, null) == 1
+    # deformation: neither phi nor jac asked for, a null input, a short workspace
+    assert lib.meta_shoot_deform(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, null,
+                                 null, fake, need, null) == 1
+    assert lib.meta_shoot_deform(ctypes.byref(pr), null, fake, fake, fake, null, null, fake,
+                                 null, fake, need, null) == 1
+    assert lib.meta_shoot_deform(ctypes.byref(pr), fake, fake, fake, fake, null, null, null,
+                                 fake, fake, need - 1, null) == 3
     # workspace: null, misaligned, too small
     assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
                                   fake, null, need, null) == 3

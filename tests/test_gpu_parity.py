@@ -109,6 +109,75 @@ def test_forward_ragged_3d(meta, dims, B, T, sigma):
     check_forward(meta, I0, p0, T, sigma, [0.2, 0.0][:B], [1.0, 1.3][:B])
 
 
+# ----------------------------------------------------------------- deformation
+# phi_T - Id against the oracle within FWD_ATOL (scaled by max(1, |w|)), the same bar as
+# I_T.  det D phi_T differences w over one or two voxels, so each entry of D phi carries
+# at most twice that error; a 3 x 3 determinant of entries near 1 sums six products of
+# three entries, hence JAC_ATOL = 2 * 3 * FWD_ATOL, rounded up to 1e-3.
+JAC_ATOL = 1e-3
+
+
+def check_deform(meta, I0, p0, T, sigma, mu, rho, ckpt=0):
+    I1, p1, phi, jac, ws = meta.shoot_deform(cuda(I0), cuda(p0), T, sigma, mu, rho, ckpt=ckpt)
+    F1, q1, _ = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho)
+    torch.cuda.synchronize()
+    assert torch.equal(I1, F1) and torch.equal(p1, q1)  # the deformation leaves the shot alone
+    phi, jac = phi.cpu().numpy(), jac.cpu().numpy()
+    moved = 0.0
+    for b in range(I0.shape[0]):
+        pick = lambda v: v[b] if np.ndim(v) else v
+        w, J = oracle.deformation(I0[b], p0[b], T, sigma, pick(mu), pick(rho))
+        assert np.abs(phi[b] - w).max() <= FWD_ATOL * max(1.0, np.abs(w).max()), b
+        assert np.abs(jac[b] - J).max() <= JAC_ATOL, b
+        moved = max(moved, float(np.abs(w).max()))
+    assert ws.status(clear=True) & 1 == 0
+    return phi, jac, moved
+
+
+@pytest.mark.parametrize("dims,B,T,sigma", [((37, 141), 2, 5, 2.3), ((5, 3), 2, 2, 0.7),
+                                            ((9, 13, 135), 2, 3, 1.5), ((21, 6, 10), 1, 4, 2.0)])
+def test_deformation_matches_oracle(meta, dims, B, T, sigma):
+    I0, _ = phantoms.random_fields(15, B, dims)
+    p0 = smooth_p(16, (B,) + dims, 40.0 if len(dims) == 2 else 30.0, s=1.5)
+    mu, rho = [0.2, 0.0][:B], [1.0, 1.4][:B]
+    phi, jac, moved = check_deform(meta, I0, p0, T, sigma, mu, rho)
+    assert moved > 0.25  # the grid moves by a good part of a voxel (up to 2.6 voxels)
+    # with step checkpointing the same launches run on the same data
+    _, _, phi3, jac3, _ = meta.shoot_deform(cuda(I0), cuda(p0), T, sigma, mu, rho, ckpt=2)
+    assert np.array_equal(phi3.cpu().numpy(), phi) and np.array_equal(jac3.cpu().numpy(), jac)
+
+
+def test_deformation_at_zero_momentum_is_identity_bitwise(meta):
+    w = phantoms.disk_pair_64(random_p0=False)
+    _, _, phi, jac, _ = meta.shoot_deform(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho)
+    assert bool((phi == 0).all()) and bool((jac == 1).all())
+    _, _, phi1, jac1, _ = meta.shoot_deform(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho,
+                                            want_jac=False)
+    assert jac1 is None and torch.equal(phi1, phi)
+
+
+@pytest.mark.parametrize("which", ["ellipses16x256", "mri160"])
+def test_lddmm_deformation_carries_an_affine_image_full_size(meta, which):
+    """At the workloads' full sizes (16 x 256^2 sigma 6; 160 x 192 x 160 sigma 6), T = 20,
+    mu = 0: I_T = I_0 o phi_T for an affine I_0, since image and grid are interpolated at
+    the same feet with the same weights.  FP32 bound for |I| <= 1: a step rounds at
+    most 3 times in each of its 3 lerp levels (6e-8 each, not amplified by the convex
+    weights), 5.4e-7 per step and 1.1e-5 over 20 steps."""
+    if which == "ellipses16x256":
+        dims, B, a = (256, 256), 16, (0.5 / 256, -0.4 / 256)
+    else:
+        dims, B, a = (160, 192, 160), 1, (0.3 / 160, -0.25 / 192, 0.35 / 160)
+    X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims], indexing="ij")
+    ramp = 0.45 + sum(ae * Xe for ae, Xe in zip(a, X))
+    I0 = np.broadcast_to(ramp, (B,) + dims).astype(np.float32)
+    p0 = smooth_p(17, (B,) + dims, 20000.0, s=4.0)
+    I1, _, phi, _, _ = meta.shoot_deform(cuda(I0), cuda(p0), 20, 6.0, 0.0, 1.0, want_jac=False)
+    I1, phi = I1.cpu().numpy().astype(np.float64), phi.cpu().numpy().astype(np.float64)
+    carried = 0.45 + sum(ae * (Xe[None] + phi[:, e]) for e, (ae, Xe) in enumerate(zip(a, X)))
+    assert np.abs(I1 - carried).max() <= 2e-5
+    assert np.abs(phi).max() > 0.5  # the grid moves by a voxel or more (2-D: about 5)
+
+
 # ----------------------------------------------------------------- cost + gradient
 
 def test_cost_and_grad_disk64(meta):

@@ -347,3 +347,81 @@ def test_oracle_matches_independent_torch_implementation(dims):
     np.testing.assert_allclose(pT[0].numpy(), pt[-1], atol=1e-11)
     np.testing.assert_allclose(c2[0].numpy(), c, rtol=1e-12)
     np.testing.assert_allclose(g2[0].numpy(), g, atol=1e-12 * np.abs(g).max())
+
+
+# ------------------------------------------------------------- deformation
+
+def _ramp(dims, a, c):
+    """The affine image c + sum_e a[e] x_e (axis 0 first)."""
+    X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims], indexing="ij")
+    return c + sum(ae * Xe for ae, Xe in zip(a, X))
+
+
+@pytest.mark.parametrize("dims", [(14, 11), (7, 9, 8)])
+def test_deformation_at_zero_momentum_is_identity(dims):
+    w, J = oracle.deformation(RNG.random(dims), np.zeros(dims), 5, 1.5, 0.1, 1.0)
+    np.testing.assert_array_equal(w, 0.0)
+    np.testing.assert_array_equal(J, 1.0)
+
+
+@pytest.mark.parametrize("dims", [(17, 13), (9, 8, 10)])
+def test_first_deformation_step_is_the_clamped_foot(dims):
+    """T = 1: phi_1 = Id - dt v_0 clamped to the domain, computed here from u_0 alone."""
+    T, sigma, rho = 1, 1.2, 1.7
+    I0 = RNG.random(dims)
+    p0 = smooth_random(dims, 4.0, seed=3)
+    w, _ = oracle.deformation(I0, p0, T, sigma, 0.0, rho)
+    _, _, u = oracle.shoot(I0, p0, T, sigma, 0.0, rho, want_u=True)
+    X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims], indexing="ij")
+    for a, n in enumerate(dims):
+        y = np.clip(X[a] + rho * u[0, a], 0, n - 1)
+        np.testing.assert_allclose(w[a], y - X[a], atol=1e-13)
+    assert np.abs(w).max() > 0.05  # the test moves the grid
+
+
+@pytest.mark.parametrize("dims,a", [((19, 16), (0.7, -1.3)), ((10, 9, 11), (0.4, -0.9, 1.6))])
+def test_lddmm_carries_an_affine_image_by_the_deformation(dims, a):
+    """mu = 0: I_{t+1} = S(y) I_t and phi_{t+1} = S(y) phi_t share feet and weights, and an
+    affine I_0 commutes with interpolation, so I_T = I_0 o phi_T to rounding.  Fails on a
+    wrong composition order, a sign of the displacement, or swapped components."""
+    T, sigma = 6, 1.5
+    I0 = _ramp(dims, a, 0.3)
+    p0 = smooth_random(dims, 0.6, seed=5)
+    It, _, _ = oracle.shoot(I0, p0, T, sigma, 0.0, 1.0)
+    w, _ = oracle.deformation(I0, p0, T, sigma, 0.0, 1.0)
+    X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims], indexing="ij")
+    carried = 0.3 + sum(ae * (Xe + we) for ae, Xe, we in zip(a, X, w))
+    np.testing.assert_allclose(It[T], carried, atol=1e-12)
+    assert np.abs(It[T] - I0).max() > 0.1  # the image did move
+
+
+def test_jacobian_of_affine_maps_is_their_determinant():
+    r = np.random.default_rng(7)
+    for dims in [(6, 9), (5, 4, 7)]:
+        nd = len(dims)
+        A = r.normal(size=(nd, nd)) + 2 * np.eye(nd)
+        b = r.normal(size=nd)
+        X = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims],
+                                 indexing="ij"))
+        phi = np.einsum("ae,e...->a...", A, X) + b.reshape((nd,) + (1,) * nd)
+        np.testing.assert_allclose(oracle.jacobian_det(phi), np.linalg.det(A), rtol=1e-12)
+
+
+def test_jacobian_of_a_shear_and_of_a_separable_map():
+    """phi = (x0 + s(x1), x1): det = 1 for any s.  phi = (f(x0), g(x1)): det = f' g' with
+    the difference quotients written out (one-sided on the edges)."""
+    n0, n1 = 9, 12
+    X0, X1 = np.meshgrid(np.arange(n0, dtype=float), np.arange(n1, dtype=float), indexing="ij")
+    s = 0.3 * np.sin(0.7 * X1)
+    np.testing.assert_allclose(oracle.jacobian_det(np.stack([X0 + s, X1])), 1.0, atol=1e-14)
+    f = np.cumsum(np.linspace(0.5, 1.5, n0))
+    g = np.sqrt(np.arange(n1, dtype=float) + 1.0)
+
+    def quot(v):
+        q = np.empty_like(v)
+        q[1:-1] = (v[2:] - v[:-2]) / 2
+        q[0], q[-1] = v[1] - v[0], v[-1] - v[-2]
+        return q
+
+    phi = np.stack([np.broadcast_to(f[:, None], (n0, n1)), np.broadcast_to(g[None, :], (n0, n1))])
+    np.testing.assert_allclose(oracle.jacobian_det(phi), np.outer(quot(f), quot(g)), rtol=1e-14)
