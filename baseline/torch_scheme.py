@@ -13,6 +13,8 @@ Scheme (Eq. 3 in the semi-Lagrangian form of Sec. 2.3; cost Eq. 4):
     v = -rho K*(p grad I);  y = x - dt v;  I~ = I(y), p~ = p(y);
     p' = p~ (1 - dt div v);  I' = I~ + dt mu p~;
     L = 1/2 |I_T - J|^2 + lambda [ <m0, K m0> + rho |p0|^2 ],  m0 = p0 grad I_0.
+With p_update = "det" the momentum update is p' = p~ det(Id - dt Dv), Dv_ae = D_e v_a,
+the determinant taken by torch.linalg.det.
 """
 from __future__ import annotations
 
@@ -85,8 +87,17 @@ def sample(fields: torch.Tensor, feet: torch.Tensor) -> torch.Tensor:
                          align_corners=True)
 
 
+def jacobian_factor(v: torch.Tensor, dt: float) -> torch.Tensor:
+    """det(Id - dt Dv) for v [B, nd, *dims], Dv_ae = D_e v_a: [B, *dims]."""
+    nd = v.shape[1]
+    Dv = torch.stack([central_diff(v[:, a]) for a in range(nd)], 1)  # [B, a, e, *dims]
+    eye = torch.eye(nd, dtype=v.dtype, device=v.device).reshape(1, nd, nd, *([1] * nd))
+    M = (eye - dt * Dv).movedim(1, -1).movedim(1, -1)  # [B, *dims, a, e]
+    return torch.linalg.det(M)
+
+
 def shoot(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu: torch.Tensor,
-          rho: torch.Tensor, keep: bool = False):
+          rho: torch.Tensor, keep: bool = False, p_update="div"):
     """I0, p0 [B, *dims]; mu, rho [B].  Returns (I_T, p_T, v_0[, trajectory])."""
     B, dims = I0.shape[0], I0.shape[1:]
     nd = len(dims)
@@ -104,20 +115,22 @@ def shoot(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu: torch.Te
         v = -rho_b.unsqueeze(1) * u
         if v0 is None:
             v0 = u
-        div = divergence(v)
         Ip = sample(torch.stack([I, p], 1), x - dt * v)
         It, pt = Ip[:, 0], Ip[:, 1]
-        p = pt * (1.0 - dt * div)
+        if p_update in ("det", 1):
+            p = pt * jacobian_factor(v, dt)
+        else:
+            p = pt * (1.0 - dt * divergence(v))
         I = It + dt * mu_b * pt
         if keep:
             traj.append((I, p))
     return (I, p, v0, traj) if keep else (I, p, v0)
 
 
-def cost(I0, J, p0, T, sigma, mu, rho, lam) -> torch.Tensor:
+def cost(I0, J, p0, T, sigma, mu, rho, lam, p_update="div") -> torch.Tensor:
     """[B, 3]: data, lambda*kinetic, lambda*rho*residual (Eq. 4)."""
     B, nd = I0.shape[0], I0.dim() - 1
-    IT, _, u0 = shoot(I0, p0, T, sigma, mu, rho)
+    IT, _, u0 = shoot(I0, p0, T, sigma, mu, rho, p_update=p_update)
     m0 = p0.unsqueeze(1) * central_diff(I0)
     red = tuple(range(1, nd + 1))
     data = 0.5 * ((IT - J) ** 2).sum(red)
@@ -126,9 +139,10 @@ def cost(I0, J, p0, T, sigma, mu, rho, lam) -> torch.Tensor:
     return torch.stack([data, lam * kin, lam * rho * res], 1)
 
 
-def cost_and_grad(I0, J, p0, T, sigma, mu, rho, lam) -> Tuple[torch.Tensor, torch.Tensor]:
+def cost_and_grad(I0, J, p0, T, sigma, mu, rho, lam,
+                  p_update="div") -> Tuple[torch.Tensor, torch.Tensor]:
     """Cost [B, 3] and dL/dp0 [B, *dims] by torch.autograd."""
     p = p0.detach().clone().requires_grad_(True)
-    c = cost(I0, J, p, T, sigma, mu, rho, lam)
+    c = cost(I0, J, p, T, sigma, mu, rho, lam, p_update)
     (g,) = torch.autograd.grad(c.sum(), p)
     return c.detach(), g

@@ -92,7 +92,7 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
                                void* ws, size_t ws_bytes, void* stream);
 
 /* Forward shooting that also integrates the deformation of the grid (the
- * deformation grids of Fig. 1-2, obtained by integrating every v_t):
+ * deformation grids of Fig. 1-2, built from all the v_t of the shot):
  *
  *     phi_0 = Id,   phi_{t+1} = phi_t o (Id - dt v_t),
  *

@@ -11,6 +11,7 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``diff(f, axis, transpose=False)``      -- central difference D_axis (or its transpose)
 * ``interp(F, disp, transpose=False)``    -- S(y) F with y = x + disp (or S(y)^T F)
 * ``shoot(I0, p0, T, sigma, mu, rho)``    -- states (I_t, p_t), t=0..T, and u_t
+  (``p_update="det"`` on shoot / adjoint / cost_and_grad: p' = p~ det(Id - dt Dv))
 * ``adjoint(I0, p0, gI1, gp1, ...)``      -- gradient of <gI1,I_T>+<gp1,p_T> w.r.t. (I0, p0)
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
 * ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
@@ -65,12 +66,14 @@ def _load():
         lib.oracle_diff.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_int, _D, _D]
         lib.oracle_interp.argtypes = [ctypes.c_int, _L, _D, ctypes.c_int, _D, _D]
         lib.oracle_shoot.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     _D, _D, _D, _D, _D]
         lib.oracle_adjoint.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       _D, _D, _D, _D, _D, _D]
         lib.oracle_cost_and_grad.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                             _D, _D, _D, _D, _D]
+                                             ctypes.c_int, _D, _D, _D, _D, _D]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         for f in ("oracle_blur", "oracle_diff", "oracle_interp", "oracle_shoot",
@@ -140,8 +143,16 @@ def interp(F, disp, transpose: bool = False) -> np.ndarray:
     return out
 
 
+def _pdet(p_update) -> int:
+    """Momentum update: 0 / "div" = p~ (1 - dt div v), 1 / "det" = p~ det(Id - dt Dv)."""
+    m = {0: 0, 1: 1, "div": 0, "det": 1}
+    if p_update not in m:
+        raise ValueError("p_update must be 0, 1, 'div' or 'det'")
+    return m[p_update]
+
+
 def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
-          want_u: bool = False) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
+          want_u: bool = False, p_update=0) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
     """Returns (I[T+1, ...], p[T+1, ...], u[T, ndim, ...] or None)."""
     I0, p0 = _f64(I0), _f64(p0)
     shp = I0.shape
@@ -149,13 +160,13 @@ def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
     pt = np.empty((T + 1,) + shp)
     ut = np.empty((T, len(shp)) + shp) if want_u else None
     _check(_load().oracle_shoot(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                float(rho), _ptr(I0), _ptr(p0), _ptr(It), _ptr(pt),
-                                _ptr(ut)), "shoot")
+                                float(rho), _pdet(p_update), _ptr(I0), _ptr(p0), _ptr(It),
+                                _ptr(pt), _ptr(ut)), "shoot")
     return It, pt, ut
 
 
 def adjoint(I0, p0, gI1, gp1, T: int, sigma: float, mu: float,
-            rho: float) -> Tuple[np.ndarray, np.ndarray]:
+            rho: float, p_update=0) -> Tuple[np.ndarray, np.ndarray]:
     """Returns (gI0, gp0) for the scalar <gI1, I_T> + <gp1, p_T>."""
     I0, p0, gI1 = _f64(I0), _f64(p0), _f64(gI1)
     gp1 = None if gp1 is None else _f64(gp1)
@@ -163,21 +174,21 @@ def adjoint(I0, p0, gI1, gp1, T: int, sigma: float, mu: float,
     gI0 = np.empty(shp)
     gp0 = np.empty(shp)
     _check(_load().oracle_adjoint(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                  float(rho), _ptr(I0), _ptr(p0), _ptr(gI1), _ptr(gp1),
-                                  _ptr(gI0), _ptr(gp0)), "adjoint")
+                                  float(rho), _pdet(p_update), _ptr(I0), _ptr(p0), _ptr(gI1),
+                                  _ptr(gp1), _ptr(gI0), _ptr(gp0)), "adjoint")
     return gI0, gp0
 
 
 def cost_and_grad(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
-                  want_grad: bool = True) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+                  want_grad: bool = True, p_update=0) -> Tuple[np.ndarray, Optional[np.ndarray]]:
     """Returns (cost3 = [data, lambda*kinetic, lambda*rho*residual], dL/dp0 or None)."""
     I0, J, p0 = _f64(I0), _f64(J), _f64(p0)
     shp = I0.shape
     c3 = np.zeros(3)
     g = np.empty(shp) if want_grad else None
     _check(_load().oracle_cost_and_grad(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                        float(rho), float(lam), _ptr(I0), _ptr(J), _ptr(p0),
-                                        _ptr(c3), _ptr(g)), "cost_and_grad")
+                                        float(rho), float(lam), _pdet(p_update), _ptr(I0),
+                                        _ptr(J), _ptr(p0), _ptr(c3), _ptr(g)), "cost_and_grad")
     return c3, g
 
 
@@ -197,7 +208,7 @@ def jacobian_det(phi) -> np.ndarray:
 def deformation(I0, p0, T: int, sigma: float, mu: float,
                 rho: float) -> Tuple[np.ndarray, np.ndarray]:
     """Deformation of the grid along the shot (the deformation grids of Fig. 1-2,
-    obtained by integrating every v_t): phi_0 = Id and phi_{t+1} = phi_t o (Id - dt v_t),
+    built from all the v_t of the shot): phi_0 = Id and phi_{t+1} = phi_t o (Id - dt v_t),
     each composition evaluated as S(y) phi_t, the interpolation of phi_t (in
     coordinates) at the clamped foot y of step t, exactly as the image is.
     Returns (phi_T - Id as [ndim, *shape], det D phi_T)."""

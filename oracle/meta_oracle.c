@@ -26,6 +26,9 @@
  *       y = x - dt v, clamped to the domain; I~ = I_t(y), p~ = p_t(y) by
  *       multilinear interpolation; p_{t+1} = p~ (1 - dt div v);
  *       I_{t+1} = I~ + dt mu p~.
+ *   - variant of the momentum update (p_update = 1): p_{t+1} = p~ J with
+ *       J = det(Id - dt Dv), Dv_ae = D_e v_a, the Jacobian of the backtrack
+ *       Id - dt v, of which 1 - dt div v is the first-order part.
  *   - cost (Eq. 4): 1/2 sum (I_T - J)^2 + lambda [ sum_i <m0_i, K m0_i>
  *       + rho sum p0^2 ], m0 = p0 grad S.
  *   - gradient: the exact transpose of the discrete scheme above
@@ -233,16 +236,18 @@ static double interp_deriv(const grid_t* g, const foot_t* ft, int ax, const doub
 typedef struct {
     grid_t g;
     int T;
+    int pdet; /* momentum update: 0 = p~ (1 - dt div v), 1 = p~ det(Id - dt Dv) */
     double dt, mu, rho;
     int r;
     double w[OR_MAXTAPS];
 } scheme_t;
 
 static int scheme_init(scheme_t* s, int ndim, const long* dims, int T, double sigma,
-                       double mu, double rho) {
+                       double mu, double rho, int pdet) {
     if (grid_init(&s->g, ndim, dims) != 0) return -1;
-    if (T < 1 || !(mu >= 0.0) || !(rho > 0.0)) return -1;
+    if (T < 1 || !(mu >= 0.0) || !(rho > 0.0) || (pdet != 0 && pdet != 1)) return -1;
     s->T = T;
+    s->pdet = pdet;
     s->dt = 1.0 / (double)T;
     s->mu = mu;
     s->rho = rho;
@@ -255,16 +260,21 @@ typedef struct {
     double* g[3];  /* D_i I_t */
     double* u[3];  /* K (p_t D_i I_t);  v_i = -rho u_i */
     double* div;   /* sum_i D_i v_i */
+    double* dv[3][3]; /* D_e v_a, kept for the det update only */
     double* tmp;
     double* tmp2;
 } stepbuf_t;
 
-static int stepbuf_alloc(stepbuf_t* b, long N, int ndim) {
+static int stepbuf_alloc(stepbuf_t* b, long N, int ndim, int pdet) {
     memset(b, 0, sizeof(*b));
     for (int a = 0; a < ndim; ++a) {
         b->g[a] = (double*)malloc(sizeof(double) * (size_t)N);
         b->u[a] = (double*)malloc(sizeof(double) * (size_t)N);
         if (!b->g[a] || !b->u[a]) return -1;
+        for (int e = 0; pdet && e < ndim; ++e) {
+            b->dv[a][e] = (double*)malloc(sizeof(double) * (size_t)N);
+            if (!b->dv[a][e]) return -1;
+        }
     }
     b->div = (double*)malloc(sizeof(double) * (size_t)N);
     b->tmp = (double*)malloc(sizeof(double) * (size_t)N);
@@ -276,6 +286,7 @@ static void stepbuf_free(stepbuf_t* b) {
     for (int a = 0; a < 3; ++a) {
         free(b->g[a]);
         free(b->u[a]);
+        for (int e = 0; e < 3; ++e) free(b->dv[a][e]);
     }
     free(b->div);
     free(b->tmp);
@@ -295,7 +306,39 @@ static void velocity(const scheme_t* s, const double* I, const double* p, stepbu
         for (long x = 0; x < g->N; ++x) b->tmp[x] = -s->rho * b->u[a][x]; /* v_a */
         diff_axis(g, a, b->tmp, b->tmp2);
         for (long x = 0; x < g->N; ++x) b->div[x] += b->tmp2[x];
+        for (int e = 0; s->pdet && e < g->ndim; ++e) diff_axis(g, e, b->tmp, b->dv[a][e]);
     }
+}
+
+/* M = Id - dt Dv at voxel x; returns det M and its cofactors
+ * cof[a][e] = d det M / d M_ae (the derivative of the determinant). */
+static double jacobian_det(const scheme_t* s, const stepbuf_t* b, long x, double cof[3][3]) {
+    const int d = s->g.ndim;
+    double M[3][3];
+    for (int a = 0; a < d; ++a)
+        for (int e = 0; e < d; ++e) M[a][e] = (a == e ? 1.0 : 0.0) - s->dt * b->dv[a][e][x];
+    if (d == 2) {
+        cof[0][0] = M[1][1];
+        cof[0][1] = -M[1][0];
+        cof[1][0] = -M[0][1];
+        cof[1][1] = M[0][0];
+        return M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int e = 0; e < 3; ++e) {
+            /* minor of (a, e): rows a1 < a2 and columns e1 < e2 other than a and e */
+            const int a1 = a == 0 ? 1 : 0, a2 = a == 2 ? 1 : 2;
+            const int e1 = e == 0 ? 1 : 0, e2 = e == 2 ? 1 : 2;
+            const double minor = M[a1][e1] * M[a2][e2] - M[a1][e2] * M[a2][e1];
+            cof[a][e] = ((a + e) % 2 ? -1.0 : 1.0) * minor;
+        }
+    return M[0][0] * cof[0][0] + M[0][1] * cof[0][1] + M[0][2] * cof[0][2];
+}
+
+/* the factor of p~ in p_{t+1}: 1 - dt div v, or det(Id - dt Dv) */
+static double p_factor(const scheme_t* s, const stepbuf_t* b, long x) {
+    double cof[3][3];
+    return s->pdet ? jacobian_det(s, b, x, cof) : 1.0 - s->dt * b->div[x];
 }
 
 /* displacement of the foot: y - x = -dt v = dt rho u */
@@ -317,7 +360,7 @@ static void step_forward(const scheme_t* s, const double* I, const double* p, st
         foot_of(g, c, disp, &ft);
         double It = interp(g, &ft, I);
         double pt = interp(g, &ft, p);
-        p1[x] = pt * (1.0 - s->dt * b->div[x]);
+        p1[x] = pt * p_factor(s, b, x);
         I1[x] = It + s->dt * s->mu * pt;
     }
 }
@@ -375,19 +418,20 @@ int oracle_interp(int ndim, const long* dims, const double* disp, int transpose,
 }
 
 /* Shooting: states (I_t, p_t), t = 0..T, written to Itraj/ptraj [(T+1)*N];
- * u_traj (nullable) receives u_t = K(p_t grad I_t), [T*ndim*N]. */
+ * u_traj (nullable) receives u_t = K(p_t grad I_t), [T*ndim*N].  pdet selects
+ * the momentum update (0: p~ (1 - dt div v), 1: p~ det(Id - dt Dv)). */
 int oracle_shoot(int ndim, const long* dims, int T, double sigma, double mu, double rho,
-                 const double* I0, const double* p0, double* Itraj, double* ptraj,
+                 int pdet, const double* I0, const double* p0, double* Itraj, double* ptraj,
                  double* utraj) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
-    if (scheme_init(s, ndim, dims, T, sigma, mu, rho) != 0) {
+    if (scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet) != 0) {
         free(s);
         return -1;
     }
     long N = s->g.N;
     stepbuf_t b;
-    if (stepbuf_alloc(&b, N, ndim) != 0) {
+    if (stepbuf_alloc(&b, N, ndim, pdet) != 0) {
         stepbuf_free(&b);
         free(s);
         return -2;
@@ -418,8 +462,12 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
     const double dt = s->dt;
     stepbuf_t b;
     double *pth = NULL, *dh = NULL, *Inew = NULL, *pnew = NULL, *vh[3] = {0, 0, 0};
+    double* dvh[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; /* adjoint of D_e v_a (det update) */
     int rc = -2;
-    if (stepbuf_alloc(&b, N, d) != 0) goto done;
+    if (stepbuf_alloc(&b, N, d, s->pdet) != 0) goto done;
+    for (int a = 0; s->pdet && a < d; ++a)
+        for (int e = 0; e < d; ++e)
+            if (!(dvh[a][e] = (double*)malloc(sizeof(double) * (size_t)N))) goto done;
     pth = (double*)malloc(sizeof(double) * (size_t)N);  /* adjoint of p~ */
     dh = (double*)malloc(sizeof(double) * (size_t)N);   /* adjoint of div v */
     Inew = (double*)malloc(sizeof(double) * (size_t)N);
@@ -432,7 +480,9 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
         const double* p = ptraj + (long)t * N;
         velocity(s, I, p, &b);
 
-        /* pointwise part: I' = I~ + dt mu p~ ; p' = p~ (1 - dt div) */
+        /* pointwise part: I' = I~ + dt mu p~ ; p' = p~ (1 - dt div), or
+         * p' = p~ J with J = det M, M = Id - dt Dv, so that
+         * Dv_hat_ae = (p~ p'_hat) dJ/dDv_ae = -dt (p~ p'_hat) cof(M)_ae */
 #pragma omp parallel for schedule(static)
         for (long x = 0; x < N; ++x) {
             long c[3];
@@ -442,8 +492,16 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
             displacement(s, &b, x, disp);
             foot_of(g, c, disp, &ft);
             double pt = interp(g, &ft, p);
-            pth[x] = ph[x] * (1.0 - dt * b.div[x]) + dt * s->mu * Ih[x];
-            dh[x] = -dt * pt * ph[x];
+            if (s->pdet) {
+                double cof[3][3];
+                const double J = jacobian_det(s, &b, x, cof);
+                pth[x] = ph[x] * J + dt * s->mu * Ih[x];
+                for (int a = 0; a < d; ++a)
+                    for (int e = 0; e < d; ++e) dvh[a][e][x] = -dt * pt * ph[x] * cof[a][e];
+            } else {
+                pth[x] = ph[x] * (1.0 - dt * b.div[x]) + dt * s->mu * Ih[x];
+                dh[x] = -dt * pt * ph[x];
+            }
             /* y = x - dt v, so dy_a/dv_a = -dt; I~ and p~ both depend on y */
             for (int a = 0; a < d; ++a) {
                 double yh = interp_deriv(g, &ft, a, I) * Ih[x] +
@@ -467,10 +525,18 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
                 pnew[q] += wgt * pth[x];
             }
         }
-        /* div = sum_a D_a v_a  ->  v_hat_a += D_a^T div_hat */
+        /* div = sum_a D_a v_a  ->  v_hat_a += D_a^T div_hat;
+         * det update: Dv_ae = D_e v_a  ->  v_hat_a += sum_e D_e^T Dv_hat_ae */
         for (int a = 0; a < d; ++a) {
-            diff_axis_T(g, a, dh, b.tmp);
-            for (long x = 0; x < N; ++x) vh[a][x] += b.tmp[x];
+            if (s->pdet) {
+                for (int e = 0; e < d; ++e) {
+                    diff_axis_T(g, e, dvh[a][e], b.tmp);
+                    for (long x = 0; x < N; ++x) vh[a][x] += b.tmp[x];
+                }
+            } else {
+                diff_axis_T(g, a, dh, b.tmp);
+                for (long x = 0; x < N; ++x) vh[a][x] += b.tmp[x];
+            }
         }
         for (int a = 0; a < d; ++a) {
             /* v_a = -rho u_a, u_a = K m_a  ->  m_hat_a = K^T(-rho v_hat_a), K^T = K */
@@ -492,7 +558,10 @@ done:
     free(dh);
     free(Inew);
     free(pnew);
-    for (int a = 0; a < 3; ++a) free(vh[a]);
+    for (int a = 0; a < 3; ++a) {
+        free(vh[a]);
+        for (int e = 0; e < 3; ++e) free(dvh[a][e]);
+    }
     return rc;
 }
 
@@ -500,11 +569,11 @@ done:
  * gradient of some scalar w.r.t. I_T, p_T; gp1 nullable = 0) returns its
  * gradient w.r.t. I0 (gI0, nullable) and p0 (gp0). */
 int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, double rho,
-                   const double* I0, const double* p0, const double* gI1, const double* gp1,
-                   double* gI0, double* gp0) {
+                   int pdet, const double* I0, const double* p0, const double* gI1,
+                   const double* gp1, double* gI0, double* gp0) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
-    int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho);
+    int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet);
     if (rc != 0) {
         free(s);
         return -1;
@@ -515,7 +584,7 @@ int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, d
     double* Ih = (double*)malloc(sizeof(double) * (size_t)N);
     rc = -2;
     if (It && pt && Ih) {
-        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, I0, p0, It, pt, NULL);
+        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, pdet, I0, p0, It, pt, NULL);
         if (rc == 0) {
             memcpy(Ih, gI1, sizeof(double) * (size_t)N);
             if (gp1)
@@ -535,13 +604,13 @@ int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, d
 
 /* Cost of Eq. 4 and its gradient w.r.t. p0.
  * cost3 = { 1/2 sum (I_T - J)^2, lambda sum_i <m0_i, K m0_i>, lambda rho sum p0^2 }.
- * grad (nullable) = dL/dp0. */
+ * grad (nullable) = dL/dp0.  pdet as in oracle_shoot. */
 int oracle_cost_and_grad(int ndim, const long* dims, int T, double sigma, double mu,
-                         double rho, double lambda, const double* I0, const double* J,
+                         double rho, double lambda, int pdet, const double* I0, const double* J,
                          const double* p0, double* cost3, double* grad) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
-    int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho);
+    int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet);
     if (rc != 0 || !(lambda >= 0.0)) {
         free(s);
         return -1;
@@ -553,10 +622,10 @@ int oracle_cost_and_grad(int ndim, const long* dims, int T, double sigma, double
     double* Ih = (double*)malloc(sizeof(double) * (size_t)N);
     double* ph = (double*)malloc(sizeof(double) * (size_t)N);
     stepbuf_t b;
-    int have_b = stepbuf_alloc(&b, N, ndim) == 0;
+    int have_b = stepbuf_alloc(&b, N, ndim, pdet) == 0;
     rc = -2;
     if (It && pt && Ih && ph && have_b) {
-        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, I0, p0, It, pt, NULL);
+        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, pdet, I0, p0, It, pt, NULL);
         if (rc == 0) {
             const double* IT = It + (long)T * N;
             double data = 0.0, kin = 0.0, res = 0.0;

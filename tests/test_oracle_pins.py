@@ -273,16 +273,17 @@ def _fd_problem(dims, seed):
     return I, J, p
 
 
+@pytest.mark.parametrize("p_update", ["div", "det"])
 @pytest.mark.parametrize("dims,T,sigma", [((16, 16), 5, 1.5), ((8, 8, 8), 4, 1.0)])
-def test_gradient_matches_central_differences(dims, T, sigma):
+def test_gradient_matches_central_differences(dims, T, sigma, p_update):
     I, J, p = _fd_problem(dims, 20)
     args = (T, sigma, 0.25, 1.3, 0.05)
-    _, g = oracle.cost_and_grad(I, J, p, *args)
-    _, _, u = oracle.shoot(I, p, *args[:4], want_u=True)
+    _, g = oracle.cost_and_grad(I, J, p, *args, p_update=p_update)
+    _, _, u = oracle.shoot(I, p, *args[:4], want_u=True, p_update=p_update)
     assert np.abs(u).max() * 1.3 / T > 0.05  # feet well away from grid nodes
 
     def L(q):
-        return oracle.cost_and_grad(I, J, q, *args, want_grad=False)[0].sum()
+        return oracle.cost_and_grad(I, J, q, *args, want_grad=False, p_update=p_update)[0].sum()
 
     r = np.random.default_rng(7)
     for _ in range(3):
@@ -312,7 +313,8 @@ def test_taylor_remainder_is_second_order():
     assert 3.0 < rem[0] / rem[1] < 5.0 and 3.0 < rem[1] / rem[2] < 5.0
 
 
-def test_adjoint_of_shooting_map_dot_product():
+@pytest.mark.parametrize("p_update", ["div", "det"])
+def test_adjoint_of_shooting_map_dot_product(p_update):
     """<gI1, dI_T> + <gp1, dp_T> = <gI0, dI0> + <gp0, dp0> for a tangent (dI0, dp0)."""
     dims = (12, 13)
     I, J, p = _fd_problem(dims, 40)
@@ -320,29 +322,34 @@ def test_adjoint_of_shooting_map_dot_product():
     r = np.random.default_rng(9)
     gI1, gp1 = r.normal(size=dims), r.normal(size=dims)
     dI, dp = r.normal(size=dims), r.normal(size=dims)
-    gI0, gp0 = oracle.adjoint(I, p, gI1, gp1, *args)
+    gI0, gp0 = oracle.adjoint(I, p, gI1, gp1, *args, p_update=p_update)
     eps = 1e-6
-    Ap = oracle.shoot(I + eps * dI, p + eps * dp, *args)
-    Am = oracle.shoot(I - eps * dI, p - eps * dp, *args)
+    Ap = oracle.shoot(I + eps * dI, p + eps * dp, *args, p_update=p_update)
+    Am = oracle.shoot(I - eps * dI, p - eps * dp, *args, p_update=p_update)
     tang = ((Ap[0][-1] - Am[0][-1]) * gI1).sum() + ((Ap[1][-1] - Am[1][-1]) * gp1).sum()
     tang /= 2 * eps
     adj = (gI0 * dI).sum() + (gp0 * dp).sum()
     assert abs(tang - adj) < 1e-6 * abs(adj)
 
 
+@pytest.mark.parametrize("p_update", ["div", "det"])
 @pytest.mark.parametrize("dims", [(16, 20), (9, 11, 10)])
-def test_oracle_matches_independent_torch_implementation(dims):
-    """grid_sample + conv + torch.autograd in FP64 reproduce the oracle to ~1e-13."""
+def test_oracle_matches_independent_torch_implementation(dims, p_update):
+    """grid_sample + conv + torch.autograd in FP64 reproduce the oracle to ~1e-13; for the
+    det update torch takes det(Id - dt Dv) by torch.linalg.det (LU) and differentiates it
+    by autograd, the oracle by its cofactor expansion and a hand-written transpose."""
     torch = pytest.importorskip("torch")
     from baseline import torch_scheme as ts
     I, J, p = _fd_problem(dims, 50)
     T, sig, mu, rho, lam = 5, 1.5, 0.3, 1.7, 1e-2
-    c, g = oracle.cost_and_grad(I, J, p, T, sig, mu, rho, lam)
-    It, pt, _ = oracle.shoot(I, p, T, sig, mu, rho)
+    if p_update == "det":
+        p = 4.0 * p  # larger Dv, so that the second- and third-order terms of det matter
+    c, g = oracle.cost_and_grad(I, J, p, T, sig, mu, rho, lam, p_update=p_update)
+    It, pt, _ = oracle.shoot(I, p, T, sig, mu, rho, p_update=p_update)
     t = lambda a: torch.tensor(np.asarray(a)[None], dtype=torch.float64)
     tmu, trho = torch.tensor([mu], dtype=torch.float64), torch.tensor([rho], dtype=torch.float64)
-    c2, g2 = ts.cost_and_grad(t(I), t(J), t(p), T, sig, tmu, trho, lam)
-    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, tmu, trho)
+    c2, g2 = ts.cost_and_grad(t(I), t(J), t(p), T, sig, tmu, trho, lam, p_update=p_update)
+    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, tmu, trho, p_update=p_update)
     np.testing.assert_allclose(IT[0].numpy(), It[-1], atol=1e-12)
     np.testing.assert_allclose(pT[0].numpy(), pt[-1], atol=1e-11)
     np.testing.assert_allclose(c2[0].numpy(), c, rtol=1e-12)
@@ -425,3 +432,47 @@ def test_jacobian_of_a_shear_and_of_a_separable_map():
 
     phi = np.stack([np.broadcast_to(f[:, None], (n0, n1)), np.broadcast_to(g[None, :], (n0, n1))])
     np.testing.assert_allclose(oracle.jacobian_det(phi), np.outer(quot(f), quot(g)), rtol=1e-14)
+
+
+# ------------------------------------------------------- det momentum update
+
+@pytest.mark.parametrize("dims", [(15, 13), (8, 9, 7)])
+def test_det_update_differs_from_div_update_by_the_higher_order_terms(dims):
+    """T = 1 from the same (I0, p0): both updates share p~, so
+    p_1^det / p_1^div = det(Id - dt Dv) / (1 - dt tr Dv), with Dv from u_0 by central
+    differences written here and the determinant by numpy.linalg.det."""
+    T, sigma, mu, rho = 1, 1.3, 0.1, 1.4
+    I0 = RNG.random(dims)
+    p0 = smooth_random(dims, 60.0, seed=8)
+    _, pa, u = oracle.shoot(I0, p0, T, sigma, mu, rho, want_u=True)
+    _, pb, _ = oracle.shoot(I0, p0, T, sigma, mu, rho, p_update="det")
+    nd = len(dims)
+
+    def D(f, e):  # central difference along e, edge neighbour replicated
+        q = np.concatenate([np.take(f, [0], e), f, np.take(f, [-1], e)], e)
+        n = f.shape[e]
+        return 0.5 * (np.take(q, range(2, n + 2), e) - np.take(q, range(0, n), e))
+
+    v = -rho * u[0]
+    A = np.stack([np.stack([D(v[a], e) for e in range(nd)], -1) for a in range(nd)], -2)
+    M = np.eye(nd) - A / T
+    ratio = np.linalg.det(M) / (1.0 - np.trace(A, axis1=-2, axis2=-1) / T)
+    big = np.abs(pa[1]) > 1e-3 * np.abs(pa[1]).max()
+    np.testing.assert_allclose(pb[1][big] / pa[1][big], ratio[big], rtol=1e-10)
+    assert np.abs(ratio - 1).max() > 1e-3  # the higher-order terms are not negligible here
+
+
+@pytest.mark.parametrize("dims", [(14, 12), (8, 7, 9)])
+def test_det_update_equals_div_update_for_an_image_varying_along_one_axis(dims):
+    """I_0 = f(x_0): in the first step m and v have only their axis-0 component, Dv has
+    one non-zero row, and det(Id - dt Dv) = 1 - dt D_0 v_0 = 1 - dt div v.  (Later steps
+    mix the axes: I_1 = f(x_0 - dt v_0(x)) varies along every axis.)"""
+    x0 = np.arange(dims[0], dtype=np.float64)
+    I0 = np.broadcast_to((0.5 + 0.4 * np.sin(0.5 * x0)).reshape((-1,) + (1,) * (len(dims) - 1)),
+                         dims).copy()
+    p0 = smooth_random(dims, 30.0, seed=9)
+    a = oracle.shoot(I0, p0, 1, 1.5, 0.2, 1.0)
+    b = oracle.shoot(I0, p0, 1, 1.5, 0.2, 1.0, p_update="det")
+    np.testing.assert_array_equal(b[0], a[0])
+    np.testing.assert_allclose(b[1], a[1], atol=1e-13 * np.abs(a[1]).max())
+    assert np.abs(a[1][1] - p0).max() > 1e-3  # the momentum did change
