@@ -77,6 +77,7 @@ def bytes_per_voxel(kclass: str, d: int) -> int:
         "unpack": 16,
         "deform": 12 * d,              # read u (d), phi_t - Id (d) at the feet; write phi_t+1 - Id
         "deform_out": 8 * d + 4,       # read phi_T - Id (d); write it (d) and det D phi_T
+        "adj_jac": 4 + 12 * d,         # det update: read div^, u (d), v^ (d); write v^ (d)
     }[kclass]
 
 
@@ -349,6 +350,52 @@ def measure_deformation(meta, w, I0, p0, mu, rho, ws, ckpt, flush, stream, reps=
     return out
 
 
+def measure_det_update(meta, w, I0, J, p0, mu, rho, lam, ws, ckpt, flush, stream, reps=10):
+    """cost_and_grad with the exact-Jacobian momentum update p' = p~ det(Id - dt Dv)
+    (eager calls, L2 flushed before each), against the same eager call with the
+    default update, and the extra adjoint kernel's algorithmic bandwidth."""
+    import torch
+    B, N, d, T = w.batch, w.voxels, w.ndim, w.T
+    out = (torch.empty((B, 3), dtype=torch.float64, device=I0.device), torch.empty_like(p0))
+
+    def call(pu):
+        return lambda: meta.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam, workspace=ws,
+                                          out=out, ckpt=ckpt, p_update=pu)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+    ms_div, ms_det = timed(call("div")), timed(call("det"))
+    meta.timer_start(1 << 14)
+    for _ in range(reps):
+        flush.zero_()
+        call("det")()
+    torch.cuda.synchronize()
+    kt = meta.timer_stop()
+    peak, _ = peaks()
+    ms, scopes, _ = kt["adj_jac"]
+    avg = ms / max(scopes, 1)
+    gbps = bytes_per_voxel("adj_jac", d) * B * N / (avg * 1e-3) / 1e9
+    vs = B * N * T / (ms_det * 1e-3)
+    return {"ms_cost_and_grad_det": ms_det, "ms_cost_and_grad_div_eager": ms_div,
+            "value": vs, "unit": UNIT, "overhead_frac": ms_det / ms_div - 1.0, "reps": reps,
+            "model_frac": vs * model_bytes_per_voxel_step(d) / 1e9 / peak,
+            "adj_jac": {"launches": scopes, "avg_us": avg * 1e3,
+                        "bytes_per_voxel": bytes_per_voxel("adj_jac", d),
+                        "GBps_algorithmic": gbps, "frac_of_measured_hbm": gbps / peak}}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -455,6 +502,12 @@ def run_ours(args):
     if not args.no_deform:
         deformation = measure_deformation(meta, w, I0, p0, mu, rho, ws, args.ckpt, flush, stream)
 
+    # ---- the exact-Jacobian momentum update (cost_and_grad, eager)
+    det_update = None
+    if not args.no_det:
+        det_update = measure_det_update(meta, w, I0, J, p0, mu, rho, lam, ws, args.ckpt, flush,
+                                        stream)
+
     # ---- end to end through the public API: pinned host inputs, H2D + launch + D2H
     hI, hJ, hp = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                   for a in (w.I0, w.J, p0.cpu().numpy()))
@@ -540,6 +593,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "torch_autograd": torch_cmp,
             "deformation": deformation,
+            "det_update": det_update,
             "kernels": kernels,
             "device_fault_bits": fault,
             "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
@@ -632,6 +686,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-deform", action="store_true",
                     help="skip the deformation measurement (meta_shoot_deform)")
+    ap.add_argument("--no-det", action="store_true",
+                    help="skip the measurement of the det momentum update")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",

@@ -73,7 +73,15 @@ typedef struct {
                         k-th state and recompute each segment of k steps during the
                         adjoint (step checkpointing), trading k forward steps of
                         compute per segment for memory */
+    int p_update;    /* momentum update of a step: META_P_UPDATE_DIV (0, the default),
+                        p' = p~ (1 - dt div v), the first-order Jacobian of the backtrack
+                        (Eq. 9); or META_P_UPDATE_DET (1), p' = p~ det(Id - dt Dv), its
+                        exact Jacobian, Dv_ae = D_e v_a by central differences.  Every
+                        call on one trajectory must use the same value. */
 } meta_problem;
+
+#define META_P_UPDATE_DIV 0
+#define META_P_UPDATE_DET 1
 
 /* Bytes of workspace that every call below needs for this problem (enough
  * for any batch split of meta_plan_create as well).
@@ -268,6 +276,7 @@ enum {
     META_K_UNPACK,         /* copy I_T, p_T out */
     META_K_DEFORM,         /* one step of the deformation phi_{t+1} = phi_t o (Id - dt v_t) */
     META_K_DEFORM_OUT,     /* phi_T - Id and det D phi_T out */
+    META_K_ADJ_JAC,        /* META_P_UPDATE_DET: the higher-order part of the adjoint of det */
     META_K_COUNT
 };
 

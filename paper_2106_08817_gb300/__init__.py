@@ -28,7 +28,7 @@ __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoo
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
-                  "deform_out")
+                  "deform_out", "adj_jac")
 # kernels launched per timed scope of each class (the cost scope launches two)
 _LAUNCHES_PER_SCOPE = {"cost": 2}
 
@@ -49,7 +49,8 @@ class MetaError(RuntimeError):
 
 class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3), ("batch", ctypes.c_int),
-                ("T", ctypes.c_int), ("sigma", ctypes.c_float), ("ckpt_stride", ctypes.c_int)]
+                ("T", ctypes.c_int), ("sigma", ctypes.c_float), ("ckpt_stride", ctypes.c_int),
+                ("p_update", ctypes.c_int)]
 
 
 class _Tuning(ctypes.Structure):
@@ -114,11 +115,21 @@ def _load():
     return _lib
 
 
+P_UPDATES = {0: 0, 1: 1, "div": 0, "det": 1}
+
+
+def _pupd(p_update) -> int:
+    """Momentum update: 0 / "div" = p~ (1 - dt div v); 1 / "det" = p~ det(Id - dt Dv)."""
+    if p_update not in P_UPDATES:
+        raise ValueError("p_update must be 0, 1, 'div' or 'det' (got %r)" % (p_update,))
+    return P_UPDATES[p_update]
+
+
 def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float,
-             ckpt: int = 0) -> _Problem:
+             ckpt: int = 0, p_update=0) -> _Problem:
     d3 = list(dims) + [0] * (3 - len(dims))
     return _Problem(int(ndim), (ctypes.c_int * 3)(*d3), int(batch), int(T), float(sigma),
-                    int(ckpt))
+                    int(ckpt), _pupd(p_update))
 
 
 def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float, ckpt: int = 0) -> int:
@@ -227,7 +238,7 @@ def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0
 
 def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
                   workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                  ckpt: int = 0) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
+                  ckpt: int = 0, p_update=0) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
     """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
@@ -236,7 +247,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     I1 = torch.empty_like(I0b)
     p1 = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
     rc = _load().meta_shoot_forward(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
                                     _p(I1), _p(p1), ctypes.c_void_p(ws.ptr()), ws.nbytes,
                                     _stream(dev))
@@ -249,7 +260,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
 
 def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                 ckpt: int = 0, want_phi: bool = True, want_jac: bool = True
+                 ckpt: int = 0, want_phi: bool = True, want_jac: bool = True, p_update=0
                  ) -> Tuple[torch.Tensor, torch.Tensor, Optional[torch.Tensor],
                             Optional[torch.Tensor], Workspace]:
     """Shooting with the deformation of the grid, phi_0 = Id, phi_{t+1} = phi_t o (Id - dt v_t):
@@ -266,7 +277,7 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
     p1 = torch.empty_like(I0b)
     phi = torch.empty((B, nd) + tuple(dims), dtype=torch.float32, device=dev) if want_phi else None
     jac = torch.empty_like(I0b) if want_jac else None
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
     rc = _load().meta_shoot_deform(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
                                    _p(I1), _p(p1), _p(phi), _p(jac), ctypes.c_void_p(ws.ptr()),
                                    ws.nbytes, _stream(dev))
@@ -280,10 +291,10 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
 
 
 def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Workspace, T: int,
-                  sigma: float, mu, rho=1.0, want_gI0: bool = True, ndim: Optional[int] = None
-                  ) -> Tuple[Optional[torch.Tensor], torch.Tensor]:
-    """Adjoint of the shooting map on the trajectory kept in `workspace`:
-    returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1, dL/dp_T = gp1."""
+                  sigma: float, mu, rho=1.0, want_gI0: bool = True, ndim: Optional[int] = None,
+                  p_update=0) -> Tuple[Optional[torch.Tensor], torch.Tensor]:
+    """Adjoint of the shooting map on the trajectory kept in `workspace` (shot with the
+    same p_update): returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1, dL/dp_T = gp1."""
     g1, nd, dims, sq = _shape(_as_batch(gI1, "gI1")[0], ndim)
     B, dev = g1.shape[0], g1.device
     if not workspace.matches(dims, B, T, sigma, workspace.ckpt):
@@ -292,7 +303,7 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     gp0 = torch.empty_like(g1)
     gI0 = torch.empty_like(g1) if want_gI0 else None
-    pr = _problem(nd, dims, B, T, sigma, workspace.ckpt)
+    pr = _problem(nd, dims, B, T, sigma, workspace.ckpt, p_update)
     rc = _load().meta_shoot_adjoint(ctypes.byref(pr), _p(mu_t), _p(rho_t), _p(g1), _p(gp1b),
                                     _p(gI0), _p(gp0), ctypes.c_void_p(workspace.ptr()),
                                     workspace.nbytes, _stream(dev))
@@ -307,10 +318,11 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
 def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
                   mu, rho=1.0, lam=1e-3, want_grad: bool = True,
                   workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                  out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0
-                  ) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+                  out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0,
+                  p_update=0) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
     """Eq. 4 cost per instance ([B, 3] float64: data, lambda*kinetic, lambda*rho*residual)
-    and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint."""
+    and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint.  p_update "det"
+    shoots with p' = p~ det(Id - dt Dv) instead of p~ (1 - dt div v)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
@@ -322,7 +334,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b) if want_grad else None
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
     rc = _load().meta_cost_and_grad(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b), _p(mu_t),
                                     _p(rho_t), _p(lam_t), _p(cost), _p(grad),
                                     ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev))
@@ -359,7 +371,7 @@ def set_tuning(dims: Sequence[int], batch: int, sigma: float, tun: Optional[dict
 
 
 def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu,
-             rho=1.0, lam=1e-3, ndim: Optional[int] = None, ckpt: int = 0) -> dict:
+             rho=1.0, lam=1e-3, ndim: Optional[int] = None, ckpt: int = 0, p_update=0) -> dict:
     """Times cost_and_grad on these inputs for candidate tile shapes (meta_autotune),
     records the fastest for the problem shape and returns it.  Blocking."""
     I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
@@ -371,7 +383,8 @@ def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma:
     cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
     grad = torch.empty_like(I0b)
     t = _Tuning()
-    rc = _load().meta_autotune(ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt)), _p(I0b),
+    rc = _load().meta_autotune(ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update)),
+                               _p(I0b),
                                _p(Jb), _p(p0b), _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
                                _p(grad), ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev),
                                ctypes.byref(t))
@@ -389,7 +402,7 @@ class CostAndGradPlan:
     """
 
     def __init__(self, I0, J, p0, T: int, sigma: float, mu, rho=1.0, lam=1e-3,
-                 ndim: Optional[int] = None, ckpt: int = 0):
+                 ndim: Optional[int] = None, ckpt: int = 0, p_update=0):
         I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
         B, dev = I0b.shape[0], I0b.device
         self.I0 = I0b.clone()
@@ -401,7 +414,7 @@ class CostAndGradPlan:
         self.grad = torch.empty_like(I0b)
         self.ws = Workspace(dims, B, T, sigma, dev, ckpt)
         self.device = dev
-        pr = _problem(nd, dims, B, T, sigma, ckpt)
+        pr = _problem(nd, dims, B, T, sigma, ckpt, p_update)
         h = ctypes.c_void_p(0)
         torch.cuda.synchronize(dev)
         rc = _load().meta_plan_create(ctypes.byref(pr), _p(self.I0), _p(self.J), _p(self.p0),
@@ -430,7 +443,7 @@ class GroupPlan:
     mixed) recorded into one CUDA graph as parallel branches (meta_plan_create_group).
 
     `problems` is a list of dicts with keys I0, J, p0 ([B, *dims] CUDA tensors),
-    T, sigma, mu, rho, lam.  Each item keeps its own copies of the inputs
+    T, sigma, mu, rho, lam (optional: ckpt, p_update).  Each item keeps its own copies of the inputs
     (``plan.items[k]["p0"]`` etc.), cost [B, 3] and grad; ``launch()`` runs all.
     """
 
@@ -454,7 +467,8 @@ class GroupPlan:
                   "dims": dims, "B": B}
             it["ckpt"] = int(pb.get("ckpt", 0))
             it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev, it["ckpt"])
-            probs[k] = _problem(nd, dims, B, it["T"], it["sigma"], it["ckpt"])
+            probs[k] = _problem(nd, dims, B, it["T"], it["sigma"], it["ckpt"],
+                                pb.get("p_update", 0))
             for arr, key in ((I0s, "I0"), (Js, "J"), (p0s, "p0"), (mus, "mu"), (rhos, "rho"),
                              (lams, "lam"), (costs, "cost"), (grads, "grad")):
                 arr[k] = it[key].data_ptr()
@@ -490,8 +504,8 @@ NOALLOC_MAX_BYTES = 64 << 20
 
 def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int,
                           sigma: float, mu, rho=1.0, lam=1e-3, ndim: Optional[int] = None,
-                          out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0
-                          ) -> Tuple[torch.Tensor, torch.Tensor]:
+                          out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0,
+                          p_update=0) -> Tuple[torch.Tensor, torch.Tensor]:
     """cost_and_grad on the library's fixed 64 MiB device scratch: no workspace
     argument.  For callers that cannot allocate device memory; pass `out` (and
     device tensors for mu, rho, lam) so that this call allocates nothing either.
@@ -506,7 +520,7 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma, ckpt)
+    pr = _problem(nd, dims, B, T, sigma, ckpt, p_update)
     rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
                                             _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
                                             _p(grad), _stream(dev))
@@ -525,27 +539,28 @@ class Shoot(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, I0, p0, T, sigma, mu, rho):
+    def forward(ctx, I0, p0, T, sigma, mu, rho, p_update=0):
         I0c, p0c = I0.detach().contiguous(), p0.detach().contiguous()
         b_, nd, dims, sq = _shape(I0c, None)
         ws = Workspace(dims, b_.shape[0], T, sigma, I0c.device)
-        I1, p1, _ = shoot_forward(I0c, p0c, T, sigma, mu, rho, workspace=ws)
-        ctx.ws, ctx.args, ctx.shape = ws, (T, sigma, mu, rho), I0c.shape
+        I1, p1, _ = shoot_forward(I0c, p0c, T, sigma, mu, rho, workspace=ws, p_update=p_update)
+        ctx.ws, ctx.args, ctx.shape = ws, (T, sigma, mu, rho, p_update), I0c.shape
         return I1, p1
 
     @staticmethod
     def backward(ctx, gI1, gp1):
-        T, sigma, mu, rho = ctx.args
+        T, sigma, mu, rho, p_update = ctx.args
         if gI1 is None:
             gI1 = torch.zeros(ctx.shape, device=ctx.ws.buf.device)
         gI0, gp0 = shoot_adjoint(gI1.contiguous(), None if gp1 is None else gp1.contiguous(),
-                                 ctx.ws, T, sigma, mu, rho, want_gI0=ctx.needs_input_grad[0])
-        return gI0, gp0, None, None, None, None
+                                 ctx.ws, T, sigma, mu, rho, want_gI0=ctx.needs_input_grad[0],
+                                 p_update=p_update)
+        return gI0, gp0, None, None, None, None, None
 
 
-def shoot(I0, p0, T: int, sigma: float, mu, rho=1.0):
+def shoot(I0, p0, T: int, sigma: float, mu, rho=1.0, p_update=0):
     """Differentiable shooting: torch autograd calls the library's adjoint."""
-    return Shoot.apply(I0, p0, T, sigma, mu, rho)
+    return Shoot.apply(I0, p0, T, sigma, mu, rho, p_update)
 
 
 def timer_start(cap: int = 1 << 16) -> None:

@@ -20,6 +20,10 @@
 //       then the record of step t-1 (or, at t = 0, the outputs; the cost
 //       gradient adds lambda (2 sum_i (D_i I_0)(K m0)_i + 2 rho p0)).
 //
+// With the det momentum update p' = p~ J, J = det(Id - dt Dv), the record
+// holds p~^ = p^' J + dt mu I^' and the same div^, and k_adj_jacT adds the
+// part of D^T (div^ cof(Id - dt Dv)) beyond D^T div^ to v^ before the blur.
+//
 // Each record is built once per voxel, so the transport only gathers.
 #include "meta_stencil.cuh"
 
@@ -78,12 +82,12 @@ struct Rec {
 };
 
 // Record of step t at voxel v from I^' = Ih1, p^' = ph1, the displacement d
-// of the foot per axis and div v_t (the same expressions as the forward step),
-// with p_t at pprev.
-template <int NDIM>
+// of the foot per axis and fac = div v_t (PDET: fac = J = det(Id - dt Dv_t))
+// (the same expressions as the forward step), with p_t at pprev.
+template <int NDIM, bool PDET = false>
 __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
                                             long long o, float Ih1, float ph1, const float* d,
-                                            float div, const float* __restrict__ pprev,
+                                            float fac, const float* __restrict__ pprev,
                                             float* rec) {
     const int b = v.b;
     const float mu = cf.mu[b], dt = cf.dt;
@@ -108,14 +112,15 @@ __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, cons
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) r[(1 + a) * sl] = F.f[a].f;
     r[Rec<NDIM>::kI * sl] = Ih1;
-    r[Rec<NDIM>::kP * sl] = rn_ptilde_hat(ph1, Ih1, dt, mu, div);
+    r[Rec<NDIM>::kP * sl] = PDET ? rn_ptilde_hat_J(ph1, Ih1, dt, mu, fac)
+                                 : rn_ptilde_hat(ph1, Ih1, dt, mu, fac);
     r[Rec<NDIM>::kD * sl] = rn_div_hat(dt, pw, ph1);
 }
 
 // Record of step t at voxel v (pitched offset o in its instance) from
 // I^' = Ih1 and p^' = ph1; state t sits in slot s_state, u_t in slot s_u.  The
 // same expressions as the forward step t.
-template <int NDIM>
+template <int NDIM, bool PDET = false>
 __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
                                              const Vox& v, long long o, float Ih1, float ph1,
                                              const float* __restrict__ states,
@@ -127,15 +132,38 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
     axis_info<NDIM>(g, v, c, n, s);
     float d[NDIM];
     float du = 0.f;
+    float A[NDIM][NDIM];  // PDET: A[a][e] = D_e u_a
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
         const float* ua = slice_of(u, g, ((long long)s_u * NDIM + a) * g.B + b);
         d[a] = disp_of(dtrho, ua[o]);
-        const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
-        du = __fadd_rn(du, rn_cdiff(ua[o + hi], ua[o - lo]));
+        if constexpr (PDET) {
+#pragma unroll
+            for (int e = 0; e < NDIM; ++e) {
+                const long long hi = (c[e] < n[e] - 1) ? s[e] : 0, lo = (c[e] > 0) ? s[e] : 0;
+                A[a][e] = rn_cdiff(ua[o + hi], ua[o - lo]);
+            }
+        } else {
+            const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
+            du = __fadd_rn(du, rn_cdiff(ua[o + hi], ua[o - lo]));
+        }
     }
-    emit_record<NDIM>(g, cf, v, o, Ih1, ph1, d, __fmul_rn(-rho, du),
-                      slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b), rec);
+    const float fac = PDET ? rn_jac_det<NDIM>(A, dtrho) : __fmul_rn(-rho, du);
+    emit_record<NDIM, PDET>(g, cf, v, o, Ih1, ph1, d, fac,
+                            slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b), rec);
+}
+
+// build_record with the momentum update of the call (cf.pdet), for kernels
+// that build records once per call.
+template <int NDIM>
+__device__ __forceinline__ void build_record_any(const Geom& g, const Coefs& cf, int s_state,
+                                                 int s_u, const Vox& v, long long o, float Ih1,
+                                                 float ph1, const float* __restrict__ states,
+                                                 const float* __restrict__ u, float* rec) {
+    if (cf.pdet)
+        build_record<NDIM, true>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
+    else
+        build_record<NDIM, false>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
 }
 
 // Packed per-axis weights of a source whose foot moved by less than one voxel:
@@ -197,7 +225,7 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
             kin += (double)(p * ga) * (double)ua[o];
         }
         res += (double)p * (double)p;
-        build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec);
+        build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec);
         if (zero_sums) {  // scatter accumulators start at zero
             slice_of(Ihp, g, b)[o] = 0.f;
             slice_of(php, g, b)[o] = 0.f;
@@ -254,7 +282,8 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
-    build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u, rec);
+    build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u,
+                           rec);
     if (gather_radius(maxdisp, g.nT - 1, g.B, v.b) > GatherTile<NDIM>::RMAX) {
         slice_of(Ihp, g, v.b)[o] = 0.f;  // the first transport scatters into these
         slice_of(php, g, v.b)[o] = 0.f;
@@ -366,7 +395,7 @@ k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ob = (long long)v.b * g.inst + o;
-    build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, rawI[ob], rawP[ob], states, u, rec);
+    build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, rawI[ob], rawP[ob], states, u, rec);
 }
 
 // S^T and v^ of adjoint step t at one node v, from the records of step t in
@@ -720,14 +749,14 @@ k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __rest
 // raw I^_t, p^_t into rawI / rawP (step t-1 lies in a forward segment that is
 // recomputed first); at t = 0, mode 1: the cost gradient, mode 2: the
 // shooting adjoint.
-template <int NDIM>
+template <int NDIM, bool PDET>
 __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t, int mode,
                                            const Slots& sl, const Vox& v, long long o, float Ihv,
                                            float phv, float kg, float p0v, const float* states,
                                            const float* u, float* rec, float* rawI, float* rawP,
                                            float* out0, float* gI0) {
     if (mode == 0) {
-        build_record<NDIM>(g, cf, sl.st1, sl.ut1, v, o, Ihv, phv, states, u, rec);
+        build_record<NDIM, PDET>(g, cf, sl.st1, sl.ut1, v, o, Ihv, phv, states, u, rec);
     } else if (mode == 3) {
         rawI[(long long)v.b * g.inst + o] = Ihv;
         rawP[(long long)v.b * g.inst + o] = phv;
@@ -747,6 +776,7 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
 // (both components), I_t and p_t staged with a one-voxel halo by cp.async.  When the record of step t-1 has R = 1,
 // u_{t-1} and p_{t-1} are staged too and the record is built from them (the
 // same expressions as build_record).
+template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
               const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
@@ -826,10 +856,20 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
             const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
             const float dtrho = dt * rho;
             const float d0 = disp_of(dtrho, sU0[c]), d1 = disp_of(dtrho, sU1[c]);
-            float du = 0.f;
-            du = __fadd_rn(du, rn_cdiff(sU0[c + (y < g.ny - 1 ? W : 0)], sU0[c - (y > 0 ? W : 0)]));
-            du = __fadd_rn(du, rn_cdiff(sU1[c + (x < g.nx - 1 ? 1 : 0)], sU1[c - (x > 0 ? 1 : 0)]));
-            const float div = __fmul_rn(-rho, du);
+            const int ys = (y < g.ny - 1 ? W : 0), yl = (y > 0 ? W : 0);
+            const int xs = (x < g.nx - 1 ? 1 : 0), xl = (x > 0 ? 1 : 0);
+            float fac;  // div v, or (PDET) det(Id - dt Dv)
+            if constexpr (PDET) {
+                const float A[2][2] = {
+                    {rn_cdiff(sU0[c + ys], sU0[c - yl]), rn_cdiff(sU0[c + xs], sU0[c - xl])},
+                    {rn_cdiff(sU1[c + ys], sU1[c - yl]), rn_cdiff(sU1[c + xs], sU1[c - xl])}};
+                fac = rn_jac_det<2>(A, dtrho);
+            } else {
+                float du = 0.f;
+                du = __fadd_rn(du, rn_cdiff(sU0[c + ys], sU0[c - yl]));
+                du = __fadd_rn(du, rn_cdiff(sU1[c + xs], sU1[c - xl]));
+                fac = __fmul_rn(-rho, du);
+            }
             const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
             const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
             const bool ins[3] = {fy.inside, fx.inside, false};
@@ -840,7 +880,8 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
             r[rsl] = fy.f;
             r[2 * rsl] = fx.f;
             r[Rec<2>::kI * rsl] = Ihv;
-            r[Rec<2>::kP * rsl] = rn_ptilde_hat(phv, Ihv, dt, mu, div);
+            r[Rec<2>::kP * rsl] = PDET ? rn_ptilde_hat_J(phv, Ihv, dt, mu, fac)
+                                       : rn_ptilde_hat(phv, Ihv, dt, mu, fac);
             r[Rec<2>::kD * rsl] = rn_div_hat(dt, pw, phv);
             continue;
         }
@@ -849,12 +890,12 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
             kg += g0 * slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o];
             kg += g1 * slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o];
         }
-        gradp_tail<2>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI, rawP,
-                      out0, gI0);
+        gradp_tail<2, PDET>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI,
+                            rawP, out0, gI0);
     }
 }
 
-template <int NDIM>
+template <int NDIM, bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
             const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
@@ -894,8 +935,98 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict
         Ihv += r;
         if (t == 0 && mode == 1) kg += ga * slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b)[o];
     }
-    gradp_tail<NDIM>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, pt[o], states, u, rec, rawI, rawP,
-                     out0, gI0);
+    gradp_tail<NDIM, PDET>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, pt[o], states, u, rec, rawI,
+                           rawP, out0, gI0);
+}
+
+// R = cof(M) - Id for M = Id + B, B = dt rho Du at one voxel (the
+// derivative of det M is cof M), column e only, written without the
+// cancellation of cof - 1 on the diagonal.
+template <int NDIM>
+__device__ __forceinline__ void cof_minus_id_col(const float (&B)[NDIM][NDIM], int e,
+                                                 float* R) {
+    if constexpr (NDIM == 2) {
+        // cof(M) = [[M11, -M10], [-M01, M00]]
+        R[0] = e == 0 ? B[1][1] : -B[1][0];
+        R[1] = e == 0 ? -B[0][1] : B[0][0];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int a1 = a == 0 ? 1 : 0, a2 = a == 2 ? 1 : 2;  // rows other than a
+            const int e1 = e == 0 ? 1 : 0, e2 = e == 2 ? 1 : 2;  // columns other than e
+            if (a == e) {
+                R[a] = B[a1][a1] + B[a2][a2] + (B[a1][a1] * B[a2][a2] - B[a1][a2] * B[a2][a1]);
+            } else {
+                const float m11 = (a1 == e1 ? 1.f : 0.f) + B[a1][e1];
+                const float m22 = (a2 == e2 ? 1.f : 0.f) + B[a2][e2];
+                const float m12 = (a1 == e2 ? 1.f : 0.f) + B[a1][e2];
+                const float m21 = (a2 == e1 ? 1.f : 0.f) + B[a2][e1];
+                const float minor = m11 * m22 - m12 * m21;
+                R[a] = ((a + e) & 1) ? -minor : minor;
+            }
+        }
+    }
+}
+
+// Adjoint of the det momentum update beyond its first-order part.  With
+// M = Id - dt Dv, dJ/dDv_ae = -dt cof(M)_ae, so v^_a receives
+// sum_e D_e^T (div^ cof(M)_ae), div^ = -dt p~ p^' (record field kD).  The
+// transport added the identity part of cof, D_a^T div^; this kernel adds
+// sum_e D_e^T (div^ R_ae), R = cof(M) - Id, evaluating M at the neighbours
+// that D_e^T reads from u_t (slot sl.ut), each thread for its own node.
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float* __restrict__ rec,
+           float* vh) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float dtrho = cf.dt * cf.rho[b];
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* ua[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) ua[a] = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
+    const float* dh = slice_of(rec, g, (long long)Rec<NDIM>::kD * g.B + b);
+    float acc[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) acc[a] = 0.f;
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) {
+        // D_e^T f at the node: +f/2 from the node below, -f/2 from the node above,
+        // and the edge rows of D (replicated neighbour) at the node itself
+#pragma unroll
+        for (int k = -1; k <= 1; ++k) {
+            float w;
+            if (k < 0) w = c[e] >= 1 ? 0.5f : 0.f;
+            else if (k > 0) w = c[e] <= n[e] - 2 ? -0.5f : 0.f;
+            else w = (c[e] == n[e] - 1 ? 0.5f : 0.f) - (c[e] == 0 ? 0.5f : 0.f);
+            if (w == 0.f) continue;
+            const long long q = o + k * s[e];
+            int cq[NDIM];
+#pragma unroll
+            for (int f = 0; f < NDIM; ++f) cq[f] = c[f] + (f == e ? k : 0);
+            float B[NDIM][NDIM];  // dt rho D_f u_a at q
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a)
+#pragma unroll
+                for (int f = 0; f < NDIM; ++f) {
+                    const long long hi = (cq[f] < n[f] - 1) ? s[f] : 0, lo = (cq[f] > 0) ? s[f] : 0;
+                    B[a][f] = dtrho * (0.5f * (ua[a][q + hi] - ua[a][q - lo]));
+                }
+            float R[NDIM];
+            cof_minus_id_col<NDIM>(B, e, R);
+            const float wd = w * dh[q];
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) acc[a] += wd * R[a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) slice_of(vh, g, (long long)a * g.B + b)[o] += acc[a];
 }
 
 }  // namespace
@@ -971,14 +1102,26 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
                              float* rec, float* rawI, float* rawP, float* out0, float* gI0,
                              cudaStream_t st) {
     const dim3 blk(kPX, kPY);
-    if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_adj_gradp2d,
-                                   dim3((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B), blk,
+    if (ndim == 2) {
+        const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B);
+        META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp2d<true> : k_adj_gradp2d<false>, grid, blk,
                                    0, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
                                    rec, rawI, rawP, out0, gI0));
+    } else {
+        META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp<3, true> : k_adj_gradp<3, false>,
+                                   pgrid<3>(g), blk, 0, st, g, c, t, mode, sl, states, u, maxdisp,
+                                   mh, Ihp, php, rec, rawI, rawP, out0, gI0));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_adj_jacT(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* u, const float* rec, float* vh, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_adj_jacT<2>, pgrid<2>(g), blk, 0, st, g, c, sl, u, rec, vh));
     else
-        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3>, pgrid<3>(g), blk, 0, st, g, c, t, mode, sl,
-                                   states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0));
+        META_CHECK_LAUNCH(launch_k(k_adj_jacT<3>, pgrid<3>(g), blk, 0, st, g, c, sl, u, rec, vh));
     return cudaSuccess;
 }
 

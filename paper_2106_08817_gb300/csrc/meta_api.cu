@@ -56,6 +56,7 @@ struct Layout {
     Geom g;
     int ndim, T, nblk;
     int k;        // checkpoint stride; 0 = every state kept (slot = time)
+    int pdet;     // momentum update p~ det(Id - dt Dv) (else p~ (1 - dt div v))
     int nseg;     // segments of k steps (k > 0)
     int nstate;   // state slots
     int nu;       // u slots
@@ -90,6 +91,8 @@ meta_status validate(const meta_problem* pr) {
     if (pr->T < 1 || pr->T > 4096) return META_ERR_INVALID_ARG;
     if (!(pr->sigma > 0.f) || !(pr->sigma <= 18.f)) return META_ERR_INVALID_ARG;
     if (pr->ckpt_stride < 0 || pr->ckpt_stride > 4096) return META_ERR_INVALID_ARG;
+    if (pr->p_update != META_P_UPDATE_DIV && pr->p_update != META_P_UPDATE_DET)
+        return META_ERR_INVALID_ARG;
     for (int a = 0; a < pr->ndim; ++a)
         if (pr->dims[a] < 2 || pr->dims[a] > 65536) return META_ERR_SHAPE;
     if (pr->ndim == 3) {
@@ -113,6 +116,7 @@ Layout make_layout(const meta_problem* pr) {
     const int d = pr->ndim;
     L.ndim = d;
     L.T = pr->T;
+    L.pdet = pr->p_update == META_P_UPDATE_DET ? 1 : 0;
     Geom& g = L.g;
     g.nz = d == 3 ? pr->dims[0] : 1;
     g.ny = pr->dims[d - 2];
@@ -462,10 +466,14 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         }
         Slots sl{};
         sl.st = L.state_slot(t, s);
+        sl.ut = L.u_slot(t);
         sl.u0 = L.u_slot(0);
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
                     launch_adj_transport(g, d, cf, t, sl, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
                                          c.PHP, c.fault, c.st));
+        if (L.pdet)
+            META_LAUNCH(META_K_ADJ_JAC, c.st,
+                        launch_adj_jacT(g, d, cf, sl, c.u, c.REC, c.SV, c.st));
         // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
                     launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
@@ -528,7 +536,7 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
     if (s != META_OK) return s;
     if (fault) c.fault = fault;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T};
+    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T, c.L.pdet};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     s = run_forward(c, cf);
@@ -736,7 +744,7 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     s = run_forward(c, cf);
@@ -758,7 +766,7 @@ meta_status meta_shoot_deform(const meta_problem* prob, const float* I0, const f
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     const float* wT = nullptr;
@@ -781,7 +789,7 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     Ctx c;
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
     // With checkpoints, an earlier adjoint left another segment in the segment
     // slots: bring the last one back so that the adjoint can be called again.
     if (c.L.k) {
@@ -1091,7 +1099,7 @@ const char* meta_kernel_name(int k) {
     static const char* names[META_K_COUNT] = {
         "pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init",
         "adj_pre", "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack",
-        "deform", "deform_out"};
+        "deform", "deform_out", "adj_jac"};
     return (k >= 0 && k < META_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -133,6 +133,7 @@ struct Coefs {
     const float* rho;     // [B]
     const float* lambda;  // [B]
     float dt;             // 1/T
+    int pdet;             // momentum update: 0 p~ (1 - dt div v), 1 p~ det(Id - dt Dv)
 };
 
 // ------------------------------------------------- relative-coordinate foot

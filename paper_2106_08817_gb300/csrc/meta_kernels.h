@@ -76,6 +76,10 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
 // records of step t-1 (state sl.st1, u sl.ut1); 3 raw I^_t, p^_t into rawI /
 // rawP; at t = 0, 1 the cost gradient (u sl.u0) and 2 the shooting adjoint,
 // into contiguous grad_or_gp0 / gI0 (gI0 nullable).
+// Det momentum update (c.pdet): adds sum_e D_e^T (div^ (cof(M) - Id)_ae) to
+// v^_a (d slices of vh), M = Id - dt Dv_t from u slot sl.ut, div^ from rec.
+cudaError_t launch_adj_jacT(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* u, const float* rec, float* vh, cudaStream_t st);
 cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int mode,
                              const Slots& sl, const float* states, const float* u,
                              const unsigned int* maxdisp, const float* mh, float* Ihp, float* php,

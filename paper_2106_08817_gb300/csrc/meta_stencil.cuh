@@ -128,6 +128,33 @@ __device__ __forceinline__ float rn_div_hat(float dt, float pw, float ph1) {
     return __fmul_rn(__fmul_rn(-dt, pw), ph1);
 }
 
+// Exact Jacobian of the backtrack Id - dt v with v = -rho u:
+// J = det(Id + dt rho A), A[a][e] = D_e u_a, every rounding explicit so that
+// the forward step and every record builder compute the same bits.
+template <int NDIM>
+__device__ __forceinline__ float rn_jac_det(const float (&A)[NDIM][NDIM], float dtrho) {
+    float M[NDIM][NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a)
+#pragma unroll
+        for (int e = 0; e < NDIM; ++e)
+            M[a][e] = __fadd_rn(a == e ? 1.f : 0.f, __fmul_rn(dtrho, A[a][e]));
+    if constexpr (NDIM == 2) {
+        return __fsub_rn(__fmul_rn(M[0][0], M[1][1]), __fmul_rn(M[0][1], M[1][0]));
+    } else {
+        const float c0 = __fsub_rn(__fmul_rn(M[1][1], M[2][2]), __fmul_rn(M[1][2], M[2][1]));
+        const float c1 = __fsub_rn(__fmul_rn(M[1][0], M[2][2]), __fmul_rn(M[1][2], M[2][0]));
+        const float c2 = __fsub_rn(__fmul_rn(M[1][0], M[2][1]), __fmul_rn(M[1][1], M[2][0]));
+        return __fadd_rn(__fsub_rn(__fmul_rn(M[0][0], c0), __fmul_rn(M[0][1], c1)),
+                         __fmul_rn(M[0][2], c2));
+    }
+}
+// p~^ = p^' J + dt mu I^'  (the det update)
+__device__ __forceinline__ float rn_ptilde_hat_J(float ph1, float Ih1, float dt, float mu,
+                                                 float J) {
+    return __fadd_rn(__fmul_rn(ph1, J), __fmul_rn(__fmul_rn(dt, mu), Ih1));
+}
+
 template <int NDIM>
 struct Feet {
     Foot1 f[NDIM];

@@ -3,7 +3,8 @@
 // u_t = K(p_t grad I_t) (v_t = -rho u_t):
 //   k_advect2d / k_advect3d  div v, foot y = x - dt v, bi/trilinear gathers of
 //       I_t and p_t, p_{t+1} = p~ (1 - dt div v), I_{t+1} = I~ + dt mu p~, and
-//       the per-instance max displacement (the window of the adjoint); 2-D on
+//       the per-instance max displacement (the window of the adjoint), or with
+//       the det update p_{t+1} = p~ det(Id - dt Dv); 2-D on
 //       staged 32 x 8 tiles, 3-D marching along z through a ring of planes.
 //   k_deform / k_deform_out  the deformation phi_t of the grid and det D phi_T.
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
@@ -48,6 +49,7 @@ k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, flo
 constexpr int kAdvHalo = 4;
 constexpr int kAdvTY = 2 * kPY;  // rows per tile
 
+template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
            const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
@@ -88,6 +90,15 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
         du += 0.5f * (sU1[ui + (x < g.nx - 1 ? 1 : 0)] - sU1[ui - (x > 0 ? 1 : 0)]);
         dmax = fmaxf(dmax, fmaxf(fabsf(d0), fabsf(d1)));
         const float div = -rho * du;
+        float jac = 0.f;  // PDET: det(Id - dt Dv)
+        if constexpr (PDET) {
+            const int ys = y < g.ny - 1 ? W : 0, yl = y > 0 ? W : 0;
+            const int xs = x < g.nx - 1 ? 1 : 0, xl = x > 0 ? 1 : 0;
+            const float A[2][2] = {
+                {rn_cdiff(sU0[ui + ys], sU0[ui - yl]), rn_cdiff(sU0[ui + xs], sU0[ui - xl])},
+                {rn_cdiff(sU1[ui + ys], sU1[ui - yl]), rn_cdiff(sU1[ui + xs], sU1[ui - xl])}};
+            jac = rn_jac_det<2>(A, dtrho);
+        }
         const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
         const int ly = fy.i0 - (y0 - kAdvHalo), lx = fx.i0 - (x0 - kAdvHalo);
         float Iw, pw;
@@ -100,7 +111,7 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
             pw = bilin(pt + o, g.P, fy.f, fx.f);
         }
         const int o = y * g.P + x;
-        p1[o] = pw * (1.f - dt * div);
+        p1[o] = PDET ? pw * jac : pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
@@ -128,6 +139,7 @@ constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
 constexpr int kARing = 4;                              // plane slots
 constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float);
 
+template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states,
            const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
@@ -234,6 +246,19 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
 #pragma unroll
         for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
         const float div = -rho * du;  // div v, v = -rho u
+        float jac = 0.f;  // PDET: det(Id - dt Dv)
+        if constexpr (PDET) {
+            float A[3][3];  // A[a][e] = D_e u_a
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float* c0 = s0 + a * kAUS;
+                A[a][0] = rn_cdiff(z < g.nz - 1 ? sp1[a * kAUS + ui] : c0[ui],
+                                   z > 0 ? sm1[a * kAUS + ui] : c0[ui]);
+                A[a][1] = rn_cdiff(c0[ui + (y < g.ny - 1 ? kAW : 0)], c0[ui - (y > 0 ? kAW : 0)]);
+                A[a][2] = rn_cdiff(c0[ui + (x < g.nx - 1 ? 1 : 0)], c0[ui - (x > 0 ? 1 : 0)]);
+            }
+            jac = rn_jac_det<3>(A, dtrho);
+        }
         const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
         const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
         float Iw, pw;
@@ -251,7 +276,7 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
             pw = trilin<long long>(pt + gi, g.P, g.slab, fz.f, fy.f, fx.f);
         }
         const long long o = gidx(g, z, y, x);
-        p1[o] = pw * (1.f - dt * div);
+        p1[o] = PDET ? pw * jac : pw * (1.f - dt * div);
         I1[o] = Iw + (dt * mu) * pw;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -368,17 +393,19 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
-    if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_advect2d, dim3((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B), blk, 0, st, g, c, t, sl, states, u, maxdisp));
-    else
-    {
-        cudaError_t e = cudaFuncSetAttribute(k_advect3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (ndim == 2) {
+        const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B);
+        META_CHECK_LAUNCH(launch_k(c.pdet ? k_advect2d<true> : k_advect2d<false>, grid, blk, 0, st,
+                                   g, c, t, sl, states, u, maxdisp));
+    } else {
+        auto kern = c.pdet ? k_advect3d<true> : k_advect3d<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kAdvMarchSmem);
         if (e != cudaSuccess) return e;
         const int zc = g.zca > 0 ? g.zca : march_chunk(g, 4, 4);
         const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
-        META_CHECK_LAUNCH(launch_k(k_advect3d, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc,
-                                   states, u, maxdisp));
+        META_CHECK_LAUNCH(launch_k(kern, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc, states, u,
+                                   maxdisp));
     }
     return cudaGetLastError();
 }

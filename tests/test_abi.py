@@ -57,6 +57,17 @@ def test_invalid_problems_are_rejected(meta, kw, code):
     assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == code
 
 
+def test_momentum_update_values(meta):
+    n = ctypes.c_size_t(0)
+    for val, code in ((0, 0), (1, 0), (2, 1), (-1, 1)):
+        pr = meta._problem(2, (16, 16), 1, 4, 2.0)
+        pr.p_update = val
+        assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == code
+    with pytest.raises(ValueError):
+        meta._problem(2, (16, 16), 1, 4, 2.0, 0, "exact")
+    assert meta._problem(2, (16, 16), 1, 4, 2.0, 0, "det").p_update == 1
+
+
 def test_workspace_size_grows_with_T_and_batch(meta):
     a = meta.workspace_size((64, 64), 1, 10, 3.0)
     b = meta.workspace_size((64, 64), 2, 10, 3.0)

@@ -49,30 +49,32 @@ def smooth_p(seed, shape, scale, s=2.0):
     return out
 
 
-def check_forward(meta, I0, p0, T, sigma, mu, rho):
-    I1, p1, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho)
+def check_forward(meta, I0, p0, T, sigma, mu, rho, p_update=0):
+    I1, p1, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho, p_update=p_update)
     I1, p1 = I1.cpu().numpy(), p1.cpu().numpy()
     for b in range(I0.shape[0]):
         mb = mu[b] if np.ndim(mu) else mu
         rb = rho[b] if np.ndim(rho) else rho
-        It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb)
+        It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb, p_update=p_update)
         assert np.abs(I1[b] - It[-1]).max() <= FWD_ATOL, b
         assert np.abs(p1[b] - pt[-1]).max() <= FWD_ATOL * max(1.0, np.abs(pt[-1]).max()), b
     assert ws.status(clear=True) & 1 == 0
 
 
-def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL, ckpt=0):
+def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL, ckpt=0,
+                    p_update=0):
     B = I0.shape[0]
     ws = meta.Workspace(I0.shape[1:], B, T, sigma, "cuda", ckpt)
     cost, grad = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
-                                    workspace=ws, ckpt=ckpt)
+                                    workspace=ws, ckpt=ckpt, p_update=p_update)
     check_cost_grad.status = ws.status()
     assert check_cost_grad.status & 1 == 0
     cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
     worst = 0.0
     for b in range(I0.shape[0]):
         pick = lambda v: v[b] if np.ndim(v) else v
-        c, g = oracle.cost_and_grad(I0[b], J[b], p0[b], T, sigma, pick(mu), pick(rho), pick(lam))
+        c, g = oracle.cost_and_grad(I0[b], J[b], p0[b], T, sigma, pick(mu), pick(rho), pick(lam),
+                                    p_update=p_update)
         np.testing.assert_allclose(cost[b], c, rtol=COST_RTOL, atol=1e-12)
         e = rel_l2(grad[b], g)
         worst = max(worst, e)
@@ -107,6 +109,56 @@ def test_forward_ragged_3d(meta, dims, B, T, sigma):
     I0, _ = phantoms.random_fields(13, B, dims)
     p0 = smooth_p(14, (B,) + dims, 30.0, s=1.5)
     check_forward(meta, I0, p0, T, sigma, [0.2, 0.0][:B], [1.0, 1.3][:B])
+
+
+# ----------------------------------------------------------------- det momentum update
+# p' = p~ det(Id - dt Dv): the same tolerances as the default update.
+
+@pytest.mark.parametrize("dims,B,T,sigma", [((37, 141), 3, 4, 2.3), ((5, 3), 2, 2, 0.7),
+                                            ((9, 13, 135), 2, 3, 1.5), ((21, 6, 10), 1, 4, 2.0)])
+def test_det_update_forward(meta, dims, B, T, sigma):
+    I0, _ = phantoms.random_fields(21, B, dims)
+    p0 = smooth_p(22, (B,) + dims, 40.0 if len(dims) == 2 else 30.0, s=1.5)
+    mu, rho = [0.0, 0.05, 0.02][:B], [1.0, 0.7, 1.5][:B]
+    check_forward(meta, I0, p0, T, sigma, mu, rho, p_update="det")
+    # here the two updates differ by more than the tolerance (oracle: 8e-4 to 40)
+    a = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho)
+    b = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho, p_update="det")
+    assert float((a[1] - b[1]).abs().max()) > 5 * FWD_ATOL
+
+
+@pytest.mark.parametrize("dims,B,T,sigma,scale,k", [((37, 141), 2, 5, 2.3, 40.0, 0),
+                                                    ((37, 141), 2, 5, 2.3, 40.0, 2),
+                                                    ((9, 13, 135), 2, 3, 1.5, 30.0, 0),
+                                                    ((12, 10, 11), 1, 4, 1.0, 30.0, 3)])
+def test_det_update_cost_and_grad(meta, dims, B, T, sigma, scale, k):
+    """Cost and dL/dp0 against the oracle with the det update, keep-all and with step
+    checkpointing (bit-identical to keep-all).  An FP32 torch.autograd run of the same
+    scheme is within 3e-5 (relative L2) of the oracle on these inputs."""
+    I0, J = phantoms.random_fields(23, B, dims)
+    p0 = smooth_p(24, (B,) + dims, scale, s=1.5)
+    mu, rho, lam = [0.05, 0.0][:B], [1.0, 1.3][:B], 1e-3
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, ckpt=k, p_update="det")
+    if k:
+        c0, g0 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                                    p_update="det")
+        ck, gk = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                                    ckpt=k, p_update="det")
+        torch.cuda.synchronize()
+        assert torch.equal(c0, ck) and torch.equal(g0, gk)
+
+
+def test_det_update_shoot_adjoint(meta):
+    dims, T, sigma = (40, 52), 4, 2.0
+    I0, _ = phantoms.random_fields(25, 1, dims)
+    p0 = smooth_p(26, (1,) + dims, 120.0, s=1.5)
+    r = np.random.default_rng(27)
+    gI1, gp1 = r.normal(size=(1,) + dims), r.normal(size=(1,) + dims)
+    _, _, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, 0.2, 1.0, p_update="det")
+    gI0, gp0 = meta.shoot_adjoint(cuda(gI1), cuda(gp1), ws, T, sigma, 0.2, 1.0, p_update="det")
+    eI, ep = oracle.adjoint(I0[0], p0[0], gI1[0], gp1[0], T, sigma, 0.2, 1.0, p_update="det")
+    assert rel_l2(gp0.cpu().numpy()[0], ep) <= GRAD_RTOL
+    assert rel_l2(gI0.cpu().numpy()[0], eI) <= GRAD_RTOL
 
 
 # ----------------------------------------------------------------- deformation
@@ -225,11 +277,12 @@ def test_extreme_aspect_ratios(meta, dims, T, sigma):
                     np.array([1e-3, 1e-2]))
 
 
+@pytest.mark.parametrize("p_update", ["div", "det"])
 @pytest.mark.parametrize("dims,seed,scale,T,sigma,mu,rho,lam", [
     ((70, 33), 21, 200.0, 5, 3.0, 0.2, 0.8, 1e-2),     # per-step |d|: .2 1.6 4.3 8.1 17
     ((14, 16, 18), 31, 300.0, 4, 1.5, 0.1, 1.0, 1e-3),  # per-step |d|: .3 1.8 4.8 17
 ])
-def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam):
+def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_update):
     """Per-step displacements of 0.2 to 17 voxels: the gather window grows with
     them (R = 1 + floor(max|d|)) and, beyond 8 voxels in 2-D or 3 in 3-D, the
     adjoint switches to the atomic scatter.  These inputs stay well conditioned
@@ -237,10 +290,10 @@ def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam):
     I0, _ = phantoms.random_fields(seed, 1, dims)
     J, _ = phantoms.random_fields(seed + 1, 1, dims)
     p0 = smooth_p(seed + 2, (1,) + dims, scale)
-    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True)
+    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True, p_update=p_update)
     per_step = [np.abs(u[k]).max() * rho / T for k in range(T)]
     assert max(per_step) > 9 and min(per_step) < 1
-    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam)
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update)
     assert check_cost_grad.status & 2  # the scatter fallback ran
 
 
