@@ -14,7 +14,9 @@ Scheme (Eq. 3 in the semi-Lagrangian form of Sec. 2.3; cost Eq. 4):
     p' = p~ (1 - dt div v);  I' = I~ + dt mu p~;
     L = 1/2 |I_T - J|^2 + lambda [ <m0, K m0> + rho |p0|^2 ],  m0 = p0 grad I_0.
 With p_update = "det" the momentum update is p' = p~ det(Id - dt Dv), Dv_ae = D_e v_a,
-the determinant taken by torch.linalg.det.
+the determinant taken by torch.linalg.det.  scheme = "euler" integrates Eq. 5 and the
+conservative Eq. 7 by explicit Euler steps, I' = I - dt <grad I, v> + dt mu p and
+p' = p - dt div(p v); scheme = "hybrid" keeps the semi-Lagrangian I' and takes that p'.
 """
 from __future__ import annotations
 
@@ -97,7 +99,7 @@ def jacobian_factor(v: torch.Tensor, dt: float) -> torch.Tensor:
 
 
 def shoot(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu: torch.Tensor,
-          rho: torch.Tensor, keep: bool = False, p_update="div"):
+          rho: torch.Tensor, keep: bool = False, p_update="div", scheme: str = "sl"):
     """I0, p0 [B, *dims]; mu, rho [B].  Returns (I_T, p_T, v_0[, trajectory])."""
     B, dims = I0.shape[0], I0.shape[1:]
     nd = len(dims)
@@ -115,13 +117,18 @@ def shoot(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu: torch.Te
         v = -rho_b.unsqueeze(1) * u
         if v0 is None:
             v0 = u
-        Ip = sample(torch.stack([I, p], 1), x - dt * v)
-        It, pt = Ip[:, 0], Ip[:, 1]
-        if p_update in ("det", 1):
-            p = pt * jacobian_factor(v, dt)
+        if scheme == "euler":
+            I, p = I - dt * (g * v).sum(1) + dt * mu_b * p, p - dt * divergence(p.unsqueeze(1) * v)
         else:
-            p = pt * (1.0 - dt * divergence(v))
-        I = It + dt * mu_b * pt
+            Ip = sample(torch.stack([I, p], 1), x - dt * v)
+            It, pt = Ip[:, 0], Ip[:, 1]
+            if scheme == "hybrid":
+                p = p - dt * divergence(p.unsqueeze(1) * v)
+            elif p_update in ("det", 1):
+                p = pt * jacobian_factor(v, dt)
+            else:
+                p = pt * (1.0 - dt * divergence(v))
+            I = It + dt * mu_b * pt
         if keep:
             traj.append((I, p))
     return (I, p, v0, traj) if keep else (I, p, v0)

@@ -11,7 +11,8 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``diff(f, axis, transpose=False)``      -- central difference D_axis (or its transpose)
 * ``interp(F, disp, transpose=False)``    -- S(y) F with y = x + disp (or S(y)^T F)
 * ``shoot(I0, p0, T, sigma, mu, rho)``    -- states (I_t, p_t), t=0..T, and u_t
-  (``p_update="det"`` on shoot / adjoint / cost_and_grad: p' = p~ det(Id - dt Dv))
+  (``p_update="det"`` on shoot / adjoint / cost_and_grad: p' = p~ det(Id - dt Dv);
+  ``scheme="euler"`` / ``"hybrid"`` on shoot: the other integration schemes of Sec. 2.3)
 * ``adjoint(I0, p0, gI1, gp1, ...)``      -- gradient of <gI1,I_T>+<gp1,p_T> w.r.t. (I0, p0)
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
 * ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
@@ -68,6 +69,9 @@ def _load():
         lib.oracle_shoot.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      _D, _D, _D, _D, _D]
+        lib.oracle_shoot_scheme.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, _D, _D, _D, _D, _D]
         lib.oracle_adjoint.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        _D, _D, _D, _D, _D, _D]
@@ -77,6 +81,7 @@ def _load():
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         for f in ("oracle_blur", "oracle_diff", "oracle_interp", "oracle_shoot",
+                  "oracle_shoot_scheme",
                   "oracle_adjoint", "oracle_cost_and_grad"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -151,17 +156,22 @@ def _pdet(p_update) -> int:
     return m[p_update]
 
 
+SCHEMES = {"sl": 0, "euler": 1, "hybrid": 2}
+
+
 def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
-          want_u: bool = False, p_update=0) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
-    """Returns (I[T+1, ...], p[T+1, ...], u[T, ndim, ...] or None)."""
+          want_u: bool = False, p_update=0,
+          scheme: str = "sl") -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
+    """Returns (I[T+1, ...], p[T+1, ...], u[T, ndim, ...] or None).  scheme: "sl"
+    (semi-Lagrangian, the method), "euler" or "hybrid" (Sec. 2.3, forward only)."""
     I0, p0 = _f64(I0), _f64(p0)
     shp = I0.shape
     It = np.empty((T + 1,) + shp)
     pt = np.empty((T + 1,) + shp)
     ut = np.empty((T, len(shp)) + shp) if want_u else None
-    _check(_load().oracle_shoot(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                float(rho), _pdet(p_update), _ptr(I0), _ptr(p0), _ptr(It),
-                                _ptr(pt), _ptr(ut)), "shoot")
+    _check(_load().oracle_shoot_scheme(len(shp), _dims(shp), int(T), float(sigma), float(mu),
+                                       float(rho), _pdet(p_update), SCHEMES[scheme], _ptr(I0),
+                                       _ptr(p0), _ptr(It), _ptr(pt), _ptr(ut)), "shoot")
     return It, pt, ut
 
 

@@ -29,6 +29,13 @@
  *   - variant of the momentum update (p_update = 1): p_{t+1} = p~ J with
  *       J = det(Id - dt Dv), Dv_ae = D_e v_a, the Jacobian of the backtrack
  *       Id - dt v, of which 1 - dt div v is the first-order part.
+ *   - the two other integration schemes of Sec. 2.3 (forward shooting only),
+ *       explicit Euler steps of Eq. 5 and of the conservative form of Eq. 7
+ *       with the same central differences D:
+ *       Eulerian: I_{t+1} = I_t - dt sum_a (D_a I_t) v_a + dt mu p_t,
+ *                 p_{t+1} = p_t - dt sum_a D_a (p_t v_a);
+ *       hybrid:   I_{t+1} = I~ + dt mu p~ (the semi-Lagrangian advection),
+ *                 p_{t+1} = p_t - dt sum_a D_a (p_t v_a) (Eulerian momentum).
  *   - cost (Eq. 4): 1/2 sum (I_T - J)^2 + lambda [ sum_i <m0_i, K m0_i>
  *       + rho sum p0^2 ], m0 = p0 grad S.
  *   - gradient: the exact transpose of the discrete scheme above
@@ -237,6 +244,7 @@ typedef struct {
     grid_t g;
     int T;
     int pdet; /* momentum update: 0 = p~ (1 - dt div v), 1 = p~ det(Id - dt Dv) */
+    int scheme; /* 0 semi-Lagrangian, 1 Eulerian, 2 hybrid (set by oracle_shoot) */
     double dt, mu, rho;
     int r;
     double w[OR_MAXTAPS];
@@ -248,6 +256,7 @@ static int scheme_init(scheme_t* s, int ndim, const long* dims, int T, double si
     if (T < 1 || !(mu >= 0.0) || !(rho > 0.0) || (pdet != 0 && pdet != 1)) return -1;
     s->T = T;
     s->pdet = pdet;
+    s->scheme = 0;
     s->dt = 1.0 / (double)T;
     s->mu = mu;
     s->rho = rho;
@@ -346,10 +355,45 @@ static void displacement(const scheme_t* s, const stepbuf_t* b, long x, double* 
     for (int a = 0; a < s->g.ndim; ++a) disp[a] = -s->dt * (-s->rho * b->u[a][x]);
 }
 
+/* Eulerian momentum step: p_{t+1} = p_t - dt sum_a D_a (p_t v_a), conservative form of
+ * Eq. 7; uses b->tmp and b->tmp2. */
+static void euler_momentum(const scheme_t* s, const double* p, stepbuf_t* b, double* p1) {
+    const grid_t* g = &s->g;
+    for (long x = 0; x < g->N; ++x) p1[x] = p[x];
+    for (int a = 0; a < g->ndim; ++a) {
+        for (long x = 0; x < g->N; ++x) b->tmp[x] = p[x] * (-s->rho * b->u[a][x]); /* p v_a */
+        diff_axis(g, a, b->tmp, b->tmp2);
+        for (long x = 0; x < g->N; ++x) p1[x] -= s->dt * b->tmp2[x];
+    }
+}
+
 static void step_forward(const scheme_t* s, const double* I, const double* p, stepbuf_t* b,
                          double* I1, double* p1) {
     const grid_t* g = &s->g;
     velocity(s, I, p, b);
+    if (s->scheme == 1) { /* Eulerian: Eq. 5 and Eq. 7 by explicit Euler steps */
+        for (long x = 0; x < g->N; ++x) {
+            double adv = 0.0; /* <grad I, v> */
+            for (int a = 0; a < g->ndim; ++a) adv += b->g[a][x] * (-s->rho * b->u[a][x]);
+            I1[x] = I[x] - s->dt * adv + s->dt * s->mu * p[x];
+        }
+        euler_momentum(s, p, b, p1);
+        return;
+    }
+    if (s->scheme == 2) { /* hybrid: semi-Lagrangian I, Eulerian p */
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < g->N; ++x) {
+            long c[3];
+            double disp[3];
+            foot_t ft;
+            coords(g, x, c);
+            displacement(s, b, x, disp);
+            foot_of(g, c, disp, &ft);
+            I1[x] = interp(g, &ft, I) + s->dt * s->mu * interp(g, &ft, p);
+        }
+        euler_momentum(s, p, b, p1);
+        return;
+    }
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < g->N; ++x) {
         long c[3];
@@ -420,15 +464,17 @@ int oracle_interp(int ndim, const long* dims, const double* disp, int transpose,
 /* Shooting: states (I_t, p_t), t = 0..T, written to Itraj/ptraj [(T+1)*N];
  * u_traj (nullable) receives u_t = K(p_t grad I_t), [T*ndim*N].  pdet selects
  * the momentum update (0: p~ (1 - dt div v), 1: p~ det(Id - dt Dv)). */
-int oracle_shoot(int ndim, const long* dims, int T, double sigma, double mu, double rho,
-                 int pdet, const double* I0, const double* p0, double* Itraj, double* ptraj,
-                 double* utraj) {
+static int shoot_scheme(int ndim, const long* dims, int T, double sigma, double mu,
+                        double rho, int pdet, int scheme, const double* I0, const double* p0,
+                        double* Itraj, double* ptraj, double* utraj) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
-    if (scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet) != 0) {
+    if (scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet) != 0 || scheme < 0 || scheme > 2 ||
+        (scheme != 0 && pdet)) {
         free(s);
         return -1;
     }
+    s->scheme = scheme;
     long N = s->g.N;
     stepbuf_t b;
     if (stepbuf_alloc(&b, N, ndim, pdet) != 0) {
@@ -448,6 +494,21 @@ int oracle_shoot(int ndim, const long* dims, int T, double sigma, double mu, dou
     stepbuf_free(&b);
     free(s);
     return 0;
+}
+
+int oracle_shoot(int ndim, const long* dims, int T, double sigma, double mu, double rho,
+                 int pdet, const double* I0, const double* p0, double* Itraj, double* ptraj,
+                 double* utraj) {
+    return shoot_scheme(ndim, dims, T, sigma, mu, rho, pdet, 0, I0, p0, Itraj, ptraj, utraj);
+}
+
+/* Forward shooting with integration scheme `scheme`: 0 semi-Lagrangian (as
+ * oracle_shoot), 1 Eulerian, 2 hybrid (Sec. 2.3; see the header).  pdet must
+ * be 0 unless scheme is 0. */
+int oracle_shoot_scheme(int ndim, const long* dims, int T, double sigma, double mu, double rho,
+                        int pdet, int scheme, const double* I0, const double* p0, double* Itraj,
+                        double* ptraj, double* utraj) {
+    return shoot_scheme(ndim, dims, T, sigma, mu, rho, pdet, scheme, I0, p0, Itraj, ptraj, utraj);
 }
 
 /* Reverse sweep through the T steps.  On entry Ih/ph hold the adjoints of

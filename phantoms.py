@@ -15,6 +15,8 @@ available; these phantoms stand in for them:
   ellipses) whose targets are jittered copies plus one blob.
 * ``head_pair_3d``   - nested-ellipsoid "brain" volume, target warped by a
   random smooth displacement plus a blob, optional Rician-like noise.
+* ``c_pair_64``      - a disk and a 'C' (an annulus with a gap), the stand-in for
+  the 'C' picture of the scheme comparison (Fig. 1).
 
 All arrays are float32, C-contiguous, axis 0 first, values clipped to [0, 1].
 """
@@ -106,6 +108,24 @@ def disk_pair_64(seed: int = 1001, random_p0: bool = True, p0_std: float = 0.01)
                     np.ascontiguousarray(p0, dtype=np.float32)[None],
                     np.array([0.1], np.float32), np.array([1.0], np.float32),
                     np.array([1e-3], np.float32))
+
+
+def c_pair_64(size: int = 64) -> Workload:
+    """Disk (radius 0.28 size) -> a 'C': an annulus (radii 0.17 and 0.36 size) with a
+    gap of 0.24 size on the axis-1 positive side, both blurred with sigma 1.  The
+    stand-in for the 'C' picture of the stability comparison (Fig. 1).  T=20, sigma=3,
+    mu=0 (LDDMM), rho=1, lambda=1e-3, p0 = 0."""
+    dims = (size, size)
+    Y, X = _grid(dims)
+    c = (size - 1) / 2.0
+    r2 = (Y - c) ** 2 + (X - c) ** 2
+    S = _smooth((r2 <= (0.28 * size) ** 2).astype(np.float64), 1.0)
+    ring = (r2 <= (0.36 * size) ** 2) & (r2 >= (0.17 * size) ** 2)
+    gap = (np.abs(Y - c) <= 0.12 * size) & (X > c)
+    J = _smooth((ring & ~gap).astype(np.float64), 1.0)
+    return Workload("c64", 2, dims, 20, 3.0, _f32(S)[None], _f32(J)[None],
+                    np.zeros((1,) + dims, np.float32), np.array([0.0], np.float32),
+                    np.array([1.0], np.float32), np.array([1e-3], np.float32))
 
 
 def _random_ellipse_image(rng, dims, ellipses) -> np.ndarray:

@@ -476,3 +476,97 @@ def test_det_update_equals_div_update_for_an_image_varying_along_one_axis(dims):
     np.testing.assert_array_equal(b[0], a[0])
     np.testing.assert_allclose(b[1], a[1], atol=1e-13 * np.abs(a[1]).max())
     assert np.abs(a[1][1] - p0).max() > 1e-3  # the momentum did change
+
+
+# ------------------------------------------- Eulerian and hybrid schemes (Sec. 2.3)
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+def test_other_schemes_at_zero_momentum_and_on_a_flat_image(scheme):
+    dims = (13, 17)
+    I0 = RNG.random(dims)
+    It, pt, _ = oracle.shoot(I0, np.zeros(dims), 5, 1.5, 0.3, 1.0, scheme=scheme)
+    np.testing.assert_array_equal(It[-1], I0)
+    np.testing.assert_array_equal(pt[-1], 0.0)
+    # flat image: grad I = 0, v = 0, so I_1 = I_0 + dt mu p_0 and p_1 = p_0 (Eq. 1)
+    p0 = RNG.normal(size=dims)
+    It, pt, _ = oracle.shoot(np.full(dims, 0.4), p0, 1, 1.5, 0.3, 1.0, scheme=scheme)
+    np.testing.assert_allclose(It[1], 0.4 + 0.3 * p0, atol=1e-15)
+    np.testing.assert_array_equal(pt[1], p0)
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+@pytest.mark.parametrize("dims", [(48, 46), (30, 28, 32)])
+def test_eulerian_momentum_conserves_its_total(dims, scheme):
+    """p' = p - dt sum_a D_a(p v_a): with D the central difference with replicated edges,
+    sum_x D_a f = f(last) - f(first) along each line, so the total of p is kept exactly
+    while p v vanishes on the border.  (The semi-Lagrangian p~ (1 - dt div v) does not
+    keep it.)"""
+    c = [n // 2 for n in dims]
+    X = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in dims], indexing="ij")
+    r2 = sum((x - ci) ** 2 for x, ci in zip(X, c))
+    I0 = np.exp(-r2 / 40.0)
+    p0 = np.where(r2 <= 25.0, smooth_random(dims, 30.0, seed=11), 0.0)
+    _, pt, _ = oracle.shoot(I0, p0, 4, 1.5, 0.1, 1.0, scheme=scheme)
+    np.testing.assert_allclose(pt[-1].sum(), p0.sum(), rtol=1e-12)
+    assert np.abs(pt[-1] - p0).max() > 1e-2
+    _, ps, _ = oracle.shoot(I0, p0, 4, 1.5, 0.1, 1.0)
+    assert abs(ps[-1].sum() - p0.sum()) > 1e-6 * np.abs(p0).sum()
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+@pytest.mark.parametrize("dims", [(16, 20), (9, 11, 10)])
+def test_other_schemes_match_the_torch_implementation(dims, scheme):
+    """The Eulerian and hybrid steps written with torch ops (FP64: conv blur, replicate-
+    padded central differences, grid_sample) reproduce the oracle's."""
+    torch = pytest.importorskip("torch")
+    from baseline import torch_scheme as ts
+    I, _, p = _fd_problem(dims, 60)
+    T, sig, mu, rho = 6, 1.5, 0.2, 1.3
+    It, pt, _ = oracle.shoot(I, p, T, sig, mu, rho, scheme=scheme)
+    t = lambda a: torch.tensor(np.asarray(a)[None], dtype=torch.float64)
+    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, torch.tensor([mu], dtype=torch.float64),
+                         torch.tensor([rho], dtype=torch.float64), scheme=scheme)
+    np.testing.assert_allclose(IT[0].numpy(), It[-1], atol=1e-12)
+    np.testing.assert_allclose(pT[0].numpy(), pt[-1], atol=1e-11 * np.abs(pt[-1]).max())
+    assert np.abs(It[-1] - I).max() > 1e-2
+
+
+def test_eulerian_scheme_is_first_order_in_time():
+    """Explicit Euler steps converge at first order in dt on a fixed grid: the change of
+    (I_1, p_1) from T to 2T steps halves each time T doubles.  (The semi-Lagrangian
+    scheme does not converge as dt shrinks on a fixed grid -- every step interpolates
+    once more, Sec. 2.3 -- so the schemes are compared by their stability below, not
+    by their limits.)"""
+    dims = (40, 36)
+    I, _, p = _fd_problem(dims, 70)
+    E = {T: oracle.shoot(I, p, T, 2.0, 0.1, 1.0, scheme="euler") for T in (20, 40, 80, 160)}
+    for k in (0, 1):
+        d = [np.abs(E[T][k][-1] - E[2 * T][k][-1]).max() for T in (20, 40, 80)]
+        assert d[0] > 1e-3
+        assert 1.8 < d[0] / d[1] < 2.4 and 1.8 < d[1] / d[2] < 2.4, d
+
+
+def test_scheme_stability_on_the_c_phantom():
+    """The comparison of Fig. 1, qualitatively: a momentum from LDDMM gradient descent
+    towards a 'C' (mu = 0), shot by the three schemes.  The semi-Lagrangian and hybrid
+    images stay within the range of I_0 (the interpolation is a convex combination), at
+    20 and at 38 steps; the Eulerian image overshoots it at 20 steps (ripples: a larger
+    total variation) and less at 38."""
+    w = phantoms.c_pair_64()
+    I0, J = w.I0[0].astype(np.float64), w.J[0].astype(np.float64)
+    p = np.zeros_like(I0)
+    for _ in range(40):
+        _, g = oracle.cost_and_grad(I0, J, p, 20, 3.0, 0.0, 1.0, 1e-4)
+        p -= 4.0 * g / np.abs(g).max()
+    res = {}
+    for sc in ("sl", "hybrid", "euler"):
+        for T in (20, 38):
+            It = oracle.shoot(I0, p, T, 3.0, 0.0, 1.0, scheme=sc)[0][-1]
+            over = max(It.max() - I0.max(), I0.min() - It.min(), 0.0)
+            tv = sum(np.abs(np.diff(It, axis=a)).sum() for a in range(2))
+            res[sc, T] = (over, tv)
+    for T in (20, 38):
+        assert res["sl", T][0] <= 1e-12 and res["hybrid", T][0] <= 1e-12
+    assert res["euler", 20][0] > 0.1
+    assert res["euler", 38][0] < 0.6 * res["euler", 20][0]
+    assert res["euler", 20][1] > 1.3 * res["sl", 20][1]
