@@ -78,6 +78,7 @@ def bytes_per_voxel(kclass: str, d: int) -> int:
         "deform": 12 * d,              # read u (d), phi_t - Id (d) at the feet; write phi_t+1 - Id
         "deform_out": 8 * d + 4,       # read phi_T - Id (d); write it (d) and det D phi_T
         "adj_jac": 4 + 12 * d,         # det update: read div^, u (d), v^ (d); write v^ (d)
+        "euler": 16 + 4 * d,           # Eulerian / hybrid step: read u (d), I, p; write I', p'
     }[kclass]
 
 
@@ -396,6 +397,66 @@ def measure_det_update(meta, w, I0, J, p0, mu, rho, lam, ws, ckpt, flush, stream
                         "GBps_algorithmic": gbps, "frac_of_measured_hbm": gbps / peak}}
 
 
+def measure_schemes(meta, w, I0, p0, mu, rho, flush, stream, reps=10):
+    """The three integration schemes of Sec. 2.3: forward shooting time on the workload
+    (eager calls, L2 flushed before each) with the Eulerian step kernel's algorithmic
+    bandwidth, and the stability comparison of Fig. 1 on the 'C' phantom: a momentum
+    from 40 normalised LDDMM gradient steps (the library's cost_and_grad), shot by each
+    scheme with 20 and 38 steps; how far I_T leaves the range of I_0 and its total
+    variation (ripples)."""
+    import torch
+    import phantoms
+    B, N, d, T = w.batch, w.voxels, w.ndim, w.T
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+    out = {"ms_shoot_forward": {}}
+    for sc in ("sl", "euler", "hybrid"):
+        out["ms_shoot_forward"][sc] = timed(
+            lambda: meta.shoot_forward(I0, p0, T, w.sigma, mu, rho, scheme=sc))
+    meta.timer_start(1 << 14)
+    for _ in range(reps):
+        flush.zero_()
+        meta.shoot_forward(I0, p0, T, w.sigma, mu, rho, scheme="euler")
+    torch.cuda.synchronize()
+    kt = meta.timer_stop()
+    peak, _ = peaks()
+    ms, scopes, _ = kt["euler"]
+    avg = ms / max(scopes, 1)
+    gbps = bytes_per_voxel("euler", d) * B * N / (avg * 1e-3) / 1e9
+    out["euler_step"] = {"avg_us": avg * 1e3, "bytes_per_voxel": bytes_per_voxel("euler", d),
+                         "GBps_algorithmic": gbps, "frac_of_measured_hbm": gbps / peak}
+    c = phantoms.c_pair_64()
+    dev = I0.device
+    cI0, cJ = torch.from_numpy(c.I0).to(dev), torch.from_numpy(c.J).to(dev)
+    cp = torch.zeros_like(cI0)
+    for _ in range(40):
+        _, g = meta.cost_and_grad(cI0, cJ, cp, c.T, c.sigma, 0.0, 1.0, 1e-4)
+        cp -= 4.0 * g / g.abs().max()
+    lo, hi = float(cI0.min()), float(cI0.max())
+    study = {}
+    for sc in ("sl", "hybrid", "euler"):
+        for Tc in (20, 38):
+            IT = meta.shoot_forward(cI0, cp, Tc, c.sigma, 0.0, 1.0, scheme=sc)[0][0].double()
+            tv = float((IT[1:] - IT[:-1]).abs().sum() + (IT[:, 1:] - IT[:, :-1]).abs().sum())
+            study["%s_T%d" % (sc, Tc)] = {
+                "overshoot": max(float(IT.max()) - hi, lo - float(IT.min()), 0.0), "tv": tv}
+    out["c64_stability"] = study
+    return out
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -508,6 +569,11 @@ def run_ours(args):
         det_update = measure_det_update(meta, w, I0, J, p0, mu, rho, lam, ws, args.ckpt, flush,
                                         stream)
 
+    # ---- the Eulerian and hybrid schemes, and their stability on the 'C' phantom
+    schemes = None
+    if not args.no_schemes:
+        schemes = measure_schemes(meta, w, I0, p0, mu, rho, flush, stream)
+
     # ---- end to end through the public API: pinned host inputs, H2D + launch + D2H
     hI, hJ, hp = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                   for a in (w.I0, w.J, p0.cpu().numpy()))
@@ -594,6 +660,7 @@ def run_ours(args):
             "torch_autograd": torch_cmp,
             "deformation": deformation,
             "det_update": det_update,
+            "schemes": schemes,
             "kernels": kernels,
             "device_fault_bits": fault,
             "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
@@ -688,6 +755,8 @@ def main():
                     help="skip the deformation measurement (meta_shoot_deform)")
     ap.add_argument("--no-det", action="store_true",
                     help="skip the measurement of the det momentum update")
+    ap.add_argument("--no-schemes", action="store_true",
+                    help="skip the Eulerian / hybrid schemes and the 'C' stability study")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",

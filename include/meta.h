@@ -59,7 +59,8 @@ typedef enum {
     META_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed */
     META_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out */
     META_ERR_NONFINITE = 6,   /* reserved: non-finite cost detected */
-    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, or the driver lacks TMA support */
+    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, the driver lacks TMA support, or the
+                                 call needs the adjoint of a forward-only scheme */
 } meta_status;
 
 /* Shape of one batch of independent registration problems. */
@@ -78,10 +79,22 @@ typedef struct {
                         (Eq. 9); or META_P_UPDATE_DET (1), p' = p~ det(Id - dt Dv), its
                         exact Jacobian, Dv_ae = D_e v_a by central differences.  Every
                         call on one trajectory must use the same value. */
+    int scheme;      /* integration scheme (Sec. 2.3): META_SCHEME_SL (0, the method:
+                        semi-Lagrangian I and p); META_SCHEME_EULER (1: explicit Euler
+                        steps of Eq. 5, I' = I - dt <grad I, v> + dt mu p, and of the
+                        conservative Eq. 7, p' = p - dt div(p v), central differences);
+                        META_SCHEME_HYBRID (2: the semi-Lagrangian I' with that Eulerian
+                        p').  The Eulerian and hybrid schemes are forward only:
+                        meta_shoot_forward and meta_shoot_deform take them, the calls
+                        that need the adjoint return META_ERR_UNSUPPORTED.
+                        META_P_UPDATE_DET requires META_SCHEME_SL. */
 } meta_problem;
 
 #define META_P_UPDATE_DIV 0
 #define META_P_UPDATE_DET 1
+#define META_SCHEME_SL 0
+#define META_SCHEME_EULER 1
+#define META_SCHEME_HYBRID 2
 
 /* Bytes of workspace that every call below needs for this problem (enough
  * for any batch split of meta_plan_create as well).
@@ -277,6 +290,7 @@ enum {
     META_K_DEFORM,         /* one step of the deformation phi_{t+1} = phi_t o (Id - dt v_t) */
     META_K_DEFORM_OUT,     /* phi_T - Id and det D phi_T out */
     META_K_ADJ_JAC,        /* META_P_UPDATE_DET: the higher-order part of the adjoint of det */
+    META_K_EULER,          /* Eulerian or hybrid step (META_SCHEME_EULER / _HYBRID) */
     META_K_COUNT
 };
 

@@ -215,8 +215,8 @@ def jacobian_det(phi) -> np.ndarray:
     return np.linalg.det(A)
 
 
-def deformation(I0, p0, T: int, sigma: float, mu: float,
-                rho: float) -> Tuple[np.ndarray, np.ndarray]:
+def deformation(I0, p0, T: int, sigma: float, mu: float, rho: float,
+                scheme: str = "sl") -> Tuple[np.ndarray, np.ndarray]:
     """Deformation of the grid along the shot (the deformation grids of Fig. 1-2,
     built from all the v_t of the shot): phi_0 = Id and phi_{t+1} = phi_t o (Id - dt v_t),
     each composition evaluated as S(y) phi_t, the interpolation of phi_t (in
@@ -225,7 +225,7 @@ def deformation(I0, p0, T: int, sigma: float, mu: float,
     I0 = _f64(I0)
     shp = I0.shape
     nd = len(shp)
-    _, _, u = shoot(I0, p0, T, sigma, mu, rho, want_u=True)
+    _, _, u = shoot(I0, p0, T, sigma, mu, rho, want_u=True, scheme=scheme)
     ident = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shp],
                                  indexing="ij"))
     phi = ident.copy()

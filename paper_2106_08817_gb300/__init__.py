@@ -24,11 +24,11 @@ import torch
 
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoot_adjoint",
            "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
-           "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan"]
+           "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
-                  "deform_out", "adj_jac")
+                  "deform_out", "adj_jac", "euler")
 # kernels launched per timed scope of each class (the cost scope launches two)
 _LAUNCHES_PER_SCOPE = {"cost": 2}
 
@@ -50,7 +50,7 @@ class MetaError(RuntimeError):
 class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3), ("batch", ctypes.c_int),
                 ("T", ctypes.c_int), ("sigma", ctypes.c_float), ("ckpt_stride", ctypes.c_int),
-                ("p_update", ctypes.c_int)]
+                ("p_update", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 class _Tuning(ctypes.Structure):
@@ -125,11 +125,21 @@ def _pupd(p_update) -> int:
     return P_UPDATES[p_update]
 
 
+SCHEMES = {"sl": 0, "euler": 1, "hybrid": 2}
+
+
+def _scheme(scheme) -> int:
+    """Integration scheme (Sec. 2.3): "sl" (the method), "euler", "hybrid" (forward only)."""
+    if scheme not in SCHEMES:
+        raise ValueError("scheme must be 'sl', 'euler' or 'hybrid' (got %r)" % (scheme,))
+    return SCHEMES[scheme]
+
+
 def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float,
-             ckpt: int = 0, p_update=0) -> _Problem:
+             ckpt: int = 0, p_update=0, scheme="sl") -> _Problem:
     d3 = list(dims) + [0] * (3 - len(dims))
     return _Problem(int(ndim), (ctypes.c_int * 3)(*d3), int(batch), int(T), float(sigma),
-                    int(ckpt), _pupd(p_update))
+                    int(ckpt), _pupd(p_update), _scheme(scheme))
 
 
 def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float, ckpt: int = 0) -> int:
@@ -238,8 +248,10 @@ def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0
 
 def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
                   workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                  ckpt: int = 0, p_update=0) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
-    """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory)."""
+                  ckpt: int = 0, p_update=0, scheme: str = "sl"
+                  ) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
+    """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory).
+    scheme "euler" / "hybrid": the other integration schemes of Sec. 2.3 (forward only)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
@@ -247,7 +259,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     I1 = torch.empty_like(I0b)
     p1 = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update, scheme)
     rc = _load().meta_shoot_forward(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
                                     _p(I1), _p(p1), ctypes.c_void_p(ws.ptr()), ws.nbytes,
                                     _stream(dev))
@@ -260,8 +272,8 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
 
 def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, rho=1.0,
                  workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
-                 ckpt: int = 0, want_phi: bool = True, want_jac: bool = True, p_update=0
-                 ) -> Tuple[torch.Tensor, torch.Tensor, Optional[torch.Tensor],
+                 ckpt: int = 0, want_phi: bool = True, want_jac: bool = True, p_update=0,
+                 scheme: str = "sl") -> Tuple[torch.Tensor, torch.Tensor, Optional[torch.Tensor],
                             Optional[torch.Tensor], Workspace]:
     """Shooting with the deformation of the grid, phi_0 = Id, phi_{t+1} = phi_t o (Id - dt v_t):
     returns (I_T, p_T, phi_T - Id as [B, ndim, *dims] or None, det D phi_T or None,
@@ -277,7 +289,7 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
     p1 = torch.empty_like(I0b)
     phi = torch.empty((B, nd) + tuple(dims), dtype=torch.float32, device=dev) if want_phi else None
     jac = torch.empty_like(I0b) if want_jac else None
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update, scheme)
     rc = _load().meta_shoot_deform(ctypes.byref(pr), _p(I0b), _p(p0b), _p(mu_t), _p(rho_t),
                                    _p(I1), _p(p1), _p(phi), _p(jac), ctypes.c_void_p(ws.ptr()),
                                    ws.nbytes, _stream(dev))
@@ -319,7 +331,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
                   mu, rho=1.0, lam=1e-3, want_grad: bool = True,
                   workspace: Optional[Workspace] = None, ndim: Optional[int] = None,
                   out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0,
-                  p_update=0) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+                  p_update=0, scheme: str = "sl") -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
     """Eq. 4 cost per instance ([B, 3] float64: data, lambda*kinetic, lambda*rho*residual)
     and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint.  p_update "det"
     shoots with p' = p~ det(Id - dt Dv) instead of p~ (1 - dt div v)."""
@@ -334,7 +346,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b) if want_grad else None
-    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update)
+    pr = _problem(nd, dims, B, T, sigma, ws.ckpt, p_update, scheme)
     rc = _load().meta_cost_and_grad(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b), _p(mu_t),
                                     _p(rho_t), _p(lam_t), _p(cost), _p(grad),
                                     ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev))

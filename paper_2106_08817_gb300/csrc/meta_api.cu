@@ -57,6 +57,7 @@ struct Layout {
     int ndim, T, nblk;
     int k;        // checkpoint stride; 0 = every state kept (slot = time)
     int pdet;     // momentum update p~ det(Id - dt Dv) (else p~ (1 - dt div v))
+    int scheme;   // META_SCHEME_SL / _EULER / _HYBRID
     int nseg;     // segments of k steps (k > 0)
     int nstate;   // state slots
     int nu;       // u slots
@@ -93,6 +94,11 @@ meta_status validate(const meta_problem* pr) {
     if (pr->ckpt_stride < 0 || pr->ckpt_stride > 4096) return META_ERR_INVALID_ARG;
     if (pr->p_update != META_P_UPDATE_DIV && pr->p_update != META_P_UPDATE_DET)
         return META_ERR_INVALID_ARG;
+    if (pr->scheme != META_SCHEME_SL && pr->scheme != META_SCHEME_EULER &&
+        pr->scheme != META_SCHEME_HYBRID)
+        return META_ERR_INVALID_ARG;
+    if (pr->scheme != META_SCHEME_SL && pr->p_update != META_P_UPDATE_DIV)
+        return META_ERR_INVALID_ARG;
     for (int a = 0; a < pr->ndim; ++a)
         if (pr->dims[a] < 2 || pr->dims[a] > 65536) return META_ERR_SHAPE;
     if (pr->ndim == 3) {
@@ -117,6 +123,7 @@ Layout make_layout(const meta_problem* pr) {
     L.ndim = d;
     L.T = pr->T;
     L.pdet = pr->p_update == META_P_UPDATE_DET ? 1 : 0;
+    L.scheme = pr->scheme;
     Geom& g = L.g;
     g.nz = d == 3 ? pr->dims[0] : 1;
     g.ny = pr->dims[d - 2];
@@ -387,8 +394,13 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
         sl.st = sin;
         sl.st1 = sout;
         sl.ut = su;
-        META_LAUNCH(META_K_ADVECT, c.st,
-                    launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.st));
+        if (L.scheme == META_SCHEME_SL)
+            META_LAUNCH(META_K_ADVECT, c.st,
+                        launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.st));
+        else
+            META_LAUNCH(META_K_EULER, c.st,
+                        launch_euler(g, d, cf, sl, L.scheme == META_SCHEME_HYBRID, c.states, c.u,
+                                     c.st));
     }
     return META_OK;
 }
@@ -526,11 +538,22 @@ size_t split_bytes(const meta_problem* pr, int S) {
 
 // One cost_and_grad call with an optional fault word other than the one in
 // its workspace (the sub-batches of a split plan all report to the first).
+// The calls that run the adjoint take only the semi-Lagrangian scheme.
+meta_status adjoint_scheme(const meta_problem* pr) {
+    const meta_status s = validate(pr);
+    if (s != META_OK) return s;
+    return pr->scheme == META_SCHEME_SL ? META_OK : META_ERR_UNSUPPORTED;
+}
+
 meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const float* J,
                                const float* p0, const float* mu, const float* rho,
                                const float* lambda, double* cost, float* grad, void* ws,
                                size_t ws_bytes, void* stream, unsigned int* fault) {
     if (!I0 || !J || !p0 || !mu || !rho || !lambda || !cost) return META_ERR_INVALID_ARG;
+    {
+        const meta_status a = adjoint_scheme(prob);
+        if (a != META_OK) return a;
+    }
     Ctx c;
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
@@ -608,7 +631,7 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
                           const float* p0, const float* mu, const float* rho, const float* lambda,
                           double* cost, float* grad, void* ws, size_t ws_bytes, void* stream,
                           meta_tuning* out) {
-    meta_status s = validate(prob);
+    meta_status s = adjoint_scheme(prob);
     if (s != META_OK) return s;
     meta_tuning cur;
     s = meta_tuning_get(prob, &cur);
@@ -786,8 +809,10 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
                                const float* gI1, const float* gp1, float* gI0, float* gp0,
                                void* ws, size_t ws_bytes, void* stream) {
     if (!mu || !rho || !gI1 || !gp0) return META_ERR_INVALID_ARG;
+    meta_status s = adjoint_scheme(prob);
+    if (s != META_OK) return s;
     Ctx c;
-    meta_status s = setup(prob, ws, ws_bytes, stream, &c);
+    s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
     // With checkpoints, an earlier adjoint left another segment in the segment
@@ -958,6 +983,8 @@ meta_status meta_plan_create(const meta_problem* prob, const float* I0, const fl
     size_t need = 0;
     meta_status s = meta_workspace_size(prob, &need);
     if (s != META_OK) return s;
+    s = adjoint_scheme(prob);
+    if (s != META_OK) return s;
     meta_tuning tn;
     const int S = (find_tuning(prob, &tn) && tn.split > 1 && tn.split <= prob->batch) ? tn.split : 1;
     if (S > 1) return plan_create_split(prob, S, I0, J, p0, mu, rho, lambda, cost, grad, ws,
@@ -1008,7 +1035,8 @@ meta_status meta_plan_create_group(int n, const meta_problem* probs, const float
     *plan = nullptr;
     for (int k = 0; k < n; ++k) {
         size_t need = 0;
-        const meta_status s = meta_workspace_size(&probs[k], &need);
+        meta_status s = meta_workspace_size(&probs[k], &need);
+        if (s == META_OK) s = adjoint_scheme(&probs[k]);
         if (s != META_OK) return s;
         if (ws_bytes[k] < need) return META_ERR_WORKSPACE;
     }
@@ -1099,7 +1127,7 @@ const char* meta_kernel_name(int k) {
     static const char* names[META_K_COUNT] = {
         "pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init",
         "adj_pre", "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack",
-        "deform", "deform_out", "adj_jac"};
+        "deform", "deform_out", "adj_jac", "euler"};
     return (k >= 0 && k < META_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -39,6 +39,10 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
 // Forward step t: reads state slot sl.st and u slot sl.ut, writes slot sl.st1.
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st);
+// Eulerian (hybrid = false) or hybrid step t: state slot sl.st -> sl.st1
+// with u slot sl.ut (forward only).
+cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, const Slots& sl, bool hybrid,
+                         float* states, const float* u, cudaStream_t st);
 // Deformation step t: w_{t+1} = (y - x) + S(y) w_t from u slot su, with
 // w = phi - Id in slices a*B + b of win / wout (win NULL: w_t = 0).
 cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const float* u,

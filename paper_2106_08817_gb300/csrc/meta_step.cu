@@ -6,6 +6,7 @@
 //       the per-instance max displacement (the window of the adjoint), or with
 //       the det update p_{t+1} = p~ det(Id - dt Dv); 2-D on
 //       staged 32 x 8 tiles, 3-D marching along z through a ring of planes.
+//   k_euler  the Eulerian and hybrid steps of Sec. 2.3 (forward only).
 //   k_deform / k_deform_out  the deformation phi_t of the grid and det D phi_T.
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
 //       pitched trajectory.
@@ -290,6 +291,49 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
 
+// Eulerian (HYBRID = false) and hybrid steps of Sec. 2.3, forward only.  With
+// v = -rho u (slot sl.ut) and the central differences D of the scheme:
+//   p' = p - dt sum_a D_a (p v_a)                       (conservative Eq. 7)
+//   I' = I - dt sum_a (D_a I) v_a + dt mu p             (Eq. 5, Eulerian)
+//   I' = I~ + dt mu p~ at the foot of the advect         (hybrid)
+// from state slot sl.st into sl.st1.  Plain L1-cached loads of the 2d
+// neighbours; no per-step window is recorded (there is no adjoint).
+template <int NDIM, bool HYBRID>
+__global__ void __launch_bounds__(kPX * kPY)
+k_euler(Geom g, Coefs cf, Slots sl, float* __restrict__ states, const float* __restrict__ u) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+    float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+    float divpv = 0.f, adv = 0.f, d[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
+        const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
+        divpv += 0.5f * (pt[o + hi] * (-rho * ua[o + hi]) - pt[o - lo] * (-rho * ua[o - lo]));
+        if constexpr (HYBRID) d[a] = disp_of(dt * rho, ua[o]);
+        else adv += (0.5f * (It[o + hi] - It[o - lo])) * (-rho * ua[o]);
+    }
+    p1[o] = pt[o] - dt * divpv;
+    if constexpr (HYBRID) {
+        const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+        const float pw = interp<NDIM>(g, F, pt);
+        I1[o] = interp<NDIM>(g, F, It) + (dt * mu) * pw;
+    } else {
+        I1[o] = It[o] - dt * adv + (dt * mu) * pt[o];
+    }
+}
+
 // Deformation of the grid (the deformation grids of Fig. 1-2, Sec. 3): phi_0 = Id and
 // phi_{t+1} = phi_t o (Id - dt v_t), i.e. phi_{t+1}(x) = S(y) phi_t at the same
 // clamped foot y as the advect of step t.  Kept as the displacement
@@ -427,6 +471,18 @@ cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* ph
         META_CHECK_LAUNCH(launch_k(k_deform_out<2>, pgrid<2>(g), blk, 0, st, g, w, phi, jac));
     else
         META_CHECK_LAUNCH(launch_k(k_deform_out<3>, pgrid<3>(g), blk, 0, st, g, w, phi, jac));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, const Slots& sl, bool hybrid,
+                         float* states, const float* u, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(hybrid ? k_euler<2, true> : k_euler<2, false>, pgrid<2>(g), blk,
+                                   0, st, g, c, sl, states, u));
+    else
+        META_CHECK_LAUNCH(launch_k(hybrid ? k_euler<3, true> : k_euler<3, false>, pgrid<3>(g), blk,
+                                   0, st, g, c, sl, states, u));
     return cudaGetLastError();
 }
 

@@ -68,6 +68,30 @@ def test_momentum_update_values(meta):
     assert meta._problem(2, (16, 16), 1, 4, 2.0, 0, "det").p_update == 1
 
 
+def test_schemes_and_what_they_support(meta):
+    lib = meta._load()
+    n = ctypes.c_size_t(0)
+    for sch, pu, code in ((0, 0, 0), (1, 0, 0), (2, 0, 0), (3, 0, 1), (1, 1, 1), (2, 1, 1)):
+        pr = meta._problem(2, (16, 16), 1, 4, 2.0)
+        pr.scheme, pr.p_update = sch, pu
+        assert lib.meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == code
+    # the Eulerian and hybrid schemes are forward only: calls that need the adjoint
+    # refuse them before any CUDA call
+    fake, null = ctypes.c_void_p(0x1000), ctypes.c_void_p(0)
+    need = meta.workspace_size((16, 16), 1, 4, 2.0)
+    for sch in ("euler", "hybrid"):
+        pr = meta._problem(2, (16, 16), 1, 4, 2.0, scheme=sch)
+        assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake,
+                                      fake, fake, fake, need, null) == 7
+        assert lib.meta_shoot_adjoint(ctypes.byref(pr), fake, fake, fake, fake, fake, fake,
+                                      fake, need, null) == 7
+        h = ctypes.c_void_p(0)
+        assert lib.meta_plan_create(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                    fake, fake, need, ctypes.byref(h)) == 7
+    with pytest.raises(ValueError):
+        meta._problem(2, (16, 16), 1, 4, 2.0, scheme="lagrangian")
+
+
 def test_workspace_size_grows_with_T_and_batch(meta):
     a = meta.workspace_size((64, 64), 1, 10, 3.0)
     b = meta.workspace_size((64, 64), 2, 10, 3.0)

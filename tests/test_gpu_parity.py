@@ -49,13 +49,15 @@ def smooth_p(seed, shape, scale, s=2.0):
     return out
 
 
-def check_forward(meta, I0, p0, T, sigma, mu, rho, p_update=0):
-    I1, p1, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho, p_update=p_update)
+def check_forward(meta, I0, p0, T, sigma, mu, rho, p_update=0, scheme="sl"):
+    I1, p1, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho, p_update=p_update,
+                                    scheme=scheme)
     I1, p1 = I1.cpu().numpy(), p1.cpu().numpy()
     for b in range(I0.shape[0]):
         mb = mu[b] if np.ndim(mu) else mu
         rb = rho[b] if np.ndim(rho) else rho
-        It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb, p_update=p_update)
+        It, pt, _ = oracle.shoot(I0[b], p0[b], T, sigma, mb, rb, p_update=p_update,
+                                 scheme=scheme)
         assert np.abs(I1[b] - It[-1]).max() <= FWD_ATOL, b
         assert np.abs(p1[b] - pt[-1]).max() <= FWD_ATOL * max(1.0, np.abs(pt[-1]).max()), b
     assert ws.status(clear=True) & 1 == 0
@@ -159,6 +161,62 @@ def test_det_update_shoot_adjoint(meta):
     eI, ep = oracle.adjoint(I0[0], p0[0], gI1[0], gp1[0], T, sigma, 0.2, 1.0, p_update="det")
     assert rel_l2(gp0.cpu().numpy()[0], ep) <= GRAD_RTOL
     assert rel_l2(gI0.cpu().numpy()[0], eI) <= GRAD_RTOL
+
+
+# ----------------------------------------------------------------- Eulerian and hybrid
+# Forward only (Sec. 2.3): the same tolerances as the semi-Lagrangian forward.
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+@pytest.mark.parametrize("dims,B,T,sigma,scale", [((37, 141), 2, 4, 2.3, 40.0),
+                                                  ((5, 3), 2, 2, 0.7, 10.0),
+                                                  ((9, 13, 135), 2, 3, 1.5, 30.0),
+                                                  ((21, 6, 10), 1, 4, 2.0, 30.0)])
+def test_other_schemes_forward(meta, dims, B, T, sigma, scale, scheme):
+    I0, _ = phantoms.random_fields(31, B, dims)
+    p0 = smooth_p(32, (B,) + dims, scale, s=1.5)
+    check_forward(meta, I0, p0, T, sigma, [0.1, 0.0][:B], [1.0, 1.3][:B], scheme=scheme)
+    # with step checkpoints the forward runs the same launches on the same data
+    a = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, [0.1, 0.0][:B], [1.0, 1.3][:B],
+                           scheme=scheme)
+    b = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, [0.1, 0.0][:B], [1.0, 1.3][:B],
+                           scheme=scheme, ckpt=2)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+def test_other_schemes_zero_momentum_deformation_and_refusals(meta, scheme):
+    w = phantoms.disk_pair_64(random_p0=False)
+    I1, p1, _ = meta.shoot_forward(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho,
+                                   scheme=scheme)
+    np.testing.assert_array_equal(I1.cpu().numpy(), w.I0)
+    assert bool((p1 == 0).all())
+    # the deformation integrates the scheme's own v_t
+    I0, _ = phantoms.random_fields(33, 1, (40, 52))
+    p0 = smooth_p(34, (1, 40, 52), 40.0, s=1.5)
+    _, _, phi, jac, _ = meta.shoot_deform(cuda(I0), cuda(p0), 4, 2.0, 0.1, 1.0, scheme=scheme)
+    wr, Jr = oracle.deformation(I0[0], p0[0], 4, 2.0, 0.1, 1.0, scheme=scheme)
+    assert np.abs(phi.cpu().numpy()[0] - wr).max() <= FWD_ATOL * max(1.0, np.abs(wr).max())
+    assert np.abs(jac.cpu().numpy()[0] - Jr).max() <= 1e-3
+    with pytest.raises(meta.MetaError):
+        meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam,
+                           scheme=scheme)
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+def test_eulerian_momentum_total_full_size(meta, scheme):
+    """16 x 256^2, T = 20, sigma 6: p0 inside a disk of radius 60 around the centre, so p v
+    vanishes on the border for all 20 steps and sum p_T = sum p_0 exactly in exact
+    arithmetic; FP32 keeps it to 1e-4 of sum |p_0|."""
+    w = phantoms.ellipse_pairs()
+    Y, X = np.meshgrid(np.arange(256.0), np.arange(256.0), indexing="ij")
+    inside = ((Y - 127.5) ** 2 + (X - 127.5) ** 2 <= 60.0 ** 2)
+    p0 = (smooth_p(35, w.p0.shape, 1000.0, s=3.0) * inside).astype(np.float32)
+    I1, p1, _ = meta.shoot_forward(cuda(w.I0), cuda(p0), w.T, w.sigma, 0.0, 1.0, scheme=scheme)
+    p1 = p1.cpu().numpy().astype(np.float64)
+    for b in range(p0.shape[0]):
+        tot0, tot1 = float(p0[b].astype(np.float64).sum()), float(p1[b].sum())
+        assert abs(tot1 - tot0) <= 1e-4 * np.abs(p0[b]).sum(), (b, tot0, tot1)
+        assert np.abs(p1[b] - p0[b]).max() > 1.0  # the momentum moved (oracle: by up to 66)
 
 
 # ----------------------------------------------------------------- deformation
