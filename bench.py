@@ -457,6 +457,33 @@ def measure_schemes(meta, w, I0, p0, mu, rho, flush, stream, reps=10):
     return out
 
 
+def measure_lbfgs(meta, w, I0, J, mu, rho, lam, ckpt, iters=10, m=5, step=0.02):
+    """L-BFGS (meta_lbfgs_minimize, m pairs) against the normalised gradient descent of
+    the timed loop (p0 <- p0 - step g / max|g|), both `iters` iterations from p0 = 0 on
+    the workload: the mean total cost per instance after each, and the wall time of
+    the L-BFGS run (it reads every line-search trial's cost back)."""
+    import time
+    import torch
+    p0 = torch.zeros_like(I0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, hist, done = meta.lbfgs_minimize(I0, J, p0, w.T, w.sigma, mu, rho, lam, iters=iters, m=m,
+                                        h0=step, ckpt=ckpt)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    p = torch.zeros_like(I0)
+    gd = []
+    for _ in range(iters + 1):
+        c, g = meta.cost_and_grad(I0, J, p, w.T, w.sigma, mu, rho, lam, ckpt=ckpt)
+        gd.append(float(c.sum(1).mean()))
+        gmax = g.abs().amax(dim=tuple(range(1, w.ndim + 1)), keepdim=True).clamp_min(1e-30)
+        p -= step * g / gmax
+    return {"iters": iters, "m": m, "h0": step,
+            "mean_cost_lbfgs": [float(x) for x in hist.mean(1)],
+            "mean_cost_gd": gd, "ms_per_lbfgs_iter": wall * 1e3 / iters,
+            "iters_moved": [int(x) for x in done]}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -574,6 +601,11 @@ def run_ours(args):
     if not args.no_schemes:
         schemes = measure_schemes(meta, w, I0, p0, mu, rho, flush, stream)
 
+    # ---- L-BFGS against the gradient descent of the timed loop
+    lbfgs = None
+    if not args.no_lbfgs:
+        lbfgs = measure_lbfgs(meta, w, I0, J, mu, rho, lam, args.ckpt)
+
     # ---- end to end through the public API: pinned host inputs, H2D + launch + D2H
     hI, hJ, hp = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                   for a in (w.I0, w.J, p0.cpu().numpy()))
@@ -661,6 +693,7 @@ def run_ours(args):
             "deformation": deformation,
             "det_update": det_update,
             "schemes": schemes,
+            "lbfgs": lbfgs,
             "kernels": kernels,
             "device_fault_bits": fault,
             "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
@@ -757,6 +790,8 @@ def main():
                     help="skip the measurement of the det momentum update")
     ap.add_argument("--no-schemes", action="store_true",
                     help="skip the Eulerian / hybrid schemes and the 'C' stability study")
+    ap.add_argument("--no-lbfgs", action="store_true",
+                    help="skip the L-BFGS against gradient-descent comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",

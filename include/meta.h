@@ -250,6 +250,39 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out);
  * exceeds the launch limits. */
 meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun);
 
+/* L-BFGS over the cost of Eq. 4 (the quasi-Newton alternative to the paper's
+ * gradient descent, Sec. 3): the inverse-Hessian product by the two-loop
+ * recursion (Nocedal & Wright, Algorithm 7.4) over the last m pairs
+ * s = x_{k+1} - x_k, y = g_{k+1} - g_k of each instance, H_0 = gamma I with
+ * gamma = s^T y / y^T y of the newest usable pair; a pair with s^T y <= 1e-12 y^T y
+ * is not used.  Vectors are FP32 [batch, N] (N voxels); dot products are FP64
+ * with a fixed summation order.  m in [1, 64].
+ * meta_lbfgs_workspace_size: device bytes of the L-BFGS workspace `lws`
+ * (256-byte aligned, separate from the cost workspace `ws`). */
+meta_status meta_lbfgs_workspace_size(const meta_problem* prob, int m, size_t* bytes);
+
+/* d = -H g for given pairs: s[i], y[i] (device [batch, N], i < npairs <= m,
+ * oldest first).  Synchronises the stream (it reads s^T y back). */
+meta_status meta_lbfgs_direction(const meta_problem* prob, int m, int npairs,
+                                 const float* const* s, const float* const* y, const float* g,
+                                 float* d, void* lws, size_t lws_bytes, void* stream);
+
+/* Minimises L(p0) = the sum of the three terms of Eq. 4 per instance, starting
+ * from p0 (device, overwritten by the last accepted iterate).  Each iteration:
+ * the direction d = -H g (or d = -h0 g / max|g| without a usable pair, or when
+ * -H g does not descend, which also forgets the instance's pairs), then a
+ * backtracking line search from step 1, halving up to 12 times, that accepts
+ * the first step a with L(x + a d) <= L(x) + 1e-4 a g^T d.  An instance whose
+ * search fails keeps its iterate and stops.  cost_hist (host, nullable):
+ * [iters + 1][batch] costs, entry 0 at the start; iters_done (host, nullable):
+ * [batch] the last iteration that moved each instance.  Blocks the host: the
+ * costs of every trial are read back.  ws: a cost workspace (meta_workspace_size). */
+meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const float* J,
+                                float* p0, const float* mu, const float* rho,
+                                const float* lambda, int iters, int m, float h0, void* ws,
+                                size_t ws_bytes, void* lws, size_t lws_bytes, double* cost_hist,
+                                int* iters_done, void* stream);
+
 /* Device-side status word latched in ws since it was last cleared.  Bit 0: a
  * bounded TMA wait ran out (the call's results are invalid; returns
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step

@@ -17,6 +17,7 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
 * ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
 * ``jacobian_det(phi)``                   -- det D phi of a map given in coordinates (numpy)
+* ``lbfgs_direction(g, S, Y)``, ``lbfgs_minimize(...)`` -- L-BFGS over the Eq. 4 cost (numpy)
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, dot-product
 transpose identities, finite differences, an independent torch re-implementation).
@@ -234,3 +235,74 @@ def deformation(I0, p0, T: int, sigma: float, mu: float, rho: float,
         disp = -dt * (-rho * u[t])  # y - x = -dt v_t, v_t = -rho u_t
         phi = np.stack([interp(phi[a], disp) for a in range(nd)])
     return phi - ident, jacobian_det(phi)
+
+
+def lbfgs_direction(g, S, Y, gamma=None) -> np.ndarray:
+    """d = -H g by the two-loop recursion (Nocedal & Wright, Numerical Optimization,
+    Algorithm 7.4).  S, Y: the stored pairs s_i = x_{i+1} - x_i, y_i = g_{i+1} - g_i,
+    oldest first; a pair with s.y <= 1e-12 y.y is skipped.  H_0 = gamma I, gamma by
+    default s.y / y.y of the newest usable pair (1 without one)."""
+    g = _f64(g)
+    use = [(_f64(s), _f64(y)) for s, y in zip(S, Y)
+           if (_f64(s) * _f64(y)).sum() > 1e-12 * (_f64(y) ** 2).sum() and (_f64(y) ** 2).sum() > 0]
+    q = g.copy()
+    alpha = []
+    for s, y in reversed(use):
+        a = (s * q).sum() / (s * y).sum()
+        alpha.append(a)
+        q = q - a * y
+    if gamma is None:
+        gamma = ((use[-1][0] * use[-1][1]).sum() / (use[-1][1] ** 2).sum()) if use else 1.0
+    r = gamma * q
+    for (s, y), a in zip(use, reversed(alpha)):
+        b = (y * r).sum() / (s * y).sum()
+        r = r + (a - b) * s
+    return -r
+
+
+def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
+                   iters: int, m: int, h0: float, p_update=0):
+    """L-BFGS on the cost of Eq. 4 for one instance, the rules of the GPU driver:
+    direction -H g over the last m pairs (pairs that fail s.y > 1e-12 y.y stay in the
+    window but are skipped); without a usable pair in the window, or when -H g does
+    not descend, d = -h0 g / max|g| and the pairs are forgotten; a backtracking
+    line search from step 1, halving up to 12 times, takes the first step a with
+    L(x + a d) <= L(x) + 1e-4 a g.d; if none passes, the iterate stays and the run
+    stops.  Returns (x, costs [iters + 1], margins): margins[k] lists, for every trial
+    of iteration k, (L + 1e-4 a g.d - L_trial) / |L| (positive: accepted)."""
+    x = _f64(p0).copy()
+    c, g = cost_and_grad(I0, J, x, T, sigma, mu, rho, lam, p_update=p_update)
+    L = c.sum()
+    window = []  # (s, y, usable), oldest first, at most m
+    hist, margins, stopped = [L], [], False
+    for _ in range(iters):
+        margins.append([])
+        if stopped:
+            hist.append(L)
+            continue
+        usable = [(s, y) for s, y, ok in window if ok]
+        d = lbfgs_direction(g, [s for s, _ in usable], [y for _, y in usable]) if usable else None
+        if d is None or not ((g * d).sum() < 0):
+            d = -(h0 / np.abs(g).max()) * g
+            window = [(s, y, False) for s, y, _ in window]
+        gd = (g * d).sum()
+        step, acc = 1.0, None
+        for _t in range(13):
+            xt = x + step * d
+            ct, gt = cost_and_grad(I0, J, xt, T, sigma, mu, rho, lam, p_update=p_update)
+            margins[-1].append((L + 1e-4 * step * gd - ct.sum()) / max(abs(L), 1e-300))
+            if ct.sum() <= L + 1e-4 * step * gd:
+                acc = (xt, gt, ct.sum())
+                break
+            step *= 0.5
+        if acc is None:
+            stopped = True
+            hist.append(L)
+            continue
+        xt, gt, Lt = acc
+        s, y = xt - x, gt - g
+        window.append((s, y, (s * y).sum() > 1e-12 * (y * y).sum() and (y * y).sum() > 0))
+        window = window[-m:]
+        x, g, L = xt, gt, Lt
+        hist.append(L)
+    return x, np.array(hist), margins

@@ -24,7 +24,8 @@ import torch
 
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoot_adjoint",
            "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
-           "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES"]
+           "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES",
+           "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
@@ -103,6 +104,14 @@ def _load():
         lib.meta_tuning_get.argtypes = [P, T]
         lib.meta_tuning_set.argtypes = [P, T]
         for f in ("meta_autotune", "meta_tuning_get", "meta_tuning_set"):
+            getattr(lib, f).restype = ctypes.c_int
+        lib.meta_lbfgs_workspace_size.argtypes = [P, ctypes.c_int, ctypes.POINTER(S)]
+        lib.meta_lbfgs_direction.argtypes = [P, ctypes.c_int, ctypes.c_int, PP, PP, F, F, V, S, V]
+        lib.meta_lbfgs_minimize.argtypes = [P, F, F, F, F, F, F, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_float, V, S, V, S,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int), V]
+        for f in ("meta_lbfgs_workspace_size", "meta_lbfgs_direction", "meta_lbfgs_minimize"):
             getattr(lib, f).restype = ctypes.c_int
         lib.meta_kernel_name.argtypes = [ctypes.c_int]
         lib.meta_kernel_name.restype = ctypes.c_char_p
@@ -403,6 +412,61 @@ def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma:
     if rc:
         raise MetaError(rc, "meta_autotune")
     return {f: getattr(t, f) for f in TUNING_FIELDS}
+
+
+def lbfgs_workspace_size(dims: Sequence[int], batch: int, m: int = 5) -> int:
+    """Bytes of the L-BFGS workspace (m pairs) of a batch of this shape."""
+    n = ctypes.c_size_t(0)
+    rc = _load().meta_lbfgs_workspace_size(
+        ctypes.byref(_problem(len(dims), dims, batch, 1, 1.0)), int(m), ctypes.byref(n))
+    if rc:
+        raise MetaError(rc, "meta_lbfgs_workspace_size")
+    return int(n.value)
+
+
+def lbfgs_direction(g: torch.Tensor, S: Sequence[torch.Tensor], Y: Sequence[torch.Tensor],
+                    m: Optional[int] = None, ndim: Optional[int] = None) -> torch.Tensor:
+    """d = -H g by the two-loop recursion over the pairs S[i], Y[i] (oldest first) of
+    every instance (meta_lbfgs_direction)."""
+    gb, nd, dims, sq = _shape(_as_batch(g, "g")[0], ndim)
+    B, dev = gb.shape[0], gb.device
+    m = int(m or max(1, len(S)))
+    Sb = [_as_batch(x, "s")[0].reshape(gb.shape) for x in S]
+    Yb = [_as_batch(x, "y")[0].reshape(gb.shape) for x in Y]
+    arr = lambda ts: (ctypes.c_void_p * max(1, len(ts)))(*[t.data_ptr() for t in ts])
+    lws = torch.empty(lbfgs_workspace_size(dims, B, m), dtype=torch.uint8, device=dev)
+    d = torch.empty_like(gb)
+    rc = _load().meta_lbfgs_direction(ctypes.byref(_problem(nd, dims, B, 1, 1.0)), m, len(Sb),
+                                      arr(Sb), arr(Yb), _p(gb), _p(d),
+                                      ctypes.c_void_p(lws.data_ptr()), lws.numel(), _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_lbfgs_direction")
+    return d[0] if sq else d
+
+
+def lbfgs_minimize(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
+                   mu, rho=1.0, lam=1e-3, iters: int = 10, m: int = 5, h0: float = 0.05,
+                   ndim: Optional[int] = None, ckpt: int = 0, p_update=0):
+    """L-BFGS on the Eq. 4 cost from p0 (meta_lbfgs_minimize).  Returns (p, costs
+    [iters + 1, B] float64 numpy, last moving iteration per instance)."""
+    I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
+    p = _as_batch(p0, "p0")[0].reshape(I0b.shape).clone()
+    B, dev = I0b.shape[0], I0b.device
+    ws = _workspace(dims, B, T, sigma, dev, None, ckpt)
+    lws = torch.empty(lbfgs_workspace_size(dims, B, m), dtype=torch.uint8, device=dev)
+    mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
+    hist = np.zeros((iters + 1, B), dtype=np.float64)
+    done = np.zeros(B, dtype=np.int32)
+    rc = _load().meta_lbfgs_minimize(
+        ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update)), _p(I0b), _p(Jb), _p(p),
+        _p(mu_t), _p(rho_t), _p(lam_t), int(iters), int(m), float(h0), ctypes.c_void_p(ws.ptr()),
+        ws.nbytes, ctypes.c_void_p(lws.data_ptr()), lws.numel(),
+        hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        done.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_lbfgs_minimize")
+    return (p[0] if sq else p), hist, done
 
 
 class CostAndGradPlan:

@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmeta.so")
-SOURCES = ["meta_api.cu", "meta_blur.cu", "meta_step.cu", "meta_adjoint.cu", "meta_noalloc.cu"]
+SOURCES = ["meta_api.cu", "meta_blur.cu", "meta_step.cu", "meta_adjoint.cu", "meta_noalloc.cu",
+           "meta_lbfgs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,521 @@
+// meta_lbfgs.cu -- L-BFGS over the cost of Eq. 4 (the quasi-Newton option the
+// paper mentions beside gradient descent, Sec. 3), sm_103a.
+//
+// The inverse-Hessian product is the two-loop recursion (Nocedal & Wright,
+// Numerical Optimization, Algorithm 7.4) over the last m pairs
+// s_i = x_{i+1} - x_i, y_i = g_{i+1} - g_i of each instance, with
+// H_0 = gamma I, gamma = s^T y / y^T y of the newest pair.  Every vector
+// operation runs on the device: FP64 dot products with a fixed summation order
+// (per-CTA partials over fixed chunks, then one CTA per instance), FP32 axpys
+// whose coefficients stay on the device, so a direction needs no host round
+// trip.  meta_lbfgs_minimize drives the iterations from the host: a
+// backtracking Armijo line search per instance that reads the costs of each
+// trial back (one synchronisation per trial).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "meta.h"
+#include "meta_common.cuh"
+
+namespace meta {
+namespace {
+
+constexpr int kLT = 256;       // threads per CTA
+constexpr int kLMaxBlk = 512;  // dot-product CTAs per instance
+
+int dot_blocks(long long N) {
+    long long nb = (N + kLT * 8 - 1) / (kLT * 8);
+    if (nb < 1) nb = 1;
+    if (nb > kLMaxBlk) nb = kLMaxBlk;
+    return (int)nb;
+}
+
+// Per-CTA FP64 partial sums of a[b] . b[b] (or of max |a[b]| when MAX) over a
+// fixed chunk of instance b; partials[b * nb + blk].
+template <bool MAX>
+__global__ void __launch_bounds__(kLT)
+k_ldot(long long N, const float* __restrict__ a, const float* __restrict__ b, double* partials) {
+    const int inst = blockIdx.y, nb = gridDim.x;
+    const long long chunk = (N + nb - 1) / nb;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = lo + chunk < N ? lo + chunk : N;
+    const float* pa = a + (long long)inst * N;
+    const float* pb = b ? b + (long long)inst * N : nullptr;
+    double acc = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kLT) {
+        if constexpr (MAX) acc = fmax(acc, (double)fabsf(pa[i]));
+        else acc += (double)pa[i] * (double)pb[i];
+    }
+    __shared__ double red[kLT];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kLT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            red[threadIdx.x] = MAX ? fmax(red[threadIdx.x], red[threadIdx.x + w])
+                                   : red[threadIdx.x] + red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[(long long)inst * nb + blockIdx.x] = red[0];
+}
+
+// out[b] = the partials of instance b combined in a fixed order.
+template <bool MAX>
+__global__ void __launch_bounds__(kLT)
+k_lred(int nb, const double* __restrict__ partials, double* out) {
+    const int inst = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kLT) {
+        const double v = partials[(long long)inst * nb + i];
+        acc = MAX ? fmax(acc, v) : acc + v;
+    }
+    __shared__ double red[kLT];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kLT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            red[threadIdx.x] = MAX ? fmax(red[threadIdx.x], red[threadIdx.x + w])
+                                   : red[threadIdx.x] + red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[inst] = red[0];
+}
+
+// Coefficients of the two-loop recursion, one thread per instance:
+//   mode 0 (first loop):  alpha_i = rho_i (s_i . q),   coef = -alpha_i
+//   mode 1 (second loop): beta = rho_i (y_i . r),      coef = alpha_i - beta
+__global__ void k_lcoef(int B, int mode, const double* __restrict__ rho_i, double* alpha_i,
+                        const double* __restrict__ dot, double* coef) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (mode == 0) {
+        alpha_i[b] = rho_i[b] * dot[b];
+        coef[b] = -alpha_i[b];
+    } else {
+        coef[b] = alpha_i[b] - rho_i[b] * dot[b];
+    }
+}
+
+// y[b] += coef[b] x[b]  (coef rounded to FP32 once per instance)
+__global__ void __launch_bounds__(kLT)
+k_laxpy(long long N, const double* __restrict__ coef, const float* __restrict__ x, float* y) {
+    const int b = blockIdx.y;
+    const float c = (float)coef[b];
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        y[o + i] = fmaf(c, x[o + i], y[o + i]);
+}
+
+// y[b] *= coef[b]
+__global__ void __launch_bounds__(kLT)
+k_lscale(long long N, const double* __restrict__ coef, float* y) {
+    const int b = blockIdx.y;
+    const float c = (float)coef[b];
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        y[o + i] *= c;
+}
+
+// d[b] = c[b] g[b] where use[b] (a scaled steepest-descent step)
+__global__ void __launch_bounds__(kLT)
+k_lsteep(long long N, const int* __restrict__ use, const double* __restrict__ c,
+         const float* __restrict__ g, float* d) {
+    const int b = blockIdx.y;
+    if (!use[b]) return;
+    const float cb = (float)c[b];
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        d[o + i] = cb * g[o + i];
+}
+
+// xt[b] = x[b] + step[b] d[b]  (exactly x[b] where step[b] = 0)
+__global__ void __launch_bounds__(kLT)
+k_ltrial(long long N, const double* __restrict__ step, const float* __restrict__ x,
+         const float* __restrict__ d, float* xt) {
+    const int b = blockIdx.y;
+    const float a = (float)step[b];
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        xt[o + i] = a == 0.f ? x[o + i] : fmaf(a, d[o + i], x[o + i]);
+}
+
+// where keep[b]: xa[b] = xt[b], ga[b] = gt[b] (the accepted trial point)
+__global__ void __launch_bounds__(kLT)
+k_lkeep(long long N, const int* __restrict__ keep, const float* __restrict__ xt,
+        const float* __restrict__ gt, float* xa, float* ga) {
+    const int b = blockIdx.y;
+    if (!keep[b]) return;
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT) {
+        xa[o + i] = xt[o + i];
+        ga[o + i] = gt[o + i];
+    }
+}
+
+// New pair: where moved[b], s = xa - x, y = ga - g, then x = xa, g = ga;
+// elsewhere s = y = 0 (a pair with rho = 0 has no effect).
+__global__ void __launch_bounds__(kLT)
+k_lpair(long long N, const int* __restrict__ moved, float* x, float* g,
+        const float* __restrict__ xa, const float* __restrict__ ga, float* s, float* y) {
+    const int b = blockIdx.y;
+    const bool mv = moved[b] != 0;
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT) {
+        if (mv) {
+            s[o + i] = xa[o + i] - x[o + i];
+            y[o + i] = ga[o + i] - g[o + i];
+            x[o + i] = xa[o + i];
+            g[o + i] = ga[o + i];
+        } else {
+            s[o + i] = 0.f;
+            y[o + i] = 0.f;
+        }
+    }
+}
+
+dim3 vec_grid(long long N, int B) {
+    long long gx = (N + kLT * 4 - 1) / (kLT * 4);
+    if (gx < 1) gx = 1;
+    if (gx > 4096) gx = 4096;
+    return dim3((unsigned)gx, (unsigned)B);
+}
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// L-BFGS workspace map for B instances of N voxels and m pairs.
+struct LMap {
+    long long N;
+    int B, m, nb;
+    size_t oS, oY, oG, oGt, oXt, oXa, oGa, oD;        // float vectors
+    size_t oRho, oAlpha, oGamma, oDot, oCoef, oStep, oPart, oCost;  // doubles
+    size_t oFlag;                                   // int[B]
+    size_t total;
+};
+
+LMap lbfgs_map(long long N, int B, int m) {
+    LMap M;
+    std::memset(&M, 0, sizeof(M));
+    M.N = N;
+    M.B = B;
+    M.m = m;
+    M.nb = dot_blocks(N);
+    const size_t vec = up256(sizeof(float) * (size_t)N * B);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += up256(bytes);
+        return o;
+    };
+    M.oS = take(vec * m);
+    M.oY = take(vec * m);
+    M.oG = take(vec);
+    M.oGt = take(vec);
+    M.oXt = take(vec);
+    M.oXa = take(vec);
+    M.oGa = take(vec);
+    M.oD = take(vec);
+    M.oRho = take(sizeof(double) * (size_t)m * B);
+    M.oAlpha = take(sizeof(double) * (size_t)m * B);
+    M.oGamma = take(sizeof(double) * B);
+    M.oDot = take(sizeof(double) * B);
+    M.oCoef = take(sizeof(double) * B);
+    M.oStep = take(sizeof(double) * B);
+    M.oPart = take(sizeof(double) * (size_t)B * M.nb);
+    M.oCost = take(sizeof(double) * 3 * (size_t)B);
+    M.oFlag = take(sizeof(int) * B);
+    M.total = off;
+    return M;
+}
+
+struct LCtx {
+    LMap M;
+    char* base;
+    cudaStream_t st;
+    float* vec(size_t o) const { return reinterpret_cast<float*>(base + o); }
+    double* dbl(size_t o) const { return reinterpret_cast<double*>(base + o); }
+    float* S(int i) const { return vec(M.oS) + (size_t)i * M.N * M.B; }
+    float* Y(int i) const { return vec(M.oY) + (size_t)i * M.N * M.B; }
+};
+
+#define L_TRY(x)                                                 \
+    do {                                                         \
+        if ((x) != cudaSuccess) return META_ERR_CUDA;            \
+    } while (0)
+
+// out[b] = a[b] . b[b]  (b NULL with MAX: max |a[b]|)
+template <bool MAX>
+meta_status ldot(const LCtx& c, const float* a, const float* b, double* out) {
+    k_ldot<MAX><<<dim3(c.M.nb, c.M.B), kLT, 0, c.st>>>(c.M.N, a, b, c.dbl(c.M.oPart));
+    k_lred<MAX><<<c.M.B, kLT, 0, c.st>>>(c.M.nb, c.dbl(c.M.oPart), out);
+    L_TRY(cudaGetLastError());
+    return META_OK;
+}
+
+// d = -H g by the two-loop recursion over h stored pairs, the newest in ring
+// slot head - 1.
+meta_status two_loop(const LCtx& c, const float* g, float* d, int h, int head) {
+    const LMap& M = c.M;
+    const dim3 vg = vec_grid(M.N, M.B);
+    L_TRY(cudaMemcpyAsync(d, g, sizeof(float) * (size_t)M.N * M.B, cudaMemcpyDeviceToDevice,
+                          c.st));
+    double* rho = c.dbl(M.oRho);
+    double* alpha = c.dbl(M.oAlpha);
+    const int cb = (M.B + 127) / 128;
+    for (int j = 0; j < h; ++j) {  // newest first
+        const int i = ((head - 1 - j) % M.m + M.m) % M.m;
+        meta_status s = ldot<false>(c, c.S(i), d, c.dbl(M.oDot));
+        if (s != META_OK) return s;
+        k_lcoef<<<cb, 128, 0, c.st>>>(M.B, 0, rho + (size_t)i * M.B, alpha + (size_t)i * M.B,
+                                      c.dbl(M.oDot), c.dbl(M.oCoef));
+        k_laxpy<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), c.Y(i), d);
+    }
+    k_lscale<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oGamma), d);
+    for (int j = h - 1; j >= 0; --j) {  // oldest first
+        const int i = ((head - 1 - j) % M.m + M.m) % M.m;
+        meta_status s = ldot<false>(c, c.Y(i), d, c.dbl(M.oDot));
+        if (s != META_OK) return s;
+        k_lcoef<<<cb, 128, 0, c.st>>>(M.B, 1, rho + (size_t)i * M.B, alpha + (size_t)i * M.B,
+                                      c.dbl(M.oDot), c.dbl(M.oCoef));
+        k_laxpy<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), c.S(i), d);
+    }
+    std::vector<double> neg(M.B, -1.0);
+    L_TRY(cudaMemcpyAsync(c.dbl(M.oCoef), neg.data(), sizeof(double) * M.B,
+                          cudaMemcpyHostToDevice, c.st));
+    k_lscale<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), d);
+    L_TRY(cudaGetLastError());
+    // the host vector must outlive the copy
+    L_TRY(cudaStreamSynchronize(c.st));
+    return META_OK;
+}
+
+meta_status lsetup(const meta_problem* prob, int m, void* lws, size_t lws_bytes, void* stream,
+                   LCtx* c) {
+    size_t need = 0;
+    meta_status s = meta_lbfgs_workspace_size(prob, m, &need);
+    if (s != META_OK) return s;
+    if (!lws || (reinterpret_cast<uintptr_t>(lws) % 256) != 0 || lws_bytes < need)
+        return META_ERR_WORKSPACE;
+    long long N = 1;
+    for (int a = 0; a < prob->ndim; ++a) N *= prob->dims[a];
+    c->M = lbfgs_map(N, prob->batch, m);
+    c->base = static_cast<char*>(lws);
+    c->st = static_cast<cudaStream_t>(stream);
+    return META_OK;
+}
+
+}  // namespace
+}  // namespace meta
+
+using namespace meta;
+
+extern "C" {
+
+meta_status meta_lbfgs_workspace_size(const meta_problem* prob, int m, size_t* bytes) {
+    if (!bytes || m < 1 || m > 64) return META_ERR_INVALID_ARG;
+    size_t ws = 0;
+    const meta_status s = meta_workspace_size(prob, &ws);  // validates prob
+    if (s != META_OK) return s;
+    long long N = 1;
+    for (int a = 0; a < prob->ndim; ++a) N *= prob->dims[a];
+    *bytes = lbfgs_map(N, prob->batch, m).total;
+    return META_OK;
+}
+
+meta_status meta_lbfgs_direction(const meta_problem* prob, int m, int npairs,
+                                 const float* const* s, const float* const* y, const float* g,
+                                 float* d, void* lws, size_t lws_bytes, void* stream) {
+    if (!g || !d || npairs < 0 || npairs > m || (npairs > 0 && (!s || !y)))
+        return META_ERR_INVALID_ARG;
+    LCtx c;
+    meta_status st = lsetup(prob, m, lws, lws_bytes, stream, &c);
+    if (st != META_OK) return st;
+    const LMap& M = c.M;
+    const size_t vbytes = sizeof(float) * (size_t)M.N * M.B;
+    std::vector<double> rho((size_t)M.m * M.B, 0.0), gamma(M.B, 1.0), sy(M.B), yy(M.B);
+    for (int i = 0; i < npairs; ++i) {
+        if (!s[i] || !y[i]) return META_ERR_INVALID_ARG;
+        L_TRY(cudaMemcpyAsync(c.S(i), s[i], vbytes, cudaMemcpyDeviceToDevice, c.st));
+        L_TRY(cudaMemcpyAsync(c.Y(i), y[i], vbytes, cudaMemcpyDeviceToDevice, c.st));
+        st = ldot<false>(c, c.S(i), c.Y(i), c.dbl(M.oDot));
+        if (st != META_OK) return st;
+        L_TRY(cudaMemcpyAsync(sy.data(), c.dbl(M.oDot), sizeof(double) * M.B,
+                              cudaMemcpyDeviceToHost, c.st));
+        st = ldot<false>(c, c.Y(i), c.Y(i), c.dbl(M.oDot));
+        if (st != META_OK) return st;
+        L_TRY(cudaMemcpyAsync(yy.data(), c.dbl(M.oDot), sizeof(double) * M.B,
+                              cudaMemcpyDeviceToHost, c.st));
+        L_TRY(cudaStreamSynchronize(c.st));
+        for (int b = 0; b < M.B; ++b) {
+            const bool ok = sy[b] > 1e-12 * yy[b] && yy[b] > 0.0;
+            rho[(size_t)i * M.B + b] = ok ? 1.0 / sy[b] : 0.0;
+            if (ok) gamma[b] = sy[b] / yy[b];
+        }
+    }
+    L_TRY(cudaMemcpyAsync(c.dbl(M.oRho), rho.data(), sizeof(double) * rho.size(),
+                          cudaMemcpyHostToDevice, c.st));
+    L_TRY(cudaMemcpyAsync(c.dbl(M.oGamma), gamma.data(), sizeof(double) * M.B,
+                          cudaMemcpyHostToDevice, c.st));
+    return two_loop(c, g, d, npairs, npairs % M.m);
+}
+
+meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const float* J,
+                                float* p0, const float* mu, const float* rho,
+                                const float* lambda, int iters, int m, float h0, void* ws,
+                                size_t ws_bytes, void* lws, size_t lws_bytes, double* cost_hist,
+                                int* iters_done, void* stream) {
+    if (!I0 || !J || !p0 || !mu || !rho || !lambda || iters < 0 || !(h0 > 0.f))
+        return META_ERR_INVALID_ARG;
+    LCtx c;
+    meta_status st = lsetup(prob, m, lws, lws_bytes, stream, &c);
+    if (st != META_OK) return st;
+    const LMap& M = c.M;
+    const int B = M.B;
+    const size_t vbytes = sizeof(float) * (size_t)M.N * B;
+    const dim3 vg = vec_grid(M.N, B);
+    constexpr double kC1 = 1e-4;     // Armijo constant
+    constexpr int kHalvings = 12;    // backtracking steps per line search
+    float* g = c.vec(M.oG);
+    float* gt = c.vec(M.oGt);
+    float* xt = c.vec(M.oXt);
+    float* xa = c.vec(M.oXa);
+    float* ga = c.vec(M.oGa);
+    float* d = c.vec(M.oD);
+    double* costd = c.dbl(M.oCost);
+    int* flag = reinterpret_cast<int*>(c.base + M.oFlag);
+
+    std::vector<double> cost(3 * (size_t)B), L(B), gd(B), gmax(B), gg(B), step(B), coef(B);
+    (void)vbytes;
+    std::vector<double> rhoh((size_t)M.m * B, 0.0), gamma(B, 1.0), sy(B), yy(B);
+    std::vector<int> stopped(B, 0), accepted(B, 0), use(B, 0), keep(B, 0);
+    std::vector<int> done(B, 0);
+    auto read_costs = [&](std::vector<double>& Lout) -> meta_status {
+        L_TRY(cudaMemcpyAsync(cost.data(), costd, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost,
+                              c.st));
+        L_TRY(cudaStreamSynchronize(c.st));
+        for (int b = 0; b < B; ++b) Lout[b] = cost[3 * b] + cost[3 * b + 1] + cost[3 * b + 2];
+        return META_OK;
+    };
+    auto to_host = [&](const double* dev, std::vector<double>& h) -> meta_status {
+        L_TRY(cudaMemcpyAsync(h.data(), dev, sizeof(double) * B, cudaMemcpyDeviceToHost, c.st));
+        L_TRY(cudaStreamSynchronize(c.st));
+        return META_OK;
+    };
+    auto to_dev = [&](void* dev, const void* h, size_t bytes) -> meta_status {
+        L_TRY(cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, c.st));
+        L_TRY(cudaStreamSynchronize(c.st));  // the host vectors change right after
+        return META_OK;
+    };
+#define L_DO(x)                         \
+    do {                                \
+        const meta_status _s = (x);     \
+        if (_s != META_OK) return _s;   \
+    } while (0)
+
+    L_TRY(cudaMemsetAsync(d, 0, vbytes, c.st));
+    L_DO(meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, costd, g, ws, ws_bytes, c.st));
+    L_DO(read_costs(L));
+    if (cost_hist)
+        for (int b = 0; b < B; ++b) cost_hist[b] = L[b];
+    int h = 0, head = 0;
+    for (int k = 0; k < iters; ++k) {
+        // direction: the two-loop recursion, or a scaled steepest-descent step
+        // for an instance without a usable pair in the window or whose direction
+        // does not descend (its pairs are then forgotten)
+        if (h > 0) L_DO(two_loop(c, g, d, h, head));
+        L_DO(ldot<false>(c, g, d, c.dbl(M.oDot)));
+        L_DO(to_host(c.dbl(M.oDot), gd));
+        L_DO(ldot<true>(c, g, nullptr, c.dbl(M.oDot)));
+        L_DO(to_host(c.dbl(M.oDot), gmax));
+        L_DO(ldot<false>(c, g, g, c.dbl(M.oDot)));
+        L_DO(to_host(c.dbl(M.oDot), gg));
+        bool any_restart = false;
+        for (int b = 0; b < B; ++b) {
+            int nvalid = 0;
+            for (int i = 0; i < M.m; ++i) nvalid += rhoh[(size_t)i * B + b] != 0.0;
+            use[b] = (!stopped[b] && (nvalid == 0 || !(gd[b] < 0.0))) ? 1 : 0;
+            coef[b] = gmax[b] > 0.0 ? -(double)h0 / gmax[b] : 0.0;
+            if (use[b]) {
+                gd[b] = coef[b] * gg[b];
+                any_restart = any_restart || nvalid > 0;
+                for (int i = 0; i < M.m; ++i) rhoh[(size_t)i * B + b] = 0.0;  // forget
+                gamma[b] = 1.0;
+            }
+        }
+        L_DO(to_dev(flag, use.data(), sizeof(int) * B));
+        L_DO(to_dev(c.dbl(M.oCoef), coef.data(), sizeof(double) * B));
+        k_lsteep<<<vg, kLT, 0, c.st>>>(M.N, flag, c.dbl(M.oCoef), g, d);
+        L_TRY(cudaGetLastError());
+        if (any_restart) {
+            L_DO(to_dev(c.dbl(M.oRho), rhoh.data(), sizeof(double) * rhoh.size()));
+            L_DO(to_dev(c.dbl(M.oGamma), gamma.data(), sizeof(double) * B));
+        }
+        // backtracking Armijo line search, per instance
+        std::vector<double> Lt(B);
+        for (int b = 0; b < B; ++b) {
+            accepted[b] = 0;
+            step[b] = stopped[b] || !(gd[b] < 0.0) ? 0.0 : 1.0;
+            if (step[b] == 0.0) stopped[b] = 1;
+        }
+        for (int t = 0; t <= kHalvings; ++t) {
+            bool searching = false;
+            for (int b = 0; b < B; ++b) searching = searching || (!stopped[b] && !accepted[b]);
+            if (!searching) break;
+            std::vector<double> tstep(B);
+            for (int b = 0; b < B; ++b) tstep[b] = (!stopped[b] && !accepted[b]) ? step[b] : 0.0;
+            L_DO(to_dev(c.dbl(M.oStep), tstep.data(), sizeof(double) * B));
+            k_ltrial<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oStep), p0, d, xt);
+            L_TRY(cudaGetLastError());
+            L_DO(meta_cost_and_grad(prob, I0, J, xt, mu, rho, lambda, costd, gt, ws, ws_bytes,
+                                    c.st));
+            L_DO(read_costs(Lt));
+            for (int b = 0; b < B; ++b) {
+                keep[b] = 0;
+                if (stopped[b] || accepted[b]) continue;
+                if (Lt[b] <= L[b] + kC1 * step[b] * gd[b]) {
+                    accepted[b] = 1;
+                    keep[b] = 1;
+                    L[b] = Lt[b];
+                } else {
+                    step[b] *= 0.5;
+                }
+            }
+            L_DO(to_dev(flag, keep.data(), sizeof(int) * B));
+            k_lkeep<<<vg, kLT, 0, c.st>>>(M.N, flag, xt, gt, xa, ga);
+            L_TRY(cudaGetLastError());
+        }
+        for (int b = 0; b < B; ++b)
+            if (!accepted[b]) stopped[b] = 1;  // no decrease found: keep the iterate
+        // new pair (s, y) of the instances that moved; x and g advance
+        L_DO(to_dev(flag, accepted.data(), sizeof(int) * B));
+        k_lpair<<<vg, kLT, 0, c.st>>>(M.N, flag, p0, g, xa, ga, c.S(head), c.Y(head));
+        L_TRY(cudaGetLastError());
+        L_DO(ldot<false>(c, c.S(head), c.Y(head), c.dbl(M.oDot)));
+        L_DO(to_host(c.dbl(M.oDot), sy));
+        L_DO(ldot<false>(c, c.Y(head), c.Y(head), c.dbl(M.oDot)));
+        L_DO(to_host(c.dbl(M.oDot), yy));
+        for (int b = 0; b < B; ++b) {
+            const bool ok = accepted[b] && sy[b] > 1e-12 * yy[b] && yy[b] > 0.0;
+            rhoh[(size_t)head * B + b] = ok ? 1.0 / sy[b] : 0.0;
+            if (ok) gamma[b] = sy[b] / yy[b];
+            if (accepted[b]) done[b] = k + 1;
+        }
+        L_DO(to_dev(c.dbl(M.oRho), rhoh.data(), sizeof(double) * rhoh.size()));
+        L_DO(to_dev(c.dbl(M.oGamma), gamma.data(), sizeof(double) * B));
+        head = (head + 1) % M.m;
+        h = h < M.m ? h + 1 : M.m;
+        if (cost_hist)
+            for (int b = 0; b < B; ++b) cost_hist[(size_t)(k + 1) * B + b] = L[b];
+    }
+    if (iters_done)
+        for (int b = 0; b < B; ++b) iters_done[b] = done[b];
+#undef L_DO
+    return META_OK;
+}
+
+}  // extern "C"

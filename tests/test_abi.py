@@ -186,3 +186,29 @@ def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
                                   fake, ctypes.c_void_p(0x1010), need, null) == 3
     assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
                                   fake, fake, need - 1, null) == 3
+
+
+def test_lbfgs_arguments_fail_before_any_cuda_call(meta):
+    lib = meta._load()
+    pr = meta._problem(2, (16, 16), 2, 4, 2.0)
+    n = ctypes.c_size_t(0)
+    assert lib.meta_lbfgs_workspace_size(ctypes.byref(pr), 0, ctypes.byref(n)) == 1
+    assert lib.meta_lbfgs_workspace_size(ctypes.byref(pr), 65, ctypes.byref(n)) == 1
+    assert lib.meta_lbfgs_workspace_size(ctypes.byref(pr), 5, ctypes.byref(n)) == 0
+    need = n.value
+    # 2 x 5 pairs + 6 vectors of 2 x 256 floats, plus the per-instance scalars
+    assert need >= (2 * 5 + 6) * 2 * 256 * 4
+    assert meta.lbfgs_workspace_size((16, 16), 2, 5) == need
+    fake, null = ctypes.c_void_p(0x1000), ctypes.c_void_p(0)
+    ws = meta.workspace_size((16, 16), 2, 4, 2.0)
+    args = [ctypes.byref(pr), fake, fake, fake, fake, fake, fake]
+    # h0 <= 0, a null input, a short or misaligned L-BFGS workspace
+    assert lib.meta_lbfgs_minimize(*args, 3, 5, 0.0, fake, ws, fake, need, None, None, null) == 1
+    assert lib.meta_lbfgs_minimize(ctypes.byref(pr), null, fake, fake, fake, fake, fake, 3, 5,
+                                   0.1, fake, ws, fake, need, None, None, null) == 1
+    assert lib.meta_lbfgs_minimize(*args, 3, 5, 0.1, fake, ws, fake, need - 1, None, None,
+                                   null) == 3
+    assert lib.meta_lbfgs_minimize(*args, 3, 5, 0.1, fake, ws, ctypes.c_void_p(0x1010), need,
+                                   None, None, null) == 3
+    assert lib.meta_lbfgs_direction(ctypes.byref(pr), 5, 6, None, None, fake, fake, fake, need,
+                                    null) == 1

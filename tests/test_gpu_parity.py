@@ -219,6 +219,47 @@ def test_eulerian_momentum_total_full_size(meta, scheme):
         assert np.abs(p1[b] - p0[b]).max() > 1.0  # the momentum moved (oracle: by up to 66)
 
 
+# ----------------------------------------------------------------- L-BFGS
+
+def test_lbfgs_direction_matches_oracle(meta):
+    """Two instances, three pairs each; in instance 1 the middle pair has s.y < 0 and is
+    skipped.  Vectors are FP32, dot products FP64: relative L2 1e-5."""
+    dims, B = (33, 47), 2
+    r = np.random.default_rng(41)
+    S = [smooth_p(42 + i, (B,) + dims, 1.0) for i in range(3)]
+    Y = [(1.5 + 0.5 * i) * S[i] + 0.1 * smooth_p(52 + i, (B,) + dims, 1.0) for i in range(3)]
+    Y[1][1] = -Y[1][1]
+    g = smooth_p(60, (B,) + dims, 1.0)
+    d = meta.lbfgs_direction(cuda(g), [cuda(x) for x in S], [cuda(x) for x in Y], m=4)
+    d = d.cpu().numpy()
+    for b in range(B):
+        ref = oracle.lbfgs_direction(g[b], [x[b] for x in S], [x[b] for x in Y])
+        assert rel_l2(d[b], ref) <= 1e-5, b
+
+
+def test_lbfgs_minimize_follows_the_oracle(meta):
+    """Four L-BFGS iterations on two registrations at once (the 64^2 disk pair with
+    mu = 0.1 and with mu = 0): the GPU driver's cost history against the oracle's, same
+    rules.  Every line-search decision of these iterations clears the Armijo threshold
+    by at least 1e-4 of the cost (checked on the oracle's trials), far above the FP32
+    cost error, so both take the same steps."""
+    w = phantoms.disk_pair_64(random_p0=False)
+    I0 = np.concatenate([w.I0, w.I0]); J = np.concatenate([w.J, w.J])
+    p0 = np.zeros_like(I0)
+    mu, rho, lam = [0.1, 0.0], [1.0, 1.0], [1e-3, 1e-3]
+    iters, m, h0 = 4, 5, 0.5
+    p, hist, done = meta.lbfgs_minimize(cuda(I0), cuda(J), cuda(p0), w.T, w.sigma, mu, rho, lam,
+                                        iters=iters, m=m, h0=h0)
+    p = p.cpu().numpy()
+    for b in range(2):
+        x, h_ref, margins = oracle.lbfgs_minimize(I0[b], J[b], p0[b], w.T, w.sigma, mu[b],
+                                                  rho[b], lam[b], iters, m, h0)
+        assert min(abs(v) for it in margins for v in it) > 1e-4
+        np.testing.assert_allclose(hist[:, b], h_ref, rtol=1e-4)
+        assert rel_l2(p[b], x) <= 1e-3
+        assert done[b] == iters and h_ref[-1] < (0.25 if mu[b] > 0 else 0.9) * h_ref[0]
+
+
 # ----------------------------------------------------------------- deformation
 # phi_T - Id against the oracle within FWD_ATOL (scaled by max(1, |w|)), the same bar as
 # I_T.  det D phi_T differences w over one or two voxels, so each entry of D phi carries
