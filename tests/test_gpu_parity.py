@@ -583,6 +583,29 @@ def test_ellipse_batch_16x256_full_size(meta):
     check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam)
 
 
+def test_det_update_and_deformation_at_the_batch_size(meta):
+    """The 16 x 256^2 batch (T = 20, sigma 6, mu = 0) at a momentum that moves feet by up
+    to 0.7 voxel a step, with the det momentum update: cost and dL/dp0 of instances 0 and
+    3 against the oracle (the GPU runs the whole batch; there the two updates differ by
+    0.4 and 5.5 in p_T, and an FP32 torch run of the scheme is within 5e-8 of the oracle),
+    and the deformation of instance 2 against the oracle's."""
+    w = phantoms.ellipse_pairs()
+    p0 = smooth_p(65, w.p0.shape, 1500.0, s=4.0)
+    cost, grad = meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(p0), w.T, w.sigma, 0.0, w.rho,
+                                    w.lam, p_update="det")
+    cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
+    for b in (0, 3):
+        c, g = oracle.cost_and_grad(w.I0[b], w.J[b], p0[b], w.T, w.sigma, 0.0,
+                                    float(w.rho[b]), float(w.lam[b]), p_update="det")
+        np.testing.assert_allclose(cost[b], c, rtol=COST_RTOL, atol=1e-12)
+        assert rel_l2(grad[b], g) <= GRAD_RTOL, b
+    _, _, phi, jac, _ = meta.shoot_deform(cuda(w.I0), cuda(p0), w.T, w.sigma, 0.0, w.rho)
+    wr, Jr = oracle.deformation(w.I0[2], p0[2], w.T, w.sigma, 0.0, float(w.rho[2]))
+    assert np.abs(phi.cpu().numpy()[2] - wr).max() <= FWD_ATOL * max(1.0, np.abs(wr).max())
+    assert np.abs(jac.cpu().numpy()[2] - Jr).max() <= JAC_ATOL * max(1.0, np.abs(wr).max())
+    assert np.abs(wr).max() > 1.0
+
+
 def test_head_128_full_size(meta):
     """128^3, T=20, sigma=5 head phantom: cost and gradient at a smooth momentum,
     with a checkpoint every 5 steps (the workload's configuration) and without."""
