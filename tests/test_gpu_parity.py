@@ -621,6 +621,16 @@ def test_head_128_full_size(meta):
     assert torch.equal(c5, c0) and torch.equal(g5, g0)
 
 
+def test_mri_160_full_size_against_the_oracle(meta):
+    """160 x 192 x 160, T = 20, sigma 6, mu 0.05, lambda 1e-4 with a checkpoint every 5
+    steps (the benchmark's configuration): the whole cost and dL/dp0 against the FP64
+    oracle at full size (about a minute of the host's cores)."""
+    w = phantoms.mri_pair_3d()
+    oracle.set_threads(oracle.max_threads())
+    p0 = smooth_p(66, w.I0.shape, 3.0, s=3.0)
+    check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam, ckpt=5)
+
+
 def test_gradient_descent_follows_torch_autograd(meta):
     """Gradient descent on p0 driven by the hand-written adjoint and by torch.autograd
     through the same scheme in PyTorch ops (FP32, same GPU) follows the same path:
