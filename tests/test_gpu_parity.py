@@ -624,10 +624,12 @@ def test_head_128_full_size(meta):
 def test_mri_160_full_size_against_the_oracle(meta):
     """160 x 192 x 160, T = 20, sigma 6, mu 0.05, lambda 1e-4 with a checkpoint every 5
     steps (the benchmark's configuration): the whole cost and dL/dp0 against the FP64
-    oracle at full size (about a minute of the host's cores)."""
+    oracle at full size (about a minute of the host's cores), at a momentum that moves
+    feet by about 0.2 voxel a step (an FP32 torch run of the scheme on the central
+    80 x 96 x 80 block is within 2e-5 of the oracle there)."""
     w = phantoms.mri_pair_3d()
     oracle.set_threads(oracle.max_threads())
-    p0 = smooth_p(66, w.I0.shape, 3.0, s=3.0)
+    p0 = smooth_p(66, w.I0.shape, 1000.0, s=3.0)
     check_cost_grad(meta, w.I0, w.J, p0, w.T, w.sigma, w.mu, w.rho, w.lam, ckpt=5)
 
 
