@@ -376,6 +376,43 @@ def test_extreme_aspect_ratios(meta, dims, T, sigma):
                     np.array([1e-3, 1e-2]))
 
 
+@pytest.mark.parametrize("dims,B,T,sigma,p_update", [
+    ((21, 19), 3, 1, 1.5, "div"),       # a single step
+    ((11, 12, 13), 2, 1, 1.0, "det"),   # a single 3-D step, det update
+    ((17, 19), 40, 3, 1.2, "div"),      # many small instances in one launch (blockIdx.z)
+    ((9, 10, 11), 24, 2, 0.3, "div"),   # the narrowest kernel: sigma 0.3, r = 1
+    ((24, 30), 2, 64, 2.0, "det"),      # a long trajectory
+])
+def test_edge_cases_of_T_batch_and_sigma(meta, dims, B, T, sigma, p_update):
+    I0, J = phantoms.random_fields(151, B, dims)
+    p0 = smooth_p(152, (B,) + dims, 20.0 if len(dims) == 2 else 15.0, s=1.2)
+    mu = np.linspace(0.0, 0.2, B).astype(np.float32)
+    rho = np.linspace(0.8, 1.4, B).astype(np.float32)
+    lam = np.full(B, 1e-3, np.float32)
+    check_forward(meta, I0, p0, T, sigma, mu, rho, p_update=p_update)
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update)
+
+
+def test_deformation_with_the_det_update(meta):
+    I0, _ = phantoms.random_fields(153, 2, (30, 41))
+    p0 = smooth_p(154, (2, 30, 41), 40.0, s=1.5)
+    I1, p1, phi, jac, _ = meta.shoot_deform(cuda(I0), cuda(p0), 4, 2.0, [0.1, 0.0], 1.0,
+                                            p_update="det")
+    F1, q1, _ = meta.shoot_forward(cuda(I0), cuda(p0), 4, 2.0, [0.1, 0.0], 1.0, p_update="det")
+    torch.cuda.synchronize()
+    assert torch.equal(I1, F1) and torch.equal(p1, q1)
+    for b, mu in enumerate((0.1, 0.0)):
+        # the deformation integrates the v_t of the det-update shot: the oracle's shot
+        # with the same update gives the same v_t
+        It, pt, u = oracle.shoot(I0[b], p0[b], 4, 2.0, mu, 1.0, want_u=True, p_update="det")
+        X = np.stack(np.meshgrid(np.arange(30.0), np.arange(41.0), indexing="ij"))
+        ph = X.copy()
+        for t in range(4):
+            ph = np.stack([oracle.interp(ph[a], u[t] / 4.0) for a in range(2)])
+        assert np.abs(phi.cpu().numpy()[b] - (ph - X)).max() <= FWD_ATOL * max(1.0, np.abs(ph - X).max())
+        np.testing.assert_allclose(jac.cpu().numpy()[b], oracle.jacobian_det(ph), atol=JAC_ATOL)
+
+
 @pytest.mark.parametrize("p_update", ["div", "det"])
 @pytest.mark.parametrize("dims,seed,scale,T,sigma,mu,rho,lam", [
     ((70, 33), 21, 200.0, 5, 3.0, 0.2, 0.8, 1e-2),     # per-step |d|: .2 1.6 4.3 8.1 17
