@@ -27,7 +27,6 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-import sys
 from typing import Optional, Tuple
 
 import numpy as np
