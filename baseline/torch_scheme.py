@@ -134,10 +134,10 @@ def shoot(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu: torch.Te
     return (I, p, v0, traj) if keep else (I, p, v0)
 
 
-def cost(I0, J, p0, T, sigma, mu, rho, lam, p_update="div") -> torch.Tensor:
+def cost(I0, J, p0, T, sigma, mu, rho, lam, p_update="div", scheme="sl") -> torch.Tensor:
     """[B, 3]: data, lambda*kinetic, lambda*rho*residual (Eq. 4)."""
     B, nd = I0.shape[0], I0.dim() - 1
-    IT, _, u0 = shoot(I0, p0, T, sigma, mu, rho, p_update=p_update)
+    IT, _, u0 = shoot(I0, p0, T, sigma, mu, rho, p_update=p_update, scheme=scheme)
     m0 = p0.unsqueeze(1) * central_diff(I0)
     red = tuple(range(1, nd + 1))
     data = 0.5 * ((IT - J) ** 2).sum(red)
@@ -146,10 +146,10 @@ def cost(I0, J, p0, T, sigma, mu, rho, lam, p_update="div") -> torch.Tensor:
     return torch.stack([data, lam * kin, lam * rho * res], 1)
 
 
-def cost_and_grad(I0, J, p0, T, sigma, mu, rho, lam,
-                  p_update="div") -> Tuple[torch.Tensor, torch.Tensor]:
+def cost_and_grad(I0, J, p0, T, sigma, mu, rho, lam, p_update="div",
+                  scheme="sl") -> Tuple[torch.Tensor, torch.Tensor]:
     """Cost [B, 3] and dL/dp0 [B, *dims] by torch.autograd."""
     p = p0.detach().clone().requires_grad_(True)
-    c = cost(I0, J, p, T, sigma, mu, rho, lam, p_update)
+    c = cost(I0, J, p, T, sigma, mu, rho, lam, p_update, scheme)
     (g,) = torch.autograd.grad(c.sum(), p)
     return c.detach(), g

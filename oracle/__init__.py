@@ -12,7 +12,8 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``interp(F, disp, transpose=False)``    -- S(y) F with y = x + disp (or S(y)^T F)
 * ``shoot(I0, p0, T, sigma, mu, rho)``    -- states (I_t, p_t), t=0..T, and u_t
   (``p_update="det"`` on shoot / adjoint / cost_and_grad: p' = p~ det(Id - dt Dv);
-  ``scheme="euler"`` / ``"hybrid"`` on shoot: the other integration schemes of Sec. 2.3)
+  ``scheme="euler"`` / ``"hybrid"`` on shoot / adjoint / cost_and_grad: the other
+  integration schemes of Sec. 2.3)
 * ``adjoint(I0, p0, gI1, gp1, ...)``      -- gradient of <gI1,I_T>+<gp1,p_T> w.r.t. (I0, p0)
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
 * ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
@@ -74,10 +75,10 @@ def _load():
                                             ctypes.c_int, _D, _D, _D, _D, _D]
         lib.oracle_adjoint.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                       _D, _D, _D, _D, _D, _D]
+                                       ctypes.c_int, _D, _D, _D, _D, _D, _D]
         lib.oracle_cost_and_grad.argtypes = [ctypes.c_int, _L, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                             ctypes.c_int, _D, _D, _D, _D, _D]
+                                             ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         for f in ("oracle_blur", "oracle_diff", "oracle_interp", "oracle_shoot",
@@ -176,7 +177,7 @@ def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
 
 
 def adjoint(I0, p0, gI1, gp1, T: int, sigma: float, mu: float,
-            rho: float, p_update=0) -> Tuple[np.ndarray, np.ndarray]:
+            rho: float, p_update=0, scheme: str = "sl") -> Tuple[np.ndarray, np.ndarray]:
     """Returns (gI0, gp0) for the scalar <gI1, I_T> + <gp1, p_T>."""
     I0, p0, gI1 = _f64(I0), _f64(p0), _f64(gI1)
     gp1 = None if gp1 is None else _f64(gp1)
@@ -184,21 +185,24 @@ def adjoint(I0, p0, gI1, gp1, T: int, sigma: float, mu: float,
     gI0 = np.empty(shp)
     gp0 = np.empty(shp)
     _check(_load().oracle_adjoint(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                  float(rho), _pdet(p_update), _ptr(I0), _ptr(p0), _ptr(gI1),
-                                  _ptr(gp1), _ptr(gI0), _ptr(gp0)), "adjoint")
+                                  float(rho), _pdet(p_update), SCHEMES[scheme], _ptr(I0),
+                                  _ptr(p0), _ptr(gI1), _ptr(gp1), _ptr(gI0), _ptr(gp0)),
+           "adjoint")
     return gI0, gp0
 
 
 def cost_and_grad(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
-                  want_grad: bool = True, p_update=0) -> Tuple[np.ndarray, Optional[np.ndarray]]:
+                  want_grad: bool = True, p_update=0,
+                  scheme: str = "sl") -> Tuple[np.ndarray, Optional[np.ndarray]]:
     """Returns (cost3 = [data, lambda*kinetic, lambda*rho*residual], dL/dp0 or None)."""
     I0, J, p0 = _f64(I0), _f64(J), _f64(p0)
     shp = I0.shape
     c3 = np.zeros(3)
     g = np.empty(shp) if want_grad else None
     _check(_load().oracle_cost_and_grad(len(shp), _dims(shp), int(T), float(sigma), float(mu),
-                                        float(rho), float(lam), _pdet(p_update), _ptr(I0),
-                                        _ptr(J), _ptr(p0), _ptr(c3), _ptr(g)), "cost_and_grad")
+                                        float(rho), float(lam), _pdet(p_update), SCHEMES[scheme],
+                                        _ptr(I0), _ptr(J), _ptr(p0), _ptr(c3), _ptr(g)),
+           "cost_and_grad")
     return c3, g
 
 

@@ -511,6 +511,74 @@ int oracle_shoot_scheme(int ndim, const long* dims, int T, double sigma, double 
     return shoot_scheme(ndim, dims, T, sigma, mu, rho, pdet, scheme, I0, p0, Itraj, ptraj, utraj);
 }
 
+/* Transpose of one Eulerian (scheme 1) or hybrid (scheme 2) step up to v:
+ * from (Ih, ph), the adjoints of (I', p'), it writes Inew, pnew (the adjoints of
+ * (I, p) through every path except v) and vh (the adjoint of v).
+ *   Eulerian: I' = I - dt sum_a g_a v_a + dt mu p, g_a = D_a I
+ *   hybrid:   I' = I~ + dt mu p~ (the semi-Lagrangian image step)
+ *   both:     p' = p - dt sum_a D_a (p v_a) */
+static void other_scheme_T(const scheme_t* s, const double* I, const double* p, stepbuf_t* b,
+                           const double* Ih, const double* ph, double* pth, double* Inew,
+                           double* pnew, double** vh) {
+    const grid_t* g = &s->g;
+    const long N = g->N;
+    const int d = g->ndim;
+    const double dt = s->dt, mu = s->mu, rho = s->rho;
+    if (s->scheme == 1) {
+        for (long x = 0; x < N; ++x) {
+            Inew[x] = Ih[x];
+            pnew[x] = ph[x] + dt * mu * Ih[x];
+        }
+        for (int a = 0; a < d; ++a) {
+            for (long x = 0; x < N; ++x) vh[a][x] = -dt * Ih[x] * b->g[a][x];
+            /* g_a = D_a I  ->  I_hat += D_a^T (-dt I'_hat v_a) */
+            for (long x = 0; x < N; ++x) b->tmp[x] = -dt * Ih[x] * (-rho * b->u[a][x]);
+            diff_axis_T(g, a, b->tmp, b->tmp2);
+            for (long x = 0; x < N; ++x) Inew[x] += b->tmp2[x];
+        }
+    } else {
+        /* I~ = S I, p~ = S p, y = x - dt v: the adjoint of p~ is dt mu I'_hat */
+        for (long x = 0; x < N; ++x) pth[x] = dt * mu * Ih[x];
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < N; ++x) {
+            long c[3];
+            double disp[3];
+            foot_t ft;
+            coords(g, x, c);
+            displacement(s, b, x, disp);
+            foot_of(g, c, disp, &ft);
+            for (int a = 0; a < d; ++a)
+                vh[a][x] = -dt * (interp_deriv(g, &ft, a, I) * Ih[x] +
+                                  interp_deriv(g, &ft, a, p) * pth[x]);
+        }
+        memset(Inew, 0, sizeof(double) * (size_t)N);
+        memset(pnew, 0, sizeof(double) * (size_t)N);
+        for (long x = 0; x < N; ++x) {
+            long c[3], q;
+            double disp[3];
+            foot_t ft;
+            coords(g, x, c);
+            displacement(s, b, x, disp);
+            foot_of(g, c, disp, &ft);
+            for (int bb = 0; bb < (1 << d); ++bb) {
+                double wgt = corner(g, &ft, bb, &q);
+                Inew[q] += wgt * Ih[x];
+                pnew[q] += wgt * pth[x];
+            }
+        }
+        for (long x = 0; x < N; ++x) pnew[x] += ph[x];
+    }
+    /* p' = p - dt sum_a D_a f_a, f_a = p v_a:  f_hat_a = -dt D_a^T p'_hat */
+    for (int a = 0; a < d; ++a) {
+        diff_axis_T(g, a, ph, b->tmp);
+        for (long x = 0; x < N; ++x) {
+            const double fh = -dt * b->tmp[x];
+            pnew[x] += fh * (-rho * b->u[a][x]);
+            vh[a][x] += fh * p[x];
+        }
+    }
+}
+
 /* Reverse sweep through the T steps.  On entry Ih/ph hold the adjoints of
  * (I_T, p_T); on exit those of (I_0, p_0).  Every step recomputes its forward
  * quantities from the stored state (I_t, p_t).  The i-th line of the step
@@ -540,6 +608,10 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
         const double* I = Itraj + (long)t * N;
         const double* p = ptraj + (long)t * N;
         velocity(s, I, p, &b);
+        if (s->scheme != 0) {
+            other_scheme_T(s, I, p, &b, Ih, ph, pth, Inew, pnew, vh);
+            goto velocity_T;
+        }
 
         /* pointwise part: I' = I~ + dt mu p~ ; p' = p~ (1 - dt div), or
          * p' = p~ J with J = det M, M = Id - dt Dv, so that
@@ -599,6 +671,7 @@ static int adjoint_sweep(const scheme_t* s, const double* Itraj, const double* p
                 for (long x = 0; x < N; ++x) vh[a][x] += b.tmp[x];
             }
         }
+    velocity_T:
         for (int a = 0; a < d; ++a) {
             /* v_a = -rho u_a, u_a = K m_a  ->  m_hat_a = K^T(-rho v_hat_a), K^T = K */
             for (long x = 0; x < N; ++x) b.tmp[x] = -s->rho * vh[a][x];
@@ -630,11 +703,13 @@ done:
  * gradient of some scalar w.r.t. I_T, p_T; gp1 nullable = 0) returns its
  * gradient w.r.t. I0 (gI0, nullable) and p0 (gp0). */
 int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, double rho,
-                   int pdet, const double* I0, const double* p0, const double* gI1,
+                   int pdet, int scheme, const double* I0, const double* p0, const double* gI1,
                    const double* gp1, double* gI0, double* gp0) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
     int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet);
+    if (rc == 0 && (scheme < 0 || scheme > 2 || (scheme != 0 && pdet))) rc = -1;
+    if (rc == 0) s->scheme = scheme;
     if (rc != 0) {
         free(s);
         return -1;
@@ -645,7 +720,7 @@ int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, d
     double* Ih = (double*)malloc(sizeof(double) * (size_t)N);
     rc = -2;
     if (It && pt && Ih) {
-        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, pdet, I0, p0, It, pt, NULL);
+        rc = shoot_scheme(ndim, dims, T, sigma, mu, rho, pdet, scheme, I0, p0, It, pt, NULL);
         if (rc == 0) {
             memcpy(Ih, gI1, sizeof(double) * (size_t)N);
             if (gp1)
@@ -667,11 +742,13 @@ int oracle_adjoint(int ndim, const long* dims, int T, double sigma, double mu, d
  * cost3 = { 1/2 sum (I_T - J)^2, lambda sum_i <m0_i, K m0_i>, lambda rho sum p0^2 }.
  * grad (nullable) = dL/dp0.  pdet as in oracle_shoot. */
 int oracle_cost_and_grad(int ndim, const long* dims, int T, double sigma, double mu,
-                         double rho, double lambda, int pdet, const double* I0, const double* J,
-                         const double* p0, double* cost3, double* grad) {
+                         double rho, double lambda, int pdet, int scheme, const double* I0,
+                         const double* J, const double* p0, double* cost3, double* grad) {
     scheme_t* s = (scheme_t*)malloc(sizeof(scheme_t));
     if (!s) return -2;
     int rc = scheme_init(s, ndim, dims, T, sigma, mu, rho, pdet);
+    if (rc == 0 && (scheme < 0 || scheme > 2 || (scheme != 0 && pdet))) rc = -1;
+    if (rc == 0) s->scheme = scheme;
     if (rc != 0 || !(lambda >= 0.0)) {
         free(s);
         return -1;
@@ -686,7 +763,7 @@ int oracle_cost_and_grad(int ndim, const long* dims, int T, double sigma, double
     int have_b = stepbuf_alloc(&b, N, ndim, pdet) == 0;
     rc = -2;
     if (It && pt && Ih && ph && have_b) {
-        rc = oracle_shoot(ndim, dims, T, sigma, mu, rho, pdet, I0, p0, It, pt, NULL);
+        rc = shoot_scheme(ndim, dims, T, sigma, mu, rho, pdet, scheme, I0, p0, It, pt, NULL);
         if (rc == 0) {
             const double* IT = It + (long)T * N;
             double data = 0.0, kin = 0.0, res = 0.0;

@@ -273,17 +273,19 @@ def _fd_problem(dims, seed):
     return I, J, p
 
 
-@pytest.mark.parametrize("p_update", ["div", "det"])
+@pytest.mark.parametrize("p_update,scheme", [("div", "sl"), ("det", "sl"), ("div", "euler"),
+                                             ("div", "hybrid")])
 @pytest.mark.parametrize("dims,T,sigma", [((16, 16), 5, 1.5), ((8, 8, 8), 4, 1.0)])
-def test_gradient_matches_central_differences(dims, T, sigma, p_update):
+def test_gradient_matches_central_differences(dims, T, sigma, p_update, scheme):
     I, J, p = _fd_problem(dims, 20)
     args = (T, sigma, 0.25, 1.3, 0.05)
-    _, g = oracle.cost_and_grad(I, J, p, *args, p_update=p_update)
-    _, _, u = oracle.shoot(I, p, *args[:4], want_u=True, p_update=p_update)
+    kw = dict(p_update=p_update, scheme=scheme)
+    _, g = oracle.cost_and_grad(I, J, p, *args, **kw)
+    _, _, u = oracle.shoot(I, p, *args[:4], want_u=True, **kw)
     assert np.abs(u).max() * 1.3 / T > 0.05  # feet well away from grid nodes
 
     def L(q):
-        return oracle.cost_and_grad(I, J, q, *args, want_grad=False, p_update=p_update)[0].sum()
+        return oracle.cost_and_grad(I, J, q, *args, want_grad=False, **kw)[0].sum()
 
     r = np.random.default_rng(7)
     for _ in range(3):
@@ -292,12 +294,17 @@ def test_gradient_matches_central_differences(dims, T, sigma, p_update):
         fd = (L(p + eps * h) - L(p - eps * h)) / (2 * eps)
         an = (g * h).sum()
         assert abs(fd - an) < 2e-6 * abs(an) + 1e-9
-    # single coordinates, including edge voxels
+    # single coordinates, including edge voxels (central differences at h and h/2
+    # combined by Richardson extrapolation: truncation error O(h^4); the rounding of
+    # L itself, about 1e-16 |L| / h, sets the absolute floor)
+    floor = 1e-8 + 1e-11 * abs(L(p))
     for idx in [(0,) * len(dims), tuple(n // 2 for n in dims), tuple(n - 1 for n in dims)]:
         e = np.zeros(dims)
         e[idx] = 1.0
-        fd = (L(p + 1e-4 * e) - L(p - 1e-4 * e)) / 2e-4
-        assert abs(fd - g[idx]) < 1e-6 * abs(g[idx]) + 1e-8
+        d1 = (L(p + 1e-4 * e) - L(p - 1e-4 * e)) / 2e-4
+        d2 = (L(p + 5e-5 * e) - L(p - 5e-5 * e)) / 1e-4
+        fd = (4.0 * d2 - d1) / 3.0
+        assert abs(fd - g[idx]) < 1e-6 * abs(g[idx]) + floor
 
 
 def test_taylor_remainder_is_second_order():
@@ -313,19 +320,21 @@ def test_taylor_remainder_is_second_order():
     assert 3.0 < rem[0] / rem[1] < 5.0 and 3.0 < rem[1] / rem[2] < 5.0
 
 
-@pytest.mark.parametrize("p_update", ["div", "det"])
-def test_adjoint_of_shooting_map_dot_product(p_update):
+@pytest.mark.parametrize("p_update,scheme", [("div", "sl"), ("det", "sl"), ("div", "euler"),
+                                             ("div", "hybrid")])
+def test_adjoint_of_shooting_map_dot_product(p_update, scheme):
     """<gI1, dI_T> + <gp1, dp_T> = <gI0, dI0> + <gp0, dp0> for a tangent (dI0, dp0)."""
     dims = (12, 13)
     I, J, p = _fd_problem(dims, 40)
     args = (4, 1.3, 0.4, 1.1)
+    kw = dict(p_update=p_update, scheme=scheme)
     r = np.random.default_rng(9)
     gI1, gp1 = r.normal(size=dims), r.normal(size=dims)
     dI, dp = r.normal(size=dims), r.normal(size=dims)
-    gI0, gp0 = oracle.adjoint(I, p, gI1, gp1, *args, p_update=p_update)
+    gI0, gp0 = oracle.adjoint(I, p, gI1, gp1, *args, **kw)
     eps = 1e-6
-    Ap = oracle.shoot(I + eps * dI, p + eps * dp, *args, p_update=p_update)
-    Am = oracle.shoot(I - eps * dI, p - eps * dp, *args, p_update=p_update)
+    Ap = oracle.shoot(I + eps * dI, p + eps * dp, *args, **kw)
+    Am = oracle.shoot(I - eps * dI, p - eps * dp, *args, **kw)
     tang = ((Ap[0][-1] - Am[0][-1]) * gI1).sum() + ((Ap[1][-1] - Am[1][-1]) * gp1).sum()
     tang /= 2 * eps
     adj = (gI0 * dI).sum() + (gp0 * dp).sum()
@@ -517,18 +526,23 @@ def test_eulerian_momentum_conserves_its_total(dims, scheme):
 @pytest.mark.parametrize("dims", [(16, 20), (9, 11, 10)])
 def test_other_schemes_match_the_torch_implementation(dims, scheme):
     """The Eulerian and hybrid steps written with torch ops (FP64: conv blur, replicate-
-    padded central differences, grid_sample) reproduce the oracle's."""
+    padded central differences, grid_sample) reproduce the oracle's shot, and torch.autograd
+    through them its cost and dL/dp0 (the oracle's hand-written transposes)."""
     torch = pytest.importorskip("torch")
     from baseline import torch_scheme as ts
-    I, _, p = _fd_problem(dims, 60)
-    T, sig, mu, rho = 6, 1.5, 0.2, 1.3
+    I, J, p = _fd_problem(dims, 60)
+    T, sig, mu, rho, lam = 6, 1.5, 0.2, 1.3, 1e-2
     It, pt, _ = oracle.shoot(I, p, T, sig, mu, rho, scheme=scheme)
     t = lambda a: torch.tensor(np.asarray(a)[None], dtype=torch.float64)
-    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, torch.tensor([mu], dtype=torch.float64),
-                         torch.tensor([rho], dtype=torch.float64), scheme=scheme)
+    tmu, trho = torch.tensor([mu], dtype=torch.float64), torch.tensor([rho], dtype=torch.float64)
+    IT, pT, _ = ts.shoot(t(I), t(p), T, sig, tmu, trho, scheme=scheme)
     np.testing.assert_allclose(IT[0].numpy(), It[-1], atol=1e-12)
     np.testing.assert_allclose(pT[0].numpy(), pt[-1], atol=1e-11 * np.abs(pt[-1]).max())
     assert np.abs(It[-1] - I).max() > 1e-2
+    c, g = oracle.cost_and_grad(I, J, p, T, sig, mu, rho, lam, scheme=scheme)
+    c2, g2 = ts.cost_and_grad(t(I), t(J), t(p), T, sig, tmu, trho, lam, scheme=scheme)
+    np.testing.assert_allclose(c2[0].numpy(), c, rtol=1e-12)
+    np.testing.assert_allclose(g2[0].numpy(), g, atol=1e-12 * np.abs(g).max())
 
 
 def test_eulerian_scheme_is_first_order_in_time():
