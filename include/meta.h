@@ -59,8 +59,7 @@ typedef enum {
     META_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed */
     META_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out */
     META_ERR_NONFINITE = 6,   /* reserved: non-finite cost detected */
-    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, the driver lacks TMA support, or the
-                                 call needs the adjoint of a forward-only scheme */
+    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, or the driver lacks TMA support */
 } meta_status;
 
 /* Shape of one batch of independent registration problems. */
@@ -84,10 +83,9 @@ typedef struct {
                         steps of Eq. 5, I' = I - dt <grad I, v> + dt mu p, and of the
                         conservative Eq. 7, p' = p - dt div(p v), central differences);
                         META_SCHEME_HYBRID (2: the semi-Lagrangian I' with that Eulerian
-                        p').  The Eulerian and hybrid schemes are forward only:
-                        meta_shoot_forward and meta_shoot_deform take them, the calls
-                        that need the adjoint return META_ERR_UNSUPPORTED.
-                        META_P_UPDATE_DET requires META_SCHEME_SL. */
+                        p').  Every call takes every scheme; the adjoint is the exact
+                        transpose of the chosen one.  META_P_UPDATE_DET requires
+                        META_SCHEME_SL. */
 } meta_problem;
 
 #define META_P_UPDATE_DIV 0

@@ -151,11 +151,13 @@ def _problem(ndim: int, dims: Sequence[int], batch: int, T: int, sigma: float,
                     int(ckpt), _pupd(p_update), _scheme(scheme))
 
 
-def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float, ckpt: int = 0) -> int:
+def workspace_size(dims: Sequence[int], batch: int, T: int, sigma: float, ckpt: int = 0,
+                   scheme: str = "sl") -> int:
     """Workspace bytes; ckpt > 1 keeps every ckpt-th state and recomputes the rest."""
     n = ctypes.c_size_t(0)
     rc = _load().meta_workspace_size(
-        ctypes.byref(_problem(len(dims), dims, batch, T, sigma, ckpt)), ctypes.byref(n))
+        ctypes.byref(_problem(len(dims), dims, batch, T, sigma, ckpt, 0, scheme)),
+        ctypes.byref(n))
     if rc:
         raise MetaError(rc, "meta_workspace_size")
     return int(n.value)
@@ -169,15 +171,19 @@ class Workspace:
     """
 
     def __init__(self, dims: Sequence[int], batch: int, T: int, sigma: float,
-                 device: Union[torch.device, str, int] = "cuda", ckpt: int = 0):
-        self.key = (tuple(int(x) for x in dims), int(batch), int(T), float(sigma), int(ckpt))
+                 device: Union[torch.device, str, int] = "cuda", ckpt: int = 0,
+                 scheme: str = "sl"):
+        _scheme(scheme)
+        self.key = (tuple(int(x) for x in dims), int(batch), int(T), float(sigma), int(ckpt),
+                    scheme)
         self.ckpt = int(ckpt)
-        self.nbytes = workspace_size(dims, batch, T, sigma, ckpt)
+        self.scheme = scheme
+        self.nbytes = workspace_size(dims, batch, T, sigma, ckpt, scheme)
         self.buf = torch.zeros(self.nbytes, dtype=torch.uint8, device=device)
 
-    def matches(self, dims, batch, T, sigma, ckpt: int = 0) -> bool:
+    def matches(self, dims, batch, T, sigma, ckpt: int = 0, scheme: str = "sl") -> bool:
         return self.key == (tuple(int(x) for x in dims), int(batch), int(T), float(sigma),
-                            int(ckpt))
+                            int(ckpt), scheme)
 
     def ptr(self) -> int:
         return self.buf.data_ptr()
@@ -241,16 +247,17 @@ def _p(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
 _ws_cache = {}
 
 
-def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0) -> Workspace:
+def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0,
+               scheme: str = "sl") -> Workspace:
     if ws is not None:
-        if not ws.matches(dims, B, T, sigma, ckpt):
+        if not ws.matches(dims, B, T, sigma, ckpt, scheme):
             raise ValueError("workspace was made for another problem")
         return ws
-    key = (tuple(dims), B, T, float(sigma), int(ckpt), str(device),
+    key = (tuple(dims), B, T, float(sigma), int(ckpt), scheme, str(device),
            torch.cuda.current_stream(device).cuda_stream)
     w = _ws_cache.get(key)
     if w is None:
-        w = Workspace(dims, B, T, sigma, device, ckpt)
+        w = Workspace(dims, B, T, sigma, device, ckpt, scheme)
         _ws_cache[key] = w
     return w
 
@@ -264,7 +271,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     I1 = torch.empty_like(I0b)
     p1 = torch.empty_like(I0b)
@@ -292,7 +299,7 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     I1 = torch.empty_like(I0b)
     p1 = torch.empty_like(I0b)
@@ -313,18 +320,19 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
 
 def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Workspace, T: int,
                   sigma: float, mu, rho=1.0, want_gI0: bool = True, ndim: Optional[int] = None,
-                  p_update=0) -> Tuple[Optional[torch.Tensor], torch.Tensor]:
+                  p_update=0, scheme: str = "sl") -> Tuple[Optional[torch.Tensor], torch.Tensor]:
     """Adjoint of the shooting map on the trajectory kept in `workspace` (shot with the
-    same p_update): returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1, dL/dp_T = gp1."""
+    same p_update and scheme): returns (dL/dI0 or None, dL/dp0) for dL/dI_T = gI1,
+    dL/dp_T = gp1."""
     g1, nd, dims, sq = _shape(_as_batch(gI1, "gI1")[0], ndim)
     B, dev = g1.shape[0], g1.device
-    if not workspace.matches(dims, B, T, sigma, workspace.ckpt):
+    if not workspace.matches(dims, B, T, sigma, workspace.ckpt, scheme):
         raise ValueError("workspace was made for another problem")
     gp1b = None if gp1 is None else _as_batch(gp1, "gp1")[0].reshape(g1.shape)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     gp0 = torch.empty_like(g1)
     gI0 = torch.empty_like(g1) if want_gI0 else None
-    pr = _problem(nd, dims, B, T, sigma, workspace.ckpt, p_update)
+    pr = _problem(nd, dims, B, T, sigma, workspace.ckpt, p_update, scheme)
     rc = _load().meta_shoot_adjoint(ctypes.byref(pr), _p(mu_t), _p(rho_t), _p(g1), _p(gp1b),
                                     _p(gI0), _p(gp0), ctypes.c_void_p(workspace.ptr()),
                                     workspace.nbytes, _stream(dev))
@@ -348,7 +356,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt)
+    ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     if out is not None:
         cost, grad = out
@@ -478,7 +486,7 @@ class CostAndGradPlan:
     """
 
     def __init__(self, I0, J, p0, T: int, sigma: float, mu, rho=1.0, lam=1e-3,
-                 ndim: Optional[int] = None, ckpt: int = 0, p_update=0):
+                 ndim: Optional[int] = None, ckpt: int = 0, p_update=0, scheme: str = "sl"):
         I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
         B, dev = I0b.shape[0], I0b.device
         self.I0 = I0b.clone()
@@ -488,9 +496,9 @@ class CostAndGradPlan:
                                        _coef(lam, B, dev).clone())
         self.cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         self.grad = torch.empty_like(I0b)
-        self.ws = Workspace(dims, B, T, sigma, dev, ckpt)
+        self.ws = Workspace(dims, B, T, sigma, dev, ckpt, scheme)
         self.device = dev
-        pr = _problem(nd, dims, B, T, sigma, ckpt, p_update)
+        pr = _problem(nd, dims, B, T, sigma, ckpt, p_update, scheme)
         h = ctypes.c_void_p(0)
         torch.cuda.synchronize(dev)
         rc = _load().meta_plan_create(ctypes.byref(pr), _p(self.I0), _p(self.J), _p(self.p0),

@@ -84,7 +84,7 @@ struct Rec {
 // Record of step t at voxel v from I^' = Ih1, p^' = ph1, the displacement d
 // of the foot per axis and fac = div v_t (PDET: fac = J = det(Id - dt Dv_t))
 // (the same expressions as the forward step), with p_t at pprev.
-template <int NDIM, bool PDET = false>
+template <int NDIM, bool PDET = false, bool HYB = false>
 __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
                                             long long o, float Ih1, float ph1, const float* d,
                                             float fac, const float* __restrict__ pprev,
@@ -92,12 +92,15 @@ __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, cons
     const int b = v.b;
     const float mu = cf.mu[b], dt = cf.dt;
     const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-    float pw;
-    if constexpr (NDIM == 2)
+    float pw = 0.f;
+    if constexpr (HYB) {
+        // the hybrid's momentum step is Eulerian: p~ is not used and div^ = 0
+    } else if constexpr (NDIM == 2) {
         pw = rn_bilin(pprev + F.base, g.P, F.f[0].f, F.f[1].f);
-    else
+    } else {
         pw = rn_trilin(pprev + F.base, pprev + F.base + g.slab, g.P, F.f[0].f, F.f[1].f,
                        F.f[2].f);
+    }
     const int c[3] = {NDIM == 3 ? v.z : v.y, NDIM == 3 ? v.y : v.x, v.x};
     int off[3] = {0, 0, 0};
     bool ins[3] = {false, false, false};
@@ -112,15 +115,21 @@ __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, cons
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) r[(1 + a) * sl] = F.f[a].f;
     r[Rec<NDIM>::kI * sl] = Ih1;
-    r[Rec<NDIM>::kP * sl] = PDET ? rn_ptilde_hat_J(ph1, Ih1, dt, mu, fac)
-                                 : rn_ptilde_hat(ph1, Ih1, dt, mu, fac);
-    r[Rec<NDIM>::kD * sl] = rn_div_hat(dt, pw, ph1);
+    if constexpr (HYB) {
+        // I' = I~ + dt mu p~: the adjoint of p~ is dt mu I^'
+        r[Rec<NDIM>::kP * sl] = __fmul_rn(__fmul_rn(dt, mu), Ih1);
+        r[Rec<NDIM>::kD * sl] = 0.f;
+    } else {
+        r[Rec<NDIM>::kP * sl] = PDET ? rn_ptilde_hat_J(ph1, Ih1, dt, mu, fac)
+                                     : rn_ptilde_hat(ph1, Ih1, dt, mu, fac);
+        r[Rec<NDIM>::kD * sl] = rn_div_hat(dt, pw, ph1);
+    }
 }
 
 // Record of step t at voxel v (pitched offset o in its instance) from
 // I^' = Ih1 and p^' = ph1; state t sits in slot s_state, u_t in slot s_u.  The
 // same expressions as the forward step t.
-template <int NDIM, bool PDET = false>
+template <int NDIM, bool PDET = false, bool HYB = false>
 __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
                                              const Vox& v, long long o, float Ih1, float ph1,
                                              const float* __restrict__ states,
@@ -149,8 +158,9 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
         }
     }
     const float fac = PDET ? rn_jac_det<NDIM>(A, dtrho) : __fmul_rn(-rho, du);
-    emit_record<NDIM, PDET>(g, cf, v, o, Ih1, ph1, d, fac,
-                            slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b), rec);
+    emit_record<NDIM, PDET, HYB>(g, cf, v, o, Ih1, ph1, d, fac,
+                                 slice_of(states, g, ((long long)s_state * 2 + 1) * g.B + b),
+                                 rec);
 }
 
 // build_record with the momentum update of the call (cf.pdet), for kernels
@@ -160,10 +170,28 @@ __device__ __forceinline__ void build_record_any(const Geom& g, const Coefs& cf,
                                                  int s_u, const Vox& v, long long o, float Ih1,
                                                  float ph1, const float* __restrict__ states,
                                                  const float* __restrict__ u, float* rec) {
-    if (cf.pdet)
+    if (cf.scheme == 2)
+        build_record<NDIM, false, true>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
+    else if (cf.pdet)
         build_record<NDIM, true>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
     else
         build_record<NDIM, false>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
+}
+
+// The start of the adjoint from the adjoints (Ih1, ph1) of (I_T, p_T): the
+// record of step T-1 (semi-Lagrangian, hybrid) and the raw adjoints the
+// Eulerian steps read (Eulerian: both; hybrid: ph1 for its momentum step).
+template <int NDIM>
+__device__ __forceinline__ void adjoint_start(const Geom& g, const Coefs& cf, int s_state,
+                                              int s_u, const Vox& v, long long o, float Ih1,
+                                              float ph1, const float* __restrict__ states,
+                                              const float* __restrict__ u, float* rec,
+                                              float* rawI, float* rawP) {
+    const long long ob = (long long)v.b * g.inst + o;
+    if (cf.scheme != 1)
+        build_record_any<NDIM>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
+    if (cf.scheme == 1) rawI[ob] = Ih1;
+    if (cf.scheme != 0) rawP[ob] = ph1;
 }
 
 // Packed per-axis weights of a source whose foot moved by less than one voxel:
@@ -189,7 +217,7 @@ __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
                 const float* __restrict__ u, const float* __restrict__ J,
                 const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php,
-                double* partials) {
+                float* rawI, float* rawP, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const int b = blockIdx.y;
@@ -225,7 +253,7 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
             kin += (double)(p * ga) * (double)ua[o];
         }
         res += (double)p * (double)p;
-        build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec);
+        adjoint_start<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec, rawI, rawP);
         if (zero_sums) {  // scatter accumulators start at zero
             slice_of(Ihp, g, b)[o] = 0.f;
             slice_of(php, g, b)[o] = 0.f;
@@ -275,15 +303,15 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
            const float* __restrict__ u, const float* __restrict__ gI1,
            const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec,
-           float* Ihp, float* php) {
+           float* Ihp, float* php, float* rawI, float* rawP) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
-    build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u,
-                           rec);
+    adjoint_start<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u,
+                        rec, rawI, rawP);
     if (gather_radius(maxdisp, g.nT - 1, g.B, v.b) > GatherTile<NDIM>::RMAX) {
         slice_of(Ihp, g, v.b)[o] = 0.f;  // the first transport scatters into these
         slice_of(php, g, v.b)[o] = 0.f;
@@ -1029,6 +1057,86 @@ k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float*
     for (int a = 0; a < NDIM; ++a) slice_of(vh, g, (long long)a * g.B + b)[o] += acc[a];
 }
 
+// Adjoint of one Eulerian step (I' = I - dt sum_a (D_a I) v_a + dt mu p,
+// p' = p - dt sum_a D_a (p v_a), v = -rho u_t) up to v, from the raw adjoints
+// I^', p^' (rawI, rawP) of step t+1:
+//   Ihp = I^' + sum_a D_a^T (-dt I^' v_a)
+//   php = p^' + dt mu I^' + sum_a f^_a v_a,    f^_a = -dt D_a^T p^'
+//   v^_a = -dt I^' D_a I + f^_a p
+// The blur of v^ and k_adj_gradp (raw mode) complete the step.
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_euler_adj(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
+            const float* __restrict__ u, const float* __restrict__ rawI,
+            const float* __restrict__ rawP, float* Ihp, float* php, float* vh) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    const float* RI = slice_of(rawI, g, b);
+    const float* RP = slice_of(rawP, g, b);
+    const float Ih = RI[o];
+    float Inew = Ih, pnew = RP[o] + (dt * mu) * Ih;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
+        const long long sa = s[a];
+        // D_a^T of f = -dt I^' v_a = dt rho I^' u_a at this node
+        auto f = [&](long long q) { return (dt * rho) * (RI[q] * ua[q]); };
+        float r = 0.f;
+        if (c[a] >= 1) r += 0.5f * f(o - sa);
+        if (c[a] == n[a] - 1) r += 0.5f * f(o);
+        if (c[a] <= n[a] - 2) r -= 0.5f * f(o + sa);
+        if (c[a] == 0) r -= 0.5f * f(o);
+        Inew += r;
+        const float fh = -dt * cdiff_T(RP, o, sa, c[a], n[a]);
+        const float va = -rho * ua[o];
+        pnew += fh * va;
+        const float ga = cdiff(It, o, sa, c[a], n[a]);
+        vh[((long long)a * g.B + b) * g.inst + o] = -dt * Ih * ga + fh * pt[o];
+    }
+    slice_of(Ihp, g, b)[o] = Inew;
+    slice_of(php, g, b)[o] = pnew;
+}
+
+// The Eulerian momentum step of the hybrid scheme, transposed, added to what
+// the semi-Lagrangian transport left for its image step:
+//   php += p^' + sum_a f^_a v_a,   v^_a += f^_a p,   f^_a = -dt D_a^T p^'
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_hybrid_p(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
+           const float* __restrict__ u, const float* __restrict__ rawP, float* php, float* vh) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    const Vox v = vox_of<NDIM>(g);
+    if (!v.ok) return;
+    const int b = v.b;
+    const float rho = cf.rho[b], dt = cf.dt;
+    const long long o = gidx(g, v.z, v.y, v.x);
+    int c[NDIM], n[NDIM];
+    long long s[NDIM];
+    axis_info<NDIM>(g, v, c, n, s);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    const float* RP = slice_of(rawP, g, b);
+    float pnew = RP[o];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
+        const float fh = -dt * cdiff_T(RP, o, s[a], c[a], n[a]);
+        pnew += fh * (-rho * ua[o]);
+        vh[((long long)a * g.B + b) * g.inst + o] += fh * pt[o];
+    }
+    slice_of(php, g, b)[o] += pnew;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1036,14 +1144,15 @@ k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float*
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                         const float* states, const float* u, const float* J,
                         const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
-                        double* partials, int nblk, double* cost, cudaStream_t st) {
+                        float* rawI, float* rawP, double* partials, int nblk, double* cost,
+                        cudaStream_t st) {
     const dim3 grid(nblk, g.B);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   maxdisp, rec, Ihp, php, partials));
+                                   maxdisp, rec, Ihp, php, rawI, rawP, partials));
     else
         META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   maxdisp, rec, Ihp, php, partials));
+                                   maxdisp, rec, Ihp, php, rawI, rawP, partials));
     META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
     return cudaSuccess;
 }
@@ -1051,14 +1160,14 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl
 cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* states, const float* u, const float* gI1,
                             const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp,
-                            float* php, cudaStream_t st) {
+                            float* php, float* rawI, float* rawP, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, maxdisp, rec, Ihp, php));
+                                   gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
     else
         META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, maxdisp, rec, Ihp, php));
+                                   gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
     return cudaSuccess;
 }
 
@@ -1122,6 +1231,33 @@ cudaError_t launch_adj_jacT(const Geom& g, int ndim, const Coefs& c, const Slots
         META_CHECK_LAUNCH(launch_k(k_adj_jacT<2>, pgrid<2>(g), blk, 0, st, g, c, sl, u, rec, vh));
     else
         META_CHECK_LAUNCH(launch_k(k_adj_jacT<3>, pgrid<3>(g), blk, 0, st, g, c, sl, u, rec, vh));
+    return cudaSuccess;
+}
+
+cudaError_t launch_euler_adj(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                             const float* states, const float* u, const float* rawI,
+                             const float* rawP, float* Ihp, float* php, float* vh,
+                             cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_euler_adj<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawI, rawP, Ihp, php, vh));
+    else
+        META_CHECK_LAUNCH(launch_k(k_euler_adj<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawI, rawP, Ihp, php, vh));
+    return cudaSuccess;
+}
+
+cudaError_t launch_hybrid_p(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* states, const float* u, const float* rawP, float* php,
+                            float* vh, cudaStream_t st) {
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2)
+        META_CHECK_LAUNCH(launch_k(k_hybrid_p<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawP, php, vh));
+    else
+        META_CHECK_LAUNCH(launch_k(k_hybrid_p<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
+                                   rawP, php, vh));
     return cudaSuccess;
 }
 

@@ -181,7 +181,8 @@ Layout make_layout(const meta_problem* pr) {
     L.off_REC = take(fslice * (size_t)(d + 4) * B);
     L.off_IHP = take(fslice * B);
     L.off_PHP = take(fslice * B);
-    L.off_RAW = L.k ? take(fslice * 2 * B) : 0;  // raw I^, p^ at segment starts
+    // raw I^, p^: at segment starts (stride k), or every step (Eulerian, hybrid)
+    L.off_RAW = (L.k || L.scheme != META_SCHEME_SL) ? take(fslice * 2 * B) : 0;
     L.total = off;
     return L;
 }
@@ -282,6 +283,9 @@ struct Ctx {
     float *states, *u, *SA, *SB, *SV, *REC, *IHP, *PHP, *RAW;
 };
 
+// Raw p^ half of the RAW region (NULL when RAW is not allocated).
+float* raw_p(const Ctx& c) { return c.RAW ? c.RAW + (size_t)c.L.g.B * c.L.g.inst : nullptr; }
+
 meta_status map_status(cudaError_t e) { return e == cudaSuccess ? META_OK : META_ERR_CUDA; }
 
 // Optional per-launch event timer (profiling aid; see meta_timer_start).
@@ -327,7 +331,7 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     c->SB = F(L.off_SB);
     c->SV = F(L.off_SV);
     c->REC = F(L.off_REC);
-    c->RAW = L.k ? F(L.off_RAW) : nullptr;
+    c->RAW = L.off_RAW ? F(L.off_RAW) : nullptr;
     c->IHP = F(L.off_IHP);
     c->PHP = F(L.off_PHP);
     make_taps(pr->sigma, &c->tx, &c->ts);
@@ -399,8 +403,8 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
                         launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.st));
         else
             META_LAUNCH(META_K_EULER, c.st,
-                        launch_euler(g, d, cf, sl, L.scheme == META_SCHEME_HYBRID, c.states, c.u,
-                                     c.st));
+                        launch_euler(g, d, cf, t, sl, L.scheme == META_SCHEME_HYBRID, c.states,
+                                     c.u, c.maxdisp, c.st));
     }
     return META_OK;
 }
@@ -458,7 +462,10 @@ Slots start_slots(const Layout& L) {
 // but the last (still in place after the forward) is recomputed before its
 // steps; the adjoint of the segment's first step writes raw I^, p^ whose
 // record is built once the previous segment is back.
+meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0);
+
 meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
+    if (c.L.scheme != META_SCHEME_SL) return run_adjoint_other(c, cf, mode, out0, gI0);
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
@@ -522,6 +529,73 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
     return META_OK;
 }
 
+// Adjoint sweep of the Eulerian (one pointwise transpose per step) and hybrid
+// schemes (its semi-Lagrangian image step through the records and the gather
+// transport, then the Eulerian momentum part); both then blur v^ and run
+// k_adj_gradp, which leaves the raw I^_t, p^_t in RAW for the step before
+// (mode 3) or the outputs at t = 0.
+meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
+    const Layout& L = c.L;
+    const Geom& g = L.g;
+    const int d = L.ndim, B = g.B;
+    const int s_last = L.seg_of(L.T - 1);
+    float* rawI = c.RAW;
+    float* rawP = raw_p(c);
+    for (int t = L.T - 1; t >= 0; --t) {
+        const int s = L.seg_of(t);
+        if (L.k && s != s_last && t == L.seg_end(s) - 1) {
+            const meta_status st = recompute_segment(c, cf, s);
+            if (st != META_OK) return st;
+        }
+        Slots sl{};
+        sl.st = L.state_slot(t, s);
+        sl.ut = L.u_slot(t);
+        sl.u0 = L.u_slot(0);
+        if (L.scheme == META_SCHEME_EULER) {
+            META_LAUNCH(META_K_ADJ_GATHER, c.st,
+                        launch_euler_adj(g, d, cf, sl, c.states, c.u, rawI, rawP, c.IHP, c.PHP,
+                                         c.SV, c.st));
+        } else {
+            if (t < L.T - 1) {  // the record of step T-1 comes from the adjoint start
+                Slots rs{};
+                rs.st1 = sl.st;
+                rs.ut1 = sl.ut;
+                META_LAUNCH(META_K_ADJ_INIT, c.st,
+                            launch_adj_records(g, d, cf, rs, c.states, c.u, rawI, rawP, c.REC,
+                                               c.st));
+            }
+            META_LAUNCH(META_K_ADJ_GATHER, c.st,
+                        launch_adj_transport(g, d, cf, t, sl, c.states, c.maxdisp, c.REC, c.SV,
+                                             c.IHP, c.PHP, c.fault, c.st));
+            META_LAUNCH(META_K_ADJ_GATHER, c.st,
+                        launch_hybrid_p(g, d, cf, sl, c.states, c.u, rawP, c.PHP, c.SV, c.st));
+        }
+        META_LAUNCH(META_K_XPASS_ADJ, c.st,
+                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
+                                 c.fault, c.st));
+        float* mh;
+        if (d == 2) {
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(2, 0, c.tmSAy, c.ts, g, 0, 0, d * B, cf.rho, -1.f, c.SB,
+                                       c.fault, c.st));
+            mh = c.SB;
+        } else {
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(3, 1, c.tmSAy, c.ts, g, 0, 0, d * B, nullptr, 1.f, c.SB,
+                                       c.fault, c.st));
+            META_LAUNCH(META_K_STRIDED_ADJ, c.st,
+                        launch_strided(3, 0, c.tmSBz, c.ts, g, 0, 0, d * B, cf.rho, -1.f, c.SV,
+                                       c.fault, c.st));
+            mh = c.SV;
+        }
+        META_LAUNCH(META_K_ADJ_GRADP, c.st,
+                    launch_adj_gradp(g, d, cf, t, t == 0 ? mode : 3, sl, c.states, c.u,
+                                     c.maxdisp, mh, c.IHP, c.PHP, c.REC, rawI, rawP, out0, gI0,
+                                     c.st));
+    }
+    return META_OK;
+}
+
 // Workspace bytes of a batch split into S sub-batches, each in its own
 // 256-byte aligned region.
 size_t split_bytes(const meta_problem* pr, int S) {
@@ -538,12 +612,9 @@ size_t split_bytes(const meta_problem* pr, int S) {
 
 // One cost_and_grad call with an optional fault word other than the one in
 // its workspace (the sub-batches of a split plan all report to the first).
-// The calls that run the adjoint take only the semi-Lagrangian scheme.
-meta_status adjoint_scheme(const meta_problem* pr) {
-    const meta_status s = validate(pr);
-    if (s != META_OK) return s;
-    return pr->scheme == META_SCHEME_SL ? META_OK : META_ERR_UNSUPPORTED;
-}
+// Every scheme has its adjoint; the det momentum update belongs to the
+// semi-Lagrangian scheme (validate refuses the other combinations).
+meta_status adjoint_scheme(const meta_problem* pr) { return validate(pr); }
 
 meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const float* J,
                                const float* p0, const float* mu, const float* rho,
@@ -559,14 +630,15 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
     if (s != META_OK) return s;
     if (fault) c.fault = fault;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T, c.L.pdet};
+    const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     s = run_forward(c, cf);
     if (s != META_OK) return s;
     META_LAUNCH(META_K_COST, c.st,
                 launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.maxdisp,
-                            c.REC, c.IHP, c.PHP, c.partials, c.L.nblk, cost, c.st));
+                            c.REC, c.IHP, c.PHP, c.RAW, raw_p(c), c.partials, c.L.nblk, cost,
+                            c.st));
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
 }
@@ -767,7 +839,7 @@ meta_status meta_shoot_forward(const meta_problem* prob, const float* I0, const 
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     s = run_forward(c, cf);
@@ -789,7 +861,7 @@ meta_status meta_shoot_deform(const meta_problem* prob, const float* I0, const f
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Geom& g = c.L.g;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
     META_LAUNCH(META_K_PACK, c.st,
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     const float* wT = nullptr;
@@ -814,7 +886,7 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     Ctx c;
     s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
-    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet};
+    const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
     // With checkpoints, an earlier adjoint left another segment in the segment
     // slots: bring the last one back so that the adjoint can be called again.
     if (c.L.k) {
@@ -823,7 +895,7 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     }
     META_LAUNCH(META_K_ADJ_INIT, c.st,
                 launch_adj_init(c.L.g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, gI1, gp1,
-                                c.maxdisp, c.REC, c.IHP, c.PHP, c.st));
+                                c.maxdisp, c.REC, c.IHP, c.PHP, c.RAW, raw_p(c), c.st));
     return run_adjoint(c, cf, 2, gp0, gI0);
 }
 

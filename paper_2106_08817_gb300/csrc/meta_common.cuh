@@ -134,6 +134,7 @@ struct Coefs {
     const float* lambda;  // [B]
     float dt;             // 1/T
     int pdet;             // momentum update: 0 p~ (1 - dt div v), 1 p~ det(Id - dt Dv)
+    int scheme;           // 0 semi-Lagrangian, 1 Eulerian, 2 hybrid
 };
 
 // ------------------------------------------------- relative-coordinate foot

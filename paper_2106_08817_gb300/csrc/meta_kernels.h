@@ -40,9 +40,10 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st);
 // Eulerian (hybrid = false) or hybrid step t: state slot sl.st -> sl.st1
-// with u slot sl.ut (forward only).
-cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, const Slots& sl, bool hybrid,
-                         float* states, const float* u, cudaStream_t st);
+// with u slot sl.ut; the hybrid also records max |d| of step t in maxdisp.
+cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
+                         bool hybrid, float* states, const float* u, unsigned int* maxdisp,
+                         cudaStream_t st);
 // Deformation step t: w_{t+1} = (y - x) + S(y) w_t from u slot su, with
 // w = phi - Id in slices a*B + b of win / wout (win NULL: w_t = 0).
 cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const float* u,
@@ -60,12 +61,25 @@ cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* ph
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                         const float* states, const float* u, const float* J,
                         const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
-                        double* partials, int nblk, double* cost, cudaStream_t st);
+                        float* rawI, float* rawP, double* partials, int nblk, double* cost,
+                        cudaStream_t st);
 // Records of step T-1 from given gradients gI1, gp1 (gp1 nullable: zero).
 cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* states, const float* u, const float* gI1,
                             const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp,
-                            float* php, cudaStream_t st);
+                            float* php, float* rawI, float* rawP, cudaStream_t st);
+// Eulerian / hybrid schemes (c.scheme 1 / 2): the start above also writes the raw
+// adjoints of (I_T, p_T) into rawI / rawP (Eulerian) or rawP (hybrid, whose
+// records are those of its semi-Lagrangian image step).  One Eulerian adjoint
+// step up to v^ (Ihp, php, vh from rawI, rawP, state sl.st, u sl.ut), and the
+// hybrid's Eulerian momentum part added after the transport.
+cudaError_t launch_euler_adj(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                             const float* states, const float* u, const float* rawI,
+                             const float* rawP, float* Ihp, float* php, float* vh,
+                             cudaStream_t st);
+cudaError_t launch_hybrid_p(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
+                            const float* states, const float* u, const float* rawP, float* php,
+                            float* vh, cudaStream_t st);
 // Records of a step (state sl.st1, u sl.ut1) from pitched raw adjoints.
 cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                                const float* states, const float* u, const float* rawI,

@@ -300,37 +300,53 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
 // neighbours; no per-step window is recorded (there is no adjoint).
 template <int NDIM, bool HYBRID>
 __global__ void __launch_bounds__(kPX * kPY)
-k_euler(Geom g, Coefs cf, Slots sl, float* __restrict__ states, const float* __restrict__ u) {
+k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
+        const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
-    if (!v.ok) return;
-    const int b = v.b;
-    const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
-    const long long o = gidx(g, v.z, v.y, v.x);
-    int c[NDIM], n[NDIM];
-    long long s[NDIM];
-    axis_info<NDIM>(g, v, c, n, s);
-    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
-    float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
-    float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
-    float divpv = 0.f, adv = 0.f, d[NDIM];
+    float dmax = 0.f;  // hybrid: max |d| of the CTA (the window of its adjoint transport)
+    if (v.ok) {
+        const int b = v.b;
+        const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
+        const long long o = gidx(g, v.z, v.y, v.x);
+        int c[NDIM], n[NDIM];
+        long long s[NDIM];
+        axis_info<NDIM>(g, v, c, n, s);
+        const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+        const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+        float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
+        float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+        float divpv = 0.f, adv = 0.f, d[NDIM];
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) {
-        const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
-        const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
-        divpv += 0.5f * (pt[o + hi] * (-rho * ua[o + hi]) - pt[o - lo] * (-rho * ua[o - lo]));
-        if constexpr (HYBRID) d[a] = disp_of(dt * rho, ua[o]);
-        else adv += (0.5f * (It[o + hi] - It[o - lo])) * (-rho * ua[o]);
+        for (int a = 0; a < NDIM; ++a) {
+            const float* ua = slice_of(u, g, ((long long)sl.ut * NDIM + a) * g.B + b);
+            const long long hi = (c[a] < n[a] - 1) ? s[a] : 0, lo = (c[a] > 0) ? s[a] : 0;
+            divpv += 0.5f * (pt[o + hi] * (-rho * ua[o + hi]) - pt[o - lo] * (-rho * ua[o - lo]));
+            if constexpr (HYBRID) d[a] = disp_of(dt * rho, ua[o]);
+            else adv += (0.5f * (It[o + hi] - It[o - lo])) * (-rho * ua[o]);
+        }
+        p1[o] = pt[o] - dt * divpv;
+        if constexpr (HYBRID) {
+            const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
+            const float pw = interp<NDIM>(g, F, pt);
+            I1[o] = interp<NDIM>(g, F, It) + (dt * mu) * pw;
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
+        } else {
+            I1[o] = It[o] - dt * adv + (dt * mu) * pt[o];
+        }
     }
-    p1[o] = pt[o] - dt * divpv;
-    if constexpr (HYBRID) {
-        const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
-        const float pw = interp<NDIM>(g, F, pt);
-        I1[o] = interp<NDIM>(g, F, It) + (dt * mu) * pw;
-    } else {
-        I1[o] = It[o] - dt * adv + (dt * mu) * pt[o];
+    if constexpr (HYBRID) {  // one atomic per CTA, as in the advect
+        __shared__ unsigned int s_m;
+        const int tid = threadIdx.y * kPX + threadIdx.x;
+        if (tid == 0) s_m = 0u;
+        __syncthreads();
+        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+        if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+        __syncthreads();
+        if (tid == 0 && s_m != 0u)
+            atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + blockIdx.z), s_m);
     }
 }
 
@@ -474,15 +490,16 @@ cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* ph
     return cudaGetLastError();
 }
 
-cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, const Slots& sl, bool hybrid,
-                         float* states, const float* u, cudaStream_t st) {
+cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
+                         bool hybrid, float* states, const float* u, unsigned int* maxdisp,
+                         cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(hybrid ? k_euler<2, true> : k_euler<2, false>, pgrid<2>(g), blk,
-                                   0, st, g, c, sl, states, u));
+                                   0, st, g, c, t, sl, states, u, maxdisp));
     else
         META_CHECK_LAUNCH(launch_k(hybrid ? k_euler<3, true> : k_euler<3, false>, pgrid<3>(g), blk,
-                                   0, st, g, c, sl, states, u));
+                                   0, st, g, c, t, sl, states, u, maxdisp));
     return cudaGetLastError();
 }
 

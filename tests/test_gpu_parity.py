@@ -64,11 +64,11 @@ def check_forward(meta, I0, p0, T, sigma, mu, rho, p_update=0, scheme="sl"):
 
 
 def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL, ckpt=0,
-                    p_update=0):
+                    p_update=0, scheme="sl"):
     B = I0.shape[0]
-    ws = meta.Workspace(I0.shape[1:], B, T, sigma, "cuda", ckpt)
+    ws = meta.Workspace(I0.shape[1:], B, T, sigma, "cuda", ckpt, scheme)
     cost, grad = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
-                                    workspace=ws, ckpt=ckpt, p_update=p_update)
+                                    workspace=ws, ckpt=ckpt, p_update=p_update, scheme=scheme)
     check_cost_grad.status = ws.status()
     assert check_cost_grad.status & 1 == 0
     cost, grad = cost.cpu().numpy(), grad.cpu().numpy()
@@ -76,7 +76,7 @@ def check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, grad_rtol=GRAD_RTOL
     for b in range(I0.shape[0]):
         pick = lambda v: v[b] if np.ndim(v) else v
         c, g = oracle.cost_and_grad(I0[b], J[b], p0[b], T, sigma, pick(mu), pick(rho), pick(lam),
-                                    p_update=p_update)
+                                    p_update=p_update, scheme=scheme)
         np.testing.assert_allclose(cost[b], c, rtol=COST_RTOL, atol=1e-12)
         e = rel_l2(grad[b], g)
         worst = max(worst, e)
@@ -184,7 +184,7 @@ def test_other_schemes_forward(meta, dims, B, T, sigma, scale, scheme):
 
 
 @pytest.mark.parametrize("scheme", ["euler", "hybrid"])
-def test_other_schemes_zero_momentum_deformation_and_refusals(meta, scheme):
+def test_other_schemes_zero_momentum_and_deformation(meta, scheme):
     w = phantoms.disk_pair_64(random_p0=False)
     I1, p1, _ = meta.shoot_forward(cuda(w.I0), cuda(w.p0), w.T, w.sigma, w.mu, w.rho,
                                    scheme=scheme)
@@ -197,9 +197,42 @@ def test_other_schemes_zero_momentum_deformation_and_refusals(meta, scheme):
     wr, Jr = oracle.deformation(I0[0], p0[0], 4, 2.0, 0.1, 1.0, scheme=scheme)
     assert np.abs(phi.cpu().numpy()[0] - wr).max() <= FWD_ATOL * max(1.0, np.abs(wr).max())
     assert np.abs(jac.cpu().numpy()[0] - Jr).max() <= 1e-3
-    with pytest.raises(meta.MetaError):
-        meta.cost_and_grad(cuda(w.I0), cuda(w.J), cuda(w.p0), w.T, w.sigma, w.mu, w.rho, w.lam,
-                           scheme=scheme)
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+@pytest.mark.parametrize("dims,B,T,sigma,scale,k", [((37, 141), 2, 5, 2.3, 40.0, 0),
+                                                    ((37, 141), 2, 5, 2.3, 40.0, 2),
+                                                    ((5, 3), 2, 2, 0.7, 10.0, 0),
+                                                    ((9, 13, 135), 2, 3, 1.5, 30.0, 0),
+                                                    ((12, 10, 11), 1, 4, 1.0, 30.0, 3)])
+def test_other_schemes_cost_and_grad(meta, dims, B, T, sigma, scale, k, scheme):
+    """Cost and dL/dp0 of the Eulerian and hybrid schemes against the oracle's
+    transposes, keep-all and with step checkpointing (bit-identical to keep-all)."""
+    I0, J = phantoms.random_fields(37, B, dims)
+    p0 = smooth_p(38, (B,) + dims, scale, s=1.5)
+    mu, rho, lam = [0.05, 0.0][:B], [1.0, 1.3][:B], 1e-3
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, ckpt=k, scheme=scheme)
+    if k:
+        c0, g0 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                                    scheme=scheme)
+        ck, gk = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                                    ckpt=k, scheme=scheme)
+        torch.cuda.synchronize()
+        assert torch.equal(c0, ck) and torch.equal(g0, gk)
+
+
+@pytest.mark.parametrize("scheme", ["euler", "hybrid"])
+def test_other_schemes_shoot_adjoint(meta, scheme):
+    dims, T, sigma = (40, 52), 4, 2.0
+    I0, _ = phantoms.random_fields(39, 1, dims)
+    p0 = smooth_p(40, (1,) + dims, 40.0, s=1.5)
+    r = np.random.default_rng(41)
+    gI1, gp1 = r.normal(size=(1,) + dims), r.normal(size=(1,) + dims)
+    _, _, ws = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, 0.2, 1.0, scheme=scheme)
+    gI0, gp0 = meta.shoot_adjoint(cuda(gI1), cuda(gp1), ws, T, sigma, 0.2, 1.0, scheme=scheme)
+    eI, ep = oracle.adjoint(I0[0], p0[0], gI1[0], gp1[0], T, sigma, 0.2, 1.0, scheme=scheme)
+    assert rel_l2(gp0.cpu().numpy()[0], ep) <= GRAD_RTOL
+    assert rel_l2(gI0.cpu().numpy()[0], eI) <= GRAD_RTOL
 
 
 @pytest.mark.parametrize("scheme", ["euler", "hybrid"])
@@ -413,12 +446,12 @@ def test_deformation_with_the_det_update(meta):
         np.testing.assert_allclose(jac.cpu().numpy()[b], oracle.jacobian_det(ph), atol=JAC_ATOL)
 
 
-@pytest.mark.parametrize("p_update", ["div", "det"])
+@pytest.mark.parametrize("p_update,scheme", [("div", "sl"), ("det", "sl"), ("div", "hybrid")])
 @pytest.mark.parametrize("dims,seed,scale,T,sigma,mu,rho,lam", [
     ((70, 33), 21, 200.0, 5, 3.0, 0.2, 0.8, 1e-2),     # per-step |d|: .2 1.6 4.3 8.1 17
     ((14, 16, 18), 31, 300.0, 4, 1.5, 0.1, 1.0, 1e-3),  # per-step |d|: .3 1.8 4.8 17
 ])
-def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_update):
+def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_update, scheme):
     """Per-step displacements of 0.2 to 17 voxels: the gather window grows with
     them (R = 1 + floor(max|d|)) and, beyond 8 voxels in 2-D or 3 in 3-D, the
     adjoint switches to the atomic scatter.  These inputs stay well conditioned
@@ -426,10 +459,11 @@ def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_
     I0, _ = phantoms.random_fields(seed, 1, dims)
     J, _ = phantoms.random_fields(seed + 1, 1, dims)
     p0 = smooth_p(seed + 2, (1,) + dims, scale)
-    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True, p_update=p_update)
+    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True, p_update=p_update,
+                           scheme=scheme)
     per_step = [np.abs(u[k]).max() * rho / T for k in range(T)]
     assert max(per_step) > 9 and min(per_step) < 1
-    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update)
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
     assert check_cost_grad.status & 2  # the scatter fallback ran
 
 
