@@ -397,10 +397,11 @@ def measure_det_update(meta, w, I0, J, p0, mu, rho, lam, ws, ckpt, flush, stream
                         "GBps_algorithmic": gbps, "frac_of_measured_hbm": gbps / peak}}
 
 
-def measure_schemes(meta, w, I0, p0, mu, rho, flush, stream, reps=10):
-    """The three integration schemes of Sec. 2.3: forward shooting time on the workload
-    (eager calls, L2 flushed before each) with the Eulerian step kernel's algorithmic
-    bandwidth, and the stability comparison of Fig. 1 on the 'C' phantom: a momentum
+def measure_schemes(meta, w, I0, J, p0, mu, rho, lam, flush, stream, reps=10):
+    """The three integration schemes of Sec. 2.3: forward shooting and cost_and_grad time
+    on the workload (eager calls, L2 flushed before each) with the Eulerian step
+    kernel's algorithmic bandwidth, and the stability comparison of Fig. 1 on the 'C'
+    phantom: a momentum
     from 40 normalised LDDMM gradient steps (the library's cost_and_grad), shot by each
     scheme with 20 and 38 steps; how far I_T leaves the range of I_0 and its total
     variation (ripples)."""
@@ -422,10 +423,12 @@ def measure_schemes(meta, w, I0, p0, mu, rho, flush, stream, reps=10):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / reps
 
-    out = {"ms_shoot_forward": {}}
+    out = {"ms_shoot_forward": {}, "ms_cost_and_grad": {}}
     for sc in ("sl", "euler", "hybrid"):
         out["ms_shoot_forward"][sc] = timed(
             lambda: meta.shoot_forward(I0, p0, T, w.sigma, mu, rho, scheme=sc))
+        out["ms_cost_and_grad"][sc] = timed(
+            lambda: meta.cost_and_grad(I0, J, p0, T, w.sigma, mu, rho, lam, scheme=sc))
     meta.timer_start(1 << 14)
     for _ in range(reps):
         flush.zero_()
@@ -599,7 +602,7 @@ def run_ours(args):
     # ---- the Eulerian and hybrid schemes, and their stability on the 'C' phantom
     schemes = None
     if not args.no_schemes:
-        schemes = measure_schemes(meta, w, I0, p0, mu, rho, flush, stream)
+        schemes = measure_schemes(meta, w, I0, J, p0, mu, rho, lam, flush, stream)
 
     # ---- L-BFGS against the gradient descent of the timed loop
     lbfgs = None
