@@ -623,28 +623,29 @@ class Shoot(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, I0, p0, T, sigma, mu, rho, p_update=0):
+    def forward(ctx, I0, p0, T, sigma, mu, rho, p_update=0, scheme="sl"):
         I0c, p0c = I0.detach().contiguous(), p0.detach().contiguous()
         b_, nd, dims, sq = _shape(I0c, None)
-        ws = Workspace(dims, b_.shape[0], T, sigma, I0c.device)
-        I1, p1, _ = shoot_forward(I0c, p0c, T, sigma, mu, rho, workspace=ws, p_update=p_update)
-        ctx.ws, ctx.args, ctx.shape = ws, (T, sigma, mu, rho, p_update), I0c.shape
+        ws = Workspace(dims, b_.shape[0], T, sigma, I0c.device, 0, scheme)
+        I1, p1, _ = shoot_forward(I0c, p0c, T, sigma, mu, rho, workspace=ws, p_update=p_update,
+                                  scheme=scheme)
+        ctx.ws, ctx.args, ctx.shape = ws, (T, sigma, mu, rho, p_update, scheme), I0c.shape
         return I1, p1
 
     @staticmethod
     def backward(ctx, gI1, gp1):
-        T, sigma, mu, rho, p_update = ctx.args
+        T, sigma, mu, rho, p_update, scheme = ctx.args
         if gI1 is None:
             gI1 = torch.zeros(ctx.shape, device=ctx.ws.buf.device)
         gI0, gp0 = shoot_adjoint(gI1.contiguous(), None if gp1 is None else gp1.contiguous(),
                                  ctx.ws, T, sigma, mu, rho, want_gI0=ctx.needs_input_grad[0],
-                                 p_update=p_update)
-        return gI0, gp0, None, None, None, None, None
+                                 p_update=p_update, scheme=scheme)
+        return gI0, gp0, None, None, None, None, None, None
 
 
-def shoot(I0, p0, T: int, sigma: float, mu, rho=1.0, p_update=0):
+def shoot(I0, p0, T: int, sigma: float, mu, rho=1.0, p_update=0, scheme: str = "sl"):
     """Differentiable shooting: torch autograd calls the library's adjoint."""
-    return Shoot.apply(I0, p0, T, sigma, mu, rho, p_update)
+    return Shoot.apply(I0, p0, T, sigma, mu, rho, p_update, scheme)
 
 
 def timer_start(cap: int = 1 << 16) -> None:
