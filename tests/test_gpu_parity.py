@@ -233,6 +233,11 @@ def test_other_schemes_shoot_adjoint(meta, scheme):
     eI, ep = oracle.adjoint(I0[0], p0[0], gI1[0], gp1[0], T, sigma, 0.2, 1.0, scheme=scheme)
     assert rel_l2(gp0.cpu().numpy()[0], ep) <= GRAD_RTOL
     assert rel_l2(gI0.cpu().numpy()[0], eI) <= GRAD_RTOL
+    # the autograd Function runs the same calls
+    Ia, pa = cuda(I0).requires_grad_(True), cuda(p0).requires_grad_(True)
+    I1, p1 = meta.shoot(Ia, pa, T, sigma, 0.2, 1.0, scheme=scheme)
+    ((I1 * cuda(gI1)).sum() + (p1 * cuda(gp1)).sum()).backward()
+    assert torch.equal(pa.grad, gp0) and torch.equal(Ia.grad, gI0)
 
 
 @pytest.mark.parametrize("scheme", ["euler", "hybrid"])
