@@ -211,13 +211,12 @@ __device__ __forceinline__ float gw(float g) {
 // ------------------------------------------------------------------ kernels
 
 // Cost partials: one CTA = 8 warps over a fixed set of (z, y) rows of
-// instance blockIdx.y; also starts the adjoint: I^_T = I_T - J, p^_T = 0 -> record T-1.
+// instance blockIdx.y.  (The adjoint start from I^_T = I_T - J, p^_T = 0 is
+// k_adj_init<NDIM, true>, a pointwise kernel of its own.)
 template <int NDIM>
 __global__ void __launch_bounds__(256)
-k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
-                const float* __restrict__ u, const float* __restrict__ J,
-                const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php,
-                float* rawI, float* rawP, double* partials) {
+k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float* __restrict__ u,
+                const float* __restrict__ J, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     const int b = blockIdx.y;
@@ -225,8 +224,6 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     const float* IT = slice_of(states, g, ((long long)sl.sT * 2 + 0) * g.B + b);
     const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
     const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
-    // the transport of step T-1 scatters into Ihp / php only beyond the gather window
-    const bool zero_sums = gather_radius(maxdisp, g.nT - 1, g.B, b) > GatherTile<NDIM>::RMAX;
     double data = 0.0, kin = 0.0, res = 0.0;
     // one warp per (z, y) row at a time; a fixed assignment, so fixed sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,11 +250,6 @@ k_cost_partials(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
             kin += (double)(p * ga) * (double)ua[o];
         }
         res += (double)p * (double)p;
-        adjoint_start<NDIM>(g, cf, sl.st1, sl.ut1, v, o, r, 0.f, states, u, rec, rawI, rawP);
-        if (zero_sums) {  // scatter accumulators start at zero
-            slice_of(Ihp, g, b)[o] = 0.f;
-            slice_of(php, g, b)[o] = 0.f;
-        }
     }
     __shared__ double red[3][256];
     red[0][threadIdx.x] = data;
@@ -297,8 +289,10 @@ k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* co
     }
 }
 
-// Adjoint start from given gradients w.r.t. (I_T, p_T): record of step T-1.
-template <int NDIM>
+// Adjoint start from given gradients w.r.t. (I_T, p_T): record of step T-1
+// (and the raw adjoints of the Eulerian steps).  FROM_J: the cost's start,
+// I^_T = I_T - J with J (contiguous) in gI1, p^_T = 0.
+template <int NDIM, bool FROM_J>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
            const float* __restrict__ u, const float* __restrict__ gI1,
@@ -310,8 +304,14 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
-    adjoint_start<NDIM>(g, cf, sl.st1, sl.ut1, v, o, gI1[ci], gp1 ? gp1[ci] : 0.f, states, u,
-                        rec, rawI, rawP);
+    float Ih1, ph1 = 0.f;
+    if constexpr (FROM_J) {
+        Ih1 = slice_of(states, g, ((long long)sl.sT * 2 + 0) * g.B + v.b)[o] - gI1[ci];
+    } else {
+        Ih1 = gI1[ci];
+        ph1 = gp1 ? gp1[ci] : 0.f;
+    }
+    adjoint_start<NDIM>(g, cf, sl.st1, sl.ut1, v, o, Ih1, ph1, states, u, rec, rawI, rawP);
     if (gather_radius(maxdisp, g.nT - 1, g.B, v.b) > GatherTile<NDIM>::RMAX) {
         slice_of(Ihp, g, v.b)[o] = 0.f;  // the first transport scatters into these
         slice_of(php, g, v.b)[o] = 0.f;
@@ -1147,12 +1147,20 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl
                         float* rawI, float* rawP, double* partials, int nblk, double* cost,
                         cudaStream_t st) {
     const dim3 grid(nblk, g.B);
-    if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   maxdisp, rec, Ihp, php, rawI, rawP, partials));
-    else
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, c, sl, states, u, J,
-                                   maxdisp, rec, Ihp, php, rawI, rawP, partials));
+    const dim3 blk(kPX, kPY);
+    if (ndim == 2) {
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, sl, states, u, J,
+                                   partials));
+        META_CHECK_LAUNCH(launch_k(k_adj_init<2, true>, pgrid<2>(g), blk, 0, st, g, c, sl, states,
+                                   u, J, (const float*)nullptr, maxdisp, rec, Ihp, php, rawI,
+                                   rawP));
+    } else {
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, sl, states, u, J,
+                                   partials));
+        META_CHECK_LAUNCH(launch_k(k_adj_init<3, true>, pgrid<3>(g), blk, 0, st, g, c, sl, states,
+                                   u, J, (const float*)nullptr, maxdisp, rec, Ihp, php, rawI,
+                                   rawP));
+    }
     META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
     return cudaSuccess;
 }
@@ -1163,11 +1171,11 @@ cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots
                             float* php, float* rawI, float* rawP, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
-        META_CHECK_LAUNCH(launch_k(k_adj_init<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
+        META_CHECK_LAUNCH(launch_k(k_adj_init<2, false>, pgrid<2>(g), blk, 0, st, g, c, sl, states,
+                                   u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
     else
-        META_CHECK_LAUNCH(launch_k(k_adj_init<3>, pgrid<3>(g), blk, 0, st, g, c, sl, states, u,
-                                   gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
+        META_CHECK_LAUNCH(launch_k(k_adj_init<3, false>, pgrid<3>(g), blk, 0, st, g, c, sl, states,
+                                   u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP));
     return cudaSuccess;
 }
 
