@@ -400,19 +400,21 @@ def set_tuning(dims: Sequence[int], batch: int, sigma: float, tun: Optional[dict
 
 
 def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu,
-             rho=1.0, lam=1e-3, ndim: Optional[int] = None, ckpt: int = 0, p_update=0) -> dict:
+             rho=1.0, lam=1e-3, ndim: Optional[int] = None, ckpt: int = 0, p_update=0,
+             scheme: str = "sl") -> dict:
     """Times cost_and_grad on these inputs for candidate tile shapes (meta_autotune),
     records the fastest for the problem shape and returns it.  Blocking."""
     I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
     Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, None, ckpt)
+    ws = _workspace(dims, B, T, sigma, dev, None, ckpt, scheme)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
     grad = torch.empty_like(I0b)
     t = _Tuning()
-    rc = _load().meta_autotune(ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update)),
+    rc = _load().meta_autotune(ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update,
+                                                     scheme)),
                                _p(I0b),
                                _p(Jb), _p(p0b), _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
                                _p(grad), ctypes.c_void_p(ws.ptr()), ws.nbytes, _stream(dev),
@@ -454,20 +456,21 @@ def lbfgs_direction(g: torch.Tensor, S: Sequence[torch.Tensor], Y: Sequence[torc
 
 def lbfgs_minimize(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
                    mu, rho=1.0, lam=1e-3, iters: int = 10, m: int = 5, h0: float = 0.05,
-                   ndim: Optional[int] = None, ckpt: int = 0, p_update=0):
+                   ndim: Optional[int] = None, ckpt: int = 0, p_update=0, scheme: str = "sl"):
     """L-BFGS on the Eq. 4 cost from p0 (meta_lbfgs_minimize).  Returns (p, costs
     [iters + 1, B] float64 numpy, last moving iteration per instance)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
     p = _as_batch(p0, "p0")[0].reshape(I0b.shape).clone()
     B, dev = I0b.shape[0], I0b.device
-    ws = _workspace(dims, B, T, sigma, dev, None, ckpt)
+    ws = _workspace(dims, B, T, sigma, dev, None, ckpt, scheme)
     lws = torch.empty(lbfgs_workspace_size(dims, B, m), dtype=torch.uint8, device=dev)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     hist = np.zeros((iters + 1, B), dtype=np.float64)
     done = np.zeros(B, dtype=np.int32)
     rc = _load().meta_lbfgs_minimize(
-        ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update)), _p(I0b), _p(Jb), _p(p),
+        ctypes.byref(_problem(nd, dims, B, T, sigma, ws.ckpt, p_update, scheme)), _p(I0b), _p(Jb),
+        _p(p),
         _p(mu_t), _p(rho_t), _p(lam_t), int(iters), int(m), float(h0), ctypes.c_void_p(ws.ptr()),
         ws.nbytes, ctypes.c_void_p(lws.data_ptr()), lws.numel(),
         hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
@@ -527,7 +530,7 @@ class GroupPlan:
     mixed) recorded into one CUDA graph as parallel branches (meta_plan_create_group).
 
     `problems` is a list of dicts with keys I0, J, p0 ([B, *dims] CUDA tensors),
-    T, sigma, mu, rho, lam (optional: ckpt, p_update).  Each item keeps its own copies of the inputs
+    T, sigma, mu, rho, lam (optional: ckpt, p_update, scheme).  Each item keeps its own copies of the inputs
     (``plan.items[k]["p0"]`` etc.), cost [B, 3] and grad; ``launch()`` runs all.
     """
 
@@ -550,9 +553,10 @@ class GroupPlan:
                   "grad": torch.empty_like(I0b), "T": int(pb["T"]), "sigma": float(pb["sigma"]),
                   "dims": dims, "B": B}
             it["ckpt"] = int(pb.get("ckpt", 0))
-            it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev, it["ckpt"])
+            it["scheme"] = pb.get("scheme", "sl")
+            it["ws"] = Workspace(dims, B, it["T"], it["sigma"], dev, it["ckpt"], it["scheme"])
             probs[k] = _problem(nd, dims, B, it["T"], it["sigma"], it["ckpt"],
-                                pb.get("p_update", 0))
+                                pb.get("p_update", 0), it["scheme"])
             for arr, key in ((I0s, "I0"), (Js, "J"), (p0s, "p0"), (mus, "mu"), (rhos, "rho"),
                              (lams, "lam"), (costs, "cost"), (grads, "grad")):
                 arr[k] = it[key].data_ptr()
@@ -589,7 +593,7 @@ NOALLOC_MAX_BYTES = 64 << 20
 def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int,
                           sigma: float, mu, rho=1.0, lam=1e-3, ndim: Optional[int] = None,
                           out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0,
-                          p_update=0) -> Tuple[torch.Tensor, torch.Tensor]:
+                          p_update=0, scheme: str = "sl") -> Tuple[torch.Tensor, torch.Tensor]:
     """cost_and_grad on the library's fixed 64 MiB device scratch: no workspace
     argument.  For callers that cannot allocate device memory; pass `out` (and
     device tensors for mu, rho, lam) so that this call allocates nothing either.
@@ -604,7 +608,7 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b)
-    pr = _problem(nd, dims, B, T, sigma, ckpt, p_update)
+    pr = _problem(nd, dims, B, T, sigma, ckpt, p_update, scheme)
     rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
                                             _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
                                             _p(grad), _stream(dev))
