@@ -264,7 +264,7 @@ def lbfgs_direction(g, S, Y, gamma=None) -> np.ndarray:
 
 
 def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
-                   iters: int, m: int, h0: float, p_update=0):
+                   iters: int, m: int, h0: float, p_update=0, scheme: str = "sl"):
     """L-BFGS on the cost of Eq. 4 for one instance, the rules of the GPU driver:
     direction -H g over the last m pairs (pairs that fail s.y > 1e-12 y.y stay in the
     window but are skipped); without a usable pair in the window, or when -H g does
@@ -274,7 +274,7 @@ def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: 
     stops.  Returns (x, costs [iters + 1], margins): margins[k] lists, for every trial
     of iteration k, (L + 1e-4 a g.d - L_trial) / |L| (positive: accepted)."""
     x = _f64(p0).copy()
-    c, g = cost_and_grad(I0, J, x, T, sigma, mu, rho, lam, p_update=p_update)
+    c, g = cost_and_grad(I0, J, x, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
     L = c.sum()
     window = []  # (s, y, usable), oldest first, at most m
     hist, margins, stopped = [L], [], False
@@ -292,7 +292,8 @@ def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: 
         step, acc = 1.0, None
         for _t in range(13):
             xt = x + step * d
-            ct, gt = cost_and_grad(I0, J, xt, T, sigma, mu, rho, lam, p_update=p_update)
+            ct, gt = cost_and_grad(I0, J, xt, T, sigma, mu, rho, lam, p_update=p_update,
+                                   scheme=scheme)
             margins[-1].append((L + 1e-4 * step * gd - ct.sum()) / max(abs(L), 1e-300))
             if ct.sum() <= L + 1e-4 * step * gd:
                 acc = (xt, gt, ct.sum())

@@ -534,6 +534,46 @@ def test_group_plan_runs_mixed_shapes_in_one_graph(meta):
     assert rel_l2(it["grad"][0].cpu().numpy(), g_ref) <= GRAD_RTOL
 
 
+def test_variants_through_plans_and_lbfgs(meta):
+    """The momentum update and the scheme reach every entry point: a group plan whose
+    members use the det update, the Eulerian and the hybrid scheme gives what their
+    separate calls give, bit for bit; a recorded plan of a hybrid call likewise; and
+    two L-BFGS iterations with the Eulerian scheme follow the oracle's driver."""
+    specs = [((40, 44), 2, 4, 2.0, "div", "sl"), ((36, 30), 1, 3, 1.5, "det", "sl"),
+             ((10, 12, 11), 1, 3, 1.2, "div", "euler"), ((30, 34), 2, 4, 2.0, "div", "hybrid")]
+    problems = []
+    for k, (dims, B, T, sigma, pu, sch) in enumerate(specs):
+        I0, J = phantoms.random_fields(160 + k, B, dims)
+        p0 = smooth_p(170 + k, (B,) + dims, 25.0, s=1.5)
+        problems.append(dict(I0=cuda(I0), J=cuda(J), p0=cuda(p0), T=T, sigma=sigma, mu=0.05,
+                             rho=1.0, lam=1e-2, p_update=pu, scheme=sch))
+    plan = meta.GroupPlan(problems, streams=2)
+    plan.launch()
+    torch.cuda.synchronize()
+    for pb, it in zip(problems, plan.items):
+        c, g = meta.cost_and_grad(pb["I0"], pb["J"], pb["p0"], pb["T"], pb["sigma"], pb["mu"],
+                                  pb["rho"], pb["lam"], p_update=pb["p_update"],
+                                  scheme=pb["scheme"])
+        torch.cuda.synchronize()
+        assert torch.equal(c, it["cost"]) and torch.equal(g, it["grad"])
+    pb = problems[3]
+    single = meta.CostAndGradPlan(pb["I0"], pb["J"], pb["p0"], pb["T"], pb["sigma"], pb["mu"],
+                                  pb["rho"], pb["lam"], scheme="hybrid")
+    single.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(single.cost, plan.items[3]["cost"])
+    assert torch.equal(single.grad, plan.items[3]["grad"])
+    # L-BFGS with the Eulerian scheme on one 2-D pair
+    I0, J = phantoms.random_fields(180, 1, (32, 36))
+    p, hist, done = meta.lbfgs_minimize(cuda(I0), cuda(J), cuda(np.zeros_like(I0)), 4, 2.0, 0.05,
+                                        1.0, 1e-3, iters=2, m=3, h0=0.5, scheme="euler")
+    x, h_ref, margins = oracle.lbfgs_minimize(I0[0], J[0], np.zeros((32, 36)), 4, 2.0, 0.05, 1.0,
+                                              1e-3, 2, 3, 0.5, scheme="euler")
+    assert min(abs(v) for it in margins for v in it) > 1e-4
+    np.testing.assert_allclose(hist[:, 0], h_ref, rtol=1e-4)
+    assert rel_l2(p.cpu().numpy()[0], x) <= 1e-3
+
+
 @pytest.mark.parametrize("dims,B,T,sigma,k", [((37, 141), 2, 7, 2.3, 2), ((37, 141), 2, 7, 2.3, 3),
                                               ((64, 64), 1, 10, 3.0, 5), ((12, 10, 11), 2, 6, 1.5, 4),
                                               ((70, 33), 1, 5, 3.0, 2)])
