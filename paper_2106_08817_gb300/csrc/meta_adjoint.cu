@@ -7,8 +7,9 @@
 // p^' = p^_{t+1}:
 //
 //   record of step t at every source x (built by the kernel that produced
-//   I^', p^' at x -- the cost kernel, the adjoint start, or k_adj_gradp of
-//   step t+1):  the cell and f of the foot of x,  I^'(x),
+//   I^', p^' at x -- the adjoint start k_adj_init from I_T - J or from given
+//   gradients, or k_adj_gradp of step t+1):  the cell and f of the foot of x,
+//   I^'(x),
 //       p~^(x) = p^'(x) (1 - dt div v_t(x)) + dt mu I^'(x),
 //       div^(x) = -dt p~_t(x) p^'(x)
 //   k_adj_transport2d / 3d  Ihp = S^T I^', php = S^T p~^ (gather over the

@@ -456,8 +456,8 @@ Slots start_slots(const Layout& L) {
     return sl;
 }
 
-// Reverse sweep; REC holds the records of step T-1 on entry (from the cost
-// kernel or the adjoint start).  mode 1: cost gradient into out0; mode 2:
+// Reverse sweep; REC holds the records of step T-1 on entry (from the adjoint
+// start of the cost or of meta_shoot_adjoint).  mode 1: cost gradient into out0; mode 2:
 // shooting adjoint into out0 / gI0.  With step checkpointing, each segment
 // but the last (still in place after the forward) is recomputed before its
 // steps; the adjoint of the segment's first step writes raw I^, p^ whose

@@ -56,8 +56,9 @@ cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* ph
 // slice (k * B + b), k = 0 foot cell (int bits), 1..NDIM f per axis, NDIM+1
 // I^', NDIM+2 p~^, NDIM+3 div^.  Ihp / php: the S^T accumulators.
 // Eq. 4 partial sums (states sl.sT, sl.s0, u sl.u0), their reduction into
-// cost[B][3], and the records of step T-1 (state sl.st1, u sl.ut1) from
-// I^_T = I_T - J, p^_T = 0.
+// cost[B][3], and the adjoint start from I^_T = I_T - J, p^_T = 0 (k_adj_init:
+// the records of step T-1, state sl.st1, u sl.ut1, and for the Eulerian and
+// hybrid schemes the raw adjoints in rawI / rawP).
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                         const float* states, const float* u, const float* J,
                         const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
