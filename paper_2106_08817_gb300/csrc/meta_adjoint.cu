@@ -25,6 +25,12 @@
 // holds p~^ = p^' J + dt mu I^' and the same div^, and k_adj_jacT adds the
 // part of D^T (div^ cof(Id - dt Dv)) beyond D^T div^ to v^ before the blur.
 //
+// The Eulerian scheme passes raw adjoints (I^', p^') between steps: k_euler_adj
+// transposes its step up to v^, and k_adj_gradp (raw mode) finishes it.  The
+// hybrid scheme's image step is semi-Lagrangian: its records (p~^ = dt mu I^',
+// div^ = 0) go through the same transport, and k_hybrid_p adds the transpose of
+// its Eulerian momentum step.
+//
 // Each record is built once per voxel, so the transport only gathers.
 #include "meta_stencil.cuh"
 
