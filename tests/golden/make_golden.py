@@ -36,6 +36,21 @@ def compute():
             "I_T_sum": float(It[-1].sum()),
             "p_T_l2": float(np.sqrt((pt[-1] ** 2).sum())),
         }
+    # the variants at the random momentum: det momentum update, Eulerian and hybrid
+    # schemes, and the deformation of the grid
+    w = phantoms.disk_pair_64(random_p0=True)
+    args = (w.I0[0], w.J[0], w.p0[0], w.T, w.sigma, float(w.mu[0]), float(w.rho[0]),
+            float(w.lam[0]))
+    for tag, kw in (("det", dict(p_update="det")), ("euler", dict(scheme="euler")),
+                    ("hybrid", dict(scheme="hybrid"))):
+        c, g = oracle.cost_and_grad(*args, **kw)
+        out["p0_random_" + tag] = {"cost": [float(x) for x in c],
+                                   "grad_l2": float(np.sqrt((g ** 2).sum())),
+                                   "grad_at": {"32,32": float(g[32, 32]), "10,50": float(g[10, 50])}}
+    wdef, jac = oracle.deformation(w.I0[0], w.p0[0], w.T, w.sigma, float(w.mu[0]), float(w.rho[0]))
+    out["p0_random_deformation"] = {"phi_l2": float(np.sqrt((wdef ** 2).sum())),
+                                    "jac_min": float(jac.min()), "jac_max": float(jac.max()),
+                                    "jac_sum": float(jac.sum())}
     return out
 
 
