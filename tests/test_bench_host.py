@@ -56,3 +56,22 @@ def test_committed_traffic_is_scaled_by_voxels_and_keyed_by_dimension():
     assert full == pytest.approx(k2["dram_bytes_per_launch"])
     assert bench.ncu_traffic("adj_gather", 2, k2["voxels_per_launch"] // 2) == pytest.approx(full / 2)
     assert bench.ncu_traffic("no_such_class", 2, 1000) is None
+
+
+def test_reference_arm_prints_one_complete_line():
+    """bench.py --impl reference: the FP64 oracle on the host cores prints one JSON line with
+    the same metric and workload as the GPU arm, its own cpu_baseline and e2e."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "disk64", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"]
+    assert d["config"]["workload"] == "disk64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
