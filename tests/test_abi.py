@@ -88,6 +88,102 @@ def test_schemes_and_their_workspace(meta):
         meta._problem(2, (16, 16), 1, 4, 2.0, scheme="lagrangian")
 
 
+def test_workspace_size_grows_with_T_and_batch(meta):
+    a = meta.workspace_size((64, 64), 1, 10, 3.0)
+    b = meta.workspace_size((64, 64), 2, 10, 3.0)
+    c = meta.workspace_size((64, 64), 1, 20, 3.0)
+    assert b > a and c > a
+    # the trajectory (2 (T+1) + d T fields) dominates: check the order of magnitude
+    fields = 2 * 11 + 2 * 10 + 4 * 2 + 6
+    assert fields * 64 * 64 * 4 <= a < (fields + 8) * 64 * 64 * 4
+
+
+def test_checkpointing_shrinks_the_workspace(meta):
+    """ckpt_stride k keeps ceil(T/k) checkpoints plus one segment instead of T+1 states."""
+    full = meta.workspace_size((64, 64, 64), 1, 20, 5.0)
+    k5 = meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=5)
+    f = 64 * 64 * 64 * 4
+    assert full >= (2 * 21 + 3 * 20) * f
+    assert k5 <= (2 * (4 + 5) + 3 * 6 + 4 * 3 + 8 + 1) * f
+    assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=1) == full
+    assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=20) == full
+    pr = meta._problem(3, (8, 8, 8), 1, 4, 1.0, -1)
+    n = ctypes.c_size_t(0)
+    assert meta._load().meta_workspace_size(ctypes.byref(pr), ctypes.byref(n)) == 1
+
+
+def test_tuning_table_round_trip_and_validation(meta):
+    """Tile shapes per problem shape: built-in equal tiles, set / get / forget,
+    and range checks before anything runs."""
+    dims, B, s = (160, 192, 160), 1, 6.0
+    meta.set_tuning(dims, B, s, None)
+    t0 = meta.tuning(dims, B, s)
+    assert (t0["ly"], t0["lz"], t0["txw"]) == (96, 80, 80)  # 192 = 2 x 96, 160 = 2 x 80
+    assert 1 <= t0["zc_transport"] <= 160 and 1 <= t0["zc_advect"] <= 160 and t0["split"] == 1
+    mine = dict(zc_transport=8, zc_advect=16, ly=64, lz=48, txw=64, split=1)
+    meta.set_tuning(dims, B, s, mine)
+    assert meta.tuning(dims, B, s) == mine
+    meta.set_tuning(dims, B, s, dict(ly=32))  # zero fields: built-in choice
+    assert meta.tuning(dims, B, s)["ly"] == 32 and meta.tuning(dims, B, s)["lz"] == 80
+    for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
+                dict(lz=-16), dict(zc_advect=-1), dict(split=2)):  # split <= batch (1 here)
+        with pytest.raises(meta.MetaError):
+            meta.set_tuning(dims, B, s, bad)
+    with pytest.raises(meta.MetaError):
+        meta.set_tuning((64, 64), 1, 2.0, dict(lz=16))  # 2-D problems have no z tiles
+    with pytest.raises(meta.MetaError):  # y tiles x nz beyond the launch grid limit
+        meta.set_tuning((4000, 2000, 64), 1, 2.0, dict(ly=16))
+    meta.set_tuning(dims, B, s, None)
+    assert meta.tuning(dims, B, s) == t0
+    t2 = meta.tuning((256, 256), 16, 6.0)
+    assert (t2["ly"], t2["txw"], t2["lz"], t2["zc_transport"], t2["split"]) == (128, 128, 0, 0, 1)
+    meta.set_tuning((256, 256), 16, 6.0, dict(split=4))
+    assert meta.tuning((256, 256), 16, 6.0)["split"] == 4
+    with pytest.raises(meta.MetaError):
+        meta.set_tuning((256, 256), 16, 6.0, dict(split=17))
+    meta.set_tuning((256, 256), 16, 6.0, None)
+
+
+def test_workspace_covers_every_batch_split(meta):
+    """A split plan runs sub-batch k in its own aligned region of the caller's
+    workspace: meta_workspace_size covers the sum for every split."""
+    one = meta.workspace_size((37, 141), 1, 5, 2.3)
+    for B in (2, 5, 16):  # split into B regions of one instance each
+        n = meta.workspace_size((37, 141), B, 5, 2.3)
+        assert B * one <= n <= B * one + 64 * 1024
+    n = meta.workspace_size((37, 141), 40, 5, 2.3)  # at most 16 regions
+    assert abs(n - 40 * one) <= 64 * 1024
+
+
+def test_null_pointers_and_bad_workspace_fail_before_any_cuda_call(meta):
+    lib = meta._load()
+    pr = meta._problem(2, (16, 16), 1, 4, 2.0)
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    need = meta.workspace_size((16, 16), 1, 4, 2.0)
+    # null inputs
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), null, fake, fake, fake, fake, fake, fake,
+                                  fake, fake, need, null) == 1
+    assert lib.meta_shoot_forward(ctypes.byref(pr), fake, null, fake, fake, fake, fake, fake,
+                                  need, null) == 1
+    assert lib.meta_shoot_adjoint(ctypes.byref(pr), fake, fake, fake, fake, fake, null, fake,
+                                  need, null) == 1
+    # deformation: neither phi nor jac asked for, a null input, a short workspace
+    assert lib.meta_shoot_deform(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, null,
+                                 null, fake, need, null) == 1
+    assert lib.meta_shoot_deform(ctypes.byref(pr), null, fake, fake, fake, null, null, fake,
+                                 null, fake, need, null) == 1
+    assert lib.meta_shoot_deform(ctypes.byref(pr), fake, fake, fake, fake, null, null, null,
+                                 fake, fake, need - 1, null) == 3
+    # workspace: null, misaligned, too small
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, null, need, null) == 3
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, ctypes.c_void_p(0x1010), need, null) == 3
+    assert lib.meta_cost_and_grad(ctypes.byref(pr), fake, fake, fake, fake, fake, fake, fake,
+                                  fake, fake, need - 1, null) == 3
+
+
 def test_lbfgs_arguments_fail_before_any_cuda_call(meta):
     lib = meta._load()
     pr = meta._problem(2, (16, 16), 2, 4, 2.0)
