@@ -263,19 +263,18 @@ def lbfgs_direction(g, S, Y, gamma=None) -> np.ndarray:
     return -r
 
 
-def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
-                   iters: int, m: int, h0: float, p_update=0, scheme: str = "sl"):
-    """L-BFGS on the cost of Eq. 4 for one instance, the rules of the GPU driver:
+def lbfgs_run(f, x0, iters: int, m: int, h0: float):
+    """L-BFGS with the rules of the GPU driver, on any objective f(x) -> (L, dL/dx):
     direction -H g over the last m pairs (pairs that fail s.y > 1e-12 y.y stay in the
     window but are skipped); without a usable pair in the window, or when -H g does
-    not descend, d = -h0 g / max|g| and the pairs are forgotten; a backtracking
-    line search from step 1, halving up to 12 times, takes the first step a with
-    L(x + a d) <= L(x) + 1e-4 a g.d; if none passes, the iterate stays and the run
-    stops.  Returns (x, costs [iters + 1], margins): margins[k] lists, for every trial
-    of iteration k, (L + 1e-4 a g.d - L_trial) / |L| (positive: accepted)."""
-    x = _f64(p0).copy()
-    c, g = cost_and_grad(I0, J, x, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
-    L = c.sum()
+    not descend, d = -h0 g / max|g| and the pairs are forgotten (d = 0 at a zero
+    gradient, where the run stops); a backtracking line search from step 1, halving
+    up to 12 times, takes the first step a with L(x + a d) <= L(x) + 1e-4 a g.d; if
+    none passes, the iterate stays and the run stops.  Returns (x, costs [iters + 1],
+    margins): margins[k] lists, for every trial of iteration k,
+    (L + 1e-4 a g.d - L_trial) / |L| (positive: accepted)."""
+    x = _f64(x0).copy()
+    L, g = f(x)
     window = []  # (s, y, usable), oldest first, at most m
     hist, margins, stopped = [L], [], False
     for _ in range(iters):
@@ -286,17 +285,21 @@ def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: 
         usable = [(s, y) for s, y, ok in window if ok]
         d = lbfgs_direction(g, [s for s, _ in usable], [y for _, y in usable]) if usable else None
         if d is None or not ((g * d).sum() < 0):
-            d = -(h0 / np.abs(g).max()) * g
+            gmax = np.abs(g).max()
+            d = -(h0 / gmax) * g if gmax > 0 else np.zeros_like(g)
             window = [(s, y, False) for s, y, _ in window]
         gd = (g * d).sum()
+        if not gd < 0:  # a stationary point: nothing descends from here
+            stopped = True
+            hist.append(L)
+            continue
         step, acc = 1.0, None
         for _t in range(13):
             xt = x + step * d
-            ct, gt = cost_and_grad(I0, J, xt, T, sigma, mu, rho, lam, p_update=p_update,
-                                   scheme=scheme)
-            margins[-1].append((L + 1e-4 * step * gd - ct.sum()) / max(abs(L), 1e-300))
-            if ct.sum() <= L + 1e-4 * step * gd:
-                acc = (xt, gt, ct.sum())
+            Lt, gt = f(xt)
+            margins[-1].append((L + 1e-4 * step * gd - Lt) / max(abs(L), 1e-300))
+            if Lt <= L + 1e-4 * step * gd:
+                acc = (xt, gt, Lt)
                 break
             step *= 0.5
         if acc is None:
@@ -310,3 +313,14 @@ def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: 
         x, g, L = xt, gt, Lt
         hist.append(L)
     return x, np.array(hist), margins
+
+
+def lbfgs_minimize(I0, J, p0, T: int, sigma: float, mu: float, rho: float, lam: float,
+                   iters: int, m: int, h0: float, p_update=0, scheme: str = "sl"):
+    """L-BFGS (`lbfgs_run`'s rules) on the cost of Eq. 4 for one instance, from p0.
+    Returns (p, costs [iters + 1], margins) as `lbfgs_run` does."""
+    def f(x):
+        c, g = cost_and_grad(I0, J, x, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
+        return c.sum(), g
+
+    return lbfgs_run(f, p0, iters, m, h0)

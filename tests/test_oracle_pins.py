@@ -630,3 +630,66 @@ def test_lbfgs_beats_the_normalised_gradient_descent_on_the_disk_pair():
     assert hist[-1] < 0.5 * gd
     np.testing.assert_allclose(oracle.cost_and_grad(*args, x, *prm, want_grad=False)[0].sum(),
                                hist[-1], rtol=1e-12)
+
+
+def _rosenbrock(x):
+    """The extended Rosenbrock function sum 100 (x_{i+1} - x_i^2)^2 + (1 - x_i)^2 and its
+    gradient; its only minimiser is (1, ..., 1)."""
+    L = np.sum(100.0 * (x[1:] - x[:-1] ** 2) ** 2 + (1.0 - x[:-1]) ** 2)
+    g = np.zeros_like(x)
+    g[:-1] += -400.0 * x[:-1] * (x[1:] - x[:-1] ** 2) - 2.0 * (1.0 - x[:-1])
+    g[1:] += 200.0 * (x[1:] - x[:-1] ** 2)
+    return L, g
+
+
+@pytest.mark.parametrize("n,iters,tol", [(2, 60, 1e-8), (10, 120, 1e-6)])
+def test_lbfgs_driver_reaches_the_rosenbrock_minimiser(n, iters, tol):
+    """From the classical start (-1.2, 1, -1.2, 1, ...), the driver (m = 5) reaches the
+    minimiser (1, ..., 1) of the Rosenbrock valley with a cost that never rises.  Stale
+    pairs (the window keeping its oldest entries), a flipped y or H_0 = I in place of
+    gamma I each leave it short of the minimiser within these iterations."""
+    x, hist, _ = oracle.lbfgs_run(_rosenbrock, np.array([-1.2, 1.0] * (n // 2)), iters, 5, 0.1)
+    assert np.abs(x - 1.0).max() < tol
+    assert np.all(np.diff(hist) <= 0)
+
+
+def test_lbfgs_driver_solves_a_quadratic_much_faster_than_gradient_descent():
+    """On a 30-dimensional convex quadratic with Hessian eigenvalues 1 .. 100, 100
+    iterations from 0 reach A^-1 b to 1e-7, where 100 gradient steps of 1/100 (the
+    largest safe fixed step) are still 0.1 away."""
+    r = np.random.default_rng(3)
+    n = 30
+    Q, _ = np.linalg.qr(r.normal(size=(n, n)))
+    A = Q @ np.diag(np.logspace(0, 2, n)) @ Q.T
+    b = r.normal(size=n)
+    xs = np.linalg.solve(A, b)
+    x, hist, _ = oracle.lbfgs_run(lambda v: (0.5 * v @ A @ v - b @ v, A @ v - b), np.zeros(n),
+                                  100, 5, 1.0)
+    assert np.abs(x - xs).max() < 1e-7
+    z = np.zeros(n)
+    for _ in range(100):
+        z = z - (A @ z - b) / 100.0
+    assert np.abs(z - xs).max() > 0.05
+
+
+def test_lbfgs_line_search_on_a_parabola_worked_by_hand():
+    """f(x) = x^2 from x = 1 (g = 2), first direction -h0 g / max|g| = -h0.
+    * h0 = 1.9999: step 1 lands on -0.9999, f = 0.99980001, above the Armijo bound
+      1 + 1e-4 * 2 * (-1.9999) = 0.99960002, so the search halves once and takes
+      x = 5e-5;
+    * h0 = 1.5 * 2^12: only the 13th trial, 2^-12, gives |1 - a h0| < 1 (x = -0.5);
+    * h0 = 1.5 * 2^13: no trial down to 2^-12 decreases f, so x stays at 1 and the
+      run stops;
+    * from x = 0 (g = 0) nothing descends: the run stops at once, without a trial."""
+    f = lambda v: (float(v @ v), 2.0 * v)
+    x, hist, margins = oracle.lbfgs_run(f, np.array([1.0]), 1, 5, 1.9999)
+    assert len(margins[0]) == 2 and margins[0][0] < 0 <= margins[0][1]
+    np.testing.assert_allclose(x, [1.0 - 0.5 * 1.9999], rtol=0, atol=1e-15)
+    x, hist, margins = oracle.lbfgs_run(f, np.array([1.0]), 1, 5, 1.5 * 2 ** 12)
+    assert len(margins[0]) == 13 and margins[0][-1] >= 0
+    np.testing.assert_allclose(x, [-0.5], rtol=0, atol=1e-15)
+    x, hist, margins = oracle.lbfgs_run(f, np.array([1.0]), 3, 5, 1.5 * 2 ** 13)
+    assert len(margins[0]) == 13 and max(margins[0]) < 0 and margins[1:] == [[], []]
+    assert x[0] == 1.0 and list(hist) == [1.0] * 4
+    x, hist, margins = oracle.lbfgs_run(f, np.array([0.0]), 2, 5, 1.0)
+    assert margins == [[], []] and x[0] == 0.0 and list(hist) == [0.0] * 3
