@@ -271,7 +271,7 @@ meta_status meta_lbfgs_direction(const meta_problem* prob, int m, int npairs,
  * -H g does not descend, which also forgets the instance's pairs), then a
  * backtracking line search from step 1, halving up to 12 times, that accepts
  * the first step a with L(x + a d) <= L(x) + 1e-4 a g^T d.  An instance whose
- * search fails keeps its iterate and stops.  cost_hist (host, nullable):
+ * search fails, or whose gradient is zero (d = 0), keeps its iterate and stops.  cost_hist (host, nullable):
  * [iters + 1][batch] costs, entry 0 at the start; iters_done (host, nullable):
  * [batch] the last iteration that moved each instance.  Blocks the host: the
  * costs of every trial are read back.  ws: a cost workspace (meta_workspace_size). */
