@@ -25,7 +25,7 @@ import torch
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoot_adjoint",
            "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
            "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES",
-           "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize"]
+           "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize", "clear_workspaces"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
@@ -138,7 +138,8 @@ SCHEMES = {"sl": 0, "euler": 1, "hybrid": 2}
 
 
 def _scheme(scheme) -> int:
-    """Integration scheme (Sec. 2.3): "sl" (the method), "euler", "hybrid" (forward only)."""
+    """Integration scheme (Sec. 2.3): "sl" (the method), "euler" or "hybrid"; every call
+    takes every scheme, and the adjoint is the exact transpose of the chosen one."""
     if scheme not in SCHEMES:
         raise ValueError("scheme must be 'sl', 'euler' or 'hybrid' (got %r)" % (scheme,))
     return SCHEMES[scheme]
@@ -244,7 +245,15 @@ def _p(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+# Workspaces of the calls made without `workspace=`: one per (problem shape, device,
+# stream), kept for reuse (each holds a whole trajectory) until clear_workspaces().
 _ws_cache = {}
+
+
+def clear_workspaces() -> None:
+    """Drops the cached workspaces of calls made without `workspace=` (their device
+    memory returns to torch's allocator once no plan or tensor refers to it)."""
+    _ws_cache.clear()
 
 
 def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0,
@@ -267,7 +276,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
                   ckpt: int = 0, p_update=0, scheme: str = "sl"
                   ) -> Tuple[torch.Tensor, torch.Tensor, Workspace]:
     """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory).
-    scheme "euler" / "hybrid": the other integration schemes of Sec. 2.3 (forward only)."""
+    scheme "euler" / "hybrid": the other integration schemes of Sec. 2.3."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
     B, dev = I0b.shape[0], I0b.device

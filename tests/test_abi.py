@@ -208,3 +208,10 @@ def test_lbfgs_arguments_fail_before_any_cuda_call(meta):
                                    None, None, null) == 3
     assert lib.meta_lbfgs_direction(ctypes.byref(pr), 5, 6, None, None, fake, fake, fake, need,
                                     null) == 1
+
+
+def test_workspace_cache_can_be_cleared(meta):
+    meta._ws_cache[("probe",)] = object()
+    meta.clear_workspaces()
+    assert meta._ws_cache == {}
+    assert "clear_workspaces" in meta.__all__
