@@ -164,7 +164,7 @@ def shoot(I0, p0, T: int, sigma: float, mu: float, rho: float,
           want_u: bool = False, p_update=0,
           scheme: str = "sl") -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
     """Returns (I[T+1, ...], p[T+1, ...], u[T, ndim, ...] or None).  scheme: "sl"
-    (semi-Lagrangian, the method), "euler" or "hybrid" (Sec. 2.3, forward only)."""
+    (semi-Lagrangian, the method), "euler" or "hybrid" (the other schemes of Sec. 2.3)."""
     I0, p0 = _f64(I0), _f64(p0)
     shp = I0.shape
     It = np.empty((T + 1,) + shp)

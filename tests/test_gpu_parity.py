@@ -379,6 +379,40 @@ def test_cost_and_grad_disk64_zero_momentum(meta):
     check_cost_grad(meta, w.I0, w.J, w.p0, w.T, w.sigma, w.mu, w.rho, w.lam)
 
 
+FD_EPS, FD_RTOL = 3e-2, 5e-3
+
+
+@pytest.mark.parametrize("p_update,scheme", [(0, "sl"), (1, "sl"), (0, "euler"), (0, "hybrid")])
+@pytest.mark.parametrize("dims,T,sigma", [((40, 37), 6, 2.0), ((12, 14, 13), 5, 1.5)])
+def test_gradient_matches_central_differences_of_the_gpu_cost(meta, dims, T, sigma, p_update,
+                                                              scheme):
+    """The library's dL/dp0 against central differences of its own cost, with no oracle
+    involved: L(p0 + eps d) - L(p0 - eps d) = <dL/dp0, 2 eps d> up to O(eps^3), along the
+    gradient and along a smooth direction (|d| <= 1, eps = 0.03, feet moving up to 0.3
+    voxel a step).  The FP32 torch re-implementation of the scheme meets this within
+    7e-4 on the same inputs; the bound is 5e-3."""
+    shape = (1,) + dims
+    I0 = phantoms.random_fields(20, 1, dims)[0]
+    J = np.clip(I0 + 0.2 * smooth_p(21, shape, 1.0, s=1.5), 0.0, 1.0).astype(np.float32)
+    p0 = smooth_p(22, shape, 25.0, s=1.5)
+    args = (T, sigma, 0.1, 1.0, 1e-3)
+    kw = dict(p_update=p_update, scheme=scheme)
+
+    def L(q):
+        c, _ = meta.cost_and_grad(cuda(I0), cuda(J), cuda(q), *args, want_grad=False, **kw)
+        return float(c.cpu().numpy().sum())
+
+    _, g = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args, **kw)
+    g = g.cpu().numpy().astype(np.float64)
+    for d in (g, smooth_p(99, shape, 1.0).astype(np.float64)):
+        d = d / np.abs(d).max()
+        qp = (p0 + FD_EPS * d).astype(np.float32)
+        qm = (p0 - FD_EPS * d).astype(np.float32)
+        fd = L(qp) - L(qm)
+        an = float((g * (qp.astype(np.float64) - qm)).sum())  # the steps actually taken
+        assert abs(fd - an) <= FD_RTOL * abs(an), (fd, an)
+
+
 @pytest.mark.parametrize("dims,B,T,sigma,scale", [((37, 141), 3, 4, 2.3, 40.0),
                                                   ((70, 33), 2, 5, 3.0, 100.0)])
 def test_cost_and_grad_ragged_2d(meta, dims, B, T, sigma, scale):
