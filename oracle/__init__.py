@@ -18,7 +18,9 @@ Functions (arrays are numpy, converted to float64 C-contiguous):
 * ``cost_and_grad(I0, J, p0, ...)``       -- Eq. 4 cost (3 terms) and dL/dp0
 * ``deformation(I0, p0, T, sigma, mu, rho)`` -- phi_T - Id and det D phi_T (numpy)
 * ``jacobian_det(phi)``                   -- det D phi of a map given in coordinates (numpy)
-* ``lbfgs_direction(g, S, Y)``, ``lbfgs_minimize(...)`` -- L-BFGS over the Eq. 4 cost (numpy)
+* ``lbfgs_direction(g, S, Y)``              -- the two-loop recursion (numpy)
+* ``lbfgs_run(f, x0, ...)``, ``lbfgs_minimize(...)`` -- L-BFGS on any objective, and
+  on the Eq. 4 cost (numpy)
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, dot-product
 transpose identities, finite differences, an independent torch re-implementation).

@@ -29,7 +29,7 @@
  *   - variant of the momentum update (p_update = 1): p_{t+1} = p~ J with
  *       J = det(Id - dt Dv), Dv_ae = D_e v_a, the Jacobian of the backtrack
  *       Id - dt v, of which 1 - dt div v is the first-order part.
- *   - the two other integration schemes of Sec. 2.3 (forward shooting only),
+ *   - the two other integration schemes of Sec. 2.3 (shooting and adjoint),
  *       explicit Euler steps of Eq. 5 and of the conservative form of Eq. 7
  *       with the same central differences D:
  *       Eulerian: I_{t+1} = I_t - dt sum_a (D_a I_t) v_a + dt mu p_t,

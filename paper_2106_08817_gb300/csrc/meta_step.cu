@@ -6,7 +6,8 @@
 //       the per-instance max displacement (the window of the adjoint), or with
 //       the det update p_{t+1} = p~ det(Id - dt Dv); 2-D on
 //       staged 32 x 8 tiles, 3-D marching along z through a ring of planes.
-//   k_euler  the Eulerian and hybrid steps of Sec. 2.3 (forward only).
+//   k_euler  the Eulerian and hybrid steps of Sec. 2.3 (their adjoints are in
+//       meta_adjoint.cu).
 //   k_deform / k_deform_out  the deformation phi_t of the grid and det D phi_T.
 //   k_pack / k_unpack  copies between the caller's contiguous arrays and the
 //       pitched trajectory.
@@ -291,13 +292,14 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
 
-// Eulerian (HYBRID = false) and hybrid steps of Sec. 2.3, forward only.  With
+// Eulerian (HYBRID = false) and hybrid steps of Sec. 2.3.  With
 // v = -rho u (slot sl.ut) and the central differences D of the scheme:
 //   p' = p - dt sum_a D_a (p v_a)                       (conservative Eq. 7)
 //   I' = I - dt sum_a (D_a I) v_a + dt mu p             (Eq. 5, Eulerian)
 //   I' = I~ + dt mu p~ at the foot of the advect         (hybrid)
 // from state slot sl.st into sl.st1.  Plain L1-cached loads of the 2d
-// neighbours; no per-step window is recorded (there is no adjoint).
+// neighbours.  The hybrid records its per-step max displacement, the gather
+// window of its adjoint's image step; the Eulerian adjoint needs none.
 template <int NDIM, bool HYBRID>
 __global__ void __launch_bounds__(kPX * kPY)
 k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
