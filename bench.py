@@ -251,21 +251,46 @@ def ncu_traffic(kclass: str, ndim: int, launch_voxels: int):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(w, target_s: float, max_instances: int = None):
-    """Time oracle cost_and_grad on instances 0, 1, ... until ~target_s seconds."""
+def oracle_sample(w, target_s: float, max_instances: int = None, threads: int = None):
+    """Time oracle cost_and_grad on instances 0, 1, ... until ~target_s seconds, on
+    `threads` threads (default: the current count, every host core unless changed);
+    the count is restored afterwards.  Returns (instances, seconds, threads)."""
     import oracle
-    oracle.set_threads(oracle.max_threads())
+    prev = oracle.max_threads()
+    n_thr = int(threads or prev)
+    oracle.set_threads(n_thr)
     done, t0 = 0, time.perf_counter()
     n_max = max_instances or 100 * w.batch
-    while done < n_max:
-        b = done % w.batch
-        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
-                             float(w.rho[b]), float(w.lam[b]))
-        done += 1
-        if time.perf_counter() - t0 >= target_s:
-            break
+    try:
+        while done < n_max:
+            b = done % w.batch
+            oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
+                                 float(w.rho[b]), float(w.lam[b]))
+            done += 1
+            if time.perf_counter() - t0 >= target_s:
+                break
+    finally:
+        oracle.set_threads(prev)
     el = time.perf_counter() - t0
-    return done, el, oracle.max_threads()
+    return done, el, n_thr
+
+
+def cpu_baseline_entry(w, seconds: float) -> dict:
+    """The bench line's cpu_baseline: the FP64 oracle on every host core over about
+    `seconds` (the value), plus one thread over a third of that when one instance fits
+    in it (estimated from the all-core rate), else single_thread is null."""
+    N, T, B = w.voxels, w.T, w.batch
+    n_inst, el, cores = oracle_sample(w, seconds)
+    out = {"value": n_inst * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d of %d instances, one FP64 cost_and_grad each (%s, T=%d), %.1f s"
+                     % (n_inst, B, "x".join(map(str, w.dims)), T, el),
+           "single_thread": None}
+    budget = seconds / 3.0
+    if el / n_inst * cores <= budget:
+        n1, el1, _ = oracle_sample(w, budget, threads=1)
+        out["single_thread"] = {"value": n1 * N * T / el1, "unit": UNIT, "cores": 1,
+                                "sample": "%d instances, %.1f s" % (n1, el1)}
+    return out
 
 
 def run_reference(args):
@@ -660,10 +685,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            n_inst, el, cores = oracle_sample(w, args.cpu_seconds)
-            cpu = {"value": n_inst * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "%d of %d instances, one FP64 cost_and_grad each (%s, T=%d), "
-                             "%.1f s" % (n_inst, B, "x".join(map(str, w.dims)), T, el)}
+            cpu = cpu_baseline_entry(w, args.cpu_seconds)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -75,3 +75,16 @@ def test_reference_arm_prints_one_complete_line():
     assert d["config"]["workload"] == "disk64"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    """cpu_baseline: the oracle on every host core (value, cores), and on one thread when
+    an instance fits in a third of the sample time (null otherwise)."""
+    import oracle
+    w = bench.workload("disk64")
+    d = bench.cpu_baseline_entry(w, 0.6)
+    assert d["kind"] == "oracle" and d["unit"] == bench.UNIT and d["value"] > 0
+    assert d["cores"] == oracle.max_threads()
+    assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
+    assert oracle.max_threads() == d["cores"]  # the thread count is restored
+    assert bench.cpu_baseline_entry(w, 1e-9)["single_thread"] is None
