@@ -413,6 +413,41 @@ def test_gradient_matches_central_differences_of_the_gpu_cost(meta, dims, T, sig
         assert abs(fd - an) <= FD_RTOL * abs(an), (fd, an)
 
 
+@pytest.mark.parametrize("p_update,scheme", [(0, "sl"), (1, "sl"), (0, "euler"), (0, "hybrid")])
+@pytest.mark.parametrize("dims,T,sigma", [((40, 37), 6, 2.0), ((12, 14, 13), 5, 1.5)])
+def test_shooting_adjoint_against_central_differences_of_the_gpu_shot(meta, dims, T, sigma,
+                                                                      p_update, scheme):
+    """meta_shoot_adjoint against central differences of the library's own forward
+    shooting, with no oracle involved: for F = <gI1, I_T> + <gp1, p_T> and a tangent
+    (dI, dp), F(+eps) - F(-eps) = <dL/dI0, 2 eps dI> + <dL/dp0, 2 eps dp> up to O(eps^3)
+    (eps = 0.01, |dI|, |dp| <= 1).  The FP32 torch re-implementation meets this within
+    3e-4 against the oracle's adjoint; the bound is 5e-3."""
+    shape = (1,) + dims
+    I0 = phantoms.random_fields(20, 1, dims)[0]
+    p0 = smooth_p(22, shape, 25.0, s=1.5)
+    gI1, gp1 = smooth_p(30, shape, 1.0), smooth_p(31, shape, 0.05)
+    dI, dp = smooth_p(32, shape, 1.0), smooth_p(33, shape, 1.0)
+    dI, dp = dI / np.abs(dI).max(), dp / np.abs(dp).max()
+    args = (T, sigma, 0.1, 1.0)
+    kw = dict(p_update=p_update, scheme=scheme)
+    _, _, ws = meta.shoot_forward(cuda(I0), cuda(p0), *args, **kw)
+    gI0, gp0 = meta.shoot_adjoint(cuda(gI1), cuda(gp1), ws, *args, **kw)
+    gI0 = gI0.cpu().numpy().astype(np.float64)
+    gp0 = gp0.cpu().numpy().astype(np.float64)
+
+    def F(I, p):
+        IT, pT, _ = meta.shoot_forward(cuda(I), cuda(p), *args, **kw)
+        return float((IT.cpu().numpy().astype(np.float64) * gI1).sum()
+                     + (pT.cpu().numpy().astype(np.float64) * gp1).sum())
+
+    eps = 1e-2
+    Ip, Im = (I0 + eps * dI).astype(np.float32), (I0 - eps * dI).astype(np.float32)
+    pp, pm = (p0 + eps * dp).astype(np.float32), (p0 - eps * dp).astype(np.float32)
+    fd = F(Ip, pp) - F(Im, pm)
+    an = float((gI0 * (Ip.astype(np.float64) - Im)).sum() + (gp0 * (pp.astype(np.float64) - pm)).sum())
+    assert abs(fd - an) <= 5e-3 * abs(an), (fd, an)
+
+
 @pytest.mark.parametrize("dims,B,T,sigma,scale", [((37, 141), 3, 4, 2.3, 40.0),
                                                   ((70, 33), 2, 5, 3.0, 100.0)])
 def test_cost_and_grad_ragged_2d(meta, dims, B, T, sigma, scale):
