@@ -693,3 +693,26 @@ def test_lbfgs_line_search_on_a_parabola_worked_by_hand():
     assert x[0] == 1.0 and list(hist) == [1.0] * 4
     x, hist, margins = oracle.lbfgs_run(f, np.array([0.0]), 2, 5, 1.0)
     assert margins == [[], []] and x[0] == 0.0 and list(hist) == [0.0] * 3
+
+
+@pytest.mark.parametrize("p_update,scheme", [("div", "sl"), ("det", "sl"), ("div", "euler"),
+                                             ("div", "hybrid")])
+@pytest.mark.parametrize("dims", [(33, 29), (9, 11, 10)])
+def test_results_do_not_depend_on_the_thread_count(dims, p_update, scheme):
+    """The oracle parallelises only loops whose iterations write their own voxel with a
+    fixed summation order, so one thread and every host core give the same bits (the
+    golden values and the host baselines are taken on machines with different core
+    counts)."""
+    I, J, p = _fd_problem(dims, 50)
+    args = (4, 1.3, 0.2, 1.1, 0.01)
+    kw = dict(p_update=p_update, scheme=scheme)
+    n = oracle.max_threads()
+    try:
+        oracle.set_threads(1)
+        c1, g1 = oracle.cost_and_grad(I, J, p, *args, **kw)
+        oracle.set_threads(max(n, 2))
+        cn, gn = oracle.cost_and_grad(I, J, p, *args, **kw)
+    finally:
+        oracle.set_threads(n)
+    np.testing.assert_array_equal(c1, cn)
+    np.testing.assert_array_equal(g1, gn)
