@@ -483,6 +483,28 @@ def test_extreme_aspect_ratios(meta, dims, T, sigma):
                     np.array([1e-3, 1e-2]))
 
 
+@pytest.mark.parametrize("dims,sigma", [
+    ((6, 128), 7.0), ((5, 129), 8.5), ((7, 127), 7.0), ((3, 257), 8.5),   # x: 1 and 2-3 tiles
+    ((129, 5), 7.0), ((128, 6), 8.5), ((257, 4), 7.0),                    # y: strided tiles
+    ((5, 33, 129), 8.5), ((129, 6, 7), 7.0), ((33, 17, 20), 8.0),         # 3-D, z tiles
+])
+def test_tile_multiples_and_the_widest_compiled_tap_loops(meta, dims, sigma):
+    """Extents at, one below and one above the 128-wide tiles of the blur passes, with
+    sigma 7 to 8.5 (r = 21 to 26): the tap loops compiled for 6 and 7 chunks of 8 taps,
+    whose halos are wider than most of these images.  Momenta move the feet 0.15 to 2.3
+    voxels a step (in 3-D past the deterministic gather window, into the scatter
+    fallback).  Forward and cost / gradient against the oracle (the FP32 torch
+    re-implementation meets them within 3.4e-5 of the gradient bound's 1e-3)."""
+    B = 2
+    I0, _ = phantoms.random_fields(161, B, dims)
+    J, _ = phantoms.random_fields(162, B, dims)
+    p0 = smooth_p(163, (B,) + dims, 300.0 if len(dims) == 2 else 3000.0, s=1.2)
+    check_forward(meta, I0, p0, 3, sigma, [0.002, 0.0], [1.0, 1.3])
+    # lambda small enough that dL/dp0 is the adjoint's, not the regulariser's 2 lambda rho p0
+    check_cost_grad(meta, I0, J, p0, 3, sigma, np.array([0.002, 0.0]), np.array([1.0, 1.3]),
+                    np.array([1e-7, 1e-6]))
+
+
 @pytest.mark.parametrize("dims,B,T,sigma,p_update", [
     ((21, 19), 3, 1, 1.5, "div"),       # a single step
     ((11, 12, 13), 2, 1, 1.0, "det"),   # a single 3-D step, det update
