@@ -596,6 +596,31 @@ def test_plan_replays_the_recorded_call(meta):
     assert plan.ws.status() == 0
 
 
+@pytest.mark.parametrize("scheme", ["sl", "hybrid"])
+@pytest.mark.parametrize("dims,B,T,sigma", [((45, 70), 5, 4, 2.5), ((10, 12, 14), 3, 3, 1.5)])
+def test_batched_instances_equal_their_single_calls_bitwise(meta, dims, B, T, sigma, scheme):
+    """Instances share every launch of a batch (one grid z index each) but nothing else:
+    each one's I_T, p_T, cost and dL/dp0 are, bit for bit, what a call on it alone
+    gives, with its own mu, rho, lambda and its own displacement window."""
+    I0, _ = phantoms.random_fields(171, B, dims)
+    J, _ = phantoms.random_fields(172, B, dims)
+    p0 = smooth_p(173, (B,) + dims, 20.0 if len(dims) == 2 else 15.0, s=1.5)
+    p0 *= np.linspace(0.2, 1.0, B, dtype=np.float32).reshape((B,) + (1,) * len(dims))
+    mu = np.linspace(0.0, 0.2, B).astype(np.float32)
+    rho = np.linspace(0.8, 1.3, B).astype(np.float32)
+    lam = np.geomspace(1e-3, 1e-1, B).astype(np.float32)
+    I1, p1, _ = meta.shoot_forward(cuda(I0), cuda(p0), T, sigma, mu, rho, scheme=scheme)
+    c, g = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam, scheme=scheme)
+    for b in range(B):
+        one = slice(b, b + 1)
+        I1b, p1b, _ = meta.shoot_forward(cuda(I0[one]), cuda(p0[one]), T, sigma, mu[one], rho[one],
+                                         scheme=scheme)
+        cb, gb = meta.cost_and_grad(cuda(I0[one]), cuda(J[one]), cuda(p0[one]), T, sigma, mu[one],
+                                    rho[one], lam[one], scheme=scheme)
+        assert torch.equal(I1b[0], I1[b]) and torch.equal(p1b[0], p1[b]), b
+        assert torch.equal(cb[0], c[b]) and torch.equal(gb[0], g[b]), b
+
+
 def test_group_plan_runs_mixed_shapes_in_one_graph(meta):
     """Problems of different size, dimension, T and sigma recorded as parallel
     graph branches give what their separate calls give, bit for bit; one small
