@@ -4,7 +4,7 @@
 // The inverse-Hessian product is the two-loop recursion (Nocedal & Wright,
 // Numerical Optimization, Algorithm 7.4) over the last m pairs
 // s_i = x_{i+1} - x_i, y_i = g_{i+1} - g_i of each instance, with
-// H_0 = gamma I, gamma = s^T y / y^T y of the newest pair.  Every vector
+// H_0 = gamma I, gamma = s^T y / y^T y of the newest usable pair.  Every vector
 // operation runs on the device: FP64 dot products with a fixed summation order
 // (per-CTA partials over fixed chunks, then one CTA per instance), FP32 axpys
 // whose coefficients stay on the device, so a direction needs no host round
