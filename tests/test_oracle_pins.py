@@ -716,3 +716,65 @@ def test_results_do_not_depend_on_the_thread_count(dims, p_update, scheme):
         oracle.set_threads(n)
     np.testing.assert_array_equal(c1, cn)
     np.testing.assert_array_equal(g1, gn)
+
+
+# ------------------------------------------------- conservation along the geodesic
+
+def _hamiltonian_problem(n):
+    """One continuous picture on [0, 1]^2 sampled on n^2 voxels: two Gaussian blobs and a
+    windowed oscillating momentum, with sigma and rho scaled so that K and v are the same
+    physical operators at every n (sigma in voxels ~ n, rho ~ n^2 since v and grad I are
+    both measured in voxels)."""
+    x = (np.arange(n) + 0.5) / n
+    Y, X = np.meshgrid(x, x, indexing="ij")
+
+    def blob(cy, cx, s):
+        return np.exp(-((Y - cy) ** 2 + (X - cx) ** 2) / (2 * s * s))
+
+    I0 = 0.8 * blob(0.47, 0.53, 0.11) + 0.4 * blob(0.56, 0.41, 0.08)
+    p0 = 12.0 * blob(0.5, 0.5, 0.14) * np.sin(X * 64 / 5.0) * np.cos(Y * 64 / 6.0)
+    return I0, p0, 3.0 * n / 64, 0.05, (n / 64) ** 2
+
+
+def _hamiltonian_drift(n, scheme, p_update="div", Ts=(20, 40, 80)):
+    """Relative change of H = rho/2 <m, K m> + mu/2 |p|^2 (m = p grad I) over the shot,
+    for each T, and its limit dt -> 0 by Richardson extrapolation of the first-order
+    time error."""
+    I0, p0, sigma, mu, rho = _hamiltonian_problem(n)
+
+    def H(I, p):
+        m = np.stack([p * oracle.diff(I, a) for a in range(2)])
+        return 0.5 * rho * sum((m[a] * oracle.blur(m[a], sigma)).sum() for a in range(2)) \
+            + 0.5 * mu * (p * p).sum()
+
+    d = []
+    for T in Ts:
+        It, pt, _ = oracle.shoot(I0, p0, T, sigma, mu, rho, scheme=scheme, p_update=p_update)
+        h0 = H(It[0], pt[0])
+        d.append((H(It[-1], pt[-1]) - h0) / h0)
+    return d[2] - (d[1] - d[2]), d
+
+
+@pytest.mark.parametrize("scheme,p_update,bound", [("sl", "div", 1e-2), ("sl", "det", 1e-2),
+                                                   ("hybrid", "div", 5e-4)])
+def test_hamiltonian_is_conserved_in_the_limit(scheme, p_update, bound):
+    """Eq. 3 with v = -rho K(p grad I) is Hamiltonian: with H(I, p) = rho/2 <p grad I,
+    K(p grad I)> + mu/2 |p|^2, dI/dt = dH/dp = -<grad I, v> + mu p and dp/dt = -dH/dI =
+    -div(p v), so H (the energy of the geodesic, Sec. 2.1) is constant in time.  The
+    discrete shot changes H by a first-order time error plus a first-order space error
+    (linear interpolation); extrapolated to dt -> 0, the change halves each time the same
+    picture is sampled twice as finely.  A wrong sign of the source mu p, of div v or of
+    the backtrack, or p left untransported, each leave a change that does not vanish."""
+    lim = [_hamiltonian_drift(n, scheme, p_update)[0] for n in (32, 64, 128)]
+    assert 1.6 < lim[0] / lim[1] < 2.4 and 1.6 < lim[1] / lim[2] < 2.4, lim
+    assert abs(lim[2]) < bound, lim
+
+
+def test_hamiltonian_of_the_eulerian_scheme_drifts_only_in_time():
+    """The Eulerian scheme's central differences are the ones H is built from, so the
+    semi-discrete scheme conserves H up to the boundary: the change is the first-order
+    time error alone (halving as T doubles) and extrapolates to ~0 at every n."""
+    for n in (32, 64, 128):
+        lim, d = _hamiltonian_drift(n, "euler")
+        assert abs(lim) < 1e-5, (n, lim)
+        assert 1.9 < d[0] / d[1] < 2.1 and 1.9 < d[1] / d[2] < 2.1, (n, d)
