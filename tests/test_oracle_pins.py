@@ -778,3 +778,27 @@ def test_hamiltonian_of_the_eulerian_scheme_drifts_only_in_time():
         lim, d = _hamiltonian_drift(n, "euler")
         assert abs(lim) < 1e-5, (n, lim)
         assert 1.9 < d[0] / d[1] < 2.1 and 1.9 < d[1] / d[2] < 2.1, (n, d)
+
+
+def test_metamorphosis_creates_the_blob_that_lddmm_cannot():
+    """The qualitative claim of Sec. 3 (Fig. 2): the target has a small blob that the
+    source lacks.  Metamorphosis (mu > 0) creates it through its intensity source;
+    LDDMM (mu = 0) can only move the disk's intensities.  After 100 normalised gradient
+    steps from p0 = 0 on the 64^2 disk pair, the Metamorphosis shot matches the blob
+    (mean within 0.05 of the target's, data term under 1% of LDDMM's), while the LDDMM
+    shot leaves it below half of the target's mean."""
+    w = phantoms.disk_pair_64(random_p0=False)
+    I0, J = w.I0[0].astype(np.float64), w.J[0].astype(np.float64)
+    Y, X = np.meshgrid(np.arange(64.0), np.arange(64.0), indexing="ij")
+    blob = (Y - 52) ** 2 + (X - 32) ** 2 <= 16
+    res = {}
+    for mu in (0.0, 0.2):
+        p = np.zeros_like(I0)
+        for it in range(100):
+            c, g = oracle.cost_and_grad(I0, J, p, w.T, w.sigma, mu, 1.0, 1e-4)
+            p -= 0.5 * 0.98 ** it * g / np.abs(g).max()
+        IT = oracle.shoot(I0, p, w.T, w.sigma, mu, 1.0)[0][-1]
+        res[mu] = (c[0], IT[blob].mean())
+    assert abs(res[0.2][1] - J[blob].mean()) < 0.05
+    assert res[0.2][0] < 0.01 * res[0.0][0]
+    assert res[0.0][1] < 0.5 * J[blob].mean()
