@@ -614,6 +614,33 @@ def test_momentum_ripples_and_the_eulerian_step_limit_on_the_c_phantom():
     assert eu20 > 1e3 * sl and eu38 < 2.0 * sl
 
 
+def test_with_ssd_objects_that_do_not_overlap_do_not_attract():
+    """Sec. 3: the sum of squared differences gives no force between objects that do not
+    overlap.  LDDMM gradient descent (60 normalised steps) moves a disk towards a copy of
+    it shifted by 6 voxels (they overlap), but not towards a copy shifted by 24: its
+    centroid stays put and the cost falls only by shrinking it."""
+    from scipy import ndimage
+    Y, X = np.meshgrid(np.arange(64.0), np.arange(64.0), indexing="ij")
+
+    def disk(cx):
+        return ndimage.gaussian_filter(((Y - 32) ** 2 + (X - cx) ** 2 <= 64).astype(float), 1.0)
+
+    def centroid(I):
+        return (I * X).sum() / I.sum()
+
+    S = disk(20.0)
+    moved = {}
+    for shift in (6, 24):
+        J = disk(20.0 + shift)
+        p = np.zeros_like(S)
+        for _ in range(60):
+            c, g = oracle.cost_and_grad(S, J, p, 10, 3.0, 0.0, 1.0, 1e-4)
+            p -= 0.5 * g / np.abs(g).max()
+        moved[shift] = centroid(oracle.shoot(S, p, 10, 3.0, 0.0, 1.0)[0][-1]) - centroid(S)
+        assert c[0] < 0.8 * 0.5 * ((S - J) ** 2).sum()  # the cost fell either way
+    assert moved[6] > 1.5 and abs(moved[24]) < 0.1, moved
+
+
 # ------------------------------------------------------------------- L-BFGS
 
 def test_lbfgs_direction_is_scipys_inverse_hessian_product():
