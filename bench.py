@@ -802,13 +802,17 @@ def run_mix(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ellipses16x256")
-    ap.add_argument("--no-torch", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1,
+                    help="ranks (one GPU each; launch with torch.distributed.run when > 1)")
+    ap.add_argument("--steps", type=int, default=200, help="timed steps (cost_and_grad calls)")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed steps before them")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours",
+                    help="reference: the FP64 oracle on the host cores")
+    ap.add_argument("--workload", default="ellipses16x256",
+                    help="ellipses16x256, disk64, head128, mri160 or mix64")
+    ap.add_argument("--no-torch", action="store_true",
+                    help="skip torch.autograd through the PyTorch-ops scheme")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's cpu_baseline")
     ap.add_argument("--no-deform", action="store_true",
                     help="skip the deformation measurement (meta_shoot_deform)")
     ap.add_argument("--no-det", action="store_true",
@@ -817,7 +821,8 @@ def main():
                     help="skip the Eulerian / hybrid schemes and the 'C' stability study")
     ap.add_argument("--no-lbfgs", action="store_true",
                     help="skip the L-BFGS against gradient-descent comparison")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="length of the cpu_baseline sample")
     ap.add_argument("--streams", type=int, default=8, help="graph branches for mix64")
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in tile shapes instead of the autotuner's")
