@@ -232,6 +232,18 @@ def _shape(I0: torch.Tensor, ndim: Optional[int]) -> Tuple[torch.Tensor, int, Tu
     raise ValueError("expected [B, *dims] or [*dims] with ndim = %d" % ndim)
 
 
+def _like(x: torch.Tensor, ref: torch.Tensor, name: str) -> torch.Tensor:
+    """x with the shape of ref, [B, *dims]: x must have that shape or, for B = 1, the
+    shape [*dims].  Any other shape raises, even one with as many elements (transposed
+    axes would otherwise be read silently in the wrong order)."""
+    shp, want = tuple(x.shape), tuple(ref.shape)
+    if shp == want:
+        return x
+    if want[0] == 1 and shp == want[1:]:
+        return x.reshape(want)
+    raise ValueError("%s has shape %s where %s is expected" % (name, shp, want))
+
+
 def _coef(v, B: int, device) -> torch.Tensor:
     t = torch.as_tensor(v, dtype=torch.float32, device=device).reshape(-1)
     if t.numel() == 1:
@@ -278,7 +290,7 @@ def shoot_forward(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, 
     """Geodesic shooting (Eq. 3, Sec. 2.3): returns (I_T, p_T, workspace with the trajectory).
     scheme "euler" / "hybrid": the other integration schemes of Sec. 2.3."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
-    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
     B, dev = I0b.shape[0], I0b.device
     ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
@@ -306,7 +318,7 @@ def shoot_deform(I0: torch.Tensor, p0: torch.Tensor, T: int, sigma: float, mu, r
     if not (want_phi or want_jac):
         raise ValueError("ask for phi, jac or both")
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
-    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
     B, dev = I0b.shape[0], I0b.device
     ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
@@ -337,7 +349,7 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
     B, dev = g1.shape[0], g1.device
     if not workspace.matches(dims, B, T, sigma, workspace.ckpt, scheme):
         raise ValueError("workspace was made for another problem")
-    gp1b = None if gp1 is None else _as_batch(gp1, "gp1")[0].reshape(g1.shape)
+    gp1b = None if gp1 is None else _like(_as_batch(gp1, "gp1")[0], g1, "gp1")
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     gp0 = torch.empty_like(g1)
     gI0 = torch.empty_like(g1) if want_gI0 else None
@@ -362,8 +374,8 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     and dL/dp0 ([B, *dims] float32) by the hand-written discrete adjoint.  p_update "det"
     shoots with p' = p~ det(Id - dt Dv) instead of p~ (1 - dt div v)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
-    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
-    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    Jb = _like(_as_batch(J, "J")[0], I0b, "J")
+    p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
     B, dev = I0b.shape[0], I0b.device
     ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
@@ -414,8 +426,8 @@ def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma:
     """Times cost_and_grad on these inputs for candidate tile shapes (meta_autotune),
     records the fastest for the problem shape and returns it.  Blocking."""
     I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
-    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
-    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    Jb = _like(_as_batch(J, "J")[0], I0b, "J")
+    p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
     B, dev = I0b.shape[0], I0b.device
     ws = _workspace(dims, B, T, sigma, dev, None, ckpt, scheme)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
@@ -450,8 +462,8 @@ def lbfgs_direction(g: torch.Tensor, S: Sequence[torch.Tensor], Y: Sequence[torc
     gb, nd, dims, sq = _shape(_as_batch(g, "g")[0], ndim)
     B, dev = gb.shape[0], gb.device
     m = int(m or max(1, len(S)))
-    Sb = [_as_batch(x, "s")[0].reshape(gb.shape) for x in S]
-    Yb = [_as_batch(x, "y")[0].reshape(gb.shape) for x in Y]
+    Sb = [_like(_as_batch(x, "s")[0], gb, "s") for x in S]
+    Yb = [_like(_as_batch(x, "y")[0], gb, "y") for x in Y]
     arr = lambda ts: (ctypes.c_void_p * max(1, len(ts)))(*[t.data_ptr() for t in ts])
     lws = torch.empty(lbfgs_workspace_size(dims, B, m), dtype=torch.uint8, device=dev)
     d = torch.empty_like(gb)
@@ -469,8 +481,8 @@ def lbfgs_minimize(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, 
     """L-BFGS on the Eq. 4 cost from p0 (meta_lbfgs_minimize).  Returns (p, costs
     [iters + 1, B] float64 numpy, last moving iteration per instance)."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
-    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
-    p = _as_batch(p0, "p0")[0].reshape(I0b.shape).clone()
+    Jb = _like(_as_batch(J, "J")[0], I0b, "J")
+    p = _like(_as_batch(p0, "p0")[0], I0b, "p0").clone()
     B, dev = I0b.shape[0], I0b.device
     ws = _workspace(dims, B, T, sigma, dev, None, ckpt, scheme)
     lws = torch.empty(lbfgs_workspace_size(dims, B, m), dtype=torch.uint8, device=dev)
@@ -502,8 +514,8 @@ class CostAndGradPlan:
         I0b, nd, dims, _ = _shape(_as_batch(I0, "I0")[0], ndim)
         B, dev = I0b.shape[0], I0b.device
         self.I0 = I0b.clone()
-        self.J = _as_batch(J, "J")[0].reshape(I0b.shape).clone()
-        self.p0 = _as_batch(p0, "p0")[0].reshape(I0b.shape).clone()
+        self.J = _like(_as_batch(J, "J")[0], I0b, "J").clone()
+        self.p0 = _like(_as_batch(p0, "p0")[0], I0b, "p0").clone()
         self.mu, self.rho, self.lam = (_coef(mu, B, dev).clone(), _coef(rho, B, dev).clone(),
                                        _coef(lam, B, dev).clone())
         self.cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
@@ -554,8 +566,8 @@ class GroupPlan:
         for k, pb in enumerate(problems):
             I0b, nd, dims, _ = _shape(_as_batch(pb["I0"], "I0")[0], pb.get("ndim"))
             B, dev = I0b.shape[0], I0b.device
-            it = {"I0": I0b.clone(), "J": _as_batch(pb["J"], "J")[0].reshape(I0b.shape).clone(),
-                  "p0": _as_batch(pb["p0"], "p0")[0].reshape(I0b.shape).clone(),
+            it = {"I0": I0b.clone(), "J": _like(_as_batch(pb["J"], "J")[0], I0b, "J").clone(),
+                  "p0": _like(_as_batch(pb["p0"], "p0")[0], I0b, "p0").clone(),
                   "mu": _coef(pb["mu"], B, dev).clone(), "rho": _coef(pb.get("rho", 1.0), B, dev).clone(),
                   "lam": _coef(pb.get("lam", 1e-3), B, dev).clone(),
                   "cost": torch.empty((B, 3), dtype=torch.float64, device=dev),
@@ -608,8 +620,8 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
     device tensors for mu, rho, lam) so that this call allocates nothing either.
     Calls share the scratch: order them on one stream."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
-    Jb = _as_batch(J, "J")[0].reshape(I0b.shape)
-    p0b = _as_batch(p0, "p0")[0].reshape(I0b.shape)
+    Jb = _like(_as_batch(J, "J")[0], I0b, "J")
+    p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
     B, dev = I0b.shape[0], I0b.device
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     if out is not None:

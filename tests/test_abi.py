@@ -215,3 +215,18 @@ def test_workspace_cache_can_be_cleared(meta):
     meta.clear_workspaces()
     assert meta._ws_cache == {}
     assert "clear_workspaces" in meta.__all__
+
+
+def test_arrays_must_match_the_image_shape(meta):
+    """Every array of a call has the image batch's shape [B, *dims] (or [*dims] when
+    B = 1); a transposed or otherwise reshaped array raises instead of being read in
+    the wrong order."""
+    import torch
+    ref = torch.zeros(2, 5, 7)
+    assert meta._like(torch.ones(2, 5, 7), ref, "J").shape == (2, 5, 7)
+    one = torch.zeros(1, 5, 7)
+    assert meta._like(torch.ones(5, 7), one, "J").shape == (1, 5, 7)
+    for bad in (torch.ones(2, 7, 5), torch.ones(5, 7), torch.ones(2, 35), torch.ones(70),
+                torch.ones(3, 5, 7)):
+        with pytest.raises(ValueError):
+            meta._like(bad, ref, "J")
