@@ -233,9 +233,11 @@ def _shape(I0: torch.Tensor, ndim: Optional[int]) -> Tuple[torch.Tensor, int, Tu
 
 
 def _like(x: torch.Tensor, ref: torch.Tensor, name: str) -> torch.Tensor:
-    """x with the shape of ref, [B, *dims]: x must have that shape or, for B = 1, the
-    shape [*dims].  Any other shape raises, even one with as many elements (transposed
-    axes would otherwise be read silently in the wrong order)."""
+    """x with the shape of ref, [B, *dims], on ref's device: x must have that shape or,
+    for B = 1, the shape [*dims].  Any other shape raises, even one with as many
+    elements (transposed axes would otherwise be read silently in the wrong order)."""
+    if x.device != ref.device:
+        raise ValueError("%s is on %s, the images on %s" % (name, x.device, ref.device))
     shp, want = tuple(x.shape), tuple(ref.shape)
     if shp == want:
         return x
@@ -273,6 +275,8 @@ def _workspace(dims, B, T, sigma, device, ws: Optional[Workspace], ckpt: int = 0
     if ws is not None:
         if not ws.matches(dims, B, T, sigma, ckpt, scheme):
             raise ValueError("workspace was made for another problem")
+        if ws.buf.device != torch.device(device):
+            raise ValueError("workspace is on %s, the images on %s" % (ws.buf.device, device))
         return ws
     key = (tuple(dims), B, T, float(sigma), int(ckpt), scheme, str(device),
            torch.cuda.current_stream(device).cuda_stream)
@@ -349,6 +353,8 @@ def shoot_adjoint(gI1: torch.Tensor, gp1: Optional[torch.Tensor], workspace: Wor
     B, dev = g1.shape[0], g1.device
     if not workspace.matches(dims, B, T, sigma, workspace.ckpt, scheme):
         raise ValueError("workspace was made for another problem")
+    if workspace.buf.device != dev:
+        raise ValueError("workspace is on %s, the arrays on %s" % (workspace.buf.device, dev))
     gp1b = None if gp1 is None else _like(_as_batch(gp1, "gp1")[0], g1, "gp1")
     mu_t, rho_t = _coef(mu, B, dev), _coef(rho, B, dev)
     gp0 = torch.empty_like(g1)

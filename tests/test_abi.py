@@ -227,6 +227,6 @@ def test_arrays_must_match_the_image_shape(meta):
     one = torch.zeros(1, 5, 7)
     assert meta._like(torch.ones(5, 7), one, "J").shape == (1, 5, 7)
     for bad in (torch.ones(2, 7, 5), torch.ones(5, 7), torch.ones(2, 35), torch.ones(70),
-                torch.ones(3, 5, 7)):
+                torch.ones(3, 5, 7), torch.empty(2, 5, 7, device="meta")):
         with pytest.raises(ValueError):
             meta._like(bad, ref, "J")
