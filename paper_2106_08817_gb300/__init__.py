@@ -246,6 +246,25 @@ def _like(x: torch.Tensor, ref: torch.Tensor, name: str) -> torch.Tensor:
     raise ValueError("%s has shape %s where %s is expected" % (name, shp, want))
 
 
+def _outputs(out, ref: torch.Tensor):
+    """The caller's (cost, grad) for a batch shaped like ref: cost a contiguous float64
+    [B, 3], grad None or a contiguous float32 array of ref's shape, both on ref's device
+    (the kernels write them whole)."""
+    cost, grad = out
+    B = ref.shape[0]
+    if not (isinstance(cost, torch.Tensor) and cost.dtype == torch.float64
+            and tuple(cost.shape) == (B, 3) and cost.is_contiguous()
+            and cost.device == ref.device):
+        raise ValueError("out cost must be a contiguous float64 [%d, 3] tensor on %s"
+                         % (B, ref.device))
+    if grad is not None:
+        if not (isinstance(grad, torch.Tensor) and grad.dtype == torch.float32
+                and grad.is_contiguous()):
+            raise ValueError("out grad must be a contiguous float32 tensor")
+        _like(grad, ref, "out grad")
+    return cost, grad
+
+
 def _coef(v, B: int, device) -> torch.Tensor:
     t = torch.as_tensor(v, dtype=torch.float32, device=device).reshape(-1)
     if t.numel() == 1:
@@ -386,7 +405,7 @@ def cost_and_grad(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, s
     ws = _workspace(dims, B, T, sigma, dev, workspace, ckpt, scheme)
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     if out is not None:
-        cost, grad = out
+        cost, grad = _outputs(out, I0b)
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b) if want_grad else None
@@ -631,7 +650,7 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
     B, dev = I0b.shape[0], I0b.device
     mu_t, rho_t, lam_t = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
     if out is not None:
-        cost, grad = out
+        cost, grad = _outputs(out, I0b)
     else:
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b)

@@ -230,3 +230,20 @@ def test_arrays_must_match_the_image_shape(meta):
                 torch.ones(3, 5, 7), torch.empty(2, 5, 7, device="meta")):
         with pytest.raises(ValueError):
             meta._like(bad, ref, "J")
+
+
+def test_caller_outputs_are_checked(meta):
+    """cost_and_grad(out=(cost, grad)): the kernels write cost [B, 3] (float64) and grad
+    (float32, the images' shape) whole, so anything else raises before the call."""
+    import torch
+    ref = torch.zeros(2, 5, 7)
+    cost, grad = torch.zeros(2, 3, dtype=torch.float64), torch.zeros(2, 5, 7)
+    assert meta._outputs((cost, grad), ref)[1] is grad
+    assert meta._outputs((cost, None), ref)[1] is None
+    bad = [(torch.zeros(2, 3), grad), (torch.zeros(3, 3, dtype=torch.float64), grad),
+           (torch.zeros(3, 2, dtype=torch.float64).t(), grad),
+           (cost, torch.zeros(2, 5, 7, dtype=torch.float64)), (cost, torch.zeros(2, 7, 5)),
+           (cost, torch.zeros(2, 7, 5).transpose(1, 2)), (cost, torch.zeros(2, 5, 6))]
+    for c, g in bad:
+        with pytest.raises(ValueError):
+            meta._outputs((c, g), ref)
