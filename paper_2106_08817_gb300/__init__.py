@@ -486,6 +486,8 @@ def lbfgs_direction(g: torch.Tensor, S: Sequence[torch.Tensor], Y: Sequence[torc
     every instance (meta_lbfgs_direction)."""
     gb, nd, dims, sq = _shape(_as_batch(g, "g")[0], ndim)
     B, dev = gb.shape[0], gb.device
+    if len(S) != len(Y):
+        raise ValueError("%d s vectors but %d y vectors" % (len(S), len(Y)))
     m = int(m or max(1, len(S)))
     Sb = [_like(_as_batch(x, "s")[0], gb, "s") for x in S]
     Yb = [_like(_as_batch(x, "y")[0], gb, "y") for x in Y]

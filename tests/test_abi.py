@@ -247,3 +247,17 @@ def test_caller_outputs_are_checked(meta):
     for c, g in bad:
         with pytest.raises(ValueError):
             meta._outputs((c, g), ref)
+
+
+def test_lbfgs_pairs_must_come_in_pairs(meta):
+    """lbfgs_direction with unequal numbers of s and y vectors raises before the C call
+    (which would otherwise read past the shorter pointer array)."""
+    import torch
+    real = meta._as_batch
+    meta._as_batch = lambda x, name: (x.contiguous(), False)  # CPU tensors for the check
+    try:
+        g = torch.zeros(1, 4, 5)
+        with pytest.raises(ValueError):
+            meta.lbfgs_direction(g, [g, g], [g])
+    finally:
+        meta._as_batch = real
