@@ -8,7 +8,7 @@ takes a gradient-descent update and L2 is flushed (both outside the timed
 events).  voxel-steps = batch x voxels x T per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload ellipses16x256|disk64|head128|mri160|mix64]
+                    [--workload mri160|ellipses16x256|disk64|head128|mix64]
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 the host cores instead (the deliberately slow reference arm).
@@ -61,6 +61,20 @@ def own_bytes_per_voxel_step(d: int, T: int, k: int) -> float:
     return fwd + adj + rec
 
 
+# Algorithmic bytes per voxel of one launch of each kernel class in the fixed model
+# of the method's data movement (the same model as model_bytes_per_voxel_step):
+# the fused gradient + first blur pass 8 + 4d, a blur pass 8d, the advect
+# 16 + 4d, the gather-form transpose 24 + 8d (records and states in, v^ and the
+# two transported adjoints out), the transpose of m = p grad I 24 + 4d.  The
+# roofline of the bench line is taken on these; bytes_per_voxel below is this
+# implementation's own count (its records carry more fields than the model).
+def model_bytes_per_voxel(kclass: str, d: int) -> int:
+    m = {"xpass_m": 8 + 4 * d, "strided_fwd": 8 * d, "advect": 16 + 4 * d,
+         "adj_gather": 24 + 8 * d, "xpass_adj": 8 * d, "strided_adj": 8 * d,
+         "adj_gradp": 24 + 4 * d}
+    return m[kclass] if kclass in m else bytes_per_voxel(kclass, d)
+
+
 def bytes_per_voxel(kclass: str, d: int) -> int:
     return {
         "pack": 16,
@@ -91,6 +105,8 @@ def workload(name: str, rank: int = 0):
         return phantoms.ellipse_pairs(seed=1002 + off)
     if name == "ellipses2x32":  # tiny case for the multi-rank CPU test
         return phantoms.ellipse_pairs(batch=2, size=(32, 32), T=3, sigma=1.5, seed=1002 + off)
+    if name == "head16":  # tiny single volume for the host tests
+        return phantoms.head_pair_3d(dims=(16, 16, 16), T=3, sigma=1.5, seed=1003 + off)
     if name == "disk64":
         return phantoms.disk_pair_64(seed=1001 + off, random_p0=False)
     if name == "head128":
@@ -251,6 +267,22 @@ def ncu_traffic(kclass: str, ndim: int, launch_voxels: int):
 
 
 # ------------------------------------------------------------------ CPU oracle
+def downsampled_copy(w):
+    """The 2x block-averaged copy of a single-volume workload: half the extent per
+    axis, half the kernel width, the same T, mu, rho, lambda and block-averaged p0."""
+    import phantoms
+    return phantoms.Workload(w.name + "_2x", w.ndim, tuple(n // 2 for n in w.dims), w.T,
+                             w.sigma / 2.0, phantoms.block_average(w.I0),
+                             phantoms.block_average(w.J), phantoms.block_average(w.p0),
+                             w.mu.copy(), w.rho.copy(), w.lam.copy())
+
+
+def single_volume(w) -> bool:
+    """A workload of one 3-D volume whose extents halve evenly (its oracle baseline
+    runs the full volume once and the 2x block-averaged copy)."""
+    return w.batch == 1 and w.ndim == 3 and all(n % 2 == 0 for n in w.dims)
+
+
 def oracle_sample(w, target_s: float, max_instances: int = None, threads: int = None):
     """Time oracle cost_and_grad on instances 0, 1, ... until ~target_s seconds, on
     `threads` threads (default: the current count, every host core unless changed);
@@ -275,15 +307,54 @@ def oracle_sample(w, target_s: float, max_instances: int = None, threads: int = 
     return done, el, n_thr
 
 
-def cpu_baseline_entry(w, seconds: float) -> dict:
-    """The bench line's cpu_baseline: the FP64 oracle on every host core over about
-    `seconds` (the value), plus one thread over a third of that when one instance fits
-    in it (estimated from the all-core rate), else single_thread is null."""
+def cpu_baseline_entry(w, seconds: float, gpu_cost_and_grad=None) -> dict:
+    """The bench line's cpu_baseline: the FP64 oracle on every host core.
+
+    A single volume (the 160x192x160 MRI workload): one cost_and_grad of the full
+    volume (the value), then one of its 2x block-averaged copy, where the library's
+    own result on the same copy (gpu_cost_and_grad, if given) is compared with the
+    oracle's (the error of the registration's cost and gradient against FP64).
+    A batch: instances 0, 1, ... over about `seconds`.  Either way one thread too,
+    over a third of that, when one instance (of the copy, for a volume) fits in it
+    (estimated from the all-core rate), else single_thread is null."""
+    import oracle
     N, T, B = w.voxels, w.T, w.batch
+    shape = "x".join(map(str, w.dims))
+    if single_volume(w):
+        n_inst, el, cores = oracle_sample(w, 0.0, max_instances=1)
+        out = {"value": N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one FP64 cost_and_grad of the full %s volume (T=%d forward + "
+                         "adjoint steps), %.1f s" % (shape, T, el),
+               "single_thread": None}
+        h = downsampled_copy(w)
+        Nh = h.voxels
+        t0 = time.perf_counter()
+        c_or, g_or = oracle.cost_and_grad(h.I0[0], h.J[0], h.p0[0], h.T, h.sigma,
+                                          float(h.mu[0]), float(h.rho[0]), float(h.lam[0]))
+        elh = time.perf_counter() - t0
+        ds = {"value": Nh * T / elh, "unit": UNIT, "cores": cores,
+              "sample": "one FP64 cost_and_grad of the 2x block-averaged copy (%s, sigma=%g, "
+                        "T=%d), %.1f s" % ("x".join(map(str, h.dims)), h.sigma, T, elh)}
+        if gpu_cost_and_grad is not None:
+            c_gpu, g_gpu = gpu_cost_and_grad(h)
+            ds["vs_gpu"] = {
+                "cost_rel_err": [float(abs(a - b) / max(abs(b), 1e-30))
+                                 for a, b in zip(c_gpu, c_or)],
+                "grad_relL2": float(np.linalg.norm(g_gpu - g_or) / max(np.linalg.norm(g_or),
+                                                                       1e-300)),
+                "what": "the library's FP32 cost terms and dL/dp0 on the copy (same inputs, "
+                        "the p0 the timed steps reached) against the FP64 oracle's"}
+        out["downsampled_2x"] = ds
+        budget = seconds / 3.0
+        if elh * cores <= budget:
+            n1, el1, _ = oracle_sample(h, budget, max_instances=1, threads=1)
+            out["single_thread"] = {"value": n1 * Nh * T / el1, "unit": UNIT, "cores": 1,
+                                    "sample": "the 2x copy once, %.1f s" % el1}
+        return out
     n_inst, el, cores = oracle_sample(w, seconds)
     out = {"value": n_inst * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "%d of %d instances, one FP64 cost_and_grad each (%s, T=%d), %.1f s"
-                     % (n_inst, B, "x".join(map(str, w.dims)), T, el),
+                     % (n_inst, B, shape, T, el),
            "single_thread": None}
     budget = seconds / 3.0
     if el / n_inst * cores <= budget:
@@ -294,7 +365,10 @@ def cpu_baseline_entry(w, seconds: float) -> dict:
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    """The reference arm: the FP64 oracle on the host cores, same metric and workload.
+    Each step is one instance's cost_and_grad; for a single volume, one cost_and_grad
+    of its 2x block-averaged copy (a bounded sample: the full volume takes tens of
+    seconds per call on the host), with the copy's voxel-steps counted."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -302,21 +376,27 @@ def run_reference(args):
     import oracle
     oracle.build()
     oracle.set_threads(oracle.max_threads())
-    vs = w.voxels * w.T
+    ws = downsampled_copy(w) if single_volume(w) else w
+    vs = ws.voxels * ws.T
     for i in range(args.warmup):
-        b = i % w.batch
-        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
-                             float(w.rho[b]), float(w.lam[b]))
+        b = i % ws.batch
+        oracle.cost_and_grad(ws.I0[b], ws.J[b], ws.p0[b], ws.T, ws.sigma, float(ws.mu[b]),
+                             float(ws.rho[b]), float(ws.lam[b]))
     t0 = time.perf_counter()
     for i in range(args.steps):
-        b = i % w.batch
-        oracle.cost_and_grad(w.I0[b], w.J[b], w.p0[b], w.T, w.sigma, float(w.mu[b]),
-                             float(w.rho[b]), float(w.lam[b]))
+        b = i % ws.batch
+        oracle.cost_and_grad(ws.I0[b], ws.J[b], ws.p0[b], ws.T, ws.sigma, float(ws.mu[b]),
+                             float(ws.rho[b]), float(ws.lam[b]))
     el = time.perf_counter() - t0
     value = vs * args.steps / el
     cores = oracle.max_threads()
-    sample = ("one instance's cost_and_grad (%s, T=%d fwd + adjoint, FP64) per step, "
-              "cycling over the %d instances" % ("x".join(map(str, w.dims)), w.T, w.batch))
+    if ws is w:
+        sample = ("one instance's cost_and_grad (%s, T=%d fwd + adjoint, FP64) per step, "
+                  "cycling over the %d instances" % ("x".join(map(str, w.dims)), w.T, w.batch))
+    else:
+        sample = ("one cost_and_grad (T=%d fwd + adjoint, FP64) per step of the workload's 2x "
+                  "block-averaged copy, %s with sigma=%g, in place of the full %s volume"
+                  % (w.T, "x".join(map(str, ws.dims)), ws.sigma, "x".join(map(str, w.dims))))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -590,7 +670,8 @@ def run_ours(args):
     value = job_value(vs_per_step, world, ms)
     first_cost = cost.clone()
 
-    # ---- kernel timing: the same steps again, every library launch bracketed by events
+    # ---- kernel timing: the same steps again, eager, every library launch bracketed
+    # by CUDA events on the launching stream (meta_timer_*)
     meta.timer_start(1 << 16)
     for k in range(args.steps):
         flush.zero_()
@@ -602,15 +683,20 @@ def run_ours(args):
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_scopes, _ = kt[dom]
     avg_ms = dom_ms / max(dom_scopes, 1)
-    per_launch_bytes = bytes_per_voxel(dom, d) * B * N
+    per_launch_bytes = model_bytes_per_voxel(dom, d) * B * N
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peak, peak_src = peaks()
     traffic = ncu_traffic(dom, d, B * N)
+    kernels_ms_per_step = sum(v[0] for v in kt.values()) / args.steps
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[2],
                    "share": round(v[0] / max(sum(x[0] for x in kt.values()), 1e-9), 4),
                    "avg_us": round(v[0] / max(v[1], 1) * 1e3, 3),
-                   "GBps_algorithmic": round(bytes_per_voxel(k, d) * B * N / (v[0] / v[1] * 1e-3)
-                                             / 1e9, 1) if v[1] else None}
+                   "model_bytes_per_voxel": model_bytes_per_voxel(k, d),
+                   "GBps_model": round(model_bytes_per_voxel(k, d) * B * N
+                                       / (v[0] / v[1] * 1e-3) / 1e9, 1) if v[1] else None,
+                   "own_bytes_per_voxel": bytes_per_voxel(k, d),
+                   "GBps_own": round(bytes_per_voxel(k, d) * B * N / (v[0] / v[1] * 1e-3)
+                                     / 1e9, 1) if v[1] else None}
                for k, v in kt.items() if v[1]}
 
     # ---- deformation of the grid: forward shooting with phi_T and det D phi_T
@@ -680,12 +766,30 @@ def run_ours(args):
                      "what": "baseline/torch_scheme.py: grid_sample + grouped conv + "
                              "torch.autograd, FP32, eager"}
 
+    # ---- the other configurations' own lines, as side keys (same run, same GPU)
+    side = None
+    if not args.no_side and world == 1:
+        side = {}
+        for name in SIDE_WORKLOADS.get(args.workload, ()):
+            side[name] = (measure_mix(meta, args, dev, flush, stream) if name == "mix64"
+                          else measure_side(meta, name, args, dev, flush, stream))
+
     fault = ws.status()
     out = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            cpu = cpu_baseline_entry(w, args.cpu_seconds)
+            import dataclasses
+
+            def gpu_cg(h):
+                tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                c, g = meta.cost_and_grad(tt(h.I0), tt(h.J), tt(h.p0), h.T, h.sigma, tt(h.mu),
+                                          tt(h.rho), tt(h.lam), ckpt=args.ckpt)
+                return c[0].cpu().numpy(), g[0].cpu().numpy()
+
+            # the oracle on the momentum the timed steps reached
+            wq = dataclasses.replace(w, p0=p0.cpu().numpy())
+            cpu = cpu_baseline_entry(wq, args.cpu_seconds, gpu_cg)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -708,7 +812,17 @@ def run_ours(args):
                          if peak_src == "measured" else "fallback 6800 GB/s",
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_us": avg_ms * 1e3},
+                         "model_bytes_per_voxel": model_bytes_per_voxel(dom, d),
+                         "avg_launch_us": avg_ms * 1e3,
+                         "timing": "CUDA events around each launch of the class on the "
+                                   "launching stream, in eager calls of the same steps",
+                         "own": {"bytes_per_voxel": bytes_per_voxel(dom, d),
+                                 "achieved": bytes_per_voxel(dom, d) * B * N
+                                 / (avg_ms * 1e-3) / 1e9,
+                                 "frac": bytes_per_voxel(dom, d) * B * N
+                                 / (avg_ms * 1e-3) / 1e9 / peak}},
+            "kernels_ms_per_step": kernels_ms_per_step,
+            "kernels_over_step": kernels_ms_per_step / ms,
             "cpu_baseline": cpu,
             "e2e": {"value": job_value(vs_per_step, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -719,6 +833,7 @@ def run_ours(args):
             "det_update": det_update,
             "schemes": schemes,
             "lbfgs": lbfgs,
+            "side_workloads": side,
             "kernels": kernels,
             "device_fault_bits": fault,
             "cost_last": [float(x) for x in first_cost.sum(dim=1).cpu()[:4]],
@@ -729,24 +844,64 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_mix(args):
+# configurations measured beside the headline workload (their own keys in its line)
+SIDE_WORKLOADS = {"mri160": ("ellipses16x256", "mix64")}
+
+
+def measure_side(meta, name, args, dev, flush, stream, steps=20):
+    """One more single-shape workload timed the headline's way (autotuned tiles,
+    recorded plan, L2 flushed between steps, gradient descent on p0 between steps)."""
+    import torch
+    w = workload(name)
+    ck = WORKLOAD_CKPT.get(name, 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    I0, J, p0 = t(w.I0), t(w.J), t(w.p0)
+    mu, rho, lam = t(w.mu), t(w.rho), t(w.lam)
+    tiles = (meta.tuning(w.dims, w.batch, w.sigma) if args.no_autotune else
+             meta.autotune(I0, J, p0, w.T, w.sigma, mu, rho, lam, ckpt=ck))
+    plan = meta.CostAndGradPlan(I0, J, p0, w.T, w.sigma, mu, rho, lam, ckpt=ck)
+
+    def gd():
+        g = plan.grad
+        gmax = g.abs().amax(dim=tuple(range(1, w.ndim + 1)), keepdim=True).clamp_min(1e-30)
+        plan.p0.sub_(0.02 * g / gmax)
+
+    for _ in range(3):
+        plan.launch()
+        gd()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        plan.launch()
+        b.record(stream)
+        gd()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    vs = w.batch * w.voxels * w.T
+    peak, _ = peaks()
+    value = vs / (ms * 1e-3)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "config": dict(workload_config(w, name), ckpt_stride=ck, tiles=tiles),
+            "path_roofline": {"model_bytes_per_voxel_step": model_bytes_per_voxel_step(w.ndim),
+                              "model_frac": value * model_bytes_per_voxel_step(w.ndim) / 1e9
+                              / peak, "peak_GBps": peak},
+            "device_fault_bits": plan.ws.status()}
+
+
+def measure_mix(meta, args, dev, flush, stream, steps=20):
     """The 64 uneven 2-D/3-D pairs of phantoms.mixed_pairs in one CUDA graph with
     parallel branches (meta_plan_create_group); value = sum of voxel-steps / time."""
     import torch
     import phantoms
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2106_08817_gb300 as meta
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
     ws = phantoms.mixed_pairs(seed=1004 + 7919 * int(os.environ.get("RANK", "0")))
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     probs = [dict(I0=t(w.I0), J=t(w.J), p0=t(w.p0), T=w.T, sigma=w.sigma, mu=t(w.mu),
                   rho=t(w.rho), lam=t(w.lam)) for w in ws]
     plan = meta.GroupPlan(probs, streams=args.streams)
     vs = plan.voxel_steps()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
 
     def gd():
         for it in plan.items:
@@ -754,21 +909,20 @@ def run_mix(args):
             gmax = g.abs().amax(dim=tuple(range(1, g.dim())), keepdim=True).clamp_min(1e-30)
             it["p0"].sub_(0.02 * g / gmax)
 
-    for _ in range(args.warmup):
+    for _ in range(3):
         plan.launch()
         gd()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    with ClockSampler(dev.index) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            plan.launch()
-            evs[k][1].record(stream)
-            gd()
-        torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+           for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        plan.launch()
+        evs[k][1].record(stream)
+        gd()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     # per-class times from eager calls of every member
     meta.timer_start(1 << 18)
     for it in plan.items:
@@ -777,27 +931,50 @@ def run_mix(args):
     torch.cuda.synchronize()
     kt = meta.timer_stop()
     dom = max(kt, key=lambda k: kt[k][0])
-    dom_bytes = sum(bytes_per_voxel(dom, len(it["dims"])) * it["B"] * int(np.prod(it["dims"])) *
-                    launches_per_call(dom, len(it["dims"]), it["T"]) for it in plan.items)
+    dom_bytes = sum(model_bytes_per_voxel(dom, len(it["dims"])) * it["B"]
+                    * int(np.prod(it["dims"])) * launches_per_call(dom, len(it["dims"]), it["T"])
+                    for it in plan.items)
     achieved = dom_bytes / (kt[dom][0] * 1e-3) / 1e9
     peak, peak_src = peaks()
-    fault = max(it["ws"].status() for it in plan.items)
-    print(json.dumps({
-        "metric": METRIC, "value": vs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    model_bytes = sum(model_bytes_per_voxel_step(len(it["dims"])) * it["B"]
+                      * int(np.prod(it["dims"])) * it["T"] for it in plan.items)
+    return {
+        "value": vs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
         "config": {"workload": "mix64", "pairs": len(ws),
                    "sizes": sorted(set("x".join(map(str, w.dims)) for w in ws)),
                    "voxel_steps_per_step": vs, "graph_branches": args.streams,
                    "step": "one graph launch of 64 cost_and_grad calls (parallel branches)",
                    "l2": "flushed (256 MiB write) between timed steps"},
+        "path_roofline": {"model_bytes_per_step": model_bytes,
+                          "model_frac": model_bytes / (ms * 1e-3) / 1e9 / peak,
+                          "peak_GBps": peak},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": peak_src},
-        "gpu_launches": int(sum(v[2] for v in kt.values()) * args.steps),
-        "clocks": clk.summary(), "device_fault_bits": fault,
-        "kernels": {k: {"ms_total": round(v[0], 3), "launches": v[2]} for k, v in kt.items() if v[1]},
-    }), flush=True)
+        "gpu_launches_per_step": int(sum(v[2] for v in kt.values())),
+        "device_fault_bits": max(it["ws"].status() for it in plan.items),
+        "kernels": {k: {"ms_total": round(v[0], 3), "launches": v[2]}
+                    for k, v in kt.items() if v[1]},
+    }
+
+
+def run_mix(args):
+    """The mixed batch as the headline workload (--workload mix64)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2106_08817_gb300 as meta
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with ClockSampler(dev.index) as clk:
+        r = measure_mix(meta, args, dev, flush, stream, steps=args.steps)
+    print(json.dumps(dict({
+        "metric": METRIC, "n_gpus": 1, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "gpu_launches": r["gpu_launches_per_step"] * args.steps, "clocks": clk.summary()},
+        **r)), flush=True)
 
 
 def main():
@@ -808,8 +985,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5, help="untimed steps before them")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours",
                     help="reference: the FP64 oracle on the host cores")
-    ap.add_argument("--workload", default="ellipses16x256",
-                    help="ellipses16x256, disk64, head128, mri160 or mix64")
+    ap.add_argument("--workload", default="mri160",
+                    help="mri160 (160x192x160 volume, the default), ellipses16x256, disk64, "
+                         "head128 or mix64")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the side workloads measured beside mri160 (the 16 x 256^2 "
+                         "batch and the 64 uneven pairs)")
     ap.add_argument("--no-torch", action="store_true",
                     help="skip torch.autograd through the PyTorch-ops scheme")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's cpu_baseline")

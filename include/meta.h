@@ -203,11 +203,31 @@ meta_status meta_plan_destroy(meta_plan* plan);
  * first call before any stream capture.  Every call uses the same array, which
  * keeps the previous call's contents (its status word is cleared at each call):
  * calls that overlap on the GPU -- from two streams or two threads -- race and
- * corrupt each other, so order them on one stream. */
+ * corrupt each other, so order them on one stream.  The images and outputs must
+ * live on the current device, whose array the call uses.  Faults detected on
+ * the device (a bounded wait that ran out) are latched in the array's status
+ * word, which meta_noalloc_status reads: check it after a call, before the next
+ * call clears it. */
 meta_status meta_cost_and_grad_noalloc(const meta_problem* prob, const float* I0, const float* J,
                                        const float* p0, const float* mu, const float* rho,
                                        const float* lambda, double* cost, float* grad,
                                        void* stream);
+
+/* meta_workspace_status for the array of meta_cost_and_grad_noalloc on the
+ * current device: the bits latched since the last call began (bit 0: a bounded
+ * wait ran out and the call's results are invalid, returned as
+ * META_ERR_TIMEOUT; bit 1, information only: an adjoint step transposed the
+ * interpolation by the atomic scatter).  Synchronises `stream`; clear != 0
+ * resets the word.  Allocates nothing.  (Deployment aid; the paper has no
+ * counterpart.) */
+meta_status meta_noalloc_status(int clear, void* stream, unsigned int* fault_bits);
+
+/* meta_selftest_timeout on the array of meta_cost_and_grad_noalloc on the
+ * current device: a bounded device wait that runs out after limit_ns (in
+ * [1 ms, 2 s]) and latches bit 0, which meta_noalloc_status then reports.
+ * Nothing faults; the next call clears the word.  (Test aid for the failure
+ * detection of callers that cannot allocate; the paper has no counterpart.) */
+meta_status meta_noalloc_selftest_timeout(unsigned long long limit_ns, void* stream);
 
 /* Tile shapes of the kernels for one problem shape (ndim, dims, batch,
  * sigma): planes per CTA of the 3-D kernels that march along z (adjoint

@@ -25,7 +25,8 @@ import torch
 __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoot_adjoint",
            "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
            "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES",
-           "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize", "clear_workspaces"]
+           "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize", "clear_workspaces",
+           "cost_and_grad_noalloc", "noalloc_status", "noalloc_selftest_timeout"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
@@ -90,6 +91,10 @@ def _load():
             getattr(lib, f).restype = ctypes.c_int
         lib.meta_cost_and_grad_noalloc.argtypes = [P, F, F, F, F, F, F, D, F, V]
         lib.meta_cost_and_grad_noalloc.restype = ctypes.c_int
+        lib.meta_noalloc_status.argtypes = [ctypes.c_int, V, ctypes.POINTER(ctypes.c_uint)]
+        lib.meta_noalloc_status.restype = ctypes.c_int
+        lib.meta_noalloc_selftest_timeout.argtypes = [ctypes.c_ulonglong, V]
+        lib.meta_noalloc_selftest_timeout.restype = ctypes.c_int
         lib.meta_workspace_status.argtypes = [V, S, ctypes.c_int, V,
                                               ctypes.POINTER(ctypes.c_uint)]
         lib.meta_status_string.argtypes = [ctypes.c_int]
@@ -641,11 +646,15 @@ NOALLOC_MAX_BYTES = 64 << 20
 def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int,
                           sigma: float, mu, rho=1.0, lam=1e-3, ndim: Optional[int] = None,
                           out: Optional[Tuple[torch.Tensor, torch.Tensor]] = None, ckpt: int = 0,
-                          p_update=0, scheme: str = "sl") -> Tuple[torch.Tensor, torch.Tensor]:
+                          p_update=0, scheme: str = "sl", check_status: bool = False
+                          ) -> Tuple[torch.Tensor, torch.Tensor]:
     """cost_and_grad on the library's fixed 64 MiB device scratch: no workspace
     argument.  For callers that cannot allocate device memory; pass `out` (and
     device tensors for mu, rho, lam) so that this call allocates nothing either.
-    Calls share the scratch: order them on one stream."""
+    Calls share the scratch: order them on one stream.  The call runs with the
+    images' device current (the library picks that device's scratch).
+    check_status: wait for the call and raise MetaError (status 5) if a device-side
+    wait ran out; otherwise read noalloc_status() before the next call."""
     I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
     Jb = _like(_as_batch(J, "J")[0], I0b, "J")
     p0b = _like(_as_batch(p0, "p0")[0], I0b, "p0")
@@ -657,14 +666,43 @@ def cost_and_grad_noalloc(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T
         cost = torch.empty((B, 3), dtype=torch.float64, device=dev)
         grad = torch.empty_like(I0b)
     pr = _problem(nd, dims, B, T, sigma, ckpt, p_update, scheme)
-    rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
-                                            _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
-                                            _p(grad), _stream(dev))
-    if rc:
-        raise MetaError(rc, "meta_cost_and_grad_noalloc")
+    with torch.cuda.device(dev):
+        rc = _load().meta_cost_and_grad_noalloc(ctypes.byref(pr), _p(I0b), _p(Jb), _p(p0b),
+                                                _p(mu_t), _p(rho_t), _p(lam_t), _p(cost),
+                                                _p(grad), _stream(dev))
+        if rc:
+            raise MetaError(rc, "meta_cost_and_grad_noalloc")
+        if check_status and noalloc_status(device=dev) & 1:
+            raise MetaError(5, "meta_cost_and_grad_noalloc")
     if sq and out is None:
         grad = grad[0]
     return cost, grad
+
+
+def noalloc_status(clear: bool = False, device=None) -> int:
+    """Device fault bits of the no-allocation scratch of `device` (default: the current
+    one) latched since the last cost_and_grad_noalloc began (meta_noalloc_status;
+    synchronises the stream).  Bit 0: a bounded device wait ran out (that call's results
+    are invalid); bit 1: an adjoint step used the atomic scatter (order not fixed)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    bits = ctypes.c_uint(0)
+    with torch.cuda.device(dev):
+        rc = _load().meta_noalloc_status(int(clear), _stream(dev), ctypes.byref(bits))
+    if rc not in (0, 5):
+        raise MetaError(rc, "meta_noalloc_status")
+    return int(bits.value)
+
+
+def noalloc_selftest_timeout(limit_ns: int = 50_000_000, device=None) -> None:
+    """Enqueues a bounded device wait that runs out on the no-allocation scratch
+    (meta_noalloc_selftest_timeout): the timeout bit then shows in noalloc_status()."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    with torch.cuda.device(dev):
+        rc = _load().meta_noalloc_selftest_timeout(int(limit_ns), _stream(dev))
+    if rc:
+        raise MetaError(rc, "meta_noalloc_selftest_timeout")
 
 
 class Shoot(torch.autograd.Function):

@@ -88,3 +88,61 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
     assert oracle.max_threads() == d["cores"]  # the thread count is restored
     assert bench.cpu_baseline_entry(w, 1e-9)["single_thread"] is None
+
+
+def test_model_bytes_per_kernel_class_add_up_to_the_model():
+    """The roofline's per-class bytes are the parts of the fixed model: forward
+    F = (8 + 4d) + (d - 1) 8d + (16 + 4d), adjoint (24 + 8d) + 8d + (d - 1) 8d + (24 + 4d),
+    and the path is 2F + 4d + A."""
+    for d in (2, 3):
+        m = lambda k: bench.model_bytes_per_voxel(k, d)
+        F = m("xpass_m") + (d - 1) * m("strided_fwd") + m("advect")
+        A = m("adj_gather") + m("xpass_adj") + (d - 1) * m("strided_adj") + m("adj_gradp")
+        assert F == 24 + 8 * d * d and A == 48 + 12 * d + 8 * d * d
+        assert 2 * F + 4 * d + A == bench.model_bytes_per_voxel_step(d)
+    assert bench.model_bytes_per_voxel("adj_gather", 3) == 48
+    # classes outside the model fall back to the implementation's own count
+    assert bench.model_bytes_per_voxel("cost", 3) == bench.bytes_per_voxel("cost", 3)
+
+
+def test_downsampled_copy_halves_extent_and_kernel_width():
+    w = bench.workload("head16")
+    h = bench.downsampled_copy(w)
+    assert bench.single_volume(w) and not bench.single_volume(bench.workload("disk64"))
+    assert h.dims == (8, 8, 8) and h.sigma == w.sigma / 2 and h.T == w.T
+    assert h.I0.shape == (1, 8, 8, 8)
+    assert abs(float(h.I0.mean()) - float(w.I0.mean())) < 1e-6  # block means keep the mean
+
+
+def test_cpu_baseline_of_a_single_volume_runs_it_whole_and_its_2x_copy():
+    """A single volume: the oracle once on the full volume (the value), once on its 2x
+    block-averaged copy, and the library's result on the copy compared with the
+    oracle's (here a stand-in that returns the oracle's own result: zero error)."""
+    import oracle
+    w = bench.workload("head16")
+
+    def same(h):
+        return oracle.cost_and_grad(h.I0[0], h.J[0], h.p0[0], h.T, h.sigma, float(h.mu[0]),
+                                    float(h.rho[0]), float(h.lam[0]))
+
+    d = bench.cpu_baseline_entry(w, 3.0, same)
+    assert d["kind"] == "oracle" and d["value"] > 0 and d["cores"] == oracle.max_threads()
+    assert "16x16x16" in d["sample"]
+    ds = d["downsampled_2x"]
+    assert ds["value"] > 0 and "8x8x8" in ds["sample"]
+    assert ds["vs_gpu"]["grad_relL2"] == 0.0 and max(ds["vs_gpu"]["cost_rel_err"]) == 0.0
+    assert d["single_thread"]["cores"] == 1
+
+
+def test_reference_arm_samples_a_single_volume_by_its_2x_copy():
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "head16", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    d = json.loads(lines[0])
+    assert d["config"]["workload"] == "head16" and d["config"]["dims"] == [16, 16, 16]
+    assert "2x block-averaged copy" in d["cpu_baseline"]["sample"]
+    assert d["ms_per_step"] > 0 and d["value"] > 0
