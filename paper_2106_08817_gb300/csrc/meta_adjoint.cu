@@ -581,35 +581,46 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
     }
 }
 
-// 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 8 column of nodes over
-// planes [zs, zs + zc) and marches along z.
-//   R = 1: plane p of the records (cell, f_z, f_y, f_x, I^', p~^, div^) and of
-//     I_t, p_t, grown by one voxel in x and y, is staged by cp.async into a
-//     ring of 4 plane slots (plane p + 1 loads while plane p is used).  Its
-//     sources are packed once into the float4 (g_z, g_y, g_x, I^') and p~^,
+// 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 16 column of nodes
+// over planes [zs, zs + zc) and marches along z; each thread owns the two
+// adjacent nodes (x, 2 ty) and (x, 2 ty + 1) of the column.
+//   R = 1: plane p of the records and of I_t, p_t over the column grown by one
+//     voxel in x and y is staged by TMA (three bulk tensor copies issued by
+//     one thread, completion on an mbarrier per plane parity, plane p + 1 in
+//     flight while plane p is used) into two rings: the record fields used
+//     only when the plane is packed and when its own nodes complete (cell,
+//     f_z, f_y, f_x, I^', p~^; 3 slots) and the fields read from the planes
+//     around a completing node (div^, I_t, p_t; 4 slots).  The sources of the
+//     plane are packed once into the float4 (g_z, g_y, g_x, I^') and p~^,
 //     where per axis g = f - 1 if the foot cell lies below the source (cell
 //     offset -1) and g = f otherwise.  The weight with which a source at
 //     offset e from a node passes its value along one axis is then max(g, 0)
 //     for e = -1, 1 - |g| for e = 0, max(-g, 0) for e = +1 (the bilinear
 //     weights f and 1 - f; 1 - |g| = f when the cell lies below holds up to
-//     one rounding).  Each thread reads the 9 sources of plane p around its
-//     column once and adds them to its running sums of nodes p+1, p, p-1
-//     (branch-free; zero weights add exact zeros); node p-1 is then complete
-//     and takes y^, D^T div^ from the staged planes p-2 .. p.  Every staged
-//     value is read from L2 about 1.6 times.
+//     one rounding).  Each thread reads the 12 sources of plane p around its
+//     two nodes once (rows 2 ty - 1 .. 2 ty + 2: the middle two serve both
+//     nodes) and adds them, in the order (row, column) of each node's 3 x 3
+//     window, to the running sums of its nodes at planes p+1, p, p-1
+//     (branch-free; zero weights add exact zeros); the nodes at p-1 are then
+//     complete and take y^, D^T div^ from the staged planes p-2 .. p.
 //   R > 1: transport_node for each node of the column.
-constexpr int kMW = 40, kMHY = 10, kMPL = kMW * kMHY;   // staged plane window (x, y)
-constexpr int kMRX = 34, kMRY = 10, kMPR = kMRX * kMRY;  // source region of a plane
-constexpr int kMF = 9;                                   // staged fields per plane
-constexpr int kMChunks = kMF * kMHY * (kMW / 4);         // 16-byte copies per plane
-constexpr int kMPer = (kMChunks + kPX * kPY - 1) / (kPX * kPY);
-constexpr size_t kMarchSmem = (size_t)(4 * kMF * kMPL + 5 * kMPR) * sizeof(float);
+constexpr int kMW = 40, kMHY = 18, kMPL = kMW * kMHY;    // staged window (x, y) of a plane
+constexpr int kMRX = 34, kMRY = 18, kMPR = kMRX * kMRY;  // source region of a plane
+constexpr int kMFA = 6;                                  // ring A: cell f_z f_y f_x I^' p~^
+constexpr int kMSA = kMFA * kMPL;                        // ring A slot (floats)
+constexpr int kMBI = 736, kMBP = kMBI + kMPL;            // ring B: div^ at 0, I_t, p_t
+constexpr int kMSB = kMBP + kMPL;                        // ring B slot (floats, 128-byte multiple)
+constexpr int kMSlotsA = 3, kMSlotsB = 4;
+constexpr size_t kMarchSmem =
+    128 + (size_t)(kMSlotsA * kMSA + kMSlotsB * kMSB + 5 * kMPR) * sizeof(float);
+constexpr uint32_t kMBytesA = kMFA * kMPL * 4, kMBytesB = 3 * kMPL * 4;
+static_assert((kMSA * 4) % 128 == 0 && (kMSB * 4) % 128 == 0 && (kMBI * 4) % 128 == 0,
+              "TMA destinations start on 128-byte boundaries");
 
-
-// Packs the sources of one staged plane at z (zero outside the domain).
+// Packs the sources of one staged plane at z (zero outside the domain) from
+// its ring-A slot.
 __device__ __forceinline__ void march_pack(const float* raw, float4* q, float* pp, const Geom& g,
-                                           int x0, int y0, int z) {
-    const int tid = threadIdx.y * kPX + threadIdx.x;
+                                           int x0, int y0, int z, int tid) {
     const bool zin = z >= 0 && z < g.nz;
     for (int i = tid; i < kMPR; i += kPX * kPY) {
         const int ry = i / kMRX, rx = i - ry * kMRX;
@@ -631,153 +642,211 @@ __device__ __forceinline__ void march_pack(const float* raw, float4* q, float* p
     }
 }
 
-__global__ void __launch_bounds__(kPX * kPY, 3)
-k_adj_transport3d(Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states,
-                  const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
-                  float* vh, float* Ihp, float* php, unsigned int* fault) {
+// Weight of a source at offset E from a node along one axis, from its packed g.
+template <int E>
+__device__ __forceinline__ float gwe(float g) {
+    if constexpr (E < 0) return gw<-1>(g);
+    else if constexpr (E > 0) return gw<1>(g);
+    else return gw<0>(g);
+}
+
+// Adds the packed source (qv, pv) at offset (DY, DX) in y and x of a node to
+// its running sums at the planes below, at and above the source's plane,
+// with the z weights zm, z0, zp of the source.
+template <int DY, int DX>
+__device__ __forceinline__ void gather_add(const float4& qv, float pv, float wx, float zm, float z0,
+                                           float zp, float2& am, float2& a0, float2& ap) {
+    const float wyx = gwe<DY>(qv.y) * wx;
+    const float2 tv = fmul2(make_float2(wyx, wyx), make_float2(qv.w, pv));
+    am = ffma2(make_float2(zm, zm), tv, am);
+    a0 = ffma2(make_float2(z0, z0), tv, a0);
+    ap = ffma2(make_float2(zp, zp), tv, ap);
+}
+
+// y^ and D^T div^ of the completed node (z, y, x) (window index mw in its
+// plane), and its outputs.
+__device__ __forceinline__ void transport_complete(const Geom& g, float dt, int b, int z, int y,
+                                                   int x, int mw, const float* A_z,
+                                                   const float* B_zm, const float* B_z,
+                                                   const float* B_zp, const float* B_lo,
+                                                   const float* B_hi, float2 acc, float* vh,
+                                                   float* Ihp, float* php) {
+    const long long o = gidx(g, z, y, x);
+    Ihp[(long long)b * g.inst + o] = acc.x;
+    php[(long long)b * g.inst + o] = acc.y;
+    const int cell = __float_as_int(A_z[mw]);
+    const float fz = A_z[kMPL + mw], fy = A_z[2 * kMPL + mw], fx = A_z[3 * kMPL + mw];
+    const int ci = mw + cell_off(cell, 1) * kMW + cell_off(cell, 2);
+    const bool inz = (cell >> 24) & 1, iny = (cell >> 25) & 1, inx = (cell >> 26) & 1;
+    float Iv, pv, dI[3], dP[3];
+    trilin_grad_pq(B_lo + kMBI + ci, B_hi + kMBI + ci, kMW, fz, fy, fx, inz, iny, inx, &Iv, dI);
+    trilin_grad_pq(B_lo + kMBP + ci, B_hi + kMBP + ci, kMW, fz, fy, fx, inz, iny, inx, &pv, dP);
+    const float Ihv = A_z[4 * kMPL + mw], pthv = A_z[5 * kMPL + mw];
+    float dT[3];
+    {  // (D^T div^) along z: the neighbouring planes' div^
+        float r = 0.f;
+        if (z >= 1) r += 0.5f * B_zm[mw];
+        if (z == g.nz - 1) r += 0.5f * B_z[mw];
+        if (z <= g.nz - 2) r -= 0.5f * B_zp[mw];
+        if (z == 0) r -= 0.5f * B_z[mw];
+        dT[0] = r;
+    }
+    const int c2[2] = {y, x}, n2[2] = {g.ny, g.nx}, s2[2] = {kMW, 1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float r = 0.f;
+        if (c2[a] >= 1) r += 0.5f * B_z[mw - s2[a]];
+        if (c2[a] == n2[a] - 1) r += 0.5f * B_z[mw];
+        if (c2[a] <= n2[a] - 2) r -= 0.5f * B_z[mw + s2[a]];
+        if (c2[a] == 0) r -= 0.5f * B_z[mw];
+        dT[1 + a] = r;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        vh[((long long)a * g.B + b) * g.inst + o] = -dt * (dI[a] * Ihv + dP[a] * pthv) + dT[a];
+}
+
+__global__ void __launch_bounds__(kPX * kPY, 2)
+k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
+                  const __grid_constant__ CUtensorMap tmRecD,
+                  const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl,
+                  int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp,
+                  const float* __restrict__ rec, float* vh, float* Ihp, float* php,
+                  unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int b = blockIdx.z;
     const int nxc = (g.nx + 31) / 32;
     const int x0 = (blockIdx.x % nxc) * 32;
     const int zs = (blockIdx.x / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = blockIdx.y * 8;
+    const int y0 = blockIdx.y * 16;
     const int R = gather_radius(maxdisp, t, g.B, b);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kPX + tx;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool col_ok = x < g.nx && y < g.ny;
+    const int x = x0 + tx, ya = y0 + 2 * ty, yb = ya + 1;
+    const bool ok_a = x < g.nx && ya < g.ny, ok_b = x < g.nx && yb < g.ny;
     if (R != 1) {  // uniform over the CTA
-        if (!col_ok) return;
         Vox v;
         v.b = b;
         v.x = x;
-        v.y = y;
         for (int z = zs; z < ze; ++z) {
             v.z = z;
-            transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+            v.y = ya;
+            if (ok_a) transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+            v.y = yb;
+            if (ok_b) transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
         }
         return;
     }
-    const long long rsl = (long long)g.B * g.inst;
-    const float* rb = rec + (long long)b * g.inst;
-    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
-    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
-    float* raw = sm;                                              // [4][kMF][kMPL]
-    float4* Q = reinterpret_cast<float4*>(sm + 4 * kMF * kMPL);  // [kMPR]
-    float* PP = sm + 4 * kMF * kMPL + 4 * kMPR;                   // [kMPR]
-    // ring slot of plane p: (p - zs + 1) & 3
-    auto rslot = [&](int p) { return raw + ((p - zs + 1) & 3) * (kMF * kMPL); };
-    // this thread's 16-byte copies of every plane: source (plane 0), slot offset
-    const float* csrc[kMPer];
-    int cdst[kMPer];
-    bool cok[kMPer];
-#pragma unroll
-    for (int j = 0; j < kMPer; ++j) {
-        const int i = tid + j * kPX * kPY;
-        const int k = i / (kMHY * (kMW / 4)), r = i - k * (kMHY * (kMW / 4));
-        const int row = r / (kMW / 4), c = r - row * (kMW / 4);
-        const int yy = y0 - 1 + row, xx = x0 - 4 + 4 * c;
-        const float* base = (k < 7) ? rb + k * rsl : (k == 7 ? It : pt);
-        cok[j] = i < kMChunks && yy >= 0 && yy < g.ny && xx >= 0 && xx < g.P;
-        csrc[j] = cok[j] ? base + (long long)yy * g.P + xx : base;
-        cdst[j] = (i < kMChunks) ? k * kMPL + row * kMW + 4 * c : -1;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [2]: planes of even / odd index
+    float* ringA = reinterpret_cast<float*>(smem_raw + 128);
+    float* ringB = ringA + kMSlotsA * kMSA;
+    float4* Q = reinterpret_cast<float4*>(ringB + kMSlotsB * kMSB);  // [kMPR]
+    float* PP = reinterpret_cast<float*>(Q + kMPR);                  // [kMPR]
+    // plane p sits in slots (p - zs + 1) mod 3 of A and mod 4 of B
+    auto slotA = [&](int p) { return ringA + ((p - zs + 1) % kMSlotsA) * kMSA; };
+    auto slotB = [&](int p) { return ringB + ((p - zs + 1) & 3) * kMSB; };
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
     }
+    __syncthreads();
+    // one thread stages plane p: records 0..5 into A, div^ and (I_t, p_t) into
+    // B; planes outside the volume are never read, so no copy is made for them
     auto load_plane = [&](int p) {
-        float* dst = rslot(p);
-        const bool zin = p >= 0 && p < g.nz;
-        const long long zo = zin ? (long long)p * g.slab : 0;
-#pragma unroll
-        for (int j = 0; j < kMPer; ++j)
-            if (cdst[j] >= 0) cp_async16(dst + cdst[j], csrc[j] + (cok[j] && zin ? zo : 0),
-                                         cok[j] && zin);
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        uint64_t* br = &bar[(p - zs + 1) & 1];
+        if (p >= 0 && p < g.nz) {
+            mbar_arrive_expect_tx(br, kMBytesA + kMBytesB);
+            float* dB = slotB(p);
+            tma_load_5d(slotA(p), &tmRecA, br, x0 - 4, y0 - 1, p, b, 0);
+            tma_load_5d(dB, &tmRecD, br, x0 - 4, y0 - 1, p, b, Rec<3>::kD);
+            tma_load_5d(dB + kMBI, &tmSt, br, x0 - 4, y0 - 1, p, b, 2 * sl.st);
+        } else {
+            mbar_arrive(br);
+        }
     };
     const float dt = cf.dt;
-    const int mw = (ty + 1) * kMW + tx + 4;   // window index of the node in a plane
-    const int me = (ty + 1) * kMRX + tx + 1;  // region index of the node in a plane
-    // running sums (S^T I^', S^T p~^) at nodes p-1, p, p+1 (packed FMAs)
-    float2 am = make_float2(0.f, 0.f), a0 = am, ap = am;
-    load_plane(zs - 1);
+    const int mwa = (2 * ty + 1) * kMW + tx + 4;   // window index of node a in a plane
+    const int mea = (2 * ty + 1) * kMRX + tx + 1;  // region index of node a in a plane
+    // running sums (S^T I^', S^T p~^) of both nodes at planes p-1, p, p+1
+    float2 am_a = make_float2(0.f, 0.f), a0_a = am_a, ap_a = am_a;
+    float2 am_b = am_a, a0_b = am_a, ap_b = am_a;
+    if (tid == 0) load_plane(zs - 1);
     for (int p = zs - 1; p <= ze; ++p) {
-        __syncthreads();  // every read of the slot of plane p-3 and of Q / PP is done
-        if (p + 1 <= ze) load_plane(p + 1);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane p landed
-        __syncthreads();
-        march_pack(rslot(p), Q, PP, g, x0, y0, p);
-        __syncthreads();
-        if (!col_ok) continue;
-        // plane p is at dz = -1 from node p+1, 0 from node p, +1 from node p-1
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int i = me + dy * kMRX + dx;
-                const float4 qv = Q[i];
-                float wy, wx;
-                if (dy < 0) wy = gw<-1>(qv.y); else if (dy > 0) wy = gw<1>(qv.y); else wy = gw<0>(qv.y);
-                if (dx < 0) wx = gw<-1>(qv.z); else if (dx > 0) wx = gw<1>(qv.z); else wx = gw<0>(qv.z);
-                const float wyx = wy * wx;
-                const float2 tv = fmul2(make_float2(wyx, wyx), make_float2(qv.w, PP[i]));
-                const float wm = gw<1>(qv.x), w0 = gw<0>(qv.x), wp = gw<-1>(qv.x);
-                am = ffma2(make_float2(wm, wm), tv, am);
-                a0 = ffma2(make_float2(w0, w0), tv, a0);
-                ap = ffma2(make_float2(wp, wp), tv, ap);
-            }
+        const int j = p - zs + 1;  // planes staged so far
+        __syncthreads();  // every read of the slots plane p + 1 reuses, and of Q / PP, is done
+        if (tid == 0 && p + 1 <= ze) load_plane(p + 1);
+        bool landed = true;
+        if (tid < 32) landed = mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault);
+        if (__syncthreads_or(!landed)) {
+            // leave together, after the copy of plane p + 1 (if any) has landed
+            if (tid < 32 && p + 1 <= ze)
+                mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1, fault, 100000000ull);
+            __syncthreads();
+            return;
         }
+        march_pack(slotA(p), Q, PP, g, x0, y0, p, tid);
+        __syncthreads();
+        // plane p is at dz = -1 from nodes at p+1, 0 from p, +1 from p-1.  Sources
+        // r = 0..3 (rows 2 ty - 1 .. 2 ty + 2 of the column), columns dx = 0..2
+        // (x - 1 .. x + 1), each loaded and weighted along x and z once; each
+        // node adds its nine in its own order: rows dy = -1, 0, 1 outer, columns
+        // inner
+#define META_SRC(r, dx)                                                                   \
+        const float4 q##r##_##dx = Q[mea + (r - 1) * kMRX + (dx - 1)];                    \
+        const float p##r##_##dx = PP[mea + (r - 1) * kMRX + (dx - 1)];                    \
+        const float wx##r##_##dx = gwe<dx - 1>(q##r##_##dx.z);                            \
+        const float zm##r##_##dx = gw<1>(q##r##_##dx.x), z0##r##_##dx = gw<0>(q##r##_##dx.x), \
+                    zp##r##_##dx = gw<-1>(q##r##_##dx.x);
+        META_SRC(0, 0) META_SRC(0, 1) META_SRC(0, 2)
+        META_SRC(1, 0) META_SRC(1, 1) META_SRC(1, 2)
+        META_SRC(2, 0) META_SRC(2, 1) META_SRC(2, 2)
+        META_SRC(3, 0) META_SRC(3, 1) META_SRC(3, 2)
+#undef META_SRC
+#define META_ADD(r, dx, DY, am, a0, ap)                                                   \
+        gather_add<DY, dx - 1>(q##r##_##dx, p##r##_##dx, wx##r##_##dx, zm##r##_##dx,      \
+                               z0##r##_##dx, zp##r##_##dx, am, a0, ap);
+        // node a: source rows 0, 1, 2 at dy = -1, 0, 1
+        META_ADD(0, 0, -1, am_a, a0_a, ap_a) META_ADD(0, 1, -1, am_a, a0_a, ap_a)
+        META_ADD(0, 2, -1, am_a, a0_a, ap_a)
+        META_ADD(1, 0, 0, am_a, a0_a, ap_a) META_ADD(1, 1, 0, am_a, a0_a, ap_a)
+        META_ADD(1, 2, 0, am_a, a0_a, ap_a)
+        META_ADD(2, 0, 1, am_a, a0_a, ap_a) META_ADD(2, 1, 1, am_a, a0_a, ap_a)
+        META_ADD(2, 2, 1, am_a, a0_a, ap_a)
+        // node b: source rows 1, 2, 3 at dy = -1, 0, 1
+        META_ADD(1, 0, -1, am_b, a0_b, ap_b) META_ADD(1, 1, -1, am_b, a0_b, ap_b)
+        META_ADD(1, 2, -1, am_b, a0_b, ap_b)
+        META_ADD(2, 0, 0, am_b, a0_b, ap_b) META_ADD(2, 1, 0, am_b, a0_b, ap_b)
+        META_ADD(2, 2, 0, am_b, a0_b, ap_b)
+        META_ADD(3, 0, 1, am_b, a0_b, ap_b) META_ADD(3, 1, 1, am_b, a0_b, ap_b)
+        META_ADD(3, 2, 1, am_b, a0_b, ap_b)
+#undef META_ADD
         const int z = p - 1;  // complete: planes z-1 .. z+1 added
         if (z >= zs) {
-            const long long o = gidx(g, z, y, x);
-            Ihp[(long long)b * g.inst + o] = am.x;
-            php[(long long)b * g.inst + o] = am.y;
-            // y^ from the node's own foot (cell within one voxel of the node)
-            const float* c0 = rslot(z);
-            const int cell = __float_as_int(c0[mw]);
-            const float fz = c0[kMPL + mw], fy = c0[2 * kMPL + mw], fx = c0[3 * kMPL + mw];
-            const int oz = cell_off(cell, 0);
-            const int ci = mw + cell_off(cell, 1) * kMW + cell_off(cell, 2);
-            const float* lo = rslot(z + oz);  // planes z + oz and z + oz + 1
-            const float* hi = rslot(z + oz + 1);
-            const bool inz = (cell >> 24) & 1, iny = (cell >> 25) & 1, inx = (cell >> 26) & 1;
-            float Iv, pv, dI[3], dP[3];
-            trilin_grad_pq(lo + 7 * kMPL + ci, hi + 7 * kMPL + ci, kMW, fz, fy, fx, inz, iny,
-                           inx, &Iv, dI);
-            trilin_grad_pq(lo + 8 * kMPL + ci, hi + 8 * kMPL + ci, kMW, fz, fy, fx, inz, iny,
-                           inx, &pv, dP);
-            const float Ihv = c0[4 * kMPL + mw], pthv = c0[5 * kMPL + mw];
-            const float* sD = c0 + 6 * kMPL;
-            float dT[3];
-            {  // (D^T div^) along z: the neighbouring planes' div^
-                float r = 0.f;
-                if (z >= 1) r += 0.5f * rslot(z - 1)[6 * kMPL + mw];
-                if (z == g.nz - 1) r += 0.5f * sD[mw];
-                if (z <= g.nz - 2) r -= 0.5f * rslot(z + 1)[6 * kMPL + mw];
-                if (z == 0) r -= 0.5f * sD[mw];
-                dT[0] = r;
+            const float* A_z = slotA(z);
+            const float *B_zm = slotB(z - 1), *B_z = slotB(z), *B_zp = slotB(z + 1);
+            if (ok_a) {
+                const int oz = cell_off(__float_as_int(A_z[mwa]), 0);
+                transport_complete(g, dt, b, z, ya, x, mwa, A_z, B_zm, B_z, B_zp,
+                                   oz < 0 ? B_zm : B_z, oz < 0 ? B_z : B_zp, am_a, vh, Ihp, php);
             }
-            const int c2[2] = {y, x}, n2[2] = {g.ny, g.nx}, s2[2] = {kMW, 1};
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                float r = 0.f;
-                if (c2[a] >= 1) r += 0.5f * sD[mw - s2[a]];
-                if (c2[a] == n2[a] - 1) r += 0.5f * sD[mw];
-                if (c2[a] <= n2[a] - 2) r -= 0.5f * sD[mw + s2[a]];
-                if (c2[a] == 0) r -= 0.5f * sD[mw];
-                dT[1 + a] = r;
+            if (ok_b) {
+                const int mwb = mwa + kMW;
+                const int oz = cell_off(__float_as_int(A_z[mwb]), 0);
+                transport_complete(g, dt, b, z, yb, x, mwb, A_z, B_zm, B_z, B_zp,
+                                   oz < 0 ? B_zm : B_z, oz < 0 ? B_z : B_zp, am_b, vh, Ihp, php);
             }
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                vh[((long long)a * g.B + b) * g.inst + o] =
-                    -dt * (dI[a] * Ihv + dP[a] * pthv) + dT[a];
         }
-        am = a0;
-        a0 = ap;
-        ap = make_float2(0.f, 0.f);
+        am_a = a0_a;
+        a0_a = ap_a;
+        ap_a = make_float2(0.f, 0.f);
+        am_b = a0_b;
+        a0_b = ap_b;
+        ap_b = make_float2(0.f, 0.f);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Shared tail of the gradp kernels.  mode 0: the record of step t-1; mode 3:
@@ -1200,9 +1269,9 @@ cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Sl
 }
 
 cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
-                                 const float* states, const unsigned int* maxdisp,
-                                 const float* rec, float* vh, float* Ihp, float* php,
-                                 unsigned int* fault, cudaStream_t st) {
+                                 const CUtensorMap* maps, const float* states,
+                                 const unsigned int* maxdisp, const float* rec, float* vh,
+                                 float* Ihp, float* php, unsigned int* fault, cudaStream_t st) {
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
         META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, 0, st, g, c, t, sl,
@@ -1212,10 +1281,11 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = g.zct > 0 ? g.zct : march_chunk(g, 3, 2);
-        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
-        META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, g, c, t, sl, zc,
-                                   states, maxdisp, rec, vh, Ihp, php, fault));
+        const int zc = g.zct > 0 ? g.zct : march_chunk(g, 2, 2, 16);
+        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
+        META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, maps[0], maps[1],
+                                   maps[2], g, c, t, sl, zc, states, maxdisp, rec, vh, Ihp, php,
+                                   fault));
     }
     return cudaSuccess;
 }

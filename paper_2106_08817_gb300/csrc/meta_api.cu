@@ -271,11 +271,30 @@ bool encode_map(CUtensorMap* m, const Geom& g, int ndim, void* base, int nslices
     return r == CUDA_SUCCESS;
 }
 
+// 5-D tensor map over fields of a batch of pitched instances: dims {nx, ny,
+// nz, B, nfields}, field f of instance b at slice f * B + b; boxes of the 3-D
+// transport's plane window (40 x 18 x 1 x 1 x box_nf); zero fill outside.
+bool encode_map5(CUtensorMap* m, const Geom& g, void* base, int nfields, int box_nf) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[5] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                                (cuuint64_t)g.B, (cuuint64_t)nfields};
+    const cuuint64_t strides[4] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.slab * 4,
+                                   (cuuint64_t)g.inst * 4, (cuuint64_t)g.B * g.inst * 4};
+    const cuuint32_t box[5] = {40, 18, 1, 1, (cuuint32_t)box_nf};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 struct Ctx {
     Layout L;
     char* ws;
     Taps tx, ts;
     CUtensorMap tmI, tmP, tmSAy, tmSBz, tmSVx;
+    CUtensorMap tmTr[3];  // 3-D transport: records 0..5, div^, (I_t, p_t)
     cudaStream_t st;
     unsigned int* fault;
     unsigned int* maxdisp;
@@ -352,6 +371,9 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
         ok &= encode_map(&c->tmSAy, g, 3, c->SA, d * B, kTXS, g.ly + c->ts.kp, 1);
         ok &= encode_map(&c->tmSBz, g, 3, c->SB, d * B, kTXS, 1, g.lz + c->ts.kp);
         ok &= encode_map(&c->tmSVx, g, 3, c->SV, d * B, LW, 4, 4);
+        ok &= encode_map5(&c->tmTr[0], g, c->REC, d + 4, 6);
+        ok &= encode_map5(&c->tmTr[1], g, c->REC, d + 4, 1);
+        ok &= encode_map5(&c->tmTr[2], g, c->states, 2 * L.nstate, 2);
     }
     return ok ? META_OK : META_ERR_UNSUPPORTED;
 }
@@ -488,7 +510,7 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         sl.ut = L.u_slot(t);
         sl.u0 = L.u_slot(0);
         META_LAUNCH(META_K_ADJ_GATHER, c.st,
-                    launch_adj_transport(g, d, cf, t, sl, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
+                    launch_adj_transport(g, d, cf, t, sl, c.tmTr, c.states, c.maxdisp, c.REC, c.SV, c.IHP,
                                          c.PHP, c.fault, c.st));
         if (L.pdet)
             META_LAUNCH(META_K_ADJ_JAC, c.st,
@@ -565,7 +587,7 @@ meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, fl
                                                c.st));
             }
             META_LAUNCH(META_K_ADJ_GATHER, c.st,
-                        launch_adj_transport(g, d, cf, t, sl, c.states, c.maxdisp, c.REC, c.SV,
+                        launch_adj_transport(g, d, cf, t, sl, c.tmTr, c.states, c.maxdisp, c.REC, c.SV,
                                              c.IHP, c.PHP, c.fault, c.st));
             META_LAUNCH(META_K_ADJ_GATHER, c.st,
                         launch_hybrid_p(g, d, cf, sl, c.states, c.u, rawP, c.PHP, c.SV, c.st));
@@ -691,7 +713,7 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
     out->split = (find_tuning(prob, &tn) && tn.split > 0) ? tn.split : 1;
     if (L.ndim == 3) {
         out->lz = L.g.lz;
-        out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 3, 2);
+        out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 2, 2, 16);
         out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 4, 4);
     } else {
         out->lz = out->zc_transport = out->zc_advect = 0;

@@ -83,25 +83,40 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
         // thread (finite everywhere; columns 0 and LW-1 only ever meet zero
         // taps, and there the missing neighbour is replaced by the column itself).
         const int LW4 = LW / 4;
+        const int total = kRows * LW4;
         const float inv_lw4 = 1.f / (float)LW4;
-        for (int idx = tid; idx < kRows * LW4; idx += blockDim.x) {
+        const int lane = tid & 31;
+        // the CTA has txw / 8 x 16 threads, so its last warp may hold 16 lanes
+        const int wlast = min(31, (int)blockDim.x - 1 - (tid & ~31));
+        const unsigned wmask = wlast == 31 ? 0xffffffffu : ((2u << wlast) - 1u);
+        // a warp-uniform trip count: every lane takes part in the shuffles
+        for (int base = 0; base < total; base += blockDim.x) {
+            const int idx = min(base + tid, total - 1);  // lanes past the end repeat the last
             // idx < 2^12, so the rounded float quotient is the exact integer one
             const int row = (int)(((float)idx + 0.5f) * inv_lw4);
             const int c = 4 * (idx - row * LW4);
             const int ty = (NDIM == 2) ? row : (row & 3);
             const int tz = (NDIM == 2) ? 0 : (row >> 2);
             const int y = y0 + ty, z = z0 + tz;
+            const int rI = (NDIM == 2) ? (ty + 1) : ((tz + 1) * 6 + ty + 1);
+            const float* Ir = sI + rI * LW;
+            const float4 ic = lds4(Ir + c);
+            // columns c - 1 and c + 4 from the neighbouring lanes (same row whenever
+            // the column exists; the lanes at the warp's two ends read them), instead
+            // of scalar loads at a 16-byte stride (four-way bank conflicts)
+            float left = __shfl_up_sync(wmask, ic.w, 1);
+            float right = __shfl_down_sync(wmask, ic.x, 1);
+            if (lane == 0 && c > 0) left = Ir[c - 1];
+            if (lane == wlast && c + 4 < LW) right = Ir[c + 4];
             float mo[NDIM][4];
 #pragma unroll
             for (int a = 0; a < NDIM; ++a)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mo[a][j] = 0.f;
+            if (base + tid >= total) continue;
             if (y < g.ny && z < g.nz) {
-                const int rI = (NDIM == 2) ? (ty + 1) : ((tz + 1) * 6 + ty + 1);
-                const float* Ir = sI + rI * LW;
-                const float4 ic = lds4(Ir + c);
-                const float iv[6] = {c > 0 ? Ir[c - 1] : ic.x, ic.x, ic.y, ic.z, ic.w,
-                                     c + 4 < LW ? Ir[c + 4] : ic.w};
+                const float iv[6] = {c > 0 ? left : ic.x, ic.x, ic.y, ic.z, ic.w,
+                                     c + 4 < LW ? right : ic.w};
                 const float4 yu = lds4(sI + (rI + (y < g.ny - 1 ? 1 : 0)) * LW + c);
                 const float4 yd = lds4(sI + (rI - (y > 0 ? 1 : 0)) * LW + c);
                 const float yuv[4] = {yu.x, yu.y, yu.z, yu.w}, ydv[4] = {yd.x, yd.y, yd.z, yd.w};

@@ -74,7 +74,7 @@ __device__ __forceinline__ int div_nyt(const Geom& g, int n) {
 // Planes per CTA of a kernel that marches along z over 32 x 8 columns: the
 // chunk that best trades the `halo` extra planes each chunk stages against
 // the fill of the last wave (ctas_per_sm resident CTAs per SM).
-inline int march_chunk(const Geom& g, int ctas_per_sm, int halo) {
+inline int march_chunk(const Geom& g, int ctas_per_sm, int halo, int rows = 8) {
     static int nsm = 0;
     if (nsm == 0) {
         int dev = 0;
@@ -83,7 +83,7 @@ inline int march_chunk(const Geom& g, int ctas_per_sm, int halo) {
             nsm <= 0)
             nsm = 152;
     }
-    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.B;
+    const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + rows - 1) / rows) * g.B;
     const int cand[] = {4, 6, 8, 12, 16, 24, 32};
     int best = 8;
     double best_s = -1.0;
@@ -264,6 +264,22 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
         "r"(smem_u32(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plain arrival (no transaction bytes): completes the phase of a barrier
+// initialised with count 1 when no copy is issued for it.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Load a box whose innermost coordinate is x, at (x, y[, z], slice).

@@ -87,8 +87,11 @@ cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Sl
                                const float* rawP, float* rec, cudaStream_t st);
 // S^T of I^' and p~^ into Ihp / php and v^ (d slices) into vh, for step t
 // (state slot sl.st).
+// In 3-D, maps[0..2] are the transport's tensor maps (records 0..5, div^, and
+// the states), see encode_map5.
 cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
-                                 const float* states, const unsigned int* maxdisp,
+                                 const CUtensorMap* maps, const float* states,
+                                 const unsigned int* maxdisp,
                                  const float* rec, float* vh, float* Ihp, float* php,
                                  unsigned int* fault, cudaStream_t st);
 // I^_t, p^_t from Ihp / php and m^ (state slot sl.st), then by mode: 0 the
