@@ -240,7 +240,9 @@ typedef struct {
     int zc_advect;    /* 3-D only; in [1, dims[0]] */
     int ly;           /* multiple of 16 in [16, 128] */
     int lz;           /* 3-D only; multiple of 16 in [16, 128] */
-    int txw;          /* multiple of 8 in [8, 128] */
+    int txw;          /* multiple of 8 in [8, 256] whose staged row txw + 2 (r4 + 8)
+                         fits one TMA box of 256 floats, r4 = ceil(3 sigma) rounded up
+                         to a multiple of 4 */
     int split;        /* meta_plan_create records the batch as this many sub-batches on
                          parallel graph branches, in [1, min(batch, 16)]; the eager calls
                          ignore it */

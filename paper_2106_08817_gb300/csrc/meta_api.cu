@@ -192,6 +192,12 @@ Layout make_layout(const meta_problem* pr) {
 //  xpass:   w[k'] = tap(k' - r4) for k' in [r4 - r, r4 + r], 0 elsewhere,
 //           kp = roundup(r4 + r + 1, 8)   (window starts r4 left of the output)
 //  strided: w[k']  = tap(k' - r) for k' in [0, 2r], kp = roundup(2r + 1, 8)
+// Radius of the x pass's staged halo: r = ceil(3 sigma) rounded up to 4.
+int xpass_r4(float sigma) {
+    const int r = (int)std::ceil(3.0 * (double)sigma);
+    return (r + 3) / 4 * 4;
+}
+
 void make_taps(float sigma, Taps* xpass, Taps* strided) {
     const int r = (int)std::ceil(3.0 * (double)sigma);
     double t[2 * kMaxR + 1];
@@ -682,8 +688,11 @@ meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
     }
     const int d = prob->ndim;
     const int nz = d == 3 ? prob->dims[0] : 1, ny = prob->dims[d - 2];
-    auto len_ok = [](int v, int q) { return v == 0 || (v >= q && v <= 128 && v % q == 0); };
-    if (!len_ok(tun->ly, kBA) || !len_ok(tun->lz, kBA) || !len_ok(tun->txw, kBX))
+    auto len_ok = [](int v, int q, int mx) { return v == 0 || (v >= q && v <= mx && v % q == 0); };
+    if (!len_ok(tun->ly, kBA, 128) || !len_ok(tun->lz, kBA, 128) || !len_ok(tun->txw, kBX, 256))
+        return META_ERR_INVALID_ARG;
+    // the x pass stages rows of txw + 2 (r4 + 8) floats by one TMA box (<= 256)
+    if (tun->txw && xpass_lw(tun->txw, xpass_r4(prob->sigma)) > kMaxLW)
         return META_ERR_INVALID_ARG;
     if (tun->zc_transport < 0 || tun->zc_transport > nz || tun->zc_advect < 0 ||
         tun->zc_advect > nz)
@@ -775,7 +784,16 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         params.push_back({&cur.lz, lens(nz, kBA)});
     }
     params.push_back({&cur.ly, lens(ny, kBA)});
-    params.push_back({&cur.txw, lens(nx, kBX)});
+    {  // x-pass widths: equal tiles of at most 48 .. 256 that fit the TMA box
+        std::vector<int> v;
+        for (int m : {48, 64, 96, 128, 160, 192, 256}) {
+            const int l = even_tile(nx, m, kBX);
+            if (xpass_lw(l, xpass_r4(prob->sigma)) <= kMaxLW &&
+                std::find(v.begin(), v.end(), l) == v.end())
+                v.push_back(l);
+        }
+        params.push_back({&cur.txw, v});
+    }
     meta_status res = META_OK;
     for (auto& pv : params) {
         int best_v = *pv.first;

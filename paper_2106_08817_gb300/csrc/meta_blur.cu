@@ -24,7 +24,7 @@ namespace meta {
 // KC > 0: the tap loop has KC chunks of 8 at compile time (fully unrolled,
 // taps read as immediate constant-bank operands); KC = 0: runtime taps.kp.
 template <int NDIM, bool GRADP, int KC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
         const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0,
         float* __restrict__ out, unsigned int* fault) {
@@ -156,14 +156,17 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     }
 
     // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`,
-    // g.txw / 8 threads per row.  Consecutive threads alternate between the two
-    // rows of a row pair, so a quarter-warp's 16-byte loads cover columns of
-    // both rows and, with the row stride odd in 16-byte units, spread over the
-    // bank groups.
-    const int tpr = g.txw / kBX;
-    const int local = tid % (2 * tpr), pair = tid / (2 * tpr);
+    // g.txw / 8 threads per row, padded to a multiple of 4 (xpass_threads).
+    // Consecutive threads alternate between the two rows of a row pair, so each
+    // 8-lane phase of a 16-byte load covers 4 consecutive tx of both rows; with
+    // the row stride odd in 16-byte units their 8 addresses fall in the 8
+    // distinct bank groups.  The padding lanes only idle here: without them a
+    // phase could straddle two row pairs and meet a bank group twice.
+    const int tpr = g.txw / kBX, tprp = (tpr + 3) & ~3;
+    const int local = tid % (2 * tprp), pair = tid / (2 * tprp);
     const int tx = local >> 1;
     const int row = 2 * pair + (local & 1);
+    if (tx >= tpr) return;  // no barrier follows
     const int ty = (NDIM == 2) ? row : (row & 3);
     const int tz = (NDIM == 2) ? 0 : (row >> 2);
     const int y = y0 + ty, z = z0 + tz;
@@ -408,7 +411,7 @@ static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tm
     dim3 grid((g.nx + g.txw - 1) / g.txw,
               NDIM == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
               GRADP ? g.B : nslices);
-    const int threads = g.txw / kBX * kRows;
+    const int threads = xpass_threads(g.txw);
     META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP, KC>, grid, threads, smem, st, tmI, tmP, taps, g,
                                sliceI, sliceP, out_slice0, out, fault));
     return cudaSuccess;

@@ -39,6 +39,15 @@ __host__ __device__ constexpr int xpass_lw(int txw, int r4) {
     return txw + 2 * (r4 + 8) + ((txw + 2 * (r4 + 8) + 4 <= 256) ? 4 : 0);
 }
 
+// Threads of an x-pass CTA: kRows rows of txw / 8 threads, padded to a
+// multiple of 4 per row (conflict-free 16-byte loads in the blur phase).
+__host__ __device__ constexpr int xpass_threads(int txw) {
+    return ((txw / kBX + 3) & ~3) * kRows;
+}
+
+// Largest staged row of the x pass: the TMA box limit of 256 elements.
+constexpr int kMaxLW = 256;
+
 // The max displacement of step t, instance b lives at maxdisp[kMaxdispStride *
 // (t * B + b)]: one 128-byte line per slot, so that the per-CTA atomics of
 // different instances do not queue on one L2 line.

@@ -125,10 +125,18 @@ def test_tuning_table_round_trip_and_validation(meta):
     assert meta.tuning(dims, B, s) == mine
     meta.set_tuning(dims, B, s, dict(ly=32))  # zero fields: built-in choice
     assert meta.tuning(dims, B, s)["ly"] == 32 and meta.tuning(dims, B, s)["lz"] == 80
+    # a whole 160-wide row per x tile: staged row 160 + 2 (20 + 8) + 4 = 220 <= 256
+    meta.set_tuning(dims, B, s, dict(txw=160))
+    assert meta.tuning(dims, B, s)["txw"] == 160
     for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
-                dict(lz=-16), dict(zc_advect=-1), dict(split=2)):  # split <= batch (1 here)
+                dict(lz=-16), dict(zc_advect=-1), dict(split=2),  # split <= batch (1 here)
+                dict(txw=208), dict(txw=264)):  # staged rows of 264 and 320 floats
         with pytest.raises(meta.MetaError):
             meta.set_tuning(dims, B, s, bad)
+    with pytest.raises(meta.MetaError):  # sigma 18: r4 = 56, so 128 + 128 + 4 > 256 fits no wider
+        meta.set_tuning(dims, B, 18.0, dict(txw=136))
+    meta.set_tuning(dims, B, 18.0, dict(txw=128))
+    meta.set_tuning(dims, B, 18.0, None)
     with pytest.raises(meta.MetaError):
         meta.set_tuning((64, 64), 1, 2.0, dict(lz=16))  # 2-D problems have no z tiles
     with pytest.raises(meta.MetaError):  # y tiles x nz beyond the launch grid limit

@@ -756,6 +756,10 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
                                                          lz=16, txw=24)
     meta.set_tuning(dims, B, sigma, odd)
     c1, g1 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    # one x tile over the whole row (144 or 72 wide: 18 or 9 threads per row, padded to
+    # 20 or 12, the staged row up to the 256-float TMA box)
+    meta.set_tuning(dims, B, sigma, dict(txw=144) if len(dims) == 2 else dict(txw=72))
+    c3, g3 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
     chosen = meta.autotune(cuda(I0), cuda(J), cuda(p0), *args)
     assert meta.tuning(dims, B, sigma) == chosen
     c2, g2 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
@@ -767,6 +771,7 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
     torch.cuda.synchronize()
     assert torch.equal(c0, c1) and torch.equal(g0, g1)
     assert torch.equal(c0, c2) and torch.equal(g0, g2)
+    assert torch.equal(c0, c3) and torch.equal(g0, g3)
     assert torch.equal(c0, plan.cost) and torch.equal(g0, plan.grad)
     assert plan.ws.status() & 1 == 0
 
