@@ -768,11 +768,13 @@ def run_ours(args):
 
     # ---- the other configurations' own lines, as side keys (same run, same GPU)
     side = None
-    if not args.no_side and world == 1:
+    if not args.no_side:
         side = {}
         for name in SIDE_WORKLOADS.get(args.workload, ()):
-            side[name] = (measure_mix(meta, args, dev, flush, stream) if name == "mix64"
-                          else measure_side(meta, name, args, dev, flush, stream))
+            if name == "mix64":  # one job split across the ranks
+                side[name] = measure_mix(meta, args, dev, flush, stream)
+            elif world == 1:
+                side[name] = measure_side(meta, name, args, dev, flush, stream)
 
     fault = ws.status()
     out = None
@@ -893,36 +895,55 @@ def measure_side(meta, name, args, dev, flush, stream, steps=20):
 
 def measure_mix(meta, args, dev, flush, stream, steps=20):
     """The 64 uneven 2-D/3-D pairs of phantoms.mixed_pairs in one CUDA graph with
-    parallel branches (meta_plan_create_group); value = sum of voxel-steps / time."""
+    parallel branches (meta_plan_create_group); value = sum of voxel-steps / time.
+    With several ranks the one job of 64 pairs is split across them by voxel-steps
+    (paper_2106_08817_gb300.partition: nothing exchanged in the data path), the job
+    time is the slowest rank's, and the costs are gathered in pair order."""
     import torch
     import phantoms
-    ws = phantoms.mixed_pairs(seed=1004 + 7919 * int(os.environ.get("RANK", "0")))
+    from paper_2106_08817_gb300 import partition
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    job = phantoms.mixed_pairs(seed=1004)
+    work = [w.batch * w.voxels * w.T for w in job]
+    mine = partition.rank_share(work, world, rank)
+    ws = [job[i] for i in mine]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     probs = [dict(I0=t(w.I0), J=t(w.J), p0=t(w.p0), T=w.T, sigma=w.sigma, mu=t(w.mu),
                   rho=t(w.rho), lam=t(w.lam)) for w in ws]
-    plan = meta.GroupPlan(probs, streams=args.streams)
+    def timed(plan):
+        def gd():
+            for it in plan.items:
+                g = it["grad"]
+                gmax = g.abs().amax(dim=tuple(range(1, g.dim())), keepdim=True).clamp_min(1e-30)
+                it["p0"].sub_(0.02 * g / gmax)
+
+        for _ in range(3):
+            plan.launch()
+            gd()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            plan.launch()
+            evs[k][1].record(stream)
+            gd()
+        torch.cuda.synchronize()
+        return reduce_max(sum(a.elapsed_time(b) for a, b in evs) / steps, world, dev)
+
+    # the graph of parallel branches first (for comparison), then the persistent launch
+    branches = meta.GroupPlan(probs, streams=args.streams)
+    ms_branches = timed(branches)
+    del branches
+    plan = meta.GroupPlan(probs, persistent=True)
     vs = plan.voxel_steps()
-
-    def gd():
-        for it in plan.items:
-            g = it["grad"]
-            gmax = g.abs().amax(dim=tuple(range(1, g.dim())), keepdim=True).clamp_min(1e-30)
-            it["p0"].sub_(0.02 * g / gmax)
-
-    for _ in range(3):
-        plan.launch()
-        gd()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(steps)]
-    for k in range(steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        plan.launch()
-        evs[k][1].record(stream)
-        gd()
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ms = timed(plan)
+    plan_fault = plan.status()
+    costs = [[float(x) for x in it["cost"].sum(dim=1).cpu()] for it in plan.items]
+    if world > 1:
+        costs = partition.gather_in_order(mine, costs, len(job))
     # per-class times from eager calls of every member
     meta.timer_start(1 << 18)
     for it in plan.items:
@@ -939,42 +960,73 @@ def measure_mix(meta, args, dev, flush, stream, steps=20):
     model_bytes = sum(model_bytes_per_voxel_step(len(it["dims"])) * it["B"]
                       * int(np.prod(it["dims"])) * it["T"] for it in plan.items)
     return {
-        "value": vs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-        "config": {"workload": "mix64", "pairs": len(ws),
-                   "sizes": sorted(set("x".join(map(str, w.dims)) for w in ws)),
-                   "voxel_steps_per_step": vs, "graph_branches": args.streams,
-                   "step": "one graph launch of 64 cost_and_grad calls (parallel branches)",
+        "value": sum(work) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+        "scaling": "strong",
+        "config": {"workload": "mix64", "pairs": len(job),
+                   "sizes": sorted(set("x".join(map(str, w.dims)) for w in job)),
+                   "voxel_steps_per_step": sum(work),
+                   "ranks": world, "pairs_this_rank": len(ws),
+                   "voxel_steps_this_rank": vs,
+                   "step": "one persistent kernel launch (meta_plan_create_persistent) over "
+                           "every tile of this rank's cost_and_grad calls; the 64 pairs split "
+                           "across ranks by voxel-steps",
                    "l2": "flushed (256 MiB write) between timed steps"},
+        "graph_branches": {"value": sum(work) / (ms_branches * 1e-3), "unit": UNIT,
+                           "ms_per_step": ms_branches, "branches": args.streams,
+                           "what": "the same calls recorded as parallel branches of one CUDA "
+                                   "graph (meta_plan_create_group), one launch per kernel"},
+        "plan_fault_bits": plan_fault,
+        "cost_per_pair": costs,
         "path_roofline": {"model_bytes_per_step": model_bytes,
                           "model_frac": model_bytes / (ms * 1e-3) / 1e9 / peak,
                           "peak_GBps": peak},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        # the persistent kernel is the only kernel of the step: its bandwidth on the
+        # fixed byte model of every pair's voxel-steps
+        "roofline": {"bound": "hbm", "kernel": "k_persist", "achieved": model_bytes / (ms * 1e-3)
+                     / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": model_bytes / (ms * 1e-3) / 1e9 / peak, "traffic": None,
                      "peak_source": peak_src},
-        "gpu_launches_per_step": int(sum(v[2] for v in kt.values())),
+        "gpu_launches_per_step": 1,
         "device_fault_bits": max(it["ws"].status() for it in plan.items),
-        "kernels": {k: {"ms_total": round(v[0], 3), "launches": v[2]}
-                    for k, v in kt.items() if v[1]},
+        "eager_kernels": {
+            "what": "the same calls eager, one launch per kernel, CUDA events around each: "
+                    "where the time of the pairs' work goes",
+            "dominant": dom, "dominant_GBps_model": achieved,
+            "classes": {k: {"ms_total": round(v[0], 3), "launches": v[2]}
+                        for k, v in kt.items() if v[1]}},
     }
 
 
 def run_mix(args):
-    """The mixed batch as the headline workload (--workload mix64)."""
+    """The mixed batch as the headline workload (--workload mix64): one job of 64
+    pairs, split across the ranks when there are several (strong scaling)."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2106_08817_gb300 as meta
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2106_08817_gb300 as meta
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     with ClockSampler(dev.index) as clk:
         r = measure_mix(meta, args, dev, flush, stream, steps=args.steps)
-    print(json.dumps(dict({
-        "metric": METRIC, "n_gpus": 1, "warmup": args.warmup, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "gpu_launches": r["gpu_launches_per_step"] * args.steps, "clocks": clk.summary()},
-        **r)), flush=True)
+    if rank == 0:
+        print(json.dumps(dict({
+            "metric": METRIC, "n_gpus": world, "warmup": args.warmup, "higher_is_better": True,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "gpu_launches": r["gpu_launches_per_step"] * args.steps, "clocks": clk.summary()},
+            **r)), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def main():

@@ -180,7 +180,45 @@ meta_status meta_plan_create_group(int n, const meta_problem* probs, const float
                                    const float* const* lambda, double* const* cost,
                                    float* const* grad, void* const* ws, const size_t* ws_bytes,
                                    int streams, meta_plan** plan);
+/* The same n problems (arguments as meta_plan_create_group) in ONE persistent
+ * kernel launch: many registrations of uneven sizes, 2-D and 3-D, T and sigma
+ * (each one cost_and_grad: Eq. 3 shooting in the semi-Lagrangian form of
+ * Sec. 2.3, the Eq. 4 cost and its adjoint).  Every problem's launch sequence
+ * is recorded once into per-problem phases (one per kernel launch of its call,
+ * each with that launch's tiles); the phases of all problems are interleaved
+ * by progress into one order, and the kernel's CTAs take tiles from one work
+ * counter in that order.  A tile waits (bounded spin) until its problem's
+ * earlier phases are complete, then runs the same kernel body on that tile, so
+ * every problem's cost and grad are bit-identical to its own
+ * meta_cost_and_grad.  Supported: the semi-Lagrangian scheme with the default
+ * momentum update (else META_ERR_UNSUPPORTED), any checkpoint stride; x tiles
+ * of at most 128 voxels (tuned wider ones give META_ERR_UNSUPPORTED).  Creation
+ * allocates the plan's device tables (phases, tensor maps, taps, counters) and
+ * records one CUDA graph: the counters cleared, then the kernel.  Each
+ * workspace's header must be zero as for meta_cost_and_grad. */
+meta_status meta_plan_create_persistent(int n, const meta_problem* probs,
+                                        const float* const* I0, const float* const* J,
+                                        const float* const* p0, const float* const* mu,
+                                        const float* const* rho, const float* const* lambda,
+                                        double* const* cost, float* const* grad, void* const* ws,
+                                        const size_t* ws_bytes, meta_plan** plan);
 meta_status meta_plan_launch(meta_plan* plan, void* stream);
+/* Status of a plan's launches since the status was last cleared.  Persistent
+ * plans: bit 0 = a dependency wait ran out (after 5 s) and that launch
+ * was abandoned (its results are invalid; returns META_ERR_TIMEOUT); the
+ * waiting problem's workspace status word has bit 0 as well.  Other plans
+ * report their status through their workspaces (meta_workspace_status) and give
+ * 0 here.  Synchronises `stream`; clear != 0 resets the word. */
+meta_status meta_plan_status(meta_plan* plan, int clear, void* stream, unsigned int* bits);
+/* Self-test of the persistent kernel's failure detection: one launch in which
+ * the first phase of problem `hold` never reports its tiles as complete and
+ * dependency waits give up after limit_ns (in [1 ms, 2 s]).  The problem's
+ * second phase waits until the limit runs out, the launch is abandoned, and
+ * meta_plan_status reports META_ERR_TIMEOUT; nothing faults.  After clearing
+ * the plan's status and the workspaces' status words, meta_plan_launch runs
+ * normally.  META_ERR_INVALID_ARG for a plan that is not persistent. */
+meta_status meta_plan_selftest_timeout(meta_plan* plan, int hold, unsigned long long limit_ns,
+                                       void* stream);
 meta_status meta_plan_destroy(meta_plan* plan);
 
 /* Size of the library's own device scratch used by meta_cost_and_grad_noalloc. */
@@ -307,7 +345,7 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
  * bounded TMA wait ran out (the call's results are invalid; returns
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step
  * displacements beyond the deterministic gather window (8 voxels or more in
- * 2-D, 2 or more in 3-D) and transposed the interpolation by an atomic scatter
+ * 2-D, 4 or more in 3-D) and transposed the interpolation by an atomic scatter
  * instead, so its summation order is not fixed.  Synchronises `stream`.
  * clear != 0 resets it. */
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,

@@ -85,6 +85,14 @@ def _load():
                                                PP, ctypes.POINTER(S), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_void_p)]
         lib.meta_plan_create_group.restype = ctypes.c_int
+        lib.meta_plan_create_persistent.argtypes = [ctypes.c_int, P, PP, PP, PP, PP, PP, PP, PP,
+                                                    PP, PP, ctypes.POINTER(S),
+                                                    ctypes.POINTER(ctypes.c_void_p)]
+        lib.meta_plan_create_persistent.restype = ctypes.c_int
+        lib.meta_plan_status.argtypes = [V, ctypes.c_int, V, ctypes.POINTER(ctypes.c_uint)]
+        lib.meta_plan_status.restype = ctypes.c_int
+        lib.meta_plan_selftest_timeout.argtypes = [V, ctypes.c_int, ctypes.c_ulonglong, V]
+        lib.meta_plan_selftest_timeout.restype = ctypes.c_int
         lib.meta_plan_launch.argtypes = [V, V]
         lib.meta_plan_destroy.argtypes = [V]
         for f in ("meta_plan_create", "meta_plan_launch", "meta_plan_destroy"):
@@ -580,14 +588,17 @@ class CostAndGradPlan:
 
 class GroupPlan:
     """Many independent problems of different shapes / T / sigma (2-D and 3-D
-    mixed) recorded into one CUDA graph as parallel branches (meta_plan_create_group).
+    mixed) recorded into one CUDA graph as parallel branches (meta_plan_create_group),
+    or, with ``persistent=True``, run by ONE persistent kernel launch
+    (meta_plan_create_persistent: the semi-Lagrangian scheme, default momentum update).
 
     `problems` is a list of dicts with keys I0, J, p0 ([B, *dims] CUDA tensors),
     T, sigma, mu, rho, lam (optional: ckpt, p_update, scheme).  Each item keeps its own copies of the inputs
     (``plan.items[k]["p0"]`` etc.), cost [B, 3] and grad; ``launch()`` runs all.
     """
 
-    def __init__(self, problems, streams: int = 8):
+    def __init__(self, problems, streams: int = 8, persistent: bool = False):
+        self.persistent = bool(persistent)
         self.items = []
         n = len(problems)
         probs = (_Problem * n)()
@@ -619,16 +630,41 @@ class GroupPlan:
         self.device = dev
         h = ctypes.c_void_p(0)
         torch.cuda.synchronize(dev)
-        rc = _load().meta_plan_create_group(n, probs, I0s, Js, p0s, mus, rhos, lams, costs,
-                                            grads, wss, wsb, int(streams), ctypes.byref(h))
+        with torch.cuda.device(dev):
+            if self.persistent:
+                rc = _load().meta_plan_create_persistent(n, probs, I0s, Js, p0s, mus, rhos, lams,
+                                                         costs, grads, wss, wsb, ctypes.byref(h))
+            else:
+                rc = _load().meta_plan_create_group(n, probs, I0s, Js, p0s, mus, rhos, lams,
+                                                    costs, grads, wss, wsb, int(streams),
+                                                    ctypes.byref(h))
         if rc:
-            raise MetaError(rc, "meta_plan_create_group")
+            raise MetaError(rc, "meta_plan_create_persistent" if self.persistent
+                            else "meta_plan_create_group")
         self._h = h
 
     def launch(self):
         rc = _load().meta_plan_launch(self._h, _stream(self.device))
         if rc:
             raise MetaError(rc, "meta_plan_launch")
+
+    def status(self, clear: bool = False) -> int:
+        """The plan's own status bits (meta_plan_status; persistent plans: bit 0 = a
+        dependency wait ran out and a launch was abandoned).  Synchronises the stream."""
+        bits = ctypes.c_uint(0)
+        rc = _load().meta_plan_status(self._h, int(clear), _stream(self.device),
+                                      ctypes.byref(bits))
+        if rc not in (0, 5):
+            raise MetaError(rc, "meta_plan_status")
+        return int(bits.value)
+
+    def selftest_timeout(self, hold: int = 0, limit_ns: int = 50_000_000) -> None:
+        """One persistent launch in which problem `hold`'s first phase never reports
+        completion: its next phase's bounded wait runs out (meta_plan_selftest_timeout)."""
+        rc = _load().meta_plan_selftest_timeout(self._h, int(hold), int(limit_ns),
+                                                _stream(self.device))
+        if rc:
+            raise MetaError(rc, "meta_plan_selftest_timeout")
 
     def voxel_steps(self) -> int:
         return sum(it["B"] * int(np.prod(it["dims"])) * it["T"] for it in self.items)

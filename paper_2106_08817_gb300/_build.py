@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmeta.so")
 SOURCES = ["meta_api.cu", "meta_blur.cu", "meta_step.cu", "meta_adjoint.cu", "meta_noalloc.cu",
-           "meta_lbfgs.cu"]
+           "meta_lbfgs.cu", "meta_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

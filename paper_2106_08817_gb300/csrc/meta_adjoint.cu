@@ -54,7 +54,9 @@ struct GatherTile<2> {
 };
 template <>
 struct GatherTile<3> {
-    static constexpr int RMAX = 2;  // nodes are marched along z (k_adj_transport3d)
+    // per-step displacements under 4 voxels: up to 9^3 sources per node, read
+    // through L1 in a fixed order (R = 1 marches along z, k_adj_transport3d)
+    static constexpr int RMAX = 4;
 };
 
 dim3 gather_grid2d(const Geom& g) {
@@ -94,7 +96,7 @@ struct Rec {
 template <int NDIM, bool PDET = false, bool HYB = false>
 __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
                                             long long o, float Ih1, float ph1, const float* d,
-                                            float fac, const float* __restrict__ pprev,
+                                            float fac, const float* pprev,
                                             float* rec) {
     const int b = v.b;
     const float mu = cf.mu[b], dt = cf.dt;
@@ -139,8 +141,8 @@ __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, cons
 template <int NDIM, bool PDET = false, bool HYB = false>
 __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int s_state, int s_u,
                                              const Vox& v, long long o, float Ih1, float ph1,
-                                             const float* __restrict__ states,
-                                             const float* __restrict__ u, float* rec) {
+                                             const float* states,
+                                             const float* u, float* rec) {
     const int b = v.b;
     const float rho = cf.rho[b], dtrho = cf.dt * rho;
     int c[NDIM], n[NDIM];
@@ -175,8 +177,8 @@ __device__ __forceinline__ void build_record(const Geom& g, const Coefs& cf, int
 template <int NDIM>
 __device__ __forceinline__ void build_record_any(const Geom& g, const Coefs& cf, int s_state,
                                                  int s_u, const Vox& v, long long o, float Ih1,
-                                                 float ph1, const float* __restrict__ states,
-                                                 const float* __restrict__ u, float* rec) {
+                                                 float ph1, const float* states,
+                                                 const float* u, float* rec) {
     if (cf.scheme == 2)
         build_record<NDIM, false, true>(g, cf, s_state, s_u, v, o, Ih1, ph1, states, u, rec);
     else if (cf.pdet)
@@ -191,8 +193,8 @@ __device__ __forceinline__ void build_record_any(const Geom& g, const Coefs& cf,
 template <int NDIM>
 __device__ __forceinline__ void adjoint_start(const Geom& g, const Coefs& cf, int s_state,
                                               int s_u, const Vox& v, long long o, float Ih1,
-                                              float ph1, const float* __restrict__ states,
-                                              const float* __restrict__ u, float* rec,
+                                              float ph1, const float* states,
+                                              const float* u, float* rec,
                                               float* rawI, float* rawP) {
     const long long ob = (long long)v.b * g.inst + o;
     if (cf.scheme != 1)
@@ -217,25 +219,29 @@ __device__ __forceinline__ float gw(float g) {
 
 // ------------------------------------------------------------------ kernels
 
+// Shared memory of the bodies that carve fixed arrays from the block context:
+// the cost reductions (3 x 256 doubles), the 2-D transport (8 staged windows of
+// 40 x 18 floats and 612 packed float4 sources) and the 2-D gradp (7 staged
+// tiles of 40 x 18 floats).
+constexpr int kCostSmem = 3 * 256 * 8;
+constexpr int kTr2dSmem = (8 * 720 + 4 * 612) * 4;
+constexpr int kGradp2dSmem = 7 * (2 * kPY + 2) * (kPX + 8) * 4;
+
 // Cost partials: one CTA = 8 warps over a fixed set of (z, y) rows of
 // instance blockIdx.y.  (The adjoint start from I^_T = I_T - J, p^_T = 0 is
 // k_adj_init<NDIM, true>, a pointwise kernel of its own.)
-template <int NDIM>
-__global__ void __launch_bounds__(256)
-k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float* __restrict__ u,
-                const float* __restrict__ J, double* partials) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    const int b = blockIdx.y;
+template <class K, int NDIM>
+__device__ __forceinline__ void body_cost_partials(const K& kb, Geom g, Slots sl, const float* states, const float* u, const float* J, double* partials) {
+    const int b = kb.by();
     const long long N = (long long)g.nz * g.ny * g.nx;
     const float* IT = slice_of(states, g, ((long long)sl.sT * 2 + 0) * g.B + b);
     const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
     const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
     double data = 0.0, kin = 0.0, res = 0.0;
     // one warp per (z, y) row at a time; a fixed assignment, so fixed sums
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = kb.tx() >> 5, lane = kb.tx() & 31;
     const int nrows = g.nz * g.ny;
-    for (int row = blockIdx.x * 8 + warp; row < nrows; row += gridDim.x * 8)
+    for (int row = kb.bx() * 8 + warp; row < nrows; row += kb.gx() * 8)
     for (int x = lane; x < g.nx; x += 32) {
         Vox v;
         v.b = b;
@@ -258,37 +264,47 @@ k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float*
         }
         res += (double)p * (double)p;
     }
-    __shared__ double red[3][256];
-    red[0][threadIdx.x] = data;
-    red[1][threadIdx.x] = kin;
-    red[2][threadIdx.x] = res;
-    __syncthreads();
+    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem);
+    red[0][kb.tx()] = data;
+    red[1][kb.tx()] = kin;
+    red[2][kb.tx()] = res;
+    kb.sync();
     for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
-        __syncthreads();
+        if ((int)kb.tx() < w)
+            for (int k = 0; k < 3; ++k) red[k][kb.tx()] += red[k][kb.tx() + w];
+        kb.sync();
     }
-    if (threadIdx.x < 3)
-        partials[((long long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+    if (kb.tx() < 3)
+        partials[((long long)b * kb.gx() + kb.bx()) * 3 + kb.tx()] = red[kb.tx()][0];
 }
 
+
+#ifndef META_BODIES_ONLY
+template <int NDIM>
 __global__ void __launch_bounds__(256)
-k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
+k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ J, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    const int b = blockIdx.x;
-    __shared__ double red[3][256];
+    __shared__ __align__(16) unsigned char st[kCostSmem];
+    body_cost_partials<HwBlk, NDIM>(HwBlk{st}, g, sl, states, u, J, partials);
+}
+#endif
+
+template <class K>
+__device__ __forceinline__ void body_cost_final(const K& kb, int nblk, Coefs cf, const double* partials, double* cost) {
+    const int b = kb.bx();
+    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem);
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+    for (int i = kb.tx(); i < nblk; i += kb.ndx())
         for (int k = 0; k < 3; ++k) acc[k] += partials[((long long)b * nblk + i) * 3 + k];
-    for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
-    __syncthreads();
+    for (int k = 0; k < 3; ++k) red[k][kb.tx()] = acc[k];
+    kb.sync();
     for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
-        __syncthreads();
+        if ((int)kb.tx() < w)
+            for (int k = 0; k < 3; ++k) red[k][kb.tx()] += red[k][kb.tx() + w];
+        kb.sync();
     }
-    if (threadIdx.x == 0) {
+    if (kb.tx() == 0) {
         const double lam = (double)cf.lambda[b], rho = (double)cf.rho[b];
         cost[b * 3 + 0] = red[0][0];
         cost[b * 3 + 1] = lam * red[1][0];
@@ -296,18 +312,23 @@ k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* co
     }
 }
 
+
+#ifndef META_BODIES_ONLY
+__global__ void __launch_bounds__(256)
+k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    __shared__ __align__(16) unsigned char st[kCostSmem];
+    body_cost_final<HwBlk>(HwBlk{st}, nblk, cf, partials, cost);
+}
+#endif
+
 // Adjoint start from given gradients w.r.t. (I_T, p_T): record of step T-1
 // (and the raw adjoints of the Eulerian steps).  FROM_J: the cost's start,
 // I^_T = I_T - J with J (contiguous) in gI1, p^_T = 0.
-template <int NDIM, bool FROM_J>
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
-           const float* __restrict__ u, const float* __restrict__ gI1,
-           const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec,
-           float* Ihp, float* php, float* rawI, float* rawP) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    const Vox v = vox_of<NDIM>(g);
+template <class K, int NDIM, bool FROM_J>
+__device__ __forceinline__ void body_adj_init(const K& kb, Geom g, Coefs cf, Slots sl, const float* states, const float* u, const float* gI1, const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp, float* php, float* rawI, float* rawP) {
+    const Vox v = vox_of<NDIM>(g, kb);
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
@@ -325,18 +346,30 @@ k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     }
 }
 
+
+#ifndef META_BODIES_ONLY
+template <int NDIM, bool FROM_J>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ gI1, const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php, float* rawI, float* rawP) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    body_adj_init<HwBlk, NDIM, FROM_J>(HwBlk{nullptr}, g, cf, sl, states, u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP);
+}
+#endif
+
 // 2-D adjoint step t with R = 1 on a 32 x 16 tile (two rows per thread), all
 // operands staged: the records (cell, f_y, f_x, I^', p~^, div^) and I_t, p_t
 // over the tile grown by one voxel, by cp.async.  Each source of the grown tile is packed once into the float4
 // (g_y, g_x, I^', p~^) (pack_g); each node then sums 9 branch-free products.
-__device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const float* rb,
+template <class K>
+__device__ __forceinline__ void transport_r1_2d(const K& kb, const Geom& g, float dt, const float* rb,
                                                 long long sl, const float* It, const float* pt,
                                                 float* vh0, float* vh1, float* Ihpb,
                                                 float* phpb, float* smem) {
     constexpr int TX = 32, TY = 16, W = TX + 8, HR = TY + 2, WIN = W * HR;
     constexpr int RX = TX + 2, RY = TY + 2, NR = RX * RY;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+    const int x0 = kb.bx() * TX, y0 = kb.by() * TY;
+    const int tx = kb.tx(), ty = kb.ty(), tid = ty * kPX + tx;
     float* sC = smem;            // cell bits
     float* sF0 = sC + WIN;
     float* sF1 = sF0 + WIN;
@@ -347,16 +380,16 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
     float* sPt = sIt + WIN;
     float4* sQ = reinterpret_cast<float4*>(sPt + WIN);  // [NR]: g_y, g_x, I^', p~^
     const int xl = x0 - 4, yl = y0 - 1;
-    stage_async<W, HR>(sC, rb, g, xl, yl);
-    stage_async<W, HR>(sF0, rb + sl, g, xl, yl);
-    stage_async<W, HR>(sF1, rb + 2 * sl, g, xl, yl);
-    stage_async<W, HR>(sI, rb + 3 * sl, g, xl, yl);
-    stage_async<W, HR>(sP, rb + 4 * sl, g, xl, yl);
-    stage_async<W, HR>(sD, rb + 5 * sl, g, xl, yl);
-    stage_async<W, HR>(sIt, It, g, xl, yl);
-    stage_async<W, HR>(sPt, pt, g, xl, yl);
+    stage_async<W, HR>(sC, rb, g, xl, yl, tid);
+    stage_async<W, HR>(sF0, rb + sl, g, xl, yl, tid);
+    stage_async<W, HR>(sF1, rb + 2 * sl, g, xl, yl, tid);
+    stage_async<W, HR>(sI, rb + 3 * sl, g, xl, yl, tid);
+    stage_async<W, HR>(sP, rb + 4 * sl, g, xl, yl, tid);
+    stage_async<W, HR>(sD, rb + 5 * sl, g, xl, yl, tid);
+    stage_async<W, HR>(sIt, It, g, xl, yl, tid);
+    stage_async<W, HR>(sPt, pt, g, xl, yl, tid);
     cp_async_wait_all();
-    __syncthreads();
+    kb.sync();
     for (int i = tid; i < NR; i += kPX * kPY) {
         const int ry = i / RX, rx = i - ry * RX;
         const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
@@ -369,7 +402,7 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
         }
         sQ[i] = q;
     }
-    __syncthreads();
+    kb.sync();
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {  // rows ty and ty + 8 of the tile
         const int ly = ty + rr * kPY;
@@ -419,19 +452,25 @@ __device__ __forceinline__ void transport_r1_2d(const Geom& g, float dt, const f
 
 // Records of step t from raw adjoints I^_{t+1}, p^_{t+1} (pitched), once the
 // forward segment holding step t has been recomputed (step checkpointing).
-template <int NDIM>
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
-              const float* __restrict__ u, const float* __restrict__ rawI,
-              const float* __restrict__ rawP, float* rec) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    const Vox v = vox_of<NDIM>(g);
+template <class K, int NDIM>
+__device__ __forceinline__ void body_adj_records(const K& kb, Geom g, Coefs cf, Slots sl, const float* states, const float* u, const float* rawI, const float* rawP, float* rec) {
+    const Vox v = vox_of<NDIM>(g, kb);
     if (!v.ok) return;
     const long long o = gidx(g, v.z, v.y, v.x);
     const long long ob = (long long)v.b * g.inst + o;
     build_record_any<NDIM>(g, cf, sl.st1, sl.ut1, v, o, rawI[ob], rawP[ob], states, u, rec);
 }
+
+
+#ifndef META_BODIES_ONLY
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ rawI, const float* __restrict__ rawP, float* rec) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    body_adj_records<HwBlk, NDIM>(HwBlk{nullptr}, g, cf, sl, states, u, rawI, rawP, rec);
+}
+#endif
 
 // S^T and v^ of adjoint step t at one node v, from the records of step t in
 // global memory, for R > 1 (R = 1 has staged paths below).
@@ -439,10 +478,11 @@ k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
 //   R > RMAX: the node's own source scatters its 2^d corner terms with
 //     atomics into the zeroed Ihp / php (bounded work; summation order not
 //     fixed; info bit).
-template <int NDIM>
-__device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, const Slots& sl,
-                                               const float* __restrict__ states, int R,
-                                               const float* __restrict__ rec, float* vh,
+template <int NDIM, class K>
+__device__ __forceinline__ void transport_node(const K& kb, const Geom& g, const Coefs& cf,
+                                               const Slots& sl,
+                                               const float* states, int R,
+                                               const float* rec, float* vh,
                                                float* Ihp, float* php, unsigned int* fault,
                                                const Vox& v) {
     const int b = v.b;
@@ -469,7 +509,7 @@ __device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, c
             for (int sy = lo[NDIM - 2]; sy <= hi[NDIM - 2]; ++sy) {
                 for (int sx = lo[NDIM - 1]; sx <= hi[NDIM - 1]; ++sx) {
                     const long long so = gidx(g, sz, sy, sx);
-                    const int cell = __float_as_int(__ldg(rb + so));
+                    const int cell = __float_as_int(ld_ro<K>(rb + so));
                     const int sc[3] = {NDIM == 3 ? sz : sy, NDIM == 3 ? sy : sx, sx};
                     bool hit = true;
 #pragma unroll
@@ -481,25 +521,25 @@ __device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, c
                     float w = 1.f;
 #pragma unroll
                     for (int a = 0; a < NDIM; ++a) {
-                        const float f = __ldg(rb + (1 + a) * rsl + so);
+                        const float f = ld_ro<K>(rb + (1 + a) * rsl + so);
                         w = (a == 0) ? (e[a] ? f : 1.f - f) : w * (e[a] ? f : 1.f - f);
                     }
-                    accI += w * __ldg(rI + so);
-                    accP += w * __ldg(rP + so);
+                    accI += w * ld_ro<K>(rI + so);
+                    accP += w * ld_ro<K>(rP + so);
                 }
             }
         }
         Ihp[(long long)b * g.inst + o] = accI;
         php[(long long)b * g.inst + o] = accP;
     } else {
-        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(fault, kInfoScatter);
-        const int cell = __float_as_int(__ldg(rb + o));
-        const float fI = __ldg(rI + o), fP = __ldg(rP + o);
+        if (kb.tx() == 0 && kb.ty() == 0) atomicOr(fault, kInfoScatter);
+        const int cell = __float_as_int(ld_ro<K>(rb + o));
+        const float fI = ld_ro<K>(rI + o), fP = ld_ro<K>(rP + o);
         float f[NDIM];
         long long q0 = 0;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
-            f[a] = __ldg(rb + (1 + a) * rsl + o);
+            f[a] = ld_ro<K>(rb + (1 + a) * rsl + o);
             q0 += (long long)(c[a] + cell_off(cell, a)) * st[a];
         }
         float* Isc = Ihp + (long long)b * g.inst;
@@ -521,14 +561,14 @@ __device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, c
 
     // y^ from this node's own foot, v^ = -dt y^ + D^T div^.
     const float dt = cf.dt;
-    const int cell = __float_as_int(__ldg(rb + o));
+    const int cell = __float_as_int(ld_ro<K>(rb + o));
     Feet<NDIM> F;
     int i0[NDIM];
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
         i0[a] = c[a] + cell_off(cell, a);
         F.f[a].i0 = i0[a];
-        F.f[a].f = __ldg(rb + (1 + a) * rsl + o);
+        F.f[a].f = ld_ro<K>(rb + (1 + a) * rsl + o);
         F.f[a].inside = (cell >> (24 + a)) & 1;
     }
     if constexpr (NDIM == 2)
@@ -540,7 +580,7 @@ __device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, c
     float Iv, pv, dI[NDIM], dP[NDIM];
     interp_grad<NDIM>(g, F, It, &Iv, dI);
     interp_grad<NDIM>(g, F, pt, &pv, dP);
-    const float Ihv = __ldg(rI + o), pthv = __ldg(rP + o);
+    const float Ihv = ld_ro<K>(rI + o), pthv = ld_ro<K>(rP + o);
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
         const float yh = dI[a] * Ihv + dP[a] * pthv;
@@ -550,20 +590,16 @@ __device__ __forceinline__ void transport_node(const Geom& g, const Coefs& cf, c
 
 // 2-D S^T and v^ of adjoint step t: transport_r1_2d when every per-step
 // displacement is under one voxel (R = 1), else transport_node per node.
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states,
-                  const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec,
-                  float* vh, float* Ihp, float* php, unsigned int* fault) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
+template <class K>
+__device__ __forceinline__ void body_adj_transport2d(const K& kb, Geom g, Coefs cf, int t, Slots sl, const float* states, const unsigned int* maxdisp, const float* rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     // 8 staged windows of 40 x 18 and 34 x 18 packed sources (transport_r1_2d)
-    __shared__ __align__(16) float s2[8 * 720 + 4 * 612];
+    float* s2 = reinterpret_cast<float*>(kb.smem);
     using G = GatherTile<2>;
-    const int b = blockIdx.z;
+    const int b = kb.bz();
     const int R = gather_radius(maxdisp, t, g.B, b);
     if (R == 1) {  // uniform over the CTA
         const long long rsl = (long long)g.B * g.inst;
-        transport_r1_2d(g, cf.dt, rec + (long long)b * g.inst, rsl,
+        transport_r1_2d(kb, g, cf.dt, rec + (long long)b * g.inst, rsl,
                         slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b),
                         slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b),
                         vh + (long long)b * g.inst, vh + ((long long)g.B + b) * g.inst,
@@ -573,13 +609,24 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
     for (int rr = 0; rr < 2; ++rr) {
         Vox v;
         v.b = b;
-        v.x = blockIdx.x * G::TX + threadIdx.x;
-        v.y = blockIdx.y * G::TY + threadIdx.y + rr * kPY;
+        v.x = kb.bx() * G::TX + kb.tx();
+        v.y = kb.by() * G::TY + kb.ty() + rr * kPY;
         v.z = 0;
         if (v.x >= g.nx || v.y >= g.ny) continue;
-        transport_node<2>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+        transport_node<2>(kb, g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
     }
 }
+
+
+#ifndef META_BODIES_ONLY
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    __shared__ __align__(16) unsigned char st[kTr2dSmem];
+    body_adj_transport2d<HwBlk>(HwBlk{st}, g, cf, t, sl, states, maxdisp, rec, vh, Ihp, php, fault);
+}
+#endif
 
 // 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 16 column of nodes
 // over planes [zs, zs + zc) and marches along z; each thread owns the two
@@ -706,24 +753,17 @@ __device__ __forceinline__ void transport_complete(const Geom& g, float dt, int 
         vh[((long long)a * g.B + b) * g.inst + o] = -dt * (dI[a] * Ihv + dP[a] * pthv) + dT[a];
 }
 
-__global__ void __launch_bounds__(kPX * kPY, 2)
-k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
-                  const __grid_constant__ CUtensorMap tmRecD,
-                  const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl,
-                  int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp,
-                  const float* __restrict__ rec, float* vh, float* Ihp, float* php,
-                  unsigned int* fault) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int b = blockIdx.z;
+template <class K>
+__device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensorMap& tmRecA, const CUtensorMap& tmRecD, const CUtensorMap& tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* states, const unsigned int* maxdisp, const float* rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem;
+    const int b = kb.bz();
     const int nxc = (g.nx + 31) / 32;
-    const int x0 = (blockIdx.x % nxc) * 32;
-    const int zs = (blockIdx.x / nxc) * zc;
+    const int x0 = (kb.bx() % nxc) * 32;
+    const int zs = (kb.bx() / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = blockIdx.y * 16;
+    const int y0 = kb.by() * 16;
     const int R = gather_radius(maxdisp, t, g.B, b);
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tx = kb.tx(), ty = kb.ty();
     const int tid = ty * kPX + tx;
     const int x = x0 + tx, ya = y0 + 2 * ty, yb = ya + 1;
     const bool ok_a = x < g.nx && ya < g.ny, ok_b = x < g.nx && yb < g.ny;
@@ -734,9 +774,9 @@ k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
         for (int z = zs; z < ze; ++z) {
             v.z = z;
             v.y = ya;
-            if (ok_a) transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+            if (ok_a) transport_node<3>(kb, g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
             v.y = yb;
-            if (ok_b) transport_node<3>(g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
+            if (ok_b) transport_node<3>(kb, g, cf, sl, states, R, rec, vh, Ihp, php, fault, v);
         }
         return;
     }
@@ -752,8 +792,14 @@ k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
+        if constexpr (K::kPersistent) {
+            tmap_acquire(&tmRecA);
+            tmap_acquire(&tmRecD);
+            tmap_acquire(&tmSt);
+            fence_proxy_async_global();
+        }
     }
-    __syncthreads();
+    kb.sync();
     // one thread stages plane p: records 0..5 into A, div^ and (I_t, p_t) into
     // B; planes outside the volume are never read, so no copy is made for them
     auto load_plane = [&](int p) {
@@ -777,19 +823,19 @@ k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
     if (tid == 0) load_plane(zs - 1);
     for (int p = zs - 1; p <= ze; ++p) {
         const int j = p - zs + 1;  // planes staged so far
-        __syncthreads();  // every read of the slots plane p + 1 reuses, and of Q / PP, is done
+        kb.sync();  // every read of the slots plane p + 1 reuses, and of Q / PP, is done
         if (tid == 0 && p + 1 <= ze) load_plane(p + 1);
         bool landed = true;
         if (tid < 32) landed = mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault);
-        if (__syncthreads_or(!landed)) {
+        if (kb.sync_or(!landed)) {
             // leave together, after the copy of plane p + 1 (if any) has landed
             if (tid < 32 && p + 1 <= ze)
                 mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1, fault, 100000000ull);
-            __syncthreads();
+            kb.sync();
             return;
         }
         march_pack(slotA(p), Q, PP, g, x0, y0, p, tid);
-        __syncthreads();
+        kb.sync();
         // plane p is at dz = -1 from nodes at p+1, 0 from p, +1 from p-1.  Sources
         // r = 0..3 (rows 2 ty - 1 .. 2 ty + 2 of the column), columns dx = 0..2
         // (x - 1 .. x + 1), each loaded and weighted along x and z once; each
@@ -847,7 +893,25 @@ k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA,
         a0_b = ap_b;
         ap_b = make_float2(0.f, 0.f);
     }
+    if constexpr (K::kPersistent) {
+        kb.sync();  // every wait on the barriers has returned
+        if (tid == 0) {
+            mbar_inval(&bar[0]);
+            mbar_inval(&bar[1]);
+        }
+    }
 }
+
+
+#ifndef META_BODIES_ONLY
+__global__ void __launch_bounds__(kPX * kPY, 2)
+k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA, const __grid_constant__ CUtensorMap tmRecD, const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    body_adj_transport3d<HwBlk>(HwBlk{smem_raw}, tmRecA, tmRecD, tmSt, g, cf, t, sl, zc, states, maxdisp, rec, vh, Ihp, php, fault);
+}
+#endif
 
 // Shared tail of the gradp kernels.  mode 0: the record of step t-1; mode 3:
 // raw I^_t, p^_t into rawI / rawP (step t-1 lies in a forward segment that is
@@ -868,7 +932,10 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
         const long long ci = cidx(g, v);
         if (mode == 1) {
             const float lam = cf.lambda[v.b], rho = cf.rho[v.b];
-            out0[ci] = phv + lam * (2.f * kg + 2.f * rho * p0v);
+            // every rounding explicit: the same bits from every kernel that runs
+            // this tail (a contraction into FMAs is free to differ between them)
+            const float reg = __fadd_rn(__fmul_rn(2.f, kg), __fmul_rn(__fmul_rn(2.f, rho), p0v));
+            out0[ci] = __fadd_rn(phv, __fmul_rn(lam, reg));
         } else {
             out0[ci] = phv;
             if (gI0) gI0[ci] = Ihv;
@@ -880,45 +947,44 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
 // (both components), I_t and p_t staged with a one-voxel halo by cp.async.  When the record of step t-1 has R = 1,
 // u_{t-1} and p_{t-1} are staged too and the record is built from them (the
 // same expressions as build_record).
-template <bool PDET>
-__global__ void __launch_bounds__(kPX * kPY)
-k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
-              const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
-              const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI,
-              float* rawP, float* out0, float* gI0) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
+template <class K, bool PDET>
+__device__ __forceinline__ void body_adj_gradp2d(const K& kb, Geom g, Coefs cf, int t, int mode, Slots sl, const float* states, const float* u, const unsigned int* maxdisp, const float* mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     constexpr int TY = 2 * kPY, W = kPX + 8, HR = TY + 2;
-    __shared__ __align__(16) float sM0[HR * W], sM1[HR * W], sI[HR * W], sP[HR * W];
-    __shared__ __align__(16) float sU0[HR * W], sU1[HR * W], sPp[HR * W];
-    const int b = blockIdx.z;
-    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * TY;
+    float* sM0 = reinterpret_cast<float*>(kb.smem);
+    float* sM1 = sM0 + HR * W;
+    float* sI = sM1 + HR * W;
+    float* sP = sI + HR * W;
+    float* sU0 = sP + HR * W;
+    float* sU1 = sU0 + HR * W;
+    float* sPp = sU1 + HR * W;
+    const int b = kb.bz();
+    const int x0 = kb.bx() * kPX, y0 = kb.by() * TY;
     const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
     const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     const float* m0 = mh + (long long)b * g.inst;
     const float* m1 = mh + ((long long)g.B + b) * g.inst;
     const int Rprev = (t > 0) ? gather_radius(maxdisp, t - 1, g.B, b) : 0;
     const bool staged_rec = (mode == 0) && Rprev == 1;  // uniform over the CTA
-    stage_async<W, HR>(sM0, m0, g, x0 - 4, y0 - 1);
-    stage_async<W, HR>(sM1, m1, g, x0 - 4, y0 - 1);
-    stage_async<W, HR>(sI, It, g, x0 - 4, y0 - 1);
-    stage_async<W, HR>(sP, pt, g, x0 - 4, y0 - 1);
+    stage_async<W, HR>(sM0, m0, g, x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
+    stage_async<W, HR>(sM1, m1, g, x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
+    stage_async<W, HR>(sI, It, g, x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
+    stage_async<W, HR>(sP, pt, g, x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
     if (staged_rec) {
         stage_async<W, HR>(sU0, slice_of(u, g, ((long long)sl.ut1 * 2 + 0) * g.B + b), g,
-                           x0 - 4, y0 - 1);
+                           x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
         stage_async<W, HR>(sU1, slice_of(u, g, ((long long)sl.ut1 * 2 + 1) * g.B + b), g,
-                           x0 - 4, y0 - 1);
+                           x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
         stage_async<W, HR>(sPp, slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b), g,
-                           x0 - 4, y0 - 1);
+                           x0 - 4, y0 - 1, kb.ty() * kPX + kb.tx());
     }
     cp_async_wait_all();
-    __syncthreads();
+    kb.sync();
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const int ty = threadIdx.y + rr * kPY;
+        const int ty = kb.ty() + rr * kPY;
         Vox v;
         v.b = b;
-        v.x = x0 + threadIdx.x;
+        v.x = x0 + kb.tx();
         v.y = y0 + ty;
         v.z = 0;
         v.ok = v.x < g.nx && v.y < g.ny;
@@ -926,7 +992,7 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
         const int x = v.x, y = v.y;
         const int o = y * g.P + x;
         const long long ob = (long long)b * g.inst + o;
-        const int c = (ty + 1) * W + threadIdx.x + 4;
+        const int c = (ty + 1) * W + kb.tx() + 4;
         float phv = php[ob];
         float Ihv = Ihp[ob];
         if (Rprev > GatherTile<2>::RMAX) {
@@ -934,26 +1000,27 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
             php[ob] = 0.f;
         }
         // axis 0 (y): stride W in the staged tile
+        // roundings explicit: the same bits from every kernel that runs this body
         const float g0 = 0.5f * (sI[c + (y < g.ny - 1 ? W : 0)] - sI[c - (y > 0 ? W : 0)]);
-        phv += sM0[c] * g0;
+        phv = __fmaf_rn(sM0[c], g0, phv);
         {
             float r = 0.f;
-            if (y >= 1) r += 0.5f * (sM0[c - W] * sP[c - W]);
-            if (y == g.ny - 1) r += 0.5f * (sM0[c] * sP[c]);
-            if (y <= g.ny - 2) r -= 0.5f * (sM0[c + W] * sP[c + W]);
-            if (y == 0) r -= 0.5f * (sM0[c] * sP[c]);
-            Ihv += r;
+            if (y >= 1) r = __fmaf_rn(0.5f, __fmul_rn(sM0[c - W], sP[c - W]), r);
+            if (y == g.ny - 1) r = __fmaf_rn(0.5f, __fmul_rn(sM0[c], sP[c]), r);
+            if (y <= g.ny - 2) r = __fmaf_rn(-0.5f, __fmul_rn(sM0[c + W], sP[c + W]), r);
+            if (y == 0) r = __fmaf_rn(-0.5f, __fmul_rn(sM0[c], sP[c]), r);
+            Ihv = __fadd_rn(Ihv, r);
         }
         // axis 1 (x)
         const float g1 = 0.5f * (sI[c + (x < g.nx - 1 ? 1 : 0)] - sI[c - (x > 0 ? 1 : 0)]);
-        phv += sM1[c] * g1;
+        phv = __fmaf_rn(sM1[c], g1, phv);
         {
             float r = 0.f;
-            if (x >= 1) r += 0.5f * (sM1[c - 1] * sP[c - 1]);
-            if (x == g.nx - 1) r += 0.5f * (sM1[c] * sP[c]);
-            if (x <= g.nx - 2) r -= 0.5f * (sM1[c + 1] * sP[c + 1]);
-            if (x == 0) r -= 0.5f * (sM1[c] * sP[c]);
-            Ihv += r;
+            if (x >= 1) r = __fmaf_rn(0.5f, __fmul_rn(sM1[c - 1], sP[c - 1]), r);
+            if (x == g.nx - 1) r = __fmaf_rn(0.5f, __fmul_rn(sM1[c], sP[c]), r);
+            if (x <= g.nx - 2) r = __fmaf_rn(-0.5f, __fmul_rn(sM1[c + 1], sP[c + 1]), r);
+            if (x == 0) r = __fmaf_rn(-0.5f, __fmul_rn(sM1[c], sP[c]), r);
+            Ihv = __fadd_rn(Ihv, r);
         }
         if (staged_rec) {
             // record of step t-1 from the staged u_{t-1}, p_{t-1}
@@ -991,23 +1058,29 @@ k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restri
         }
         float kg = 0.f;
         if (t == 0 && mode == 1) {
-            kg += g0 * slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o];
-            kg += g1 * slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o];
+            kg = __fmaf_rn(g0, slice_of(u, g, ((long long)sl.u0 * 2 + 0) * g.B + b)[o], kg);
+            kg = __fmaf_rn(g1, slice_of(u, g, ((long long)sl.u0 * 2 + 1) * g.B + b)[o], kg);
         }
         gradp_tail<2, PDET>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, sP[c], states, u, rec, rawI,
                             rawP, out0, gI0);
     }
 }
 
-template <int NDIM, bool PDET>
+
+#ifndef META_BODIES_ONLY
+template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
-k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states,
-            const float* __restrict__ u, const unsigned int* __restrict__ maxdisp,
-            const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI,
-            float* rawP, float* out0, float* gI0) {
+k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    const Vox v = vox_of<NDIM>(g);
+    __shared__ __align__(16) unsigned char st[kGradp2dSmem];
+    body_adj_gradp2d<HwBlk, PDET>(HwBlk{st}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
+}
+#endif
+
+template <class K, int NDIM, bool PDET>
+__device__ __forceinline__ void body_adj_gradp(const K& kb, Geom g, Coefs cf, int t, int mode, Slots sl, const float* states, const float* u, const unsigned int* maxdisp, const float* mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
+    const Vox v = vox_of<NDIM>(g, kb);
     if (!v.ok) return;
     const int b = v.b;
     const long long o = gidx(g, v.z, v.y, v.x);
@@ -1028,20 +1101,32 @@ k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict
     for (int a = 0; a < NDIM; ++a) {
         const float* ma = mh + ((long long)a * g.B + b) * g.inst;
         const float ga = cdiff(It, o, s[a], c[a], n[a]);
-        phv += ma[o] * ga;
-        // D_a^T (m^_a p) at this node
+        phv = __fmaf_rn(ma[o], ga, phv);
+        // D_a^T (m^_a p) at this node (roundings explicit, as in the 2-D kernel)
         float r = 0.f;
         const long long sa = s[a];
-        if (c[a] >= 1) r += 0.5f * (ma[o - sa] * pt[o - sa]);
-        if (c[a] == n[a] - 1) r += 0.5f * (ma[o] * pt[o]);
-        if (c[a] <= n[a] - 2) r -= 0.5f * (ma[o + sa] * pt[o + sa]);
-        if (c[a] == 0) r -= 0.5f * (ma[o] * pt[o]);
-        Ihv += r;
-        if (t == 0 && mode == 1) kg += ga * slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b)[o];
+        if (c[a] >= 1) r = __fmaf_rn(0.5f, __fmul_rn(ma[o - sa], pt[o - sa]), r);
+        if (c[a] == n[a] - 1) r = __fmaf_rn(0.5f, __fmul_rn(ma[o], pt[o]), r);
+        if (c[a] <= n[a] - 2) r = __fmaf_rn(-0.5f, __fmul_rn(ma[o + sa], pt[o + sa]), r);
+        if (c[a] == 0) r = __fmaf_rn(-0.5f, __fmul_rn(ma[o], pt[o]), r);
+        Ihv = __fadd_rn(Ihv, r);
+        if (t == 0 && mode == 1)
+            kg = __fmaf_rn(ga, slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b)[o], kg);
     }
     gradp_tail<NDIM, PDET>(g, cf, t, mode, sl, v, o, Ihv, phv, kg, pt[o], states, u, rec, rawI,
                            rawP, out0, gI0);
 }
+
+
+#ifndef META_BODIES_ONLY
+template <int NDIM, bool PDET>
+__global__ void __launch_bounds__(kPX * kPY)
+k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    body_adj_gradp<HwBlk, NDIM, PDET>(HwBlk{nullptr}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
+}
+#endif
 
 // R = cof(M) - Id for M = Id + B, B = dt rho Du at one voxel (the
 // derivative of det M is cof M), column e only, written without the
@@ -1078,6 +1163,7 @@ __device__ __forceinline__ void cof_minus_id_col(const float (&B)[NDIM][NDIM], i
 // transport added the identity part of cof, D_a^T div^; this kernel adds
 // sum_e D_e^T (div^ R_ae), R = cof(M) - Id, evaluating M at the neighbours
 // that D_e^T reads from u_t (slot sl.ut), each thread for its own node.
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float* __restrict__ rec,
@@ -1132,6 +1218,7 @@ k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float*
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) slice_of(vh, g, (long long)a * g.B + b)[o] += acc[a];
 }
+#endif
 
 // Adjoint of one Eulerian step (I' = I - dt sum_a (D_a I) v_a + dt mu p,
 // p' = p - dt sum_a D_a (p v_a), v = -rho u_t) up to v, from the raw adjoints
@@ -1140,6 +1227,7 @@ k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float*
 //   php = p^' + dt mu I^' + sum_a f^_a v_a,    f^_a = -dt D_a^T p^'
 //   v^_a = -dt I^' D_a I + f^_a p
 // The blur of v^ and k_adj_gradp (raw mode) complete the step.
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_euler_adj(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
@@ -1182,10 +1270,12 @@ k_euler_adj(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     slice_of(Ihp, g, b)[o] = Inew;
     slice_of(php, g, b)[o] = pnew;
 }
+#endif
 
 // The Eulerian momentum step of the hybrid scheme, transposed, added to what
 // the semi-Lagrangian transport left for its image step:
 //   php += p^' + sum_a f^_a v_a,   v^_a += f^_a p,   f^_a = -dt D_a^T p^'
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_hybrid_p(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
@@ -1212,9 +1302,11 @@ k_hybrid_p(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
     }
     slice_of(php, g, b)[o] += pnew;
 }
+#endif
 
 }  // namespace
 
+#ifndef META_BODIES_ONLY
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
@@ -1222,6 +1314,55 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl
                         const unsigned int* maxdisp, float* rec, float* Ihp, float* php,
                         float* rawI, float* rawP, double* partials, int nblk, double* cost,
                         cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_COSTP;
+        e.ndim = ndim;
+        e.grid = dim3(nblk, g.B);
+        e.bx = 256;
+        e.by = 1;
+        e.smem = kCostSmem;
+        e.a.g = g;
+        e.a.sl = sl;
+        e.a.c[0] = states;
+        e.a.c[1] = u;
+        e.a.c[2] = J;
+        e.a.d[0] = partials;
+        r->push_back(e);
+        PRec f{};
+        f.kind = PK_ADJINIT;
+        f.ndim = ndim;
+        f.sub = 1;
+        f.grid = ndim == 2 ? pgrid<2>(g) : pgrid<3>(g);
+        f.bx = kPX;
+        f.by = kPY;
+        f.a.g = g;
+        f.a.cf = c;
+        f.a.sl = sl;
+        f.a.c[0] = states;
+        f.a.c[1] = u;
+        f.a.c[2] = J;
+        f.a.cmd = maxdisp;
+        f.a.w[0] = rec;
+        f.a.w[1] = Ihp;
+        f.a.w[2] = php;
+        f.a.w[3] = rawI;
+        f.a.w[4] = rawP;
+        r->push_back(f);
+        PRec h{};
+        h.kind = PK_COSTF;
+        h.ndim = ndim;
+        h.grid = dim3(g.B);
+        h.bx = 256;
+        h.by = 1;
+        h.smem = kCostSmem;
+        h.a.n = nblk;
+        h.a.cf = c;
+        h.a.d[0] = partials;
+        h.a.d[1] = cost;
+        r->push_back(h);
+        return cudaSuccess;
+    }
     const dim3 grid(nblk, g.B);
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
@@ -1245,6 +1386,7 @@ cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots
                             const float* states, const float* u, const float* gI1,
                             const float* gp1, const unsigned int* maxdisp, float* rec, float* Ihp,
                             float* php, float* rawI, float* rawP, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_init<2, false>, pgrid<2>(g), blk, 0, st, g, c, sl, states,
@@ -1258,6 +1400,24 @@ cudaError_t launch_adj_init(const Geom& g, int ndim, const Coefs& c, const Slots
 cudaError_t launch_adj_records(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                                const float* states, const float* u, const float* rawI,
                                const float* rawP, float* rec, cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_ADJREC;
+        e.ndim = ndim;
+        e.grid = ndim == 2 ? pgrid<2>(g) : pgrid<3>(g);
+        e.bx = kPX;
+        e.by = kPY;
+        e.a.g = g;
+        e.a.cf = c;
+        e.a.sl = sl;
+        e.a.c[0] = states;
+        e.a.c[1] = u;
+        e.a.c[2] = rawI;
+        e.a.c[3] = rawP;
+        e.a.w[0] = rec;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_records<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
@@ -1272,6 +1432,37 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
                                  const CUtensorMap* maps, const float* states,
                                  const unsigned int* maxdisp, const float* rec, float* vh,
                                  float* Ihp, float* php, unsigned int* fault, cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_TRANS;
+        e.ndim = ndim;
+        e.bx = kPX;
+        e.by = kPY;
+        if (ndim == 2) {
+            e.grid = gather_grid2d(g);
+            e.smem = kTr2dSmem;
+        } else {
+            const int zc = g.zct > 0 ? g.zct : march_chunk(g, 2, 2, 16);
+            e.grid = dim3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
+            e.smem = kMarchSmem;
+            e.a.zc = zc;
+            e.ntm = 3;
+            for (int k = 0; k < 3; ++k) e.tm[k] = maps[k];
+        }
+        e.a.g = g;
+        e.a.cf = c;
+        e.a.t = t;
+        e.a.sl = sl;
+        e.a.c[0] = states;
+        e.a.cmd = maxdisp;
+        e.a.c[1] = rec;
+        e.a.w[0] = vh;
+        e.a.w[1] = Ihp;
+        e.a.w[2] = php;
+        e.a.fault = fault;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
         META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, 0, st, g, c, t, sl,
@@ -1295,6 +1486,38 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
                              const unsigned int* maxdisp, const float* mh, float* Ihp, float* php,
                              float* rec, float* rawI, float* rawP, float* out0, float* gI0,
                              cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_GRADP;
+        e.ndim = ndim;
+        e.sub = c.pdet;
+        e.bx = kPX;
+        e.by = kPY;
+        if (ndim == 2) {
+            e.grid = dim3((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B);
+            e.smem = kGradp2dSmem;
+        } else {
+            e.grid = pgrid<3>(g);
+        }
+        e.a.g = g;
+        e.a.cf = c;
+        e.a.t = t;
+        e.a.mode = mode;
+        e.a.sl = sl;
+        e.a.c[0] = states;
+        e.a.c[1] = u;
+        e.a.cmd = maxdisp;
+        e.a.c[2] = mh;
+        e.a.w[0] = Ihp;
+        e.a.w[1] = php;
+        e.a.w[2] = rec;
+        e.a.w[3] = rawI;
+        e.a.w[4] = rawP;
+        e.a.w[5] = out0;
+        e.a.w[6] = gI0;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
         const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B);
@@ -1311,6 +1534,7 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
 
 cudaError_t launch_adj_jacT(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* u, const float* rec, float* vh, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_adj_jacT<2>, pgrid<2>(g), blk, 0, st, g, c, sl, u, rec, vh));
@@ -1323,6 +1547,7 @@ cudaError_t launch_euler_adj(const Geom& g, int ndim, const Coefs& c, const Slot
                              const float* states, const float* u, const float* rawI,
                              const float* rawP, float* Ihp, float* php, float* vh,
                              cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_euler_adj<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
@@ -1336,6 +1561,7 @@ cudaError_t launch_euler_adj(const Geom& g, int ndim, const Coefs& c, const Slot
 cudaError_t launch_hybrid_p(const Geom& g, int ndim, const Coefs& c, const Slots& sl,
                             const float* states, const float* u, const float* rawP, float* php,
                             float* vh, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_hybrid_p<2>, pgrid<2>(g), blk, 0, st, g, c, sl, states, u,
@@ -1345,5 +1571,7 @@ cudaError_t launch_hybrid_p(const Geom& g, int ndim, const Coefs& c, const Slots
                                    rawP, php, vh));
     return cudaSuccess;
 }
+
+#endif  // META_BODIES_ONLY
 
 }  // namespace meta

@@ -443,8 +443,19 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
 // buffer that holds w_T.
 meta_status run_forward(Ctx& c, const Coefs& cf, const float** wT = nullptr) {
     const Layout& L = c.L;
-    META_TRY(cudaMemsetAsync(c.maxdisp, 0,
-                             sizeof(unsigned int) * kMaxdispStride * (size_t)L.T * L.g.B, c.st));
+    const size_t md_words = (size_t)kMaxdispStride * L.T * L.g.B;
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_ZERO;
+        e.grid = dim3((unsigned)((md_words + 1023) / 1024));
+        e.bx = 256;
+        e.by = 1;
+        e.a.md = c.maxdisp;
+        e.a.n = (int)md_words;
+        r->push_back(e);
+    } else {
+        META_TRY(cudaMemsetAsync(c.maxdisp, 0, sizeof(unsigned int) * md_words, c.st));
+    }
     for (int t = 0; t < L.T; ++t) {
         const meta_status s = forward_step(c, cf, t, L.state_slot(t, L.seg_of(t)),
                                            L.forward_out_slot(t), L.u_slot(t), true);
@@ -672,6 +683,12 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
 }
 
 }  // namespace
+
+std::vector<PRec>*& recorder() {
+    static thread_local std::vector<PRec>* r = nullptr;
+    return r;
+}
+
 }  // namespace meta
 
 using namespace meta;
@@ -950,6 +967,7 @@ meta_status meta_cost_and_grad(const meta_problem* prob, const float* I0, const 
 struct meta_plan {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    PersistPlan* persist = nullptr;  // meta_plan_create_persistent only
 };
 
 // Records problem k on branch k % streams of one graph (fork from a root
@@ -1156,6 +1174,96 @@ meta_status meta_plan_create_group(int n, const meta_problem* probs, const float
                            streams, nullptr, plan);
 }
 
+meta_status meta_plan_create_persistent(int n, const meta_problem* probs,
+                                        const float* const* I0, const float* const* J,
+                                        const float* const* p0, const float* const* mu,
+                                        const float* const* rho, const float* const* lambda,
+                                        double* const* cost, float* const* grad, void* const* ws,
+                                        const size_t* ws_bytes, meta_plan** plan) {
+    if (!plan) return META_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (n < 1 || !probs || !I0 || !J || !p0 || !mu || !rho || !lambda || !cost || !grad || !ws ||
+        !ws_bytes)
+        return META_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        size_t need = 0;
+        meta_status s = meta_workspace_size(&probs[k], &need);
+        if (s == META_OK) s = adjoint_scheme(&probs[k]);
+        if (s != META_OK) return s;
+        if (probs[k].scheme != META_SCHEME_SL || probs[k].p_update != META_P_UPDATE_DIV)
+            return META_ERR_UNSUPPORTED;
+        if (ws_bytes[k] < need) return META_ERR_WORKSPACE;
+        if (!grad[k]) return META_ERR_INVALID_ARG;
+    }
+    // each problem's launch sequence, recorded (nothing is launched)
+    std::vector<std::vector<PRec>> recs(n);
+    const bool timer_was_on = g_timer.on;
+    g_timer.on = false;
+    meta_status status = META_OK;
+    for (int k = 0; k < n && status == META_OK; ++k) {
+        recorder() = &recs[k];
+        status = cost_and_grad_impl(&probs[k], I0[k], J[k], p0[k], mu[k], rho[k], lambda[k],
+                                    cost[k], grad[k], ws[k], ws_bytes[k], nullptr, nullptr);
+        recorder() = nullptr;
+        // every phase reports a dependency timeout to its problem's status word
+        for (PRec& e : recs[k]) e.a.fault = static_cast<unsigned int*>(ws[k]);
+    }
+    g_timer.on = timer_was_on;
+    if (status != META_OK) return status;
+    PersistPlan* pp = nullptr;
+    {
+        const cudaError_t e = persist_build(recs, &pp);
+        if (e == cudaErrorNotSupported) return META_ERR_UNSUPPORTED;
+        if (e != cudaSuccess) return META_ERR_CUDA;
+    }
+    // one graph: clear the counters, then the persistent kernel
+    cudaStream_t st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) status = META_ERR_CUDA;
+    if (status == META_OK &&
+        cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        status = META_ERR_CUDA;
+    else if (status == META_OK) {
+        const cudaError_t e = persist_launch(pp, st, 5000000000ull, -1);
+        const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) status = META_ERR_CUDA;
+    }
+    cudaGetLastError();
+    if (status == META_OK && (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
+        status = META_ERR_CUDA;
+    if (st) cudaStreamDestroy(st);
+    meta_plan* p = status == META_OK ? new (std::nothrow) meta_plan{graph, exec} : nullptr;
+    if (!p) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        persist_free(pp);
+        return status == META_OK ? META_ERR_INVALID_ARG : status;
+    }
+    p->persist = pp;
+    *plan = p;
+    return META_OK;
+}
+
+meta_status meta_plan_status(meta_plan* plan, int clear, void* stream, unsigned int* bits) {
+    if (!plan || !bits) return META_ERR_INVALID_ARG;
+    *bits = 0u;
+    if (!plan->persist) return META_OK;
+    if (persist_status(plan->persist, clear, static_cast<cudaStream_t>(stream), bits) !=
+        cudaSuccess)
+        return META_ERR_CUDA;
+    return (*bits & 1u) ? META_ERR_TIMEOUT : META_OK;
+}
+
+meta_status meta_plan_selftest_timeout(meta_plan* plan, int hold, unsigned long long limit_ns,
+                                       void* stream) {
+    if (!plan || !plan->persist) return META_ERR_INVALID_ARG;
+    if (hold < 0 || hold >= persist_problems(plan->persist)) return META_ERR_INVALID_ARG;
+    if (limit_ns < 1000000ull || limit_ns > 2000000000ull) return META_ERR_INVALID_ARG;
+    return map_status(persist_launch(plan->persist, static_cast<cudaStream_t>(stream), limit_ns,
+                                     hold));
+}
+
 meta_status meta_plan_launch(meta_plan* plan, void* stream) {
     if (!plan) return META_ERR_INVALID_ARG;
     return map_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
@@ -1165,6 +1273,7 @@ meta_status meta_plan_destroy(meta_plan* plan) {
     if (!plan) return META_OK;
     cudaGraphExecDestroy(plan->exec);
     cudaGraphDestroy(plan->graph);
+    persist_free(plan->persist);
     delete plan;
     return META_OK;
 }

@@ -23,33 +23,28 @@ namespace meta {
 
 // KC > 0: the tap loop has KC chunks of 8 at compile time (fully unrolled,
 // taps read as immediate constant-bank operands); KC = 0: runtime taps.kp.
-template <int NDIM, bool GRADP, int KC>
-__global__ void __launch_bounds__(512)
-k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP,
-        const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0,
-        float* __restrict__ out, unsigned int* fault) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+template <class K, int NDIM, bool GRADP, int KC>
+__device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps, Geom g, int sliceI, int sliceP, int out_slice0, float* out, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
 
     const int HX = taps.r4 + 8;              // x halo (multiple of 4)
     const int LW = xpass_lw(g.txw, taps.r4); // staged row length
     const int rowsI = (NDIM == 2) ? (kRows + 2) : 36;
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * g.txw;
+    const int tid = kb.tx();
+    const int x0 = kb.bx() * g.txw;
     int y0, z0;
     if constexpr (NDIM == 2) {
-        y0 = blockIdx.y * kRows;
+        y0 = kb.by() * kRows;
         z0 = 0;
     } else {
         const int nty = (g.ny + 3) / 4;
-        y0 = (blockIdx.y % nty) * 4;
-        z0 = (blockIdx.y / nty) * 4;
+        y0 = (kb.by() % nty) * 4;
+        z0 = (kb.by() / nty) * 4;
     }
-    // GRADP: one CTA per instance b = blockIdx.z.  Plain: one CTA per slice.
-    const int b = GRADP ? (int)blockIdx.z : (int)(blockIdx.z % g.B);
+    // GRADP: one CTA per instance b = kb.bz().  Plain: one CTA per slice.
+    const int b = GRADP ? (int)kb.bz() : (int)(kb.bz() % g.B);
 
     // sub-buffers start on 128-byte boundaries (TMA destinations)
     float* sI = base;
@@ -60,22 +55,30 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
         mbar_init(bar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    kb.sync();
     if (tid == 0) {
+        if constexpr (K::kPersistent) {
+            tmap_acquire(&tmI);
+            if (GRADP) tmap_acquire(&tmP);
+            fence_proxy_async_global();
+        }
         if constexpr (GRADP) {
             mbar_arrive_expect_tx(bar, (uint32_t)((rowsI + kRows) * LW * 4));
             tma_load_box<NDIM>(sI, &tmI, bar, x0 - HX, y0 - 1, z0 - 1, sliceI + b);
             tma_load_box<NDIM>(sP, &tmP, bar, x0 - HX, y0, z0, sliceP + b);
         } else {
             mbar_arrive_expect_tx(bar, (uint32_t)(kRows * LW * 4));
-            tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)blockIdx.z);
+            tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)kb.bz());
         }
     }
     // warp 0 waits (bounded) while the others sleep in the barrier; the CTA
     // leaves together if the wait ran out
     bool landed = true;
     if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
-    if (__syncthreads_or(!landed)) return;
+    if (kb.sync_or(!landed)) return;
+    if constexpr (K::kPersistent) {
+        if (tid == 0) mbar_inval(bar);  // every wait on it has returned
+    }
 
     const int ncomp = GRADP ? NDIM : 1;
     if constexpr (GRADP) {
@@ -87,10 +90,10 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
         const float inv_lw4 = 1.f / (float)LW4;
         const int lane = tid & 31;
         // the CTA has txw / 8 x 16 threads, so its last warp may hold 16 lanes
-        const int wlast = min(31, (int)blockDim.x - 1 - (tid & ~31));
+        const int wlast = min(31, (int)kb.ndx() - 1 - (tid & ~31));
         const unsigned wmask = wlast == 31 ? 0xffffffffu : ((2u << wlast) - 1u);
         // a warp-uniform trip count: every lane takes part in the shuffles
-        for (int base = 0; base < total; base += blockDim.x) {
+        for (int base = 0; base < total; base += kb.ndx()) {
             const int idx = min(base + tid, total - 1);  // lanes past the end repeat the last
             // idx < 2^12, so the rounded float quotient is the exact integer one
             const int row = (int)(((float)idx + 0.5f) * inv_lw4);
@@ -152,7 +155,7 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
                 *reinterpret_cast<float4*>(sM + (a * kRows + row) * LW + c) =
                     make_float4(mo[a][0], mo[a][1], mo[a][2], mo[a][3]);
         }
-        __syncthreads();
+        kb.sync();
     }
 
     // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`,
@@ -222,7 +225,7 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
             }
         }
         if (row_ok) {
-            const int slice = GRADP ? (out_slice0 + a * g.B + b) : (out_slice0 + (int)blockIdx.z);
+            const int slice = GRADP ? (out_slice0 + a * g.B + b) : (out_slice0 + (int)kb.bz());
             float* o = out + (long long)slice * g.inst + gidx(g, z, y, x);
             if (x < g.P) *reinterpret_cast<float4*>(o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
             if (x + 4 < g.P)
@@ -231,44 +234,51 @@ k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtenso
     }
 }
 
-// AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
-template <int NDIM, int AXIS, int KC>
-__global__ void __launch_bounds__(256)
-k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g,
-          int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul,
-          float* __restrict__ out, unsigned int* fault) {
+
+#ifndef META_BODIES_ONLY
+template <int NDIM, bool GRADP, int KC>
+__global__ void __launch_bounds__(512)
+k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{smem_raw}, tmI, tmP, taps, g, sliceI, sliceP, out_slice0, out, fault);
+}
+#endif
+
+// AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
+template <class K, int NDIM, int AXIS, int KC>
+__device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm, const Taps& taps, Geom g, int in_slice0, int out_slice0, const float* scale, float scale_mul, float* out, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* s = reinterpret_cast<float*>(smem_raw + 128);
 
-    const int tid = threadIdx.x;
+    const int tid = kb.tx();
     const int tx = tid & 31;
     const int ta = tid >> 5;
-    const int x0 = blockIdx.x * kTXS;
-    const int slice = blockIdx.z;           // comp * B + b
+    const int x0 = kb.bx() * kTXS;
+    const int slice = kb.bz();           // comp * B + b
     const int b = slice % g.B;
     // tile of L = g.ly or g.lz outputs along the axis, L / kBA warps
     int a0, y, z, n_axis, L;
     if constexpr (NDIM == 2) {
         L = g.ly;
-        a0 = blockIdx.y * L;
+        a0 = kb.by() * L;
         y = 0;
         z = 0;
         n_axis = g.ny;
     } else if constexpr (AXIS == 1) {
         L = g.ly;
         const int nt = (g.ny + L - 1) / L;
-        a0 = (blockIdx.y % nt) * L;
-        z = blockIdx.y / nt;
+        a0 = (kb.by() % nt) * L;
+        z = kb.by() / nt;
         y = 0;
         n_axis = g.ny;
     } else {
         L = g.lz;
         const int nt = (g.nz + L - 1) / L;
-        a0 = (blockIdx.y % nt) * L;
-        y = blockIdx.y / nt;
+        a0 = (kb.by() % nt) * L;
+        y = kb.by() / nt;
         z = 0;
         n_axis = g.nz;
     }
@@ -276,8 +286,12 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
         mbar_init(bar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    kb.sync();
     if (tid == 0) {
+        if constexpr (K::kPersistent) {
+            tmap_acquire(&tm);
+            fence_proxy_async_global();
+        }
         mbar_arrive_expect_tx(bar, (uint32_t)(kTXS * (L + taps.kp) * 4));
         if constexpr (NDIM == 2)
             tma_load_3d(s, &tm, bar, x0, a0 - taps.r, in_slice0 + slice);
@@ -290,7 +304,10 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     // leaves together if the wait ran out
     bool landed = true;
     if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
-    if (__syncthreads_or(!landed)) return;
+    if (kb.sync_or(!landed)) return;
+    if constexpr (K::kPersistent) {
+        if (tid == 0) mbar_inval(bar);  // every wait on it has returned
+    }
 
     const float* src = s + (ta * kBA) * kTXS + tx;
     float acc[kBA];
@@ -363,10 +380,23 @@ k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps t
     }
 }
 
+
+#ifndef META_BODIES_ONLY
+template <int NDIM, int AXIS, int KC>
+__global__ void __launch_bounds__(256)
+k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g, int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul, float* __restrict__ out, unsigned int* fault) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    body_strided<HwBlk, NDIM, AXIS, KC>(HwBlk{smem_raw}, tm, taps, g, in_slice0, out_slice0, scale, scale_mul, out, fault);
+}
+#endif
+
 // Self-test of the failure path: one CTA arms an mbarrier for 16 bytes that no
 // copy ever delivers and waits on it exactly as the blur kernels wait on their
 // TMA tiles, with a short limit.  The wait runs out, latches kFaultTmaTimeout
 // in *fault and the CTA returns; nothing faults and nothing is left in flight.
+#ifndef META_BODIES_ONLY
 __global__ void __launch_bounds__(64) k_wait_selftest(unsigned int* fault, unsigned long long limit_ns) {
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
@@ -380,8 +410,11 @@ __global__ void __launch_bounds__(64) k_wait_selftest(unsigned int* fault, unsig
     if (tid < 32) landed = mbar_wait_bounded(&bar, 0, fault, limit_ns);
     if (__syncthreads_or(!landed)) return;
 }
+#endif
 
+#ifndef META_BODIES_ONLY
 cudaError_t launch_wait_selftest(unsigned int* fault, unsigned long long limit_ns, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     k_wait_selftest<<<1, 64, 0, st>>>(fault, limit_ns);
     return cudaGetLastError();
 }
@@ -444,6 +477,32 @@ static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP
 cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
                          const Taps& taps, const Geom& g, int sliceI, int sliceP, int out_slice0,
                          int nslices, float* out, unsigned int* fault, cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_XPASS;
+        e.ndim = ndim;
+        e.sub = gradp ? 1 : 0;
+        e.kc = taps.kp / 8;
+        e.grid = dim3((g.nx + g.txw - 1) / g.txw,
+                      ndim == 2 ? (g.ny + kRows - 1) / kRows : ((g.ny + 3) / 4) * ((g.nz + 3) / 4),
+                      gradp ? g.B : nslices);
+        e.bx = xpass_threads(g.txw);
+        e.by = 1;
+        e.smem = xpass_smem(ndim, gradp, g.txw, taps.r4);
+        e.a.g = g;
+        e.a.i0 = sliceI;
+        e.a.i1 = sliceP;
+        e.a.i2 = out_slice0;
+        e.a.w[0] = out;
+        e.a.fault = fault;
+        e.ntm = 2;
+        e.tm[0] = tmI;
+        e.tm[1] = tmP;
+        e.has_taps = 1;
+        e.taps = taps;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     if (ndim == 2)
         return gradp ? launch_xpass_t<2, true>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
                                                nslices, out, fault, st)
@@ -506,6 +565,38 @@ cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps
                            const Geom& g, int in_slice0, int out_slice0, int nslices,
                            const float* scale, float scale_mul, float* out, unsigned int* fault,
                            cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        const int L = (ndim == 3 && axis == 0) ? g.lz : g.ly;
+        unsigned gy;
+        if (ndim == 2)
+            gy = (g.ny + L - 1) / L;
+        else if (axis == 1)
+            gy = ((g.ny + L - 1) / L) * g.nz;
+        else
+            gy = ((g.nz + L - 1) / L) * g.ny;
+        PRec e{};
+        e.kind = PK_STRIDED;
+        e.ndim = ndim;
+        e.sub = axis;
+        e.kc = taps.kp / 8;
+        e.grid = dim3((g.nx + kTXS - 1) / kTXS, gy, nslices);
+        e.bx = L / kBA * 32;
+        e.by = 1;
+        e.smem = strided_smem(L, taps.kp);
+        e.a.g = g;
+        e.a.i0 = in_slice0;
+        e.a.i1 = out_slice0;
+        e.a.c[0] = scale;
+        e.a.f0 = scale_mul;
+        e.a.w[0] = out;
+        e.a.fault = fault;
+        e.ntm = 1;
+        e.tm[0] = tm;
+        e.has_taps = 1;
+        e.taps = taps;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     if (ndim == 2)
         return launch_strided_t<2, 0>(tm, taps, g, in_slice0, out_slice0, nslices, scale,
                                       scale_mul, out, fault, st);
@@ -515,5 +606,7 @@ cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps
     return launch_strided_t<3, 0>(tm, taps, g, in_slice0, out_slice0, nslices, scale, scale_mul,
                                   out, fault, st);
 }
+
+#endif  // META_BODIES_ONLY
 
 }  // namespace meta

@@ -285,6 +285,25 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// A tensor map that lives in global memory (the persistent kernel's table,
+// written by the host before the launch) is made visible to the TMA unit by an
+// acquire fence of the tensormap proxy, once per thread that issues copies
+// with it.  Tensor maps passed as kernel parameters need none.
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses to global memory (and
+// those it has acquired from other CTAs) before its later async-proxy (TMA)
+// accesses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Ends an mbarrier's life, so that its shared memory may be reused (the next
+// tile of the persistent kernel may run a body that stores data there).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Plain arrival (no transaction bytes): completes the phase of a barrier
 // initialised with count 1 when no copy is issued for it.
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -309,6 +328,67 @@ __device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Block context of a kernel body.  The bodies of the kernels read their block
+// and thread indices, block and grid shapes, barriers and dynamic shared memory
+// through it, so that one body serves two launch forms:
+//  * HwBlk: an ordinary launch, everything from the hardware built-ins (the
+//    generated code is that of a plain kernel);
+//  * VBlk: one tile of a launch replayed inside the persistent kernel
+//    (meta_persist.cu), whose CTA runs the tiles of many launches one after
+//    another: indices and shapes are the replayed launch's, and the barrier is
+//    the named barrier 1 over the first nthr threads (the tile's threads; the
+//    persistent CTA may have more).
+struct HwBlk {
+    unsigned char* smem;
+    static constexpr bool kPersistent = false;
+    __device__ __forceinline__ int bx() const { return blockIdx.x; }
+    __device__ __forceinline__ int by() const { return blockIdx.y; }
+    __device__ __forceinline__ int bz() const { return blockIdx.z; }
+    __device__ __forceinline__ int tx() const { return threadIdx.x; }
+    __device__ __forceinline__ int ty() const { return threadIdx.y; }
+    __device__ __forceinline__ int ndx() const { return blockDim.x; }
+    __device__ __forceinline__ int gx() const { return gridDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int sync_or(int p) const { return __syncthreads_or(p); }
+};
+
+struct VBlk {
+    unsigned char* smem;
+    int bx_, by_, bz_, tx_, ty_, ndx_, gx_, nthr;
+    static constexpr bool kPersistent = true;
+    __device__ __forceinline__ int bx() const { return bx_; }
+    __device__ __forceinline__ int by() const { return by_; }
+    __device__ __forceinline__ int bz() const { return bz_; }
+    __device__ __forceinline__ int tx() const { return tx_; }
+    __device__ __forceinline__ int ty() const { return ty_; }
+    __device__ __forceinline__ int ndx() const { return ndx_; }
+    __device__ __forceinline__ int gx() const { return gx_; }
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+    }
+    __device__ __forceinline__ int sync_or(int p) const {
+        int r;
+        asm volatile(
+            "{\n\t.reg .pred q, s;\n\t"
+            "setp.ne.s32 q, %1, 0;\n\t"
+            "bar.red.or.pred s, 1, %2, q;\n\t"
+            "selp.s32 %0, 1, 0, s;\n\t}"
+            : "=r"(r)
+            : "r"(p), "r"(nthr)
+            : "memory");
+        return r;
+    }
+};
+
+// Read-only global load: through the non-coherent cache in an ordinary launch;
+// a plain load in the persistent kernel, whose buffers change between tiles
+// (its gpu-scope acquire invalidates L1 before a tile reads another's output).
+template <class K>
+__device__ __forceinline__ float ld_ro(const float* p) {
+    if constexpr (K::kPersistent) return *p;
+    else return __ldg(p);
 }
 
 __device__ __forceinline__ float4 lds4(const float* p) {

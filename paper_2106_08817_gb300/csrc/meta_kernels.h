@@ -3,7 +3,72 @@
 
 #include "meta_common.cuh"
 
+#include <vector>
+
 namespace meta {
+
+// ---------------------------------------------------------------- recording
+// Launches of one call, recorded instead of launched (meta_persist.cu replays
+// them as phases of one persistent kernel).  While recorder() points to a
+// vector, each launcher below of the semi-Lagrangian path appends one record
+// per kernel launch (and run_forward one per memset) and launches nothing.
+enum PKind {
+    PK_ZERO = 0,   // zero n 32-bit words at md
+    PK_PACK,       // k_pack
+    PK_XPASS,      // k_xpass (sub: GRADP)
+    PK_STRIDED,    // k_strided (sub: AXIS)
+    PK_ADVECT,     // k_advect2d / 3d (sub: PDET)
+    PK_COSTP,      // k_cost_partials
+    PK_ADJINIT,    // k_adj_init (sub: FROM_J)
+    PK_COSTF,      // k_cost_final
+    PK_ADJREC,     // k_adj_records
+    PK_TRANS,      // k_adj_transport2d / 3d
+    PK_GRADP,      // k_adj_gradp2d / k_adj_gradp (sub: PDET)
+    PK_COUNT
+};
+
+// Every argument any recorded kernel takes; each kind reads its own fields.
+struct PArgs {
+    Geom g;
+    Coefs cf;
+    Slots sl;
+    int t, mode, zc, i0, i1, i2, n;
+    float f0;
+    const float* c[4];
+    float* w[7];
+    double* d[2];
+    unsigned int* md;     // max displacement per step (written by the advect)
+    const unsigned int* cmd;  // the same, read
+    unsigned int* fault;  // workspace status word
+};
+
+struct PRec {
+    int kind, ndim, sub, kc;  // kc: tap chunks of 8 (taps.kp / 8)
+    dim3 grid;
+    int bx, by;               // threads of the recorded block (x, y)
+    size_t smem;              // shared memory the body needs
+    PArgs a;
+    int ntm;                  // tensor maps used (by value)
+    CUtensorMap tm[3];
+    int has_taps;
+    Taps taps;
+};
+
+std::vector<PRec>*& recorder();
+
+// The persistent kernel's plan (meta_persist.cu): the recorded launches of
+// every problem as device tables, and the control block of one launch.
+struct PersistPlan;
+cudaError_t persist_build(const std::vector<std::vector<PRec>>& recs, PersistPlan** out);
+// Clears the counters and launches the kernel on st; dependency waits give up
+// after limit_ns; hold >= 0 withholds the completion of that problem's first
+// phase (self-test of the bounded waits).
+cudaError_t persist_launch(PersistPlan* p, cudaStream_t st, unsigned long long limit_ns, int hold);
+cudaError_t persist_status(PersistPlan* p, int clear, cudaStream_t st, unsigned* bits);
+void persist_free(PersistPlan* p);
+int persist_problems(const PersistPlan* p);
+long long persist_tiles(const PersistPlan* p);
+int persist_grid(const PersistPlan* p);
 
 // Blur passes (meta_blur.cu).
 size_t xpass_smem(int ndim, bool gradp, int txw, int r4);

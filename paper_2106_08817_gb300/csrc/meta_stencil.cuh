@@ -16,17 +16,21 @@ struct Vox {
     bool ok;
 };
 
-template <int NDIM>
-__device__ __forceinline__ Vox vox_of(const Geom& g) {
+template <int NDIM, class K>
+__device__ __forceinline__ Vox vox_of(const Geom& g, const K& kb) {
     Vox v;
     const int nyt = (g.ny + kPY - 1) / kPY;
-    const int zq = (NDIM == 3) ? div_nyt(g, blockIdx.y) : 0;
-    v.b = blockIdx.z;
-    v.x = blockIdx.x * kPX + threadIdx.x;
-    v.y = ((int)blockIdx.y - zq * nyt) * kPY + threadIdx.y;
+    const int zq = (NDIM == 3) ? div_nyt(g, kb.by()) : 0;
+    v.b = kb.bz();
+    v.x = kb.bx() * kPX + kb.tx();
+    v.y = (kb.by() - zq * nyt) * kPY + kb.ty();
     v.z = zq;
     v.ok = v.x < g.nx && v.y < g.ny && v.z < g.nz;
     return v;
+}
+template <int NDIM>
+__device__ __forceinline__ Vox vox_of(const Geom& g) {
+    return vox_of<NDIM>(g, HwBlk{nullptr});
 }
 
 template <int NDIM>
@@ -73,9 +77,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 template <int W, int ROWS>
 __device__ __forceinline__ void stage_async(float* dst, const float* __restrict__ src,
-                                            const Geom& g, int xlo, int ylo) {
+                                            const Geom& g, int xlo, int ylo, int tid) {
     constexpr int NC4 = W / 4;
-    const int tid = threadIdx.y * kPX + threadIdx.x;
     for (int i = tid; i < ROWS * NC4; i += kPX * kPY) {
         const int r = i / NC4, c = i - r * NC4;
         const int y = ylo + r, x = xlo + 4 * c;

@@ -19,12 +19,9 @@ namespace {
 
 // ------------------------------------------------------------------ kernels
 
-template <int NDIM>
-__global__ void __launch_bounds__(kPX * kPY)
-k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    const Vox v = vox_of<NDIM>(g);
+template <class K, int NDIM>
+__device__ __forceinline__ void body_pack(const K& kb, Geom g, const float* I0, const float* p0, float* dI, float* dP) {
+    const Vox v = vox_of<NDIM>(g, kb);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
     const long long ci = cidx(g, v);
@@ -32,6 +29,18 @@ k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float
     dP[o] = p0[ci];
 }
 
+
+#ifndef META_BODIES_ONLY
+template <int NDIM>
+__global__ void __launch_bounds__(kPX * kPY)
+k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    body_pack<HwBlk, NDIM>(HwBlk{nullptr}, g, I0, p0, dI, dP);
+}
+#endif
+
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, float* I1, float* p1) {
@@ -44,36 +53,39 @@ k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, flo
     if (I1) I1[ci] = sI[o];
     if (p1) p1[ci] = sP[o];
 }
+#endif
 
 // 2-D advect on a 32 x 16 tile, two rows per thread (y and y + 8): u staged
 // with a one-voxel halo, I_t and p_t with a four-voxel halo (feet whose cell
 // leaves it read global memory).
 constexpr int kAdvHalo = 4;
 constexpr int kAdvTY = 2 * kPY;  // rows per tile
+constexpr int kAdvW = kPX + 2 * kAdvHalo;      // 40: staged row length
+constexpr int kAdvHU = kAdvTY + 2;             // 18: staged rows of u
+constexpr int kAdvHI = kAdvTY + 2 * kAdvHalo;  // 24: staged rows of I, p
+// shared memory of the 2-D advect: u (two components), I_t, p_t and the CTA max
+constexpr int kAdv2dSmem = (2 * kAdvHU + 2 * kAdvHI) * kAdvW * 4 + 16;
 
-template <bool PDET>
-__global__ void __launch_bounds__(kPX * kPY)
-k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
-           const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    constexpr int W = kPX + 2 * kAdvHalo;        // 40
-    constexpr int HU = kAdvTY + 2;               // 18
-    constexpr int HI = kAdvTY + 2 * kAdvHalo;    // 24
-    __shared__ __align__(16) float sU0[HU * W], sU1[HU * W], sI[HI * W], sP[HI * W];
-    const int b = blockIdx.z;
-    const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kAdvTY;
+template <class K, bool PDET>
+__device__ __forceinline__ void body_advect2d(const K& kb, Geom g, Coefs cf, int t, Slots sl, float* states, const float* u, unsigned int* maxdisp) {
+    constexpr int W = kAdvW, HU = kAdvHU, HI = kAdvHI;
+    float* sU0 = reinterpret_cast<float*>(kb.smem);
+    float* sU1 = sU0 + HU * W;
+    float* sI = sU1 + HU * W;
+    float* sP = sI + HI * W;
+    const int b = kb.bz();
+    const int x0 = kb.bx() * kPX, y0 = kb.by() * kAdvTY;
     const float* u0 = slice_of(u, g, ((long long)sl.ut * 2 + 0) * g.B + b);
     const float* u1 = slice_of(u, g, ((long long)sl.ut * 2 + 1) * g.B + b);
     const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
     const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
-    stage_async<W, HU>(sU0, u0, g, x0 - kAdvHalo, y0 - 1);
-    stage_async<W, HU>(sU1, u1, g, x0 - kAdvHalo, y0 - 1);
-    stage_async<W, HI>(sI, It, g, x0 - kAdvHalo, y0 - kAdvHalo);
-    stage_async<W, HI>(sP, pt, g, x0 - kAdvHalo, y0 - kAdvHalo);
+    stage_async<W, HU>(sU0, u0, g, x0 - kAdvHalo, y0 - 1, kb.ty() * kPX + kb.tx());
+    stage_async<W, HU>(sU1, u1, g, x0 - kAdvHalo, y0 - 1, kb.ty() * kPX + kb.tx());
+    stage_async<W, HI>(sI, It, g, x0 - kAdvHalo, y0 - kAdvHalo, kb.ty() * kPX + kb.tx());
+    stage_async<W, HI>(sP, pt, g, x0 - kAdvHalo, y0 - kAdvHalo, kb.ty() * kPX + kb.tx());
     cp_async_wait_all();
-    __syncthreads();
-    const int x = x0 + threadIdx.x;
+    kb.sync();
+    const int x = x0 + kb.tx();
     float dmax = 0.f;
     const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
     const float dtrho = dt * rho;
@@ -81,10 +93,10 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
     float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const int ty = threadIdx.y + rr * kPY;
+        const int ty = kb.ty() + rr * kPY;
         const int y = y0 + ty;
         if (x >= g.nx || y >= g.ny) continue;
-        const int ui = (ty + 1) * W + threadIdx.x + kAdvHalo;
+        const int ui = (ty + 1) * W + kb.tx() + kAdvHalo;
         const float d0 = disp_of(dtrho, sU0[ui]);
         const float d1 = disp_of(dtrho, sU1[ui]);
         float du = 0.f;
@@ -117,15 +129,27 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
         I1[o] = Iw + (dt * mu) * pw;
     }
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
-    __shared__ unsigned int s_m;
-    if (threadIdx.x == 0 && threadIdx.y == 0) s_m = 0u;
-    __syncthreads();
+    unsigned int& s_m = *reinterpret_cast<unsigned int*>(sP + HI * W);
+    if (kb.tx() == 0 && kb.ty() == 0) s_m = 0u;
+    kb.sync();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
-    if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(&s_m, m);
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0 && s_m != 0u)
+    if ((kb.tx() & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    kb.sync();
+    if (kb.tx() == 0 && kb.ty() == 0 && s_m != 0u)
         atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
+
+
+#ifndef META_BODIES_ONLY
+template <bool PDET>
+__global__ void __launch_bounds__(kPX * kPY)
+k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    __shared__ __align__(16) unsigned char st[kAdv2dSmem];
+    body_advect2d<HwBlk, PDET>(HwBlk{st}, g, cf, t, sl, states, u, maxdisp);
+}
+#endif
 
 // 3-D advect: a CTA owns a 32 x 8 column over planes [zs, zs + zc) and
 // marches along z.  Plane p of u (three components) and of I_t, p_t, with a
@@ -139,22 +163,18 @@ constexpr int kASlot = 3 * kAUS + 2 * kAIS;            // floats per ring slot
 constexpr int kAChunks = (3 * kAUR + 2 * kAIR) * (kAW / 4);
 constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
 constexpr int kARing = 4;                              // plane slots
-constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float);
+constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float) + 16;  // + the CTA max
 
-template <bool PDET>
-__global__ void __launch_bounds__(kPX * kPY)
-k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states,
-           const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
-    pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
-    extern __shared__ __align__(16) float sm[];
-    const int b = blockIdx.z;
+template <class K, bool PDET>
+__device__ __forceinline__ void body_advect3d(const K& kb, Geom g, Coefs cf, int t, Slots sl, int zc, float* states, const float* u, unsigned int* maxdisp) {
+    float* sm = reinterpret_cast<float*>(kb.smem);
+    const int b = kb.bz();
     const int nxc = (g.nx + 31) / 32;
-    const int x0 = (blockIdx.x % nxc) * 32;
-    const int zs = (blockIdx.x / nxc) * zc;
+    const int x0 = (kb.bx() % nxc) * 32;
+    const int zs = (kb.bx() / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = blockIdx.y * 8;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int y0 = kb.by() * 8;
+    const int tx = kb.tx(), ty = kb.ty();
     const int tid = ty * kPX + tx;
     const int x = x0 + tx, y = y0 + ty;
     const bool col_ok = x < g.nx && y < g.ny;
@@ -212,11 +232,11 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
 #pragma unroll
     for (int i = 0; i < 3; ++i) load_plane(q[i], zs - 1 + i);
     for (int z = zs; z < ze; ++z) {
-        __syncthreads();  // every read of the slot of plane z-2 (now q[3]) is done
+        kb.sync();  // every read of the slot of plane z-2 (now q[3]) is done
         if (z + 2 <= ze) load_plane(q[3], z + 2);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+1 landed
-        __syncthreads();
+        kb.sync();
         const float* sm1 = q[0];
         const float* s0 = q[1];
         const float* sp1 = q[2];
@@ -283,14 +303,26 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
-    __shared__ unsigned int s_m;
+    unsigned int& s_m = *reinterpret_cast<unsigned int*>(sm + kARing * kASlot);
     if (tid == 0) s_m = 0u;
-    __syncthreads();
+    kb.sync();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
     if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
-    __syncthreads();
+    kb.sync();
     if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
 }
+
+
+#ifndef META_BODIES_ONLY
+template <bool PDET>
+__global__ void __launch_bounds__(kPX * kPY)
+k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    body_advect3d<HwBlk, PDET>(HwBlk{smem_raw}, g, cf, t, sl, zc, states, u, maxdisp);
+}
+#endif
 
 // Eulerian (HYBRID = false) and hybrid steps of Sec. 2.3.  With
 // v = -rho u (slot sl.ut) and the central differences D of the scheme:
@@ -300,6 +332,7 @@ k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states
 // from state slot sl.st into sl.st1.  Plain L1-cached loads of the 2d
 // neighbours.  The hybrid records its per-step max displacement, the gather
 // window of its adjoint's image step; the Eulerian adjoint needs none.
+#ifndef META_BODIES_ONLY
 template <int NDIM, bool HYBRID>
 __global__ void __launch_bounds__(kPX * kPY)
 k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
@@ -351,6 +384,7 @@ k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
             atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + blockIdx.z), s_m);
     }
 }
+#endif
 
 // Deformation of the grid (the deformation grids of Fig. 1-2, Sec. 3): phi_0 = Id and
 // phi_{t+1} = phi_t o (Id - dt v_t), i.e. phi_{t+1}(x) = S(y) phi_t at the same
@@ -358,6 +392,7 @@ k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
 // w_t = phi_t - Id: the multilinear interpolant reproduces Id at a clamped foot,
 // so w_{t+1}(x) = (y - x) + S(y) w_t.  w_t is slice a * B + b of win (NULL at
 // t = 0, where w_0 = 0), w_{t+1} goes to the same slices of wout.
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_deform(Geom g, Coefs cf, int su, const float* __restrict__ u, const float* __restrict__ win,
@@ -384,11 +419,13 @@ k_deform(Geom g, Coefs cf, int su, const float* __restrict__ u, const float* __r
         slice_of(wout, g, (long long)a * g.B + b)[o] = w;
     }
 }
+#endif
 
 // The deformation out of the pitched w = phi - Id: phi (contiguous
 // [B][NDIM][N], nullable) = w, and jac (contiguous [B][N], nullable) =
 // det(D phi) = det(Id + D w), D the central difference inside and the
 // one-sided difference at the two edges of each axis.
+#ifndef META_BODIES_ONLY
 template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_deform_out(Geom g, const float* __restrict__ w, float* __restrict__ phi,
@@ -427,13 +464,30 @@ k_deform_out(Geom g, const float* __restrict__ w, float* __restrict__ phi,
     }
     jac[(long long)b * N + xi] = det;
 }
+#endif
 
 }  // namespace
 
+#ifndef META_BODIES_ONLY
 // ---------------------------------------------------------------- launchers
 
 cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p0, float* dI,
                         float* dP, cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_PACK;
+        e.ndim = ndim;
+        e.grid = ndim == 2 ? pgrid<2>(g) : pgrid<3>(g);
+        e.bx = kPX;
+        e.by = kPY;
+        e.a.g = g;
+        e.a.c[0] = I0;
+        e.a.c[1] = p0;
+        e.a.w[0] = dI;
+        e.a.w[1] = dP;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_pack<2>, pgrid<2>(g), blk, 0, st, g, I0, p0, dI, dP));
@@ -444,6 +498,7 @@ cudaError_t launch_pack(const Geom& g, int ndim, const float* I0, const float* p
 
 cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float* sP, float* I1,
                           float* p1, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_unpack<2>, pgrid<2>(g), blk, 0, st, g, sI, sP, I1, p1));
@@ -454,6 +509,32 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
 
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp, cudaStream_t st) {
+    if (std::vector<PRec>* r = recorder()) {
+        PRec e{};
+        e.kind = PK_ADVECT;
+        e.ndim = ndim;
+        e.sub = c.pdet;
+        e.bx = kPX;
+        e.by = kPY;
+        if (ndim == 2) {
+            e.grid = dim3((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B);
+            e.smem = kAdv2dSmem;
+        } else {
+            const int zc = g.zca > 0 ? g.zca : march_chunk(g, 4, 4);
+            e.grid = dim3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
+            e.smem = kAdvMarchSmem;
+            e.a.zc = zc;
+        }
+        e.a.g = g;
+        e.a.cf = c;
+        e.a.t = t;
+        e.a.sl = sl;
+        e.a.w[0] = states;
+        e.a.c[0] = u;
+        e.a.md = maxdisp;
+        r->push_back(e);
+        return cudaSuccess;
+    }
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
         const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B);
@@ -474,6 +555,7 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
 
 cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const float* u,
                           const float* win, float* wout, cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_deform<2>, pgrid<2>(g), blk, 0, st, g, c, su, u, win, wout));
@@ -484,6 +566,7 @@ cudaError_t launch_deform(const Geom& g, int ndim, const Coefs& c, int su, const
 
 cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* phi, float* jac,
                               cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(k_deform_out<2>, pgrid<2>(g), blk, 0, st, g, w, phi, jac));
@@ -495,6 +578,7 @@ cudaError_t launch_deform_out(const Geom& g, int ndim, const float* w, float* ph
 cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                          bool hybrid, float* states, const float* u, unsigned int* maxdisp,
                          cudaStream_t st) {
+    if (recorder()) return cudaErrorNotSupported;  // not replayable by the persistent kernel
     const dim3 blk(kPX, kPY);
     if (ndim == 2)
         META_CHECK_LAUNCH(launch_k(hybrid ? k_euler<2, true> : k_euler<2, false>, pgrid<2>(g), blk,
@@ -504,5 +588,7 @@ cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, int t, const S
                                    0, st, g, c, t, sl, states, u, maxdisp));
     return cudaGetLastError();
 }
+
+#endif  // META_BODIES_ONLY
 
 }  // namespace meta

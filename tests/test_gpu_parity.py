@@ -549,7 +549,7 @@ def test_deformation_with_the_det_update(meta):
 ])
 def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_update, scheme):
     """Per-step displacements of 0.2 to 17 voxels: the gather window grows with
-    them (R = 1 + floor(max|d|)) and, beyond 8 voxels in 2-D or 3 in 3-D, the
+    them (R = 1 + floor(max|d|)) and, from 8 voxels in 2-D or 4 in 3-D on, the
     adjoint switches to the atomic scatter.  These inputs stay well conditioned
     in FP32 (an FP32 torch implementation of the same scheme is within 3e-5)."""
     I0, _ = phantoms.random_fields(seed, 1, dims)
@@ -561,6 +561,27 @@ def test_large_displacements(meta, dims, seed, scale, T, sigma, mu, rho, lam, p_
     assert max(per_step) > 9 and min(per_step) < 1
     check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
     assert check_cost_grad.status & 2  # the scatter fallback ran
+
+
+@pytest.mark.parametrize("p_update,scheme", [("div", "sl"), ("det", "sl"), ("div", "hybrid")])
+def test_3d_gather_window_up_to_four_voxels_is_deterministic(meta, p_update, scheme):
+    """3-D per-step displacements 0.18, 0.67, 1.15, 1.88, 3.76 voxels (windows R = 1,
+    1, 2, 2, 4): every step transposes the interpolation by the fixed-order gather (no
+    scatter bit), the gradient meets the oracle, and two calls agree bit for bit."""
+    dims, T, sigma, mu, rho, lam = (14, 16, 18), 5, 1.5, 0.1, 1.0, 1e-3
+    I0, _ = phantoms.random_fields(31, 1, dims)
+    J, _ = phantoms.random_fields(32, 1, dims)
+    p0 = smooth_p(33, (1,) + dims, 220.0)
+    _, _, u = oracle.shoot(I0[0], p0[0], T, sigma, mu, rho, want_u=True, p_update=p_update,
+                           scheme=scheme)
+    per_step = [np.abs(u[k]).max() * rho / T for k in range(T)]
+    assert 3.0 < max(per_step) < 4.0 and min(per_step) < 1.0
+    check_cost_grad(meta, I0, J, p0, T, sigma, mu, rho, lam, p_update=p_update, scheme=scheme)
+    assert check_cost_grad.status & 2 == 0  # no step fell back to the scatter
+    runs = [meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), T, sigma, mu, rho, lam,
+                               p_update=p_update, scheme=scheme) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
 
 
 def test_shoot_adjoint_and_autograd_function(meta):
