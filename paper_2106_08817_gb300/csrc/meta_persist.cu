@@ -74,15 +74,15 @@ int tiles_per_item(int kind, int ndim) {
         case PK_PACK:
         case PK_ADJINIT:
         case PK_ADJREC:
-            return 8;
+            return 16;
         case PK_GRADP:
-            return ndim == 3 ? 8 : 4;
+            return ndim == 3 ? 16 : 8;
         case PK_ADVECT:
         case PK_TRANS:
-            return ndim == 3 ? 1 : 4;
+            return ndim == 3 ? 1 : 8;
         case PK_XPASS:
         case PK_STRIDED:
-            return 2;
+            return 4;
         default:
             return 1;
     }
@@ -106,6 +106,11 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // block barrier that precedes it are visible to whoever acquires the counter.
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned n) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(n) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
     return *reinterpret_cast<const volatile unsigned*>(p);
@@ -305,7 +310,7 @@ k_persist(const DPhase* __restrict__ phases, const long long* __restrict__ first
         if (tid == 0 && nx < total) {  // the next item: descriptor and a first dependency read
             const int pn = scan(nx);
             fetch_phase(&sph[slot ^ 1], phases + pn);
-            early = ld_acquire(&ctl->done[phases[pn].inst]);
+            early = ld_relaxed(&ctl->done[phases[pn].inst]);  // no ordering: the tiles go on
         }
         const int t0 = (int)(s_item[slot] - P.first) * P.per;
         const int t1 = min(t0 + P.per, P.ntiles);
@@ -330,13 +335,16 @@ k_persist(const DPhase* __restrict__ phases, const long long* __restrict__ first
             // publish this item's tiles (release at gpu scope, after the barrier)
             if (!(P.inst == hold && P.need == 0u))
                 red_release_add(&ctl->done[P.inst], (unsigned)(t1 - t0));
-            int go = nx < total && !ld_volatile(&ctl->abort);
+            int go = nx < total;
             if (go) {
-                // the next item's phase (scanned above): its dependencies were read with
-                // acquire semantics before this item's tiles; wait if they were not met
+                // the next item's phase (scanned above): its dependencies were read before
+                // this item's tiles; if they were met, a fence makes that read an acquire
+                // (it also drops the SM's L1 lines), else wait with acquire loads
                 const DPhase& N = phases[ph];
                 if (early < N.need)
                     go = wait_done(&ctl->done[N.inst], N.need, ctl, limit_ns, N.a.fault);
+                else
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
             }
             asm volatile("cp.async.wait_all;" ::: "memory");
             s_item[slot ^ 1] = nx;
