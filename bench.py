@@ -573,6 +573,16 @@ def measure_lbfgs(meta, w, I0, J, mu, rho, lam, ckpt, iters=10, m=5, step=0.02):
     import time
     import torch
     p0 = torch.zeros_like(I0)
+    # one cost_and_grad on the same inputs and workspace shape (the unit of the ratio)
+    for _ in range(2):
+        meta.cost_and_grad(I0, J, p0, w.T, w.sigma, mu, rho, lam, ckpt=ckpt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        meta.cost_and_grad(I0, J, p0, w.T, w.sigma, mu, rho, lam, ckpt=ckpt)
+    torch.cuda.synchronize()
+    ms_cg = (time.perf_counter() - t0) * 1e3 / 5
+    meta.lbfgs_minimize(I0, J, p0, w.T, w.sigma, mu, rho, lam, iters=1, m=m, h0=step, ckpt=ckpt)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, hist, done = meta.lbfgs_minimize(I0, J, p0, w.T, w.sigma, mu, rho, lam, iters=iters, m=m,
@@ -589,6 +599,10 @@ def measure_lbfgs(meta, w, I0, J, mu, rho, lam, ckpt, iters=10, m=5, step=0.02):
     return {"iters": iters, "m": m, "h0": step,
             "mean_cost_lbfgs": [float(x) for x in hist.mean(1)],
             "mean_cost_gd": gd, "ms_per_lbfgs_iter": wall * 1e3 / iters,
+            "ms_per_cost_and_grad": ms_cg,
+            "iter_over_cost_and_grad": wall * 1e3 / iters / ms_cg,
+            "timing": "host wall clock of the whole minimize call (its first cost_and_grad "
+                      "included) over the iterations, against eager cost_and_grad calls",
             "iters_moved": [int(x) for x in done]}
 
 
@@ -885,8 +899,10 @@ def measure_side(meta, name, args, dev, flush, stream, steps=20):
     vs = w.batch * w.voxels * w.T
     peak, _ = peaks()
     value = vs / (ms * 1e-3)
+    lb = None if args.no_lbfgs else measure_lbfgs(meta, w, I0, J, mu, rho, lam, ck, iters=5)
     return {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "config": dict(workload_config(w, name), ckpt_stride=ck, tiles=tiles),
+            "lbfgs": lb,
             "path_roofline": {"model_bytes_per_voxel_step": model_bytes_per_voxel_step(w.ndim),
                               "model_frac": value * model_bytes_per_voxel_step(w.ndim) / 1e9
                               / peak, "peak_GBps": peak},

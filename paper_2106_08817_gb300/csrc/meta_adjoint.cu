@@ -264,7 +264,7 @@ __device__ __forceinline__ void body_cost_partials(const K& kb, Geom g, Slots sl
         }
         res += (double)p * (double)p;
     }
-    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem);
+    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem());
     red[0][kb.tx()] = data;
     red[1][kb.tx()] = kin;
     red[2][kb.tx()] = res;
@@ -285,15 +285,14 @@ __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ J, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    __shared__ __align__(16) unsigned char st[kCostSmem];
-    body_cost_partials<HwBlk, NDIM>(HwBlk{st}, g, sl, states, u, J, partials);
+    body_cost_partials<HwBlk, NDIM>(HwBlk{}, g, sl, states, u, J, partials);
 }
 #endif
 
 template <class K>
 __device__ __forceinline__ void body_cost_final(const K& kb, int nblk, Coefs cf, const double* partials, double* cost) {
     const int b = kb.bx();
-    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem);
+    double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem());
     double acc[3] = {0.0, 0.0, 0.0};
     for (int i = kb.tx(); i < nblk; i += kb.ndx())
         for (int k = 0; k < 3; ++k) acc[k] += partials[((long long)b * nblk + i) * 3 + k];
@@ -318,8 +317,7 @@ __global__ void __launch_bounds__(256)
 k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    __shared__ __align__(16) unsigned char st[kCostSmem];
-    body_cost_final<HwBlk>(HwBlk{st}, nblk, cf, partials, cost);
+    body_cost_final<HwBlk>(HwBlk{}, nblk, cf, partials, cost);
 }
 #endif
 
@@ -353,7 +351,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ gI1, const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php, float* rawI, float* rawP) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_adj_init<HwBlk, NDIM, FROM_J>(HwBlk{nullptr}, g, cf, sl, states, u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP);
+    body_adj_init<HwBlk, NDIM, FROM_J>(HwBlk{}, g, cf, sl, states, u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP);
 }
 #endif
 
@@ -468,7 +466,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ rawI, const float* __restrict__ rawP, float* rec) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_adj_records<HwBlk, NDIM>(HwBlk{nullptr}, g, cf, sl, states, u, rawI, rawP, rec);
+    body_adj_records<HwBlk, NDIM>(HwBlk{}, g, cf, sl, states, u, rawI, rawP, rec);
 }
 #endif
 
@@ -593,7 +591,7 @@ __device__ __forceinline__ void transport_node(const K& kb, const Geom& g, const
 template <class K>
 __device__ __forceinline__ void body_adj_transport2d(const K& kb, Geom g, Coefs cf, int t, Slots sl, const float* states, const unsigned int* maxdisp, const float* rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     // 8 staged windows of 40 x 18 and 34 x 18 packed sources (transport_r1_2d)
-    float* s2 = reinterpret_cast<float*>(kb.smem);
+    float* s2 = reinterpret_cast<float*>(kb.smem());
     using G = GatherTile<2>;
     const int b = kb.bz();
     const int R = gather_radius(maxdisp, t, g.B, b);
@@ -623,8 +621,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    __shared__ __align__(16) unsigned char st[kTr2dSmem];
-    body_adj_transport2d<HwBlk>(HwBlk{st}, g, cf, t, sl, states, maxdisp, rec, vh, Ihp, php, fault);
+    body_adj_transport2d<HwBlk>(HwBlk{}, g, cf, t, sl, states, maxdisp, rec, vh, Ihp, php, fault);
 }
 #endif
 
@@ -755,7 +752,7 @@ __device__ __forceinline__ void transport_complete(const Geom& g, float dt, int 
 
 template <class K>
 __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensorMap& tmRecA, const CUtensorMap& tmRecD, const CUtensorMap& tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* states, const unsigned int* maxdisp, const float* rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
-    unsigned char* smem_raw = kb.smem;
+    unsigned char* smem_raw = kb.smem();
     const int b = kb.bz();
     const int nxc = (g.nx + 31) / 32;
     const int x0 = (kb.bx() % nxc) * 32;
@@ -908,8 +905,7 @@ __global__ void __launch_bounds__(kPX * kPY, 2)
 k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA, const __grid_constant__ CUtensorMap tmRecD, const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    body_adj_transport3d<HwBlk>(HwBlk{smem_raw}, tmRecA, tmRecD, tmSt, g, cf, t, sl, zc, states, maxdisp, rec, vh, Ihp, php, fault);
+    body_adj_transport3d<HwBlk>(HwBlk{}, tmRecA, tmRecD, tmSt, g, cf, t, sl, zc, states, maxdisp, rec, vh, Ihp, php, fault);
 }
 #endif
 
@@ -950,7 +946,7 @@ __device__ __forceinline__ void gradp_tail(const Geom& g, const Coefs& cf, int t
 template <class K, bool PDET>
 __device__ __forceinline__ void body_adj_gradp2d(const K& kb, Geom g, Coefs cf, int t, int mode, Slots sl, const float* states, const float* u, const unsigned int* maxdisp, const float* mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     constexpr int TY = 2 * kPY, W = kPX + 8, HR = TY + 2;
-    float* sM0 = reinterpret_cast<float*>(kb.smem);
+    float* sM0 = reinterpret_cast<float*>(kb.smem());
     float* sM1 = sM0 + HR * W;
     float* sI = sM1 + HR * W;
     float* sP = sI + HR * W;
@@ -1073,8 +1069,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    __shared__ __align__(16) unsigned char st[kGradp2dSmem];
-    body_adj_gradp2d<HwBlk, PDET>(HwBlk{st}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
+    body_adj_gradp2d<HwBlk, PDET>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
 }
 #endif
 
@@ -1124,7 +1119,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_adj_gradp<HwBlk, NDIM, PDET>(HwBlk{nullptr}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
+    body_adj_gradp<HwBlk, NDIM, PDET>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
 }
 #endif
 
@@ -1366,19 +1361,19 @@ cudaError_t launch_cost(const Geom& g, int ndim, const Coefs& c, const Slots& sl
     const dim3 grid(nblk, g.B);
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, 0, st, g, sl, states, u, J,
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<2>, grid, 256, kCostSmem, st, g, sl, states, u, J,
                                    partials));
         META_CHECK_LAUNCH(launch_k(k_adj_init<2, true>, pgrid<2>(g), blk, 0, st, g, c, sl, states,
                                    u, J, (const float*)nullptr, maxdisp, rec, Ihp, php, rawI,
                                    rawP));
     } else {
-        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, 0, st, g, sl, states, u, J,
+        META_CHECK_LAUNCH(launch_k(k_cost_partials<3>, grid, 256, kCostSmem, st, g, sl, states, u, J,
                                    partials));
         META_CHECK_LAUNCH(launch_k(k_adj_init<3, true>, pgrid<3>(g), blk, 0, st, g, c, sl, states,
                                    u, J, (const float*)nullptr, maxdisp, rec, Ihp, php, rawI,
                                    rawP));
     }
-    META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, 0, st, nblk, c, partials, cost));
+    META_CHECK_LAUNCH(launch_k(k_cost_final, g.B, 256, kCostSmem, st, nblk, c, partials, cost));
     return cudaSuccess;
 }
 
@@ -1465,7 +1460,7 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
     }
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
-        META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, 0, st, g, c, t, sl,
+        META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, kTr2dSmem, st, g, c, t, sl,
                                    states, maxdisp, rec, vh, Ihp, php, fault));
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_adj_transport3d,
@@ -1522,7 +1517,7 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
     if (ndim == 2) {
         const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + 2 * kPY - 1) / (2 * kPY), g.B);
         META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp2d<true> : k_adj_gradp2d<false>, grid, blk,
-                                   0, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
+                                   kGradp2dSmem, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
                                    rec, rawI, rawP, out0, gI0));
     } else {
         META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp<3, true> : k_adj_gradp<3, false>,

@@ -24,8 +24,8 @@ namespace meta {
 // KC > 0: the tap loop has KC chunks of 8 at compile time (fully unrolled,
 // taps read as immediate constant-bank operands); KC = 0: runtime taps.kp.
 template <class K, int NDIM, bool GRADP, int KC>
-__device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps, Geom g, int sliceI, int sliceP, int out_slice0, float* out, unsigned int* fault) {
-    unsigned char* smem_raw = kb.smem;
+__device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps, Geom g, int sliceI, int sliceP, int out_slice0, float* __restrict__ out, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem();
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
 
@@ -241,15 +241,14 @@ __global__ void __launch_bounds__(512)
 k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{smem_raw}, tmI, tmP, taps, g, sliceI, sliceP, out_slice0, out, fault);
+    body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{}, tmI, tmP, taps, g, sliceI, sliceP, out_slice0, out, fault);
 }
 #endif
 
 // AXIS is the array axis blurred: 2-D: 0 = y; 3-D: 1 = y, 0 = z.
 template <class K, int NDIM, int AXIS, int KC>
-__device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm, const Taps& taps, Geom g, int in_slice0, int out_slice0, const float* scale, float scale_mul, float* out, unsigned int* fault) {
-    unsigned char* smem_raw = kb.smem;
+__device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm, const Taps& taps, Geom g, int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul, float* __restrict__ out, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem();
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* s = reinterpret_cast<float*>(smem_raw + 128);
 
@@ -387,8 +386,7 @@ __global__ void __launch_bounds__(256)
 k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g, int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    body_strided<HwBlk, NDIM, AXIS, KC>(HwBlk{smem_raw}, tm, taps, g, in_slice0, out_slice0, scale, scale_mul, out, fault);
+    body_strided<HwBlk, NDIM, AXIS, KC>(HwBlk{}, tm, taps, g, in_slice0, out_slice0, scale, scale_mul, out, fault);
 }
 #endif
 

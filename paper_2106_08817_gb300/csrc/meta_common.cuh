@@ -341,30 +341,40 @@ __device__ __forceinline__ void pdl_trigger() {
 //    the named barrier 1 over the first nthr threads (the tile's threads; the
 //    persistent CTA may have more).
 struct HwBlk {
-    unsigned char* smem;
     static constexpr bool kPersistent = false;
-    __device__ __forceinline__ int bx() const { return blockIdx.x; }
-    __device__ __forceinline__ int by() const { return blockIdx.y; }
-    __device__ __forceinline__ int bz() const { return blockIdx.z; }
-    __device__ __forceinline__ int tx() const { return threadIdx.x; }
-    __device__ __forceinline__ int ty() const { return threadIdx.y; }
-    __device__ __forceinline__ int ndx() const { return blockDim.x; }
-    __device__ __forceinline__ int gx() const { return gridDim.x; }
+    // the dynamic shared memory of the launch (by symbol: its address is a
+    // constant of the kernel, which keeps shared addressing cheap)
+    __device__ __forceinline__ unsigned char* smem() const {
+        extern __shared__ __align__(128) unsigned char meta_dyn_smem[];
+        return meta_dyn_smem;
+    }
+    // unsigned, as the built-ins: index arithmetic (a division by a runtime tile
+    // count, say) stays unsigned and on the uniform datapath
+    __device__ __forceinline__ unsigned bx() const { return blockIdx.x; }
+    __device__ __forceinline__ unsigned by() const { return blockIdx.y; }
+    __device__ __forceinline__ unsigned bz() const { return blockIdx.z; }
+    __device__ __forceinline__ unsigned tx() const { return threadIdx.x; }
+    __device__ __forceinline__ unsigned ty() const { return threadIdx.y; }
+    __device__ __forceinline__ unsigned ndx() const { return blockDim.x; }
+    __device__ __forceinline__ unsigned gx() const { return gridDim.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ int sync_or(int p) const { return __syncthreads_or(p); }
 };
 
 struct VBlk {
-    unsigned char* smem;
     int bx_, by_, bz_, tx_, ty_, ndx_, gx_, nthr;
     static constexpr bool kPersistent = true;
-    __device__ __forceinline__ int bx() const { return bx_; }
-    __device__ __forceinline__ int by() const { return by_; }
-    __device__ __forceinline__ int bz() const { return bz_; }
-    __device__ __forceinline__ int tx() const { return tx_; }
-    __device__ __forceinline__ int ty() const { return ty_; }
-    __device__ __forceinline__ int ndx() const { return ndx_; }
-    __device__ __forceinline__ int gx() const { return gx_; }
+    __device__ __forceinline__ unsigned char* smem() const {
+        extern __shared__ __align__(128) unsigned char meta_dyn_smem[];
+        return meta_dyn_smem;
+    }
+    __device__ __forceinline__ unsigned bx() const { return (unsigned)bx_; }
+    __device__ __forceinline__ unsigned by() const { return (unsigned)by_; }
+    __device__ __forceinline__ unsigned bz() const { return (unsigned)bz_; }
+    __device__ __forceinline__ unsigned tx() const { return (unsigned)tx_; }
+    __device__ __forceinline__ unsigned ty() const { return (unsigned)ty_; }
+    __device__ __forceinline__ unsigned ndx() const { return (unsigned)ndx_; }
+    __device__ __forceinline__ unsigned gx() const { return (unsigned)gx_; }
     __device__ __forceinline__ void sync() const {
         asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
     }

@@ -8,9 +8,12 @@
 // operation runs on the device: FP64 dot products with a fixed summation order
 // (per-CTA partials over fixed chunks, then one CTA per instance), FP32 axpys
 // whose coefficients stay on the device, so a direction needs no host round
-// trip.  meta_lbfgs_minimize drives the iterations from the host: a
-// backtracking Armijo line search per instance that reads the costs of each
-// trial back (one synchronisation per trial).
+// trip.  meta_lbfgs_minimize keeps every per-instance decision on the device
+// too (the choice of direction, the Armijo test and halving of the
+// backtracking line search, stopping, the new pair's rho and gamma); the host
+// loop only launches, and reads one small block per line-search trial (how
+// many instances still search, and the costs): one read per iteration when
+// the first step is accepted.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -131,18 +134,6 @@ k_lsteep(long long N, const int* __restrict__ use, const double* __restrict__ c,
         d[o + i] = cb * g[o + i];
 }
 
-// xt[b] = x[b] + step[b] d[b]  (exactly x[b] where step[b] = 0)
-__global__ void __launch_bounds__(kLT)
-k_ltrial(long long N, const double* __restrict__ step, const float* __restrict__ x,
-         const float* __restrict__ d, float* xt) {
-    const int b = blockIdx.y;
-    const float a = (float)step[b];
-    const long long o = (long long)b * N;
-    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
-         i += (long long)gridDim.x * kLT)
-        xt[o + i] = a == 0.f ? x[o + i] : fmaf(a, d[o + i], x[o + i]);
-}
-
 // where keep[b]: xa[b] = xt[b], ga[b] = gt[b] (the accepted trial point)
 __global__ void __launch_bounds__(kLT)
 k_lkeep(long long N, const int* __restrict__ keep, const float* __restrict__ xt,
@@ -179,6 +170,109 @@ k_lpair(long long N, const int* __restrict__ moved, float* x, float* g,
     }
 }
 
+// d[b] = -d[b]
+__global__ void __launch_bounds__(kLT)
+k_lneg(long long N, int B, float* d) {
+    const int b = blockIdx.y;
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        d[o + i] = -d[o + i];
+}
+
+// Per-instance state of meta_lbfgs_minimize, all on the device (one thread
+// per instance in the kernels below).
+struct LSt {
+    double *L, *gd, *gmax, *gg, *step, *coef, *sy, *yy, *rho, *gamma, *cost;
+    int *use, *keep, *accepted, *stopped, *searching, *done;
+    unsigned long long* any;  // an instance is still searching (read by the host)
+};
+
+// After the first cost_and_grad: L = the sum of the three terms of Eq. 4.
+__global__ void k_linit(int B, LSt st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    st.L[b] = st.cost[3 * b] + st.cost[3 * b + 1] + st.cost[3 * b + 2];
+    st.stopped[b] = 0;
+    st.done[b] = 0;
+    st.gamma[b] = 1.0;
+}
+
+// The direction of iteration k, from gd = g.d, gmax = max |g|, gg = g.g: an
+// instance without a usable pair, or whose d does not descend, takes the scaled
+// steepest-descent step -h0 g / max|g| and forgets its pairs; the line search
+// starts at step 1 (step 0 and stop where there is no descent).
+__global__ void k_ldecide(int B, int m, float h0, LSt st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    int nvalid = 0;
+    for (int i = 0; i < m; ++i) nvalid += st.rho[(size_t)i * B + b] != 0.0;
+    const int use = (!st.stopped[b] && (nvalid == 0 || !(st.gd[b] < 0.0))) ? 1 : 0;
+    st.use[b] = use;
+    st.coef[b] = st.gmax[b] > 0.0 ? -(double)h0 / st.gmax[b] : 0.0;
+    if (use) {
+        st.gd[b] = st.coef[b] * st.gg[b];
+        for (int i = 0; i < m; ++i) st.rho[(size_t)i * B + b] = 0.0;  // forget
+        st.gamma[b] = 1.0;
+    }
+    st.accepted[b] = 0;
+    st.step[b] = (st.stopped[b] || !(st.gd[b] < 0.0)) ? 0.0 : 1.0;
+    if (st.step[b] == 0.0) st.stopped[b] = 1;
+    st.searching[b] = !st.stopped[b];
+}
+
+// xt[b] = x[b] + step[b] d[b] where the instance is still searching, else x[b]
+__global__ void __launch_bounds__(kLT)
+k_ltrial2(long long N, LSt st, const float* __restrict__ x, const float* __restrict__ d,
+          float* xt) {
+    const int b = blockIdx.y;
+    const float a = st.searching[b] ? (float)st.step[b] : 0.f;
+    const long long o = (long long)b * N;
+    for (long long i = (long long)blockIdx.x * kLT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * kLT)
+        xt[o + i] = a == 0.f ? x[o + i] : fmaf(a, d[o + i], x[o + i]);
+}
+
+// Armijo test of the trial (its costs in st.cost): accept the first step with
+// L(x + a d) <= L(x) + c1 a g.d, else halve it; `any` counts the instances
+// still searching (cleared before).
+__global__ void k_larmijo(int B, double c1, LSt st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    st.keep[b] = 0;
+    if (st.searching[b]) {
+        const double Lt = st.cost[3 * b] + st.cost[3 * b + 1] + st.cost[3 * b + 2];
+        if (Lt <= st.L[b] + c1 * st.step[b] * st.gd[b]) {
+            st.accepted[b] = 1;
+            st.keep[b] = 1;
+            st.L[b] = Lt;
+            st.searching[b] = 0;
+        } else {
+            st.step[b] *= 0.5;
+        }
+    }
+    if (st.searching[b]) atomicAdd(st.any, 1ull);
+}
+
+// End of iteration k: an instance whose search found no decrease keeps its
+// iterate and stops.
+__global__ void k_lfinish(int B, LSt st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (!st.accepted[b]) st.stopped[b] = 1;
+}
+
+// The new pair's rho = 1 / s.y (0 when s.y <= 1e-12 y.y: unused) and gamma.
+__global__ void k_lrho(int B, int head, int k, LSt st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const bool acc = st.accepted[b] != 0;
+    const bool ok = acc && st.sy[b] > 1e-12 * st.yy[b] && st.yy[b] > 0.0;
+    st.rho[(size_t)head * B + b] = ok ? 1.0 / st.sy[b] : 0.0;
+    if (ok) st.gamma[b] = st.sy[b] / st.yy[b];
+    if (acc) st.done[b] = k + 1;
+}
+
 dim3 vec_grid(long long N, int B) {
     long long gx = (N + kLT * 4 - 1) / (kLT * 4);
     if (gx < 1) gx = 1;
@@ -194,7 +288,9 @@ struct LMap {
     int B, m, nb;
     size_t oS, oY, oG, oGt, oXt, oXa, oGa, oD;        // float vectors
     size_t oRho, oAlpha, oGamma, oDot, oCoef, oStep, oPart, oCost;  // doubles
-    size_t oFlag;                                   // int[B]
+    size_t oRead;                                   // {searching count, L[B]}: the host's read
+    size_t oGd, oGmax, oGg, oSy, oYy;               // doubles [B]
+    size_t oUse, oKeep, oAcc, oStop, oSearch, oDone;  // ints [B]
     size_t total;
 };
 
@@ -228,7 +324,18 @@ LMap lbfgs_map(long long N, int B, int m) {
     M.oStep = take(sizeof(double) * B);
     M.oPart = take(sizeof(double) * (size_t)B * M.nb);
     M.oCost = take(sizeof(double) * 3 * (size_t)B);
-    M.oFlag = take(sizeof(int) * B);
+    M.oRead = take(sizeof(double) * (1 + (size_t)B));
+    M.oGd = take(sizeof(double) * B);
+    M.oGmax = take(sizeof(double) * B);
+    M.oGg = take(sizeof(double) * B);
+    M.oSy = take(sizeof(double) * B);
+    M.oYy = take(sizeof(double) * B);
+    M.oUse = take(sizeof(int) * B);
+    M.oKeep = take(sizeof(int) * B);
+    M.oAcc = take(sizeof(int) * B);
+    M.oStop = take(sizeof(int) * B);
+    M.oSearch = take(sizeof(int) * B);
+    M.oDone = take(sizeof(int) * B);
     M.total = off;
     return M;
 }
@@ -284,13 +391,8 @@ meta_status two_loop(const LCtx& c, const float* g, float* d, int h, int head) {
                                       c.dbl(M.oDot), c.dbl(M.oCoef));
         k_laxpy<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), c.S(i), d);
     }
-    std::vector<double> neg(M.B, -1.0);
-    L_TRY(cudaMemcpyAsync(c.dbl(M.oCoef), neg.data(), sizeof(double) * M.B,
-                          cudaMemcpyHostToDevice, c.st));
-    k_lscale<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), d);
+    k_lneg<<<vg, kLT, 0, c.st>>>(M.N, M.B, d);
     L_TRY(cudaGetLastError());
-    // the host vector must outlive the copy
-    L_TRY(cudaStreamSynchronize(c.st));
     return META_OK;
 }
 
@@ -378,6 +480,7 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
     const int B = M.B;
     const size_t vbytes = sizeof(float) * (size_t)M.N * B;
     const dim3 vg = vec_grid(M.N, B);
+    const int ib = (B + 127) / 128;  // blocks of the per-instance kernels
     constexpr double kC1 = 1e-4;     // Armijo constant
     constexpr int kHalvings = 12;    // backtracking steps per line search
     float* g = c.vec(M.oG);
@@ -386,29 +489,34 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
     float* xa = c.vec(M.oXa);
     float* ga = c.vec(M.oGa);
     float* d = c.vec(M.oD);
-    double* costd = c.dbl(M.oCost);
-    int* flag = reinterpret_cast<int*>(c.base + M.oFlag);
-
-    std::vector<double> cost(3 * (size_t)B), L(B), gd(B), gmax(B), gg(B), step(B), coef(B);
-    (void)vbytes;
-    std::vector<double> rhoh((size_t)M.m * B, 0.0), gamma(B, 1.0), sy(B), yy(B);
-    std::vector<int> stopped(B, 0), accepted(B, 0), use(B, 0), keep(B, 0);
-    std::vector<int> done(B, 0);
-    auto read_costs = [&](std::vector<double>& Lout) -> meta_status {
-        L_TRY(cudaMemcpyAsync(cost.data(), costd, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost,
-                              c.st));
+    auto ip = [&](size_t o) { return reinterpret_cast<int*>(c.base + o); };
+    LSt S;
+    S.any = reinterpret_cast<unsigned long long*>(c.base + M.oRead);
+    S.L = c.dbl(M.oRead) + 1;
+    S.gd = c.dbl(M.oGd);
+    S.gmax = c.dbl(M.oGmax);
+    S.gg = c.dbl(M.oGg);
+    S.step = c.dbl(M.oStep);
+    S.coef = c.dbl(M.oCoef);
+    S.sy = c.dbl(M.oSy);
+    S.yy = c.dbl(M.oYy);
+    S.rho = c.dbl(M.oRho);
+    S.gamma = c.dbl(M.oGamma);
+    S.cost = c.dbl(M.oCost);
+    S.use = ip(M.oUse);
+    S.keep = ip(M.oKeep);
+    S.accepted = ip(M.oAcc);
+    S.stopped = ip(M.oStop);
+    S.searching = ip(M.oSearch);
+    S.done = ip(M.oDone);
+    // The host reads one block per line-search trial: the count of instances
+    // still searching and the costs L (which also give the cost history).
+    std::vector<double> rd(1 + (size_t)B);
+    auto read_block = [&](unsigned long long* any) -> meta_status {
+        L_TRY(cudaMemcpyAsync(rd.data(), c.dbl(M.oRead), sizeof(double) * (1 + (size_t)B),
+                              cudaMemcpyDeviceToHost, c.st));
         L_TRY(cudaStreamSynchronize(c.st));
-        for (int b = 0; b < B; ++b) Lout[b] = cost[3 * b] + cost[3 * b + 1] + cost[3 * b + 2];
-        return META_OK;
-    };
-    auto to_host = [&](const double* dev, std::vector<double>& h) -> meta_status {
-        L_TRY(cudaMemcpyAsync(h.data(), dev, sizeof(double) * B, cudaMemcpyDeviceToHost, c.st));
-        L_TRY(cudaStreamSynchronize(c.st));
-        return META_OK;
-    };
-    auto to_dev = [&](void* dev, const void* h, size_t bytes) -> meta_status {
-        L_TRY(cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, c.st));
-        L_TRY(cudaStreamSynchronize(c.st));  // the host vectors change right after
+        std::memcpy(any, rd.data(), sizeof(unsigned long long));
         return META_OK;
     };
 #define L_DO(x)                         \
@@ -418,102 +526,58 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
     } while (0)
 
     L_TRY(cudaMemsetAsync(d, 0, vbytes, c.st));
-    L_DO(meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, costd, g, ws, ws_bytes, c.st));
-    L_DO(read_costs(L));
-    if (cost_hist)
-        for (int b = 0; b < B; ++b) cost_hist[b] = L[b];
+    L_TRY(cudaMemsetAsync(S.rho, 0, sizeof(double) * (size_t)M.m * B, c.st));
+    L_DO(meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, S.cost, g, ws, ws_bytes, c.st));
+    k_linit<<<ib, 128, 0, c.st>>>(B, S);
+    L_TRY(cudaGetLastError());
+    unsigned long long any = 0;
+    if (cost_hist) {
+        L_DO(read_block(&any));
+        for (int b = 0; b < B; ++b) cost_hist[b] = rd[1 + b];
+    }
     int h = 0, head = 0;
     for (int k = 0; k < iters; ++k) {
-        // direction: the two-loop recursion, or a scaled steepest-descent step
-        // for an instance without a usable pair in the window or whose direction
-        // does not descend (its pairs are then forgotten)
+        // direction: the two-loop recursion, or (k_ldecide) a scaled steepest-descent
+        // step for an instance without a usable pair or whose direction does not descend
         if (h > 0) L_DO(two_loop(c, g, d, h, head));
-        L_DO(ldot<false>(c, g, d, c.dbl(M.oDot)));
-        L_DO(to_host(c.dbl(M.oDot), gd));
-        L_DO(ldot<true>(c, g, nullptr, c.dbl(M.oDot)));
-        L_DO(to_host(c.dbl(M.oDot), gmax));
-        L_DO(ldot<false>(c, g, g, c.dbl(M.oDot)));
-        L_DO(to_host(c.dbl(M.oDot), gg));
-        bool any_restart = false;
-        for (int b = 0; b < B; ++b) {
-            int nvalid = 0;
-            for (int i = 0; i < M.m; ++i) nvalid += rhoh[(size_t)i * B + b] != 0.0;
-            use[b] = (!stopped[b] && (nvalid == 0 || !(gd[b] < 0.0))) ? 1 : 0;
-            coef[b] = gmax[b] > 0.0 ? -(double)h0 / gmax[b] : 0.0;
-            if (use[b]) {
-                gd[b] = coef[b] * gg[b];
-                any_restart = any_restart || nvalid > 0;
-                for (int i = 0; i < M.m; ++i) rhoh[(size_t)i * B + b] = 0.0;  // forget
-                gamma[b] = 1.0;
-            }
-        }
-        L_DO(to_dev(flag, use.data(), sizeof(int) * B));
-        L_DO(to_dev(c.dbl(M.oCoef), coef.data(), sizeof(double) * B));
-        k_lsteep<<<vg, kLT, 0, c.st>>>(M.N, flag, c.dbl(M.oCoef), g, d);
+        L_DO(ldot<false>(c, g, d, S.gd));
+        L_DO(ldot<true>(c, g, nullptr, S.gmax));
+        L_DO(ldot<false>(c, g, g, S.gg));
+        k_ldecide<<<ib, 128, 0, c.st>>>(B, M.m, h0, S);
+        k_lsteep<<<vg, kLT, 0, c.st>>>(M.N, S.use, S.coef, g, d);
         L_TRY(cudaGetLastError());
-        if (any_restart) {
-            L_DO(to_dev(c.dbl(M.oRho), rhoh.data(), sizeof(double) * rhoh.size()));
-            L_DO(to_dev(c.dbl(M.oGamma), gamma.data(), sizeof(double) * B));
-        }
-        // backtracking Armijo line search, per instance
-        std::vector<double> Lt(B);
-        for (int b = 0; b < B; ++b) {
-            accepted[b] = 0;
-            step[b] = stopped[b] || !(gd[b] < 0.0) ? 0.0 : 1.0;
-            if (step[b] == 0.0) stopped[b] = 1;
-        }
+        // backtracking Armijo line search, per instance, decided on the device
         for (int t = 0; t <= kHalvings; ++t) {
-            bool searching = false;
-            for (int b = 0; b < B; ++b) searching = searching || (!stopped[b] && !accepted[b]);
-            if (!searching) break;
-            std::vector<double> tstep(B);
-            for (int b = 0; b < B; ++b) tstep[b] = (!stopped[b] && !accepted[b]) ? step[b] : 0.0;
-            L_DO(to_dev(c.dbl(M.oStep), tstep.data(), sizeof(double) * B));
-            k_ltrial<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oStep), p0, d, xt);
+            k_ltrial2<<<vg, kLT, 0, c.st>>>(M.N, S, p0, d, xt);
             L_TRY(cudaGetLastError());
-            L_DO(meta_cost_and_grad(prob, I0, J, xt, mu, rho, lambda, costd, gt, ws, ws_bytes,
+            L_DO(meta_cost_and_grad(prob, I0, J, xt, mu, rho, lambda, S.cost, gt, ws, ws_bytes,
                                     c.st));
-            L_DO(read_costs(Lt));
-            for (int b = 0; b < B; ++b) {
-                keep[b] = 0;
-                if (stopped[b] || accepted[b]) continue;
-                if (Lt[b] <= L[b] + kC1 * step[b] * gd[b]) {
-                    accepted[b] = 1;
-                    keep[b] = 1;
-                    L[b] = Lt[b];
-                } else {
-                    step[b] *= 0.5;
-                }
-            }
-            L_DO(to_dev(flag, keep.data(), sizeof(int) * B));
-            k_lkeep<<<vg, kLT, 0, c.st>>>(M.N, flag, xt, gt, xa, ga);
+            L_TRY(cudaMemsetAsync(S.any, 0, sizeof(unsigned long long), c.st));
+            k_larmijo<<<ib, 128, 0, c.st>>>(B, kC1, S);
+            k_lkeep<<<vg, kLT, 0, c.st>>>(M.N, S.keep, xt, gt, xa, ga);
             L_TRY(cudaGetLastError());
+            L_DO(read_block(&any));  // the one host read of a trial
+            if (!any) break;
         }
-        for (int b = 0; b < B; ++b)
-            if (!accepted[b]) stopped[b] = 1;  // no decrease found: keep the iterate
+        k_lfinish<<<ib, 128, 0, c.st>>>(B, S);
         // new pair (s, y) of the instances that moved; x and g advance
-        L_DO(to_dev(flag, accepted.data(), sizeof(int) * B));
-        k_lpair<<<vg, kLT, 0, c.st>>>(M.N, flag, p0, g, xa, ga, c.S(head), c.Y(head));
+        k_lpair<<<vg, kLT, 0, c.st>>>(M.N, S.accepted, p0, g, xa, ga, c.S(head), c.Y(head));
         L_TRY(cudaGetLastError());
-        L_DO(ldot<false>(c, c.S(head), c.Y(head), c.dbl(M.oDot)));
-        L_DO(to_host(c.dbl(M.oDot), sy));
-        L_DO(ldot<false>(c, c.Y(head), c.Y(head), c.dbl(M.oDot)));
-        L_DO(to_host(c.dbl(M.oDot), yy));
-        for (int b = 0; b < B; ++b) {
-            const bool ok = accepted[b] && sy[b] > 1e-12 * yy[b] && yy[b] > 0.0;
-            rhoh[(size_t)head * B + b] = ok ? 1.0 / sy[b] : 0.0;
-            if (ok) gamma[b] = sy[b] / yy[b];
-            if (accepted[b]) done[b] = k + 1;
-        }
-        L_DO(to_dev(c.dbl(M.oRho), rhoh.data(), sizeof(double) * rhoh.size()));
-        L_DO(to_dev(c.dbl(M.oGamma), gamma.data(), sizeof(double) * B));
+        L_DO(ldot<false>(c, c.S(head), c.Y(head), S.sy));
+        L_DO(ldot<false>(c, c.Y(head), c.Y(head), S.yy));
+        k_lrho<<<ib, 128, 0, c.st>>>(B, head, k, S);
+        L_TRY(cudaGetLastError());
         head = (head + 1) % M.m;
         h = h < M.m ? h + 1 : M.m;
-        if (cost_hist)
-            for (int b = 0; b < B; ++b) cost_hist[(size_t)(k + 1) * B + b] = L[b];
+        if (cost_hist)  // L of every instance as of the last trial's read
+            for (int b = 0; b < B; ++b) cost_hist[(size_t)(k + 1) * B + b] = rd[1 + b];
     }
-    if (iters_done)
-        for (int b = 0; b < B; ++b) iters_done[b] = done[b];
+    if (iters_done) {
+        L_TRY(cudaMemcpyAsync(iters_done, S.done, sizeof(int) * B, cudaMemcpyDeviceToHost, c.st));
+        L_TRY(cudaStreamSynchronize(c.st));
+    } else {
+        L_TRY(cudaStreamSynchronize(c.st));
+    }
 #undef L_DO
     return META_OK;
 }

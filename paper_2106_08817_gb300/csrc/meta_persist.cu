@@ -315,7 +315,6 @@ k_persist(const DPhase* __restrict__ phases, const long long* __restrict__ first
         const int t0 = (int)(s_item[slot] - P.first) * P.per;
         const int t1 = min(t0 + P.per, P.ntiles);
         VBlk kb;
-        kb.smem = smem;
         kb.nthr = P.bx * P.by;
         kb.tx_ = tid % P.bx;
         kb.ty_ = tid / P.bx;

@@ -30,7 +30,7 @@ __device__ __forceinline__ Vox vox_of(const Geom& g, const K& kb) {
 }
 template <int NDIM>
 __device__ __forceinline__ Vox vox_of(const Geom& g) {
-    return vox_of<NDIM>(g, HwBlk{nullptr});
+    return vox_of<NDIM>(g, HwBlk{});
 }
 
 template <int NDIM>

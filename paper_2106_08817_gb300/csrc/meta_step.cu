@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_pack<HwBlk, NDIM>(HwBlk{nullptr}, g, I0, p0, dI, dP);
+    body_pack<HwBlk, NDIM>(HwBlk{}, g, I0, p0, dI, dP);
 }
 #endif
 
@@ -63,13 +63,13 @@ constexpr int kAdvTY = 2 * kPY;  // rows per tile
 constexpr int kAdvW = kPX + 2 * kAdvHalo;      // 40: staged row length
 constexpr int kAdvHU = kAdvTY + 2;             // 18: staged rows of u
 constexpr int kAdvHI = kAdvTY + 2 * kAdvHalo;  // 24: staged rows of I, p
-// shared memory of the 2-D advect: u (two components), I_t, p_t and the CTA max
-constexpr int kAdv2dSmem = (2 * kAdvHU + 2 * kAdvHI) * kAdvW * 4 + 16;
+// dynamic shared memory of the 2-D advect: u (two components), I_t, p_t
+constexpr int kAdv2dSmem = (2 * kAdvHU + 2 * kAdvHI) * kAdvW * 4;
 
 template <class K, bool PDET>
-__device__ __forceinline__ void body_advect2d(const K& kb, Geom g, Coefs cf, int t, Slots sl, float* states, const float* u, unsigned int* maxdisp) {
+__device__ __forceinline__ void body_advect2d(const K& kb, Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     constexpr int W = kAdvW, HU = kAdvHU, HI = kAdvHI;
-    float* sU0 = reinterpret_cast<float*>(kb.smem);
+    float* sU0 = reinterpret_cast<float*>(kb.smem());
     float* sU1 = sU0 + HU * W;
     float* sI = sU1 + HU * W;
     float* sP = sI + HI * W;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void body_advect2d(const K& kb, Geom g, Coefs cf, int
         I1[o] = Iw + (dt * mu) * pw;
     }
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
-    unsigned int& s_m = *reinterpret_cast<unsigned int*>(sP + HI * W);
+    __shared__ unsigned int s_m;
     if (kb.tx() == 0 && kb.ty() == 0) s_m = 0u;
     kb.sync();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
@@ -146,8 +146,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    __shared__ __align__(16) unsigned char st[kAdv2dSmem];
-    body_advect2d<HwBlk, PDET>(HwBlk{st}, g, cf, t, sl, states, u, maxdisp);
+    body_advect2d<HwBlk, PDET>(HwBlk{}, g, cf, t, sl, states, u, maxdisp);
 }
 #endif
 
@@ -163,11 +162,11 @@ constexpr int kASlot = 3 * kAUS + 2 * kAIS;            // floats per ring slot
 constexpr int kAChunks = (3 * kAUR + 2 * kAIR) * (kAW / 4);
 constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
 constexpr int kARing = 4;                              // plane slots
-constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float) + 16;  // + the CTA max
+constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float);
 
 template <class K, bool PDET>
-__device__ __forceinline__ void body_advect3d(const K& kb, Geom g, Coefs cf, int t, Slots sl, int zc, float* states, const float* u, unsigned int* maxdisp) {
-    float* sm = reinterpret_cast<float*>(kb.smem);
+__device__ __forceinline__ void body_advect3d(const K& kb, Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
+    float* sm = reinterpret_cast<float*>(kb.smem());
     const int b = kb.bz();
     const int nxc = (g.nx + 31) / 32;
     const int x0 = (kb.bx() % nxc) * 32;
@@ -303,7 +302,7 @@ __device__ __forceinline__ void body_advect3d(const K& kb, Geom g, Coefs cf, int
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
-    unsigned int& s_m = *reinterpret_cast<unsigned int*>(sm + kARing * kASlot);
+    __shared__ unsigned int s_m;
     if (tid == 0) s_m = 0u;
     kb.sync();
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
@@ -319,8 +318,7 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    body_advect3d<HwBlk, PDET>(HwBlk{smem_raw}, g, cf, t, sl, zc, states, u, maxdisp);
+    body_advect3d<HwBlk, PDET>(HwBlk{}, g, cf, t, sl, zc, states, u, maxdisp);
 }
 #endif
 
@@ -538,7 +536,8 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
     const dim3 blk(kPX, kPY);
     if (ndim == 2) {
         const dim3 grid((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B);
-        META_CHECK_LAUNCH(launch_k(c.pdet ? k_advect2d<true> : k_advect2d<false>, grid, blk, 0, st,
+        META_CHECK_LAUNCH(launch_k(c.pdet ? k_advect2d<true> : k_advect2d<false>, grid, blk,
+                                   kAdv2dSmem, st,
                                    g, c, t, sl, states, u, maxdisp));
     } else {
         auto kern = c.pdet ? k_advect3d<true> : k_advect3d<false>;
