@@ -59,7 +59,10 @@ typedef enum {
     META_ERR_CUDA = 4,        /* a CUDA runtime or driver call failed */
     META_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out */
     META_ERR_NONFINITE = 6,   /* reserved: non-finite cost detected */
-    META_ERR_UNSUPPORTED = 7  /* no sm_103a device, or the driver lacks TMA support */
+    META_ERR_UNSUPPORTED = 7, /* no sm_103a device, or the driver lacks TMA support */
+    META_ERR_FORMAT = 8,      /* a saved optimiser state or tuning cache is malformed, or
+                                 does not match the problem (shape, m, version, checksum) */
+    META_ERR_IO = 9           /* a file could not be opened, read, written or renamed */
 } meta_status;
 
 /* Shape of one batch of independent registration problems. */
@@ -299,6 +302,27 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
                           double* cost, float* grad, void* ws, size_t ws_bytes, void* stream,
                           meta_tuning* out);
 
+/* Tile shapes on disk, a JSON file: {"format": "meta-tuning", "version": 1,
+ * "arch": ..., "entries": [{"ndim", "dims", "batch", "sigma", "sigma_bits" (the
+ * FP32 bit pattern of sigma; wins over "sigma" when present), "zc_transport",
+ * "zc_advect", "ly", "lz", "txw", "split"}, ...]}, other keys ignored.  Files
+ * are written to a temporary name and renamed, so readers see whole files.
+ * meta_tuning_save: every shape of the process-wide table.  meta_tuning_load:
+ * records every entry as meta_tuning_set does; a file with any malformed or
+ * out-of-range entry is refused whole (META_ERR_FORMAT, nothing recorded);
+ * META_ERR_IO when it cannot be read.  `entries` (nullable) receives the count.
+ * meta_tuning_cache: names the cache file of meta_autotune (NULL or "": none)
+ * and records the entries it already holds (a missing file is an empty cache).
+ * While a cache is named, meta_autotune for a shape that the cache holds
+ * records that entry and returns without timing anything (cost and grad are
+ * not written), and a new tuning result is merged into the file (entries that
+ * other processes wrote meanwhile are kept); META_ERR_IO if that write fails
+ * (the result is recorded in the table all the same).  Host only; no call
+ * here touches the GPU. */
+meta_status meta_tuning_save(const char* path);
+meta_status meta_tuning_load(const char* path, int* entries);
+meta_status meta_tuning_cache(const char* path, int* entries);
+
 /* The tile shapes a call with this problem uses (tuned, set, or built-in,
  * with 0 fields resolved). */
 meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out);
@@ -341,6 +365,58 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
                                 size_t ws_bytes, void* lws, size_t lws_bytes, double* cost_hist,
                                 int* iters_done, void* stream);
 
+/* Continues a minimisation for `iters` more iterations from the state that the
+ * last meta_lbfgs_minimize / meta_lbfgs_resume on this lws ended with (or that
+ * meta_lbfgs_state_load put there): the iterate p0 (which must hold that run's
+ * last accepted iterate), its gradient, the m pairs, the costs and stopped
+ * flags.  The same sequence of iterates results as one longer run, bit for bit.
+ * cost_hist: [iters + 1][batch], entry 0 the cost at the resume point;
+ * iters_done counts iterations across the runs.  META_ERR_FORMAT if lws holds
+ * no finished run (the state is valid only after a run returned META_OK). */
+meta_status meta_lbfgs_resume(const meta_problem* prob, const float* I0, const float* J,
+                              float* p0, const float* mu, const float* rho, const float* lambda,
+                              int iters, int m, float h0, void* ws, size_t ws_bytes, void* lws,
+                              size_t lws_bytes, double* cost_hist, int* iters_done,
+                              void* stream);
+
+/* Host save / resume of the L-BFGS state (the paper has none: its optimiser
+ * runs once, Sec. 3).  The host image is an 80-byte header (tag "METALBFS",
+ * u32 version 1, i32 ndim, dims[3] (0 past ndim), batch, m, iterations done,
+ * pairs held, ring head, two zero words, then u64 voxels per instance, payload
+ * bytes and the FNV-1a 64-bit checksum of the payload; little-endian),
+ * then the gradient [batch, N] f32, the pair rings S and Y [m][batch, N] f32,
+ * rho [m][batch] f64, gamma [batch] f64, the costs [batch] f64 and the stopped
+ * and last-moved flags [batch] i32.  p0 is not part of it: save the iterate
+ * with it.
+ * meta_lbfgs_state_size: bytes of the image.
+ * meta_lbfgs_state_check (host only): META_OK when `host` is an intact image
+ * for this problem and m, META_ERR_FORMAT when it is not (size, tag, version,
+ * shape, ring indices or checksum).
+ * meta_lbfgs_state_save: writes the image of the state in lws (META_ERR_FORMAT
+ * if lws holds no finished run).  meta_lbfgs_state_load: checks the image, then
+ * copies it into lws for meta_lbfgs_resume.  Both synchronise `stream`; the
+ * host buffer is the caller's and is not kept. */
+meta_status meta_lbfgs_state_size(const meta_problem* prob, int m, size_t* bytes);
+meta_status meta_lbfgs_state_check(const meta_problem* prob, int m, const void* host,
+                                   size_t host_bytes);
+meta_status meta_lbfgs_state_save(const meta_problem* prob, int m, const void* lws,
+                                  size_t lws_bytes, void* host, size_t host_bytes, void* stream);
+meta_status meta_lbfgs_state_load(const meta_problem* prob, int m, const void* host,
+                                  size_t host_bytes, void* lws, size_t lws_bytes, void* stream);
+
+/* Gradient descent on the cost of Eq. 4, the paper's optimiser (Sec. 3), with
+ * the step normalised per instance: p0 <- p0 - h0 g / max|g| (no step where
+ * g = 0), `iters` steps.  Its whole state is the iterate p0 and the number of
+ * steps taken, so a run of a + b steps equals a run of a steps followed by one
+ * of b (bit for bit).  lws: an L-BFGS workspace for m = 1.  cost_hist (host,
+ * nullable): [iters + 1][batch], the cost of every iterate; with it the host
+ * reads the costs once per step, without it the host does not wait between
+ * steps.  Synchronises `stream` before returning. */
+meta_status meta_gd_minimize(const meta_problem* prob, const float* I0, const float* J,
+                             float* p0, const float* mu, const float* rho, const float* lambda,
+                             int iters, float h0, void* ws, size_t ws_bytes, void* lws,
+                             size_t lws_bytes, double* cost_hist, void* stream);
+
 /* Device-side status word latched in ws since it was last cleared.  Bit 0: a
  * bounded TMA wait ran out (the call's results are invalid; returns
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step
@@ -360,6 +436,24 @@ meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* st
  * word restores the workspace. */
 meta_status meta_selftest_timeout(void* ws, size_t ws_bytes, unsigned long long limit_ns,
                                   void* stream);
+
+/* Tracing (the paper has none): every meta_cost_and_grad, and every call and
+ * plan recording built on it, marks its phases as NVTX ranges on the calling
+ * host thread: "meta.cost_and_grad" around "meta.forward" (the T steps of
+ * Eq. 3), "meta.cost" (Eq. 4) and "meta.adjoint" (the reverse sweep), which
+ * holds one "meta.recompute" per checkpoint segment re-run from its stored
+ * state (none with every state kept).  Ranges bracket the enqueueing of each
+ * phase's kernels (profilers such as ncu --nvtx attribute kernels to them);
+ * they cost a few hundred nanoseconds when no tool is attached.
+ * meta_trace_set: a host callback (NULL: none) that receives the same pushes
+ * (push = 1) and pops (push = 0) with the range's name (a static string) and
+ * `user`, on the thread that makes the call; it must not call into this
+ * library.  meta_trace_selftest: pushes "meta.selftest", pushes and pops
+ * "meta.selftest.inner", pops "meta.selftest" (host only, for checking a
+ * callback or a tool). */
+typedef void (*meta_trace_fn)(const char* name, int push, void* user);
+meta_status meta_trace_set(meta_trace_fn fn, void* user);
+meta_status meta_trace_selftest(void);
 
 /* Human-readable name of a status code (static string). */
 const char* meta_status_string(meta_status s);

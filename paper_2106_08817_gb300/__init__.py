@@ -26,7 +26,9 @@ __all__ = ["workspace_size", "Workspace", "shoot_forward", "shoot_deform", "shoo
            "cost_and_grad", "Shoot", "shoot", "library_path", "STATUS", "timer_start",
            "timer_stop", "KERNEL_CLASSES", "CostAndGradPlan", "GroupPlan", "SCHEMES",
            "lbfgs_workspace_size", "lbfgs_direction", "lbfgs_minimize", "clear_workspaces",
-           "cost_and_grad_noalloc", "noalloc_status", "noalloc_selftest_timeout"]
+           "cost_and_grad_noalloc", "noalloc_status", "noalloc_selftest_timeout",
+           "tuning", "set_tuning", "autotune", "tuning_save", "tuning_load", "tuning_cache",
+           "trace", "gd_minimize", "Registration"]
 
 KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init", "adj_pre",
                   "adj_gather", "xpass_adj", "strided_adj", "adj_gradp", "unpack", "deform",
@@ -40,7 +42,9 @@ _lib = None
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported shape", 3: "workspace",
           4: "CUDA error", 5: "device-side wait timed out", 6: "non-finite",
-          7: "unsupported device or driver"}
+          7: "unsupported device or driver", 8: "malformed or mismatched saved state",
+          9: "file I/O error"}
+_TRACE_FN = ctypes.CFUNCTYPE(None, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p)
 
 
 class MetaError(RuntimeError):
@@ -124,7 +128,25 @@ def _load():
                                             ctypes.c_float, V, S, V, S,
                                             ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_int), V]
-        for f in ("meta_lbfgs_workspace_size", "meta_lbfgs_direction", "meta_lbfgs_minimize"):
+        lib.meta_lbfgs_resume.argtypes = lib.meta_lbfgs_minimize.argtypes
+        lib.meta_lbfgs_state_size.argtypes = [P, ctypes.c_int, ctypes.POINTER(S)]
+        lib.meta_lbfgs_state_check.argtypes = [P, ctypes.c_int, V, S]
+        lib.meta_lbfgs_state_save.argtypes = [P, ctypes.c_int, V, S, V, S, V]
+        lib.meta_lbfgs_state_load.argtypes = [P, ctypes.c_int, V, S, V, S, V]
+        lib.meta_gd_minimize.argtypes = [P, F, F, F, F, F, F, ctypes.c_int, ctypes.c_float, V, S,
+                                         V, S, ctypes.POINTER(ctypes.c_double), V]
+        for f in ("meta_lbfgs_workspace_size", "meta_lbfgs_direction", "meta_lbfgs_minimize",
+                  "meta_lbfgs_resume", "meta_lbfgs_state_size", "meta_lbfgs_state_check",
+                  "meta_lbfgs_state_save", "meta_lbfgs_state_load", "meta_gd_minimize"):
+            getattr(lib, f).restype = ctypes.c_int
+        CP = ctypes.c_char_p
+        lib.meta_tuning_save.argtypes = [CP]
+        lib.meta_tuning_load.argtypes = [CP, ctypes.POINTER(ctypes.c_int)]
+        lib.meta_tuning_cache.argtypes = [CP, ctypes.POINTER(ctypes.c_int)]
+        lib.meta_trace_set.argtypes = [_TRACE_FN, V]
+        lib.meta_trace_selftest.argtypes = []
+        for f in ("meta_tuning_save", "meta_tuning_load", "meta_tuning_cache", "meta_trace_set",
+                  "meta_trace_selftest"):
             getattr(lib, f).restype = ctypes.c_int
         lib.meta_kernel_name.argtypes = [ctypes.c_int]
         lib.meta_kernel_name.restype = ctypes.c_char_p
@@ -483,6 +505,64 @@ def autotune(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma:
     return {f: getattr(t, f) for f in TUNING_FIELDS}
 
 
+def _path(path) -> bytes:
+    return os.fsencode(os.fspath(path))
+
+
+def tuning_save(path) -> None:
+    """Writes every recorded tile shape of this process to a JSON file
+    (meta_tuning_save)."""
+    rc = _load().meta_tuning_save(_path(path))
+    if rc:
+        raise MetaError(rc, "meta_tuning_save")
+
+
+def tuning_load(path) -> int:
+    """Records the tile shapes of a JSON file written by tuning_save or by the
+    autotuner's cache (meta_tuning_load); a malformed file is refused whole.
+    Returns the number of entries."""
+    n = ctypes.c_int(0)
+    rc = _load().meta_tuning_load(_path(path), ctypes.byref(n))
+    if rc:
+        raise MetaError(rc, "meta_tuning_load")
+    return int(n.value)
+
+
+def tuning_cache(path) -> int:
+    """Names the autotuner's cache file (None: none; meta_tuning_cache): shapes it
+    holds are recorded now and not re-timed by autotune, new results are merged
+    into it.  Returns the number of entries it held."""
+    n = ctypes.c_int(0)
+    rc = _load().meta_tuning_cache(None if path is None else _path(path), ctypes.byref(n))
+    if rc:
+        raise MetaError(rc, "meta_tuning_cache")
+    return int(n.value)
+
+
+class trace:
+    """Context manager that collects the phase ranges the library pushes and pops
+    (the same as its NVTX ranges; meta_trace_set) as (name, push) pairs::
+
+        with meta.trace() as events:
+            meta.cost_and_grad(...)
+    """
+
+    def __init__(self):
+        self.events = []
+        self._cb = _TRACE_FN(lambda name, push, user: self.events.append(
+            (name.decode(), int(push))))
+
+    def __enter__(self):
+        rc = _load().meta_trace_set(self._cb, None)
+        if rc:
+            raise MetaError(rc, "meta_trace_set")
+        return self.events
+
+    def __exit__(self, *exc):
+        _load().meta_trace_set(_TRACE_FN(), None)
+        return False
+
+
 def lbfgs_workspace_size(dims: Sequence[int], batch: int, m: int = 5) -> int:
     """Bytes of the L-BFGS workspace (m pairs) of a batch of this shape."""
     n = ctypes.c_size_t(0)
@@ -539,6 +619,151 @@ def lbfgs_minimize(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, 
     if rc:
         raise MetaError(rc, "meta_lbfgs_minimize")
     return (p[0] if sq else p), hist, done
+
+
+def gd_minimize(I0: torch.Tensor, J: torch.Tensor, p0: torch.Tensor, T: int, sigma: float,
+                mu, rho=1.0, lam=1e-3, iters: int = 10, h0: float = 0.05,
+                ndim: Optional[int] = None, ckpt: int = 0, p_update=0, scheme: str = "sl"):
+    """Gradient descent on the Eq. 4 cost from p0, the paper's optimiser (Sec. 3),
+    with the normalised step p <- p - h0 g / max|g| (meta_gd_minimize).  Returns
+    (p, costs [iters + 1, B] float64 numpy)."""
+    reg = Registration(I0, J, p0, T, sigma, mu, rho, lam, optimizer="gd", h0=h0, ndim=ndim,
+                       ckpt=ckpt, p_update=p_update, scheme=scheme)
+    hist = reg.run(iters)
+    return reg.p, hist
+
+
+class Registration:
+    """An iterative registration of I0 to J: the Eq. 4 cost minimised over p0 by
+    gradient descent (optimizer "gd", meta_gd_minimize) or L-BFGS ("lbfgs",
+    meta_lbfgs_minimize / meta_lbfgs_resume), whose state can be saved to a host
+    file and resumed in another process.  A run of a + b iterations and a run of
+    a iterations, saved, resumed and run for b more give the same iterates bit for
+    bit.  ``p`` is the current iterate, ``costs`` the cost history
+    [iterations + 1, B] (float64 numpy)."""
+
+    def __init__(self, I0, J, p0, T: int, sigma: float, mu, rho=1.0, lam=1e-3,
+                 optimizer: str = "lbfgs", m: int = 5, h0: float = 0.05, ckpt: int = 0,
+                 ndim: Optional[int] = None, p_update=0, scheme: str = "sl"):
+        if optimizer not in ("gd", "lbfgs"):
+            raise ValueError("optimizer must be 'gd' or 'lbfgs'")
+        I0b, nd, dims, sq = _shape(_as_batch(I0, "I0")[0], ndim)
+        self.I0 = I0b.contiguous()
+        self.J = _like(_as_batch(J, "J")[0], I0b, "J").contiguous()
+        self._p = _like(_as_batch(p0, "p0")[0], I0b, "p0").clone()
+        self._sq = sq
+        B, dev = I0b.shape[0], I0b.device
+        self.optimizer, self.ndim, self.dims, self.batch = optimizer, nd, tuple(dims), B
+        self.T, self.sigma, self.m, self.h0 = int(T), float(sigma), int(m), float(h0)
+        self.p_update, self.scheme = _pupd(p_update), scheme
+        self.ws = Workspace(dims, B, T, sigma, dev, ckpt, scheme)
+        self.ckpt = self.ws.ckpt
+        self.lws = torch.empty(lbfgs_workspace_size(dims, B, m if optimizer == "lbfgs" else 1),
+                               dtype=torch.uint8, device=dev)
+        self._mu, self._rho, self._lam = _coef(mu, B, dev), _coef(rho, B, dev), _coef(lam, B, dev)
+        self.iterations = 0
+        self.costs: Optional[np.ndarray] = None
+        self._started = False  # the L-BFGS state in lws is valid
+
+    @property
+    def p(self) -> torch.Tensor:
+        return self._p[0] if self._sq else self._p
+
+    def _prob(self) -> _Problem:
+        return _problem(self.ndim, self.dims, self.batch, self.T, self.sigma, self.ckpt,
+                        self.p_update, self.scheme)
+
+    def run(self, iters: int) -> np.ndarray:
+        """`iters` more iterations; returns their cost history [iters + 1, B]."""
+        iters = int(iters)
+        if iters < 0:
+            raise ValueError("iters must be >= 0")
+        lib, dev = _load(), self.I0.device
+        hist = np.zeros((iters + 1, self.batch), dtype=np.float64)
+        hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        common = (ctypes.byref(self._prob()), _p(self.I0), _p(self.J), _p(self._p), _p(self._mu),
+                  _p(self._rho), _p(self._lam))
+        with torch.cuda.device(dev):
+            if self.optimizer == "gd":
+                rc = lib.meta_gd_minimize(*common, iters, self.h0, ctypes.c_void_p(self.ws.ptr()),
+                                          self.ws.nbytes, ctypes.c_void_p(self.lws.data_ptr()),
+                                          self.lws.numel(), hp, _stream(dev))
+                what = "meta_gd_minimize"
+            else:
+                fn = lib.meta_lbfgs_resume if self._started else lib.meta_lbfgs_minimize
+                what = "meta_lbfgs_resume" if self._started else "meta_lbfgs_minimize"
+                done = np.zeros(self.batch, dtype=np.int32)
+                rc = fn(*common, iters, self.m, self.h0, ctypes.c_void_p(self.ws.ptr()),
+                        self.ws.nbytes, ctypes.c_void_p(self.lws.data_ptr()), self.lws.numel(), hp,
+                        done.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _stream(dev))
+        if rc:
+            raise MetaError(rc, what)
+        self._started = True
+        self.costs = hist if self.costs is None else np.concatenate([self.costs, hist[1:]])
+        self.iterations += iters
+        return hist
+
+    def _settings(self) -> dict:
+        f = lambda t: [float(x) for x in t.cpu().tolist()]
+        return dict(optimizer=self.optimizer, ndim=self.ndim, dims=list(self.dims),
+                    batch=self.batch, T=self.T, sigma=self.sigma, mu=f(self._mu),
+                    rho=f(self._rho), lam=f(self._lam), m=self.m, h0=self.h0, ckpt=self.ckpt,
+                    p_update=self.p_update, scheme=self.scheme, iterations=self.iterations)
+
+    def save(self, path) -> None:
+        """Writes p, the iteration count, the cost history and (L-BFGS) the optimiser
+        state to a host file (paper_2106_08817_gb300.checkpoint)."""
+        from . import checkpoint
+        if self.costs is None:
+            self.run(0)  # the cost at p0 (and, for L-BFGS, its gradient and an empty state)
+        blob = None
+        if self.optimizer == "lbfgs":
+            lib, dev = _load(), self.I0.device
+            n = ctypes.c_size_t(0)
+            rc = lib.meta_lbfgs_state_size(ctypes.byref(self._prob()), self.m, ctypes.byref(n))
+            if rc:
+                raise MetaError(rc, "meta_lbfgs_state_size")
+            buf = (ctypes.c_ubyte * n.value)()
+            with torch.cuda.device(dev):
+                rc = lib.meta_lbfgs_state_save(ctypes.byref(self._prob()), self.m,
+                                               ctypes.c_void_p(self.lws.data_ptr()),
+                                               self.lws.numel(), buf, n.value, _stream(dev))
+            if rc:
+                raise MetaError(rc, "meta_lbfgs_state_save")
+            blob = bytes(buf)
+        digest = checkpoint.images_digest(self.I0.cpu().numpy(), self.J.cpu().numpy())
+        checkpoint.write(path, self._settings(), self._p.cpu().numpy(), self.costs, digest, blob)
+
+    @classmethod
+    def resume(cls, path, I0, J, device=None) -> "Registration":
+        """A registration continued from a file written by save(), on the same images
+        (checked by their SHA-256)."""
+        from . import checkpoint
+        st = checkpoint.read(path)
+        dev = torch.device(device) if device is not None else (
+            I0.device if isinstance(I0, torch.Tensor) else torch.device("cuda"))
+        I0t = torch.as_tensor(I0, dtype=torch.float32).to(dev)
+        Jt = torch.as_tensor(J, dtype=torch.float32).to(dev)
+        shape = (st["batch"],) + tuple(st["dims"])
+        I0t, Jt = I0t.reshape(shape), Jt.reshape(shape)
+        if checkpoint.images_digest(I0t.cpu().numpy(), Jt.cpu().numpy()) != st["images_sha256"]:
+            raise ValueError("these are not the images the registration was saved with")
+        reg = cls(I0t, Jt, torch.from_numpy(st["p"]).to(dev), st["T"], st["sigma"], st["mu"],
+                  st["rho"], st["lam"], optimizer=st["optimizer"], m=st["m"], h0=st["h0"],
+                  ckpt=st["ckpt"], ndim=st["ndim"], p_update=st["p_update"], scheme=st["scheme"])
+        reg.iterations, reg.costs = st["iterations"], st["costs"]
+        reg._started = True
+        if reg.optimizer == "lbfgs":
+            blob = st["lbfgs_state"]
+            buf = (ctypes.c_ubyte * len(blob)).from_buffer_copy(blob)
+            with torch.cuda.device(dev):
+                rc = _load().meta_lbfgs_state_load(ctypes.byref(reg._prob()), reg.m, buf,
+                                                   len(blob),
+                                                   ctypes.c_void_p(reg.lws.data_ptr()),
+                                                   reg.lws.numel(), _stream(dev))
+            if rc:
+                raise MetaError(rc, "meta_lbfgs_state_load")
+        return reg
 
 
 class CostAndGradPlan:

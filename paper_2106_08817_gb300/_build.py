@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmeta.so")
 SOURCES = ["meta_api.cu", "meta_blur.cu", "meta_step.cu", "meta_adjoint.cu", "meta_noalloc.cu",
-           "meta_lbfgs.cu", "meta_persist.cu"]
+           "meta_lbfgs.cu", "meta_persist.cu", "meta_tuning.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra: List[str] = ()) -> 
     if failed:
         raise RuntimeError("nvcc failed for %s" % ", ".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-ldl"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -13,6 +13,8 @@
 #include "meta_kernels.h"
 
 #include <map>
+
+#include <nvtx3/nvToolsExt.h>
 #include <tuple>
 
 namespace meta {
@@ -441,7 +443,42 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
 // wT not null it also integrates the deformation w_t = phi_t - Id, ping-ponged
 // between SV and REC (neither is used by a forward pass), and sets *wT to the
 // buffer that holds w_T.
+// Phases of a call as NVTX ranges ("meta.cost_and_grad" around "meta.forward",
+// "meta.cost", "meta.adjoint" and, inside it, one "meta.recompute" per
+// re-run checkpoint segment).  They are host ranges: each brackets the
+// enqueueing of its phase's kernels, which profilers (ncu --nvtx) attribute
+// to it.  A host callback (meta_trace_set) sees the same pushes and pops.
+std::mutex g_trace_mu;
+meta_trace_fn g_trace_fn = nullptr;
+void* g_trace_user = nullptr;
+
+void trace_emit(const char* name, int push) {
+    meta_trace_fn fn;
+    void* user;
+    {
+        std::lock_guard<std::mutex> lk(g_trace_mu);
+        fn = g_trace_fn;
+        user = g_trace_user;
+    }
+    if (fn) fn(name, push, user);
+}
+
+struct Range {
+    const char* name;
+    explicit Range(const char* n) : name(n) {
+        nvtxRangePushA(n);
+        trace_emit(n, 1);
+    }
+    ~Range() {
+        trace_emit(name, 0);
+        nvtxRangePop();
+    }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
 meta_status run_forward(Ctx& c, const Coefs& cf, const float** wT = nullptr) {
+    Range r("meta.forward");
     const Layout& L = c.L;
     const size_t md_words = (size_t)kMaxdispStride * L.T * L.g.B;
     if (std::vector<PRec>* r = recorder()) {
@@ -474,6 +511,7 @@ meta_status run_forward(Ctx& c, const Coefs& cf, const float** wT = nullptr) {
 // Recomputes forward segment s from its checkpoint: the states and u of its
 // steps (the segment's last state is not needed by the adjoint).
 meta_status recompute_segment(Ctx& c, const Coefs& cf, int s) {
+    Range r("meta.recompute");
     const Layout& L = c.L;
     const int e = L.seg_end(s);
     for (int t = s * L.k; t < e; ++t) {
@@ -504,6 +542,7 @@ Slots start_slots(const Layout& L) {
 meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0);
 
 meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
+    Range r("meta.adjoint");
     if (c.L.scheme != META_SCHEME_SL) return run_adjoint_other(c, cf, mode, out0, gI0);
     const Layout& L = c.L;
     const Geom& g = L.g;
@@ -664,6 +703,7 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
         const meta_status a = adjoint_scheme(prob);
         if (a != META_OK) return a;
     }
+    Range r("meta.cost_and_grad");
     Ctx c;
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
@@ -674,10 +714,13 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
                 launch_pack(g, c.L.ndim, I0, p0, c.states, c.states + (size_t)g.B * g.inst, c.st));
     s = run_forward(c, cf);
     if (s != META_OK) return s;
-    META_LAUNCH(META_K_COST, c.st,
-                launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.maxdisp,
-                            c.REC, c.IHP, c.PHP, c.RAW, raw_p(c), c.partials, c.L.nblk, cost,
-                            c.st));
+    {
+        Range rc("meta.cost");
+        META_LAUNCH(META_K_COST, c.st,
+                    launch_cost(g, c.L.ndim, cf, start_slots(c.L), c.states, c.u, J, c.maxdisp,
+                                c.REC, c.IHP, c.PHP, c.RAW, raw_p(c), c.partials, c.L.nblk,
+                                cost, c.st));
+    }
     if (!grad) return META_OK;
     return run_adjoint(c, cf, 1, grad, nullptr);
 }
@@ -689,20 +732,11 @@ std::vector<PRec>*& recorder() {
     return r;
 }
 
-}  // namespace meta
-
-using namespace meta;
-
-extern "C" {
-
-meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
+// The range and launch-limit checks of meta_tuning_set, without storing.
+meta_status tuning_check(const meta_problem* prob, const meta_tuning* tun) {
     const meta_status s = validate(prob);
     if (s != META_OK) return s;
-    if (!tun) {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune.erase(tune_key(prob));
-        return META_OK;
-    }
+    if (!tun) return META_ERR_INVALID_ARG;
     const int d = prob->ndim;
     const int nz = d == 3 ? prob->dims[0] : 1, ny = prob->dims[d - 2];
     auto len_ok = [](int v, int q, int mx) { return v == 0 || (v >= q && v <= mx && v % q == 0); };
@@ -723,6 +757,49 @@ meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
         return META_ERR_INVALID_ARG;
     if (tun->lz && (long long)((nz + tun->lz - 1) / tun->lz) * ny > 65535)
         return META_ERR_INVALID_ARG;
+    return META_OK;
+}
+
+void tuning_snapshot(std::vector<TuneEntry>* out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    out->clear();
+    for (const auto& kv : g_tune) {
+        TuneEntry e;
+        std::memset(&e.prob, 0, sizeof(e.prob));
+        const TuneKey& k = kv.first;
+        e.prob.ndim = std::get<0>(k);
+        e.prob.dims[0] = std::get<1>(k);
+        if (e.prob.ndim == 3) {
+            e.prob.dims[1] = std::get<2>(k);
+            e.prob.dims[2] = std::get<3>(k);
+        } else {
+            e.prob.dims[1] = std::get<3>(k);
+        }
+        e.prob.batch = std::get<4>(k);
+        const uint32_t sb = std::get<5>(k);
+        std::memcpy(&e.prob.sigma, &sb, 4);
+        e.prob.T = 1;
+        e.tun = kv.second;
+        out->push_back(e);
+    }
+}
+
+}  // namespace meta
+
+using namespace meta;
+
+extern "C" {
+
+meta_status meta_tuning_set(const meta_problem* prob, const meta_tuning* tun) {
+    const meta_status s = validate(prob);
+    if (s != META_OK) return s;
+    if (!tun) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.erase(tune_key(prob));
+        return META_OK;
+    }
+    const meta_status c = tuning_check(prob, tun);
+    if (c != META_OK) return c;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(prob)] = *tun;
     return META_OK;
@@ -754,6 +831,11 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
     meta_status s = adjoint_scheme(prob);
     if (s != META_OK) return s;
     meta_tuning cur;
+    if (tuning_cache_lookup(prob, &cur)) {  // tuned before, in the cache file: no timing
+        s = meta_tuning_set(prob, &cur);
+        if (s == META_OK && out) *out = cur;
+        return s;
+    }
     s = meta_tuning_get(prob, &cur);
     if (s != META_OK) return s;
     const int d = prob->ndim;
@@ -870,8 +952,9 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         return res;
     }
     res = meta_tuning_set(prob, &cur);
-    if (res == META_OK && out) *out = cur;
-    return res;
+    if (res != META_OK) return res;
+    if (out) *out = cur;
+    return tuning_cache_note(prob, cur);  // merged into the cache file, if one is named
 }
 
 meta_status meta_workspace_size(const meta_problem* prob, size_t* bytes) {
@@ -1362,8 +1445,25 @@ const char* meta_status_string(meta_status s) {
         case META_ERR_TIMEOUT: return "device-side wait timed out";
         case META_ERR_NONFINITE: return "non-finite value";
         case META_ERR_UNSUPPORTED: return "unsupported device or driver";
+        case META_ERR_FORMAT: return "malformed or mismatched saved state";
+        case META_ERR_IO: return "file I/O error";
     }
     return "unknown status";
+}
+
+meta_status meta_trace_set(meta_trace_fn fn, void* user) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    g_trace_fn = fn;
+    g_trace_user = fn ? user : nullptr;
+    return META_OK;
+}
+
+meta_status meta_trace_selftest(void) {
+    Range outer("meta.selftest");
+    {
+        Range inner("meta.selftest.inner");
+    }
+    return META_OK;
 }
 
 }  // extern "C"

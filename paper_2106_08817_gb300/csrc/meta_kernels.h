@@ -2,6 +2,7 @@
 #pragma once
 
 #include "meta_common.cuh"
+#include "meta.h"
 
 #include <vector>
 
@@ -172,5 +173,19 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
                              const unsigned int* maxdisp, const float* mh, float* Ihp, float* php,
                              float* rec, float* rawI, float* rawP, float* grad_or_gp0,
                              float* gI0, cudaStream_t st);
+
+// The process-wide tile-shape table (meta_api.cu) as seen by the on-disk
+// cache (meta_tuning.cu).
+struct TuneEntry {
+    meta_problem prob;  // ndim, dims, batch, sigma (the key); T = 1, the rest 0
+    meta_tuning tun;
+};
+meta_status tuning_check(const meta_problem* prob, const meta_tuning* tun);
+void tuning_snapshot(std::vector<TuneEntry>* out);
+// meta_autotune's use of the cache file named by meta_tuning_cache: a hit
+// (an entry for this shape read from the file) skips the timing; a new result
+// is merged into the file.
+bool tuning_cache_lookup(const meta_problem* prob, meta_tuning* tun);
+meta_status tuning_cache_note(const meta_problem* prob, const meta_tuning& tun);
 
 }  // namespace meta

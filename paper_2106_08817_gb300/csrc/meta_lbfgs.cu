@@ -14,7 +14,10 @@
 // loop only launches, and reads one small block per line-search trial (how
 // many instances still search, and the costs): one read per iteration when
 // the first step is accepted.
+#include <climits>
+#include <cstddef>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -25,6 +28,7 @@ namespace meta {
 namespace {
 
 constexpr int kLT = 256;       // threads per CTA
+constexpr long long kStateMagic = 0x53464c4241544d45LL;  // marks a valid state header
 constexpr int kLMaxBlk = 512;  // dot-product CTAs per instance
 
 int dot_blocks(long long N) {
@@ -273,6 +277,13 @@ __global__ void k_lrho(int B, int head, int k, LSt st) {
     if (acc) st.done[b] = k + 1;
 }
 
+// Gradient-descent step size per instance: coef = -h0 / max|g| (0 where g = 0).
+__global__ void k_lgdcoef(int B, float h0, const double* __restrict__ gmax, double* coef) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    coef[b] = gmax[b] > 0.0 ? -(double)h0 / gmax[b] : 0.0;
+}
+
 dim3 vec_grid(long long N, int B) {
     long long gx = (N + kLT * 4 - 1) / (kLT * 4);
     if (gx < 1) gx = 1;
@@ -291,6 +302,7 @@ struct LMap {
     size_t oRead;                                   // {searching count, L[B]}: the host's read
     size_t oGd, oGmax, oGg, oSy, oYy;               // doubles [B]
     size_t oUse, oKeep, oAcc, oStop, oSearch, oDone;  // ints [B]
+    size_t oHdr;  // long long [4]: {kStateMagic, iterations done, pairs held, ring head}
     size_t total;
 };
 
@@ -336,6 +348,7 @@ LMap lbfgs_map(long long N, int B, int m) {
     M.oStop = take(sizeof(int) * B);
     M.oSearch = take(sizeof(int) * B);
     M.oDone = take(sizeof(int) * B);
+    M.oHdr = take(sizeof(long long) * 4);
     M.total = off;
     return M;
 }
@@ -411,6 +424,62 @@ meta_status lsetup(const meta_problem* prob, int m, void* lws, size_t lws_bytes,
     return META_OK;
 }
 
+// Host image of a minimiser state (meta_lbfgs_state_save / _load): this
+// header, then the regions of state_regions in their order.  Integers are
+// little-endian, as on every machine the library builds for.
+struct LStateFile {
+    char magic[8];  // "METALBFS"
+    uint32_t version;
+    int32_t ndim, dims[3], batch, m;
+    int32_t k, h, head;  // iterations done, pairs held, ring slot of the next pair
+    int32_t pad[2];      // zero
+    uint64_t n;         // voxels per instance
+    uint64_t payload;   // bytes after the header
+    uint64_t checksum;  // FNV-1a (64-bit) of the payload bytes
+};
+static_assert(sizeof(LStateFile) == 80 && offsetof(LStateFile, n) == 56,
+              "state header layout: no implicit padding");
+constexpr char kStateTag[8] = {'M', 'E', 'T', 'A', 'L', 'B', 'F', 'S'};
+constexpr uint32_t kStateVersion = 1;
+
+struct LRegion {
+    size_t off, bytes;  // offset in the workspace, size
+};
+
+// What a run continues from: x's gradient g, the pair rings S and Y (all m
+// slots), each pair's rho, gamma, the cost L, and the stopped / done flags.
+int state_regions(const LMap& M, LRegion* r) {
+    const size_t vb = sizeof(float) * (size_t)M.N * M.B;
+    int n = 0;
+    r[n++] = {M.oG, vb};
+    r[n++] = {M.oS, vb * M.m};
+    r[n++] = {M.oY, vb * M.m};
+    r[n++] = {M.oRho, sizeof(double) * (size_t)M.m * M.B};
+    r[n++] = {M.oGamma, sizeof(double) * M.B};
+    r[n++] = {M.oRead + sizeof(double), sizeof(double) * M.B};
+    r[n++] = {M.oStop, sizeof(int) * M.B};
+    r[n++] = {M.oDone, sizeof(int) * M.B};
+    return n;
+}
+
+size_t state_payload(const LMap& M) {
+    LRegion r[8];
+    const int n = state_regions(M, r);
+    size_t t = 0;
+    for (int i = 0; i < n; ++i) t += r[i].bytes;
+    return t;
+}
+
+// FNV-1a, 64-bit (offset basis 14695981039346656037, prime 1099511628211)
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 }  // namespace
 }  // namespace meta
 
@@ -466,11 +535,14 @@ meta_status meta_lbfgs_direction(const meta_problem* prob, int m, int npairs,
     return two_loop(c, g, d, npairs, npairs % M.m);
 }
 
-meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const float* J,
-                                float* p0, const float* mu, const float* rho,
-                                const float* lambda, int iters, int m, float h0, void* ws,
-                                size_t ws_bytes, void* lws, size_t lws_bytes, double* cost_hist,
-                                int* iters_done, void* stream) {
+// The minimiser of meta_lbfgs_minimize; with `resume` it continues from the
+// state that a previous run (or meta_lbfgs_state_load) left in lws instead of
+// starting at p0 with no pairs.
+static meta_status lbfgs_run(const meta_problem* prob, const float* I0, const float* J,
+                             float* p0, const float* mu, const float* rho, const float* lambda,
+                             int iters, int m, float h0, void* ws, size_t ws_bytes, void* lws,
+                             size_t lws_bytes, double* cost_hist, int* iters_done, void* stream,
+                             bool resume) {
     if (!I0 || !J || !p0 || !mu || !rho || !lambda || iters < 0 || !(h0 > 0.f))
         return META_ERR_INVALID_ARG;
     LCtx c;
@@ -525,17 +597,32 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
         if (_s != META_OK) return _s;   \
     } while (0)
 
-    L_TRY(cudaMemsetAsync(d, 0, vbytes, c.st));
-    L_TRY(cudaMemsetAsync(S.rho, 0, sizeof(double) * (size_t)M.m * B, c.st));
-    L_DO(meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, S.cost, g, ws, ws_bytes, c.st));
-    k_linit<<<ib, 128, 0, c.st>>>(B, S);
-    L_TRY(cudaGetLastError());
+    // the state header: valid only after a run ends (or a state is loaded)
+    long long hdr[4] = {0, 0, 0, 0};
+    int k0 = 0, h = 0, head = 0;
+    if (resume) {
+        L_TRY(cudaMemcpyAsync(hdr, c.base + M.oHdr, sizeof(hdr), cudaMemcpyDeviceToHost, c.st));
+        L_TRY(cudaStreamSynchronize(c.st));
+        if (hdr[0] != kStateMagic || hdr[1] < 0 || hdr[1] > (long long)INT_MAX - iters ||
+            hdr[2] < 0 || hdr[2] > M.m || hdr[3] < 0 || hdr[3] >= M.m)
+            return META_ERR_FORMAT;
+        k0 = (int)hdr[1];
+        h = (int)hdr[2];
+        head = (int)hdr[3];
+    }
+    L_TRY(cudaMemsetAsync(c.base + M.oHdr, 0, sizeof(hdr), c.st));
+    if (!resume) {
+        L_TRY(cudaMemsetAsync(S.rho, 0, sizeof(double) * (size_t)M.m * B, c.st));
+        L_DO(meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, S.cost, g, ws, ws_bytes, c.st));
+        k_linit<<<ib, 128, 0, c.st>>>(B, S);
+        L_TRY(cudaGetLastError());
+    }
+    if (h == 0) L_TRY(cudaMemsetAsync(d, 0, vbytes, c.st));
     unsigned long long any = 0;
     if (cost_hist) {
         L_DO(read_block(&any));
         for (int b = 0; b < B; ++b) cost_hist[b] = rd[1 + b];
     }
-    int h = 0, head = 0;
     for (int k = 0; k < iters; ++k) {
         // direction: the two-loop recursion, or (k_ldecide) a scaled steepest-descent
         // step for an instance without a usable pair or whose direction does not descend
@@ -565,20 +652,182 @@ meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const
         L_TRY(cudaGetLastError());
         L_DO(ldot<false>(c, c.S(head), c.Y(head), S.sy));
         L_DO(ldot<false>(c, c.Y(head), c.Y(head), S.yy));
-        k_lrho<<<ib, 128, 0, c.st>>>(B, head, k, S);
+        k_lrho<<<ib, 128, 0, c.st>>>(B, head, k0 + k, S);
         L_TRY(cudaGetLastError());
         head = (head + 1) % M.m;
         h = h < M.m ? h + 1 : M.m;
         if (cost_hist)  // L of every instance as of the last trial's read
             for (int b = 0; b < B; ++b) cost_hist[(size_t)(k + 1) * B + b] = rd[1 + b];
     }
-    if (iters_done) {
+    hdr[0] = kStateMagic;
+    hdr[1] = (long long)k0 + iters;
+    hdr[2] = h;
+    hdr[3] = head;
+    L_TRY(cudaMemcpyAsync(c.base + M.oHdr, hdr, sizeof(hdr), cudaMemcpyHostToDevice, c.st));
+    if (iters_done)
         L_TRY(cudaMemcpyAsync(iters_done, S.done, sizeof(int) * B, cudaMemcpyDeviceToHost, c.st));
-        L_TRY(cudaStreamSynchronize(c.st));
-    } else {
-        L_TRY(cudaStreamSynchronize(c.st));
-    }
+    L_TRY(cudaStreamSynchronize(c.st));  // also keeps hdr alive until its copy is done
 #undef L_DO
+    return META_OK;
+}
+
+meta_status meta_lbfgs_minimize(const meta_problem* prob, const float* I0, const float* J,
+                                float* p0, const float* mu, const float* rho,
+                                const float* lambda, int iters, int m, float h0, void* ws,
+                                size_t ws_bytes, void* lws, size_t lws_bytes, double* cost_hist,
+                                int* iters_done, void* stream) {
+    return lbfgs_run(prob, I0, J, p0, mu, rho, lambda, iters, m, h0, ws, ws_bytes, lws,
+                     lws_bytes, cost_hist, iters_done, stream, false);
+}
+
+meta_status meta_lbfgs_resume(const meta_problem* prob, const float* I0, const float* J,
+                              float* p0, const float* mu, const float* rho, const float* lambda,
+                              int iters, int m, float h0, void* ws, size_t ws_bytes, void* lws,
+                              size_t lws_bytes, double* cost_hist, int* iters_done,
+                              void* stream) {
+    return lbfgs_run(prob, I0, J, p0, mu, rho, lambda, iters, m, h0, ws, ws_bytes, lws,
+                     lws_bytes, cost_hist, iters_done, stream, true);
+}
+
+
+meta_status meta_lbfgs_state_size(const meta_problem* prob, int m, size_t* bytes) {
+    size_t lb = 0;
+    const meta_status s = meta_lbfgs_workspace_size(prob, m, &lb);  // validates prob, m
+    if (s != META_OK) return s;
+    long long N = 1;
+    for (int a = 0; a < prob->ndim; ++a) N *= prob->dims[a];
+    *bytes = sizeof(LStateFile) + state_payload(lbfgs_map(N, prob->batch, m));
+    return META_OK;
+}
+
+meta_status meta_lbfgs_state_check(const meta_problem* prob, int m, const void* host,
+                                   size_t host_bytes) {
+    size_t need = 0;
+    meta_status s = meta_lbfgs_state_size(prob, m, &need);
+    if (s != META_OK) return s;
+    if (!host) return META_ERR_INVALID_ARG;
+    if (host_bytes != need) return META_ERR_FORMAT;
+    LStateFile f;
+    std::memcpy(&f, host, sizeof(f));
+    if (std::memcmp(f.magic, kStateTag, 8) != 0 || f.version != kStateVersion)
+        return META_ERR_FORMAT;
+    long long N = 1;
+    for (int a = 0; a < prob->ndim; ++a) N *= prob->dims[a];
+    bool same = f.ndim == prob->ndim && f.batch == prob->batch && f.m == m &&
+                f.n == (uint64_t)N && f.payload == need - sizeof(LStateFile) && f.pad[0] == 0 &&
+                f.pad[1] == 0;
+    for (int a = 0; a < 3; ++a)
+        same = same && f.dims[a] == (a < prob->ndim ? prob->dims[a] : 0);
+    if (!same || f.k < 0 || f.h < 0 || f.h > m || f.head < 0 || f.head >= m)
+        return META_ERR_FORMAT;
+    const unsigned char* pay = static_cast<const unsigned char*>(host) + sizeof(LStateFile);
+    if (fnv1a64(pay, f.payload) != f.checksum) return META_ERR_FORMAT;
+    return META_OK;
+}
+
+meta_status meta_lbfgs_state_save(const meta_problem* prob, int m, const void* lws,
+                                  size_t lws_bytes, void* host, size_t host_bytes,
+                                  void* stream) {
+    size_t need = 0;
+    meta_status s = meta_lbfgs_state_size(prob, m, &need);
+    if (s != META_OK) return s;
+    if (!host || host_bytes < need) return META_ERR_INVALID_ARG;
+    LCtx c;
+    s = lsetup(prob, m, const_cast<void*>(lws), lws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const LMap& M = c.M;
+    long long hdr[4];
+    L_TRY(cudaMemcpyAsync(hdr, c.base + M.oHdr, sizeof(hdr), cudaMemcpyDeviceToHost, c.st));
+    L_TRY(cudaStreamSynchronize(c.st));
+    if (hdr[0] != kStateMagic) return META_ERR_FORMAT;  // no finished run in lws
+    unsigned char* out = static_cast<unsigned char*>(host);
+    LRegion r[8];
+    const int nr = state_regions(M, r);
+    size_t at = sizeof(LStateFile);
+    for (int i = 0; i < nr; ++i) {
+        L_TRY(cudaMemcpyAsync(out + at, c.base + r[i].off, r[i].bytes, cudaMemcpyDeviceToHost,
+                              c.st));
+        at += r[i].bytes;
+    }
+    L_TRY(cudaStreamSynchronize(c.st));
+    LStateFile f;
+    std::memset(&f, 0, sizeof(f));
+    std::memcpy(f.magic, kStateTag, 8);
+    f.version = kStateVersion;
+    f.ndim = prob->ndim;
+    for (int a = 0; a < prob->ndim; ++a) f.dims[a] = prob->dims[a];
+    f.batch = prob->batch;
+    f.m = m;
+    f.k = (int32_t)hdr[1];
+    f.h = (int32_t)hdr[2];
+    f.head = (int32_t)hdr[3];
+    f.n = (uint64_t)M.N;
+    f.payload = need - sizeof(LStateFile);
+    f.checksum = fnv1a64(out + sizeof(LStateFile), f.payload);
+    std::memcpy(out, &f, sizeof(f));
+    return META_OK;
+}
+
+meta_status meta_lbfgs_state_load(const meta_problem* prob, int m, const void* host,
+                                  size_t host_bytes, void* lws, size_t lws_bytes,
+                                  void* stream) {
+    meta_status s = meta_lbfgs_state_check(prob, m, host, host_bytes);
+    if (s != META_OK) return s;
+    LCtx c;
+    s = lsetup(prob, m, lws, lws_bytes, stream, &c);
+    if (s != META_OK) return s;
+    const LMap& M = c.M;
+    LStateFile f;
+    std::memcpy(&f, host, sizeof(f));
+    const unsigned char* in = static_cast<const unsigned char*>(host);
+    LRegion r[8];
+    const int nr = state_regions(M, r);
+    size_t at = sizeof(LStateFile);
+    for (int i = 0; i < nr; ++i) {
+        L_TRY(cudaMemcpyAsync(c.base + r[i].off, in + at, r[i].bytes, cudaMemcpyHostToDevice,
+                              c.st));
+        at += r[i].bytes;
+    }
+    const long long hdr[4] = {kStateMagic, f.k, f.h, f.head};
+    L_TRY(cudaMemcpyAsync(c.base + M.oHdr, hdr, sizeof(hdr), cudaMemcpyHostToDevice, c.st));
+    L_TRY(cudaStreamSynchronize(c.st));  // the host buffers may go once this returns
+    return META_OK;
+}
+
+meta_status meta_gd_minimize(const meta_problem* prob, const float* I0, const float* J,
+                             float* p0, const float* mu, const float* rho, const float* lambda,
+                             int iters, float h0, void* ws, size_t ws_bytes, void* lws,
+                             size_t lws_bytes, double* cost_hist, void* stream) {
+    if (!I0 || !J || !p0 || !mu || !rho || !lambda || iters < 0 || !(h0 > 0.f))
+        return META_ERR_INVALID_ARG;
+    LCtx c;
+    meta_status st = lsetup(prob, 1, lws, lws_bytes, stream, &c);
+    if (st != META_OK) return st;
+    const LMap& M = c.M;
+    const int B = M.B;
+    const dim3 vg = vec_grid(M.N, B);
+    const int ib = (B + 127) / 128;
+    float* g = c.vec(M.oG);
+    double* cost = c.dbl(M.oCost);
+    std::vector<double> tri(3 * (size_t)B);
+    for (int k = 0; k <= iters; ++k) {
+        st = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, g, ws, ws_bytes, c.st);
+        if (st != META_OK) return st;
+        if (cost_hist) {  // the cost of iterate k (the host's one read per iteration)
+            L_TRY(cudaMemcpyAsync(tri.data(), cost, sizeof(double) * 3 * B,
+                                  cudaMemcpyDeviceToHost, c.st));
+            L_TRY(cudaStreamSynchronize(c.st));
+            for (int b = 0; b < B; ++b)
+                cost_hist[(size_t)k * B + b] = tri[3 * b] + tri[3 * b + 1] + tri[3 * b + 2];
+        }
+        if (k == iters) break;
+        st = ldot<true>(c, g, nullptr, c.dbl(M.oGmax));
+        if (st != META_OK) return st;
+        k_lgdcoef<<<ib, 128, 0, c.st>>>(B, h0, c.dbl(M.oGmax), c.dbl(M.oCoef));
+        k_laxpy<<<vg, kLT, 0, c.st>>>(M.N, c.dbl(M.oCoef), g, p0);
+        L_TRY(cudaGetLastError());
+    }
+    L_TRY(cudaStreamSynchronize(c.st));
     return META_OK;
 }
 

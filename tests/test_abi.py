@@ -39,8 +39,9 @@ def test_library_exports_every_declared_symbol(meta):
 
 def test_status_strings(meta):
     lib = meta._load()
-    for code in range(8):
-        assert lib.meta_status_string(code).decode()
+    for code in range(10):
+        assert lib.meta_status_string(code).decode() != "unknown status", code
+        assert meta.STATUS[code]
     assert lib.meta_status_string(99).decode() == "unknown status"
 
 
