@@ -1078,9 +1078,15 @@ def main():
     ap.add_argument("--ckpt", type=int, default=None,
                     help="step checkpoint stride (0: keep the whole trajectory; default: the "
                          "workload's, 5 for head128 and mri160, else 0)")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON tile-shape cache of the autotuner (meta_tuning_cache): shapes "
+                         "it holds are not re-timed, new results are added to it")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.tuning_cache and args.impl == "ours":
+        import paper_2106_08817_gb300 as meta
+        meta.tuning_cache(args.tuning_cache)
     if args.ckpt is None:
         args.ckpt = WORKLOAD_CKPT.get(args.workload, 0)
     if args.impl == "reference":

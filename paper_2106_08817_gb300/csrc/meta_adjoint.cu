@@ -90,14 +90,21 @@ struct Rec {
     static constexpr int kCell = 0, kI = NDIM + 1, kP = NDIM + 2, kD = NDIM + 3;
 };
 
+// The fields of a record (cell bits, f per axis, I^', p~^, div^) in the
+// order of Rec.
+template <int NDIM>
+struct RecVals {
+    float v[NDIM + 4];
+};
+
 // Record of step t at voxel v from I^' = Ih1, p^' = ph1, the displacement d
 // of the foot per axis and fac = div v_t (PDET: fac = J = det(Id - dt Dv_t))
 // (the same expressions as the forward step), with p_t at pprev.
 template <int NDIM, bool PDET = false, bool HYB = false>
-__device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
-                                            long long o, float Ih1, float ph1, const float* d,
-                                            float fac, const float* pprev,
-                                            float* rec) {
+__device__ __forceinline__ RecVals<NDIM> record_values(const Geom& g, const Coefs& cf,
+                                                       const Vox& v, float Ih1, float ph1,
+                                                       const float* d, float fac,
+                                                       const float* pprev) {
     const int b = v.b;
     const float mu = cf.mu[b], dt = cf.dt;
     const Feet<NDIM> F = feet_of<NDIM>(g, v, d);
@@ -118,21 +125,33 @@ __device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, cons
         off[a] = F.f[a].i0 - c[a];
         ins[a] = F.f[a].inside;
     }
-    const long long sl = (long long)g.B * g.inst;
-    float* r = rec + (long long)b * g.inst + o;
-    r[Rec<NDIM>::kCell * sl] = __int_as_float(pack_cell(off, ins));
+    RecVals<NDIM> r;
+    r.v[Rec<NDIM>::kCell] = __int_as_float(pack_cell(off, ins));
 #pragma unroll
-    for (int a = 0; a < NDIM; ++a) r[(1 + a) * sl] = F.f[a].f;
-    r[Rec<NDIM>::kI * sl] = Ih1;
+    for (int a = 0; a < NDIM; ++a) r.v[1 + a] = F.f[a].f;
+    r.v[Rec<NDIM>::kI] = Ih1;
     if constexpr (HYB) {
         // I' = I~ + dt mu p~: the adjoint of p~ is dt mu I^'
-        r[Rec<NDIM>::kP * sl] = __fmul_rn(__fmul_rn(dt, mu), Ih1);
-        r[Rec<NDIM>::kD * sl] = 0.f;
+        r.v[Rec<NDIM>::kP] = __fmul_rn(__fmul_rn(dt, mu), Ih1);
+        r.v[Rec<NDIM>::kD] = 0.f;
     } else {
-        r[Rec<NDIM>::kP * sl] = PDET ? rn_ptilde_hat_J(ph1, Ih1, dt, mu, fac)
-                                     : rn_ptilde_hat(ph1, Ih1, dt, mu, fac);
-        r[Rec<NDIM>::kD * sl] = rn_div_hat(dt, pw, ph1);
+        r.v[Rec<NDIM>::kP] = PDET ? rn_ptilde_hat_J(ph1, Ih1, dt, mu, fac)
+                                  : rn_ptilde_hat(ph1, Ih1, dt, mu, fac);
+        r.v[Rec<NDIM>::kD] = rn_div_hat(dt, pw, ph1);
     }
+    return r;
+}
+
+template <int NDIM, bool PDET = false, bool HYB = false>
+__device__ __forceinline__ void emit_record(const Geom& g, const Coefs& cf, const Vox& v,
+                                            long long o, float Ih1, float ph1, const float* d,
+                                            float fac, const float* pprev,
+                                            float* rec) {
+    const RecVals<NDIM> r = record_values<NDIM, PDET, HYB>(g, cf, v, Ih1, ph1, d, fac, pprev);
+    const long long sl = (long long)g.B * g.inst;
+    float* w = rec + (long long)v.b * g.inst + o;
+#pragma unroll
+    for (int k = 0; k < NDIM + 4; ++k) w[k * sl] = r.v[k];
 }
 
 // Record of step t at voxel v (pitched offset o in its instance) from
@@ -1113,6 +1132,173 @@ __device__ __forceinline__ void body_adj_gradp(const K& kb, Geom g, Coefs cf, in
 }
 
 
+// 3-D adj_gradp with the momentum update p' = p~ (1 - dt div v), two voxels per
+// thread: x and x + 1 (x even), a CTA of 16 x 8 threads covering 32 x 8 voxels.
+// Each voxel takes exactly the expressions of body_adj_gradp and build_record
+// in the same order; the pair only shares its loads (8-byte loads where the
+// two voxels read adjacent addresses, the x neighbours x - 1 and x + 2 once)
+// and writes its record fields and raw adjoints as 8-byte pairs.
+__device__ __forceinline__ float2 ldg2(const float* p) {
+    return *reinterpret_cast<const float2*>(p);
+}
+__device__ __forceinline__ void st2(float* p, float a, float b, bool both) {
+    if (both) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else p[0] = a;
+}
+
+template <class K>
+__device__ __forceinline__ void body_adj_gradp3_pair(const K& kb, Geom g, Coefs cf, int t, int mode, Slots sl, const float* states, const float* u, const unsigned int* maxdisp, const float* mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
+    const int nyt = (g.ny + kPY - 1) / kPY;
+    const int z = div_nyt(g, kb.by());
+    const int y = (kb.by() - z * nyt) * kPY + kb.ty();
+    const int x = kb.bx() * kPX + 2 * kb.tx();
+    const int b = kb.bz();
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    const bool two = x + 1 < g.nx;  // the pair's second voxel exists
+    const long long o = gidx(g, z, y, x);
+    const long long ob = (long long)b * g.inst + o;
+    const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
+    const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
+    const float2 ph2 = ldg2(php + ob), Ih2 = ldg2(Ihp + ob);
+    float phv[2] = {ph2.x, ph2.y}, Ihv[2] = {Ih2.x, Ih2.y};
+    if (t > 0 && gather_radius(maxdisp, t - 1, g.B, b) > GatherTile<3>::RMAX) {
+        st2(Ihp + ob, 0.f, 0.f, two);  // the next (earlier) step scatters into these
+        st2(php + ob, 0.f, 0.f, two);
+    }
+    const float2 p2 = ldg2(pt + o);
+    const float pc[2] = {p2.x, p2.y};
+    float kg[2] = {0.f, 0.f};  // sum_a g_a u_a (cost gradient at t = 0)
+    const int cz[2] = {z, z}, cy[2] = {y, y};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float* ma = mh + ((long long)a * g.B + b) * g.inst;
+        const float2 m2 = ldg2(ma + o);
+        const float mc[2] = {m2.x, m2.y};
+        float ga[2], r[2] = {0.f, 0.f};
+        if (a < 2) {  // z or y: both voxels read the same rows
+            const long long sa = a == 0 ? g.slab : (long long)g.P;
+            const int c = a == 0 ? cz[0] : cy[0], n = a == 0 ? g.nz : g.ny;
+            const long long hi = (c < n - 1) ? sa : 0, lo = (c > 0) ? sa : 0;
+            const float2 Ih = ldg2(It + o + hi), Il = ldg2(It + o - lo);
+            ga[0] = 0.5f * (Ih.x - Il.x);
+            ga[1] = 0.5f * (Ih.y - Il.y);
+            float2 mlo = make_float2(0.f, 0.f), plo = mlo, mhi = mlo, phi = mlo;
+            if (c >= 1) {
+                mlo = ldg2(ma + o - sa);
+                plo = ldg2(pt + o - sa);
+            }
+            if (c <= n - 2) {
+                mhi = ldg2(ma + o + sa);
+                phi = ldg2(pt + o + sa);
+            }
+            const float ml[2] = {mlo.x, mlo.y}, pl[2] = {plo.x, plo.y};
+            const float mhv[2] = {mhi.x, mhi.y}, phh[2] = {phi.x, phi.y};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (c >= 1) r[k] = __fmaf_rn(0.5f, __fmul_rn(ml[k], pl[k]), r[k]);
+                if (c == n - 1) r[k] = __fmaf_rn(0.5f, __fmul_rn(mc[k], pc[k]), r[k]);
+                if (c <= n - 2) r[k] = __fmaf_rn(-0.5f, __fmul_rn(mhv[k], phh[k]), r[k]);
+                if (c == 0) r[k] = __fmaf_rn(-0.5f, __fmul_rn(mc[k], pc[k]), r[k]);
+            }
+        } else {  // x: the pair's own columns and the neighbours x - 1, x + 2
+            const float2 I2 = ldg2(It + o);
+            const float Iw = x > 0 ? It[o - 1] : 0.f;
+            const float Ie = x + 2 < g.nx ? It[o + 2] : 0.f;
+            ga[0] = 0.5f * ((x < g.nx - 1 ? I2.y : I2.x) - (x > 0 ? Iw : I2.x));
+            ga[1] = 0.5f * ((x + 1 < g.nx - 1 ? Ie : I2.y) - I2.x);
+            const float mw = x > 0 ? ma[o - 1] : 0.f, pw = x > 0 ? pt[o - 1] : 0.f;
+            const float me = x + 2 < g.nx ? ma[o + 2] : 0.f, pe = x + 2 < g.nx ? pt[o + 2] : 0.f;
+            // voxel x (c = x)
+            if (x >= 1) r[0] = __fmaf_rn(0.5f, __fmul_rn(mw, pw), r[0]);
+            if (x == g.nx - 1) r[0] = __fmaf_rn(0.5f, __fmul_rn(mc[0], pc[0]), r[0]);
+            if (x <= g.nx - 2) r[0] = __fmaf_rn(-0.5f, __fmul_rn(mc[1], pc[1]), r[0]);
+            if (x == 0) r[0] = __fmaf_rn(-0.5f, __fmul_rn(mc[0], pc[0]), r[0]);
+            // voxel x + 1 (c = x + 1 >= 1)
+            r[1] = __fmaf_rn(0.5f, __fmul_rn(mc[0], pc[0]), r[1]);
+            if (x + 1 == g.nx - 1) r[1] = __fmaf_rn(0.5f, __fmul_rn(mc[1], pc[1]), r[1]);
+            if (x + 1 <= g.nx - 2) r[1] = __fmaf_rn(-0.5f, __fmul_rn(me, pe), r[1]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            phv[k] = __fmaf_rn(mc[k], ga[k], phv[k]);
+            Ihv[k] = __fadd_rn(Ihv[k], r[k]);
+        }
+        if (t == 0 && mode == 1) {
+            const float2 u2 = ldg2(slice_of(u, g, ((long long)sl.u0 * 3 + a) * g.B + b) + o);
+            kg[0] = __fmaf_rn(ga[0], u2.x, kg[0]);
+            kg[1] = __fmaf_rn(ga[1], u2.y, kg[1]);
+        }
+    }
+    if (mode == 0) {  // the record of step t-1 (build_record, two voxels)
+        const float rho = cf.rho[b], dtrho = cf.dt * rho;
+        float d[2][3], du[2] = {0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float* ua = slice_of(u, g, ((long long)sl.ut1 * 3 + a) * g.B + b);
+            const float2 uc = ldg2(ua + o);
+            d[0][a] = disp_of(dtrho, uc.x);
+            d[1][a] = disp_of(dtrho, uc.y);
+            float cd[2];
+            if (a < 2) {
+                const long long sa = a == 0 ? g.slab : (long long)g.P;
+                const int c = a == 0 ? z : y, n = a == 0 ? g.nz : g.ny;
+                const long long hi = (c < n - 1) ? sa : 0, lo = (c > 0) ? sa : 0;
+                const float2 uh = ldg2(ua + o + hi), ul = ldg2(ua + o - lo);
+                cd[0] = rn_cdiff(uh.x, ul.x);
+                cd[1] = rn_cdiff(uh.y, ul.y);
+            } else {
+                const float uw = x > 0 ? ua[o - 1] : 0.f;
+                const float ue = x + 2 < g.nx ? ua[o + 2] : 0.f;
+                cd[0] = rn_cdiff(x < g.nx - 1 ? uc.y : uc.x, x > 0 ? uw : uc.x);
+                cd[1] = rn_cdiff(x + 1 < g.nx - 1 ? ue : uc.y, uc.x);
+            }
+            du[0] = __fadd_rn(du[0], cd[0]);
+            du[1] = __fadd_rn(du[1], cd[1]);
+        }
+        const float* pprev = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
+        Vox v{b, z, y, x, true};
+        const RecVals<3> r0 = record_values<3>(g, cf, v, Ihv[0], phv[0], d[0],
+                                               __fmul_rn(-rho, du[0]), pprev);
+        RecVals<3> r1 = r0;
+        if (two) {
+            v.x = x + 1;
+            r1 = record_values<3>(g, cf, v, Ihv[1], phv[1], d[1], __fmul_rn(-rho, du[1]), pprev);
+        }
+        const long long sls = (long long)g.B * g.inst;
+        float* w = rec + ob;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) st2(w + k * sls, r0.v[k], r1.v[k], two);
+    } else if (mode == 3) {
+        st2(rawI + ob, Ihv[0], Ihv[1], two);
+        st2(rawP + ob, phv[0], phv[1], two);
+    } else {
+        const long long ci = (((long long)b * g.nz + z) * g.ny + y) * g.nx + x;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !two) break;
+            if (mode == 1) {
+                const float lam = cf.lambda[b], rho = cf.rho[b];
+                // every rounding explicit, as in gradp_tail
+                const float reg = __fadd_rn(__fmul_rn(2.f, kg[k]),
+                                            __fmul_rn(__fmul_rn(2.f, rho), pc[k]));
+                out0[ci + k] = __fadd_rn(phv[k], __fmul_rn(lam, reg));
+            } else {
+                out0[ci + k] = phv[k];
+                if (gI0) gI0[ci + k] = Ihv[k];
+            }
+        }
+    }
+}
+
+#ifndef META_BODIES_ONLY
+__global__ void __launch_bounds__(kPX * kPY / 2)
+k_adj_gradp3_pair(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
+    pdl_wait();  // the previous kernel's writes are visible from here on
+    pdl_trigger();
+    body_adj_gradp3_pair<HwBlk>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
+}
+#endif
+
 #ifndef META_BODIES_ONLY
 template <int NDIM, bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
@@ -1493,6 +1679,7 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
             e.smem = kGradp2dSmem;
         } else {
             e.grid = pgrid<3>(g);
+            if (!c.pdet) e.bx = kPX / 2;  // two voxels per thread
         }
         e.a.g = g;
         e.a.cf = c;
@@ -1519,10 +1706,14 @@ cudaError_t launch_adj_gradp(const Geom& g, int ndim, const Coefs& c, int t, int
         META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp2d<true> : k_adj_gradp2d<false>, grid, blk,
                                    kGradp2dSmem, st, g, c, t, mode, sl, states, u, maxdisp, mh, Ihp, php,
                                    rec, rawI, rawP, out0, gI0));
+    } else if (c.pdet) {
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp<3, true>, pgrid<3>(g), blk, 0, st, g, c, t, mode,
+                                   sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0,
+                                   gI0));
     } else {
-        META_CHECK_LAUNCH(launch_k(c.pdet ? k_adj_gradp<3, true> : k_adj_gradp<3, false>,
-                                   pgrid<3>(g), blk, 0, st, g, c, t, mode, sl, states, u, maxdisp,
-                                   mh, Ihp, php, rec, rawI, rawP, out0, gI0));
+        META_CHECK_LAUNCH(launch_k(k_adj_gradp3_pair, pgrid<3>(g), dim3(kPX / 2, kPY), 0, st, g, c,
+                                   t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP,
+                                   out0, gI0));
     }
     return cudaSuccess;
 }

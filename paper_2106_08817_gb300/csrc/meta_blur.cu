@@ -253,8 +253,8 @@ __device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm,
     float* s = reinterpret_cast<float*>(smem_raw + 128);
 
     const int tid = kb.tx();
-    const int tx = tid & 31;
-    const int ta = tid >> 5;
+    const int pair = tid & 15;           // column pair
+    const int grp = tid >> 4;            // group of kBA outputs along the axis
     const int x0 = kb.bx() * kTXS;
     const int slice = kb.bz();           // comp * B + b
     const int b = slice % g.B;
@@ -308,74 +308,53 @@ __device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm,
         if (tid == 0) mbar_inval(bar);  // every wait on it has returned
     }
 
-    const float* src = s + (ta * kBA) * kTXS + tx;
-    float acc[kBA];
+    // Thread (pair, grp): columns x0 + 2 pair and x0 + 2 pair + 1, outputs
+    // a0 + 16 grp .. + 15 along the axis.  The two columns form the two lanes of
+    // every packed FMA, so tap k reads one aligned 8-byte pair (the inputs of both
+    // columns at axis offset j + k) and no pair has to be assembled; each lane is
+    // the scalar fmaf chain over the taps in order, as before.
+    if (grp >= L / kBA) return;  // lanes that round the CTA up to whole warps
+    const float* src = s + (grp * kBA) * kTXS + 2 * pair;
+    float2 a2[kBA];
 #pragma unroll
-    for (int j = 0; j < kBA; ++j) acc[j] = 0.f;
+    for (int j = 0; j < kBA; ++j) a2[j] = make_float2(0.f, 0.f);
     if constexpr (KC > 0) {
-        // outputs in pairs (2i, 2i+1): tap k reads inputs (2i+k, 2i+k+1), an
-        // even-aligned pair for even k and an odd-aligned one for odd k; each
-        // lane is the scalar fmaf of the other branch, in the same order
-        constexpr int NW = 8 * KC + kBA;
-        float2 ev[NW / 2], od[NW / 2 - 1];
-#pragma unroll
-        for (int m = 0; m < NW / 2; ++m) ev[m] = make_float2(src[(2 * m) * kTXS], src[(2 * m + 1) * kTXS]);
-#pragma unroll
-        for (int m = 0; m < NW / 2 - 1; ++m) od[m] = make_float2(ev[m].y, ev[m + 1].x);
-        float2 a2[kBA / 2];
-#pragma unroll
-        for (int i = 0; i < kBA / 2; ++i) a2[i] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 8 * KC; ++k) {
             const float2 wt = make_float2(taps.w[k], taps.w[k]);
 #pragma unroll
-            for (int i = 0; i < kBA / 2; ++i)
-                a2[i] = ffma2(wt, (k & 1) ? od[i + (k >> 1)] : ev[i + (k >> 1)], a2[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < kBA / 2; ++i) {
-            acc[2 * i] = a2[i].x;
-            acc[2 * i + 1] = a2[i].y;
+            for (int j = 0; j < kBA; ++j)
+                a2[j] = ffma2(wt, lds2(src + (j + k) * kTXS), a2[j]);
         }
     } else {
-        float cur[kBA];
-#pragma unroll
-        for (int j = 0; j < kBA; ++j) cur[j] = src[j * kTXS];
         for (int kb = 0; kb < taps.kp; kb += 8) {
-            float win[kBA + 8];
-#pragma unroll
-            for (int j = 0; j < kBA; ++j) win[j] = cur[j];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) win[kBA + j] = src[(kb + kBA + j) * kTXS];
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
-                const float wt = taps.w[kb + kk];
+                const float2 wt = make_float2(taps.w[kb + kk], taps.w[kb + kk]);
 #pragma unroll
-                for (int j = 0; j < kBA; ++j) acc[j] = fmaf(wt, win[j + kk], acc[j]);
+                for (int j = 0; j < kBA; ++j)
+                    a2[j] = ffma2(wt, lds2(src + (j + kb + kk) * kTXS), a2[j]);
             }
-#pragma unroll
-            for (int j = 0; j < kBA; ++j) cur[j] = win[8 + j];
         }
     }
-    const int x = x0 + tx;
+    const int x = x0 + 2 * pair;
     if (x >= g.nx) return;
-    // outputs a = a0 + ta kBA + j along the axis: one pointer stepped by the
-    // axis stride (P for y, slab for z)
-    const int a_first = a0 + ta * kBA;
+    // outputs a = a0 + grp kBA + j along the axis: one pointer stepped by the
+    // axis stride (P for y, slab for z); the pair (x, x + 1) is one 8-byte store
+    // (x is even and the row pitch a multiple of 4, so x + 1 < P)
+    const int a_first = a0 + grp * kBA;
     const long long stride = (NDIM == 3 && AXIS == 0) ? g.slab : (long long)g.P;
     float* op = out + (long long)(out_slice0 + slice) * g.inst +
                 ((NDIM == 2) ? gidx(g, 0, a_first, x)
                              : (AXIS == 1 ? gidx(g, z, a_first, x) : gidx(g, a_first, y, x)));
     const int nj = min(kBA, n_axis - a_first);
-    if (scale) {
-        const float sc = scale_mul * scale[b];
+    const float sc = scale ? scale_mul * scale[b] : 1.f;
 #pragma unroll
-        for (int j = 0; j < kBA; ++j)
-            if (j < nj) op[j * stride] = sc * acc[j];
-    } else {
-#pragma unroll
-        for (int j = 0; j < kBA; ++j)
-            if (j < nj) op[j * stride] = acc[j];
+    for (int j = 0; j < kBA; ++j) {
+        if (j < nj) {
+            const float2 v = scale ? make_float2(sc * a2[j].x, sc * a2[j].y) : a2[j];
+            *reinterpret_cast<float2*>(op + j * stride) = v;
+        }
     }
 }
 
@@ -530,7 +509,7 @@ static cudaError_t launch_strided_kc(const CUtensorMap& tm, const Taps& taps, co
     else
         gy = ((g.nz + L - 1) / L) * g.ny;
     dim3 grid((g.nx + kTXS - 1) / kTXS, gy, nslices);
-    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, L / kBA * 32, smem, st, tm, taps, g,
+    META_CHECK_LAUNCH(launch_k(k_strided<NDIM, AXIS, KC>, grid, strided_threads(L), smem, st, tm, taps, g,
                                in_slice0, out_slice0, scale, scale_mul, out, fault));
     return cudaSuccess;
 }
@@ -578,7 +557,7 @@ cudaError_t launch_strided(int ndim, int axis, const CUtensorMap& tm, const Taps
         e.sub = axis;
         e.kc = taps.kp / 8;
         e.grid = dim3((g.nx + kTXS - 1) / kTXS, gy, nslices);
-        e.bx = L / kBA * 32;
+        e.bx = strided_threads(L);
         e.by = 1;
         e.smem = strided_smem(L, taps.kp);
         e.a.g = g;

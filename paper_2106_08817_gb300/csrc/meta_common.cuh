@@ -21,6 +21,9 @@ constexpr int kRows = 16;      // x-pass: rows per CTA (2-D: 16 y; 3-D: 4 z x 4 
 constexpr int kBA = 16;        // strided pass: outputs per thread along the axis
 constexpr int kTA = 128;       // strided pass: largest tile length along the axis
 constexpr int kTXS = 32;       // strided pass: columns per CTA
+// strided pass: one thread per column pair and group of kBA outputs along the
+// axis (L / kBA groups of 16 threads), rounded up to whole warps
+inline int strided_threads(int L) { return (L / kBA * (kTXS / 2) + 31) / 32 * 32; }
 
 // Tiles of a blur pass split an extent n into ceil(n / maxlen) equal tiles,
 // each rounded up to a multiple of q, so that no CTA carries a mostly empty
@@ -403,6 +406,9 @@ __device__ __forceinline__ float ld_ro(const float* p) {
 
 __device__ __forceinline__ float4 lds4(const float* p) {
     return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float2 lds2(const float* p) {
+    return *reinterpret_cast<const float2*>(p);
 }
 
 // PDL is on unless the environment sets META_NO_PDL=1 (read once).

@@ -239,9 +239,9 @@ __device__ void run_tile(const VBlk& kb, const DPhase& ph, const CUtensorMap* tm
             break;
         case PK_GRADP:
             if (d3)
-                body_adj_gradp<VBlk, 3, false>(kb, a.g, a.cf, a.t, a.mode, a.sl, a.c[0], a.c[1],
-                                               a.cmd, a.c[2], a.w[0], a.w[1], a.w[2], a.w[3],
-                                               a.w[4], a.w[5], a.w[6]);
+                body_adj_gradp3_pair<VBlk>(kb, a.g, a.cf, a.t, a.mode, a.sl, a.c[0], a.c[1],
+                                           a.cmd, a.c[2], a.w[0], a.w[1], a.w[2], a.w[3],
+                                           a.w[4], a.w[5], a.w[6]);
             else
                 body_adj_gradp2d<VBlk, false>(kb, a.g, a.cf, a.t, a.mode, a.sl, a.c[0], a.c[1],
                                               a.cmd, a.c[2], a.w[0], a.w[1], a.w[2], a.w[3],
@@ -316,18 +316,24 @@ k_persist(const DPhase* __restrict__ phases, const long long* __restrict__ first
         const int t1 = min(t0 + P.per, P.ntiles);
         VBlk kb;
         kb.nthr = P.bx * P.by;
-        kb.tx_ = tid % P.bx;
-        kb.ty_ = tid / P.bx;
+        // the 3-D gradp tiles (128 threads, no barrier, no shared memory) run two
+        // at a time, one per half of the CTA
+        const int lanes = (P.kind == PK_GRADP && P.ndim == 3 && 2 * kb.nthr <= kPersistThreads)
+                              ? 2 : 1;
+        const int sub = tid / kb.nthr, ltid = tid - sub * kb.nthr;
+        kb.tx_ = ltid % P.bx;
+        kb.ty_ = ltid / P.bx;
         kb.ndx_ = P.bx;
         kb.gx_ = P.gx;
         const int gxy = P.gx * P.gy;
-        for (int t = t0; t < t1; ++t) {
-            kb.bz_ = t / gxy;
-            const int r = t - kb.bz_ * gxy;
+        for (int t = t0; t < t1; t += lanes) {
+            const int tt = t + sub;
+            kb.bz_ = tt / gxy;
+            const int r = tt - kb.bz_ * gxy;
             kb.by_ = r / P.gx;
             kb.bx_ = r - kb.by_ * P.gx;
-            if (tid < kb.nthr) run_tile(kb, P, tms, taps);
-            if (t + 1 < t1) __syncthreads();  // the next tile reuses the shared memory
+            if (sub < lanes && tt < t1) run_tile(kb, P, tms, taps);
+            if (t + lanes < t1) __syncthreads();  // the next tile reuses the shared memory
         }
         __syncthreads();
         if (tid == 0) {
