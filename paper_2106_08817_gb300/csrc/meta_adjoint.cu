@@ -257,31 +257,39 @@ __device__ __forceinline__ void body_cost_partials(const K& kb, Geom g, Slots sl
     const float* I0 = slice_of(states, g, ((long long)sl.s0 * 2 + 0) * g.B + b);
     const float* p0 = slice_of(states, g, ((long long)sl.s0 * 2 + 1) * g.B + b);
     double data = 0.0, kin = 0.0, res = 0.0;
-    // one warp per (z, y) row at a time; a fixed assignment, so fixed sums
+    // one warp per (z, y) row at a time; a fixed assignment, so fixed sums.
+    // Each lane sums its voxels of the row (at most ceil(nx / 32)) in FP32 and
+    // adds that to its FP64 totals once per row: FP64 arithmetic runs at a small
+    // fraction of the FP32 rate, and per voxel it bound the kernel.
     const int warp = kb.tx() >> 5, lane = kb.tx() & 31;
     const int nrows = g.nz * g.ny;
-    for (int row = kb.bx() * 8 + warp; row < nrows; row += kb.gx() * 8)
-    for (int x = lane; x < g.nx; x += 32) {
-        Vox v;
-        v.b = b;
-        v.z = row / g.ny;
-        v.y = row - v.z * g.ny;
-        v.x = x;
-        v.ok = true;
-        const long long o = gidx(g, v.z, v.y, v.x);
-        const float r = IT[o] - J[(long long)b * N + (long long)row * g.nx + x];
-        data += 0.5 * (double)r * (double)r;
-        int c[NDIM], n[NDIM];
-        long long s[NDIM];
-        axis_info<NDIM>(g, v, c, n, s);
-        const float p = p0[o];
+    for (int row = kb.bx() * 8 + warp; row < nrows; row += kb.gx() * 8) {
+        float ds = 0.f, ks = 0.f, rs = 0.f;
+        for (int x = lane; x < g.nx; x += 32) {
+            Vox v;
+            v.b = b;
+            v.z = row / g.ny;
+            v.y = row - v.z * g.ny;
+            v.x = x;
+            v.ok = true;
+            const long long o = gidx(g, v.z, v.y, v.x);
+            const float r = __fsub_rn(IT[o], J[(long long)b * N + (long long)row * g.nx + x]);
+            ds = __fmaf_rn(r, r, ds);
+            int c[NDIM], n[NDIM];
+            long long s[NDIM];
+            axis_info<NDIM>(g, v, c, n, s);
+            const float p = p0[o];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            const float ga = cdiff(I0, o, s[a], c[a], n[a]);
-            const float* ua = slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b);
-            kin += (double)(p * ga) * (double)ua[o];
+            for (int a = 0; a < NDIM; ++a) {
+                const float ga = cdiff(I0, o, s[a], c[a], n[a]);
+                const float* ua = slice_of(u, g, ((long long)sl.u0 * NDIM + a) * g.B + b);
+                ks = __fmaf_rn(__fmul_rn(p, ga), ua[o], ks);
+            }
+            rs = __fmaf_rn(p, p, rs);
         }
-        res += (double)p * (double)p;
+        data += 0.5 * (double)ds;
+        kin += (double)ks;
+        res += (double)rs;
     }
     double (*red)[256] = reinterpret_cast<double (*)[256]>(kb.smem());
     red[0][kb.tx()] = data;
