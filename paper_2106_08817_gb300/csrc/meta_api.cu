@@ -303,6 +303,7 @@ struct Ctx {
     Taps tx, ts;
     CUtensorMap tmI, tmP, tmSAy, tmSBz, tmSVx;
     CUtensorMap tmTr[3];  // 3-D transport: records 0..5, div^, (I_t, p_t)
+    CUtensorMap tmAdv[2];  // 3-D advect: u (3 components), (I_t, p_t)
     cudaStream_t st;
     unsigned int* fault;
     unsigned int* maxdisp;
@@ -382,6 +383,8 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
         ok &= encode_map5(&c->tmTr[0], g, c->REC, d + 4, 6);
         ok &= encode_map5(&c->tmTr[1], g, c->REC, d + 4, 1);
         ok &= encode_map5(&c->tmTr[2], g, c->states, 2 * L.nstate, 2);
+        ok &= encode_map5(&c->tmAdv[0], g, c->u, 3 * L.nu, 3);
+        c->tmAdv[1] = c->tmTr[2];
     }
     return ok ? META_OK : META_ERR_UNSUPPORTED;
 }
@@ -430,7 +433,8 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
         sl.ut = su;
         if (L.scheme == META_SCHEME_SL)
             META_LAUNCH(META_K_ADVECT, c.st,
-                        launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.st));
+                        launch_advect(g, d, cf, t, sl, c.states, c.u, c.maxdisp, c.tmAdv, c.fault,
+                                      c.st));
         else
             META_LAUNCH(META_K_EULER, c.st,
                         launch_euler(g, d, cf, t, sl, L.scheme == META_SCHEME_HYBRID, c.states,
@@ -817,7 +821,7 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
     if (L.ndim == 3) {
         out->lz = L.g.lz;
         out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 2, 2, 16);
-        out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 4, 4);
+        out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 3, 2, 16);
     } else {
         out->lz = out->zc_transport = out->zc_advect = 0;
     }

@@ -319,8 +319,12 @@ __device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm,
 #pragma unroll
     for (int j = 0; j < kBA; ++j) a2[j] = make_float2(0.f, 0.f);
     if constexpr (KC > 0) {
+        // taps past 2r are zero padding: their FMAs would add exact zeros, so the
+        // last chunk skips them (a uniform test)
+        const int khi = 2 * taps.r;
 #pragma unroll
         for (int k = 0; k < 8 * KC; ++k) {
+            if (k >= 8 * (KC - 1) && k > khi) continue;
             const float2 wt = make_float2(taps.w[k], taps.w[k]);
 #pragma unroll
             for (int j = 0; j < kBA; ++j)

@@ -104,7 +104,8 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* srcI, const floa
                           float* I1, float* p1, cudaStream_t st);
 // Forward step t: reads state slot sl.st and u slot sl.ut, writes slot sl.st1.
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
-                          float* states, const float* u, unsigned int* maxdisp, cudaStream_t st);
+                          float* states, const float* u, unsigned int* maxdisp,
+                          const CUtensorMap* maps, unsigned int* fault, cudaStream_t st);
 // Eulerian (hybrid = false) or hybrid step t: state slot sl.st -> sl.st1
 // with u slot sl.ut; the hybrid also records max |d| of step t in maxdisp.
 cudaError_t launch_euler(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,

@@ -202,7 +202,9 @@ __device__ void run_tile(const VBlk& kb, const DPhase& ph, const CUtensorMap* tm
             else run_strided<3, 0>(kb, ph, tms, taps);
             break;
         case PK_ADVECT:
-            if (d3) body_advect3d<VBlk, false>(kb, a.g, a.cf, a.t, a.sl, a.zc, a.w[0], a.c[0], a.md);
+            if (d3)
+                body_advect3d<VBlk, false>(kb, tms[ph.tm], tms[ph.tm + 1], a.g, a.cf, a.t, a.sl,
+                                           a.zc, a.w[0], a.md, a.fault);
             else body_advect2d<VBlk, false>(kb, a.g, a.cf, a.t, a.sl, a.w[0], a.c[0], a.md);
             break;
         case PK_COSTP:

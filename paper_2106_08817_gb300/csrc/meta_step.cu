@@ -150,175 +150,190 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const 
 }
 #endif
 
-// 3-D advect: a CTA owns a 32 x 8 column over planes [zs, zs + zc) and
-// marches along z.  Plane p of u (three components) and of I_t, p_t, with a
-// one-voxel y halo and x in [x0 - 4, x0 + 36), is staged by cp.async into a
-// ring of 4 plane slots (plane z + 2 loads while plane z is computed from
-// planes z-1 .. z+1).  Feet whose cell leaves the staged planes (per-step
+// 3-D advect: a CTA owns a 32 x 16 column over planes [zs, zs + zc) and
+// marches along z; each thread computes two adjacent rows (x, y0 + 2 ty) and
+// (x, y0 + 2 ty + 1).  Plane p of u (three components) and of I_t, p_t, with
+// a one-voxel y halo and x in [x0 - 4, x0 + 36), arrives by TMA (two tiled
+// copies from 5-D tensor maps over the u and state stacks, issued by one
+// thread, completing on an mbarrier per plane parity) into a ring of 4 plane
+// slots: plane p + 1 is in flight while the voxels of plane p - 1 are computed
+// from planes p - 2 .. p.  Planes outside the volume are never read, so none
+// is copied for them.  Feet whose cell leaves the staged window (per-step
 // displacements of a voxel or more) read global memory.
-constexpr int kAW = 40, kAUR = 10, kAIR = 10;          // window width, u rows, I/p rows
-constexpr int kAUS = kAW * kAUR, kAIS = kAW * kAIR;    // floats per staged field plane
-constexpr int kASlot = 3 * kAUS + 2 * kAIS;            // floats per ring slot
-constexpr int kAChunks = (3 * kAUR + 2 * kAIR) * (kAW / 4);
-constexpr int kAPer = (kAChunks + kPX * kPY - 1) / (kPX * kPY);
-constexpr int kARing = 4;                              // plane slots
-constexpr size_t kAdvMarchSmem = (size_t)kARing * kASlot * sizeof(float);
+constexpr int kAW = 40, kAH = 18, kAPL = kAW * kAH;  // staged window (x, y) of a plane
+constexpr int kAUF = 2176;                           // u fields of a slot (3 x 720, 128-byte multiple)
+constexpr int kASlot = kAUF + 2 * kAPL;              // then I_t, p_t
+constexpr int kARing = 4;                            // plane slots
+constexpr size_t kAdvMarchSmem = 128 + (size_t)kARing * kASlot * sizeof(float);
+constexpr uint32_t kABytes = 5 * kAPL * 4;           // bytes of one staged plane
+static_assert((kAUF * 4) % 128 == 0 && (kASlot * 4) % 128 == 0 && kAUF >= 3 * kAPL,
+              "TMA destinations start on 128-byte boundaries");
+
+// One voxel of the 3-D advect from the staged planes sm1, s0, sp1 (z - 1, z,
+// z + 1; window index ui of the voxel), the same expressions as the 2-D
+// advect and the record builders' feet.
+template <bool PDET>
+__device__ __forceinline__ void advect3d_voxel(const Geom& g, float rho, float mu, float dt,
+                                               float dtrho, int z, int y, int x, int y0, int x0,
+                                               int ui, const float* sm1, const float* s0,
+                                               const float* sp1, const float* It,
+                                               const float* pt, float* I1, float* p1,
+                                               float& dmax) {
+    float d[3];
+    float du = 0.f;
+    {  // axis 0 (z): neighbouring planes
+        d[0] = disp_of(dtrho, s0[ui]);
+        const float hi = (z < g.nz - 1) ? sp1[ui] : s0[ui];
+        const float lo = (z > 0) ? sm1[ui] : s0[ui];
+        du += 0.5f * (hi - lo);
+    }
+    {  // axis 1 (y)
+        const float* u1 = s0 + kAPL;
+        d[1] = disp_of(dtrho, u1[ui]);
+        du += 0.5f * (u1[ui + (y < g.ny - 1 ? kAW : 0)] - u1[ui - (y > 0 ? kAW : 0)]);
+    }
+    {  // axis 2 (x)
+        const float* u2 = s0 + 2 * kAPL;
+        d[2] = disp_of(dtrho, u2[ui]);
+        du += 0.5f * (u2[ui + (x < g.nx - 1 ? 1 : 0)] - u2[ui - (x > 0 ? 1 : 0)]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
+    const float div = -rho * du;  // div v, v = -rho u
+    float jac = 0.f;              // PDET: det(Id - dt Dv)
+    if constexpr (PDET) {
+        float A[3][3];  // A[a][e] = D_e u_a
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float* c0 = s0 + a * kAPL;
+            A[a][0] = rn_cdiff(z < g.nz - 1 ? sp1[a * kAPL + ui] : c0[ui],
+                               z > 0 ? sm1[a * kAPL + ui] : c0[ui]);
+            A[a][1] = rn_cdiff(c0[ui + (y < g.ny - 1 ? kAW : 0)], c0[ui - (y > 0 ? kAW : 0)]);
+            A[a][2] = rn_cdiff(c0[ui + (x < g.nx - 1 ? 1 : 0)], c0[ui - (x > 0 ? 1 : 0)]);
+        }
+        jac = rn_jac_det<3>(A, dtrho);
+    }
+    const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
+    const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
+    float Iw, pw;
+    if (kz >= 0 && kz + 1 < 3 && ky >= 0 && ky + 1 < kAH && kx >= 0 && kx + 1 < kAW) {
+        // planes z - 1 + kz and z + kz
+        const float* pl = kz == 0 ? sm1 : s0;
+        const float* ph = kz == 0 ? s0 : sp1;
+        const float* lo = pl + kAUF + ky * kAW + kx;
+        const float* hi = ph + kAUF + ky * kAW + kx;
+        Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
+        pw = trilin_pq<int>(lo + kAPL, hi + kAPL, kAW, fz.f, fy.f, fx.f);
+    } else {
+        const long long gi = gidx(g, fz.i0, fy.i0, fx.i0);
+        Iw = trilin<long long>(It + gi, g.P, g.slab, fz.f, fy.f, fx.f);
+        pw = trilin<long long>(pt + gi, g.P, g.slab, fz.f, fy.f, fx.f);
+    }
+    const long long o = gidx(g, z, y, x);
+    p1[o] = PDET ? pw * jac : pw * (1.f - dt * div);
+    I1[o] = Iw + (dt * mu) * pw;
+}
 
 template <class K, bool PDET>
-__device__ __forceinline__ void body_advect3d(const K& kb, Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
-    float* sm = reinterpret_cast<float*>(kb.smem());
+__device__ __forceinline__ void body_advect3d(const K& kb, const CUtensorMap& tmU, const CUtensorMap& tmS, Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, unsigned int* __restrict__ maxdisp, unsigned int* fault) {
+    unsigned char* smem_raw = kb.smem();
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [2]: planes of even / odd index
+    float* ring = reinterpret_cast<float*>(smem_raw + 128);
     const int b = kb.bz();
     const int nxc = (g.nx + 31) / 32;
     const int x0 = (kb.bx() % nxc) * 32;
     const int zs = (kb.bx() / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = kb.by() * 8;
+    const int y0 = kb.by() * 16;
     const int tx = kb.tx(), ty = kb.ty();
     const int tid = ty * kPX + tx;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool col_ok = x < g.nx && y < g.ny;
+    const int x = x0 + tx, ya = y0 + 2 * ty, yb = ya + 1;
+    const bool ok_a = x < g.nx && ya < g.ny, ok_b = x < g.nx && yb < g.ny;
     const float* It = slice_of(states, g, ((long long)sl.st * 2 + 0) * g.B + b);
     const float* pt = slice_of(states, g, ((long long)sl.st * 2 + 1) * g.B + b);
     float* I1 = slice_of(states, g, ((long long)sl.st1 * 2 + 0) * g.B + b);
     float* p1 = slice_of(states, g, ((long long)sl.st1 * 2 + 1) * g.B + b);
-    const float* ua[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ua[a] = slice_of(u, g, ((long long)sl.ut * 3 + a) * g.B + b);
-    // ring of 4 slots, each u0 u1 u2 I p [kAUR rows]; q[i] holds plane z - 1 + i
-    // while plane z is computed (rotated once per plane)
-    float* q[kARing];
-#pragma unroll
-    for (int i = 0; i < kARing; ++i) q[i] = sm + i * kASlot;
-    // this thread's 16-byte copies of every plane: source (plane 0), slot offset
-    const float* csrc[kAPer];
-    int cdst[kAPer];
-    bool cok[kAPer];
-#pragma unroll
-    for (int j = 0; j < kAPer; ++j) {
-        const int i = tid + j * kPX * kPY;
-        const int r = i / (kAW / 4), c = i - r * (kAW / 4);  // staged row, chunk
-        const float* base;
-        int yy, dst;
-        if (r < 3 * kAUR) {
-            const int a = r / kAUR, row = r - a * kAUR;
-            base = a == 0 ? ua[0] : (a == 1 ? ua[1] : ua[2]);
-            yy = y0 - 1 + row;
-            dst = a * kAUS + row * kAW + 4 * c;
-        } else {
-            const int f = (r - 3 * kAUR) / kAIR, row = (r - 3 * kAUR) - f * kAIR;
-            base = f == 0 ? It : pt;
-            yy = y0 - 1 + row;
-            dst = 3 * kAUS + f * kAIS + row * kAW + 4 * c;
+    // plane p sits in slot (p - zs + 1) mod 4
+    auto slot = [&](int p) { return ring + ((p - zs + 1) & 3) * kASlot; };
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if constexpr (K::kPersistent) {
+            tmap_acquire(&tmU);
+            tmap_acquire(&tmS);
+            fence_proxy_async_global();
         }
-        const int xx = x0 - 4 + 4 * c;
-        cok[j] = i < kAChunks && yy >= 0 && yy < g.ny && xx >= 0 && xx < g.P;
-        csrc[j] = cok[j] ? base + (long long)yy * g.P + xx : base;
-        cdst[j] = i < kAChunks ? dst : -1;
     }
-    auto load_plane = [&](float* d, int p) {
-        const bool zin = p >= 0 && p < g.nz;
-        const long long zo = zin ? (long long)p * g.slab : 0;
-#pragma unroll
-        for (int j = 0; j < kAPer; ++j)
-            if (cdst[j] >= 0) cp_async16(d + cdst[j], csrc[j] + (cok[j] && zin ? zo : 0),
-                                         cok[j] && zin);
-        asm volatile("cp.async.commit_group;" ::: "memory");
+    kb.sync();
+    auto load_plane = [&](int p) {
+        uint64_t* br = &bar[(p - zs + 1) & 1];
+        if (p >= 0 && p < g.nz) {
+            mbar_arrive_expect_tx(br, kABytes);
+            float* dst = slot(p);
+            tma_load_5d(dst, &tmU, br, x0 - 4, y0 - 1, p, b, 3 * sl.ut);
+            tma_load_5d(dst + kAUF, &tmS, br, x0 - 4, y0 - 1, p, b, 2 * sl.st);
+        } else {
+            mbar_arrive(br);
+        }
     };
     const float rho = cf.rho[b], mu = cf.mu[b], dt = cf.dt;
     const float dtrho = dt * rho;
-    const int ui = (ty + 1) * kAW + tx + 4;  // node in a u plane
+    const int uia = (2 * ty + 1) * kAW + tx + 4;  // window index of row a in a plane
     float dmax = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) load_plane(q[i], zs - 1 + i);
-    for (int z = zs; z < ze; ++z) {
-        kb.sync();  // every read of the slot of plane z-2 (now q[3]) is done
-        if (z + 2 <= ze) load_plane(q[3], z + 2);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // plane z+1 landed
-        kb.sync();
-        const float* sm1 = q[0];
-        const float* s0 = q[1];
-        const float* sp1 = q[2];
-        {
-            float* t0 = q[0];
-#pragma unroll
-            for (int i = 0; i < kARing - 1; ++i) q[i] = q[i + 1];
-            q[kARing - 1] = t0;
+    bool fine = true;
+    if (tid == 0) load_plane(zs - 1);
+    for (int p = zs - 1; p <= ze; ++p) {
+        const int j = p - zs + 1;  // planes staged so far
+        kb.sync();  // every read of the slot plane p + 1 reuses is done
+        if (tid == 0 && p + 1 <= ze) load_plane(p + 1);
+        bool landed = true;
+        if (tid < 32) landed = mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault);
+        if (kb.sync_or(!landed)) {
+            // leave together, after the copy of plane p + 1 (if any) has landed
+            if (tid < 32 && p + 1 <= ze)
+                mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1, fault, 100000000ull);
+            fine = false;
+            break;
         }
-        if (!col_ok) continue;
-        float d[3];
-        float du = 0.f;
-        {  // axis 0 (z): neighbouring planes
-            d[0] = disp_of(dtrho, s0[ui]);
-            const float hi = (z < g.nz - 1) ? sp1[ui] : s0[ui];
-            const float lo = (z > 0) ? sm1[ui] : s0[ui];
-            du += 0.5f * (hi - lo);
-        }
-        {  // axis 1 (y)
-            const float* u1 = s0 + kAUS;
-            d[1] = disp_of(dtrho, u1[ui]);
-            du += 0.5f * (u1[ui + (y < g.ny - 1 ? kAW : 0)] - u1[ui - (y > 0 ? kAW : 0)]);
-        }
-        {  // axis 2 (x)
-            const float* u2 = s0 + 2 * kAUS;
-            d[2] = disp_of(dtrho, u2[ui]);
-            du += 0.5f * (u2[ui + (x < g.nx - 1 ? 1 : 0)] - u2[ui - (x > 0 ? 1 : 0)]);
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
-        const float div = -rho * du;  // div v, v = -rho u
-        float jac = 0.f;  // PDET: det(Id - dt Dv)
-        if constexpr (PDET) {
-            float A[3][3];  // A[a][e] = D_e u_a
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float* c0 = s0 + a * kAUS;
-                A[a][0] = rn_cdiff(z < g.nz - 1 ? sp1[a * kAUS + ui] : c0[ui],
-                                   z > 0 ? sm1[a * kAUS + ui] : c0[ui]);
-                A[a][1] = rn_cdiff(c0[ui + (y < g.ny - 1 ? kAW : 0)], c0[ui - (y > 0 ? kAW : 0)]);
-                A[a][2] = rn_cdiff(c0[ui + (x < g.nx - 1 ? 1 : 0)], c0[ui - (x > 0 ? 1 : 0)]);
-            }
-            jac = rn_jac_det<3>(A, dtrho);
-        }
-        const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
-        const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
-        float Iw, pw;
-        if (kz >= 0 && kz + 1 < 3 && ky >= 0 && ky + 1 < kAIR && kx >= 0 && kx + 1 < kAW) {
-            // planes z - 1 + kz and z + kz
-            const float* pl = kz == 0 ? sm1 : s0;
-            const float* ph = kz == 0 ? s0 : sp1;
-            const float* lo = pl + 3 * kAUS + ky * kAW + kx;
-            const float* hi = ph + 3 * kAUS + ky * kAW + kx;
-            Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
-            pw = trilin_pq<int>(lo + kAIS, hi + kAIS, kAW, fz.f, fy.f, fx.f);
-        } else {
-            const long long gi = gidx(g, fz.i0, fy.i0, fx.i0);
-            Iw = trilin<long long>(It + gi, g.P, g.slab, fz.f, fy.f, fx.f);
-            pw = trilin<long long>(pt + gi, g.P, g.slab, fz.f, fy.f, fx.f);
-        }
-        const long long o = gidx(g, z, y, x);
-        p1[o] = PDET ? pw * jac : pw * (1.f - dt * div);
-        I1[o] = Iw + (dt * mu) * pw;
+        const int z = p - 1;  // planes z - 1 .. z + 1 are staged
+        if (z < zs) continue;
+        const float* sm1 = slot(z - 1);
+        const float* s0 = slot(z);
+        const float* sp1 = slot(z + 1);
+        if (ok_a)
+            advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, ya, x, y0, x0, uia, sm1, s0, sp1, It,
+                                 pt, I1, p1, dmax);
+        if (ok_b)
+            advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, yb, x, y0, x0, uia + kAW, sm1, s0,
+                                 sp1, It, pt, I1, p1, dmax);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
     __shared__ unsigned int s_m;
     if (tid == 0) s_m = 0u;
     kb.sync();
-    const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
-    if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    if (fine) {
+        const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+        if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
+    }
     kb.sync();
     if (tid == 0 && s_m != 0u) atomicMax(maxdisp + kMaxdispStride * ((long long)t * g.B + b), s_m);
+    if constexpr (K::kPersistent) {
+        if (tid == 0) {  // every wait on the barriers has returned (the barrier above)
+            mbar_inval(&bar[0]);
+            mbar_inval(&bar[1]);
+        }
+    }
 }
 
 
 #ifndef META_BODIES_ONLY
 template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
-k_advect3d(Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
+k_advect3d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS, Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, unsigned int* __restrict__ maxdisp, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_advect3d<HwBlk, PDET>(HwBlk{}, g, cf, t, sl, zc, states, u, maxdisp);
+    body_advect3d<HwBlk, PDET>(HwBlk{}, tmU, tmS, g, cf, t, sl, zc, states, maxdisp, fault);
 }
 #endif
 
@@ -506,7 +521,11 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
 }
 
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
-                          float* states, const float* u, unsigned int* maxdisp, cudaStream_t st) {
+                          float* states, const float* u, unsigned int* maxdisp,
+                          const CUtensorMap* maps, unsigned int* fault, cudaStream_t st) {
+    // 3-D: plane chunks of the 32 x 16 columns (3 CTAs per SM, 2 staged halo planes)
+    const int zc = ndim == 3 ? (g.zca > 0 ? g.zca : march_chunk(g, 3, 2, 16)) : 1;
+    const dim3 grid3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
     if (std::vector<PRec>* r = recorder()) {
         PRec e{};
         e.kind = PK_ADVECT;
@@ -518,10 +537,13 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
             e.grid = dim3((g.nx + kPX - 1) / kPX, (g.ny + kAdvTY - 1) / kAdvTY, g.B);
             e.smem = kAdv2dSmem;
         } else {
-            const int zc = g.zca > 0 ? g.zca : march_chunk(g, 4, 4);
-            e.grid = dim3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
+            e.grid = grid3;
             e.smem = kAdvMarchSmem;
             e.a.zc = zc;
+            e.ntm = 2;
+            e.tm[0] = maps[0];
+            e.tm[1] = maps[1];
+            e.a.fault = fault;
         }
         e.a.g = g;
         e.a.cf = c;
@@ -544,10 +566,8 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kAdvMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = g.zca > 0 ? g.zca : march_chunk(g, 4, 4);
-        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 7) / 8, g.B);
-        META_CHECK_LAUNCH(launch_k(kern, grid, blk, kAdvMarchSmem, st, g, c, t, sl, zc, states, u,
-                                   maxdisp));
+        META_CHECK_LAUNCH(launch_k(kern, grid3, blk, kAdvMarchSmem, st, maps[0], maps[1], g, c, t,
+                                   sl, zc, states, maxdisp, fault));
     }
     return cudaGetLastError();
 }
