@@ -281,17 +281,20 @@ typedef struct {
     int zc_advect;    /* 3-D only; in [1, dims[0]] */
     int ly;           /* multiple of 16 in [16, 128] */
     int lz;           /* 3-D only; multiple of 16 in [16, 128] */
-    int txw;          /* multiple of 8 in [8, 256] whose staged row txw + 2 (r4 + 8)
-                         fits one TMA box of 256 floats, r4 = ceil(3 sigma) rounded up
-                         to a multiple of 4 */
+    int txw;          /* multiple of 8 in [8, 256] whose staged row txw + 2 hx fits one
+                         TMA box of 256 floats; hx, the x halo, is the least multiple
+                         of 4 that is >= r + 1, >= r4 and >= kp - r4, with r =
+                         ceil(3 sigma), r4 = r rounded up to a multiple of 4 and kp =
+                         r4 + r + 1 rounded up to a multiple of 8 (20 for sigma 6) */
     int split;        /* meta_plan_create records the batch as this many sub-batches on
                          parallel graph branches, in [1, min(batch, 16)]; the eager calls
                          ignore it */
 } meta_tuning;
 
 /* Autotuner: times meta_cost_and_grad on these inputs (same arguments) for
- * candidate tile shapes (median of five calls after a warm-up), one field at a
- * time in the order above, keeps the fastest of each, then times recorded plans (meta_plan_create) for the batch
+ * candidate tile shapes (median of nine calls after a warm-up), one field at a
+ * time in the order above, in two sweeps; a field moves off its current value
+ * only for a candidate at least 1 % faster.  Then it times recorded plans (meta_plan_create) for the batch
  * split, and records the result for the problem shape in a process-wide table
  * that every later call and plan with that shape uses.  No field changes any
  * result: every output is summed in the same order.  Blocking: synchronises

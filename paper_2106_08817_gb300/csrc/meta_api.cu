@@ -158,10 +158,11 @@ Layout make_layout(const meta_problem* pr) {
     L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
     L.nstate = L.k ? L.nseg + L.k : pr->T + 1;
     L.nu = L.k ? L.k + 1 : pr->T;
-    // cost partial sums: one CTA of 8 warps per 8 rows, at most 4096 per instance
+    // cost partial sums: one CTA of 8 warps per 8 rows, at most 1024 per instance (a
+    // 3-D volume's CTAs take several rows per warp, and the final sum reads fewer)
     long long nblk = ((long long)g.nz * g.ny + 7) / 8;
     if (nblk < 1) nblk = 1;
-    if (nblk > 4096) nblk = 4096;
+    if (nblk > 1024) nblk = 1024;
     L.nblk = (int)nblk;
 
     const size_t fslice = (size_t)g.inst * 4;  // bytes of one pitched field
@@ -195,10 +196,8 @@ Layout make_layout(const meta_problem* pr) {
 //           kp = roundup(r4 + r + 1, 8)   (window starts r4 left of the output)
 //  strided: w[k']  = tap(k' - r) for k' in [0, 2r], kp = roundup(2r + 1, 8)
 // Radius of the x pass's staged halo: r = ceil(3 sigma) rounded up to 4.
-int xpass_r4(float sigma) {
-    const int r = (int)std::ceil(3.0 * (double)sigma);
-    return (r + 3) / 4 * 4;
-}
+int xpass_r(float sigma) { return (int)std::ceil(3.0 * (double)sigma); }
+int xpass_r4(float sigma) { return (xpass_r(sigma) + 3) / 4 * 4; }
 
 void make_taps(float sigma, Taps* xpass, Taps* strided) {
     const int r = (int)std::ceil(3.0 * (double)sigma);
@@ -365,7 +364,7 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     make_taps(pr->sigma, &c->tx, &c->ts);
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    const int LW = xpass_lw(g.txw, c->tx.r4);
+    const int LW = xpass_lw(g.txw, c->tx.r, c->tx.r4);
     const int nst = 2 * B * L.nstate;
     bool ok = true;
     if (d == 2) {
@@ -746,8 +745,8 @@ meta_status tuning_check(const meta_problem* prob, const meta_tuning* tun) {
     auto len_ok = [](int v, int q, int mx) { return v == 0 || (v >= q && v <= mx && v % q == 0); };
     if (!len_ok(tun->ly, kBA, 128) || !len_ok(tun->lz, kBA, 128) || !len_ok(tun->txw, kBX, 256))
         return META_ERR_INVALID_ARG;
-    // the x pass stages rows of txw + 2 (r4 + 8) floats by one TMA box (<= 256)
-    if (tun->txw && xpass_lw(tun->txw, xpass_r4(prob->sigma)) > kMaxLW)
+    // the x pass stages rows of txw + 2 hx floats by one TMA box (<= 256)
+    if (tun->txw && xpass_lw(tun->txw, xpass_r(prob->sigma), xpass_r4(prob->sigma)) > kMaxLW)
         return META_ERR_INVALID_ARG;
     if (tun->zc_transport < 0 || tun->zc_transport > nz || tun->zc_advect < 0 ||
         tun->zc_advect > nz)
@@ -850,13 +849,13 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         if (e0) cudaEventDestroy(e0);
         return META_ERR_CUDA;
     }
-    // one warm-up, then the median of five timed calls
+    // one warm-up, then the median of nine timed calls
     auto time_it = [&](float* ms) -> meta_status {
         meta_status r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws,
                                            ws_bytes, stream);
         if (r != META_OK) return r;
-        float tk[5];
-        for (int k = 0; k < 5; ++k) {
+        float tk[9];
+        for (int k = 0; k < 9; ++k) {
             if (cudaEventRecord(e0, st) != cudaSuccess) return META_ERR_CUDA;
             r = meta_cost_and_grad(prob, I0, J, p0, mu, rho, lambda, cost, grad, ws, ws_bytes,
                                    stream);
@@ -865,8 +864,8 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
                 return META_ERR_CUDA;
             if (cudaEventElapsedTime(&tk[k], e0, e1) != cudaSuccess) return META_ERR_CUDA;
         }
-        std::sort(tk, tk + 5);
-        *ms = tk[2];
+        std::sort(tk, tk + 9);
+        *ms = tk[4];
         return META_OK;
     };
     auto lens = [](int n, int q) {  // equal tiles of at most 48 .. 128
@@ -891,29 +890,44 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         std::vector<int> v;
         for (int m : {48, 64, 96, 128, 160, 192, 256}) {
             const int l = even_tile(nx, m, kBX);
-            if (xpass_lw(l, xpass_r4(prob->sigma)) <= kMaxLW &&
+            if (xpass_lw(l, xpass_r(prob->sigma), xpass_r4(prob->sigma)) <= kMaxLW &&
                 std::find(v.begin(), v.end(), l) == v.end())
                 v.push_back(l);
         }
         params.push_back({&cur.txw, v});
     }
+    // Two sweeps of one field at a time.  Each field keeps its current value (timed
+    // first) unless a candidate is at least 1 % faster, so that timing noise does
+    // not move a field between values of about the same speed.
     meta_status res = META_OK;
-    for (auto& pv : params) {
-        int best_v = *pv.first;
-        float best_ms = 1e30f;
-        for (int v : pv.second) {
-            *pv.first = v;
-            if (meta_tuning_set(prob, &cur) != META_OK) continue;  // over a launch limit
-            float ms = 0.f;
-            res = time_it(&ms);
-            if (res != META_OK) break;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_v = v;
+    for (int sweep = 0; sweep < 2 && res == META_OK; ++sweep) {
+        for (auto& pv : params) {
+            int best_v = *pv.first;
+            float best_ms = 1e30f;
+            if (meta_tuning_set(prob, &cur) == META_OK) {
+                res = time_it(&best_ms);
+                if (res != META_OK) break;
             }
+            for (int v : pv.second) {
+                if (v == best_v) continue;
+                const int keep = *pv.first;
+                *pv.first = v;
+                const bool ok = meta_tuning_set(prob, &cur) == META_OK;  // else a launch limit
+                float ms = 0.f;
+                if (ok) {
+                    res = time_it(&ms);
+                    if (res != META_OK) break;
+                }
+                *pv.first = keep;
+                if (ok && ms < 0.99f * best_ms) {
+                    best_ms = ms;
+                    best_v = v;
+                    *pv.first = v;
+                }
+            }
+            *pv.first = best_v;
+            if (res != META_OK) break;
         }
-        *pv.first = best_v;
-        if (res != META_OK) break;
     }
     // batch split of the recorded plan: time plan launches
     if (res == META_OK && prob->batch > 1) {

@@ -29,8 +29,8 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
 
-    const int HX = taps.r4 + 8;              // x halo (multiple of 4)
-    const int LW = xpass_lw(g.txw, taps.r4); // staged row length
+    const int HX = xpass_hx(taps.r, taps.r4);          // x halo (multiple of 4)
+    const int LW = xpass_lw(g.txw, taps.r, taps.r4);   // staged row length
     const int rowsI = (NDIM == 2) ? (kRows + 2) : 36;
     const int tid = kb.tx();
     const int x0 = kb.bx() * g.txw;
@@ -402,8 +402,8 @@ cudaError_t launch_wait_selftest(unsigned int* fault, unsigned long long limit_n
 
 // ------------------------------------------------------------ launchers
 
-size_t xpass_smem(int ndim, bool gradp, int txw, int r4) {
-    const int LW = xpass_lw(txw, r4);
+size_t xpass_smem(int ndim, bool gradp, int txw, int r, int r4) {
+    const int LW = xpass_lw(txw, r, r4);
     if (!gradp) return 128 + (size_t)kRows * LW * 4;
     const int rowsI = ndim == 2 ? kRows + 2 : 36;
     const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)((kRows * LW + 31) & ~31) +
@@ -418,7 +418,7 @@ static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tm
                                    const Taps& taps, const Geom& g, int sliceI, int sliceP,
                                    int out_slice0, int nslices, float* out, unsigned int* fault,
                                    cudaStream_t st) {
-    const size_t smem = xpass_smem(NDIM, GRADP, g.txw, taps.r4);
+    const size_t smem = xpass_smem(NDIM, GRADP, g.txw, taps.r, taps.r4);
     cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -469,7 +469,7 @@ cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUt
                       gradp ? g.B : nslices);
         e.bx = xpass_threads(g.txw);
         e.by = 1;
-        e.smem = xpass_smem(ndim, gradp, g.txw, taps.r4);
+        e.smem = xpass_smem(ndim, gradp, g.txw, taps.r, taps.r4);
         e.a.g = g;
         e.a.i0 = sliceI;
         e.a.i1 = sliceP;

@@ -34,12 +34,24 @@ inline int even_tile(int n, int maxlen, int q) {
     return (l + q - 1) / q * q;
 }
 
-// Staged row length of the x pass for tile width txw and halo r4 (+ 8
-// alignment columns per side): txw + 2 (r4 + 8), plus 4 pad columns where the
-// TMA box allows, so that the row stride in 16-byte units is odd and two rows
-// read by one quarter-warp hit all eight 16-byte bank groups.
-__host__ __device__ constexpr int xpass_lw(int txw, int r4) {
-    return txw + 2 * (r4 + 8) + ((txw + 2 * (r4 + 8) + 4 <= 256) ? 4 : 0);
+// x halo of the x pass for kernel radius r (r4 = r rounded up to 4): the
+// smallest multiple of 4 that (a) keeps every column a nonzero tap reaches at
+// least one column inside the staged row (its x neighbours are staged for the
+// gradient of m), (b) starts each output's tap window inside the row (>= r4) and
+// (c) ends the last thread's window of kp = roundup(r4 + r + 1, 8) taps inside
+// it.
+__host__ __device__ constexpr int xpass_hx(int r, int r4) {
+    const int kp = (r4 + r + 1 + 7) / 8 * 8;
+    const int a = r + 1, c = kp - r4;
+    const int m = a > r4 ? (a > c ? a : c) : (r4 > c ? r4 : c);
+    return (m + 3) / 4 * 4;
+}
+
+// Staged row length of the x pass for tile width txw: txw + 2 hx, plus 4 pad
+// columns where the TMA box allows, so that the row stride in 16-byte units is
+// odd and two rows read by one quarter-warp hit all eight 16-byte bank groups.
+__host__ __device__ constexpr int xpass_lw(int txw, int r, int r4) {
+    return txw + 2 * xpass_hx(r, r4) + ((txw + 2 * xpass_hx(r, r4) + 4 <= 256) ? 4 : 0);
 }
 
 // Threads of an x-pass CTA: kRows rows of txw / 8 threads, padded to a

@@ -72,7 +72,7 @@ long long persist_tiles(const PersistPlan* p);
 int persist_grid(const PersistPlan* p);
 
 // Blur passes (meta_blur.cu).
-size_t xpass_smem(int ndim, bool gradp, int txw, int r4);
+size_t xpass_smem(int ndim, bool gradp, int txw, int r, int r4);
 size_t strided_smem(int len, int kp);
 
 // Failure-path self-test: a bounded mbarrier wait that runs out after limit_ns

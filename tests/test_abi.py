@@ -126,17 +126,18 @@ def test_tuning_table_round_trip_and_validation(meta):
     assert meta.tuning(dims, B, s) == mine
     meta.set_tuning(dims, B, s, dict(ly=32))  # zero fields: built-in choice
     assert meta.tuning(dims, B, s)["ly"] == 32 and meta.tuning(dims, B, s)["lz"] == 80
-    # a whole 160-wide row per x tile: staged row 160 + 2 (20 + 8) + 4 = 220 <= 256
+    # a whole 160-wide row per x tile: staged row 160 + 2 x 20 + 4 = 204 <= 256 (halo 20:
+    # r = 18, r4 = 20, taps to 40 = r4 + 20)
     meta.set_tuning(dims, B, s, dict(txw=160))
     assert meta.tuning(dims, B, s)["txw"] == 160
     for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
                 dict(lz=-16), dict(zc_advect=-1), dict(split=2),  # split <= batch (1 here)
-                dict(txw=208), dict(txw=264)):  # staged rows of 264 and 320 floats
+                dict(txw=224), dict(txw=264)):  # staged rows of 264 and 304 floats
         with pytest.raises(meta.MetaError):
             meta.set_tuning(dims, B, s, bad)
-    with pytest.raises(meta.MetaError):  # sigma 18: r4 = 56, so 128 + 128 + 4 > 256 fits no wider
-        meta.set_tuning(dims, B, 18.0, dict(txw=136))
-    meta.set_tuning(dims, B, 18.0, dict(txw=128))
+    with pytest.raises(meta.MetaError):  # sigma 18: halo 56, so 144 + 112 = 256 fits no wider
+        meta.set_tuning(dims, B, 18.0, dict(txw=152))
+    meta.set_tuning(dims, B, 18.0, dict(txw=144))
     meta.set_tuning(dims, B, 18.0, None)
     with pytest.raises(meta.MetaError):
         meta.set_tuning((64, 64), 1, 2.0, dict(lz=16))  # 2-D problems have no z tiles
