@@ -411,7 +411,7 @@ meta_status forward_step(Ctx& c, const Coefs& cf, int t, int sin, int sout, int 
     const int d = L.ndim, B = g.B;
     float* ut = c.u + (size_t)su * d * B * g.inst;
     META_LAUNCH(META_K_XPASS_M, c.st,
-                launch_xpass(d, true, c.tmI, c.tmP, c.tx, g, 2 * sin * B, (2 * sin + 1) * B, 0, 0,
+                launch_xpass(d, true, c.tmI, c.tmP, c.tx, g, 2 * sin * B, (2 * sin + 1) * B, c.states, 0, 0,
                              c.SA, c.fault, c.st));
     if (d == 2) {
         META_LAUNCH(META_K_STRIDED_FWD, c.st,
@@ -576,7 +576,7 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
                         launch_adj_jacT(g, d, cf, sl, c.u, c.REC, c.SV, c.st));
         // m^ = K(-rho v^): x-pass SV -> SA, then the strided passes
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
-                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
+                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, nullptr, 0, d * B, c.SA,
                                  c.fault, c.st));
         float* mh;
         if (d == 2) {
@@ -652,7 +652,7 @@ meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, fl
                         launch_hybrid_p(g, d, cf, sl, c.states, c.u, rawP, c.PHP, c.SV, c.st));
         }
         META_LAUNCH(META_K_XPASS_ADJ, c.st,
-                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, 0, d * B, c.SA,
+                    launch_xpass(d, false, c.tmSVx, c.tmSVx, c.tx, g, 0, 0, nullptr, 0, d * B, c.SA,
                                  c.fault, c.st));
         float* mh;
         if (d == 2) {

@@ -24,7 +24,7 @@ namespace meta {
 // KC > 0: the tap loop has KC chunks of 8 at compile time (fully unrolled,
 // taps read as immediate constant-bank operands); KC = 0: runtime taps.kp.
 template <class K, int NDIM, bool GRADP, int KC>
-__device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps, Geom g, int sliceI, int sliceP, int out_slice0, float* __restrict__ out, unsigned int* fault) {
+__device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps, Geom g, int sliceI, int sliceP, const float* pin, int out_slice0, float* __restrict__ out, unsigned int* fault) {
     unsigned char* smem_raw = kb.smem();
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* base = reinterpret_cast<float*>(smem_raw + 128);
@@ -48,8 +48,7 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
 
     // sub-buffers start on 128-byte boundaries (TMA destinations)
     float* sI = base;
-    float* sP = GRADP ? sI + ((rowsI * LW + 31) & ~31) : nullptr;
-    float* sM = GRADP ? sP + ((kRows * LW + 31) & ~31) : base;
+    float* sM = GRADP ? sI + ((rowsI * LW + 31) & ~31) : base;
 
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -63,9 +62,8 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
             fence_proxy_async_global();
         }
         if constexpr (GRADP) {
-            mbar_arrive_expect_tx(bar, (uint32_t)((rowsI + kRows) * LW * 4));
+            mbar_arrive_expect_tx(bar, (uint32_t)(rowsI * LW * 4));
             tma_load_box<NDIM>(sI, &tmI, bar, x0 - HX, y0 - 1, z0 - 1, sliceI + b);
-            tma_load_box<NDIM>(sP, &tmP, bar, x0 - HX, y0, z0, sliceP + b);
         } else {
             mbar_arrive_expect_tx(bar, (uint32_t)(kRows * LW * 4));
             tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)kb.bz());
@@ -123,7 +121,13 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
                 const float4 yu = lds4(sI + (rI + (y < g.ny - 1 ? 1 : 0)) * LW + c);
                 const float4 yd = lds4(sI + (rI - (y > 0 ? 1 : 0)) * LW + c);
                 const float yuv[4] = {yu.x, yu.y, yu.z, yu.w}, ydv[4] = {yd.x, yd.y, yd.z, yd.w};
-                const float4 p4 = lds4(sP + row * LW + c);
+                // p at the item's four columns, read from global memory (not staged:
+                // the shared memory it would take keeps a third CTA off the SM); an
+                // item lies wholly inside or wholly outside the pitched row
+                const int xs = x0 - HX + c;
+                float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (xs >= 0 && xs < g.P)
+                    p4 = ld4_ro<K>(pin + (long long)(sliceP + b) * g.inst + gidx(g, z, y, xs));
                 const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
                 float zuv[4] = {0.f, 0.f, 0.f, 0.f}, zdv[4] = {0.f, 0.f, 0.f, 0.f};
                 if constexpr (NDIM == 3) {
@@ -238,10 +242,10 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
 #ifndef META_BODIES_ONLY
 template <int NDIM, bool GRADP, int KC>
 __global__ void __launch_bounds__(512)
-k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, int out_slice0, float* __restrict__ out, unsigned int* fault) {
+k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, const float* pin, int out_slice0, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     pdl_trigger();
-    body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{}, tmI, tmP, taps, g, sliceI, sliceP, out_slice0, out, fault);
+    body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{}, tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0, out, fault);
 }
 #endif
 
@@ -406,8 +410,7 @@ size_t xpass_smem(int ndim, bool gradp, int txw, int r, int r4) {
     const int LW = xpass_lw(txw, r, r4);
     if (!gradp) return 128 + (size_t)kRows * LW * 4;
     const int rowsI = ndim == 2 ? kRows + 2 : 36;
-    const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)((kRows * LW + 31) & ~31) +
-                     (size_t)ndim * kRows * LW;
+    const size_t f = (size_t)((rowsI * LW + 31) & ~31) + (size_t)ndim * kRows * LW;
     return 128 + f * 4;
 }
 
@@ -416,8 +419,8 @@ size_t strided_smem(int len, int kp) { return 128 + (size_t)kTXS * (len + kp) * 
 template <int NDIM, bool GRADP, int KC>
 static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tmP,
                                    const Taps& taps, const Geom& g, int sliceI, int sliceP,
-                                   int out_slice0, int nslices, float* out, unsigned int* fault,
-                                   cudaStream_t st) {
+                                   const float* pin, int out_slice0, int nslices, float* out,
+                                   unsigned int* fault, cudaStream_t st) {
     const size_t smem = xpass_smem(NDIM, GRADP, g.txw, taps.r, taps.r4);
     cudaError_t e = cudaFuncSetAttribute(k_xpass<NDIM, GRADP, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -427,18 +430,18 @@ static cudaError_t launch_xpass_kc(const CUtensorMap& tmI, const CUtensorMap& tm
               GRADP ? g.B : nslices);
     const int threads = xpass_threads(g.txw);
     META_CHECK_LAUNCH(launch_k(k_xpass<NDIM, GRADP, KC>, grid, threads, smem, st, tmI, tmP, taps, g,
-                               sliceI, sliceP, out_slice0, out, fault));
+                               sliceI, sliceP, pin, out_slice0, out, fault));
     return cudaSuccess;
 }
 
 // Compile-time tap loops for up to 7 chunks of 8 (sigma <= 8); runtime beyond.
 template <int NDIM, bool GRADP>
 static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP, const Taps& taps,
-                                  const Geom& g, int sliceI, int sliceP, int out_slice0,
+                                  const Geom& g, int sliceI, int sliceP, const float* pin, int out_slice0,
                                   int nslices, float* out, unsigned int* fault, cudaStream_t st) {
 #define META_XPASS_KC(K)                                                                      \
     case K:                                                                                   \
-        return launch_xpass_kc<NDIM, GRADP, K>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0, \
+        return launch_xpass_kc<NDIM, GRADP, K>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0, \
                                                nslices, out, fault, st);
     switch (taps.kp / 8) {
         META_XPASS_KC(1)
@@ -449,14 +452,14 @@ static cudaError_t launch_xpass_t(const CUtensorMap& tmI, const CUtensorMap& tmP
         META_XPASS_KC(6)
         META_XPASS_KC(7)
         default:
-            return launch_xpass_kc<NDIM, GRADP, 0>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+            return launch_xpass_kc<NDIM, GRADP, 0>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0,
                                                    nslices, out, fault, st);
     }
 #undef META_XPASS_KC
 }
 
 cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
-                         const Taps& taps, const Geom& g, int sliceI, int sliceP, int out_slice0,
+                         const Taps& taps, const Geom& g, int sliceI, int sliceP, const float* pin, int out_slice0,
                          int nslices, float* out, unsigned int* fault, cudaStream_t st) {
     if (std::vector<PRec>* r = recorder()) {
         PRec e{};
@@ -473,6 +476,7 @@ cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUt
         e.a.g = g;
         e.a.i0 = sliceI;
         e.a.i1 = sliceP;
+        e.a.c[0] = pin;
         e.a.i2 = out_slice0;
         e.a.w[0] = out;
         e.a.fault = fault;
@@ -485,13 +489,13 @@ cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUt
         return cudaSuccess;
     }
     if (ndim == 2)
-        return gradp ? launch_xpass_t<2, true>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+        return gradp ? launch_xpass_t<2, true>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0,
                                                nslices, out, fault, st)
-                     : launch_xpass_t<2, false>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                     : launch_xpass_t<2, false>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0,
                                                 nslices, out, fault, st);
-    return gradp ? launch_xpass_t<3, true>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0, nslices,
+    return gradp ? launch_xpass_t<3, true>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0, nslices,
                                            out, fault, st)
-                 : launch_xpass_t<3, false>(tmI, tmP, taps, g, sliceI, sliceP, out_slice0,
+                 : launch_xpass_t<3, false>(tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0,
                                             nslices, out, fault, st);
 }
 

@@ -416,6 +416,15 @@ __device__ __forceinline__ float ld_ro(const float* p) {
     else return __ldg(p);
 }
 
+// 16-byte read-only load: through the non-coherent path in an ordinary launch,
+// plain in the persistent kernel (its inputs may be written by other CTAs of
+// the same launch).
+template <class K>
+__device__ __forceinline__ float4 ld4_ro(const float* p) {
+    if constexpr (K::kPersistent) return *reinterpret_cast<const float4*>(p);
+    else return __ldg(reinterpret_cast<const float4*>(p));
+}
+
 __device__ __forceinline__ float4 lds4(const float* p) {
     return *reinterpret_cast<const float4*>(p);
 }

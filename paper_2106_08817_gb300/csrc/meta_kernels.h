@@ -84,7 +84,7 @@ cudaError_t launch_wait_selftest(unsigned int* fault, unsigned long long limit_n
 // out_slice0 + a*B + b.  Plain: reads slice sliceI + s through tmI and writes
 // out_slice0 + s, for s < nslices.
 cudaError_t launch_xpass(int ndim, bool gradp, const CUtensorMap& tmI, const CUtensorMap& tmP,
-                         const Taps& taps, const Geom& g, int sliceI, int sliceP, int out_slice0,
+                         const Taps& taps, const Geom& g, int sliceI, int sliceP, const float* pin, int out_slice0,
                          int nslices, float* out, unsigned int* fault, cudaStream_t st);
 
 // Strided pass along `axis` (2-D: 0 = y; 3-D: 1 = y, 0 = z) of slices

@@ -158,7 +158,7 @@ __device__ __forceinline__ void run_xpass(const VBlk& kb, const DPhase& ph,
     const PArgs& a = ph.a;
 #define META_X(KC)                                                                            \
     body_xpass<VBlk, NDIM, GRADP, KC>(kb, tms[ph.tm], tms[ph.tm + 1], taps[ph.taps], a.g,    \
-                                      a.i0, a.i1, a.i2, a.w[0], a.fault)
+                                      a.i0, a.i1, a.c[0], a.i2, a.w[0], a.fault)
     switch (ph.kc) { META_KC_CASES(META_X) }
 #undef META_X
 }
