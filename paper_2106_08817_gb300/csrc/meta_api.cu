@@ -184,8 +184,8 @@ Layout make_layout(const meta_problem* pr) {
     L.off_REC = take(fslice * (size_t)(d + 4) * B);
     L.off_IHP = take(fslice * B);
     L.off_PHP = take(fslice * B);
-    // raw I^, p^: at segment starts (stride k), or every step (Eulerian, hybrid)
-    L.off_RAW = (L.k || L.scheme != META_SCHEME_SL) ? take(fslice * 2 * B) : 0;
+    // raw I^, p^ of every step (Eulerian, hybrid)
+    L.off_RAW = L.scheme != META_SCHEME_SL ? take(fslice * 2 * B) : 0;
     L.total = off;
     return L;
 }
@@ -539,9 +539,9 @@ Slots start_slots(const Layout& L) {
 // Reverse sweep; REC holds the records of step T-1 on entry (from the adjoint
 // start of the cost or of meta_shoot_adjoint).  mode 1: cost gradient into out0; mode 2:
 // shooting adjoint into out0 / gI0.  With step checkpointing, each segment
-// but the last (still in place after the forward) is recomputed before its
-// steps; the adjoint of the segment's first step writes raw I^, p^ whose
-// record is built once the previous segment is back.
+// but the last (still in place after the forward) is recomputed from its
+// checkpoint just before the gradp of the step that follows it, so that every
+// gradp builds the record of the step before it directly.
 meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0);
 
 meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* gI0) {
@@ -550,20 +550,10 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    const int s_last = L.seg_of(L.T - 1);
     float* rawI = c.RAW;
     float* rawP = c.RAW ? c.RAW + (size_t)B * g.inst : nullptr;
     for (int t = L.T - 1; t >= 0; --t) {
         const int s = L.seg_of(t);
-        if (L.k && s != s_last && t == L.seg_end(s) - 1) {
-            meta_status st = recompute_segment(c, cf, s);
-            if (st != META_OK) return st;
-            Slots rs{};
-            rs.st1 = L.state_slot(t, s);
-            rs.ut1 = L.u_slot(t);
-            META_LAUNCH(META_K_ADJ_INIT, c.st,
-                        launch_adj_records(g, d, cf, rs, c.states, c.u, rawI, rawP, c.REC, c.st));
-        }
         Slots sl{};
         sl.st = L.state_slot(t, s);
         sl.ut = L.u_slot(t);
@@ -596,11 +586,18 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         int m;
         if (t == 0) {
             m = mode;
-        } else if (L.k && t == s * L.k) {
-            m = 3;  // step t-1 belongs to segment s-1, not recomputed yet
         } else {
+            if (L.k && t == s * L.k) {
+                // step t-1 ends segment s-1: that segment comes back from its
+                // checkpoint now, after this step's transport and blur and before its
+                // gradp, which then builds the record of step t-1 as in every other
+                // step (the recompute writes the segment slots, u slots, SA and SB,
+                // none of which this step still reads)
+                const meta_status st = recompute_segment(c, cf, s - 1);
+                if (st != META_OK) return st;
+            }
             m = 0;
-            sl.st1 = L.state_slot(t - 1, s);
+            sl.st1 = L.state_slot(t - 1, L.seg_of(t - 1));
             sl.ut1 = L.u_slot(t - 1);
         }
         META_LAUNCH(META_K_ADJ_GRADP, c.st,
