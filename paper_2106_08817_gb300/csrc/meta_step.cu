@@ -169,9 +169,46 @@ constexpr uint32_t kABytes = 5 * kAPL * 4;           // bytes of one staged plan
 static_assert((kAUF * 4) % 128 == 0 && (kASlot * 4) % 128 == 0 && kAUF >= 3 * kAPL,
               "TMA destinations start on 128-byte boundaries");
 
-// One voxel of the 3-D advect from the staged planes sm1, s0, sp1 (z - 1, z,
-// z + 1; window index ui of the voxel), the same expressions as the 2-D
-// advect and the record builders' feet.
+// The 3-D advect's arithmetic, every rounding explicit (no contraction), in the
+// expressions the adjoint's record builder uses: div v_t as -rho times the sum
+// of the central differences of u (rn_cdiff, summed over z, y, x), the
+// interpolated I and p by rn_lerp along x, then y, then z, p' = p~ (1 - dt div)
+// and I' = I~ + (dt mu) p~.  The forward therefore computes exactly the div and p~
+// that the records of the same step recompute.  Two rows (a pair) run the same
+// per-lane operations on packed FP32 pairs; one row runs them scalar.
+
+// Window index offsets of the central differences of row y (a row of the staged
+// window is kAW floats).
+__device__ __forceinline__ void adv_du_offsets(const Geom& g, int y, int x, int* yh, int* yl,
+                                               int* xh, int* xl) {
+    *yh = y < g.ny - 1 ? kAW : 0;
+    *yl = y > 0 ? kAW : 0;
+    *xh = x < g.nx - 1 ? 1 : 0;
+    *xl = x > 0 ? 1 : 0;
+}
+
+// Interpolated (I, p) at a foot from the staged window (planes pl, ph) or global memory.
+__device__ __forceinline__ float2 adv_interp(const Geom& g, const Foot1& fz, const Foot1& fy,
+                                             const Foot1& fx, int z, int y0, int x0,
+                                             const float* sm1, const float* s0,
+                                             const float* sp1, const float* It,
+                                             const float* pt) {
+    const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
+    if (kz >= 0 && kz + 1 < 3 && ky >= 0 && ky + 1 < kAH && kx >= 0 && kx + 1 < kAW) {
+        const float* pl = kz == 0 ? sm1 : s0;
+        const float* ph = kz == 0 ? s0 : sp1;
+        const float* lo = pl + kAUF + ky * kAW + kx;
+        const float* hi = ph + kAUF + ky * kAW + kx;
+        return make_float2(rn_trilin(lo, hi, kAW, fz.f, fy.f, fx.f),
+                           rn_trilin(lo + kAPL, hi + kAPL, kAW, fz.f, fy.f, fx.f));
+    }
+    const long long gi = gidx(g, fz.i0, fy.i0, fx.i0);
+    return make_float2(rn_trilin(It + gi, It + gi + g.slab, g.P, fz.f, fy.f, fx.f),
+                       rn_trilin(pt + gi, pt + gi + g.slab, g.P, fz.f, fy.f, fx.f));
+}
+
+// One voxel (row y, window index ui) from the staged planes sm1, s0, sp1 (z - 1,
+// z, z + 1).
 template <bool PDET>
 __device__ __forceinline__ void advect3d_voxel(const Geom& g, float rho, float mu, float dt,
                                                float dtrho, int z, int y, int x, int y0, int x0,
@@ -179,28 +216,19 @@ __device__ __forceinline__ void advect3d_voxel(const Geom& g, float rho, float m
                                                const float* sp1, const float* It,
                                                const float* pt, float* I1, float* p1,
                                                float& dmax) {
-    float d[3];
+    const float* u0 = s0;
+    const float* u1 = s0 + kAPL;
+    const float* u2 = s0 + 2 * kAPL;
+    int yh, yl, xh, xl;
+    adv_du_offsets(g, y, x, &yh, &yl, &xh, &xl);
+    const float d0 = __fmul_rn(dtrho, u0[ui]), d1 = __fmul_rn(dtrho, u1[ui]),
+                d2 = __fmul_rn(dtrho, u2[ui]);
     float du = 0.f;
-    {  // axis 0 (z): neighbouring planes
-        d[0] = disp_of(dtrho, s0[ui]);
-        const float hi = (z < g.nz - 1) ? sp1[ui] : s0[ui];
-        const float lo = (z > 0) ? sm1[ui] : s0[ui];
-        du += 0.5f * (hi - lo);
-    }
-    {  // axis 1 (y)
-        const float* u1 = s0 + kAPL;
-        d[1] = disp_of(dtrho, u1[ui]);
-        du += 0.5f * (u1[ui + (y < g.ny - 1 ? kAW : 0)] - u1[ui - (y > 0 ? kAW : 0)]);
-    }
-    {  // axis 2 (x)
-        const float* u2 = s0 + 2 * kAPL;
-        d[2] = disp_of(dtrho, u2[ui]);
-        du += 0.5f * (u2[ui + (x < g.nx - 1 ? 1 : 0)] - u2[ui - (x > 0 ? 1 : 0)]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dmax = fmaxf(dmax, fabsf(d[a]));
-    const float div = -rho * du;  // div v, v = -rho u
-    float jac = 0.f;              // PDET: det(Id - dt Dv)
+    du = __fadd_rn(du, rn_cdiff(z < g.nz - 1 ? sp1[ui] : u0[ui], z > 0 ? sm1[ui] : u0[ui]));
+    du = __fadd_rn(du, rn_cdiff(u1[ui + yh], u1[ui - yl]));
+    du = __fadd_rn(du, rn_cdiff(u2[ui + xh], u2[ui - xl]));
+    dmax = fmaxf(dmax, fmaxf(fabsf(d0), fmaxf(fabsf(d1), fabsf(d2))));
+    float fac;  // 1 - dt div v, or det(Id - dt Dv) for the det update
     if constexpr (PDET) {
         float A[3][3];  // A[a][e] = D_e u_a
 #pragma unroll
@@ -208,30 +236,109 @@ __device__ __forceinline__ void advect3d_voxel(const Geom& g, float rho, float m
             const float* c0 = s0 + a * kAPL;
             A[a][0] = rn_cdiff(z < g.nz - 1 ? sp1[a * kAPL + ui] : c0[ui],
                                z > 0 ? sm1[a * kAPL + ui] : c0[ui]);
-            A[a][1] = rn_cdiff(c0[ui + (y < g.ny - 1 ? kAW : 0)], c0[ui - (y > 0 ? kAW : 0)]);
-            A[a][2] = rn_cdiff(c0[ui + (x < g.nx - 1 ? 1 : 0)], c0[ui - (x > 0 ? 1 : 0)]);
+            A[a][1] = rn_cdiff(c0[ui + yh], c0[ui - yl]);
+            A[a][2] = rn_cdiff(c0[ui + xh], c0[ui - xl]);
         }
-        jac = rn_jac_det<3>(A, dtrho);
-    }
-    const Foot1 fz = foot1(z, d[0], g.nz), fy = foot1(y, d[1], g.ny), fx = foot1(x, d[2], g.nx);
-    const int kz = fz.i0 - (z - 1), ky = fy.i0 - (y0 - 1), kx = fx.i0 - (x0 - 4);
-    float Iw, pw;
-    if (kz >= 0 && kz + 1 < 3 && ky >= 0 && ky + 1 < kAH && kx >= 0 && kx + 1 < kAW) {
-        // planes z - 1 + kz and z + kz
-        const float* pl = kz == 0 ? sm1 : s0;
-        const float* ph = kz == 0 ? s0 : sp1;
-        const float* lo = pl + kAUF + ky * kAW + kx;
-        const float* hi = ph + kAUF + ky * kAW + kx;
-        Iw = trilin_pq<int>(lo, hi, kAW, fz.f, fy.f, fx.f);
-        pw = trilin_pq<int>(lo + kAPL, hi + kAPL, kAW, fz.f, fy.f, fx.f);
+        fac = rn_jac_det<3>(A, dtrho);
     } else {
-        const long long gi = gidx(g, fz.i0, fy.i0, fx.i0);
-        Iw = trilin<long long>(It + gi, g.P, g.slab, fz.f, fy.f, fx.f);
-        pw = trilin<long long>(pt + gi, g.P, g.slab, fz.f, fy.f, fx.f);
+        fac = __fsub_rn(1.f, __fmul_rn(dt, __fmul_rn(-rho, du)));
     }
+    const Foot1 fz = foot1(z, d0, g.nz), fy = foot1(y, d1, g.ny), fx = foot1(x, d2, g.nx);
+    const float2 w = adv_interp(g, fz, fy, fx, z, y0, x0, sm1, s0, sp1, It, pt);
     const long long o = gidx(g, z, y, x);
-    p1[o] = PDET ? pw * jac : pw * (1.f - dt * div);
-    I1[o] = Iw + (dt * mu) * pw;
+    p1[o] = __fmul_rn(w.y, fac);
+    I1[o] = __fadd_rn(w.x, __fmul_rn(__fmul_rn(dt, mu), w.y));
+}
+
+// Packed rn_lerp: (1 - f) a + f b per lane.
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 f, float2 omf) {
+    return fadd2(fmul2(omf, a), fmul2(f, b));
+}
+// Packed rn_trilin of two voxels whose corners start at pa / qa and pb / qb
+// (lower and upper plane, row stride kAW).
+__device__ __forceinline__ float2 trilin2(const float* pa, const float* qa, const float* pb,
+                                          const float* qb, float2 fz, float2 fy, float2 fx,
+                                          float2 oz, float2 oy, float2 ox) {
+    const float2 b0 = lerp2(lerp2(make_float2(pa[0], pb[0]), make_float2(pa[1], pb[1]), fx, ox),
+                            lerp2(make_float2(pa[kAW], pb[kAW]),
+                                  make_float2(pa[kAW + 1], pb[kAW + 1]), fx, ox),
+                            fy, oy);
+    const float2 b1 = lerp2(lerp2(make_float2(qa[0], qb[0]), make_float2(qa[1], qb[1]), fx, ox),
+                            lerp2(make_float2(qa[kAW], qb[kAW]),
+                                  make_float2(qa[kAW + 1], qb[kAW + 1]), fx, ox),
+                            fy, oy);
+    return lerp2(b0, b1, fz, oz);
+}
+
+// Rows y and y + 1 (window indices ui and ui + kAW) of the same column: the
+// operations of advect3d_voxel (momentum update p~ (1 - dt div v)) on packed
+// pairs, lane 0 the first row, lane 1 the second.
+__device__ __forceinline__ void advect3d_pair(const Geom& g, float rho, float mu, float dt,
+                                              float dtrho, int z, int y, int x, int y0, int x0,
+                                              int ui, const float* sm1, const float* s0,
+                                              const float* sp1, const float* It,
+                                              const float* pt, float* I1, float* p1,
+                                              float& dmax) {
+    const float* u0 = s0;
+    const float* u1 = s0 + kAPL;
+    const float* u2 = s0 + 2 * kAPL;
+    const int ub = ui + kAW;
+    int yha, yla, xh, xl, yhb, ylb;
+    adv_du_offsets(g, y, x, &yha, &yla, &xh, &xl);
+    adv_du_offsets(g, y + 1, x, &yhb, &ylb, &xh, &xl);
+    const float2 dr = make_float2(dtrho, dtrho);
+    const float2 d0 = fmul2(dr, make_float2(u0[ui], u0[ub]));
+    const float2 d1 = fmul2(dr, make_float2(u1[ui], u1[ub]));
+    const float2 d2 = fmul2(dr, make_float2(u2[ui], u2[ub]));
+    const float2 half = make_float2(0.5f, 0.5f);
+    const float* zh = z < g.nz - 1 ? sp1 : u0;
+    const float* zl = z > 0 ? sm1 : u0;
+    float2 du = make_float2(0.f, 0.f);
+    du = fadd2(du, fmul2(half, fsub2(make_float2(zh[ui], zh[ub]), make_float2(zl[ui], zl[ub]))));
+    du = fadd2(du, fmul2(half, fsub2(make_float2(u1[ui + yha], u1[ub + yhb]),
+                                     make_float2(u1[ui - yla], u1[ub - ylb]))));
+    du = fadd2(du, fmul2(half, fsub2(make_float2(u2[ui + xh], u2[ub + xh]),
+                                     make_float2(u2[ui - xl], u2[ub - xl]))));
+    dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(d0.x), fabsf(d0.y)),
+                             fmaxf(fmaxf(fabsf(d1.x), fabsf(d1.y)),
+                                   fmaxf(fabsf(d2.x), fabsf(d2.y)))));
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 fac = fsub2(one, fmul2(make_float2(dt, dt),
+                                        fmul2(make_float2(-rho, -rho), du)));
+    const Foot1 fza = foot1(z, d0.x, g.nz), fya = foot1(y, d1.x, g.ny), fxa = foot1(x, d2.x, g.nx);
+    const Foot1 fzb = foot1(z, d0.y, g.nz), fyb = foot1(y + 1, d1.y, g.ny),
+                fxb = foot1(x, d2.y, g.nx);
+    const int kza = fza.i0 - (z - 1), kya = fya.i0 - (y0 - 1), kxa = fxa.i0 - (x0 - 4);
+    const int kzb = fzb.i0 - (z - 1), kyb = fyb.i0 - (y0 - 1), kxb = fxb.i0 - (x0 - 4);
+    const bool sa = kza >= 0 && kza + 1 < 3 && kya >= 0 && kya + 1 < kAH && kxa >= 0 &&
+                    kxa + 1 < kAW;
+    const bool sb = kzb >= 0 && kzb + 1 < 3 && kyb >= 0 && kyb + 1 < kAH && kxb >= 0 &&
+                    kxb + 1 < kAW;
+    float2 Iw, pw;
+    if (sa && sb) {  // both feet inside the staged window: one packed interpolation
+        const float2 fz = make_float2(fza.f, fzb.f), fy = make_float2(fya.f, fyb.f),
+                     fx = make_float2(fxa.f, fxb.f);
+        const float2 oz = fsub2(one, fz), oy = fsub2(one, fy), ox = fsub2(one, fx);
+        const float* pa = (kza == 0 ? sm1 : s0) + kAUF + kya * kAW + kxa;
+        const float* qa = (kza == 0 ? s0 : sp1) + kAUF + kya * kAW + kxa;
+        const float* pb = (kzb == 0 ? sm1 : s0) + kAUF + kyb * kAW + kxb;
+        const float* qb = (kzb == 0 ? s0 : sp1) + kAUF + kyb * kAW + kxb;
+        Iw = trilin2(pa, qa, pb, qb, fz, fy, fx, oz, oy, ox);
+        pw = trilin2(pa + kAPL, qa + kAPL, pb + kAPL, qb + kAPL, fz, fy, fx, oz, oy, ox);
+    } else {
+        const float2 wa = adv_interp(g, fza, fya, fxa, z, y0, x0, sm1, s0, sp1, It, pt);
+        const float2 wb = adv_interp(g, fzb, fyb, fxb, z, y0, x0, sm1, s0, sp1, It, pt);
+        Iw = make_float2(wa.x, wb.x);
+        pw = make_float2(wa.y, wb.y);
+    }
+    const float2 pn = fmul2(pw, fac);
+    const float dm = __fmul_rn(dt, mu);
+    const float2 In = fadd2(Iw, fmul2(make_float2(dm, dm), pw));
+    const long long o = gidx(g, z, y, x);
+    p1[o] = pn.x;
+    I1[o] = In.x;
+    p1[o + g.P] = pn.y;
+    I1[o + g.P] = In.y;
 }
 
 template <class K, bool PDET>
@@ -301,12 +408,17 @@ __device__ __forceinline__ void body_advect3d(const K& kb, const CUtensorMap& tm
         const float* sm1 = slot(z - 1);
         const float* s0 = slot(z);
         const float* sp1 = slot(z + 1);
-        if (ok_a)
-            advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, ya, x, y0, x0, uia, sm1, s0, sp1, It,
-                                 pt, I1, p1, dmax);
-        if (ok_b)
-            advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, yb, x, y0, x0, uia + kAW, sm1, s0,
-                                 sp1, It, pt, I1, p1, dmax);
+        if (!PDET && ok_a && ok_b) {
+            advect3d_pair(g, rho, mu, dt, dtrho, z, ya, x, y0, x0, uia, sm1, s0, sp1, It, pt, I1,
+                          p1, dmax);
+        } else {
+            if (ok_a)
+                advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, ya, x, y0, x0, uia, sm1, s0, sp1,
+                                     It, pt, I1, p1, dmax);
+            if (ok_b)
+                advect3d_voxel<PDET>(g, rho, mu, dt, dtrho, z, yb, x, y0, x0, uia + kAW, sm1, s0,
+                                     sp1, It, pt, I1, p1, dmax);
+        }
     }
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
     __shared__ unsigned int s_m;
