@@ -388,20 +388,23 @@ __device__ __forceinline__ void body_advect3d(const K& kb, const CUtensorMap& tm
     const float dtrho = dt * rho;
     const int uia = (2 * ty + 1) * kAW + tx + 4;  // window index of row a in a plane
     float dmax = 0.f;
-    bool fine = true;
-    if (tid == 0) load_plane(zs - 1);
-    for (int p = zs - 1; p <= ze; ++p) {
+    // every warp waits (bounded) for each plane itself, so one CTA barrier per plane
+    // suffices; a wait that runs out raises s_fail, which all threads read after the
+    // next barrier and leave together
+    __shared__ int s_fail;
+    if (tid == 0) {
+        s_fail = 0;
+        load_plane(zs - 1);
+    }
+    int p = zs - 1;
+    for (; p <= ze; ++p) {
         const int j = p - zs + 1;  // planes staged so far
-        kb.sync();  // every read of the slot plane p + 1 reuses is done
+        kb.sync();  // every read of the slot plane p + 1 reuses is done; s_fail is seen
+        if (s_fail) break;
         if (tid == 0 && p + 1 <= ze) load_plane(p + 1);
-        bool landed = true;
-        if (tid < 32) landed = mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault);
-        if (kb.sync_or(!landed)) {
-            // leave together, after the copy of plane p + 1 (if any) has landed
-            if (tid < 32 && p + 1 <= ze)
-                mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1, fault, 100000000ull);
-            fine = false;
-            break;
+        if (!mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault)) {
+            s_fail = 1;
+            continue;
         }
         const int z = p - 1;  // planes z - 1 .. z + 1 are staged
         if (z < zs) continue;
@@ -420,11 +423,15 @@ __device__ __forceinline__ void body_advect3d(const K& kb, const CUtensorMap& tm
                                      sp1, It, pt, I1, p1, dmax);
         }
     }
+    if (p <= ze && tid < 32) {  // left after a wait ran out at plane p - 1: the copy of
+        const int j = p - zs + 1;  // plane p may still be in flight, so let it land
+        mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault, 100000000ull);  // (bounded)
+    }
     // one atomic per CTA (per-warp atomics on one word per instance serialise in L2)
     __shared__ unsigned int s_m;
     if (tid == 0) s_m = 0u;
     kb.sync();
-    if (fine) {
+    if (!s_fail) {
         const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
         if ((tid & 31) == 0 && m != 0u) atomicMax(&s_m, m);
     }
