@@ -812,7 +812,11 @@ __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensor
     // plane p sits in slots (p - zs + 1) mod 3 of A and mod 4 of B
     auto slotA = [&](int p) { return ringA + ((p - zs + 1) % kMSlotsA) * kMSA; };
     auto slotB = [&](int p) { return ringB + ((p - zs + 1) & 3) * kMSB; };
+    // every warp waits (bounded) for each plane itself; a wait that runs out raises
+    // s_fail, which all threads read after the barrier that follows the packing
+    __shared__ int s_fail;
     if (tid == 0) {
+        s_fail = 0;
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
@@ -849,17 +853,18 @@ __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensor
         const int j = p - zs + 1;  // planes staged so far
         kb.sync();  // every read of the slots plane p + 1 reuses, and of Q / PP, is done
         if (tid == 0 && p + 1 <= ze) load_plane(p + 1);
-        bool landed = true;
-        if (tid < 32) landed = mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault);
-        if (kb.sync_or(!landed)) {
+        if (!mbar_wait_bounded(&bar[j & 1], (j >> 1) & 1, fault)) s_fail = 1;
+        // (after a wait ran out the packing reads stale words at fixed in-bounds
+        // indices; its results are dropped below)
+        march_pack(slotA(p), Q, PP, g, x0, y0, p, tid);
+        kb.sync();
+        if (s_fail) {
             // leave together, after the copy of plane p + 1 (if any) has landed
             if (tid < 32 && p + 1 <= ze)
                 mbar_wait_bounded(&bar[(j + 1) & 1], ((j + 1) >> 1) & 1, fault, 100000000ull);
             kb.sync();
             return;
         }
-        march_pack(slotA(p), Q, PP, g, x0, y0, p, tid);
-        kb.sync();
         // plane p is at dz = -1 from nodes at p+1, 0 from p, +1 from p-1.  Sources
         // r = 0..3 (rows 2 ty - 1 .. 2 ty + 2 of the column), columns dx = 0..2
         // (x - 1 .. x + 1), each loaded and weighted along x and z once; each

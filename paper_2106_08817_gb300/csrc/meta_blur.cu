@@ -50,9 +50,11 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
     float* sI = base;
     float* sM = GRADP ? sI + ((rowsI * LW + 31) & ~31) : base;
 
+    __shared__ int s_fail;  // ordinary launch: a wait for the tiles ran out
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
+        s_fail = 0;
     }
     kb.sync();
     if (tid == 0) {
@@ -69,13 +71,21 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
             tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)kb.bz());
         }
     }
-    // warp 0 waits (bounded) while the others sleep in the barrier; the CTA
-    // leaves together if the wait ran out
-    bool landed = true;
-    if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
-    if (kb.sync_or(!landed)) return;
+    // Ordinary launch: every warp waits (bounded) itself and goes on as soon as the
+    // tiles have landed; a wait that runs out raises s_fail, which every thread reads
+    // after the barrier that ends the gradient phase (the plain pass has no later
+    // barrier, so its warps just leave).  Persistent kernel: warp 0 waits while the
+    // others sleep in the barrier, and the barrier is retired before the next tile.
     if constexpr (K::kPersistent) {
+        bool landed = true;
+        if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
+        if (kb.sync_or(!landed)) return;
         if (tid == 0) mbar_inval(bar);  // every wait on it has returned
+    } else {
+        if (!mbar_wait_bounded(bar, 0, fault)) {
+            if constexpr (!GRADP) return;
+            s_fail = 1;  // still takes part in the gradient phase's shuffles (reads are
+        }                // in bounds), then leaves with the others after its barrier
     }
 
     const int ncomp = GRADP ? NDIM : 1;
@@ -160,6 +170,9 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
                     make_float4(mo[a][0], mo[a][1], mo[a][2], mo[a][3]);
         }
         kb.sync();
+        if constexpr (!K::kPersistent) {
+            if (s_fail) return;
+        }
     }
 
     // Blur along x: thread (tx, row) -> outputs x0 + 8 tx .. + 7 of `row`,
@@ -303,13 +316,18 @@ __device__ __forceinline__ void body_strided(const K& kb, const CUtensorMap& tm,
         else
             tma_load_4d(s, &tm, bar, x0, y, a0 - taps.r, in_slice0 + slice);
     }
-    // warp 0 waits (bounded) while the others sleep in the barrier; the CTA
-    // leaves together if the wait ran out
-    bool landed = true;
-    if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
-    if (kb.sync_or(!landed)) return;
     if constexpr (K::kPersistent) {
+        // warp 0 waits (bounded) while the others sleep in the barrier; the tile
+        // leaves together if the wait ran out, and the barrier is retired before
+        // the next tile reuses the shared memory
+        bool landed = true;
+        if (tid < 32) landed = mbar_wait_bounded(bar, 0, fault);
+        if (kb.sync_or(!landed)) return;
         if (tid == 0) mbar_inval(bar);  // every wait on it has returned
+    } else {
+        // every warp waits (bounded) itself and starts as soon as the tile has
+        // landed: no barrier follows, so a warp whose wait ran out just leaves
+        if (!mbar_wait_bounded(bar, 0, fault)) return;
     }
 
     // Thread (pair, grp): columns x0 + 2 pair and x0 + 2 pair + 1, outputs
