@@ -425,8 +425,12 @@ meta_status meta_gd_minimize(const meta_problem* prob, const float* I0, const fl
  * META_ERR_TIMEOUT).  Bit 1 (information only): an adjoint step had per-step
  * displacements beyond the deterministic gather window (8 voxels or more in
  * 2-D, 4 or more in 3-D) and transposed the interpolation by an atomic scatter
- * instead, so its summation order is not fixed.  Synchronises `stream`.
- * clear != 0 resets it. */
+ * instead, so its summation order is not fixed.  Bit 2 (only in the
+ * bounds-checked debug build, libmeta_check.so, compiled with
+ * META_CHECK_BOUNDS): an index the kernels computed from the data (the lower
+ * corner of a foot, a record cell decoded by a transport) left its range; it was
+ * clamped, so nothing outside its buffer was read or written, but the call's
+ * results are invalid.  Synchronises `stream`.  clear != 0 resets it. */
 meta_status meta_workspace_status(void* ws, size_t ws_bytes, int clear, void* stream,
                                   unsigned int* fault_bits);
 

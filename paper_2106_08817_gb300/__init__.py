@@ -37,7 +37,9 @@ KERNEL_CLASSES = ("pack", "xpass_m", "strided_fwd", "advect", "cost", "adj_init"
 _LAUNCHES_PER_SCOPE = {"cost": 3}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libmeta.so")
+# META_LIB=check loads the bounds-checked debug build (_build.build(check=True))
+_LIB_PATH = os.path.join(_HERE, "libmeta_check.so" if os.environ.get("META_LIB") == "check"
+                         else "libmeta.so")
 _lib = None
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported shape", 3: "workspace",

@@ -14,6 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmeta.so")
+# the bounds-checked debug build (-DMETA_CHECK_BOUNDS): the same sources, its own objects
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libmeta_check.so")
 SOURCES = ["meta_api.cu", "meta_blur.cu", "meta_step.cu", "meta_adjoint.cu", "meta_noalloc.cu",
            "meta_lbfgs.cu", "meta_persist.cu", "meta_tuning.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,25 +34,32 @@ def _flags(extra: List[str]) -> List[str]:
                    "-I", INCLUDE, "-I", CSRC] + extra
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "meta.h"),
                                                                  __file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: List[str] = ()) -> str:
-    """Compile every .cu for sm_103a and link libmeta.so (skipped when up to date)."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: List[str] = (),
+          check: bool = False) -> str:
+    """Compile every .cu for sm_103a and link libmeta.so (skipped when up to date).
+    check=True: the bounds-checked debug build, libmeta_check.so (every data-dependent
+    index -- feet, decoded record cells -- checked and clamped, violations latched in
+    the workspace status word); load it with META_LIB=check."""
+    lib, bdir = (LIB_CHECK, BUILD_CHECK) if check else (LIB, BUILD)
+    if check:
+        extra = list(extra) + ["-DMETA_CHECK_BOUNDS"]
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc] + _flags(list(extra)) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
@@ -64,11 +74,11 @@ def build(force: bool = False, verbose: bool = False, extra: List[str] = ()) -> 
             failed.append(cmd[-3])
     if failed:
         raise RuntimeError("nvcc failed for %s" % ", ".join(failed))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-ldl"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -456,7 +456,9 @@ __device__ __forceinline__ void transport_r1_2d(const K& kb, const Geom& g, floa
         const int cell = __float_as_int(sC[mw]);
         const float fy = sF0[mw], fx = sF1[mw];
         const bool iny = (cell >> 24) & 1, inx = (cell >> 25) & 1;
-        const int ci = mw + cell_off(cell, 0) * W + cell_off(cell, 1);
+        // (R = 1: the cell is the node's own or the one below on each axis)
+        const int ci = mw + chk_range(g, cell_off(cell, 0), -1, 0) * W +
+                       chk_range(g, cell_off(cell, 1), -1, 0);
         float dIy, dIx, dPy, dPx;
         bilin_grad(sIt + ci, W, fy, fx, iny, inx, &dIy, &dIx);
         bilin_grad(sPt + ci, W, fy, fx, iny, inx, &dPy, &dPx);
@@ -565,7 +567,7 @@ __device__ __forceinline__ void transport_node(const K& kb, const Geom& g, const
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             f[a] = ld_ro<K>(rb + (1 + a) * rsl + o);
-            q0 += (long long)(c[a] + cell_off(cell, a)) * st[a];
+            q0 += (long long)chk_range(g, c[a] + cell_off(cell, a), 0, n[a] - 2) * st[a];
         }
         float* Isc = Ihp + (long long)b * g.inst;
         float* Psc = php + (long long)b * g.inst;
@@ -591,7 +593,7 @@ __device__ __forceinline__ void transport_node(const K& kb, const Geom& g, const
     int i0[NDIM];
 #pragma unroll
     for (int a = 0; a < NDIM; ++a) {
-        i0[a] = c[a] + cell_off(cell, a);
+        i0[a] = chk_range(g, c[a] + cell_off(cell, a), 0, n[a] - 2);
         F.f[a].i0 = i0[a];
         F.f[a].f = ld_ro<K>(rb + (1 + a) * rsl + o);
         F.f[a].inside = (cell >> (24 + a)) & 1;
@@ -747,7 +749,9 @@ __device__ __forceinline__ void transport_complete(const Geom& g, float dt, int 
     php[(long long)b * g.inst + o] = acc.y;
     const int cell = __float_as_int(A_z[mw]);
     const float fz = A_z[kMPL + mw], fy = A_z[2 * kMPL + mw], fx = A_z[3 * kMPL + mw];
-    const int ci = mw + cell_off(cell, 1) * kMW + cell_off(cell, 2);
+    // (R = 1: the cell is the node's own or the one below on each axis)
+    const int ci = mw + chk_range(g, cell_off(cell, 1), -1, 0) * kMW +
+                   chk_range(g, cell_off(cell, 2), -1, 0);
     const bool inz = (cell >> 24) & 1, iny = (cell >> 25) & 1, inx = (cell >> 26) & 1;
     float Iv, pv, dI[3], dP[3];
     trilin_grad_pq(B_lo + kMBI + ci, B_hi + kMBI + ci, kMW, fz, fy, fx, inz, iny, inx, &Iv, dI);
@@ -1069,7 +1073,7 @@ __device__ __forceinline__ void body_adj_gradp2d(const K& kb, Geom g, Coefs cf, 
                 du = __fadd_rn(du, rn_cdiff(sU1[c + xs], sU1[c - xl]));
                 fac = __fmul_rn(-rho, du);
             }
-            const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
+            const Foot1 fy = foot1g(g, y, d0, g.ny), fx = foot1g(g, x, d1, g.nx);
             const int off[3] = {fy.i0 - y, fx.i0 - x, 0};
             const bool ins[3] = {fy.inside, fx.inside, false};
             const float pw = rn_bilin(sPp + c + off[0] * W + off[1], W, fy.f, fx.f);

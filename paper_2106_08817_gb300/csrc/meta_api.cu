@@ -139,6 +139,7 @@ Layout make_layout(const meta_problem* pr) {
     g.ly = even_tile(g.ny, kTA, kBA);
     g.lz = d == 3 ? even_tile(g.nz, kTA, kBA) : kBA;
     g.zct = g.zca = 0;
+    g.chk = nullptr;  // set to the workspace status word by setup
     {
         const unsigned long long nyt = (unsigned long long)(g.ny + 7) / 8;
         g.nyt_mul = nyt == 1 ? 0u : (unsigned)(((1ull << 32) + nyt - 1) / nyt);
@@ -349,6 +350,7 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
     c->st = static_cast<cudaStream_t>(stream);
     const Layout& L = c->L;
     c->fault = reinterpret_cast<unsigned int*>(c->ws + L.off_fault);
+    c->L.g.chk = c->fault;
     c->maxdisp = reinterpret_cast<unsigned int*>(c->ws + L.off_maxdisp);
     c->partials = reinterpret_cast<double*>(c->ws + L.off_partials);
     auto F = [&](size_t off) { return reinterpret_cast<float*>(c->ws + off); };
@@ -707,7 +709,10 @@ meta_status cost_and_grad_impl(const meta_problem* prob, const float* I0, const 
     Ctx c;
     meta_status s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
-    if (fault) c.fault = fault;
+    if (fault) {
+        c.fault = fault;
+        c.L.g.chk = fault;
+    }
     const Geom& g = c.L.g;
     const Coefs cf{mu, rho, lambda, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
     META_LAUNCH(META_K_PACK, c.st,

@@ -71,6 +71,7 @@ constexpr int kMaxdispStride = 32;
 // Fault / information bits latched in the workspace header.
 constexpr unsigned kFaultTmaTimeout = 1u;  // a bounded TMA wait ran out (fault)
 constexpr unsigned kInfoScatter = 2u;      // adjoint used the atomic scatter (large steps)
+constexpr unsigned kFaultBounds = 4u;      // bounds-checked build: an index left its range
 
 // ---------------------------------------------------------------- geometry
 // An instance is an (nz,) ny x nx grid stored with row pitch P floats
@@ -88,7 +89,26 @@ struct Geom {
     int zct, zca;     // planes per CTA of the 3-D transport / advect (0: heuristic)
     unsigned nyt_mul; // ceil(2^32 / nyt), nyt = ceil(ny / 8): q = umulhi(n, nyt_mul) = n / nyt
                       // exactly for n * nyt < 2^32 (n < 65536, nyt <= 8192); 0 when nyt = 1
+    unsigned int* chk;  // the workspace status word (bounds-checked build: kFaultBounds)
 };
+
+// Bounds-checked build (META_CHECK_BOUNDS): v must lie in [lo, hi]; otherwise the
+// bounds bit is latched in the workspace status word and v is clamped into the
+// range, so that the access it indexes stays inside its buffer.  In the ordinary
+// build it returns v and costs nothing.
+__device__ __forceinline__ int chk_range(const Geom& g, int v, int lo, int hi) {
+#ifdef META_CHECK_BOUNDS
+    if (v < lo || v > hi) {
+        if (g.chk) atomicOr(g.chk, kFaultBounds);
+        v = v < lo ? lo : hi;
+    }
+#else
+    (void)g;
+    (void)lo;
+    (void)hi;
+#endif
+    return v;
+}
 
 // n / nyt for a grid index n of the pointwise kernels (see Geom::nyt_mul).
 __device__ __forceinline__ int div_nyt(const Geom& g, int n) {
@@ -190,6 +210,14 @@ __device__ __forceinline__ Foot1 foot1(int c, float d, int n) {
         r.f = d - fl;
         r.inside = true;
     }
+    return r;
+}
+
+// foot1 with the lower corner checked (bounds-checked build) against [0, n - 2],
+// the range every interpolation at a foot indexes.
+__device__ __forceinline__ Foot1 foot1g(const Geom& g, int c, float d, int n) {
+    Foot1 r = foot1(c, d, n);
+    r.i0 = chk_range(g, r.i0, 0, n - 2);
     return r;
 }
 

@@ -168,13 +168,13 @@ template <int NDIM>
 __device__ __forceinline__ Feet<NDIM> feet_of(const Geom& g, const Vox& v, const float* d) {
     Feet<NDIM> F;
     if constexpr (NDIM == 2) {
-        F.f[0] = foot1(v.y, d[0], g.ny);
-        F.f[1] = foot1(v.x, d[1], g.nx);
+        F.f[0] = foot1g(g, v.y, d[0], g.ny);
+        F.f[1] = foot1g(g, v.x, d[1], g.nx);
         F.base = gidx(g, 0, F.f[0].i0, F.f[1].i0);
     } else {
-        F.f[0] = foot1(v.z, d[0], g.nz);
-        F.f[1] = foot1(v.y, d[1], g.ny);
-        F.f[2] = foot1(v.x, d[2], g.nx);
+        F.f[0] = foot1g(g, v.z, d[0], g.nz);
+        F.f[1] = foot1g(g, v.y, d[1], g.ny);
+        F.f[2] = foot1g(g, v.x, d[2], g.nx);
         F.base = gidx(g, F.f[0].i0, F.f[1].i0, F.f[2].i0);
     }
     return F;

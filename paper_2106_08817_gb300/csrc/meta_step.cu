@@ -113,7 +113,7 @@ __device__ __forceinline__ void body_advect2d(const K& kb, Geom g, Coefs cf, int
                 {rn_cdiff(sU1[ui + ys], sU1[ui - yl]), rn_cdiff(sU1[ui + xs], sU1[ui - xl])}};
             jac = rn_jac_det<2>(A, dtrho);
         }
-        const Foot1 fy = foot1(y, d0, g.ny), fx = foot1(x, d1, g.nx);
+        const Foot1 fy = foot1g(g, y, d0, g.ny), fx = foot1g(g, x, d1, g.nx);
         const int ly = fy.i0 - (y0 - kAdvHalo), lx = fx.i0 - (x0 - kAdvHalo);
         float Iw, pw;
         if (ly >= 0 && ly + 1 < HI && lx >= 0 && lx + 1 < W) {
@@ -243,7 +243,7 @@ __device__ __forceinline__ void advect3d_voxel(const Geom& g, float rho, float m
     } else {
         fac = __fsub_rn(1.f, __fmul_rn(dt, __fmul_rn(-rho, du)));
     }
-    const Foot1 fz = foot1(z, d0, g.nz), fy = foot1(y, d1, g.ny), fx = foot1(x, d2, g.nx);
+    const Foot1 fz = foot1g(g, z, d0, g.nz), fy = foot1g(g, y, d1, g.ny), fx = foot1g(g, x, d2, g.nx);
     const float2 w = adv_interp(g, fz, fy, fx, z, y0, x0, sm1, s0, sp1, It, pt);
     const long long o = gidx(g, z, y, x);
     p1[o] = __fmul_rn(w.y, fac);
@@ -305,9 +305,9 @@ __device__ __forceinline__ void advect3d_pair(const Geom& g, float rho, float mu
     const float2 one = make_float2(1.f, 1.f);
     const float2 fac = fsub2(one, fmul2(make_float2(dt, dt),
                                         fmul2(make_float2(-rho, -rho), du)));
-    const Foot1 fza = foot1(z, d0.x, g.nz), fya = foot1(y, d1.x, g.ny), fxa = foot1(x, d2.x, g.nx);
-    const Foot1 fzb = foot1(z, d0.y, g.nz), fyb = foot1(y + 1, d1.y, g.ny),
-                fxb = foot1(x, d2.y, g.nx);
+    const Foot1 fza = foot1g(g, z, d0.x, g.nz), fya = foot1g(g, y, d1.x, g.ny), fxa = foot1g(g, x, d2.x, g.nx);
+    const Foot1 fzb = foot1g(g, z, d0.y, g.nz), fyb = foot1g(g, y + 1, d1.y, g.ny),
+                fxb = foot1g(g, x, d2.y, g.nx);
     const int kza = fza.i0 - (z - 1), kya = fya.i0 - (y0 - 1), kxa = fxa.i0 - (x0 - 4);
     const int kzb = fzb.i0 - (z - 1), kyb = fyb.i0 - (y0 - 1), kxb = fxb.i0 - (x0 - 4);
     const bool sa = kza >= 0 && kza + 1 < 3 && kya >= 0 && kya + 1 < kAH && kxa >= 0 &&
