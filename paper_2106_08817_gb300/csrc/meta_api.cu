@@ -282,14 +282,15 @@ bool encode_map(CUtensorMap* m, const Geom& g, int ndim, void* base, int nslices
 // 5-D tensor map over fields of a batch of pitched instances: dims {nx, ny,
 // nz, B, nfields}, field f of instance b at slice f * B + b; boxes of the 3-D
 // transport's plane window (40 x 18 x 1 x 1 x box_nf); zero fill outside.
-bool encode_map5(CUtensorMap* m, const Geom& g, void* base, int nfields, int box_nf) {
+bool encode_map5(CUtensorMap* m, const Geom& g, void* base, int nfields, int box_nf,
+                 int box_rows = 18) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[5] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
                                 (cuuint64_t)g.B, (cuuint64_t)nfields};
     const cuuint64_t strides[4] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.slab * 4,
                                    (cuuint64_t)g.inst * 4, (cuuint64_t)g.B * g.inst * 4};
-    const cuuint32_t box[5] = {40, 18, 1, 1, (cuuint32_t)box_nf};
+    const cuuint32_t box[5] = {40, (cuuint32_t)box_rows, 1, 1, (cuuint32_t)box_nf};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -384,8 +385,8 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
         ok &= encode_map5(&c->tmTr[0], g, c->REC, d + 4, 6);
         ok &= encode_map5(&c->tmTr[1], g, c->REC, d + 4, 1);
         ok &= encode_map5(&c->tmTr[2], g, c->states, 2 * L.nstate, 2);
-        ok &= encode_map5(&c->tmAdv[0], g, c->u, 3 * L.nu, 3);
-        c->tmAdv[1] = c->tmTr[2];
+        ok &= encode_map5(&c->tmAdv[0], g, c->u, 3 * L.nu, 3, kAdvRows + 2);
+        ok &= encode_map5(&c->tmAdv[1], g, c->states, 2 * L.nstate, 2, kAdvRows + 2);
     }
     return ok ? META_OK : META_ERR_UNSUPPORTED;
 }
@@ -822,7 +823,7 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
     if (L.ndim == 3) {
         out->lz = L.g.lz;
         out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 2, 2, 16);
-        out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 3, 2, 16);
+        out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 5, 2, kAdvRows);
     } else {
         out->lz = out->zc_transport = out->zc_advect = 0;
     }

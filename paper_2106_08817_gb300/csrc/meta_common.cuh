@@ -68,6 +68,10 @@ constexpr int kMaxLW = 256;
 // different instances do not queue on one L2 line.
 constexpr int kMaxdispStride = 32;
 
+// Rows of a 3-D advect CTA's column (two per thread); its staged window has a
+// one-row halo on each side.
+constexpr int kAdvRows = 12;
+
 // Fault / information bits latched in the workspace header.
 constexpr unsigned kFaultTmaTimeout = 1u;  // a bounded TMA wait ran out (fault)
 constexpr unsigned kInfoScatter = 2u;      // adjoint used the atomic scatter (large steps)

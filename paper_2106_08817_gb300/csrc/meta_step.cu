@@ -150,7 +150,7 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const 
 }
 #endif
 
-// 3-D advect: a CTA owns a 32 x 16 column over planes [zs, zs + zc) and
+// 3-D advect: a CTA owns a 32 x kAR (12) column over planes [zs, zs + zc) and
 // marches along z; each thread computes two adjacent rows (x, y0 + 2 ty) and
 // (x, y0 + 2 ty + 1).  Plane p of u (three components) and of I_t, p_t, with
 // a one-voxel y halo and x in [x0 - 4, x0 + 36), arrives by TMA (two tiled
@@ -160,8 +160,9 @@ k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const 
 // from planes p - 2 .. p.  Planes outside the volume are never read, so none
 // is copied for them.  Feet whose cell leaves the staged window (per-step
 // displacements of a voxel or more) read global memory.
-constexpr int kAW = 40, kAH = 18, kAPL = kAW * kAH;  // staged window (x, y) of a plane
-constexpr int kAUF = 2176;                           // u fields of a slot (3 x 720, 128-byte multiple)
+constexpr int kAR = kAdvRows;                         // rows of a CTA's column (two per thread)
+constexpr int kAW = 40, kAH = kAR + 2, kAPL = kAW * kAH;  // staged window (x, y) of a plane
+constexpr int kAUF = (3 * kAPL * 4 + 127) / 128 * 128 / 4;  // u fields of a slot, 128-byte multiple
 constexpr int kASlot = kAUF + 2 * kAPL;              // then I_t, p_t
 constexpr int kARing = 4;                            // plane slots
 constexpr size_t kAdvMarchSmem = 128 + (size_t)kARing * kASlot * sizeof(float);
@@ -351,7 +352,7 @@ __device__ __forceinline__ void body_advect3d(const K& kb, const CUtensorMap& tm
     const int x0 = (kb.bx() % nxc) * 32;
     const int zs = (kb.bx() / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = kb.by() * 16;
+    const int y0 = kb.by() * kAR;
     const int tx = kb.tx(), ty = kb.ty();
     const int tid = ty * kPX + tx;
     const int x = x0 + tx, ya = y0 + 2 * ty, yb = ya + 1;
@@ -642,9 +643,9 @@ cudaError_t launch_unpack(const Geom& g, int ndim, const float* sI, const float*
 cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const Slots& sl,
                           float* states, const float* u, unsigned int* maxdisp,
                           const CUtensorMap* maps, unsigned int* fault, cudaStream_t st) {
-    // 3-D: plane chunks of the 32 x 16 columns (3 CTAs per SM, 2 staged halo planes)
-    const int zc = ndim == 3 ? (g.zca > 0 ? g.zca : march_chunk(g, 3, 2, 16)) : 1;
-    const dim3 grid3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
+    // 3-D: plane chunks of the 32 x kAR columns (5 CTAs per SM, 2 staged halo planes)
+    const int zc = ndim == 3 ? (g.zca > 0 ? g.zca : march_chunk(g, 5, 2, kAR)) : 1;
+    const dim3 grid3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + kAR - 1) / kAR, g.B);
     if (std::vector<PRec>* r = recorder()) {
         PRec e{};
         e.kind = PK_ADVECT;
@@ -657,6 +658,7 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
             e.smem = kAdv2dSmem;
         } else {
             e.grid = grid3;
+            e.by = kAR / 2;
             e.smem = kAdvMarchSmem;
             e.a.zc = zc;
             e.ntm = 2;
@@ -685,8 +687,8 @@ cudaError_t launch_advect(const Geom& g, int ndim, const Coefs& c, int t, const 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kAdvMarchSmem);
         if (e != cudaSuccess) return e;
-        META_CHECK_LAUNCH(launch_k(kern, grid3, blk, kAdvMarchSmem, st, maps[0], maps[1], g, c, t,
-                                   sl, zc, states, maxdisp, fault));
+        META_CHECK_LAUNCH(launch_k(kern, grid3, dim3(kPX, kAR / 2), kAdvMarchSmem, st, maps[0],
+                                   maps[1], g, c, t, sl, zc, states, maxdisp, fault));
     }
     return cudaGetLastError();
 }
