@@ -71,6 +71,38 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
             tma_load_box<NDIM>(sM, &tmI, bar, x0 - HX, y0, z0, sliceI + (int)kb.bz());
         }
     }
+    // GRADP: items of four columns of one staged row (m is formed below).  Item idx
+    // -> row and first column; idx < 2^12, so the rounded float quotient is the
+    // exact integer one.
+    const int LW4 = LW / 4;
+    const int total = kRows * LW4;
+    const float inv_lw4 = 1.f / (float)LW4;
+    auto item_row = [&](int idx) { return (int)(((float)idx + 0.5f) * inv_lw4); };
+    // p at an item's four columns, read from global memory (not staged: the shared
+    // memory it would take keeps a third CTA off the SM); an item lies wholly inside
+    // or wholly outside the pitched row
+    auto load_p = [&](int idx) {
+        float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int row = item_row(idx);
+        const int c = 4 * (idx - row * LW4);
+        const int y = y0 + ((NDIM == 2) ? row : (row & 3));
+        const int z = z0 + ((NDIM == 2) ? 0 : (row >> 2));
+        const int xs = x0 - HX + c;
+        if (idx < total && y < g.ny && z < g.nz && xs >= 0 && xs < g.P)
+            p4 = ld4_ro<K>(pin + (long long)(sliceP + b) * g.inst + gidx(g, z, y, xs));
+        return p4;
+    };
+    // the p of the thread's first kPre items is requested before the wait for the
+    // I tile, so that the two latencies overlap
+    constexpr int kPre = 3;
+    float4 pre[kPre];
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) pre[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (GRADP) {
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) pre[i] = load_p(i * (int)kb.ndx() + tid);
+    }
+
     // Ordinary launch: every warp waits (bounded) itself and goes on as soon as the
     // tiles have landed; a wait that runs out raises s_fail, which every thread reads
     // after the barrier that ends the gradient phase (the plain pass has no later
@@ -93,18 +125,13 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
         // m_i = p * D_i I on the whole staged row range, four columns per
         // thread (finite everywhere; columns 0 and LW-1 only ever meet zero
         // taps, and there the missing neighbour is replaced by the column itself).
-        const int LW4 = LW / 4;
-        const int total = kRows * LW4;
-        const float inv_lw4 = 1.f / (float)LW4;
         const int lane = tid & 31;
         // the CTA has txw / 8 x 16 threads, so its last warp may hold 16 lanes
         const int wlast = min(31, (int)kb.ndx() - 1 - (tid & ~31));
         const unsigned wmask = wlast == 31 ? 0xffffffffu : ((2u << wlast) - 1u);
-        // a warp-uniform trip count: every lane takes part in the shuffles
-        for (int base = 0; base < total; base += kb.ndx()) {
+        auto form = [&](int base, const float4 p4) {
             const int idx = min(base + tid, total - 1);  // lanes past the end repeat the last
-            // idx < 2^12, so the rounded float quotient is the exact integer one
-            const int row = (int)(((float)idx + 0.5f) * inv_lw4);
+            const int row = item_row(idx);
             const int c = 4 * (idx - row * LW4);
             const int ty = (NDIM == 2) ? row : (row & 3);
             const int tz = (NDIM == 2) ? 0 : (row >> 2);
@@ -124,20 +151,13 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
             for (int a = 0; a < NDIM; ++a)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mo[a][j] = 0.f;
-            if (base + tid >= total) continue;
+            if (base + tid >= total) return;
             if (y < g.ny && z < g.nz) {
                 const float iv[6] = {c > 0 ? left : ic.x, ic.x, ic.y, ic.z, ic.w,
                                      c + 4 < LW ? right : ic.w};
                 const float4 yu = lds4(sI + (rI + (y < g.ny - 1 ? 1 : 0)) * LW + c);
                 const float4 yd = lds4(sI + (rI - (y > 0 ? 1 : 0)) * LW + c);
                 const float yuv[4] = {yu.x, yu.y, yu.z, yu.w}, ydv[4] = {yd.x, yd.y, yd.z, yd.w};
-                // p at the item's four columns, read from global memory (not staged:
-                // the shared memory it would take keeps a third CTA off the SM); an
-                // item lies wholly inside or wholly outside the pitched row
-                const int xs = x0 - HX + c;
-                float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (xs >= 0 && xs < g.P)
-                    p4 = ld4_ro<K>(pin + (long long)(sliceP + b) * g.inst + gidx(g, z, y, xs));
                 const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
                 float zuv[4] = {0.f, 0.f, 0.f, 0.f}, zdv[4] = {0.f, 0.f, 0.f, 0.f};
                 if constexpr (NDIM == 3) {
@@ -168,7 +188,14 @@ __device__ __forceinline__ void body_xpass(const K& kb, const CUtensorMap& tmI, 
             for (int a = 0; a < NDIM; ++a)
                 *reinterpret_cast<float4*>(sM + (a * kRows + row) * LW + c) =
                     make_float4(mo[a][0], mo[a][1], mo[a][2], mo[a][3]);
-        }
+        };
+        // (pre[]: the first kPre items' p); a warp-uniform trip count: every lane
+        // takes part in the shuffles
+        int base = 0;
+#pragma unroll
+        for (int i = 0; i < kPre; ++i, base += kb.ndx())
+            if (base < total) form(base, pre[i]);
+        for (; base < total; base += kb.ndx()) form(base, load_p(base + tid));
         kb.sync();
         if constexpr (!K::kPersistent) {
             if (s_fail) return;
