@@ -279,8 +279,8 @@ meta_status meta_noalloc_selftest_timeout(unsigned long long limit_ns, void* str
 typedef struct {
     int zc_transport; /* 3-D only; in [1, dims[0]] */
     int zc_advect;    /* 3-D only; in [1, dims[0]] */
-    int ly;           /* multiple of 16 in [16, 128] */
-    int lz;           /* 3-D only; multiple of 16 in [16, 128] */
+    int ly;           /* multiple of 16 in [16, 192], ly + roundup8(2 ceil(3 sigma) + 1) <= 256 */
+    int lz;           /* 3-D only; as ly */
     int txw;          /* multiple of 8 in [8, 256] whose staged row txw + 2 hx fits one
                          TMA box of 256 floats; hx, the x halo, is the least multiple
                          of 4 that is >= r + 1, >= r4 and >= kp - r4, with r =

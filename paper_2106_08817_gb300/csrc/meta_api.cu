@@ -199,6 +199,8 @@ Layout make_layout(const meta_problem* pr) {
 // Radius of the x pass's staged halo: r = ceil(3 sigma) rounded up to 4.
 int xpass_r(float sigma) { return (int)std::ceil(3.0 * (double)sigma); }
 int xpass_r4(float sigma) { return (xpass_r(sigma) + 3) / 4 * 4; }
+// Taps in the strided passes' loop: roundup(2r + 1, 8) (the TMA box holds L + kp rows).
+int strided_kp(float sigma) { return (2 * xpass_r(sigma) + 1 + 7) / 8 * 8; }
 
 void make_taps(float sigma, Taps* xpass, Taps* strided) {
     const int r = (int)std::ceil(3.0 * (double)sigma);
@@ -746,8 +748,11 @@ meta_status tuning_check(const meta_problem* prob, const meta_tuning* tun) {
     const int d = prob->ndim;
     const int nz = d == 3 ? prob->dims[0] : 1, ny = prob->dims[d - 2];
     auto len_ok = [](int v, int q, int mx) { return v == 0 || (v >= q && v <= mx && v % q == 0); };
-    if (!len_ok(tun->ly, kBA, 128) || !len_ok(tun->lz, kBA, 128) || !len_ok(tun->txw, kBX, 256))
+    if (!len_ok(tun->ly, kBA, kTAMax) || !len_ok(tun->lz, kBA, kTAMax) || !len_ok(tun->txw, kBX, 256))
         return META_ERR_INVALID_ARG;
+    // a strided tile and its taps are staged by one TMA box (<= 256 along the axis)
+    const int kp_s = strided_kp(prob->sigma);
+    if (tun->ly + kp_s > 256 || tun->lz + kp_s > 256) return META_ERR_INVALID_ARG;
     // the x pass stages rows of txw + 2 hx floats by one TMA box (<= 256)
     if (tun->txw && xpass_lw(tun->txw, xpass_r(prob->sigma), xpass_r4(prob->sigma)) > kMaxLW)
         return META_ERR_INVALID_ARG;
@@ -871,11 +876,15 @@ meta_status meta_autotune(const meta_problem* prob, const float* I0, const float
         *ms = tk[4];
         return META_OK;
     };
-    auto lens = [](int n, int q) {  // equal tiles of at most 48 .. 128
+    // equal tiles of at most 32 .. 192 (one warp holds two groups of kBA outputs, so
+    // multiples of 32 leave no idle half warp) that one TMA box can stage
+    const int kp_s = strided_kp(prob->sigma);
+    auto lens = [kp_s](int n, int q) {
         std::vector<int> v;
-        for (int m : {48, 64, 96, 128}) {
+        for (int m : {32, 48, 64, 96, 128, 160, 192}) {
             const int l = even_tile(n, m, q);
-            if (l <= 128 && std::find(v.begin(), v.end(), l) == v.end()) v.push_back(l);
+            if (l <= kTAMax && l + kp_s <= 256 && std::find(v.begin(), v.end(), l) == v.end())
+                v.push_back(l);
         }
         return v;
     };

@@ -19,7 +19,8 @@ constexpr int kBX = 8;         // x-pass: outputs per thread along x
 constexpr int kTX = 128;       // x-pass: largest tile width along x
 constexpr int kRows = 16;      // x-pass: rows per CTA (2-D: 16 y; 3-D: 4 z x 4 y)
 constexpr int kBA = 16;        // strided pass: outputs per thread along the axis
-constexpr int kTA = 128;       // strided pass: largest tile length along the axis
+constexpr int kTA = 128;       // strided pass: largest built-in tile length along the axis
+constexpr int kTAMax = 192;    // strided pass: largest tuned tile length (L + taps <= 256, one TMA box)
 constexpr int kTXS = 32;       // strided pass: columns per CTA
 // strided pass: one thread per column pair and group of kBA outputs along the
 // axis (L / kBA groups of 16 threads), rounded up to whole warps
@@ -89,7 +90,7 @@ struct Geom {
     int B;            // batch
     int nT;           // time steps T
     int txw;          // x-pass tile width (multiple of kBX, <= kTX)
-    int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTA)
+    int ly, lz;       // strided-pass tile lengths along y and z (multiples of kBA, <= kTAMax)
     int zct, zca;     // planes per CTA of the 3-D transport / advect (0: heuristic)
     unsigned nyt_mul; // ceil(2^32 / nyt), nyt = ceil(ny / 8): q = umulhi(n, nyt_mul) = n / nyt
                       // exactly for n * nyt < 2^32 (n < 65536, nyt <= 8192); 0 when nyt = 1

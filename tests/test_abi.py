@@ -131,7 +131,10 @@ def test_tuning_table_round_trip_and_validation(meta):
     # r = 18, r4 = 20, taps to 40 = r4 + 20)
     meta.set_tuning(dims, B, s, dict(txw=160))
     assert meta.tuning(dims, B, s)["txw"] == 160
-    for bad in (dict(ly=40), dict(ly=144), dict(txw=12), dict(zc_transport=161),
+    # strided tiles up to 192 whose window (tile + taps, 40 at sigma 6) one TMA box holds
+    meta.set_tuning(dims, B, s, dict(ly=192, lz=160))
+    assert (meta.tuning(dims, B, s)["ly"], meta.tuning(dims, B, s)["lz"]) == (192, 160)
+    for bad in (dict(ly=40), dict(ly=208), dict(txw=12), dict(zc_transport=161),
                 dict(lz=-16), dict(zc_advect=-1), dict(split=2),  # split <= batch (1 here)
                 dict(txw=224), dict(txw=264)):  # staged rows of 264 and 304 floats
         with pytest.raises(meta.MetaError):
@@ -139,6 +142,9 @@ def test_tuning_table_round_trip_and_validation(meta):
     with pytest.raises(meta.MetaError):  # sigma 18: halo 56, so 144 + 112 = 256 fits no wider
         meta.set_tuning(dims, B, 18.0, dict(txw=152))
     meta.set_tuning(dims, B, 18.0, dict(txw=144))
+    with pytest.raises(meta.MetaError):  # sigma 18: 112 taps, so 160 + 112 > 256
+        meta.set_tuning(dims, B, 18.0, dict(ly=160))
+    meta.set_tuning(dims, B, 18.0, dict(ly=144, lz=144))
     meta.set_tuning(dims, B, 18.0, None)
     with pytest.raises(meta.MetaError):
         meta.set_tuning((64, 64), 1, 2.0, dict(lz=16))  # 2-D problems have no z tiles
