@@ -311,7 +311,6 @@ template <int NDIM>
 __global__ void __launch_bounds__(256)
 k_cost_partials(Geom g, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ J, double* partials) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_cost_partials<HwBlk, NDIM>(HwBlk{}, g, sl, states, u, J, partials);
 }
 #endif
@@ -343,7 +342,6 @@ __device__ __forceinline__ void body_cost_final(const K& kb, int nblk, Coefs cf,
 __global__ void __launch_bounds__(256)
 k_cost_final(int nblk, Coefs cf, const double* __restrict__ partials, double* cost) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_cost_final<HwBlk>(HwBlk{}, nblk, cf, partials, cost);
 }
 #endif
@@ -377,7 +375,6 @@ template <int NDIM, bool FROM_J>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_init(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ gI1, const float* __restrict__ gp1, const unsigned int* __restrict__ maxdisp, float* rec, float* Ihp, float* php, float* rawI, float* rawP) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_init<HwBlk, NDIM, FROM_J>(HwBlk{}, g, cf, sl, states, u, gI1, gp1, maxdisp, rec, Ihp, php, rawI, rawP);
 }
 #endif
@@ -494,7 +491,6 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_records(Geom g, Coefs cf, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const float* __restrict__ rawI, const float* __restrict__ rawP, float* rec) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_records<HwBlk, NDIM>(HwBlk{}, g, cf, sl, states, u, rawI, rawP, rec);
 }
 #endif
@@ -649,7 +645,6 @@ __device__ __forceinline__ void body_adj_transport2d(const K& kb, Geom g, Coefs 
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_transport2d<HwBlk>(HwBlk{}, g, cf, t, sl, states, maxdisp, rec, vh, Ihp, php, fault);
 }
 #endif
@@ -940,7 +935,6 @@ __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensor
 __global__ void __launch_bounds__(kPX * kPY, 2)
 k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA, const __grid_constant__ CUtensorMap tmRecD, const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_transport3d<HwBlk>(HwBlk{}, tmRecA, tmRecD, tmSt, g, cf, t, sl, zc, states, maxdisp, rec, vh, Ihp, php, fault);
 }
 #endif
@@ -1104,7 +1098,6 @@ template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp2d(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_gradp2d<HwBlk, PDET>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
 }
 #endif
@@ -1311,7 +1304,6 @@ __device__ __forceinline__ void body_adj_gradp3_pair(const K& kb, Geom g, Coefs 
 __global__ void __launch_bounds__(kPX * kPY / 2)
 k_adj_gradp3_pair(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_gradp3_pair<HwBlk>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
 }
 #endif
@@ -1321,7 +1313,6 @@ template <int NDIM, bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_adj_gradp(Geom g, Coefs cf, int t, int mode, Slots sl, const float* __restrict__ states, const float* __restrict__ u, const unsigned int* __restrict__ maxdisp, const float* __restrict__ mh, float* Ihp, float* php, float* rec, float* rawI, float* rawP, float* out0, float* gI0) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_adj_gradp<HwBlk, NDIM, PDET>(HwBlk{}, g, cf, t, mode, sl, states, u, maxdisp, mh, Ihp, php, rec, rawI, rawP, out0, gI0);
 }
 #endif
@@ -1367,7 +1358,6 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_adj_jacT(Geom g, Coefs cf, Slots sl, const float* __restrict__ u, const float* __restrict__ rec,
            float* vh) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
@@ -1432,7 +1422,6 @@ k_euler_adj(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
             const float* __restrict__ u, const float* __restrict__ rawI,
             const float* __restrict__ rawP, float* Ihp, float* php, float* vh) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
@@ -1479,7 +1468,6 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_hybrid_p(Geom g, Coefs cf, Slots sl, const float* __restrict__ states,
            const float* __restrict__ u, const float* __restrict__ rawP, float* php, float* vh) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;

@@ -284,7 +284,6 @@ template <int NDIM, bool GRADP, int KC>
 __global__ void __launch_bounds__(512)
 k_xpass(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmP, const __grid_constant__ Taps taps, Geom g, int sliceI, int sliceP, const float* pin, int out_slice0, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_xpass<HwBlk, NDIM, GRADP, KC>(HwBlk{}, tmI, tmP, taps, g, sliceI, sliceP, pin, out_slice0, out, fault);
 }
 #endif
@@ -417,7 +416,6 @@ template <int NDIM, int AXIS, int KC>
 __global__ void __launch_bounds__(256)
 k_strided(const __grid_constant__ CUtensorMap tm, const __grid_constant__ Taps taps, Geom g, int in_slice0, int out_slice0, const float* __restrict__ scale, float scale_mul, float* __restrict__ out, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_strided<HwBlk, NDIM, AXIS, KC>(HwBlk{}, tm, taps, g, in_slice0, out_slice0, scale, scale_mul, out, fault);
 }
 #endif

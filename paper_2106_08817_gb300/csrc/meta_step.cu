@@ -35,7 +35,6 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_pack(Geom g, const float* __restrict__ I0, const float* __restrict__ p0, float* dI, float* dP) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_pack<HwBlk, NDIM>(HwBlk{}, g, I0, p0, dI, dP);
 }
 #endif
@@ -45,7 +44,6 @@ template <int NDIM>
 __global__ void __launch_bounds__(kPX * kPY)
 k_unpack(Geom g, const float* __restrict__ sI, const float* __restrict__ sP, float* I1, float* p1) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const long long o = (long long)v.b * g.inst + gidx(g, v.z, v.y, v.x);
@@ -145,7 +143,6 @@ template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect2d(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states, const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_advect2d<HwBlk, PDET>(HwBlk{}, g, cf, t, sl, states, u, maxdisp);
 }
 #endif
@@ -452,7 +449,6 @@ template <bool PDET>
 __global__ void __launch_bounds__(kPX * kPY)
 k_advect3d(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS, Geom g, Coefs cf, int t, Slots sl, int zc, float* __restrict__ states, unsigned int* __restrict__ maxdisp, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     body_advect3d<HwBlk, PDET>(HwBlk{}, tmU, tmS, g, cf, t, sl, zc, states, maxdisp, fault);
 }
 #endif
@@ -471,7 +467,6 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_euler(Geom g, Coefs cf, int t, Slots sl, float* __restrict__ states,
         const float* __restrict__ u, unsigned int* __restrict__ maxdisp) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     float dmax = 0.f;  // hybrid: max |d| of the CTA (the window of its adjoint transport)
     if (v.ok) {
@@ -531,7 +526,6 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_deform(Geom g, Coefs cf, int su, const float* __restrict__ u, const float* __restrict__ win,
          float* __restrict__ wout) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
@@ -564,7 +558,6 @@ __global__ void __launch_bounds__(kPX * kPY)
 k_deform_out(Geom g, const float* __restrict__ w, float* __restrict__ phi,
              float* __restrict__ jac) {
     pdl_wait();  // the previous kernel's writes are visible from here on
-    pdl_trigger();
     const Vox v = vox_of<NDIM>(g);
     if (!v.ok) return;
     const int b = v.b;
