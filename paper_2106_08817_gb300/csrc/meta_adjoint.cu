@@ -649,7 +649,7 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
 }
 #endif
 
-// 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x 16 column of nodes
+// 3-D S^T and v^ of adjoint step t.  A CTA owns a 32 x kTransRows (8) column of nodes
 // over planes [zs, zs + zc) and marches along z; each thread owns the two
 // adjacent nodes (x, 2 ty) and (x, 2 ty + 1) of the column.
 //   R = 1: plane p of the records and of I_t, p_t over the column grown by one
@@ -672,11 +672,13 @@ k_adj_transport2d(Geom g, Coefs cf, int t, Slots sl, const float* __restrict__ s
 //     (branch-free; zero weights add exact zeros); the nodes at p-1 are then
 //     complete and take y^, D^T div^ from the staged planes p-2 .. p.
 //   R > 1: transport_node for each node of the column.
-constexpr int kMW = 40, kMHY = 18, kMPL = kMW * kMHY;    // staged window (x, y) of a plane
-constexpr int kMRX = 34, kMRY = 18, kMPR = kMRX * kMRY;  // source region of a plane
+constexpr int kMTY = kTransRows / 2;                     // threads along y (two rows each)
+constexpr int kMThreads = kPX * kMTY;
+constexpr int kMW = 40, kMHY = kTransRows + 2, kMPL = kMW * kMHY;  // staged window (x, y) of a plane
+constexpr int kMRX = 34, kMRY = kTransRows + 2, kMPR = kMRX * kMRY;  // source region of a plane
 constexpr int kMFA = 6;                                  // ring A: cell f_z f_y f_x I^' p~^
 constexpr int kMSA = kMFA * kMPL;                        // ring A slot (floats)
-constexpr int kMBI = 736, kMBP = kMBI + kMPL;            // ring B: div^ at 0, I_t, p_t
+constexpr int kMBI = (kMPL + 31) / 32 * 32, kMBP = kMBI + kMPL;  // ring B: div^ at 0, I_t, p_t
 constexpr int kMSB = kMBP + kMPL;                        // ring B slot (floats, 128-byte multiple)
 constexpr int kMSlotsA = 3, kMSlotsB = 4;
 constexpr size_t kMarchSmem =
@@ -690,7 +692,7 @@ static_assert((kMSA * 4) % 128 == 0 && (kMSB * 4) % 128 == 0 && (kMBI * 4) % 128
 __device__ __forceinline__ void march_pack(const float* raw, float4* q, float* pp, const Geom& g,
                                            int x0, int y0, int z, int tid) {
     const bool zin = z >= 0 && z < g.nz;
-    for (int i = tid; i < kMPR; i += kPX * kPY) {
+    for (int i = tid; i < kMPR; i += kMThreads) {
         const int ry = i / kMRX, rx = i - ry * kMRX;
         const int sx = x0 - 1 + rx, sy = y0 - 1 + ry;
         const int wi = ry * kMW + rx + 3;
@@ -784,7 +786,7 @@ __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensor
     const int x0 = (kb.bx() % nxc) * 32;
     const int zs = (kb.bx() / nxc) * zc;
     const int ze = min(zs + zc, g.nz);
-    const int y0 = kb.by() * 16;
+    const int y0 = kb.by() * kTransRows;
     const int R = gather_radius(maxdisp, t, g.B, b);
     const int tx = kb.tx(), ty = kb.ty();
     const int tid = ty * kPX + tx;
@@ -932,7 +934,7 @@ __device__ __forceinline__ void body_adj_transport3d(const K& kb, const CUtensor
 
 
 #ifndef META_BODIES_ONLY
-__global__ void __launch_bounds__(kPX * kPY, 2)
+__global__ void __launch_bounds__(kMThreads, 4)
 k_adj_transport3d(const __grid_constant__ CUtensorMap tmRecA, const __grid_constant__ CUtensorMap tmRecD, const __grid_constant__ CUtensorMap tmSt, Geom g, Coefs cf, int t, Slots sl, int zc, const float* __restrict__ states, const unsigned int* __restrict__ maxdisp, const float* __restrict__ rec, float* vh, float* Ihp, float* php, unsigned int* fault) {
     pdl_wait();  // the previous kernel's writes are visible from here on
     body_adj_transport3d<HwBlk>(HwBlk{}, tmRecA, tmRecD, tmSt, g, cf, t, sl, zc, states, maxdisp, rec, vh, Ihp, php, fault);
@@ -1623,13 +1625,14 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
         e.kind = PK_TRANS;
         e.ndim = ndim;
         e.bx = kPX;
-        e.by = kPY;
+        e.by = ndim == 2 ? kPY : kMTY;
         if (ndim == 2) {
             e.grid = gather_grid2d(g);
             e.smem = kTr2dSmem;
         } else {
-            const int zc = g.zct > 0 ? g.zct : march_chunk(g, 2, 2, 16);
-            e.grid = dim3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
+            const int zc = g.zct > 0 ? g.zct : march_chunk(g, 4, 2, kTransRows);
+            e.grid = dim3(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc),
+                          (g.ny + kTransRows - 1) / kTransRows, g.B);
             e.smem = kMarchSmem;
             e.a.zc = zc;
             e.ntm = 3;
@@ -1649,18 +1652,18 @@ cudaError_t launch_adj_transport(const Geom& g, int ndim, const Coefs& c, int t,
         r->push_back(e);
         return cudaSuccess;
     }
-    const dim3 blk(kPX, kPY);
     if (ndim == 2) {
-        META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), blk, kTr2dSmem, st, g, c, t, sl,
-                                   states, maxdisp, rec, vh, Ihp, php, fault));
+        META_CHECK_LAUNCH(launch_k(k_adj_transport2d, gather_grid2d(g), dim3(kPX, kPY), kTr2dSmem, st,
+                                   g, c, t, sl, states, maxdisp, rec, vh, Ihp, php, fault));
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_adj_transport3d,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kMarchSmem);
         if (e != cudaSuccess) return e;
-        const int zc = g.zct > 0 ? g.zct : march_chunk(g, 2, 2, 16);
-        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc), (g.ny + 15) / 16, g.B);
-        META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, blk, kMarchSmem, st, maps[0], maps[1],
+        const int zc = g.zct > 0 ? g.zct : march_chunk(g, 4, 2, kTransRows);
+        const dim3 grid(((g.nx + 31) / 32) * ((g.nz + zc - 1) / zc),
+                        (g.ny + kTransRows - 1) / kTransRows, g.B);
+        META_CHECK_LAUNCH(launch_k(k_adj_transport3d, grid, dim3(kPX, kMTY), kMarchSmem, st, maps[0], maps[1],
                                    maps[2], g, c, t, sl, zc, states, maxdisp, rec, vh, Ihp, php,
                                    fault));
     }

@@ -282,10 +282,10 @@ bool encode_map(CUtensorMap* m, const Geom& g, int ndim, void* base, int nslices
 }
 
 // 5-D tensor map over fields of a batch of pitched instances: dims {nx, ny,
-// nz, B, nfields}, field f of instance b at slice f * B + b; boxes of the 3-D
-// transport's plane window (40 x 18 x 1 x 1 x box_nf); zero fill outside.
+// nz, B, nfields}, field f of instance b at slice f * B + b; boxes of a 3-D
+// marching kernel's plane window (40 x box_rows x 1 x 1 x box_nf); zero fill outside.
 bool encode_map5(CUtensorMap* m, const Geom& g, void* base, int nfields, int box_nf,
-                 int box_rows = 18) {
+                 int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[5] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
@@ -384,9 +384,9 @@ meta_status setup(const meta_problem* pr, void* ws, size_t ws_bytes, void* strea
         ok &= encode_map(&c->tmSAy, g, 3, c->SA, d * B, kTXS, g.ly + c->ts.kp, 1);
         ok &= encode_map(&c->tmSBz, g, 3, c->SB, d * B, kTXS, 1, g.lz + c->ts.kp);
         ok &= encode_map(&c->tmSVx, g, 3, c->SV, d * B, LW, 4, 4);
-        ok &= encode_map5(&c->tmTr[0], g, c->REC, d + 4, 6);
-        ok &= encode_map5(&c->tmTr[1], g, c->REC, d + 4, 1);
-        ok &= encode_map5(&c->tmTr[2], g, c->states, 2 * L.nstate, 2);
+        ok &= encode_map5(&c->tmTr[0], g, c->REC, d + 4, 6, kTransRows + 2);
+        ok &= encode_map5(&c->tmTr[1], g, c->REC, d + 4, 1, kTransRows + 2);
+        ok &= encode_map5(&c->tmTr[2], g, c->states, 2 * L.nstate, 2, kTransRows + 2);
         ok &= encode_map5(&c->tmAdv[0], g, c->u, 3 * L.nu, 3, kAdvRows + 2);
         ok &= encode_map5(&c->tmAdv[1], g, c->states, 2 * L.nstate, 2, kAdvRows + 2);
     }
@@ -827,7 +827,7 @@ meta_status meta_tuning_get(const meta_problem* prob, meta_tuning* out) {
     out->split = (find_tuning(prob, &tn) && tn.split > 0) ? tn.split : 1;
     if (L.ndim == 3) {
         out->lz = L.g.lz;
-        out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 2, 2, 16);
+        out->zc_transport = L.g.zct > 0 ? L.g.zct : march_chunk(L.g, 4, 2, kTransRows);
         out->zc_advect = L.g.zca > 0 ? L.g.zca : march_chunk(L.g, 5, 2, kAdvRows);
     } else {
         out->lz = out->zc_transport = out->zc_advect = 0;

@@ -72,6 +72,9 @@ constexpr int kMaxdispStride = 32;
 // Rows of a 3-D advect CTA's column (two per thread); its staged window has a
 // one-row halo on each side.
 constexpr int kAdvRows = 12;
+// Rows of a 3-D transport CTA's column (two nodes per thread, so 32 x kTransRows / 2
+// threads); its staged windows have a one-row halo on each side.
+constexpr int kTransRows = 8;
 
 // Fault / information bits latched in the workspace header.
 constexpr unsigned kFaultTmaTimeout = 1u;  // a bounded TMA wait ran out (fault)
