@@ -781,6 +781,12 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
     # 20 or 12, the staged row up to the 256-float TMA box)
     meta.set_tuning(dims, B, sigma, dict(txw=144) if len(dims) == 2 else dict(txw=72))
     c3, g3 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    # strided tiles longer than the extent (192 and 160 outputs, most of their groups
+    # past the volume) and short ones (32)
+    meta.set_tuning(dims, B, sigma, dict(ly=192) if len(dims) == 2 else dict(ly=192, lz=160))
+    c4, g4 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
+    meta.set_tuning(dims, B, sigma, dict(ly=32) if len(dims) == 2 else dict(ly=32, lz=32))
+    c5, g5 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
     chosen = meta.autotune(cuda(I0), cuda(J), cuda(p0), *args)
     assert meta.tuning(dims, B, sigma) == chosen
     c2, g2 = meta.cost_and_grad(cuda(I0), cuda(J), cuda(p0), *args)
@@ -793,6 +799,8 @@ def test_tile_shapes_and_autotuner_do_not_change_results(meta, dims, B, T, sigma
     assert torch.equal(c0, c1) and torch.equal(g0, g1)
     assert torch.equal(c0, c2) and torch.equal(g0, g2)
     assert torch.equal(c0, c3) and torch.equal(g0, g3)
+    assert torch.equal(c0, c4) and torch.equal(g0, g4)
+    assert torch.equal(c0, c5) and torch.equal(g0, g5)
     assert torch.equal(c0, plan.cost) and torch.equal(g0, plan.grad)
     assert plan.ws.status() & 1 == 0
 
