@@ -48,7 +48,8 @@ def model_bytes_per_voxel_step(d: int) -> int:
 # This implementation's own algorithmic bytes per voxel-step: one forward step
 # (xpass_m, d-1 strided passes, advect) and one adjoint step (transport,
 # xpass_adj, d-1 strided passes, gradp); with checkpoint stride k, the forward
-# steps recomputed in the adjoint (all but the last segment) on top.
+# steps recomputed in the adjoint (all but the last nbuf segments, nbuf = 2 where two
+# sets of segment slots are still smaller than the whole trajectory, else 1) on top.
 def own_bytes_per_voxel_step(d: int, T: int, k: int) -> float:
     fwd = (bytes_per_voxel("xpass_m", d) + (d - 1) * bytes_per_voxel("strided_fwd", d)
            + bytes_per_voxel("advect", d))
@@ -56,7 +57,9 @@ def own_bytes_per_voxel_step(d: int, T: int, k: int) -> float:
            + (d - 1) * bytes_per_voxel("strided_adj", d) + bytes_per_voxel("adj_gradp", d))
     rec = 0.0
     if 1 < k < T:
-        last = T - (T - 1) // k * k  # steps of the last segment (not recomputed)
+        nseg = (T + k - 1) // k
+        nbuf = 2 if 2 * (nseg + 2 * k) + d * (2 * k + 1) < 2 * (T + 1) + d * T else 1
+        last = T - (nseg - nbuf) * k  # steps of the last nbuf segments (not recomputed)
         rec = (T - last) / T * fwd
     return fwd + adj + rec
 

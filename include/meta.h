@@ -73,8 +73,10 @@ typedef struct {
     int T;        /* number of time steps, dt = 1/T, in [1, 4096] */
     float sigma;  /* std (voxels) of the Gaussian RKHS kernel, in (0, 18] */
     int ckpt_stride; /* 0 or 1: keep every state (fastest); k in [2, T-1]: keep every
-                        k-th state and recompute each segment of k steps during the
-                        adjoint (step checkpointing), trading k forward steps of
+                        k-th state plus the states of two segments of k steps (one
+                        where two would not be smaller than the whole trajectory),
+                        and recompute every other segment from its checkpoint during
+                        the adjoint (step checkpointing), trading k forward steps of
                         compute per segment for memory */
     int p_update;    /* momentum update of a step: META_P_UPDATE_DIV (0, the default),
                         p' = p~ (1 - dt div v), the first-order Jacobian of the backtrack
@@ -139,8 +141,9 @@ meta_status meta_shoot_deform(const meta_problem* prob, const float* I0, const f
  * gradient of a scalar with respect to I_T and p_T (gp1 may be NULL: zero),
  * writes its gradient with respect to p0 (gp0) and, if gI0 is not NULL, I0.
  * This is the discrete transpose of every step, run from t = T-1 down to 0.
- * With ckpt_stride > 1 it first recomputes the last segment from its
- * checkpoint, so it may be called again on the same trajectory. */
+ * With ckpt_stride > 1 it first recomputes the segments that the forward left in
+ * place (the last one or two) from their checkpoints, so it may be called again on
+ * the same trajectory. */
 meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const float* rho,
                                const float* gI1, const float* gp1, float* gI0, float* gp0,
                                void* ws, size_t ws_bytes, void* stream);

@@ -61,6 +61,7 @@ struct Layout {
     int pdet;     // momentum update p~ det(Id - dt Dv) (else p~ (1 - dt div v))
     int scheme;   // META_SCHEME_SL / _EULER / _HYBRID
     int nseg;     // segments of k steps (k > 0)
+    int nbuf;     // sets of segment slots (k > 0): 2 where that still saves memory, else 1
     int nstate;   // state slots
     int nu;       // u slots
     size_t off_fault, off_maxdisp, off_partials;
@@ -70,13 +71,20 @@ struct Layout {
 
     // Keeping every state: slot = time.  With stride k: state t of segment s
     // (t in [s k, s k + k]) lives in checkpoint slot s when t = s k, else in
-    // segment slot nseg + (t - s k) - 1; u_t in slot t % k, u_0 in slot k.
+    // segment slot nseg + (s % nbuf) k + (t - s k) - 1: nbuf sets of k segment
+    // slots, taken by the segments in turn, so that the forward leaves its last
+    // nbuf segments in place; u_t (t > 0) in slot ((t / k) % nbuf) k + t % k, u_0 in
+    // slot nbuf k.
     int state_slot(int t, int s) const {
         if (k == 0) return t;
-        return t == s * k ? s : nseg + (t - s * k) - 1;
+        return t == s * k ? s : nseg + (s % nbuf) * k + (t - s * k) - 1;
     }
-    int u_slot(int t) const { return k == 0 ? t : (t == 0 ? k : t % k); }
+    int u_slot(int t) const {
+        return k == 0 ? t : (t == 0 ? nbuf * k : ((t / k) % nbuf) * k + t % k);
+    }
     int seg_of(int t) const { return k == 0 ? 0 : t / k; }
+    // Segments the adjoint re-runs from their checkpoints: all but the last nbuf.
+    bool recomputed(int s) const { return k != 0 && s < seg_of(T - 1) - (nbuf - 1); }
     int seg_end(int s) const { return k == 0 ? T : (s * k + k < T ? s * k + k : T); }
     // slot written by the first forward pass for time t + 1
     int forward_out_slot(int t) const {
@@ -157,8 +165,13 @@ Layout make_layout(const meta_problem* pr) {
     // a stride of 0, 1 or >= T keeps every state
     L.k = (pr->ckpt_stride > 1 && pr->ckpt_stride < pr->T) ? pr->ckpt_stride : 0;
     L.nseg = L.k ? (pr->T + L.k - 1) / L.k : 1;
-    L.nstate = L.k ? L.nseg + L.k : pr->T + 1;
-    L.nu = L.k ? L.k + 1 : pr->T;
+    // two sets of segment slots (the last two segments need no recompute) where
+    // that layout is still smaller than keeping every state, else one
+    L.nbuf = 1;
+    if (L.k && 2 * (L.nseg + 2 * L.k) + d * (2 * L.k + 1) < 2 * (pr->T + 1) + d * pr->T)
+        L.nbuf = 2;
+    L.nstate = L.k ? L.nseg + L.nbuf * L.k : pr->T + 1;
+    L.nu = L.k ? L.nbuf * L.k + 1 : pr->T;
     // cost partial sums: one CTA of 8 warps per 8 rows, at most 1024 per instance (a
     // 3-D volume's CTAs take several rows per warp, and the final sum reads fewer)
     long long nblk = ((long long)g.nz * g.ny + 7) / 8;
@@ -592,12 +605,13 @@ meta_status run_adjoint(Ctx& c, const Coefs& cf, int mode, float* out0, float* g
         if (t == 0) {
             m = mode;
         } else {
-            if (L.k && t == s * L.k) {
-                // step t-1 ends segment s-1: that segment comes back from its
-                // checkpoint now, after this step's transport and blur and before its
-                // gradp, which then builds the record of step t-1 as in every other
-                // step (the recompute writes the segment slots, u slots, SA and SB,
-                // none of which this step still reads)
+            if (L.k && t == s * L.k && L.recomputed(s - 1)) {
+                // step t-1 ends segment s-1, which (unless it is one of the last two,
+                // still in place) comes back from its checkpoint now, after this
+                // step's transport and blur and before its gradp, which then builds
+                // the record of step t-1 as in every other step (the recompute writes
+                // the other parity's segment and u slots, SA and SB, none of which
+                // this step still reads)
                 const meta_status st = recompute_segment(c, cf, s - 1);
                 if (st != META_OK) return st;
             }
@@ -621,12 +635,11 @@ meta_status run_adjoint_other(Ctx& c, const Coefs& cf, int mode, float* out0, fl
     const Layout& L = c.L;
     const Geom& g = L.g;
     const int d = L.ndim, B = g.B;
-    const int s_last = L.seg_of(L.T - 1);
     float* rawI = c.RAW;
     float* rawP = raw_p(c);
     for (int t = L.T - 1; t >= 0; --t) {
         const int s = L.seg_of(t);
-        if (L.k && s != s_last && t == L.seg_end(s) - 1) {
+        if (L.recomputed(s) && t == L.seg_end(s) - 1) {
             const meta_status st = recompute_segment(c, cf, s);
             if (st != META_OK) return st;
         }
@@ -1057,10 +1070,13 @@ meta_status meta_shoot_adjoint(const meta_problem* prob, const float* mu, const 
     s = setup(prob, ws, ws_bytes, stream, &c);
     if (s != META_OK) return s;
     const Coefs cf{mu, rho, nullptr, 1.f / (float)c.L.T, c.L.pdet, c.L.scheme};
-    // With checkpoints, an earlier adjoint left another segment in the segment
-    // slots: bring the last one back so that the adjoint can be called again.
+    // With checkpoints, an earlier adjoint left other segments in the segment
+    // slots: bring the last nbuf back so that the adjoint can be called again.
     if (c.L.k) {
-        s = recompute_segment(c, cf, c.L.seg_of(c.L.T - 1));
+        const int s_last = c.L.seg_of(c.L.T - 1);
+        for (int q = s_last - c.L.nbuf + 1 < 0 ? 0 : s_last - c.L.nbuf + 1;
+             q <= s_last && s == META_OK; ++q)
+            s = recompute_segment(c, cf, q);
         if (s != META_OK) return s;
     }
     META_LAUNCH(META_K_ADJ_INIT, c.st,

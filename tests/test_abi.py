@@ -101,12 +101,14 @@ def test_workspace_size_grows_with_T_and_batch(meta):
 
 
 def test_checkpointing_shrinks_the_workspace(meta):
-    """ckpt_stride k keeps ceil(T/k) checkpoints plus one segment instead of T+1 states."""
+    """ckpt_stride k keeps ceil(T/k) checkpoints plus two segments (2k states, 2k + 1
+    velocity fields) instead of T+1 states and T velocity fields."""
     full = meta.workspace_size((64, 64, 64), 1, 20, 5.0)
     k5 = meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=5)
     f = 64 * 64 * 64 * 4
     assert full >= (2 * 21 + 3 * 20) * f
-    assert k5 <= (2 * (4 + 5) + 3 * 6 + 4 * 3 + 8 + 1) * f
+    assert (2 * (4 + 10) + 3 * 11) * f <= k5 <= (2 * (4 + 10) + 3 * 11 + 4 * 3 + 8 + 1) * f
+    assert k5 < full
     assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=1) == full
     assert meta.workspace_size((64, 64, 64), 1, 20, 5.0, ckpt=20) == full
     pr = meta._problem(3, (8, 8, 8), 1, 4, 1.0, -1)

@@ -23,10 +23,18 @@ def test_own_bytes_add_the_recomputed_forward_steps():
     assert (keep2, keep3) == (196.0, 296.0)
     fwd3 = (bench.bytes_per_voxel("xpass_m", 3) + 2 * bench.bytes_per_voxel("strided_fwd", 3)
             + bench.bytes_per_voxel("advect", 3))
-    # T = 20, k = 5: segments 0..2 are recomputed (15 of 20 steps), the last is not
-    assert bench.own_bytes_per_voxel_step(3, 20, 5) == pytest.approx(keep3 + 15 / 20 * fwd3)
-    # T = 10, k = 4: segments [0,4), [4,8) recomputed, [8,10) kept: 8 of 10 steps
-    assert bench.own_bytes_per_voxel_step(3, 10, 4) == pytest.approx(keep3 + 8 / 10 * fwd3)
+    # T = 20, k = 5: segments 0 and 1 are recomputed (10 of 20 steps), the last two
+    # stay in place after the forward
+    assert bench.own_bytes_per_voxel_step(3, 20, 5) == pytest.approx(keep3 + 10 / 20 * fwd3)
+    # T = 10, k = 4: segment [0,4) recomputed, [4,8) and [8,10) kept: 4 of 10 steps
+    assert bench.own_bytes_per_voxel_step(3, 10, 4) == pytest.approx(keep3 + 4 / 10 * fwd3)
+    # 2-D, T = 7, k = 3: two sets of segment slots would not be smaller than the whole
+    # trajectory, so one set: [0,3), [3,6) recomputed, [6,7) kept: 6 of 7 steps
+    fwd2 = (bench.bytes_per_voxel("xpass_m", 2) + bench.bytes_per_voxel("strided_fwd", 2)
+            + bench.bytes_per_voxel("advect", 2))
+    assert bench.own_bytes_per_voxel_step(2, 7, 3) == pytest.approx(keep2 + 6 / 7 * fwd2)
+    # T = 40, k = 5: two sets, segments 0..5 recomputed (30 of 40 steps)
+    assert bench.own_bytes_per_voxel_step(3, 40, 5) == pytest.approx(keep3 + 30 / 40 * fwd3)
     # strides of 0, 1 or >= T keep the whole trajectory
     for k in (0, 1, 20, 25):
         assert bench.own_bytes_per_voxel_step(3, 20, k) == keep3

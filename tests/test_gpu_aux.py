@@ -108,8 +108,9 @@ def test_gradient_descent_follows_the_oracle(meta):
 
 
 def test_phase_ranges_of_a_checkpointed_call(meta):
-    """T = 7 with checkpoint stride 3: segments [0,3), [3,6), [6,7); the adjoint
-    re-runs the two segments before the last, newest first."""
+    """T = 7 with checkpoint stride 3: segments [0,3), [3,6), [6,7); one set of segment
+    slots (two would not be smaller than the whole trajectory), so the adjoint re-runs
+    the two segments before the last, newest first."""
     dims, B, T, sigma = (24, 28), 1, 7, 2.0
     I0, J, p0 = problem(dims, B, 780)
     ws = meta.Workspace(dims, B, T, sigma, "cuda", 3)
